@@ -1,0 +1,226 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only ``tests/``, the package's ``smoke()`` check and the benchmark's
+CPU-baseline leg may import this package; the library itself never does, and
+the oracle shares no code with the CUDA path.  The arithmetic lives in
+``pyhst_oracle.c`` (plain loops, double precision, each function citing the
+passage of the PyHST2 paper it follows); this module only marshals numpy
+arrays to it.
+
+Conventions: images are [ny, nx] (row i, column j); sinograms are
+[n_angles, n_bins]; the detector coordinate of pixel (i, j) at angle th is
+t = (j - cx) cos th + (i - cy) sin th + axis(th) in bin units.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pyhst_oracle.c")
+_LIB = os.path.join(_HERE, "_pyhst_oracle.so")
+_lib = None
+
+D = ctypes.c_double
+I64 = ctypes.c_int64
+PD = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("n_angles", I64), ("n_bins", I64), ("nx", I64), ("ny", I64),
+                ("angles", PD), ("axis", PD), ("cx", D), ("cy", D), ("pixel_size", D)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.orc_tv.restype = D
+        L.orc_rof_gap.restype = D
+        L.orc_energy.restype = D
+        L.orc_power_iteration.restype = D
+        _lib = L
+    return _lib
+
+
+def _c(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(PD)
+
+
+def num_threads() -> int:
+    """Threads the OpenMP loops of the oracle use."""
+    import multiprocessing
+    return int(os.environ.get("OMP_NUM_THREADS", multiprocessing.cpu_count()))
+
+
+# ------------------------------------------------------------------ pipeline
+def normalise(I, F, D_):
+    """Sec. 2.3 flat/dark correction, p = -ln((I-D)/(F-D)); one slice:
+    I [n_rows, n_bins], F and D [n_bins]."""
+    I, pI = _c(I)
+    F, pF = _c(np.broadcast_to(F, I.shape[-1:]))
+    D_, pD = _c(np.broadcast_to(D_, I.shape[-1:]))
+    p = np.empty_like(I)
+    lib().orc_normalise(pI, pF, pD, I64(I.shape[0]), I64(I.shape[1]), p.ctypes.data_as(PD))
+    return p
+
+
+def ramlak_filter(p):
+    """Ram-Lak filtered rows, q[m] = sum_k h(m-k) p[k] (Sec. 2.3)."""
+    p, pp = _c(p)
+    q = np.empty_like(p)
+    lib().orc_ramlak_filter(pp, I64(p.shape[0]), I64(p.shape[1]), q.ctypes.data_as(PD))
+    return q
+
+
+def _centre(n, c):
+    return (n - 1) / 2.0 if c is None else float(c)
+
+
+def backproject(q, angles, axis, nx, ny, weight=1.0, cx=None, cy=None):
+    """weight * sum_a L(q_a, t_a(i, j)) (Sec. 2.3)."""
+    q, pq = _c(q)
+    na, nb = q.shape
+    ang, pa = _c(np.asarray(angles, dtype=np.float64).reshape(na))
+    ax, px = _c(np.broadcast_to(np.asarray(axis, dtype=np.float64), (na,)))
+    img = np.empty((ny, nx))
+    lib().orc_backproject(pq, I64(na), I64(nb), pa, px, I64(nx), I64(ny),
+                          D(_centre(nx, cx)), D(_centre(ny, cy)), D(weight), img.ctypes.data_as(PD))
+    return img
+
+
+def project(img, angles, axis, n_bins, scale=1.0, cx=None, cy=None):
+    """scale * (transpose of the unweighted back-projector) applied to img."""
+    img, pi = _c(img)
+    ny, nx = img.shape
+    na = len(angles)
+    ang, pa = _c(np.asarray(angles, dtype=np.float64).reshape(na))
+    ax, px = _c(np.broadcast_to(np.asarray(axis, dtype=np.float64), (na,)))
+    sino = np.empty((na, n_bins))
+    lib().orc_project(pi, I64(na), I64(n_bins), pa, px, I64(nx), I64(ny),
+                      D(_centre(nx, cx)), D(_centre(ny, cy)), D(scale), sino.ctypes.data_as(PD))
+    return sino
+
+
+def fbp_weight(n_angles, pixel_size):
+    """pi / (n_angles * s): uniform angular weight over 180 degrees."""
+    return math.pi / (n_angles * pixel_size)
+
+
+def fbp_from_sinogram(p, angles, axis, nx, ny, pixel_size, cx=None, cy=None):
+    """Filter then back-project a normalised sinogram p [n_angles, n_bins]."""
+    q = ramlak_filter(p)
+    return backproject(q, angles, axis, nx, ny, fbp_weight(len(angles), pixel_size), cx, cy)
+
+
+def fbp_from_raw(raw, flat, dark, angles, axis, nx, ny, pixel_size, cx=None, cy=None):
+    """Full per-slice path: normalise, filter, back-project.  raw is the
+    slice's sinogram of counts [n_angles, n_bins], flat/dark [n_bins]."""
+    return fbp_from_sinogram(normalise(raw, flat, dark), angles, axis, nx, ny, pixel_size, cx, cy)
+
+
+# ------------------------------------------------------------------ TV / FISTA
+def grad(x):
+    x, px = _c(x)
+    g1, g2 = np.empty_like(x), np.empty_like(x)
+    lib().orc_grad(px, I64(x.shape[0]), I64(x.shape[1]), g1.ctypes.data_as(PD), g2.ctypes.data_as(PD))
+    return g1, g2
+
+
+def div(p1, p2):
+    p1, a = _c(p1)
+    p2, b = _c(p2)
+    d = np.empty_like(p1)
+    lib().orc_div(a, b, I64(p1.shape[0]), I64(p1.shape[1]), d.ctypes.data_as(PD))
+    return d
+
+
+def tv(x):
+    """Eq. 2."""
+    x, px = _c(x)
+    return lib().orc_tv(px, I64(x.shape[0]), I64(x.shape[1]))
+
+
+def tv_prox(z, lam, n_inner, tau=0.125, p=None):
+    """prox of lam*TV by Chambolle's fixed point; returns (x, p1, p2)."""
+    z, pz = _c(z)
+    ny, nx = z.shape
+    p1 = np.zeros_like(z) if p is None else np.array(p[0], dtype=np.float64)
+    p2 = np.zeros_like(z) if p is None else np.array(p[1], dtype=np.float64)
+    x = np.empty_like(z)
+    lib().orc_tv_prox(pz, I64(ny), I64(nx), D(lam), D(tau), I64(n_inner),
+                      p1.ctypes.data_as(PD), p2.ctypes.data_as(PD), x.ctypes.data_as(PD))
+    return x, p1, p2
+
+
+def rof_gap(z, lam, p1, p2):
+    z, pz = _c(z)
+    p1, a = _c(p1)
+    p2, b = _c(p2)
+    return lib().orc_rof_gap(pz, I64(z.shape[0]), I64(z.shape[1]), D(lam), a, b)
+
+
+class Geometry:
+    """One slice's geometry for the solver functions."""
+
+    def __init__(self, angles, axis, n_bins, nx, ny, pixel_size, cx=None, cy=None):
+        self.angles = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
+        self.axis = np.ascontiguousarray(np.broadcast_to(np.asarray(axis, dtype=np.float64),
+                                                         self.angles.shape))
+        self.n_bins, self.nx, self.ny = int(n_bins), int(nx), int(ny)
+        self.pixel_size = float(pixel_size)
+        self.cx, self.cy = _centre(nx, cx), _centre(ny, cy)
+
+    def _c(self):
+        return _Geom(len(self.angles), self.n_bins, self.nx, self.ny,
+                     self.angles.ctypes.data_as(PD), self.axis.ctypes.data_as(PD),
+                     self.cx, self.cy, self.pixel_size)
+
+    def P(self, x):
+        return project(x, self.angles, self.axis, self.n_bins, self.pixel_size, self.cx, self.cy)
+
+    def PT(self, y):
+        return backproject(y, self.angles, self.axis, self.nx, self.ny, self.pixel_size, self.cx, self.cy)
+
+
+def energy(g: Geometry, sino, x, beta):
+    """Eq. 3: 1/2 ||sino - P x||^2 + beta TV(x)."""
+    sino, ps = _c(sino)
+    x, px = _c(x)
+    gc = g._c()
+    return lib().orc_energy(ctypes.byref(gc), ps, px, D(beta))
+
+
+def power_iteration(g: Geometry, v0, n_it=50):
+    """Largest eigenvalue of P^T P from start vector v0 [ny, nx]."""
+    v = np.array(v0, dtype=np.float64, copy=True)
+    gc = g._c()
+    lam = lib().orc_power_iteration(ctypes.byref(gc), v.ctypes.data_as(PD), I64(n_it))
+    return lam, v
+
+
+def fista(g: Geometry, sino, beta, L, n_iter, n_inner=20, tau=0.125, use_fista=True, x0=None):
+    """ISTA/FISTA on Eq. 3; returns (x, energy history [n_iter])."""
+    sino, ps = _c(sino)
+    x = np.zeros((g.ny, g.nx)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    e = np.empty(n_iter)
+    gc = g._c()
+    lib().orc_fista(ctypes.byref(gc), ps, D(beta), D(L), I64(n_iter), I64(n_inner), D(tau),
+                    ctypes.c_int(1 if use_fista else 0), x.ctypes.data_as(PD), e.ctypes.data_as(PD))
+    return x, e
