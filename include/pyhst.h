@@ -1,0 +1,174 @@
+/*
+ * pyhst.h — C ABI of the B300 (sm_103a) parallel-beam reconstruction library.
+ *
+ * The calls follow the problem statement of the PyHST2 paper (Mirone et al.):
+ * raw radiographies with flat ("beam profile") and dark ("detector noise")
+ * fields and a per-projection rotation-axis position and angle (Sec. 2.1),
+ * dark/flat correction and rearrangement into one sinogram per detector row
+ * (Sec. 2.3), filtered back-projection (Sec. 2.3), the forward projector used
+ * by the iterative methods (Sec. 2.3, last paragraph), and the TV-penalised
+ * least-squares problem of Eq. 3 solved by ISTA/FISTA (Sec. 3.1).
+ *
+ * Conventions shared by every call
+ *   - Images are row-major [ny][nx] float32; pixel (row i, column j).
+ *   - Sinograms are row-major [n_angles][n_bins] float32 (one row per angle).
+ *   - Detector coordinate of pixel (i, j) at angle index a, in bin units:
+ *         t = (j - cx) cos(angles[a]) + (i - cy) sin(angles[a]) + axis[a]
+ *     and bin b is centred at t = b.  Linear interpolation between bins,
+ *     zero outside [0, n_bins).
+ *   - Every pointer passed to a call is DEVICE memory unless stated, owned by
+ *     the caller; the library allocates nothing on these paths.  Scratch
+ *     memory is the caller's `workspace` of `ws_bytes` bytes, sized with
+ *     pyhst_workspace_size(); it must be 256-byte aligned.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) and returns a status; nothing synchronises the
+ *     host.  Calls sharing a workspace must be ordered on one stream.
+ *   - Errors: a negative status; pyhst_last_error() gives a message (per host
+ *     thread).  Argument errors are detected before anything is launched.
+ */
+#ifndef PYHST_H
+#define PYHST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pyhst_stream_t; /* same type as cudaStream_t */
+
+/* Status codes. */
+enum {
+    PYHST_OK = 0,
+    PYHST_ERR_INVALID_ARG = -1,  /* sizes <= 0, NULL pointers, bad enums, unsupported pad */
+    PYHST_ERR_CUDA = -2,         /* a CUDA launch or runtime call failed (message has it) */
+    PYHST_ERR_WORKSPACE = -3,    /* workspace NULL, too small or misaligned */
+    PYHST_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
+    PYHST_ERR_NUMERIC = -5       /* non-finite energy / step size */
+};
+
+/* Geometry of a stack of n_slices slices that share angles and axis
+ * (Sec. 2.1: rotation axis displacement and angle given per projection).
+ *   angles [n_angles]  DEVICE float32, radians (any order, any values)
+ *   axis   [n_angles]  DEVICE float32, detector position of the rotation axis
+ *                      at each projection, in bin units
+ *   cx, cy            image centre in pixel-index units ((nx-1)/2, (ny-1)/2
+ *                      for a centred grid)
+ *   pixel_size        s: detector bin = pixel = s in physical units
+ * Limits: 1 <= n_angles <= 65535, 1 <= n_bins <= 16384, 1 <= nx, ny <= 16384. */
+typedef struct {
+    int32_t n_angles;
+    int32_t n_bins;
+    int32_t nx;
+    int32_t ny;
+    int32_t n_slices;
+    const float *angles;
+    const float *axis;
+    float cx;
+    float cy;
+    float pixel_size;
+} pyhst_geometry;
+
+/* Input data kinds of pyhst_fbp. */
+typedef enum {
+    PYHST_U16_RAW = 0,   /* uint16 counts; normalised with flat and dark     */
+    PYHST_F32_RAW = 1,   /* float32 counts; normalised with flat and dark    */
+    PYHST_F32_SINO = 2,  /* float32 -ln(I/I0) already normalised             */
+    PYHST_F16_SINO = 3,  /* IEEE half sinogram, converted to float32 on load */
+    PYHST_BF16_SINO = 4  /* bfloat16 sinogram, converted to float32 on load  */
+} pyhst_input_t;
+
+typedef enum { PYHST_RAMLAK = 0 } pyhst_filter_t;
+
+/* Operation selectors of pyhst_workspace_size(). */
+enum { PYHST_OP_FBP = 0, PYHST_OP_BACKPROJECT = 1, PYHST_OP_PROJECT = 2, PYHST_OP_TV_SOLVE = 3 };
+
+/* Workspace bytes one call of operation `op` needs for geometry `g` (host
+ * pointer; the angle and axis pointers are not read).  For PYHST_OP_FBP the
+ * size is for the default padding and min(n_slices, 4) slices per pass
+ * (pyhst_fbp_workspace_size gives other choices); pyhst_fbp uses as many
+ * slices per pass as the workspace holds, down to one.
+ * Returns 0 for invalid arguments. */
+size_t pyhst_workspace_size(const pyhst_geometry *g, int op);
+
+/* Workspace bytes of pyhst_fbp with padding pad_len (0: the default) that
+ * filters `slices_per_pass` slices per pass (clamped to [1, n_slices]).
+ * Returns 0 for invalid arguments. */
+size_t pyhst_fbp_workspace_size(const pyhst_geometry *g, int32_t pad_len, int32_t slices_per_pass);
+
+/* Filtered back-projection of n_slices slices (Sec. 2.3).
+ * For each slice z, angle a and bin b the input value is
+ *     data[z * slice_stride + a * angle_stride + b]      (strides in elements)
+ * so a raw radiography stack [n_angles][n_slices][n_bins] is read in place
+ * with slice_stride = n_bins, angle_stride = n_slices * n_bins (the sinogram
+ * of a detector row is a strided view; Sec. 2.3, rearrangement into
+ * sinograms).  For *_RAW kinds, flat and dark are [n_slices][n_bins] float32
+ * (averaged fields, Sec. 2.3) and p = -ln((I - D) / (F - D)) with p = 0 where
+ * F - D <= 0 and the ratio clamped below at 1e-6; for *_SINO kinds flat and
+ * dark are ignored (may be NULL).  Each row is Ram-Lak filtered (linear
+ * convolution with h(0) = 1/4, h(odd n) = -1/(pi n)^2, h(even n) = 0,
+ * computed as an FFT of length pad_len; pad_len = 0 picks the smallest power
+ * of two >= 2 n_bins; otherwise pad_len must be a power of two in
+ * [2 n_bins, 16384]), then back-projected with weight pi / (n_angles *
+ * pixel_size).  out: [n_slices][ny][nx] float32, overwritten. */
+int pyhst_fbp(const pyhst_geometry *g, int input_type, const void *data,
+              int64_t slice_stride, int64_t angle_stride,
+              const float *flat, const float *dark, int filter, int32_t pad_len,
+              float *out, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* Back-projection (Sec. 2.3) of n_slices sinograms [n_slices][n_angles][n_bins]
+ * into images [n_slices][ny][nx]:
+ *     img[i][j] = weight * sum_a L(sino_a, t_a(i, j))
+ * (weight = pi / (n_angles * pixel_size) for FBP, pixel_size for the adjoint
+ * of pyhst_project).  img is overwritten. */
+int pyhst_backproject(const pyhst_geometry *g, const float *sino, float *img, float weight,
+                      void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* Forward projection, the exact transpose of the unweighted back-projector
+ * scaled by pixel_size (line integrals in physical units; the projector the
+ * iterative methods use, Sec. 2.3 and Eq. 1):
+ *     sino[a][b] = pixel_size * sum_{i,j} img[i][j] * max(0, 1 - |t_a(i,j) - b|)
+ * img [n_slices][ny][nx] -> sino [n_slices][n_angles][n_bins], overwritten. */
+int pyhst_project(const pyhst_geometry *g, const float *img, float *sino,
+                  void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* Options of the TV-penalised solve (Eq. 3, Sec. 3.1). */
+typedef struct {
+    float beta;          /* weight of TV(x) in Eq. 3 (>= 0)                         */
+    int32_t n_iter;      /* outer ISTA/FISTA iterations (>= 1)                      */
+    int32_t n_inner;     /* Chambolle dual steps of each TV prox (>= 1)             */
+    float tau;           /* Chambolle step (0 < tau <= 1/4; 1/8 is the safe bound)  */
+    int32_t use_fista;   /* 1: FISTA momentum; 0: ISTA                              */
+    int32_t warm_start;  /* 1: x holds the start iterate; 0: start from zeros       */
+    double lipschitz;    /* L >= ||P||^2; 0: estimate 1.01 * lambda_max(P^T P)       */
+    int32_t n_power_iter;/* power iterations of the estimate (from the all-ones image) */
+} pyhst_tv_opts;
+
+/* Solve x = argmin 1/2 ||sino - P x||^2 + beta TV(x) (Eq. 3) for each of the
+ * n_slices slices of g, with P = pyhst_project's operator and TV the
+ * isotropic total variation of Eq. 2 (forward differences, Neumann
+ * boundary).  Each outer iteration takes a gradient step of length 1/L and
+ * the prox of (beta/L) TV by n_inner Chambolle steps from a zero dual field.
+ *   sino   [n_slices][n_angles][n_bins]
+ *   x      [n_slices][ny][nx]  in: start (if warm_start), out: last iterate
+ *   energy [n_slices][n_iter] float64 DEVICE or NULL: Eq. 3 at every iterate
+ *   lipschitz_out  DEVICE float64 [n_slices] or NULL: the L that was used. */
+int pyhst_tv_solve(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts,
+                   float *x, double *energy, double *lipschitz_out,
+                   void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* Workspace bytes of pyhst_tv_solve for a given option set (n_inner does not
+ * matter; n_iter does not matter). */
+size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_tv_opts *opts);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *pyhst_last_error(void);
+
+/* Library version string. */
+const char *pyhst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PYHST_H */

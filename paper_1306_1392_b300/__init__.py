@@ -1,0 +1,248 @@
+"""B300 (sm_103a) parallel-beam reconstruction: PyHST2's per-slice hot path.
+
+Thin Python binding of the C ABI in include/pyhst.h.  Every function has the
+name of the C entry point it calls and only marshals arguments: tensors are
+checked (CUDA, dtype, contiguity, shape) and their device pointers, the
+caller-owned workspace and PyTorch's current stream are passed through.
+Every step of the computation runs in the library's CUDA kernels; there is
+no CPU path.
+
+Conventions (the library's): images [n_slices, ny, nx]; sinograms
+[n_slices, n_angles, n_bins]; raw radiography stacks [n_angles, n_slices,
+n_bins]; detector coordinate t = (j - cx) cos th + (i - cy) sin th + axis(th).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SINO,  # noqa: F401
+                   PYHST_OP_BACKPROJECT, PYHST_OP_FBP, PYHST_OP_PROJECT, PYHST_OP_TV_SOLVE, PYHST_RAMLAK,
+                   PYHST_U16_RAW)
+
+__all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_backproject", "pyhst_project",
+           "pyhst_tv_solve", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
+           "pyhst_version", "library_path"]
+
+
+class PyhstError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"pyhst status {code}: {message}")
+        self.code = code
+
+
+def library_path() -> str:
+    return L.LIB_PATH
+
+
+def pyhst_last_error() -> str:
+    return L.lib.pyhst_last_error().decode()
+
+
+def pyhst_version() -> str:
+    return L.lib.pyhst_version().decode()
+
+
+def _check(rc):
+    if rc != 0:
+        raise PyhstError(rc, pyhst_last_error())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _cuda(t, name, dtypes):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+@dataclass
+class Geometry:
+    """Angles and axis positions are float32 CUDA tensors [n_angles]."""
+    angles: torch.Tensor
+    axis: torch.Tensor
+    n_bins: int
+    nx: int
+    ny: int
+    pixel_size: float
+    cx: float = None
+    cy: float = None
+
+    def __post_init__(self):
+        _cuda(self.angles, "angles", (torch.float32,))
+        _cuda(self.axis, "axis", (torch.float32,))
+        if self.axis.shape != self.angles.shape or self.angles.dim() != 1:
+            raise ValueError("angles and axis must be 1-D tensors of the same length")
+
+    @property
+    def n_angles(self) -> int:
+        return int(self.angles.shape[0])
+
+    def c(self, n_slices: int = 1) -> L.pyhst_geometry:
+        cx = (self.nx - 1) / 2.0 if self.cx is None else self.cx
+        cy = (self.ny - 1) / 2.0 if self.cy is None else self.cy
+        return L.pyhst_geometry(self.n_angles, self.n_bins, self.nx, self.ny, n_slices,
+                                self.angles.data_ptr(), self.axis.data_ptr(), cx, cy, self.pixel_size)
+
+
+@dataclass
+class TvOptions:
+    beta: float
+    n_iter: int = 200
+    n_inner: int = 20
+    tau: float = 0.125
+    use_fista: bool = True
+    warm_start: bool = False
+    lipschitz: float = 0.0
+    n_power_iter: int = 50
+
+    def c(self) -> L.pyhst_tv_opts:
+        return L.pyhst_tv_opts(self.beta, self.n_iter, self.n_inner, self.tau, int(bool(self.use_fista)),
+                               int(bool(self.warm_start)), self.lipschitz, self.n_power_iter)
+
+
+def pyhst_fbp_workspace_size(geom: Geometry, n_slices: int = 1, pad_len: int = 0, slices_per_pass: int = 4) -> int:
+    g = geom.c(n_slices)
+    return int(L.lib.pyhst_fbp_workspace_size(ctypes.byref(g), pad_len, slices_per_pass))
+
+
+def pyhst_workspace_size(geom: Geometry, op: int, n_slices: int = 1) -> int:
+    g = geom.c(n_slices)
+    return int(L.lib.pyhst_workspace_size(ctypes.byref(g), op))
+
+
+def pyhst_tv_workspace_size(geom: Geometry, opts: TvOptions, n_slices: int = 1) -> int:
+    g, o = geom.c(n_slices), opts.c()
+    return int(L.lib.pyhst_tv_workspace_size(ctypes.byref(g), ctypes.byref(o)))
+
+
+def _workspace(nbytes, device, workspace):
+    if workspace is None:
+        return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    return workspace
+
+
+def _stack3(t, name):
+    return t.unsqueeze(0) if t.dim() == 2 else t
+
+
+_KINDS = {"u16_raw": (PYHST_U16_RAW, torch.uint16), "f32_raw": (PYHST_F32_RAW, torch.float32),
+          "f32_sino": (PYHST_F32_SINO, torch.float32), "f16_sino": (PYHST_F16_SINO, torch.float16),
+          "bf16_sino": (PYHST_BF16_SINO, torch.bfloat16)}
+
+
+def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
+              pad_len: int = 0, out=None, workspace=None, ws_bytes: int = None,
+              slices_per_pass: int = 4) -> torch.Tensor:
+    """Filtered back-projection of every slice in ``data``.
+
+    ``layout`` "projections": data [n_angles, n_slices, n_bins] (a raw
+    radiography stack, read in place through strides); "sinograms": data
+    [n_slices, n_angles, n_bins].  Default: projections for raw kinds,
+    sinograms otherwise.  flat/dark [n_slices, n_bins] float32 for raw kinds.
+    Without a ``workspace`` one is allocated for ``slices_per_pass`` slices.
+    """
+    code, dt = _KINDS[kind]
+    _cuda(data, "data", (dt,))
+    raw = kind.endswith("raw")
+    layout = layout or ("projections" if raw else "sinograms")
+    if data.dim() == 2:
+        data = data.unsqueeze(1 if layout == "projections" else 0)
+    if layout == "projections":
+        na, ns, nb = data.shape
+        s_stride, a_stride = nb, ns * nb
+    elif layout == "sinograms":
+        ns, na, nb = data.shape
+        s_stride, a_stride = na * nb, nb
+    else:
+        raise ValueError(f"unknown layout {layout}")
+    if na != geom.n_angles or nb != geom.n_bins:
+        raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
+    if raw:
+        _cuda(flat, "flat", (torch.float32,))
+        _cuda(dark, "dark", (torch.float32,))
+        if flat.shape != (ns, nb) or dark.shape != (ns, nb):
+            raise ValueError("flat/dark must be [n_slices, n_bins]")
+    if out is None:
+        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    need = L.lib.pyhst_fbp_workspace_size(ctypes.byref(g), pad_len, slices_per_pass)
+    ws = _workspace(need, data.device, workspace)
+    nbytes = ws.numel() * ws.element_size() if ws_bytes is None else ws_bytes
+    _check(L.lib.pyhst_fbp(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
+                           PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), nbytes, _stream()))
+    return out
+
+
+def pyhst_backproject(geom: Geometry, sino: torch.Tensor, weight: float, out=None, workspace=None):
+    """img = weight * sum_a L(sino_a, t_a); sino [n_slices, n_angles, n_bins]."""
+    sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")
+    ns = sino.shape[0]
+    if tuple(sino.shape[1:]) != (geom.n_angles, geom.n_bins):
+        raise ValueError("sinogram shape does not match the geometry")
+    if out is None:
+        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    need = L.lib.pyhst_workspace_size(ctypes.byref(g), PYHST_OP_BACKPROJECT)
+    ws = _workspace(need, sino.device, workspace)
+    _check(L.lib.pyhst_backproject(ctypes.byref(g), _ptr(sino), _ptr(out), float(weight), _ptr(ws),
+                                   ws.numel(), _stream()))
+    return out
+
+
+def pyhst_project(geom: Geometry, img: torch.Tensor, out=None, workspace=None):
+    """sino = pixel_size * A img, A the transpose of the unweighted back-projector."""
+    img = _stack3(_cuda(img, "img", (torch.float32,)), "img")
+    ns = img.shape[0]
+    if tuple(img.shape[1:]) != (geom.ny, geom.nx):
+        raise ValueError("image shape does not match the geometry")
+    if out is None:
+        out = torch.empty((ns, geom.n_angles, geom.n_bins), dtype=torch.float32, device=img.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    need = L.lib.pyhst_workspace_size(ctypes.byref(g), PYHST_OP_PROJECT)
+    ws = _workspace(need, img.device, workspace)
+    _check(L.lib.pyhst_project(ctypes.byref(g), _ptr(img), _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def pyhst_tv_solve(geom: Geometry, sino: torch.Tensor, opts: TvOptions, x=None, energy: bool = True,
+                   workspace=None):
+    """Eq. 3 by ISTA/FISTA for each slice; returns (x, energy [n_slices, n_iter]
+    float64 or None, lipschitz [n_slices] float64)."""
+    sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")
+    ns = sino.shape[0]
+    if tuple(sino.shape[1:]) != (geom.n_angles, geom.n_bins):
+        raise ValueError("sinogram shape does not match the geometry")
+    if x is None:
+        x = torch.zeros((ns, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    _cuda(x, "x", (torch.float32,))
+    e = torch.empty((ns, opts.n_iter), dtype=torch.float64, device=sino.device) if energy else None
+    lip = torch.empty((ns,), dtype=torch.float64, device=sino.device)
+    g, o = geom.c(ns), opts.c()
+    need = L.lib.pyhst_tv_workspace_size(ctypes.byref(g), ctypes.byref(o))
+    ws = _workspace(need, sino.device, workspace)
+    _check(L.lib.pyhst_tv_solve(ctypes.byref(g), _ptr(sino), ctypes.byref(o), _ptr(x), _ptr(e), _ptr(lip),
+                                _ptr(ws), ws.numel(), _stream()))
+    return x, e, lip
+
+
+def fbp_weight(n_angles: int, pixel_size: float) -> float:
+    """pi / (n_angles * s), the FBP angular weight over 180 degrees."""
+    return math.pi / (n_angles * pixel_size)

@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "pyhst.h"
+
+namespace pyhst {
+
+// Per-angle geometry, computed on the device at the start of every call from
+// the caller's float32 angle and axis arrays: cos/sin in float64 (used for the
+// per-tile reference coordinate) and their float32 roundings (used for the
+// small tile-local offsets).
+struct __align__(16) AngleInfo {
+    double c, s;      // cos(theta), sin(theta)
+    double axis;      // rotation-axis position, bins
+    float cf, sf;     // float32 roundings of c and s
+};
+
+// ----------------------------------------------------------------- errors
+int fail(int code, const char *fmt, ...);   // records the message, returns code
+int cuda_status(const char *what);          // PYHST_OK or PYHST_ERR_CUDA after a launch
+int check_geometry(const pyhst_geometry *g);
+
+// ----------------------------------------------------------------- workspace
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+    char *base;
+    size_t cap, off;
+    Carver(void *b, size_t c) : base(static_cast<char *>(b)), cap(c), off(0) {}
+    template <class T> T *take(size_t n) {
+        off = align_up(off);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+    bool ok() const { return off <= cap; }
+};
+inline size_t angle_table_bytes(int n_angles) { return align_up(sizeof(AngleInfo) * n_angles); }
+
+// ----------------------------------------------------------------- launchers
+// Fill `tab` [n_angles] from the caller's arrays.
+int launch_angle_table(const float *angles, const float *axis, int n_angles, AngleInfo *tab,
+                       cudaStream_t st);
+
+// Source of back-projected rows: plain sinogram, or the residual a - b of two
+// sinograms (used by the iterative solver's gradient step).
+struct BpSource {
+    const float *a;          // [n_slices][n_angles][n_bins]
+    const float *b;          // NULL, or subtracted from a
+};
+int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img,
+                       float weight, cudaStream_t st);
+
+// Projector: img [n_slices][ny][nx] -> sino [n_slices][n_angles][n_bins],
+// scaled by `scale`; `xt` is scratch for the transposed slice stack
+// ([n_slices][nx][ny] floats).
+int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
+                   float scale, float *xt, cudaStream_t st);
+size_t project_scratch_bytes(const pyhst_geometry *g);
+
+// ----------------------------------------------------------------- device helpers
+// floor(u) for 0 <= u < 2^22 in one add rounded toward -inf: the sum with
+// 1.5 * 2^23 has unit spacing, so its low mantissa bits hold floor(u).
+constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;
+
+__device__ __forceinline__ float add_rd(float a, float b) {
+    float r;
+    asm("add.rm.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ float2 lds64(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+}  // namespace pyhst

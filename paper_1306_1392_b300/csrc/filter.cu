@@ -1,0 +1,211 @@
+// Flat/dark normalisation fused into the Ram-Lak ramp filter (Sec. 2.3).
+//
+// For each detector row (slice z, angle a) the kernel loads the raw values,
+// forms p = -ln((I - D) / (F - D)) (p = 0 where F - D <= 0; ratio clamped
+// below at 1e-6), zero-pads to P, convolves circularly with the Ram-Lak
+// kernel h periodised on [-P/2, P/2) and keeps the first n_bins outputs.  For
+// P >= 2 n_bins this is exactly the linear convolution
+//   q[m] = sum_k h(m - k) p[k],  h(0) = 1/4, h(odd n) = -1/(pi n)^2, h(even n) = 0.
+//
+// Two real rows ride in one complex FFT (row A real, row B imaginary); since
+// the filter spectrum H is real and even, the inverse transform returns
+// (A * h) + i (B * h) with no unpacking.  The forward transform is radix-2
+// decimation in frequency (natural order in, bit-reversed order out), the
+// spectrum is multiplied in bit-reversed order, and the inverse is decimation
+// in time (bit-reversed in, natural out), so no permutation pass is needed.
+// The whole padded row pair lives in shared memory (P * 8 bytes).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pyhst {
+namespace {
+
+__global__ void twiddle_kernel(int P, float2 *__restrict__ tw, double *__restrict__ costab) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) {
+        double s, c;
+        sincospi(2.0 * (double)k / (double)P, &s, &c);
+        costab[k] = c;
+        if (k < P / 2) tw[k] = make_float2((float)c, (float)-s);   // exp(-2 pi i k / P)
+    }
+}
+
+// H[k] = sum_{n=-P/2}^{P/2-1} h(n) cos(2 pi k n / P) = 1/4 + 2 sum_{odd n < P/2} h(n) cos(...)
+// stored at bit-reversed positions with the inverse-FFT factor 1/P folded in.
+__global__ void spectrum_kernel(int P, int logP, const double *__restrict__ costab,
+                                float *__restrict__ hrev) {
+    const int k = blockIdx.x;   // frequency 0..P/2
+    double acc = 0.0;
+    for (int n = 1 + 2 * threadIdx.x; n < P / 2; n += 2 * blockDim.x) {
+        const long long m = ((long long)k * n) % P;
+        acc += -1.0 / (M_PI * M_PI * (double)n * (double)n) * costab[m];
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float H = (float)((0.25 + 2.0 * red[0]) / (double)P);
+        hrev[__brev(k) >> (32 - logP)] = H;
+        if (k > 0 && k < P / 2) hrev[__brev(P - k) >> (32 - logP)] = H;
+    }
+}
+
+template <int kKind>
+__device__ __forceinline__ float load_p(const void *data, int64_t idx, float F, float D) {
+    if (kKind == PYHST_U16_RAW || kKind == PYHST_F32_RAW) {
+        const float I = (kKind == PYHST_U16_RAW) ? (float)static_cast<const uint16_t *>(data)[idx]
+                                                 : static_cast<const float *>(data)[idx];
+        const float den = F - D;
+        if (!(den > 0.0f)) return 0.0f;
+        const float r = fmaxf((I - D) / den, 1e-6f);
+        return -logf(r);
+    } else if (kKind == PYHST_F32_SINO) {
+        return static_cast<const float *>(data)[idx];
+    } else if (kKind == PYHST_F16_SINO) {
+        return __half2float(static_cast<const __half *>(data)[idx]);
+    } else {
+        return __bfloat162float(static_cast<const __nv_bfloat16 *>(data)[idx]);
+    }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// One CTA filters rows 2*blockIdx.x and 2*blockIdx.x+1 of the chunk; row r is
+// (slice z0 + r / n_angles, angle r % n_angles).
+template <int kKind>
+__global__ void filter_kernel(const void *__restrict__ data, int64_t slice_stride, int64_t angle_stride,
+                              const float *__restrict__ flat, const float *__restrict__ dark, int z0,
+                              int n_rows, int n_angles, int n_bins, int P, int logP,
+                              const float2 *__restrict__ tw, const float *__restrict__ hrev,
+                              float *__restrict__ q) {
+    extern __shared__ float2 z[];
+    const int rA = 2 * blockIdx.x, rB = rA + 1;
+    const bool hasB = rB < n_rows;
+    const int zA = z0 + rA / n_angles, aA = rA % n_angles;
+    const int zB = z0 + rB / n_angles, aB = rB % n_angles;
+    const int64_t baseA = (int64_t)zA * slice_stride + (int64_t)aA * angle_stride;
+    const int64_t baseB = (int64_t)zB * slice_stride + (int64_t)aB * angle_stride;
+    const bool raw = (kKind == PYHST_U16_RAW || kKind == PYHST_F32_RAW);
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        float va = 0.0f, vb = 0.0f;
+        if (k < n_bins) {
+            float FA = 0.0f, DA = 0.0f, FB = 0.0f, DB = 0.0f;
+            if (raw) {
+                FA = flat[(size_t)zA * n_bins + k];
+                DA = dark[(size_t)zA * n_bins + k];
+            }
+            va = load_p<kKind>(data, baseA + k, FA, DA);
+            if (hasB) {
+                if (raw) {
+                    FB = flat[(size_t)zB * n_bins + k];
+                    DB = dark[(size_t)zB * n_bins + k];
+                }
+                vb = load_p<kKind>(data, baseB + k, FB, DB);
+            }
+        }
+        z[k] = make_float2(va, vb);
+    }
+    __syncthreads();
+    const int half = P >> 1;
+    // forward: decimation in frequency
+    for (int lh = logP - 1; lh >= 0; --lh) {
+        const int h = 1 << lh;
+        for (int bt = threadIdx.x; bt < half; bt += blockDim.x) {
+            const int j = bt & (h - 1);
+            const int i0 = ((bt >> lh) << (lh + 1)) | j;
+            const float2 u = z[i0], v = z[i0 + h];
+            z[i0] = make_float2(u.x + v.x, u.y + v.y);
+            z[i0 + h] = cmul(make_float2(u.x - v.x, u.y - v.y), tw[j << (logP - 1 - lh)]);
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        const float H = hrev[k];
+        const float2 v = z[k];
+        z[k] = make_float2(v.x * H, v.y * H);
+    }
+    __syncthreads();
+    // inverse: decimation in time with conjugate twiddles
+    for (int lh = 0; lh < logP; ++lh) {
+        const int h = 1 << lh;
+        for (int bt = threadIdx.x; bt < half; bt += blockDim.x) {
+            const int j = bt & (h - 1);
+            const int i0 = ((bt >> lh) << (lh + 1)) | j;
+            const float2 w = tw[j << (logP - 1 - lh)];
+            const float2 u = z[i0];
+            const float2 t = cmul(z[i0 + h], make_float2(w.x, -w.y));
+            z[i0] = make_float2(u.x + t.x, u.y + t.y);
+            z[i0 + h] = make_float2(u.x - t.x, u.y - t.y);
+        }
+        __syncthreads();
+    }
+    float *qA = q + (size_t)rA * n_bins;
+    float *qB = q + (size_t)rB * n_bins;
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
+        const float2 v = z[k];
+        qA[k] = v.x;
+        if (hasB) qB[k] = v.y;
+    }
+}
+
+}  // namespace
+
+size_t filter_table_bytes(int P) {
+    return align_up(sizeof(float2) * (P / 2)) + align_up(sizeof(double) * P) + align_up(sizeof(float) * P);
+}
+
+int launch_filter_tables(int P, void *tables, cudaStream_t st) {
+    Carver cv(tables, filter_table_bytes(P));
+    float2 *tw = cv.take<float2>(P / 2);
+    double *costab = cv.take<double>(P);
+    float *hrev = cv.take<float>(P);
+    int logP = 0;
+    while ((1 << logP) < P) ++logP;
+    twiddle_kernel<<<(P + 255) / 256, 256, 0, st>>>(P, tw, costab);
+    int rc = cuda_status("twiddle kernel");
+    if (rc) return rc;
+    spectrum_kernel<<<P / 2 + 1, 256, 0, st>>>(P, logP, costab, hrev);
+    return cuda_status("filter spectrum kernel");
+}
+
+int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angle_stride, const float *flat,
+                  const float *dark, int z0, int n_slices_chunk, int n_angles, int n_bins, int P,
+                  const void *tables, float *q, cudaStream_t st) {
+    Carver cv(const_cast<void *>(tables), filter_table_bytes(P));
+    const float2 *tw = cv.take<float2>(P / 2);
+    cv.take<double>(P);
+    const float *hrev = cv.take<float>(P);
+    int logP = 0;
+    while ((1 << logP) < P) ++logP;
+    const int n_rows = n_slices_chunk * n_angles;
+    const int threads = P >= 2048 ? 512 : (P >= 256 ? P / 4 : 64);
+    const size_t smem = sizeof(float2) * P;
+    const int grid = (n_rows + 1) / 2;
+#define PYHST_FILTER_CASE(K)                                                                          \
+    case K: {                                                                                         \
+        if (smem > 48 * 1024)                                                                         \
+            cudaFuncSetAttribute(filter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        filter_kernel<K><<<grid, threads, smem, st>>>(data, slice_stride, angle_stride, flat, dark, z0,   \
+                                                      n_rows, n_angles, n_bins, P, logP, tw, hrev, q); \
+        break;                                                                                        \
+    }
+    switch (kind) {
+        PYHST_FILTER_CASE(PYHST_U16_RAW)
+        PYHST_FILTER_CASE(PYHST_F32_RAW)
+        PYHST_FILTER_CASE(PYHST_F32_SINO)
+        PYHST_FILTER_CASE(PYHST_F16_SINO)
+        PYHST_FILTER_CASE(PYHST_BF16_SINO)
+        default: return fail(PYHST_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    }
+#undef PYHST_FILTER_CASE
+    return cuda_status("filter kernel");
+}
+
+}  // namespace pyhst

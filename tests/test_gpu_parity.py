@@ -1,0 +1,230 @@
+"""GPU parity of the FBP path and the projector pair against the FP64 oracle.
+
+Every comparison goes through the C ABI (the package's binding only marshals
+arguments).  Tolerances are the float32 bar: relative L2 <= 1e-5 and
+max-abs <= 1e-4 * max|reference|.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from synth import acquisition as acq
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+MAX_ABS = 1e-4
+
+
+def close(got, ref, rel=REL_L2, mx=MAX_ABS):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.abs(ref).max()
+    e = got - ref
+    r = np.linalg.norm(e) / max(np.linalg.norm(ref), 1e-300)
+    m = np.abs(e).max() / max(scale, 1e-300)
+    assert r <= rel and m <= mx, f"rel L2 {r:.3e} (<= {rel}), max-abs/max {m:.3e} (<= {mx})"
+    return r, m
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1306_1392_b300 as P
+    return P
+
+
+def geometry(P, angles, axis, n_bins, nx, ny, s, dev, cx=None, cy=None):
+    return P.Geometry(torch.as_tensor(np.asarray(angles), dtype=torch.float32, device=dev).contiguous(),
+                      torch.as_tensor(np.broadcast_to(np.asarray(axis, dtype=np.float64), (len(angles),)).copy(),
+                                      dtype=torch.float32, device=dev),
+                      n_bins, nx, ny, s, cx, cy)
+
+
+def f64(t):
+    return t.detach().double().cpu().numpy()
+
+
+CASES = [
+    # (n_angles, n_bins, nx, ny, angles kind, axis offset, seed)
+    (180, 256, 256, 256, "uniform", 0.0, 0),
+    (37, 131, 100, 77, "random", 3.3, 1),        # ragged tiles, off-centre axis
+    (1, 64, 64, 64, "zero", 0.0, 2),              # single angle
+    (64, 96, 160, 40, "wide", -2.7, 3),           # angles beyond pi, negative angles
+    (33, 300, 129, 257, "random", 10.0, 4),
+]
+
+
+def _case(P, dev, na, nb, nx, ny, kind, off, seed):
+    g = np.random.default_rng(seed)
+    if kind == "uniform":
+        ang = np.arange(na) * math.pi / na
+    elif kind == "zero":
+        ang = np.zeros(na)
+    elif kind == "wide":
+        ang = g.uniform(-2 * math.pi, 3 * math.pi, na)
+    else:
+        ang = np.sort(g.uniform(0, math.pi, na))
+    ang = ang.astype(np.float32)
+    axis = ((nb - 1) / 2.0 + off + g.uniform(-0.5, 0.5, na)).astype(np.float32)
+    return g, ang, axis, geometry(P, ang, axis, nb, nx, ny, 2.0 / max(nx, ny), dev)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_backproject_parity(P, orc, cuda_device, case):
+    na, nb, nx, ny, kind, off, seed = case
+    g, ang, axis, geo = _case(P, cuda_device, *case)
+    sino = g.standard_normal((2, na, nb)).astype(np.float32)
+    w = 0.37
+    got = P.pyhst_backproject(geo, torch.from_numpy(sino).to(cuda_device), w)
+    torch.cuda.synchronize()
+    for z in range(2):
+        ref = orc.backproject(sino[z].astype(np.float64), ang.astype(np.float64), axis.astype(np.float64),
+                              nx, ny, w)
+        close(f64(got[z]), ref)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_project_parity(P, orc, cuda_device, case):
+    na, nb, nx, ny, kind, off, seed = case
+    g, ang, axis, geo = _case(P, cuda_device, *case)
+    img = g.standard_normal((2, ny, nx)).astype(np.float32)
+    got = P.pyhst_project(geo, torch.from_numpy(img).to(cuda_device))
+    torch.cuda.synchronize()
+    for z in range(2):
+        ref = orc.project(img[z].astype(np.float64), ang.astype(np.float64), axis.astype(np.float64), nb,
+                          geo.pixel_size)
+        if np.abs(ref).max() == 0:
+            assert np.abs(f64(got[z])).max() == 0
+        else:
+            close(f64(got[z]), ref)
+
+
+def test_projector_pair_is_adjoint(P, cuda_device):
+    """<P x, y> = <x, P^T y> for the GPU pair (float32 outputs, float64 dots)."""
+    g = np.random.default_rng(9)
+    na, nb, n = 90, 200, 160
+    ang = np.sort(g.uniform(0, math.pi, na)).astype(np.float32)
+    geo = geometry(P, ang, (nb - 1) / 2 + 1.3, nb, n, n, 0.01, cuda_device)
+    x = torch.from_numpy(g.standard_normal((1, n, n)).astype(np.float32)).to(cuda_device)
+    y = torch.from_numpy(g.standard_normal((1, na, nb)).astype(np.float32)).to(cuda_device)
+    px = P.pyhst_project(geo, x)
+    pty = P.pyhst_backproject(geo, y, geo.pixel_size)
+    lhs = (px.double() * y.double()).sum().item()
+    rhs = (x.double() * pty.double()).sum().item()
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+
+
+def test_project_rays_outside_image_are_zero(P, cuda_device):
+    """An axis far off the detector: every ray misses the image."""
+    geo = geometry(P, np.array([0.0, 0.7, 2.0], np.float32), 5000.0, 64, 32, 32, 0.1, cuda_device)
+    got = P.pyhst_project(geo, torch.ones((1, 32, 32), device=cuda_device))
+    assert torch.count_nonzero(got).item() == 0
+    back = P.pyhst_backproject(geo, torch.ones((1, 3, 64), device=cuda_device), 1.0)
+    assert torch.count_nonzero(back).item() == 0
+
+
+def test_non_finite_angles_contribute_nothing(P, cuda_device):
+    """A NaN or infinite angle/axis entry is skipped, not read out of range."""
+    ang = np.array([0.3, np.nan, 1.1, np.inf], np.float32)
+    axis = np.array([31.5, 31.5, np.nan, 31.5], np.float32)
+    geo = geometry(P, ang, axis, 64, 48, 48, 0.1, cuda_device)
+    sino = torch.ones((1, 4, 64), device=cuda_device)
+    got = P.pyhst_backproject(geo, sino, 1.0)
+    ok = geometry(P, ang[:1], axis[:1], 64, 48, 48, 0.1, cuda_device)
+    ref = P.pyhst_backproject(ok, sino[:, :1].contiguous(), 1.0)
+    torch.testing.assert_close(got, ref, rtol=0, atol=0)
+
+
+# ------------------------------------------------------------------ FBP
+def test_fbp_single_slice_counts(P, orc, cuda_device):
+    """256^2, 180 angles, 256 bins, Poisson counts at 1e5 photons, flat 1e5,
+    dark 0, Ram-Lak, padding 512: the single-slice FBP workload."""
+    sl = acq.single_slice_fbp(seed=0)
+    raw = sl.extra["raw"]                              # [180, 1, 256] float32
+    geo = geometry(P, sl.angles.numpy(), sl.axis.numpy(), sl.n_bins, sl.nx, sl.ny, sl.pixel_size, cuda_device)
+    got = P.pyhst_fbp(geo, raw.to(cuda_device), "f32_raw", sl.extra["flat"].to(cuda_device),
+                      sl.extra["dark"].to(cuda_device), pad_len=512)
+    torch.cuda.synchronize()
+    ref = orc.fbp_from_raw(raw[:, 0, :].double().numpy(), sl.extra["flat"][0].double().numpy(),
+                           sl.extra["dark"][0].double().numpy(), sl.angles.double().numpy(),
+                           sl.axis.double().numpy(), sl.nx, sl.ny, sl.pixel_size)
+    close(f64(got[0]), ref)
+
+
+def _oracle_fbp_stack(orc, vol, z):
+    raw = vol.raw[:, z, :].to(torch.float64).cpu().numpy()
+    return orc.fbp_from_raw(raw, vol.flat[z].double().cpu().numpy(), vol.dark[z].double().cpu().numpy(),
+                            vol.angles.double().numpy(), vol.axis.double().numpy(), vol.nx, vol.ny,
+                            vol.pixel_size)
+
+
+@pytest.mark.parametrize("ws_slices", [1, 3, 8])
+def test_fbp_uint16_volume_in_place(P, orc, cuda_device, ws_slices):
+    """Raw uint16 radiography stack [angles][slices][bins] read in place with
+    seeded flat/dark fields; workspaces of 1, 3 and 8 slices per pass."""
+    vol = acq.ellipsoid_volume(n_slices=6, n=96, n_angles=120, seed=11, n_ellipsoids=40)
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
+                   cuda_device)
+    g6 = geo.c(6)
+    import ctypes
+    from paper_1306_1392_b300 import _lib
+    fixed = _lib.lib.pyhst_workspace_size(ctypes.byref(geo.c(1)), _lib.PYHST_OP_FBP) - 120 * 96 * 4
+    ws = torch.empty(fixed + ws_slices * 120 * 96 * 4 + 4096, dtype=torch.uint8, device=cuda_device)
+    got = P.pyhst_fbp(geo, vol.raw.to(cuda_device), "u16_raw", vol.flat.to(cuda_device),
+                      vol.dark.to(cuda_device), workspace=ws)
+    torch.cuda.synchronize()
+    for z in range(6):
+        close(f64(got[z]), _oracle_fbp_stack(orc, vol, z))
+
+
+@pytest.mark.parametrize("kind,dt", [("f32_sino", torch.float32), ("f16_sino", torch.float16),
+                                     ("bf16_sino", torch.bfloat16)])
+def test_fbp_sinogram_kinds(P, orc, cuda_device, kind, dt):
+    """Pre-normalised sinograms stored in float32 / float16 / bfloat16: the
+    GPU converts on load; the oracle gets the same rounded values."""
+    p = acq.ellipsoid_sinograms(2, 128, 90, seed=5, n_ellipsoids=30)   # [2, 90, 128] float64
+    stored = p.to(dt)
+    ang = acq.uniform_angles(90).numpy()
+    geo = geometry(P, ang, 63.5, 128, 128, 128, 2 / 128, cuda_device)
+    got = P.pyhst_fbp(geo, stored.to(cuda_device).contiguous(), kind)
+    torch.cuda.synchronize()
+    for z in range(2):
+        ref = orc.fbp_from_sinogram(stored[z].double().numpy(), ang.astype(np.float64), 63.5, 128, 128, 2 / 128)
+        close(f64(got[z]), ref)
+
+
+@pytest.mark.parametrize("pad", [0, 1024, 4096])
+def test_fbp_padding_lengths_agree(P, orc, cuda_device, pad):
+    """Any padding >= 2 n_bins gives the same linear convolution."""
+    p = acq.ellipsoid_sinograms(1, 200, 60, seed=6, n_ellipsoids=20)
+    ang = acq.uniform_angles(60).numpy()
+    geo = geometry(P, ang, 99.5, 200, 150, 170, 0.01, cuda_device)
+    got = P.pyhst_fbp(geo, p.float().to(cuda_device), "f32_sino", pad_len=pad)
+    torch.cuda.synchronize()
+    ref = orc.fbp_from_sinogram(p[0].float().double().numpy(), ang.astype(np.float64), 99.5, 150, 170, 0.01)
+    close(f64(got[0]), ref)
+
+
+def test_fbp_full_size_volume_sampled(P, orc, cuda_device):
+    """The batched-volume workload's slice geometry (2048^2 grid, 2000 angles,
+    2048 bins, uint16 raw with flat/dark) in the launch configuration the
+    benchmark times (chunks of 4 slices): sampled pixels of 2 slices of an
+    8-slice stack against the oracle evaluated at those pixels."""
+    n, na, ns = 2048, 2000, 8
+    vol = acq.ellipsoid_volume(n_slices=ns, n=n, n_angles=na, seed=1000, device=cuda_device, slices=[2, 5])
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), n, n, n, vol.pixel_size, cuda_device)
+    got = P.pyhst_fbp(geo, vol.raw, "u16_raw", vol.flat, vol.dark)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for z in (2, 5):
+        raw = vol.raw[:, z, :].double().cpu().numpy()
+        q = orc.ramlak_filter(orc.normalise(raw, vol.flat[z].double().cpu().numpy(),
+                                            vol.dark[z].double().cpu().numpy()))
+        ii = np.concatenate([rng.integers(0, n, 1500), [0, n - 1, 0, n - 1, n // 2]])
+        jj = np.concatenate([rng.integers(0, n, 1500), [0, 0, n - 1, n - 1, n // 2]])
+        ref = orc.backproject_at(q, vol.angles.double().numpy(), vol.axis.double().numpy(), n, n, ii, jj,
+                                 orc.fbp_weight(na, vol.pixel_size))
+        g = got[z].cpu().numpy()[ii, jj]
+        close(g, ref)
