@@ -105,6 +105,22 @@ def backproject(q, angles, axis, nx, ny, weight=1.0, cx=None, cy=None):
     return img
 
 
+def backproject_at(q, angles, axis, nx, ny, ii, jj, weight=1.0, cx=None, cy=None):
+    """The back-projection at pixels (ii[k], jj[k]) only."""
+    q, pq = _c(q)
+    na, nb = q.shape
+    ang, pa = _c(np.asarray(angles, dtype=np.float64).reshape(na))
+    ax, px = _c(np.broadcast_to(np.asarray(axis, dtype=np.float64), (na,)))
+    ii = np.ascontiguousarray(ii, dtype=np.int64)
+    jj = np.ascontiguousarray(jj, dtype=np.int64)
+    out = np.empty(len(ii))
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    lib().orc_backproject_at(pq, I64(na), I64(nb), pa, px, ii.ctypes.data_as(P64), jj.ctypes.data_as(P64),
+                             I64(len(ii)), D(_centre(nx, cx)), D(_centre(ny, cy)), D(weight),
+                             out.ctypes.data_as(PD))
+    return out
+
+
 def project(img, angles, axis, n_bins, scale=1.0, cx=None, cy=None):
     """scale * (transpose of the unweighted back-projector) applied to img."""
     img, pi = _c(img)

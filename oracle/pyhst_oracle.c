@@ -130,6 +130,30 @@ void orc_backproject(const double *q, int64_t n_angles, int64_t n_bins,
     free(cs);
 }
 
+/* Back-projection at selected pixels only (rows ii[k], columns jj[k]); the
+ * same definition as orc_backproject, for spot checks of large images. */
+void orc_backproject_at(const double *q, int64_t n_angles, int64_t n_bins,
+                        const double *angles, const double *axis,
+                        const int64_t *ii, const int64_t *jj, int64_t n_points,
+                        double cx, double cy, double weight, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n_points; k++) {
+        double acc = 0.0;
+        for (int64_t a = 0; a < n_angles; a++) {
+            double t = coord(ii[k], jj[k], cos(angles[a]), sin(angles[a]), axis[a], cx, cy);
+            double fl = floor(t);
+            double f = t - fl;
+            int64_t i0 = (int64_t)fl;
+            const double *row = q + a * n_bins;
+            double v0 = (i0 >= 0 && i0 < n_bins) ? row[i0] : 0.0;
+            double v1 = (i0 + 1 >= 0 && i0 + 1 < n_bins) ? row[i0 + 1] : 0.0;
+            acc += (1.0 - f) * v0 + f * v1;
+        }
+        out[k] = weight * acc;
+    }
+}
+
 /* ---------------------------------------------------------------------
  * Forward projection: the exact transpose of the unweighted back-projector,
  * scaled by `scale` (the pixel size, so that the result approximates line
