@@ -25,7 +25,7 @@ from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SIN
                    PYHST_U16_RAW)
 
 __all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_backproject", "pyhst_project",
-           "pyhst_tv_solve", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
+           "pyhst_tv_solve", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
            "pyhst_version", "library_path"]
 
 
@@ -241,6 +241,20 @@ def pyhst_tv_solve(geom: Geometry, sino: torch.Tensor, opts: TvOptions, x=None, 
     _check(L.lib.pyhst_tv_solve(ctypes.byref(g), _ptr(sino), ctypes.byref(o), _ptr(x), _ptr(e), _ptr(lip),
                                 _ptr(ws), ws.numel(), _stream()))
     return x, e, lip
+
+
+def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0.125, out=None, workspace=None):
+    """prox of lam * TV (Eq. 2) for images z [n_slices, ny, nx] (or [ny, nx])."""
+    z3 = _stack3(_cuda(z, "z", (torch.float32,)), "z")
+    ns, ny, nx = z3.shape
+    if out is None:
+        out = torch.empty_like(z3)
+    _cuda(out, "out", (torch.float32,))
+    need = L.lib.pyhst_tv_prox_workspace_size(nx, ny, ns)
+    ws = _workspace(need, z3.device, workspace)
+    _check(L.lib.pyhst_tv_prox(_ptr(z3), nx, ny, ns, float(lam), int(n_inner), float(tau), _ptr(out), _ptr(ws),
+                               ws.numel(), _stream()))
+    return out
 
 
 def fbp_weight(n_angles: int, pixel_size: float) -> float:

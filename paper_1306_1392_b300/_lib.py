@@ -51,6 +51,9 @@ SIGNATURES = [
     ("pyhst_tv_solve", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(pyhst_tv_opts),
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     ("pyhst_tv_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), ctypes.POINTER(pyhst_tv_opts)]),
+    ("pyhst_tv_prox_workspace_size", c_size_t, [c_int32, c_int32, c_int32]),
+    ("pyhst_tv_prox", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_float, c_int32, c_float, c_void_p,
+                                c_void_p, c_size_t, c_void_p]),
     ("pyhst_last_error", ctypes.c_char_p, []),
     ("pyhst_version", ctypes.c_char_p, []),
 ]

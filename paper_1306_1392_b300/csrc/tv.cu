@@ -1,8 +1,405 @@
-// TV-penalised least squares (Eq. 3) by ISTA/FISTA with a Chambolle TV prox.
+// TV-penalised least squares (Eq. 3) by ISTA/FISTA (Sec. 3.1) with the
+// isotropic TV (Eq. 2) prox computed by Chambolle's dual fixed point.
+//
+//   x_k = prox_{(beta/L) TV}( y_k - (1/L) P^T (P y_k - sino) )
+//   FISTA: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, w_k = (t_k - 1) / t_{k+1},
+//          y_{k+1} = x_k + w_k (x_k - x_{k-1});   ISTA: w_k = 0.
+//   energy_k = 1/2 ||P x_k - sino||^2 + beta TV(x_k)   (Eq. 3, float64)
+//
+// Each iteration makes one projection and one back-projection: the solver
+// projects x_k (which the energy needs anyway) and carries P y_{k+1} =
+// P x_k + w_k (P x_k - P x_{k-1}) by linearity in sinogram space, so the
+// gradient step back-projects the residual P y_k - sino directly (the
+// back-projector subtracts while staging its rows).  Reductions (energy,
+// norms) are float64, per block then in fixed order: bitwise reproducible.
+// L comes from the caller or from power iteration on P^T P started from the
+// all-ones image (float64 norms), L = 1.01 * ||P v||^2 for the final unit v.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 
 namespace pyhst {
-size_t tv_workspace_bytes(const pyhst_geometry *g, const pyhst_tv_opts *o) { (void)g; (void)o; return 0; }
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 256;  // partial sums per slice (= kRedThreads: one per finalize thread)
+
+// ----------------------------------------------------------------- layout
+struct TvLayout {
+    size_t tab, xt, img[9], sino[3], scal, part[2], bytes;
+};
+
+// images: y, xa, xb, z, g, p1a, p2a, p1b, p2b; sinograms: Axa, Axb, Ay;
+// scalars per slice: L (double), invL, lam, invnorm (float)
+TvLayout tv_layout(const pyhst_geometry *g) {
+    TvLayout l{};
+    const size_t S = (size_t)g->n_slices, N = (size_t)g->nx * g->ny, M = (size_t)g->n_angles * g->n_bins;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    l.tab = take(sizeof(AngleInfo) * g->n_angles);
+    l.xt = take(sizeof(float) * N * S);
+    for (auto &o : l.img) o = take(sizeof(float) * N * S);
+    for (auto &o : l.sino) o = take(sizeof(float) * M * S);
+    l.scal = take(sizeof(double) * 4 * S);
+    for (auto &o : l.part) o = take(sizeof(double) * kRedBlocks * S);
+    l.bytes = off;
+    return l;
+}
+
+struct Scalars {   // per-slice solver scalars in the workspace
+    double *L;     // [S]
+    float *invL;   // [S]
+    float *lam;    // [S] beta / L
+    float *invn;   // [S] 1 / ||w|| of the power iteration
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = (l < kRedThreads / 32) ? red[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;   // valid in thread 0
+}
+
+// sum over the slice of (a - b)^2 (b may be NULL) -> part[slice][block]
+__global__ void sqdiff_partial(const float *__restrict__ a, const float *__restrict__ b, size_t n,
+                               double *__restrict__ part) {
+    const size_t off = (size_t)blockIdx.y * n;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = b ? a[off + i] - b[off + i] : a[off + i];
+        acc += (double)d * (double)d;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
+}
+
+__device__ double sum_partials(const double *part) {
+    double v = threadIdx.x < kRedBlocks ? part[blockIdx.x * kRedBlocks + threadIdx.x] : 0.0;
+    return block_sum(v);
+}
+
+// mode 0: L = 1.01 * sum (power iteration end) and derived scalars;
+// mode 1: invnorm = 1 / sqrt(sum)
+__global__ void finalize_scalar(const double *__restrict__ part, Scalars sc, float beta, int mode,
+                                int broadcast) {
+    const double s = sum_partials(part);
+    if (threadIdx.x == 0) {
+        if (mode == 0) {
+            const double L = 1.01 * s;
+            for (int k = 0; k < broadcast; ++k) {
+                sc.L[k] = L;
+                sc.invL[k] = (float)(1.0 / L);
+                sc.lam[k] = (float)((double)beta / L);
+            }
+        } else {
+            sc.invn[blockIdx.x] = (float)(1.0 / sqrt(s));
+        }
+    }
+}
+
+__global__ void set_lipschitz(Scalars sc, double L, float beta, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        sc.L[k] = L;
+        sc.invL[k] = (float)(1.0 / L);
+        sc.lam[k] = (float)((double)beta / L);
+    }
+}
+
+__global__ void finalize_energy(const double *__restrict__ data_part, const double *__restrict__ tv_part,
+                                float beta, double *__restrict__ energy, int n_iter, int k) {
+    const double d = sum_partials(data_part);
+    const double t = sum_partials(tv_part);
+    if (threadIdx.x == 0 && energy) energy[(size_t)blockIdx.x * n_iter + k] = 0.5 * d + (double)beta * t;
+}
+
+__global__ void scale_kernel(const float *__restrict__ w, const float *__restrict__ invn, float *__restrict__ v,
+                             size_t n) {
+    const size_t off = (size_t)blockIdx.y * n;
+    const float s = invn[blockIdx.y];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v[off + i] = w[off + i] * s;
+}
+
+__global__ void fill_kernel(float *__restrict__ v, float val, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v[i] = val;
+}
+
+// z = y - g / L
+__global__ void grad_step_kernel(const float *__restrict__ y, const float *__restrict__ g,
+                                 const float *__restrict__ invL, float *__restrict__ z, size_t n) {
+    const size_t off = (size_t)blockIdx.y * n;
+    const float il = invL[blockIdx.y];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        z[off + i] = fmaf(-g[off + i], il, y[off + i]);
+}
+
+// One Chambolle step: G = div p - z / lam,  p <- (p + tau grad G) / (1 + tau |grad G|).
+template <bool kFirst>
+__global__ void chambolle_kernel(const float *__restrict__ z, const float *__restrict__ p1, const float *__restrict__ p2,
+                                 float *__restrict__ q1, float *__restrict__ q2, const float *__restrict__ lam,
+                                 float tau, int nx, int ny) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= ny || j >= nx) return;
+    const size_t off = (size_t)blockIdx.z * nx * ny;
+    const float l = lam[blockIdx.z];
+    const float *Z = z + off;
+    const float *P1 = p1 + off, *P2 = p2 + off;
+    auto G = [&](int r, int c) -> float {
+        float d = 0.0f;
+        if (!kFirst) {
+            const size_t k = (size_t)r * nx + c;
+            if (r + 1 < ny) d += P1[k];
+            if (r > 0) d -= P1[k - nx];
+            if (c + 1 < nx) d += P2[k];
+            if (c > 0) d -= P2[k - 1];
+        }
+        return d - Z[(size_t)r * nx + c] / l;
+    };
+    const float g0 = G(i, j);
+    const float g1 = (i + 1 < ny) ? G(i + 1, j) - g0 : 0.0f;
+    const float g2 = (j + 1 < nx) ? G(i, j + 1) - g0 : 0.0f;
+    const float den = 1.0f + tau * sqrtf(g1 * g1 + g2 * g2);
+    const size_t k = (size_t)i * nx + j;
+    const float a = kFirst ? 0.0f : P1[k], b = kFirst ? 0.0f : P2[k];
+    q1[off + k] = (a + tau * g1) / den;
+    q2[off + k] = (b + tau * g2) / den;
+}
+
+// x = z - lam div p
+__global__ void prox_final_kernel(const float *__restrict__ z, const float *__restrict__ p1,
+                                  const float *__restrict__ p2, const float *__restrict__ lam,
+                                  float *__restrict__ x, int nx, int ny) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= ny || j >= nx) return;
+    const size_t off = (size_t)blockIdx.z * nx * ny, k = (size_t)i * nx + j;
+    const float *P1 = p1 + off, *P2 = p2 + off;
+    float d = 0.0f;
+    if (i + 1 < ny) d += P1[k];
+    if (i > 0) d -= P1[k - nx];
+    if (j + 1 < nx) d += P2[k];
+    if (j > 0) d -= P2[k - 1];
+    x[off + k] = fmaf(-lam[blockIdx.z], d, z[off + k]);
+}
+
+// data partial of ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
+__global__ void sino_update_kernel(const float *__restrict__ axn, const float *__restrict__ axo,
+                                   const float *__restrict__ b, float *__restrict__ ay, float w, size_t n,
+                                   double *__restrict__ part) {
+    const size_t off = (size_t)blockIdx.y * n;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = axn[off + i];
+        const float d = v - b[off + i];
+        acc += (double)d * (double)d;
+        ay[off + i] = fmaf(w, v - axo[off + i], v);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
+}
+
+// TV(xn) partial (Eq. 2) and y = xn + w (xn - xo)
+__global__ void image_update_kernel(const float *__restrict__ xn, const float *__restrict__ xo,
+                                    float *__restrict__ y, float w, int nx, int ny,
+                                    double *__restrict__ part) {
+    const size_t n = (size_t)nx * ny, off = (size_t)blockIdx.y * n;
+    const float *X = xn + off;
+    double acc = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / nx), j = (int)(k - (size_t)i * nx);
+        const float v = X[k];
+        const float d1 = (i + 1 < ny) ? X[k + nx] - v : 0.0f;
+        const float d2 = (j + 1 < nx) ? X[k + 1] - v : 0.0f;
+        acc += (double)sqrtf(d1 * d1 + d2 * d2);
+        y[off + k] = fmaf(w, v - xo[off + k], v);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
+}
+
+struct Bufs {
+    AngleInfo *tab;
+    float *xt;
+    float *img[9];
+    float *sino[3];
+    Scalars sc;
+    double *part[2];
+};
+
+Bufs carve(const pyhst_geometry *g, void *ws) {
+    const TvLayout l = tv_layout(g);
+    char *b = static_cast<char *>(ws);
+    Bufs r;
+    r.tab = reinterpret_cast<AngleInfo *>(b + l.tab);
+    r.xt = reinterpret_cast<float *>(b + l.xt);
+    for (int i = 0; i < 9; ++i) r.img[i] = reinterpret_cast<float *>(b + l.img[i]);
+    for (int i = 0; i < 3; ++i) r.sino[i] = reinterpret_cast<float *>(b + l.sino[i]);
+    double *sc = reinterpret_cast<double *>(b + l.scal);
+    const int S = g->n_slices;
+    r.sc.L = sc;
+    r.sc.invL = reinterpret_cast<float *>(sc + S);
+    r.sc.lam = r.sc.invL + S;
+    r.sc.invn = r.sc.lam + S;
+    for (int i = 0; i < 2; ++i) r.part[i] = reinterpret_cast<double *>(b + l.part[i]);
+    return r;
+}
+
+}  // namespace
+
+size_t tv_workspace_bytes(const pyhst_geometry *g, const pyhst_tv_opts *) {
+    if (!g || g->n_angles < 1 || g->n_bins < 1 || g->nx < 1 || g->ny < 1 || g->n_slices < 1) return 0;
+    return tv_layout(g).bytes;
+}
+
+int check_tv_opts(const pyhst_tv_opts *o) {
+    if (!o) return fail(PYHST_ERR_INVALID_ARG, "options are NULL");
+    if (!(o->beta >= 0.0f) || !std::isfinite(o->beta)) return fail(PYHST_ERR_INVALID_ARG, "beta must be >= 0");
+    if (o->n_iter < 1) return fail(PYHST_ERR_INVALID_ARG, "n_iter must be >= 1");
+    if (o->n_inner < 1) return fail(PYHST_ERR_INVALID_ARG, "n_inner must be >= 1");
+    if (!(o->tau > 0.0f && o->tau <= 0.25f)) return fail(PYHST_ERR_INVALID_ARG, "tau must be in (0, 1/4]");
+    if (!(o->lipschitz >= 0.0) || !std::isfinite(o->lipschitz))
+        return fail(PYHST_ERR_INVALID_ARG, "lipschitz must be >= 0 (0: estimate)");
+    if (o->lipschitz == 0.0 && o->n_power_iter < 1)
+        return fail(PYHST_ERR_INVALID_ARG, "n_power_iter must be >= 1 when lipschitz is estimated");
+    return PYHST_OK;
+}
+
+// Enqueue the whole solve on `st`.
+int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *o, float *x,
+                     double *energy, double *lip_out, void *ws, cudaStream_t st) {
+    int rc;
+    Bufs B = carve(g, ws);
+    const int S = g->n_slices;
+    const size_t N = (size_t)g->nx * g->ny, M = (size_t)g->n_angles * g->n_bins;
+    const float s = g->pixel_size;
+    float *y = B.img[0], *xa = B.img[1], *xb = B.img[2], *z = B.img[3], *gr = B.img[4];
+    float *p1a = B.img[5], *p2a = B.img[6], *p1b = B.img[7], *p2b = B.img[8];
+    float *Axa = B.sino[0], *Axb = B.sino[1], *Ay = B.sino[2];
+    // reduction kernels always run kRedBlocks blocks per slice (every partial is written)
+    const dim3 eg(kRedBlocks, S), sg(kRedBlocks, S);
+    const dim3 tb(32, 8), tgr((g->nx + 31) / 32, (g->ny + 7) / 8, S);
+
+    if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, B.tab, st))) return rc;
+
+    // ---- step size
+    if (o->lipschitz > 0.0) {
+        set_lipschitz<<<(S + 127) / 128, 128, 0, st>>>(B.sc, o->lipschitz, o->beta, S);
+    } else {
+        // the operator is the same for every slice: iterate on slice 0 only
+        pyhst_geometry g1 = *g;
+        g1.n_slices = 1;
+        const dim3 rg1(kRedBlocks, 1), eg1(kRedBlocks, 1);
+        fill_kernel<<<256, 256, 0, st>>>(z, 1.0f, N);
+        for (int it = 0; it < o->n_power_iter; ++it) {
+            if ((rc = launch_project(&g1, B.tab, z, Axa, s, B.xt, st))) return rc;
+            if ((rc = launch_backproject(&g1, B.tab, BpSource{Axa, nullptr}, gr, s, st))) return rc;
+            sqdiff_partial<<<rg1, kRedThreads, 0, st>>>(gr, nullptr, N, B.part[0]);
+            finalize_scalar<<<1, kRedThreads, 0, st>>>(B.part[0], B.sc, o->beta, 1, 0);
+            scale_kernel<<<eg1, kRedThreads, 0, st>>>(gr, B.sc.invn, z, N);
+        }
+        if ((rc = launch_project(&g1, B.tab, z, Axa, s, B.xt, st))) return rc;
+        sqdiff_partial<<<rg1, kRedThreads, 0, st>>>(Axa, nullptr, M, B.part[0]);
+        finalize_scalar<<<1, kRedThreads, 0, st>>>(B.part[0], B.sc, o->beta, 0, S);
+    }
+    if (lip_out) cudaMemcpyAsync(lip_out, B.sc.L, sizeof(double) * S, cudaMemcpyDeviceToDevice, st);
+    if ((rc = cuda_status("step-size kernels"))) return rc;
+
+    // ---- start: x_0 = x (warm) or 0; y_1 = x_0; P y_1 = P x_0
+    float *xo = xa, *xn = xb, *Axo = Axa, *Axn = Axb;
+    if (o->warm_start) {
+        cudaMemcpyAsync(xo, x, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
+        if ((rc = launch_project(g, B.tab, xo, Axo, s, B.xt, st))) return rc;
+    } else {
+        cudaMemsetAsync(xo, 0, sizeof(float) * N * S, st);
+        cudaMemsetAsync(Axo, 0, sizeof(float) * M * S, st);
+    }
+    cudaMemcpyAsync(y, xo, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(Ay, Axo, sizeof(float) * M * S, cudaMemcpyDeviceToDevice, st);
+    if ((rc = cuda_status("solver start"))) return rc;
+
+    double t = 1.0;
+    for (int k = 0; k < o->n_iter; ++k) {
+        // gradient step: z = y - (1/L) P^T (P y - sino)
+        if ((rc = launch_backproject(g, B.tab, BpSource{Ay, sino}, gr, s, st))) return rc;
+        grad_step_kernel<<<eg, kRedThreads, 0, st>>>(y, gr, B.sc.invL, z, N);
+        // prox of (beta/L) TV
+        if (o->beta > 0.0f) {
+            float *pi1 = p1a, *pi2 = p2a, *po1 = p1b, *po2 = p2b;
+            chambolle_kernel<true><<<tgr, tb, 0, st>>>(z, nullptr, nullptr, pi1, pi2, B.sc.lam, o->tau, g->nx, g->ny);
+            for (int n = 1; n < o->n_inner; ++n) {
+                chambolle_kernel<false><<<tgr, tb, 0, st>>>(z, pi1, pi2, po1, po2, B.sc.lam, o->tau, g->nx, g->ny);
+                std::swap(pi1, po1);
+                std::swap(pi2, po2);
+            }
+            prox_final_kernel<<<tgr, tb, 0, st>>>(z, pi1, pi2, B.sc.lam, xn, g->nx, g->ny);
+        } else {
+            cudaMemcpyAsync(xn, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
+        }
+        if ((rc = cuda_status("prox kernels"))) return rc;
+        if ((rc = launch_project(g, B.tab, xn, Axn, s, B.xt, st))) return rc;
+        double w = 0.0;
+        if (o->use_fista) {
+            const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+            w = (t - 1.0) / tn;
+            t = tn;
+        }
+        sino_update_kernel<<<sg, kRedThreads, 0, st>>>(Axn, Axo, sino, Ay, (float)w, M, B.part[0]);
+        image_update_kernel<<<eg, kRedThreads, 0, st>>>(xn, xo, y, (float)w, g->nx, g->ny, B.part[1]);
+        finalize_energy<<<S, kRedThreads, 0, st>>>(B.part[0], B.part[1], o->beta, energy, o->n_iter, k);
+        if ((rc = cuda_status("update kernels"))) return rc;
+        std::swap(xn, xo);
+        std::swap(Axn, Axo);
+    }
+    cudaMemcpyAsync(x, xo, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
+    return cuda_status("solver result copy");
+}
+
+size_t tv_prox_workspace_bytes(int nx, int ny, int n_slices) {
+    if (nx < 1 || ny < 1 || n_slices < 1) return 0;
+    return 4 * align_up(sizeof(float) * (size_t)nx * ny * n_slices) + align_up(sizeof(float) * n_slices);
+}
+
+__global__ void fill_lam(float *lam, float v, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) lam[k] = v;
+}
+
+int tv_prox_enqueue(const float *z, int nx, int ny, int S, float lam, int n_inner, float tau, float *x, void *ws,
+                    cudaStream_t st) {
+    Carver cv(ws, tv_prox_workspace_bytes(nx, ny, S));
+    const size_t n = (size_t)nx * ny * S;
+    float *p1a = cv.take<float>(n), *p2a = cv.take<float>(n), *p1b = cv.take<float>(n), *p2b = cv.take<float>(n);
+    float *lamd = cv.take<float>(S);
+    const dim3 tb(32, 8), tgr((nx + 31) / 32, (ny + 7) / 8, S);
+    if (lam == 0.0f) {
+        cudaMemcpyAsync(x, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+        return cuda_status("prox copy");
+    }
+    fill_lam<<<(S + 127) / 128, 128, 0, st>>>(lamd, lam, S);
+    float *pi1 = p1a, *pi2 = p2a, *po1 = p1b, *po2 = p2b;
+    chambolle_kernel<true><<<tgr, tb, 0, st>>>(z, nullptr, nullptr, pi1, pi2, lamd, tau, nx, ny);
+    for (int k = 1; k < n_inner; ++k) {
+        chambolle_kernel<false><<<tgr, tb, 0, st>>>(z, pi1, pi2, po1, po2, lamd, tau, nx, ny);
+        std::swap(pi1, po1);
+        std::swap(pi2, po2);
+    }
+    prox_final_kernel<<<tgr, tb, 0, st>>>(z, pi1, pi2, lamd, x, nx, ny);
+    return cuda_status("prox kernels");
+}
+
 }  // namespace pyhst
 
 extern "C" size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_tv_opts *opts) {
@@ -12,5 +409,34 @@ extern "C" size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_t
 extern "C" int pyhst_tv_solve(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts, float *x,
                               double *energy, double *lipschitz_out, void *workspace, size_t ws_bytes,
                               pyhst_stream_t stream) {
-    return pyhst::fail(PYHST_ERR_INVALID_ARG, "not built yet");
+    using namespace pyhst;
+    int rc = check_geometry(g);
+    if (rc) return rc;
+    if ((rc = check_tv_opts(opts))) return rc;
+    if (!sino || !x) return fail(PYHST_ERR_INVALID_ARG, "sino/x pointer is NULL");
+    const size_t need = tv_workspace_bytes(g, opts);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    return tv_solve_enqueue(g, sino, opts, x, energy, lipschitz_out, workspace,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n_slices) {
+    return pyhst::tv_prox_workspace_bytes(nx, ny, n_slices);
+}
+
+extern "C" int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
+                             float tau, float *x, void *workspace, size_t ws_bytes, pyhst_stream_t stream) {
+    using namespace pyhst;
+    if (!z || !x) return fail(PYHST_ERR_INVALID_ARG, "z/x pointer is NULL");
+    if (nx < 1 || ny < 1 || n_slices < 1 || nx > 16384 || ny > 16384 || n_slices > 65535)
+        return fail(PYHST_ERR_INVALID_ARG, "image %d x %d x %d out of range", nx, ny, n_slices);
+    if (!(lam >= 0.0f) || !std::isfinite(lam)) return fail(PYHST_ERR_INVALID_ARG, "lam must be >= 0");
+    if (n_inner < 1) return fail(PYHST_ERR_INVALID_ARG, "n_inner must be >= 1");
+    if (!(tau > 0.0f && tau <= 0.25f)) return fail(PYHST_ERR_INVALID_ARG, "tau must be in (0, 1/4]");
+    const size_t need = tv_prox_workspace_bytes(nx, ny, n_slices);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    return tv_prox_enqueue(z, nx, ny, n_slices, lam, n_inner, tau, x, workspace,
+                           reinterpret_cast<cudaStream_t>(stream));
 }

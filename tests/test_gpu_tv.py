@@ -1,0 +1,117 @@
+"""GPU parity of the TV prox, the power-iteration step size and the ISTA/FISTA
+solve of Eq. 3 against the FP64 oracle, through the C ABI.
+
+Tolerances.  The prox and single operator applications are held to the
+float32 bar (relative L2 <= 1e-5).  An iterative solve compounds float32
+rounding over its iterations, so its iterate is held to relative L2 <= 1e-4
+after up to 50 outer iterations and its float64 energy history to relative
+1e-5 (the energy is a sum of squares and is less sensitive than x).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from synth import acquisition as acq
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1306_1392_b300 as P
+    return P
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("shape,lam,n_inner", [((64, 64), 0.3, 20), ((77, 100), 0.05, 20), ((31, 9), 1.5, 7),
+                                               ((1, 50), 0.2, 20)])
+def test_tv_prox_parity(P, orc, cuda_device, shape, lam, n_inner):
+    g = np.random.default_rng(sum(shape))
+    z = g.standard_normal((2,) + shape).astype(np.float32)
+    got = P.pyhst_tv_prox(torch.from_numpy(z).to(cuda_device), lam, n_inner).cpu().numpy()
+    for k in range(2):
+        ref, _, _ = orc.tv_prox(z[k].astype(np.float64), lam, n_inner)
+        assert rel(got[k], ref) <= 1e-5
+
+
+def test_tv_prox_zero_lambda_is_identity(P, cuda_device):
+    z = torch.randn(1, 40, 30, device=cuda_device)
+    torch.testing.assert_close(P.pyhst_tv_prox(z, 0.0), z, rtol=0, atol=0)
+
+
+def _foam_problem(P, orc, dev, n=64, na=24, seed=7):
+    fs = acq.foam_slice(n, na, seed=seed, truth=False)
+    geo = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), fs.n_bins, fs.nx, fs.ny, fs.pixel_size)
+    og = orc.Geometry(fs.angles.double().numpy(), fs.axis.double().numpy(), fs.n_bins, fs.nx, fs.ny, fs.pixel_size)
+    return fs, geo, og
+
+
+def test_power_iteration_step_size(P, orc, cuda_device):
+    """L = 1.01 ||P v||^2 after n power iterations from the all-ones image."""
+    fs, geo, og = _foam_problem(P, orc, cuda_device)
+    lam, _ = orc.power_iteration(og, np.ones((fs.ny, fs.nx)), 30)
+    _, _, lip = P.pyhst_tv_solve(geo, fs.extra["sino"].to(cuda_device),
+                                 P.TvOptions(beta=1e-3, n_iter=1, n_inner=1, n_power_iter=30), energy=False)
+    assert abs(lip.item() - 1.01 * lam) <= 1e-5 * 1.01 * lam
+
+
+@pytest.mark.parametrize("fista,beta,n_iter", [(True, 2e-3, 20), (False, 2e-3, 20), (True, 5e-3, 50),
+                                               (True, 0.0, 30)])
+def test_tv_solve_parity(P, orc, cuda_device, fista, beta, n_iter):
+    fs, geo, og = _foam_problem(P, orc, cuda_device)
+    L = 1.01 * orc.power_iteration(og, np.ones((fs.ny, fs.nx)), 30)[0]
+    sino = fs.extra["sino"]
+    opts = P.TvOptions(beta=beta, n_iter=n_iter, n_inner=20, lipschitz=L, use_fista=fista)
+    x, e, lip = P.pyhst_tv_solve(geo, sino.to(cuda_device), opts)
+    xr, er = orc.fista(og, sino.double().numpy(), beta, L, n_iter, n_inner=20, use_fista=fista)
+    assert lip.item() == L
+    assert rel(x[0].cpu().numpy(), xr) <= 1e-4
+    np.testing.assert_allclose(e[0].cpu().numpy(), er, rtol=1e-5)
+
+
+def test_tv_solve_warm_start(P, orc, cuda_device):
+    fs, geo, og = _foam_problem(P, orc, cuda_device, n=48, na=16, seed=3)
+    L = 1.01 * orc.power_iteration(og, np.ones((fs.ny, fs.nx)), 30)[0]
+    x0 = np.random.default_rng(1).uniform(0, 1, (fs.ny, fs.nx)).astype(np.float32)
+    sino = fs.extra["sino"]
+    opts = P.TvOptions(beta=3e-3, n_iter=15, n_inner=10, lipschitz=L, warm_start=True)
+    x, e, _ = P.pyhst_tv_solve(geo, sino.to(cuda_device), opts, x=torch.from_numpy(x0[None]).to(cuda_device))
+    xr, er = orc.fista(og, sino.double().numpy(), 3e-3, L, 15, n_inner=10, x0=x0.astype(np.float64))
+    assert rel(x[0].cpu().numpy(), xr) <= 1e-4
+    np.testing.assert_allclose(e[0].cpu().numpy(), er, rtol=1e-5)
+
+
+def test_tv_solve_slices_are_independent(P, orc, cuda_device):
+    """A stack of slices gives bitwise the results of solving each alone."""
+    fs, geo, og = _foam_problem(P, orc, cuda_device, n=40, na=20)
+    g = np.random.default_rng(2)
+    sinos = torch.stack([fs.extra["sino"], fs.extra["sino"] * 0.5,
+                         torch.from_numpy(g.uniform(0, 1, fs.extra["sino"].shape).astype(np.float32))]).to(cuda_device)
+    opts = P.TvOptions(beta=2e-3, n_iter=8, n_inner=5, n_power_iter=10)
+    xs, es, ls = P.pyhst_tv_solve(geo, sinos, opts)
+    for k in range(3):
+        x1, e1, l1 = P.pyhst_tv_solve(geo, sinos[k:k + 1].contiguous(), opts)
+        assert torch.equal(x1[0], xs[k]) and torch.equal(e1[0], es[k]) and torch.equal(l1[0], ls[k])
+
+
+def test_tv_solve_energy_decreases_and_beats_fbp(P, cuda_device):
+    """FISTA's energy drops over the run (Sec. 3.1) and, at one tenth of the
+    angles with Poisson noise, TV beats unregularised reconstructions."""
+    fs = acq.foam_slice(128, 26, seed=11)
+    dev = cuda_device
+    geo = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), fs.n_bins, fs.nx, fs.ny, fs.pixel_size)
+    sino = fs.extra["sino"].to(dev)
+    x, e, _ = P.pyhst_tv_solve(geo, sino, P.TvOptions(beta=2e-3, n_iter=150))
+    e = e[0].cpu().numpy()
+    assert e[-1] < 0.5 * e[0] and e[-1] <= e[10:].min() * (1 + 1e-6)
+    fbp = P.pyhst_fbp(geo, sino[None].contiguous(), "f32_sino")
+    truth = fs.truth.numpy()
+    err_tv = np.linalg.norm(x[0].cpu().numpy() - truth)
+    err_fbp = np.linalg.norm(fbp[0].cpu().numpy() - truth)
+    assert err_tv < 0.8 * err_fbp
