@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the batched-volume FBP workload on B300 GPUs.
+
+Workload (per GPU): a 1024-slice stack of raw uint16 radiographies
+[2000 angles][1024 slices][2048 bins] with seeded flat/dark fields, phantom =
+200 random ellipsoids in a unit cylinder with exact line integrals and
+Poisson counts; output 1024 x 2048 x 2048 float32.  The whole stack and the
+output stay resident in HBM; a step reconstructs the next 64 slices of the
+stack (normalise + Ram-Lak filter + back-projection) through pyhst_fbp.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "backproj Gupd/s (voxel·angle) + FBP slices/s; TV vs learned-prox s/slice @PSNR"
+N_SLICES, N_PIX, N_ANG, N_BINS = 1024, 2048, 2000, 2048
+WORKLOAD = ("batched volume FBP: 1024 slices x 2048x2048 float32 output, 2000 angles over 180 deg, 2048 bins, "
+            "raw uint16 radiographies with seeded flat (3e4 +-5% smooth) / dark (100 +-3) fields; "
+            "phantom = 200 random ellipsoids (density 0-1) in a unit cylinder")
+DATA = ("synthetic: seeded ellipsoid phantom, exact (closed-form) line integrals, Poisson counts + dark, "
+        "uint16; random numbers drawn once at set-up")
+UPD_PER_SLICE = N_PIX * N_PIX * N_ANG
+OPS_PER_UPDATE = 4          # coordinate FMA, floor add, interpolation FMA, accumulate add
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--slices-per-step", type=int, default=64)
+    ap.add_argument("--volume-slices", type=int, default=N_SLICES)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the baseline sample")
+    ap.add_argument("--kernel-case", choices=["backproject", "project", "filter"],
+                    help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def bp_traffic_from_profile():
+    """DRAM bytes per back-projection launch from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "backproject_2048x2000_ncu.md")
+    src = os.path.join(ROOT, "paper_1306_1392_b300", "csrc", "backproject.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_sample_fbp(orc, raw_slice, flat, dark, angles, axis, target_s):
+    """Oracle FBP of one slice restricted to a band of rows, sized to about
+    target_s seconds: normalise + filter all angle rows, back-project R image
+    rows.  Returns (updates, prorated seconds, R, threads).  The filter is
+    per-slice work; R/N of its time is charged to the R rows."""
+    import numpy as np
+    n = N_PIX
+    t0 = time.perf_counter()
+    p = orc.normalise(raw_slice, flat, dark)
+    q = orc.ramlak_filter(p)
+    t_filter = time.perf_counter() - t0
+    cy = (n - 1) / 2.0
+    t0 = time.perf_counter()
+    orc.backproject(q, angles, axis, n, 4, orc.fbp_weight(N_ANG, 2.0 / n), cy=cy - (n // 2))
+    per_row = (time.perf_counter() - t0) / 4
+    R = int(max(4, min(n, (target_s - t_filter) / max(per_row, 1e-6))))
+    r0 = (n - R) // 2
+    t0 = time.perf_counter()
+    orc.backproject(q, angles, axis, n, R, orc.fbp_weight(N_ANG, 2.0 / n), cy=cy - r0)
+    t_bp = time.perf_counter() - t0
+    secs = t_bp + t_filter * R / n
+    return R * n * N_ANG, secs, R, orc.num_threads()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    import numpy as np
+    import torch
+    import oracle as orc
+    from synth import acquisition as acq
+    if rank != 0:
+        return
+    orc.build()
+    z = args.volume_slices // 2
+    vol = acq.ellipsoid_volume(n_slices=args.volume_slices, n=N_PIX, n_angles=N_ANG, seed=1000, device="cpu",
+                               slices=[z], dtype=torch.float32, compact=True)
+    raw = vol.raw[:, 0, :].double().numpy()
+    fl, dk = vol.flat[0].double().numpy(), vol.dark[0].double().numpy()
+    ang, ax = vol.angles.double().numpy(), vol.axis.double().numpy()
+    per_step_s = max(1.0, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_sample_fbp(orc, raw, fl, dk, ang, ax, per_step_s)
+    upd_total, secs_total, rows = 0, 0.0, []
+    for _ in range(args.steps):
+        u, s, R, threads = cpu_sample_fbp(orc, raw, fl, dk, ang, ax, per_step_s)
+        upd_total += u
+        secs_total += s
+        rows.append(R)
+    value = upd_total / secs_total / 1e9
+    sample = (f"each step: one slice of the workload (2000 x 2048 uint16 counts): normalise + filter all rows, "
+              f"back-project a band of {min(rows)}-{max(rows)} of its 2048 image rows; filter time prorated "
+              f"by rows/2048")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gupd/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA,
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Gupd/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gupd/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    S, NZ = args.slices_per_step, args.volume_slices
+    # inputs: this rank's shard (seeded per rank), generated on the device
+    vol = acq.ellipsoid_volume(n_slices=NZ, n=N_PIX, n_angles=N_ANG, seed=1000 + rank, device=dev)
+    raw, flat, dark = vol.raw, vol.flat, vol.dark
+    geo = P.Geometry(vol.angles.to(dev), vol.axis.to(dev), N_BINS, N_PIX, N_PIX, vol.pixel_size)
+    out = torch.empty((NZ, N_PIX, N_PIX), dtype=torch.float32, device=dev)
+    ws = torch.empty(P.pyhst_fbp_workspace_size(geo, S, 0, 4), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(k):
+        z0 = (k * S) % NZ
+        z1 = min(z0 + S, NZ)
+        P.pyhst_fbp(geo, raw, "u16_raw", flat, dark, out=out[z0:z1], workspace=ws, slices=(z0, z1))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    P.pyhst_profile_read("backproject"), P.pyhst_profile_read("filter")
+    P.pyhst_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record()
+        for k in range(args.steps):
+            step(args.warmup + k)
+        ev1.record()
+        barrier()
+    P.pyhst_profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    bp_ms, bp_n = P.pyhst_profile_read("backproject")
+    fl_ms, fl_n = P.pyhst_profile_read("filter")
+    slices_done = sum(min(((args.warmup + k) * S) % NZ + S, NZ) - ((args.warmup + k) * S) % NZ
+                      for k in range(args.steps))
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    n_tot = torch.tensor([slices_done], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_tot, op=dist.ReduceOp.SUM)
+    ms_max = t.item()
+    value = n_tot.item() * UPD_PER_SLICE / (ms_max * 1e-3) / 1e9
+
+    # ---- end to end through the host-buffer C-ABI call (same metric)
+    e2e = None
+    if not args.no_e2e:
+        z0 = NZ // 2 - S // 2
+        host_raw = torch.empty((N_ANG, S, N_BINS), dtype=torch.uint16, pin_memory=True)
+        host_raw.copy_(raw[:, z0:z0 + S, :].cpu())
+        host_flat = flat[z0:z0 + S].cpu().pin_memory()
+        host_dark = dark[z0:z0 + S].cpu().pin_memory()
+        host_out = torch.empty((S, N_PIX, N_PIX), dtype=torch.float32, pin_memory=True)
+        chunk = 8
+        hws = torch.empty(P.pyhst_fbp_host_workspace_size(geo, "u16_raw", S, 0, chunk), dtype=torch.uint8,
+                          device=dev)
+
+        def estep():
+            P.pyhst_fbp_host(geo, host_raw, "u16_raw", host_flat, host_dark, out=host_out,
+                             slices_per_chunk=chunk, workspace=hws)
+
+        for _ in range(max(1, min(args.warmup, 3))):
+            estep()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            estep()
+        e1.record()
+        barrier()
+        ems = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps * S * UPD_PER_SLICE / (ems.item() * 1e-3) / 1e9, "unit": "Gupd/s",
+               "h2d_bytes_per_step": int(host_raw.numel() * 2 + 2 * host_flat.numel() * 4),
+               "d2h_bytes_per_step": int(host_out.numel() * 4),
+               "call": "pyhst_fbp_host (pinned host in/out, 8-slice chunks double-buffered)"}
+
+    # ---- roofline of the back-projection kernel (dominant)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz") or 2032.0)
+    peak_ops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12      # T FP32 lane-ops/s
+    per_launch_upd = min(4, S) * UPD_PER_SLICE
+    bp_avg_s = bp_ms / max(1, bp_n) * 1e-3
+    achieved = OPS_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T FP32-ops/s",
+                "frac": achieved / peak_ops, "traffic": bp_traffic_from_profile(),
+                "kernel": "bp_kernel", "launches": bp_n, "avg_launch_ms": bp_avg_s * 1e3,
+                "gupd_per_s": per_launch_upd / bp_avg_s / 1e9,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (of measured max "
+                              f"SM clock), {OPS_PER_UPDATE} algorithmic FP32 ops per voxel-angle update",
+                "filter_share_of_step": fl_ms / ms}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as orc
+        orc.build()
+        z = NZ // 2
+        rs = raw[:, z, :].double().cpu().numpy()
+        u, secs, R, threads = cpu_sample_fbp(orc, rs, flat[z].double().cpu().numpy(),
+                                             dark[z].double().cpu().numpy(), vol.angles.double().numpy(),
+                                             vol.axis.double().numpy(), args.cpu_seconds)
+        cpu = {"value": u / secs / 1e9, "unit": "Gupd/s", "cores": threads, "kind": "oracle",
+               "sample": f"slice {z}: normalise + filter all 2000 rows, back-project {R} of 2048 image rows "
+                         f"(filter time prorated by rows); {secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gupd/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": DATA,
+                "config": {"workload": WORKLOAD, "slices_per_step": S, "volume_slices_per_gpu": NZ,
+                           "parallelism": f"slice shards, {world} GPU(s), no collective on the data path",
+                           "l2": f"inputs larger than L2: {S * N_ANG * N_BINS * 2 / 1e6:.0f} MB of raw counts "
+                                 f"per step; the whole {NZ}-slice stack ({raw.numel() * 2 / 1e9:.1f} GB) resident",
+                           "pad_len": 4096, "slices_per_pass": 4},
+                "fbp_slices_per_s": n_tot.item() / (ms_max * 1e-3),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(bp_n + fl_n + 3 * args.steps),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
+def run_kernel_case(args):
+    """A few launches of one kernel on the workload's slice geometry (4-slice
+    launch as in the timed FBP), inputs resident: a small, fixed case for
+    profilers.  Prints one JSON line with the event-timed launches."""
+    import torch
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    dev = torch.device("cuda", 0)
+    S = 4
+    ang = acq.uniform_angles(N_ANG).to(dev)
+    geo = P.Geometry(ang, torch.full((N_ANG,), (N_BINS - 1) / 2.0, device=dev), N_BINS, N_PIX, N_PIX, 2.0 / N_PIX)
+    g = torch.Generator(device=dev).manual_seed(5)
+    if args.kernel_case == "backproject":
+        q = torch.randn((S, N_ANG, N_BINS), device=dev, generator=g)
+        out = torch.empty((S, N_PIX, N_PIX), device=dev)
+        ws = torch.empty(P.pyhst_workspace_size(geo, P.PYHST_OP_BACKPROJECT, S), dtype=torch.uint8, device=dev)
+        fn = lambda: P.pyhst_backproject(geo, q, 1.0, out=out, workspace=ws)
+        upd = S * UPD_PER_SLICE
+    elif args.kernel_case == "project":
+        img = torch.randn((S, N_PIX, N_PIX), device=dev, generator=g)
+        out = torch.empty((S, N_ANG, N_BINS), device=dev)
+        ws = torch.empty(P.pyhst_workspace_size(geo, P.PYHST_OP_PROJECT, S), dtype=torch.uint8, device=dev)
+        fn = lambda: P.pyhst_project(geo, img, out=out, workspace=ws)
+        upd = S * UPD_PER_SLICE
+    else:
+        raw = torch.randint(1000, 30000, (N_ANG, S, N_BINS), device=dev, generator=g, dtype=torch.int32).to(torch.uint16)
+        fl = torch.full((S, N_BINS), 3e4, device=dev)
+        dk = torch.full((S, N_BINS), 100.0, device=dev)
+        out = torch.empty((S, N_ANG, N_BINS), device=dev)
+        fn = lambda: P.pyhst_filter(geo, raw, "u16_raw", fl, dk, out=out)
+        upd = S * N_ANG * N_BINS
+    fn()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ms = []
+    for k in range(3):
+        ev[0].record()
+        fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    print(json.dumps({"kernel_case": args.kernel_case, "ms": ms, "units_per_launch": upd,
+                      "g_units_per_s": upd / min(ms) / 1e6}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,34 @@ int pyhst_fbp(const pyhst_geometry *g, int input_type, const void *data,
               const float *flat, const float *dark, int filter, int32_t pad_len,
               float *out, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
+/* Normalisation and ramp filter only (the first two steps of pyhst_fbp):
+ * same inputs as pyhst_fbp, output q [n_slices][n_angles][n_bins] float32,
+ * the filtered sinograms (no angular weight).  Workspace:
+ * pyhst_filter_workspace_size (the FFT tables). */
+size_t pyhst_filter_workspace_size(const pyhst_geometry *g, int32_t pad_len);
+int pyhst_filter(const pyhst_geometry *g, int input_type, const void *data,
+                 int64_t slice_stride, int64_t angle_stride,
+                 const float *flat, const float *dark, int filter, int32_t pad_len,
+                 float *q, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* pyhst_fbp with HOST input and output: host_data (strides as in pyhst_fbp),
+ * host_flat/host_dark [n_slices][n_bins] and host_out [n_slices][ny][nx] are
+ * host memory (page-locked for the copies to overlap compute).  Chunks of
+ * slices_per_chunk slices are copied to the device on an internal stream,
+ * reconstructed on `stream` and copied back on a second internal stream, with
+ * two buffers of each so that copies overlap compute.  The internal streams
+ * start after the work already queued on `stream`, and the call's completion
+ * is ordered on `stream` (synchronise it before reading host_out).  The
+ * workspace (pyhst_fbp_host_workspace_size) holds the FBP scratch and the
+ * double-buffered chunks. */
+size_t pyhst_fbp_host_workspace_size(const pyhst_geometry *g, int input_type, int32_t pad_len,
+                                     int32_t slices_per_chunk);
+int pyhst_fbp_host(const pyhst_geometry *g, int input_type, const void *host_data,
+                   int64_t slice_stride, int64_t angle_stride,
+                   const float *host_flat, const float *host_dark, int filter, int32_t pad_len,
+                   float *host_out, int32_t slices_per_chunk, void *workspace, size_t ws_bytes,
+                   pyhst_stream_t stream);
+
 /* Back-projection (Sec. 2.3) of n_slices sinograms [n_slices][n_angles][n_bins]
  * into images [n_slices][ny][nx]:
  *     img[i][j] = weight * sum_a L(sino_a, t_a(i, j))
@@ -172,6 +200,14 @@ size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_tv_opts *opt
 size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n_slices);
 int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
                   float tau, float *x, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* Opt-in per-kernel timing for measurement: while enabled (per host thread),
+ * every launch of the back-projection, filter and projection kernels is
+ * bracketed by CUDA events on its launch stream.  pyhst_profile_read waits for
+ * the recorded launches of one kernel ("backproject", "filter" or "project"),
+ * returns their summed duration (ms) and count, and forgets them. */
+int pyhst_profile_enable(int on);
+int pyhst_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *pyhst_last_error(void);

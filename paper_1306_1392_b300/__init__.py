@@ -24,8 +24,9 @@ from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SIN
                    PYHST_OP_BACKPROJECT, PYHST_OP_FBP, PYHST_OP_PROJECT, PYHST_OP_TV_SOLVE, PYHST_RAMLAK,
                    PYHST_U16_RAW)
 
-__all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_backproject", "pyhst_project",
-           "pyhst_tv_solve", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
+__all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_filter", "pyhst_fbp_host",
+           "pyhst_profile_enable", "pyhst_profile_read", "pyhst_backproject", "pyhst_project",
+           "pyhst_tv_solve", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
            "pyhst_version", "library_path"]
 
 
@@ -120,6 +121,12 @@ def pyhst_fbp_workspace_size(geom: Geometry, n_slices: int = 1, pad_len: int = 0
     return int(L.lib.pyhst_fbp_workspace_size(ctypes.byref(g), pad_len, slices_per_pass))
 
 
+def pyhst_fbp_host_workspace_size(geom: Geometry, kind: str, n_slices: int, pad_len: int = 0,
+                                  slices_per_chunk: int = 16) -> int:
+    g = geom.c(n_slices)
+    return int(L.lib.pyhst_fbp_host_workspace_size(ctypes.byref(g), _KINDS[kind][0], pad_len, slices_per_chunk))
+
+
 def pyhst_workspace_size(geom: Geometry, op: int, n_slices: int = 1) -> int:
     g = geom.c(n_slices)
     return int(L.lib.pyhst_workspace_size(ctypes.byref(g), op))
@@ -147,7 +154,7 @@ _KINDS = {"u16_raw": (PYHST_U16_RAW, torch.uint16), "f32_raw": (PYHST_F32_RAW, t
 
 def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
               pad_len: int = 0, out=None, workspace=None, ws_bytes: int = None,
-              slices_per_pass: int = 4) -> torch.Tensor:
+              slices_per_pass: int = 4, slices: tuple = None) -> torch.Tensor:
     """Filtered back-projection of every slice in ``data``.
 
     ``layout`` "projections": data [n_angles, n_slices, n_bins] (a raw
@@ -155,21 +162,13 @@ def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=Non
     [n_slices, n_angles, n_bins].  Default: projections for raw kinds,
     sinograms otherwise.  flat/dark [n_slices, n_bins] float32 for raw kinds.
     Without a ``workspace`` one is allocated for ``slices_per_pass`` slices.
+    ``slices=(z0, z1)`` reconstructs only that range of the stack (read in
+    place); ``out`` then holds z1 - z0 slices.
     """
     code, dt = _KINDS[kind]
     _cuda(data, "data", (dt,))
     raw = kind.endswith("raw")
-    layout = layout or ("projections" if raw else "sinograms")
-    if data.dim() == 2:
-        data = data.unsqueeze(1 if layout == "projections" else 0)
-    if layout == "projections":
-        na, ns, nb = data.shape
-        s_stride, a_stride = nb, ns * nb
-    elif layout == "sinograms":
-        ns, na, nb = data.shape
-        s_stride, a_stride = na * nb, nb
-    else:
-        raise ValueError(f"unknown layout {layout}")
+    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
     if na != geom.n_angles or nb != geom.n_bins:
         raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
     if raw:
@@ -177,16 +176,95 @@ def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=Non
         _cuda(dark, "dark", (torch.float32,))
         if flat.shape != (ns, nb) or dark.shape != (ns, nb):
             raise ValueError("flat/dark must be [n_slices, n_bins]")
+    z0, z1 = (0, ns) if slices is None else slices
+    if not 0 <= z0 < z1 <= ns:
+        raise ValueError(f"slice range {slices} outside [0, {ns}]")
     if out is None:
-        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
+        out = torch.empty((z1 - z0, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
     _cuda(out, "out", (torch.float32,))
-    g = geom.c(ns)
+    if out.numel() < (z1 - z0) * geom.ny * geom.nx:
+        raise ValueError("out is too small")
+    g = geom.c(z1 - z0)
     need = L.lib.pyhst_fbp_workspace_size(ctypes.byref(g), pad_len, slices_per_pass)
     ws = _workspace(need, data.device, workspace)
     nbytes = ws.numel() * ws.element_size() if ws_bytes is None else ws_bytes
-    _check(L.lib.pyhst_fbp(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
+    es = data.element_size()
+    dptr = ctypes.c_void_p(data.data_ptr() + z0 * s_stride * es)
+    fptr = ctypes.c_void_p(flat.data_ptr() + z0 * nb * 4) if raw else None
+    kptr = ctypes.c_void_p(dark.data_ptr() + z0 * nb * 4) if raw else None
+    _check(L.lib.pyhst_fbp(ctypes.byref(g), code, dptr, s_stride, a_stride, fptr, kptr,
                            PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), nbytes, _stream()))
     return out
+
+
+def _layout(data, kind, layout):
+    raw = kind.endswith("raw")
+    layout = layout or ("projections" if raw else "sinograms")
+    if data.dim() == 2:
+        data = data.unsqueeze(1 if layout == "projections" else 0)
+    if layout == "projections":
+        na, ns, nb = data.shape
+        return data, ns, na, nb, nb, ns * nb
+    if layout == "sinograms":
+        ns, na, nb = data.shape
+        return data, ns, na, nb, na * nb, nb
+    raise ValueError(f"unknown layout {layout}")
+
+
+def pyhst_filter(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
+                 pad_len: int = 0, out=None, workspace=None) -> torch.Tensor:
+    """Normalised, Ram-Lak filtered sinograms q [n_slices, n_angles, n_bins]
+    (the first two steps of pyhst_fbp; same data conventions)."""
+    code, dt = _KINDS[kind]
+    _cuda(data, "data", (dt,))
+    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
+    if na != geom.n_angles or nb != geom.n_bins:
+        raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
+    if out is None:
+        out = torch.empty((ns, na, nb), dtype=torch.float32, device=data.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    ws = _workspace(L.lib.pyhst_filter_workspace_size(ctypes.byref(g), pad_len), data.device, workspace)
+    _check(L.lib.pyhst_filter(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
+                              PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def pyhst_fbp_host(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, out=None,
+                   layout: str = None, pad_len: int = 0, slices_per_chunk: int = 16, workspace=None,
+                   device=None) -> torch.Tensor:
+    """pyhst_fbp on HOST tensors (pin them for overlap): chunks are streamed
+    through the device by the library.  Returns the host output; the work is
+    queued on the current stream (synchronise before reading it)."""
+    code, dt = _KINDS[kind]
+    if data.is_cuda or data.dtype != dt or not data.is_contiguous():
+        raise TypeError("data must be a contiguous host tensor of the kind's dtype")
+    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
+    if kind.endswith("raw"):
+        for t, nm in ((flat, "flat"), (dark, "dark")):
+            if t is None or t.is_cuda or t.dtype != torch.float32 or tuple(t.shape) != (ns, nb) or not t.is_contiguous():
+                raise TypeError(f"{nm} must be a contiguous float32 host tensor [n_slices, n_bins]")
+    if out is None:
+        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, pin_memory=True)
+    g = geom.c(ns)
+    need = L.lib.pyhst_fbp_host_workspace_size(ctypes.byref(g), code, pad_len, slices_per_chunk)
+    ws = _workspace(need, device or geom.angles.device, workspace)
+    _check(L.lib.pyhst_fbp_host(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
+                                PYHST_RAMLAK, pad_len, _ptr(out), slices_per_chunk, _ptr(ws), ws.numel(),
+                                _stream()))
+    return out
+
+
+def pyhst_profile_enable(on: bool = True) -> None:
+    _check(L.lib.pyhst_profile_enable(int(bool(on))))
+
+
+def pyhst_profile_read(kernel: str):
+    """(total ms, launches) of the recorded launches of "backproject",
+    "filter" or "project" since the last read."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(L.lib.pyhst_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def pyhst_backproject(geom: Geometry, sino: torch.Tensor, weight: float, out=None, workspace=None):

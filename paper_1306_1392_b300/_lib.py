@@ -44,6 +44,12 @@ SIGNATURES = [
     ("pyhst_fbp_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32]),
     ("pyhst_fbp", c_int32, [ctypes.POINTER(pyhst_geometry), c_int32, c_void_p, c_int64, c_int64, c_void_p,
                             c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_filter_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32]),
+    ("pyhst_filter", c_int32, [ctypes.POINTER(pyhst_geometry), c_int32, c_void_p, c_int64, c_int64, c_void_p,
+                               c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_fbp_host_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32, c_int32]),
+    ("pyhst_fbp_host", c_int32, [ctypes.POINTER(pyhst_geometry), c_int32, c_void_p, c_int64, c_int64, c_void_p,
+                                 c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     ("pyhst_backproject", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_float, c_void_p,
                                     c_size_t, c_void_p]),
     ("pyhst_project", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_void_p, c_size_t,
@@ -54,6 +60,8 @@ SIGNATURES = [
     ("pyhst_tv_prox_workspace_size", c_size_t, [c_int32, c_int32, c_int32]),
     ("pyhst_tv_prox", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_float, c_int32, c_float, c_void_p,
                                 c_void_p, c_size_t, c_void_p]),
+    ("pyhst_profile_enable", c_int32, [c_int32]),
+    ("pyhst_profile_read", c_int32, [ctypes.c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     ("pyhst_last_error", ctypes.c_char_p, []),
     ("pyhst_version", ctypes.c_char_p, []),
 ]

@@ -146,6 +146,7 @@ int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource s
     const int tiles_y = (g->ny + kTY - 1) / kTY;
     dim3 grid(tiles_x * tiles_y, g->n_slices);
     if (grid.y > 65535) return fail(PYHST_ERR_INVALID_ARG, "too many slices in one call (%d)", g->n_slices);
+    ProfScope prof(kProfBackproject, st);
     if (src.b)
         bp_kernel<true><<<grid, kThreads, 0, st>>>(tab, src.a, src.b, img, g->n_angles, g->n_bins, g->nx,
                                                    g->ny, g->cx, g->cy, weight, tiles_x);

@@ -65,6 +65,18 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
                    float scale, float *xt, cudaStream_t st);
 size_t project_scratch_bytes(const pyhst_geometry *g);
 
+// ----------------------------------------------------------------- profiling
+// Opt-in per-launch timing (pyhst_profile_enable): events recorded on the
+// launch stream around each kernel of a kind; off by default.
+enum ProfKind { kProfBackproject = 0, kProfFilter = 1, kProfProject = 2, kProfKinds = 3 };
+struct ProfScope {
+    int kind;
+    cudaStream_t st;
+    void *end;
+    ProfScope(int kind, cudaStream_t st);
+    ~ProfScope();
+};
+
 // ----------------------------------------------------------------- device helpers
 // floor(u) for 0 <= u < 2^22 in one add rounded toward -inf: the sum with
 // 1.5 * 2^23 has unit spacing, so its low mantissa bits hold floor(u).

@@ -196,6 +196,7 @@ int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angl
                                                       n_rows, n_angles, n_bins, P, logP, tw, hrev, q); \
         break;                                                                                        \
     }
+    ProfScope prof(kProfFilter, st);
     switch (kind) {
         PYHST_FILTER_CASE(PYHST_U16_RAW)
         PYHST_FILTER_CASE(PYHST_F32_RAW)

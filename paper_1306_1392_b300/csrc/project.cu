@@ -118,6 +118,7 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     int rc = cuda_status("transpose kernel");
     if (rc) return rc;
     dim3 grid((g->n_bins + kRayThreads - 1) / kRayThreads, g->n_angles, g->n_slices);
+    ProfScope prof(kProfProject, st);
     ray_kernel<<<grid, kRayThreads, 0, st>>>(tab, img, xt, sino, g->n_angles, g->n_bins, g->nx, g->ny,
                                              g->cx, g->cy, scale);
     return cuda_status("projection kernel");

@@ -104,12 +104,15 @@ class Volume:
 
 
 def ellipsoid_volume(n_slices: int, n: int, n_angles: int, seed: int, device="cpu",
-                     n_ellipsoids: int = 200, slices=None, dtype=None) -> Volume:
+                     n_ellipsoids: int = 200, slices=None, dtype=None, compact: bool = False) -> Volume:
     """Raw uint16 radiographies of ``n_ellipsoids`` random ellipsoids: the
     detector has n bins of size s = 2/n across [-1,1], the n_slices detector
     rows sit at z = (k - (n_slices-1)/2) * s.  Counts are
-    clip(round(Poisson(F_true * exp(-p)) + D), 0, 65535).  ``slices`` restricts
-    generation to a subset of rows (others stay zero)."""
+    clip(round(Poisson(F_true * exp(-p)) + D), 0, 65535), with the noise of
+    detector row k drawn from its own seeded generator (so any subset of rows
+    is generated identically on a given device).  ``slices`` restricts
+    generation to a subset of rows: the others stay zero, or with
+    ``compact`` the stack holds only the listed rows (flat/dark likewise)."""
     device = torch.device(device)
     dtype = dtype or (torch.float64 if device.type == "cpu" else torch.float32)
     s = 2.0 / n
@@ -117,18 +120,22 @@ def ellipsoid_volume(n_slices: int, n: int, n_angles: int, seed: int, device="cp
     ax = torch.full((n_angles,), (n - 1) / 2.0, dtype=torch.float32)
     E = ph.random_ellipsoids(n_ellipsoids, seed, z_half=0.5 * n_slices * s)
     flat, dark, F_true = flat_dark_fields(n_slices, n, seed)
-    raw = torch.zeros((n_angles, n_slices, n), dtype=torch.uint16, device=device)
+    rows = list(range(n_slices)) if slices is None else list(slices)
+    raw = torch.zeros((n_angles, len(rows) if compact else n_slices, n), dtype=torch.uint16, device=device)
     t = bin_offsets(ang, ax, n, s, dtype=dtype, device=device)
     th = ang.to(dtype=dtype, device=device)
-    gen = torch.Generator(device=device).manual_seed(seed)
+    gen = torch.Generator(device=device)
     zs = (torch.arange(n_slices, dtype=torch.float64) - (n_slices - 1) / 2.0) * s
     Fd = F_true.to(device=device, dtype=dtype)
     Dd = dark.to(device=device, dtype=dtype)
-    for k in (range(n_slices) if slices is None else slices):
+    for o, k in enumerate(rows):
         ell = ph.ellipsoid_section(E, float(zs[k]))
         p = ph.ellipse_sinogram(ell, th, t) if len(ell) else torch.zeros_like(t)
+        gen.manual_seed(seed * 1_000_003 + k)
         cnt = torch.poisson(Fd[k][None, :] * torch.exp(-p), generator=gen) + Dd[k][None, :]
-        raw[:, k, :] = torch.clamp(torch.round(cnt), 0, 65535).to(torch.int32).to(torch.uint16)
+        raw[:, o if compact else k, :] = torch.clamp(torch.round(cnt), 0, 65535).to(torch.int32).to(torch.uint16)
+    if compact:
+        flat, dark, zs = flat[rows], dark[rows], zs[rows]
     return Volume(raw, flat.to(device), dark.to(device), ang, ax, n, n, n, s, zs, E)
 
 

@@ -228,3 +228,45 @@ def test_fbp_full_size_volume_sampled(P, orc, cuda_device):
                                  orc.fbp_weight(na, vol.pixel_size))
         g = got[z].cpu().numpy()[ii, jj]
         close(g, ref)
+
+
+def test_filter_only_parity(P, orc, cuda_device):
+    """pyhst_filter: normalised and Ram-Lak filtered rows (the first two
+    steps of the FBP) against the oracle's, for raw uint16 input."""
+    vol = acq.ellipsoid_volume(n_slices=3, n=200, n_angles=50, seed=21, n_ellipsoids=30)
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
+                   cuda_device)
+    q = P.pyhst_filter(geo, vol.raw.to(cuda_device), "u16_raw", vol.flat.to(cuda_device), vol.dark.to(cuda_device))
+    torch.cuda.synchronize()
+    for z in range(3):
+        ref = orc.ramlak_filter(orc.normalise(vol.raw[:, z, :].double().numpy(), vol.flat[z].double().numpy(),
+                                              vol.dark[z].double().numpy()))
+        close(f64(q[z]), ref)
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 8])
+def test_fbp_host_pipeline_matches_device_call(P, cuda_device, chunk):
+    """pyhst_fbp_host on pinned host buffers gives bitwise the device call's
+    slices, for chunk sizes that do and do not divide the stack."""
+    vol = acq.ellipsoid_volume(n_slices=7, n=128, n_angles=90, seed=31, n_ellipsoids=40)
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
+                   cuda_device)
+    dev_out = P.pyhst_fbp(geo, vol.raw.to(cuda_device), "u16_raw", vol.flat.to(cuda_device),
+                          vol.dark.to(cuda_device))
+    host_out = P.pyhst_fbp_host(geo, vol.raw.contiguous().pin_memory(), "u16_raw", vol.flat.pin_memory(),
+                                vol.dark.pin_memory(), slices_per_chunk=chunk)
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, dev_out.cpu())
+
+
+def test_fbp_slice_range_in_place(P, cuda_device):
+    """A slice range of a resident stack, read in place, equals the same
+    slices of a whole-stack call."""
+    vol = acq.ellipsoid_volume(n_slices=9, n=96, n_angles=60, seed=41, n_ellipsoids=40)
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
+                   cuda_device)
+    raw, fl, dk = vol.raw.to(cuda_device), vol.flat.to(cuda_device), vol.dark.to(cuda_device)
+    full = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk)
+    part = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk, slices=(3, 8))
+    torch.cuda.synchronize()
+    assert torch.equal(full[3:8], part)
