@@ -35,6 +35,8 @@ DATA = ("synthetic: seeded ellipsoid phantom, exact (closed-form) line integrals
         "uint16; random numbers drawn once at set-up")
 UPD_PER_SLICE = N_PIX * N_PIX * N_ANG
 OPS_PER_UPDATE = 4          # coordinate FMA, floor add, interpolation FMA, accumulate add
+SMEM_BYTES_PER_UPDATE = 8   # one float32 (dq, c0) window entry read from shared memory
+SMEM_BYTES_PER_CLK = 128    # shared-memory data pipe per SM per clock
 
 
 def parse():
@@ -296,13 +298,20 @@ def run_ours(args, rank, world, local_rank):
     peak_ops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12      # T FP32 lane-ops/s
     per_launch_upd = min(4, S) * UPD_PER_SLICE
     bp_avg_s = bp_ms / max(1, bp_n) * 1e-3
-    achieved = OPS_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "T FP32-ops/s",
-                "frac": achieved / peak_ops, "traffic": bp_traffic_from_profile(),
+    peak_smem = props.multi_processor_count * SMEM_BYTES_PER_CLK * sm_max * 1e6 / 1e12   # TB/s
+    achieved = SMEM_BYTES_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
+    alu = OPS_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
+    roofline = {"bound": "smem", "achieved": achieved, "peak": peak_smem, "unit": "TB/s",
+                "frac": achieved / peak_smem, "traffic": bp_traffic_from_profile(),
                 "kernel": "bp_kernel", "launches": bp_n, "avg_launch_ms": bp_avg_s * 1e3,
                 "gupd_per_s": per_launch_upd / bp_avg_s / 1e9,
-                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (of measured max "
-                              f"SM clock), {OPS_PER_UPDATE} algorithmic FP32 ops per voxel-angle update",
+                "peak_basis": f"shared-memory data pipe: {props.multi_processor_count} SMs x "
+                              f"{SMEM_BYTES_PER_CLK} B/clk x {sm_max:.0f} MHz (measured max SM clock); "
+                              f"{SMEM_BYTES_PER_UPDATE} B (one float32 (dq, c0) pair) per voxel-angle update; "
+                              "traffic = DRAM bytes per launch from the committed ncu capture",
+                "alu": {"achieved": alu, "peak": peak_ops, "unit": "T FP32 lane-ops/s", "frac": alu / peak_ops,
+                        "basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz; "
+                                 f"{OPS_PER_UPDATE} FP32 ops per update"},
                 "filter_share_of_step": fl_ms / ms}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
