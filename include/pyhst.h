@@ -145,6 +145,27 @@ int pyhst_fbp_host(const pyhst_geometry *g, int input_type, const void *host_dat
                    float *host_out, int32_t slices_per_chunk, void *workspace, size_t ws_bytes,
                    pyhst_stream_t stream);
 
+/* pyhst_fbp without a workspace, for callers that cannot allocate device
+ * memory (for example code inside a host framework that owns all device
+ * allocations and exposes none to plug-ins, or an acquisition loop that may
+ * not call cudaMalloc once it runs).  The paper has no counterpart: this is
+ * an interface of this library only.  Arguments and results are those of
+ * pyhst_fbp; the scratch is one fixed device array of
+ * pyhst_fbp_static_max_bytes() bytes (32 MiB) inside the library, which every
+ * GPU that loads the library holds until the process exits.  A geometry whose
+ * angle table, FFT tables and one slice of filtered rows do not fit
+ * (n_angles * n_bins * 4 bytes plus about 16 * pad_len bytes) is rejected with
+ * PYHST_ERR_INVALID_ARG before anything runs.  The first call on a device
+ * looks up the array's address on that device (make it before any stream
+ * capture).  All calls share the array: calls that overlap on the GPU race on
+ * it, so order them on one stream.  Nothing in it needs clearing between
+ * calls; it allocates nothing. */
+size_t pyhst_fbp_static_max_bytes(void);
+int pyhst_fbp_static(const pyhst_geometry *g, int input_type, const void *data,
+                     int64_t slice_stride, int64_t angle_stride,
+                     const float *flat, const float *dark, int filter, int32_t pad_len,
+                     float *out, pyhst_stream_t stream);
+
 /* Back-projection (Sec. 2.3) of n_slices sinograms [n_slices][n_angles][n_bins]
  * into images [n_slices][ny][nx]:
  *     img[i][j] = weight * sum_a L(sino_a, t_a(i, j))

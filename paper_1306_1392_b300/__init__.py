@@ -25,7 +25,7 @@ from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SIN
                    PYHST_U16_RAW)
 
 __all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_filter", "pyhst_fbp_host",
-           "pyhst_profile_enable", "pyhst_profile_read", "pyhst_backproject", "pyhst_project",
+           "pyhst_profile_enable", "pyhst_profile_read", "pyhst_fbp_static", "pyhst_backproject", "pyhst_project",
            "pyhst_tv_solve", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
            "pyhst_version", "library_path"]
 
@@ -252,6 +252,25 @@ def pyhst_fbp_host(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dar
     _check(L.lib.pyhst_fbp_host(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
                                 PYHST_RAMLAK, pad_len, _ptr(out), slices_per_chunk, _ptr(ws), ws.numel(),
                                 _stream()))
+    return out
+
+
+def pyhst_fbp_static(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
+                     pad_len: int = 0, out=None) -> torch.Tensor:
+    """pyhst_fbp for callers that cannot allocate device scratch: the library
+    uses its own fixed device array (see include/pyhst.h); calls that overlap
+    on the GPU race on it."""
+    code, dt = _KINDS[kind]
+    _cuda(data, "data", (dt,))
+    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
+    if na != geom.n_angles or nb != geom.n_bins:
+        raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
+    if out is None:
+        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    _check(L.lib.pyhst_fbp_static(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
+                                  PYHST_RAMLAK, pad_len, _ptr(out), _stream()))
     return out
 
 

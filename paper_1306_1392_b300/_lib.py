@@ -50,6 +50,9 @@ SIGNATURES = [
     ("pyhst_fbp_host_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32, c_int32]),
     ("pyhst_fbp_host", c_int32, [ctypes.POINTER(pyhst_geometry), c_int32, c_void_p, c_int64, c_int64, c_void_p,
                                  c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_fbp_static_max_bytes", c_size_t, []),
+    ("pyhst_fbp_static", c_int32, [ctypes.POINTER(pyhst_geometry), c_int32, c_void_p, c_int64, c_int64, c_void_p,
+                                   c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     ("pyhst_backproject", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_float, c_void_p,
                                     c_size_t, c_void_p]),
     ("pyhst_project", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_void_p, c_size_t,
