@@ -7,15 +7,23 @@
 // The paper's kernel reads the sinogram through the texture unit with hardware
 // interpolation, one output tile per thread block.  Hardware filtering keeps
 // only 8 fractional bits of the weight, too coarse for float32 parity, so
-// here each CTA owns a 64 x 32 output tile and, for blocks of 32 angles,
+// here each CTA owns a 64 x 64 output tile and, for blocks of 16 angles,
 // stages in shared memory the window of each filtered row that the tile can
 // reach.  Each window entry k holds (dq, c0) = (q[g+1] - q[g], q[g] - k dq)
 // for bin g = w0 + k, so that at the tile-local coordinate u (k <= u < k+1)
 //   L = c0 + u * dq     (one FMA),
 // and floor(u) comes from one add rounded toward -inf (see add_rd).  The
-// tile-local coordinate u = (T0 - w0) + dx cos + dy sin is small (< 76), so
-// float32 keeps ~4e-6 bins of accuracy; T0, the coordinate of the tile origin,
+// tile-local coordinate u = (T0 - w0) + dx cos + dy sin is small (< 96), so
+// float32 keeps ~1e-5 bins of accuracy; T0, the coordinate of the tile origin,
 // is formed in float64 once per (tile, angle).
+//
+// Throughput: the inner loop reads one 8-byte window entry per update, which
+// the shared-memory data pipe serves in two wavefronts per warp, so the kernel
+// is bound by shared memory (128 B/clk/SM).  Everything else is kept off that
+// pipe and off the issue slots: 16 pixels per thread amortise the per-angle
+// set-up, paired float32 instructions (f32x2) form the floors and the
+// accumulations, and the next block's windows are prefetched into registers
+// from L2 while the current block is computed, with one barrier per block.
 #include <climits>
 #include <cmath>
 
@@ -25,10 +33,12 @@ namespace pyhst {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTX = 64, kTY = 32;   // CTA output tile (x, y)
-constexpr int kRX = 4, kRY = 2;     // pixels per thread: x stride 8, y stride 4
-constexpr int kNA = 32;             // angles staged per pass
-constexpr int kW = 76;              // window entries per angle: ceil(hypot(63, 31)) + 4, rounded up
+constexpr int kTX = 64, kTY = 64;   // CTA output tile (x, y)
+constexpr int kRX = 4, kRY = 4;     // pixels per thread: x stride 8, y stride 4 (warp: 32 x 16)
+constexpr int kNA = 16;             // angles staged per block
+constexpr int kW = 96;              // window entries per angle: ceil(hypot(63, 63)) + 4, rounded up
+constexpr int kFill = kNA * kW / kThreads;   // window entries each thread fills per block (6)
+static_assert(kNA % (kThreads / 32) == 0 && kW % 32 == 0, "fill mapping");
 
 struct __align__(16) StageInfo {
     float base;   // u at the tile origin
@@ -36,13 +46,35 @@ struct __align__(16) StageInfo {
     int w0;       // detector bin of window entry 0
 };
 
+// Per-(tile, angle) set-up in float64.  Padding angles (past n_angles) and
+// angles whose coordinates are not finite or beyond any detector read an
+// all-zero window at a fixed in-range position.
+__device__ __forceinline__ StageInfo stage_info(const AngleInfo *tab, int a, int n_angles, int X0, int Y0,
+                                                double cx, double cy) {
+    StageInfo si;
+    si.base = 1.5f; si.cf = 0.0f; si.sf = 0.0f; si.w0 = INT_MIN / 2;
+    if (a < n_angles) {
+        const AngleInfo e = tab[a];
+        const double T0 = ((double)X0 - cx) * e.c + ((double)Y0 - cy) * e.s + e.axis;
+        const double tmin = T0 + fmin(0.0, (kTX - 1) * e.c) + fmin(0.0, (kTY - 1) * e.s);
+        const double w0 = floor(tmin) - 1.0;       // one guard entry below
+        if (fabs(T0) < 1.0e9) {
+            si.base = (float)(T0 - w0);
+            si.cf = e.cf;
+            si.sf = e.sf;
+            si.w0 = (int)w0;
+        }
+    }
+    return si;
+}
+
 template <bool kResidual>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
 bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
           const float *__restrict__ srcB, float *__restrict__ img, int n_angles, int n_bins,
           int nx, int ny, double cx, double cy, float weight, int tiles_x) {
-    __shared__ __align__(16) float2 win[kNA * kW];
-    __shared__ StageInfo info[kNA];
+    __shared__ __align__(16) float2 win[2][kNA * kW];
+    __shared__ StageInfo info[3][kNA];
 
     const int slice = blockIdx.y;
     const int X0 = (blockIdx.x % tiles_x) * kTX;
@@ -51,80 +83,87 @@ bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
     const float *A = srcA + sino_off;
     const float *B = kResidual ? srcB + sino_off : nullptr;
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int px = (warp & 1) * 32 + (lane & 7);   // first pixel of this thread in the tile
-    const int py = (warp >> 1) * 8 + (lane >> 3);
+    const int py = (warp >> 1) * 16 + (lane >> 3);
     const float fpx = (float)px, fpy = (float)py;
-    const uint32_t win_s = smem_addr(win);
+    const int n_blocks = (n_angles + kNA - 1) / kNA;
 
-    float acc[kRY][kRX];
+    // Window fill: warp w fills angles w and w + 8 of a block, lanes the entries.
+    float q0r[kFill], q1r[kFill];
+    auto prefetch = [&](int blk) {
+        const StageInfo *ib = info[blk % 3];
+#pragma unroll
+        for (int j = 0; j < kFill; ++j) {
+            const int a = warp + (j / 3) * (kThreads / 32), e = lane + 32 * (j % 3);
+            const int g = ib[a].w0 + e;
+            const int ag = blk * kNA + a;
+            const size_t row = (size_t)min(ag, n_angles - 1) * n_bins;
+            float v0 = 0.0f, v1 = 0.0f;
+            if (g >= 0 && g < n_bins) {
+                v0 = __ldg(A + row + g);
+                if (kResidual) v0 -= __ldg(B + row + g);
+            }
+            if (g + 1 >= 0 && g + 1 < n_bins) {
+                v1 = __ldg(A + row + g + 1);
+                if (kResidual) v1 -= __ldg(B + row + g + 1);
+            }
+            q0r[j] = v0;
+            q1r[j] = v1;
+        }
+    };
+    auto commit = [&](int buf) {
+#pragma unroll
+        for (int j = 0; j < kFill; ++j) {
+            const int a = warp + (j / 3) * (kThreads / 32), e = lane + 32 * (j % 3);
+            const float dq = q1r[j] - q0r[j];
+            win[buf][a * kW + e] = make_float2(dq, fmaf(-(float)e, dq, q0r[j]));
+        }
+    };
+
+    float2 acc[kRY][kRX / 2];
 #pragma unroll
     for (int ry = 0; ry < kRY; ++ry)
 #pragma unroll
-        for (int rx = 0; rx < kRX; ++rx) acc[ry][rx] = 0.0f;
+        for (int rp = 0; rp < kRX / 2; ++rp) acc[ry][rp] = make_float2(0.0f, 0.0f);
+    const float2 magic2 = make_float2(kMagic, kMagic);
 
-    for (int a0 = 0; a0 < n_angles; a0 += kNA) {
-        const int na = min(kNA, n_angles - a0);
-        if (threadIdx.x < kNA) {
-            StageInfo si;
-            si.base = 0.0f; si.w0 = 0;
-            if ((int)threadIdx.x < na) {
-                const AngleInfo e = tab[a0 + threadIdx.x];
-                const double T0 = ((double)X0 - cx) * e.c + ((double)Y0 - cy) * e.s + e.axis;
-                const double tmin = T0 + fmin(0.0, (kTX - 1) * e.c) + fmin(0.0, (kTY - 1) * e.s);
-                const double w0 = floor(tmin) - 1.0;       // one guard entry below
-                si.base = (float)(T0 - w0);
-                si.cf = e.cf;
-                si.sf = e.sf;
-                si.w0 = (int)w0;
-            }
-            // Padding angles of the last block, and angles whose coordinates
-            // are not finite or beyond any detector (|t| >= 1e9 bins), read
-            // an all-zero window at a fixed in-range position.
-            if ((int)threadIdx.x >= na || !(fabs(si.base) < 1.0e3f) || !(fabs((double)si.w0) < 1.0e9)) {
-                si.base = 1.5f; si.cf = 0.0f; si.sf = 0.0f; si.w0 = INT_MIN / 2;
-            }
-            info[threadIdx.x] = si;
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < kNA * kW; k += kThreads) {
-            const int a = k / kW, e = k - a * kW;
-            float2 v = make_float2(0.0f, 0.0f);
-            if (a < na) {
-                const int g = info[a].w0 + e;
-                const size_t row = (size_t)(a0 + a) * n_bins;
-                float q0 = 0.0f, q1 = 0.0f;
-                if (g >= 0 && g < n_bins) {
-                    q0 = A[row + g];
-                    if (kResidual) q0 -= B[row + g];
-                }
-                if (g + 1 >= 0 && g + 1 < n_bins) {
-                    q1 = A[row + g + 1];
-                    if (kResidual) q1 -= B[row + g + 1];
-                }
-                const float dq = q1 - q0;
-                v = make_float2(dq, fmaf(-(float)e, dq, q0));
-            }
-            win[k] = v;
-        }
-        __syncthreads();
+    // prologue: info of blocks 0 and 1, window of block 0
+    if (tid < kNA) info[0][tid] = stage_info(tab, tid, n_angles, X0, Y0, cx, cy);
+    __syncthreads();
+    prefetch(0);
+    commit(0);
+    if (tid < kNA) info[1][tid] = stage_info(tab, kNA + tid, n_angles, X0, Y0, cx, cy);
+    __syncthreads();
+
+    for (int blk = 0; blk < n_blocks; ++blk) {
+        const int cur = blk & 1;
+        const bool more = blk + 1 < n_blocks;
+        if (more) prefetch(blk + 1);
+        if (tid < kNA && blk + 2 < n_blocks)
+            info[(blk + 2) % 3][tid] = stage_info(tab, (blk + 2) * kNA + tid, n_angles, X0, Y0, cx, cy);
+        const StageInfo *ib = info[blk % 3];
+        const uint32_t wbase = smem_addr(win[cur]) - (kMagicBits << 3);
 #pragma unroll 2
-        for (int a = 0; a < na; ++a) {
-            const StageInfo si = info[a];
-            const uint32_t wb = win_s + (uint32_t)(a * kW * 8) - (kMagicBits << 3);
+        for (int a = 0; a < kNA; ++a) {
+            const StageInfo si = ib[a];
+            const uint32_t wb = wbase + (uint32_t)(a * kW * 8);
             const float r0 = fmaf(fpy, si.sf, fmaf(fpx, si.cf, si.base));
 #pragma unroll
             for (int ry = 0; ry < kRY; ++ry) {
                 const float rb = fmaf((float)(4 * ry), si.sf, r0);
 #pragma unroll
-                for (int rx = 0; rx < kRX; ++rx) {
-                    const float u = fmaf((float)(8 * rx), si.cf, rb);
-                    const uint32_t bits = __float_as_uint(add_rd(u, kMagic));
-                    const float2 w = lds64(wb + (bits << 3));
-                    acc[ry][rx] += fmaf(u, w.x, w.y);
+                for (int rp = 0; rp < kRX / 2; ++rp) {
+                    const float u0 = fmaf((float)(16 * rp), si.cf, rb);
+                    const float u1 = fmaf((float)(16 * rp + 8), si.cf, rb);
+                    const float2 tm = add2_rd(make_float2(u0, u1), magic2);
+                    const float2 w0 = lds64(wb + (__float_as_uint(tm.x) << 3));
+                    const float2 w1 = lds64(wb + (__float_as_uint(tm.y) << 3));
+                    acc[ry][rp] = add2(acc[ry][rp], make_float2(fmaf(u0, w0.x, w0.y), fmaf(u1, w1.x, w1.y)));
                 }
             }
         }
+        if (more) commit(cur ^ 1);
         __syncthreads();
     }
 
@@ -132,9 +171,13 @@ bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
 #pragma unroll
     for (int ry = 0; ry < kRY; ++ry)
 #pragma unroll
-        for (int rx = 0; rx < kRX; ++rx) {
-            const int x = X0 + px + 8 * rx, y = Y0 + py + 4 * ry;
-            if (x < nx && y < ny) out[(size_t)y * nx + x] = weight * acc[ry][rx];
+        for (int rp = 0; rp < kRX / 2; ++rp) {
+            const int y = Y0 + py + 4 * ry;
+            const int x0 = X0 + px + 16 * rp;
+            if (y < ny) {
+                if (x0 < nx) out[(size_t)y * nx + x0] = weight * acc[ry][rp].x;
+                if (x0 + 8 < nx) out[(size_t)y * nx + x0 + 8] = weight * acc[ry][rp].y;
+            }
         }
 }
 
