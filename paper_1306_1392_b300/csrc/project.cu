@@ -4,15 +4,38 @@
 // last paragraph; Eq. 1 and Eq. 3).
 //
 // The paper keeps the volume in a texture.  Here the projector is ray-driven
-// and deterministic (no atomics): one thread per (angle, bin).  For an angle
-// whose |cos| >= |sin| the ray walks the image rows; on row i the hat weight of
-// pixel j is 1 - |cos| * |j - x*(i)|, with x*(i) the column where t = b, so at
-// most three pixels per row are non-zero.  For |sin| > |cos| the same walk runs
-// over the rows of a transposed copy of the image, so warps always read
-// consecutive pixels.  x*(i) is anchored in float64 every 64 rows and followed
-// in float32 as a small fractional offset inside the block, which keeps the
-// weights within a few 1e-6 of their float64 values (the back-projector's own
-// accuracy), so the pair stays adjoint to float32 rounding.
+// and deterministic (no atomics).  For an angle whose |cos| >= |sin| a ray
+// walks the image rows; on row i the hat weight of pixel j is
+// 1 - |cos| * |j - x*(i)|, x*(i) being the column where t = b, so at most
+// three pixels per row are non-zero.  For |sin| > |cos| the same walk runs over
+// the rows of a transposed copy of the image.
+//
+// A CTA takes a group of 8 consecutive angles and 128 consecutive bins (1024
+// rays, 4 per thread).  A warp holds 16 consecutive bins of two neighbouring
+// angles, so the pixels its lanes read in one row span at most ~26 words of
+// shared memory (one wavefront per load).  The CTA walks its array in chunks
+// of 16 rows; for each chunk it stages the rectangle of pixels that its rays
+// can touch (for neighbouring angles their bands nearly coincide, so one
+// staged pixel serves about eight times more rays than a one-angle band
+// would).  The next chunk is loaded from L2 into registers (float4) while the
+// current one is walked, with one barrier per chunk.  If a group's band does
+// not fit the staging buffer (angles far apart) the CTA walks its angles one
+// at a time; the band width is convex in the row, so checking the first and
+// last chunks decides it.
+//
+// x*(b, r) = X0 + b dX - r rho is computed in 32.32 fixed point (int64), so the
+// staged bands, computed with the same integers, provably contain every tap
+// (with one column to spare on each side).  Inside a chunk each ray follows
+// x* - L0 (L0: the chunk's first staged column) in 9.23 fixed point (int32),
+// re-anchored exactly at every chunk, so a row costs one integer add and the
+// error stays below 1e-6 pixel; the fraction becomes a float by placing its
+// bits in a mantissa.  Pairs of rays share paired float32 (f32x2) arithmetic.
+// Rays that do not take part in a pass get zero weights and a fixed in-range
+// position, so the walk has no branches.  The weights
+// of the taps jc-1, jc, jc+1 (jc = round(x*), psi = x* - jc in [-1/2, 1/2)) are
+// sat(1 - a - a psi), 1 - a |psi|, sat(1 - a + a psi) with a = |cos| (or |sin|);
+// no fourth pixel can have a non-zero weight since a >= 1/sqrt(2).
+#include <climits>
 #include <cmath>
 
 #include "common.cuh"
@@ -20,8 +43,14 @@
 namespace pyhst {
 namespace {
 
-constexpr int kRayThreads = 128;
-constexpr int kAnchor = 64;   // rows per float64 anchor
+constexpr int kPThreads = 256;
+constexpr int kPG = 8;          // angles per group
+constexpr int kPB = 128;        // bins per CTA
+constexpr int kPR = 16;         // rows per staged chunk
+constexpr int kPW = 256;        // staged pixels per row (band capacity, multiple of 4)
+constexpr int kPRays = kPG / 2; // rays per thread
+constexpr int kPVec = kPR * kPW / 4 / kPThreads;   // float4 staged per thread per chunk (4)
+constexpr double kFix = 4294967296.0;   // 2^32
 
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int rows,
                                  int cols) {
@@ -39,69 +68,252 @@ __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict
     }
 }
 
-// One ray (angle a, bin b) per thread.
-__global__ void __launch_bounds__(kRayThreads)
-ray_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img,
-           const float *__restrict__ imgT, float *__restrict__ sino, int n_angles, int n_bins, int nx,
-           int ny, double cx, double cy, float scale) {
-    const int b = blockIdx.x * kRayThreads + threadIdx.x;
-    const int a = blockIdx.y;
-    const int slice = blockIdx.z;
-    if (b >= n_bins) return;
-    const AngleInfo e = tab[a];
-    float acc = 0.0f;
-    // Walk geometry: rows r of a row-major [R][C] array M; the column
-    // coefficient cc multiplies the column index, rr the row index.
-    const bool xmajor = fabs(e.c) >= fabs(e.s);
-    const float *M = xmajor ? img + (size_t)slice * nx * ny : imgT + (size_t)slice * nx * ny;
-    const int R = xmajor ? ny : nx, C = xmajor ? nx : ny;
-    const double cc = xmajor ? e.c : e.s, rr = xmajor ? e.s : e.c;
-    const double ccen = xmajor ? cx : cy, rcen = xmajor ? cy : cx;
-    if (isfinite(cc) && isfinite(rr) && isfinite(e.axis) && cc != 0.0) {
-        // x*(r) = ccen + (b - axis - (r - rcen) rr) / cc = X - r rho
-        const double inv = 1.0 / cc, rho = rr * inv;
-        const double X = ccen + ((double)b - e.axis + rcen * rr) * inv;
-        // rows where x* lies in [-2, C + 1]: the only rows with non-zero weights
-        int r_lo = 0, r_hi = R - 1;
-        if (rho != 0.0) {
-            double ra = (X + 2.0) / rho, rb = (X - (C + 1.0)) / rho;
-            double lo = fmin(ra, rb), hi = fmax(ra, rb);
-            lo = fmax(lo, 0.0);
-            hi = fmin(hi, (double)(R - 1));
-            r_lo = (lo > hi) ? 1 : (int)ceil(lo);
-            r_hi = (lo > hi) ? 0 : (int)floor(hi);
-        } else if (!(X >= -2.0 && X <= C + 1.0)) {
-            r_lo = 1; r_hi = 0;
-        }
-        const float rhof = (float)rho;
-        const float acf = (float)fabs(cc);
-        for (int r0 = r_lo; r0 <= r_hi; r0 += kAnchor) {
-            const double xs = X - (double)r0 * rho;
-            const double J0d = floor(xs);
-            const int J0 = (int)J0d;
-            const float phi0 = (float)(xs - J0d);
-            const int rend = min(r_hi, r0 + kAnchor - 1);
-            const float *row = M + (size_t)r0 * C;
-            for (int r = r0; r <= rend; ++r, row += C) {
-                const float xr = fmaf(-(float)(r - r0), rhof, phi0);   // x*(r) - J0
-                const float tm = add_rd(xr, kMagic);
-                const float fl = tm - kMagic;                          // floor(xr), exact
-                const float phi = xr - fl;                             // in [0, 1)
-                const int J = J0 + (int)(__float_as_uint(tm) - kMagicBits);
-                // at most three non-zero weights: J-1..J+1 when phi < 1/2, J..J+2 otherwise
-                const int sh = phi < 0.5f ? 0 : 1;
-                const int j0 = J - 1 + sh;
-                const float d0 = (float)(sh - 1) - phi;                // j0 - x*
+// One angle's walk over a row-major [R][C] array (image rows when |cos| >=
+// |sin|, transposed rows otherwise): x*(b, r) = X0 + b dX - r rho in 32.32.
+struct RayGeom {
+    long long X0, dX, rho;
+    float a;        // |cc|
+    int major;      // 0: image rows, 1: transposed rows, -1: no contribution
+};
+
+__device__ RayGeom ray_geom(const AngleInfo &e, double cx, double cy) {
+    RayGeom g;
+    g.major = -1;
+    g.X0 = g.dX = g.rho = 0;
+    g.a = 0.0f;
+    if (!(isfinite(e.c) && isfinite(e.s) && isfinite(e.axis))) return g;
+    const bool xm = fabs(e.c) >= fabs(e.s);
+    const double cc = xm ? e.c : e.s, rr = xm ? e.s : e.c;
+    const double ccen = xm ? cx : cy, rcen = xm ? cy : cx;
+    if (cc == 0.0) return g;
+    const double X0 = ccen + (rcen * rr - e.axis) / cc;
+    if (!(fabs(X0) < 1.0e9)) return g;          // rays that miss any image
+    g.X0 = llrint(X0 * kFix);
+    g.dX = llrint(kFix / cc);
+    g.rho = llrint(rr / cc * kFix);
+    g.a = (float)fabs(cc);
+    g.major = xm ? 0 : 1;
+    return g;
+}
+
+__device__ __forceinline__ int hi32(long long v) { return (int)(v >> 32); }
+
+// Band of a chunk: columns [L0, H] covering every tap of the rays of the
+// masked angles between rows r_first and r_last (warp 0; result in lane 0).
+__device__ __forceinline__ void chunk_band(const RayGeom *rg, int mask, int b0, int bhi, int r_first, int r_last,
+                                           int &L0, int &H) {
+    const int lane = threadIdx.x & 31;
+    int lo = INT_MAX, hi = INT_MIN;
+    if (lane < kPG && ((mask >> lane) & 1)) {
+        const RayGeom g = rg[lane];
+        const long long p = g.X0 + (long long)b0 * g.dX, q = g.X0 + (long long)bhi * g.dX;
+        const long long u = (long long)r_first * g.rho, v = (long long)r_last * g.rho;
+        const long long mn = min(min(p - u, q - u), min(p - v, q - v));
+        const long long mx = max(max(p - u, q - u), max(p - v, q - v));
+        lo = hi32(mn) - 2;
+        hi = hi32(mx) + 3;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    L0 = lo & ~3;   // float4-aligned start
+    H = hi;
+}
+
+struct WalkArgs {
+    const float *M;
+    int R, C;
+    int b0, bhi, b;
+    bool vec;       // float4 staging allowed (16-byte aligned rows)
+};
+
+// Walk all rows of one array for the rays of the masked angles.
+__device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 acc[2],
+                                          float (*strip)[kPR][kPW], int *L0_s, int *H_s) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int asub = lane >> 4;
+    const int n_chunks = (w.R + kPR - 1) / kPR;
+    long long X64[kPRays];          // x* + 1/2 at row 0, 32.32
+    float aa[kPRays], t1[kPRays], c1[kPRays];
+    bool act[kPRays];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int j = j0 + k;
-                    const float w = fmaxf(0.0f, fmaf(-acf, fabsf(d0 + (float)k), 1.0f));
-                    if ((unsigned)j < (unsigned)C) acc = fmaf(w, __ldg(row + j), acc);
+    for (int k = 0; k < kPRays; ++k) {
+        const RayGeom g = rg[asub + 2 * k];
+        act[k] = ((mask >> (asub + 2 * k)) & 1) && w.b <= w.bhi;
+        X64[k] = g.X0 + (long long)w.b * g.dX + (1LL << 31);
+        aa[k] = act[k] ? g.a : 0.0f;          // inactive: all three weights 0
+        t1[k] = act[k] ? 1.0f - g.a : -1.0f;
+        c1[k] = act[k] ? 1.0f : 0.0f;
+    }
+    float4 pre[kPVec];
+    auto load = [&](int c, int slot) {   // chunk c -> registers
+        const int r0 = c * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[slot];
+#pragma unroll
+        for (int v = 0; v < kPVec; ++v) {
+            const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
+            const int j = L0 + col;
+            float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (rr < nr) {
+                const float *row = w.M + (size_t)(r0 + rr) * w.C;
+                if (w.vec) {
+                    if (j >= 0 && j + 3 < w.C) val = __ldg(reinterpret_cast<const float4 *>(row + j));
+                } else {
+                    if ((unsigned)j < (unsigned)w.C) val.x = __ldg(row + j);
+                    if ((unsigned)(j + 1) < (unsigned)w.C) val.y = __ldg(row + j + 1);
+                    if ((unsigned)(j + 2) < (unsigned)w.C) val.z = __ldg(row + j + 2);
+                    if ((unsigned)(j + 3) < (unsigned)w.C) val.w = __ldg(row + j + 3);
                 }
             }
+            pre[v] = val;
+        }
+    };
+    auto commit = [&](int sbuf) {
+#pragma unroll
+        for (int v = 0; v < kPVec; ++v) {
+            const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
+            *reinterpret_cast<float4 *>(&strip[sbuf][rr][col]) = pre[v];
+        }
+    };
+    auto band = [&](int c, int slot) {
+        if (warp == 0) {
+            int L0, H;
+            const int r0 = c * kPR;
+            chunk_band(rg, mask, w.b0, w.bhi, r0, min(r0 + kPR, w.R) - 1, L0, H);
+            if (lane == 0) { L0_s[slot] = L0; H_s[slot] = H; }
+        }
+    };
+    // prologue
+    band(0, 0);
+    if (n_chunks > 1) band(1, 1);
+    __syncthreads();
+    load(0, 0);
+    commit(0);
+    __syncthreads();
+    const float2 m15 = make_float2(-1.5f, -1.5f);
+    for (int c = 0; c < n_chunks; ++c) {
+        const int cur = c & 1;
+        const bool more = c + 1 < n_chunks;
+        if (more) load(c + 1, (c + 1) % 3);
+        if (c + 2 < n_chunks) band(c + 2, (c + 2) % 3);
+        const int r0 = c * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[c % 3];
+        // chunk anchors: x* + 1/2 - L0 in 9.23 fixed point (0 < value < 2^31)
+        int x32[kPRays], r32[kPRays];
+#pragma unroll
+        for (int k = 0; k < kPRays; ++k) {
+            const long long rho = rg[asub + 2 * k].rho;
+            const long long rel = X64[k] - (long long)r0 * rho - ((long long)L0 << 32);
+            x32[k] = act[k] ? (int)(rel >> 9) : (3 << 23);
+            r32[k] = act[k] ? (int)((rho + 256) >> 9) : 0;
+        }
+        const float *S = &strip[cur][0][0];
+        for (int rr = 0; rr < nr; ++rr, S += kPW) {
+            float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
+#pragma unroll
+            for (int k = 0; k < kPRays; ++k) {
+                const float *q = S + (x32[k] >> 23) - 1;
+                v[k] = __int_as_float((x32[k] & 0x7FFFFF) | 0x3F800000);   // 1 + frac in [1, 2)
+                q0[k] = q[0];
+                q1[k] = q[1];
+                q2[k] = q[2];
+                x32[k] -= r32[k];
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int k = 2 * p;
+                const float2 ps = add2(make_float2(v[k], v[k + 1]), m15);       // psi in [-1/2, 1/2)
+                const float2 ap = mul2(make_float2(aa[k], aa[k + 1]), ps);
+                const float2 wl = make_float2(__saturatef(t1[k] - ap.x), __saturatef(t1[k + 1] - ap.y));
+                const float2 wc = make_float2(fmaf(-aa[k], fabsf(ps.x), c1[k]), fmaf(-aa[k + 1], fabsf(ps.y), c1[k + 1]));
+                const float2 wr = make_float2(__saturatef(t1[k] + ap.x), __saturatef(t1[k + 1] + ap.y));
+                acc[p] = fma2(wl, make_float2(q0[k], q0[k + 1]), acc[p]);
+                acc[p] = fma2(wc, make_float2(q1[k], q1[k + 1]), acc[p]);
+                acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
+            }
+        }
+        if (more) commit(cur ^ 1);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kPThreads, 3)
+proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
+            float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
+            float scale) {
+    __shared__ __align__(16) float strip[2][kPR][kPW];
+    __shared__ RayGeom rg[kPG];
+    __shared__ int L0_s[3], H_s[3];
+    __shared__ int phase_mask[2], fits_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g0 = blockIdx.y * kPG;
+    const int b0 = blockIdx.x * kPB;
+    const int slice = blockIdx.z;
+    const int b = b0 + 16 * warp + (lane & 15);
+    const int asub = lane >> 4;
+    const int bhi = min(b0 + kPB, n_bins) - 1;
+    const size_t img_off = (size_t)slice * nx * ny;
+
+    if (tid < kPG) {
+        RayGeom g;
+        g.major = -1; g.X0 = g.dX = g.rho = 0; g.a = 0.0f;
+        if (g0 + tid < n_angles) g = ray_geom(tab[g0 + tid], cx, cy);
+        rg[tid] = g;
+    }
+    if (tid < 2) phase_mask[tid] = 0;
+    __syncthreads();
+    if (tid < kPG && rg[tid].major >= 0) atomicOr(&phase_mask[rg[tid].major], 1 << tid);
+    __syncthreads();
+
+    float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};   // rays (0,1), (2,3)
+
+    for (int major = 0; major < 2; ++major) {
+        const int mask_all = phase_mask[major];
+        if (!mask_all) continue;
+        WalkArgs w;
+        w.M = (major == 0 ? img : imgT) + img_off;
+        w.R = major == 0 ? ny : nx;
+        w.C = major == 0 ? nx : ny;
+        w.b0 = b0; w.bhi = bhi; w.b = b;
+        w.vec = (w.C % 4 == 0) && ((reinterpret_cast<uintptr_t>(w.M) & 15) == 0);
+        // Largest subset of consecutive angles (8, 4, 2, 1) whose bands fit:
+        // the band of rows [r, r + 15] has a width convex in r, every chunk
+        // lies within the range of the first and last 16-row windows, and the
+        // float4 alignment of a chunk's start adds at most 3 columns.  A
+        // single angle always fits (127 sqrt 2 + 16 + 8 < 256).
+        if (warp == 0) {
+            int gs = kPG;
+            const int last0 = max(0, w.R - kPR);
+            for (; gs > 1; gs >>= 1) {
+                bool ok = true;
+                for (int s0 = 0; s0 < kPG; s0 += gs) {
+                    const int m = mask_all & (((1 << gs) - 1) << s0);
+                    if (!m) continue;
+                    int L0a, Ha, L0b, Hb;
+                    chunk_band(rg, m, b0, bhi, 0, min(kPR, w.R) - 1, L0a, Ha);
+                    chunk_band(rg, m, b0, bhi, last0, w.R - 1, L0b, Hb);
+                    ok = ok && (Ha - L0a + 4 <= kPW) && (Hb - L0b + 4 <= kPW);
+                }
+                if (ok) break;
+            }
+            if (lane == 0) fits_s = gs;
+        }
+        __syncthreads();
+        const int gs = fits_s;
+        for (int s0 = 0; s0 < kPG; s0 += gs) {
+            const int m = mask_all & (((1 << gs) - 1) << s0);
+            if (m) walk_pass(w, rg, m, acc, strip, L0_s, H_s);
+        }
+        __syncthreads();
+    }
+    if (b <= bhi) {
+        const float r[kPRays] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y};
+#pragma unroll
+        for (int k = 0; k < kPRays; ++k) {
+            const int a = g0 + asub + 2 * k;
+            if (a < n_angles) sino[((size_t)slice * n_angles + a) * n_bins + b] = scale * r[k];
         }
     }
-    sino[((size_t)slice * n_angles + a) * n_bins + b] = scale * acc;
 }
 
 }  // namespace
@@ -117,10 +329,10 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     transpose_kernel<<<tg, tb, 0, st>>>(img, xt, g->ny, g->nx);
     int rc = cuda_status("transpose kernel");
     if (rc) return rc;
-    dim3 grid((g->n_bins + kRayThreads - 1) / kRayThreads, g->n_angles, g->n_slices);
+    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG, g->n_slices);
     ProfScope prof(kProfProject, st);
-    ray_kernel<<<grid, kRayThreads, 0, st>>>(tab, img, xt, sino, g->n_angles, g->n_bins, g->nx, g->ny,
-                                             g->cx, g->cy, scale);
+    proj_kernel<<<grid, kPThreads, 0, st>>>(tab, img, xt, sino, g->n_angles, g->n_bins, g->nx, g->ny, g->cx,
+                                            g->cy, scale);
     return cuda_status("projection kernel");
 }
 
