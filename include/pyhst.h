@@ -230,6 +230,30 @@ int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, floa
 int pyhst_profile_enable(int on);
 int pyhst_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
+/* One slice of a mixed-size batch: its own geometry (n_slices is ignored),
+ * sinogram [n_angles][n_bins], iterate x [ny][nx] (in: start if warm_start,
+ * out: result) and energy [n_iter] float64 (DEVICE, or NULL). */
+typedef struct {
+    pyhst_geometry geom;
+    const float *sino;
+    float *x;
+    double *energy;
+} pyhst_tv_item;
+
+/* pyhst_tv_solve for many slices of different sizes and angle sets at once
+ * (same options for all): every stage of an iteration is one launch over the
+ * whole batch, and the n_iter iterations are captured in one CUDA graph on
+ * `stream` (when `stream` is not already capturing and is not the legacy
+ * NULL stream, where the launches are issued directly).  The step size is
+ * estimated once per distinct geometry (same angle and axis pointers, sizes,
+ * centre and pixel size).  items is a HOST array of n_items entries whose
+ * pointers are device memory; lipschitz_out: DEVICE float64 [n_items] or
+ * NULL.  The call copies small tables from host memory into the workspace
+ * (pyhst_tv_batch_workspace_size) before launching. */
+size_t pyhst_tv_batch_workspace_size(const pyhst_tv_item *items, int32_t n_items, const pyhst_tv_opts *opts);
+int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items, const pyhst_tv_opts *opts,
+                         double *lipschitz_out, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *pyhst_last_error(void);
 

@@ -26,7 +26,7 @@ from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SIN
 
 __all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_filter", "pyhst_fbp_host",
            "pyhst_profile_enable", "pyhst_profile_read", "pyhst_fbp_static", "pyhst_backproject", "pyhst_project",
-           "pyhst_tv_solve", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
+           "pyhst_tv_solve", "pyhst_tv_solve_batch", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
            "pyhst_version", "library_path"]
 
 
@@ -352,6 +352,34 @@ def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0
     _check(L.lib.pyhst_tv_prox(_ptr(z3), nx, ny, ns, float(lam), int(n_inner), float(tau), _ptr(out), _ptr(ws),
                                ws.numel(), _stream()))
     return out
+
+
+def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace=None):
+    """Eq. 3 for a mixed batch: ``slices`` is a list of (Geometry, sino
+    [n_angles, n_bins], x or None).  Returns (list of x, list of energy
+    [n_iter] float64 or None, lipschitz [n] float64)."""
+    items = (L.pyhst_tv_item * len(slices))()
+    xs, es = [], []
+    dev = None
+    for k, (geom, sino, x) in enumerate(slices):
+        sino = _cuda(sino, "sino", (torch.float32,))
+        if tuple(sino.shape[-2:]) != (geom.n_angles, geom.n_bins):
+            raise ValueError(f"slice {k}: sinogram shape does not match its geometry")
+        dev = sino.device
+        if x is None:
+            x = torch.zeros((geom.ny, geom.nx), dtype=torch.float32, device=dev)
+        _cuda(x, "x", (torch.float32,))
+        e = torch.empty((opts.n_iter,), dtype=torch.float64, device=dev) if energy else None
+        items[k] = L.pyhst_tv_item(geom.c(1), sino.data_ptr(), x.data_ptr(), e.data_ptr() if e is not None else None)
+        xs.append(x)
+        es.append(e)
+    o = opts.c()
+    lip = torch.empty((len(slices),), dtype=torch.float64, device=dev)
+    need = L.lib.pyhst_tv_batch_workspace_size(items, len(slices), ctypes.byref(o))
+    ws = _workspace(need, dev, workspace)
+    _check(L.lib.pyhst_tv_solve_batch(items, len(slices), ctypes.byref(o), _ptr(lip), _ptr(ws), ws.numel(),
+                                      _stream()))
+    return xs, es, lip
 
 
 def fbp_weight(n_angles: int, pixel_size: float) -> float:

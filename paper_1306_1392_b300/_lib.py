@@ -38,6 +38,10 @@ class pyhst_tv_opts(ctypes.Structure):
                 ("n_power_iter", c_int32)]
 
 
+class pyhst_tv_item(ctypes.Structure):
+    _fields_ = [("geom", pyhst_geometry), ("sino", c_void_p), ("x", c_void_p), ("energy", c_void_p)]
+
+
 # (name, restype, argtypes) of every exported entry point
 SIGNATURES = [
     ("pyhst_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32]),
@@ -65,6 +69,10 @@ SIGNATURES = [
                                 c_void_p, c_size_t, c_void_p]),
     ("pyhst_profile_enable", c_int32, [c_int32]),
     ("pyhst_profile_read", c_int32, [ctypes.c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
+    ("pyhst_tv_batch_workspace_size", c_size_t, [ctypes.POINTER(pyhst_tv_item), c_int32,
+                                                 ctypes.POINTER(pyhst_tv_opts)]),
+    ("pyhst_tv_solve_batch", c_int32, [ctypes.POINTER(pyhst_tv_item), c_int32, ctypes.POINTER(pyhst_tv_opts),
+                                       c_void_p, c_void_p, c_size_t, c_void_p]),
     ("pyhst_last_error", ctypes.c_char_p, []),
     ("pyhst_version", ctypes.c_char_p, []),
 ]

@@ -68,20 +68,15 @@ __device__ __forceinline__ StageInfo stage_info(const AngleInfo *tab, int a, int
     return si;
 }
 
+// One CTA: the 64 x 64 tile at (X0, Y0) of one slice.  A (and B in residual
+// mode) are that slice's rows, out its image.
 template <bool kResidual>
-__global__ void __launch_bounds__(kThreads, 3)
-bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
-          const float *__restrict__ srcB, float *__restrict__ img, int n_angles, int n_bins,
-          int nx, int ny, double cx, double cy, float weight, int tiles_x) {
+__device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const float *__restrict__ A,
+                                        const float *__restrict__ B, float *__restrict__ out, int n_angles,
+                                        int n_bins, int nx, int ny, double cx, double cy, float weight,
+                                        int X0, int Y0) {
     __shared__ __align__(16) float2 win[2][kNA * kW];
     __shared__ StageInfo info[3][kNA];
-
-    const int slice = blockIdx.y;
-    const int X0 = (blockIdx.x % tiles_x) * kTX;
-    const int Y0 = (blockIdx.x / tiles_x) * kTY;
-    const size_t sino_off = (size_t)slice * n_angles * n_bins;
-    const float *A = srcA + sino_off;
-    const float *B = kResidual ? srcB + sino_off : nullptr;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int px = (warp & 1) * 32 + (lane & 7);   // first pixel of this thread in the tile
@@ -167,7 +162,6 @@ bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
         __syncthreads();
     }
 
-    float *out = img + (size_t)slice * nx * ny;
 #pragma unroll
     for (int ry = 0; ry < kRY; ++ry)
 #pragma unroll
@@ -181,7 +175,46 @@ bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
         }
 }
 
+template <bool kResidual>
+__global__ void __launch_bounds__(kThreads, 3)
+bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
+          const float *__restrict__ srcB, float *__restrict__ img, int n_angles, int n_bins,
+          int nx, int ny, double cx, double cy, float weight, int tiles_x) {
+    const int slice = blockIdx.y;
+    const size_t sino_off = (size_t)slice * n_angles * n_bins;
+    bp_tile<kResidual>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + (size_t)slice * nx * ny,
+                       n_angles, n_bins, nx, ny, cx, cy, weight, (blockIdx.x % tiles_x) * kTX,
+                       (blockIdx.x / tiles_x) * kTY);
+}
+
+// Mixed batch: CTA k reconstructs tile (items[k].y, items[k].z) of slice items[k].x.
+template <bool kResidual>
+__global__ void __launch_bounds__(kThreads, 3)
+bp_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items, float weight_scale) {
+    const int4 it = items[blockIdx.x];
+    const BatchSlice s = slices[it.x];
+    bp_tile<kResidual>(s.tab, s.bp_a, s.bp_b, s.bp_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
+                       weight_scale * s.pixel_size, it.y * kTX, it.z * kTY);
+}
+
 }  // namespace
+
+int bp_tiles(int nx, int ny, int *tx, int *ty) {
+    *tx = (nx + kTX - 1) / kTX;
+    *ty = (ny + kTY - 1) / kTY;
+    return *tx * *ty;
+}
+
+int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
+                             cudaStream_t st) {
+    if (n_items <= 0) return PYHST_OK;
+    ProfScope prof(kProfBackproject, st);
+    if (residual)
+        bp_batch_kernel<true><<<n_items, kThreads, 0, st>>>(slices, items, 1.0f);
+    else
+        bp_batch_kernel<false><<<n_items, kThreads, 0, st>>>(slices, items, 1.0f);
+    return cuda_status("batched back-projection kernel");
+}
 
 int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img,
                        float weight, cudaStream_t st) {

@@ -65,6 +65,28 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
                    float scale, float *xt, cudaStream_t st);
 size_t project_scratch_bytes(const pyhst_geometry *g);
 
+// ----------------------------------------------------------------- mixed batches
+// Per-slice descriptor of a mixed-size batch (device memory).  The
+// back-projector reads bp_a (- bp_b) into bp_out with weight pixel_size; the
+// projector reads proj_in (and proj_inT, its transpose) into proj_out scaled
+// by pixel_size.  The solver fills the remaining fields.
+struct BatchSlice {
+    const AngleInfo *tab;
+    int n_angles, n_bins, nx, ny;
+    double cx, cy;
+    float pixel_size;
+    const float *bp_a, *bp_b;
+    float *bp_out;
+    const float *proj_in;
+    float *proj_inT, *proj_out;
+};
+int bp_tiles(int nx, int ny, int *tx, int *ty);
+int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
+                             cudaStream_t st);
+int proj_blocks(int n_angles, int n_bins, int *nb, int *na);
+int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
+                         const int4 *tr_items, int n_tr_items, cudaStream_t st);
+
 // ----------------------------------------------------------------- profiling
 // Opt-in per-launch timing (pyhst_profile_enable): events recorded on the
 // launch stream around each kernel of a kind; off by default.

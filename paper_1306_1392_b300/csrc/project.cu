@@ -236,23 +236,21 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     }
 }
 
-__global__ void __launch_bounds__(kPThreads, 3)
-proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
-            float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
-            float scale) {
+// One CTA: angles [g0, g0 + 8) x bins [b0, b0 + 128) of one slice; img/imgT
+// are that slice's image and its transpose, sino its sinogram.
+__device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, const float *__restrict__ img,
+                                         const float *__restrict__ imgT, float *__restrict__ sino, int n_angles,
+                                         int n_bins, int nx, int ny, double cx, double cy, float scale, int g0,
+                                         int b0) {
     __shared__ __align__(16) float strip[2][kPR][kPW];
     __shared__ RayGeom rg[kPG];
     __shared__ int L0_s[3], H_s[3];
     __shared__ int phase_mask[2], fits_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g0 = blockIdx.y * kPG;
-    const int b0 = blockIdx.x * kPB;
-    const int slice = blockIdx.z;
     const int b = b0 + 16 * warp + (lane & 15);
     const int asub = lane >> 4;
     const int bhi = min(b0 + kPB, n_bins) - 1;
-    const size_t img_off = (size_t)slice * nx * ny;
 
     if (tid < kPG) {
         RayGeom g;
@@ -271,7 +269,7 @@ proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, co
         const int mask_all = phase_mask[major];
         if (!mask_all) continue;
         WalkArgs w;
-        w.M = (major == 0 ? img : imgT) + img_off;
+        w.M = major == 0 ? img : imgT;
         w.R = major == 0 ? ny : nx;
         w.C = major == 0 ? nx : ny;
         w.b0 = b0; w.bhi = bhi; w.b = b;
@@ -311,12 +309,67 @@ proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, co
 #pragma unroll
         for (int k = 0; k < kPRays; ++k) {
             const int a = g0 + asub + 2 * k;
-            if (a < n_angles) sino[((size_t)slice * n_angles + a) * n_bins + b] = scale * r[k];
+            if (a < n_angles) sino[(size_t)a * n_bins + b] = scale * r[k];
         }
     }
 }
 
+__global__ void __launch_bounds__(kPThreads, 3)
+proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
+            float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
+            float scale) {
+    const size_t img_off = (size_t)blockIdx.z * nx * ny;
+    proj_cta(tab, img + img_off, imgT + img_off, sino + (size_t)blockIdx.z * n_angles * n_bins, n_angles, n_bins,
+             nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB);
+}
+
+// Mixed batch: CTA k projects angle group items[k].z, bin block items[k].y of slice items[k].x.
+__global__ void __launch_bounds__(kPThreads, 3)
+proj_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    const BatchSlice s = slices[it.x];
+    proj_cta(s.tab, s.proj_in, s.proj_inT, s.proj_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy, s.pixel_size,
+             it.z * kPG, it.y * kPB);
+}
+
+// Mixed batch transpose: CTA k moves 32 x 32 tile (items[k].y, items[k].z) of slice items[k].x.
+__global__ void transpose_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items) {
+    __shared__ float tile[32][33];
+    const int4 it = items[blockIdx.x];
+    const BatchSlice s = slices[it.x];
+    const int rows = s.ny, cols = s.nx;
+    const int c0 = it.y * 32, r0 = it.z * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = s.proj_in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) s.proj_inT[(size_t)c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
 }  // namespace
+
+int proj_blocks(int n_angles, int n_bins, int *nb, int *na) {
+    *nb = (n_bins + kPB - 1) / kPB;
+    *na = (n_angles + kPG - 1) / kPG;
+    return *nb * *na;
+}
+
+int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
+                         const int4 *tr_items, int n_tr_items, cudaStream_t st) {
+    if (n_tr_items > 0) {
+        transpose_batch_kernel<<<n_tr_items, dim3(32, 8), 0, st>>>(slices, tr_items);
+        int rc = cuda_status("batched transpose kernel");
+        if (rc) return rc;
+    }
+    if (n_proj_items <= 0) return PYHST_OK;
+    ProfScope prof(kProfProject, st);
+    proj_batch_kernel<<<n_proj_items, kPThreads, 0, st>>>(slices, proj_items);
+    return cuda_status("batched projection kernel");
+}
 
 size_t project_scratch_bytes(const pyhst_geometry *g) {
     return align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices);

@@ -1,0 +1,609 @@
+// Mixed-size batch of TV-penalised solves (Eq. 3 by ISTA/FISTA, Sec. 3.1).
+//
+// Slices of different sizes and angle sets run together: every stage of an
+// outer iteration (gradient back-projection, gradient step, each Chambolle
+// step, prox end, projection, momentum and energy) is ONE launch over the
+// whole batch, each CTA taking a (slice, tile) work item from a list built on
+// the host, with per-slice descriptors in device memory.  The n_iter
+// iterations are captured in one CUDA graph and launched once (unless the
+// caller's stream is already being captured, in which case the launches join
+// the caller's capture).  The arithmetic is that of pyhst_tv_solve: one
+// projection and one back-projection per iteration (P y carried by linearity),
+// float64 energies from block partials summed in a fixed order.  The step
+// size is estimated once per distinct geometry (same angle/axis arrays, sizes,
+// centre and pixel size) by power iteration on one representative slice.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pyhst {
+namespace {
+
+constexpr int kBT = 256;            // threads of the element-wise kernels
+constexpr int kSinoBlock = 1024;    // sinogram elements per work item (4 per thread)
+
+struct TvSlice {
+    float *y, *xa, *xb, *z, *g, *p1a, *p2a, *p1b, *p2b;
+    float *Axa, *Axb, *Ay;
+    const float *sino;
+    float *x_user;
+    double *energy;
+    int nx, ny, M;        // image size, sinogram elements
+    int px_first, sn_first;
+    int rep;              // representative slice of the geometry group (power iteration)
+};
+
+struct Scal {
+    double *L;            // [n]
+    double *ray;          // [n] ||P v||^2 of representatives
+    float *invL, *lam, *invn;
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[kBT / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = (l < kBT / 32) ? red[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+// Partial-sum slots: a slice's pixel items (32 x 8) and sinogram items are
+// numbered from its px_first / sn_first in the order the host lists them, so
+// that work lists over any subset of slices write the same slots.
+__device__ __forceinline__ int px_slot(const int4 it, const TvSlice &s) {
+    return s.px_first + it.z * ((s.nx + 31) / 32) + it.y;
+}
+__device__ __forceinline__ int sn_slot(const int4 it, const TvSlice &s) { return s.sn_first + it.y; }
+
+// pixel (i, j) of a 32 x 8 work item; false if outside the slice
+__device__ __forceinline__ bool px_of(const int4 it, const TvSlice &s, int &i, int &j) {
+    j = it.y * 32 + (threadIdx.x & 31);
+    i = it.z * 8 + (threadIdx.x >> 5);
+    return i < s.ny && j < s.nx;
+}
+
+__global__ void b_grad_step(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    if (!px_of(it, s, i, j)) return;
+    const size_t k = (size_t)i * s.nx + j;
+    s.z[k] = fmaf(-s.g[k], sc.invL[it.x], s.y[k]);
+}
+
+template <bool kFirst>
+__global__ void b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau,
+                            int parity) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    if (!px_of(it, s, i, j)) return;
+    const int nx = s.nx, ny = s.ny;
+    const float *P1 = parity ? s.p1b : s.p1a, *P2 = parity ? s.p2b : s.p2a;
+    float *Q1 = parity ? s.p1a : s.p1b, *Q2 = parity ? s.p2a : s.p2b;
+    if (kFirst) {   // the first step writes the "a" buffers from a zero field
+        Q1 = s.p1a;
+        Q2 = s.p2a;
+    }
+    const float l = sc.lam[it.x];
+    auto G = [&](int r, int c) -> float {
+        float dv = 0.0f;
+        if (!kFirst) {
+            const size_t k = (size_t)r * nx + c;
+            if (r + 1 < ny) dv += P1[k];
+            if (r > 0) dv -= P1[k - nx];
+            if (c + 1 < nx) dv += P2[k];
+            if (c > 0) dv -= P2[k - 1];
+        }
+        return dv - s.z[(size_t)r * nx + c] / l;
+    };
+    const float g0 = G(i, j);
+    const float g1 = (i + 1 < ny) ? G(i + 1, j) - g0 : 0.0f;
+    const float g2 = (j + 1 < nx) ? G(i, j + 1) - g0 : 0.0f;
+    const float den = 1.0f + tau * sqrtf(g1 * g1 + g2 * g2);
+    const size_t k = (size_t)i * nx + j;
+    const float a = kFirst ? 0.0f : P1[k], b = kFirst ? 0.0f : P2[k];
+    Q1[k] = (a + tau * g1) / den;
+    Q2[k] = (b + tau * g2) / den;
+}
+
+// x_new = z - lam div p (p in the buffers of `parity`); with lam = 0, x_new = z
+__global__ void b_prox_final(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, int parity,
+                             int it_parity, int identity) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    if (!px_of(it, s, i, j)) return;
+    const size_t k = (size_t)i * s.nx + j;
+    float *xn = it_parity ? s.xa : s.xb;
+    if (identity) {
+        xn[k] = s.z[k];
+        return;
+    }
+    const float *P1 = parity ? s.p1b : s.p1a, *P2 = parity ? s.p2b : s.p2a;
+    float dv = 0.0f;
+    if (i + 1 < s.ny) dv += P1[k];
+    if (i > 0) dv -= P1[k - s.nx];
+    if (j + 1 < s.nx) dv += P2[k];
+    if (j > 0) dv -= P2[k - 1];
+    xn[k] = fmaf(-sc.lam[it.x], dv, s.z[k]);
+}
+
+// data partial ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
+__global__ void b_sino_update(const TvSlice *__restrict__ d, const int4 *__restrict__ items, float w, int it_parity,
+                              double *__restrict__ part) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    const float *axn = it_parity ? s.Axa : s.Axb, *axo = it_parity ? s.Axb : s.Axa;
+    double acc = 0.0;
+    const int base = it.y * kSinoBlock;
+    for (int e = base + threadIdx.x; e < min(base + kSinoBlock, s.M); e += kBT) {
+        const float v = axn[e];
+        const float r = v - s.sino[e];
+        acc += (double)r * (double)r;
+        s.Ay[e] = fmaf(w, v - axo[e], v);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[sn_slot(it, s)] = acc;
+}
+
+// TV(xn) partial (Eq. 2) and y = xn + w (xn - xo)
+__global__ void b_image_update(const TvSlice *__restrict__ d, const int4 *__restrict__ items, float w, int it_parity,
+                               double *__restrict__ part) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    const float *xn = it_parity ? s.xa : s.xb, *xo = it_parity ? s.xb : s.xa;
+    int i, j;
+    double acc = 0.0;
+    if (px_of(it, s, i, j)) {
+        const size_t k = (size_t)i * s.nx + j;
+        const float v = xn[k];
+        const float d1 = (i + 1 < s.ny) ? xn[k + s.nx] - v : 0.0f;
+        const float d2 = (j + 1 < s.nx) ? xn[k + 1] - v : 0.0f;
+        acc = (double)sqrtf(d1 * d1 + d2 * d2);
+        s.y[k] = fmaf(w, v - xo[k], v);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[px_slot(it, s)] = acc;
+}
+
+// energy[k] of slice blockIdx.x from its partials, in a fixed order
+__global__ void b_finalize_energy(const TvSlice *__restrict__ d, const double *__restrict__ part_sn,
+                                  const double *__restrict__ part_px, float beta, int n_iter, int k, int n) {
+    const TvSlice s = d[blockIdx.x];
+    (void)n;
+    double a = 0.0, t = 0.0;
+    for (int e = s.sn_first + threadIdx.x; e < s.sn_first + (s.M + kSinoBlock - 1) / kSinoBlock; e += kBT)
+        a += part_sn[e];
+    const int n_px = ((s.nx + 31) / 32) * ((s.ny + 7) / 8);
+    for (int e = s.px_first + threadIdx.x; e < s.px_first + n_px; e += kBT) t += part_px[e];
+    a = block_sum(a);
+    t = block_sum(t);
+    if (threadIdx.x == 0 && s.energy) s.energy[(size_t)k] = 0.5 * a + (double)beta * t;
+}
+
+// ||g||^2 partial of a slice's pixels (power iteration)
+__global__ void b_sqnorm_g(const TvSlice *__restrict__ d, const int4 *__restrict__ items, double *__restrict__ part) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    double acc = 0.0;
+    if (px_of(it, s, i, j)) {
+        const float v = s.g[(size_t)i * s.nx + j];
+        acc = (double)v * (double)v;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[px_slot(it, s)] = acc;
+}
+
+// ||P v||^2 partial of a slice's sinogram (power iteration end)
+__global__ void b_sqnorm_axa(const TvSlice *__restrict__ d, const int4 *__restrict__ items, double *__restrict__ part) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    double acc = 0.0;
+    const int base = it.y * kSinoBlock;
+    for (int e = base + threadIdx.x; e < min(base + kSinoBlock, s.M); e += kBT) {
+        const float v = s.Axa[e];
+        acc += (double)v * (double)v;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[sn_slot(it, s)] = acc;
+}
+
+// per representative: invn = 1/sqrt(sum) (mode 0) or ray = sum (mode 1)
+__global__ void b_finalize_norm(const TvSlice *__restrict__ d, const int *__restrict__ reps, const double *__restrict__ part,
+                                Scal sc, int mode) {
+    const int r = reps[blockIdx.x];
+    const TvSlice s = d[r];
+    double a = 0.0;
+    if (mode == 0) {
+        const int n_px = ((s.nx + 31) / 32) * ((s.ny + 7) / 8);
+        for (int e = s.px_first + threadIdx.x; e < s.px_first + n_px; e += kBT) a += part[e];
+    } else {
+        for (int e = s.sn_first + threadIdx.x; e < s.sn_first + (s.M + kSinoBlock - 1) / kSinoBlock; e += kBT)
+            a += part[e];
+    }
+    a = block_sum(a);
+    if (threadIdx.x == 0) {
+        if (mode == 0) sc.invn[r] = (float)(1.0 / sqrt(a));
+        else sc.ray[r] = a;
+    }
+}
+
+__global__ void b_scale_v(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    if (!px_of(it, s, i, j)) return;
+    const size_t k = (size_t)i * s.nx + j;
+    s.z[k] = s.g[k] * sc.invn[it.x];
+}
+
+__global__ void b_fill_v(const TvSlice *__restrict__ d, const int4 *__restrict__ items) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    if (!px_of(it, s, i, j)) return;
+    s.z[(size_t)i * s.nx + j] = 1.0f;
+}
+
+__global__ void b_set_step(const TvSlice *__restrict__ d, Scal sc, double L_fixed, float beta, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double L = L_fixed > 0.0 ? L_fixed : 1.01 * sc.ray[d[k].rep];
+    sc.L[k] = L;
+    sc.invL[k] = (float)(1.0 / L);
+    sc.lam[k] = (float)((double)beta / L);
+}
+
+// start: xa = x_user (warm) or 0, y = xa; result: x_user = x of the last iteration
+__global__ void b_copy_x(const TvSlice *__restrict__ d, const int4 *__restrict__ items, int mode, int it_parity) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    int i, j;
+    if (!px_of(it, s, i, j)) return;
+    const size_t k = (size_t)i * s.nx + j;
+    if (mode == 0) {           // cold start
+        s.xa[k] = 0.0f;
+        s.y[k] = 0.0f;
+    } else if (mode == 1) {    // warm start
+        const float v = s.x_user[k];
+        s.xa[k] = v;
+        s.y[k] = v;
+    } else {                   // result
+        s.x_user[k] = it_parity ? s.xa[k] : s.xb[k];
+    }
+}
+
+__global__ void b_copy_sino_start(const TvSlice *__restrict__ d, const int4 *__restrict__ items, int warm) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    const int base = it.y * kSinoBlock;
+    for (int e = base + threadIdx.x; e < min(base + kSinoBlock, s.M); e += kBT) {
+        const float v = warm ? s.Axa[e] : 0.0f;
+        s.Axa[e] = v;
+        s.Ay[e] = v;
+    }
+}
+
+// ------------------------------------------------------------------ host plan
+struct Plan {
+    int n = 0;
+    std::vector<int> rep;                       // representative of each slice
+    std::vector<int> reps;                      // distinct representatives
+    std::vector<int4> bp, proj, tr, px, sn;     // all slices
+    std::vector<int4> bp_r, proj_r, tr_r, px_r, sn_r;   // representatives only
+    std::vector<size_t> img_off, sino_off;      // per slice, in floats
+    size_t img_total = 0, sino_total = 0;
+    std::vector<int> px_first, sn_first;
+};
+
+size_t up4(size_t v) { return (v + 63) / 64 * 64; }   // 256-byte multiples of floats
+
+void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
+    int tx, ty;
+    bp_tiles(g.nx, g.ny, &tx, &ty);
+    auto &bp = rep_only ? P.bp_r : P.bp;
+    for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) bp.push_back(make_int4(s, x, y, 0));
+    int nb, na;
+    proj_blocks(g.n_angles, g.n_bins, &nb, &na);
+    auto &pr = rep_only ? P.proj_r : P.proj;
+    for (int a = 0; a < na; ++a)
+        for (int b = 0; b < nb; ++b) pr.push_back(make_int4(s, b, a, 0));
+    auto &tr = rep_only ? P.tr_r : P.tr;
+    for (int y = 0; y < (g.ny + 31) / 32; ++y)
+        for (int x = 0; x < (g.nx + 31) / 32; ++x) tr.push_back(make_int4(s, x, y, 0));
+    auto &px = rep_only ? P.px_r : P.px;
+    for (int y = 0; y < (g.ny + 7) / 8; ++y)
+        for (int x = 0; x < (g.nx + 31) / 32; ++x) px.push_back(make_int4(s, x, y, 0));
+    auto &sn = rep_only ? P.sn_r : P.sn;
+    const int M = g.n_angles * g.n_bins;
+    for (int e = 0; e < (M + kSinoBlock - 1) / kSinoBlock; ++e) sn.push_back(make_int4(s, e, 0, 0));
+}
+
+Plan make_plan(const pyhst_tv_item *items, int n) {
+    Plan P;
+    P.n = n;
+    P.rep.resize(n);
+    std::map<std::tuple<const void *, const void *, int, int, int, int, float, float, float>, int> groups;
+    for (int s = 0; s < n; ++s) {
+        const pyhst_geometry &g = items[s].geom;
+        auto key = std::make_tuple((const void *)g.angles, (const void *)g.axis, g.n_angles, g.n_bins, g.nx, g.ny,
+                                   g.cx, g.cy, g.pixel_size);
+        auto f = groups.find(key);
+        if (f == groups.end()) {
+            groups[key] = s;
+            P.rep[s] = s;
+            P.reps.push_back(s);
+        } else {
+            P.rep[s] = f->second;
+        }
+        P.img_off.push_back(P.img_total);
+        P.img_total += up4((size_t)g.nx * g.ny);
+        P.sino_off.push_back(P.sino_total);
+        P.sino_total += up4((size_t)g.n_angles * g.n_bins);
+        P.px_first.push_back((int)P.px.size());
+        P.sn_first.push_back((int)P.sn.size());
+        add_items(P, s, g, false);
+    }
+    for (int r : P.reps) add_items(P, r, items[r].geom, true);
+    return P;
+}
+
+struct Layout {
+    size_t desc_even, desc_odd, desc_init, desc_pow, tvs, reps, items, tabs, imgs, sinos, scal, part_px, part_sn, bytes;
+    size_t n_items_total;
+    std::vector<size_t> tab_off;
+};
+
+Layout make_layout(const Plan &P, const pyhst_tv_item *items) {
+    Layout l{};
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
+    l.desc_even = take(sizeof(BatchSlice) * P.n);
+    l.desc_odd = take(sizeof(BatchSlice) * P.n);
+    l.desc_init = take(sizeof(BatchSlice) * P.n);
+    l.desc_pow = take(sizeof(BatchSlice) * P.n);
+    l.tvs = take(sizeof(TvSlice) * P.n);
+    l.reps = take(sizeof(int) * P.reps.size());
+    l.n_items_total = P.bp.size() + P.proj.size() + P.tr.size() + P.px.size() + P.sn.size() + P.bp_r.size() +
+                      P.proj_r.size() + P.tr_r.size() + P.px_r.size() + P.sn_r.size();
+    l.items = take(sizeof(int4) * l.n_items_total);
+    for (int s = 0; s < P.n; ++s) l.tab_off.push_back(take(sizeof(AngleInfo) * items[s].geom.n_angles));
+    l.imgs = take(sizeof(float) * P.img_total * 10);
+    l.sinos = take(sizeof(float) * P.sino_total * 3);
+    l.scal = take(sizeof(double) * P.n * 2 + sizeof(float) * P.n * 3);
+    l.part_px = take(sizeof(double) * P.px.size());
+    l.part_sn = take(sizeof(double) * P.sn.size());
+    l.bytes = off;
+    return l;
+}
+
+int check_items(const pyhst_tv_item *items, int n) {
+    if (!items || n < 1) return fail(PYHST_ERR_INVALID_ARG, "need at least one batch item");
+    for (int s = 0; s < n; ++s) {
+        pyhst_geometry g = items[s].geom;
+        g.n_slices = 1;
+        int rc = check_geometry(&g);
+        if (rc) return fail(rc, "item %d: %s", s, pyhst_last_error());
+        if (!items[s].sino || !items[s].x) return fail(PYHST_ERR_INVALID_ARG, "item %d: sino/x pointer is NULL", s);
+    }
+    return PYHST_OK;
+}
+
+int check_tv_opts_b(const pyhst_tv_opts *o) {
+    if (!o) return fail(PYHST_ERR_INVALID_ARG, "options are NULL");
+    if (!(o->beta >= 0.0f) || !std::isfinite(o->beta)) return fail(PYHST_ERR_INVALID_ARG, "beta must be >= 0");
+    if (o->n_iter < 1) return fail(PYHST_ERR_INVALID_ARG, "n_iter must be >= 1");
+    if (o->n_inner < 1) return fail(PYHST_ERR_INVALID_ARG, "n_inner must be >= 1");
+    if (!(o->tau > 0.0f && o->tau <= 0.25f)) return fail(PYHST_ERR_INVALID_ARG, "tau must be in (0, 1/4]");
+    if (!(o->lipschitz >= 0.0) || !std::isfinite(o->lipschitz))
+        return fail(PYHST_ERR_INVALID_ARG, "lipschitz must be >= 0 (0: estimate)");
+    if (o->lipschitz == 0.0 && o->n_power_iter < 1)
+        return fail(PYHST_ERR_INVALID_ARG, "n_power_iter must be >= 1 when lipschitz is estimated");
+    return PYHST_OK;
+}
+
+}  // namespace
+}  // namespace pyhst
+
+using namespace pyhst;
+
+extern "C" size_t pyhst_tv_batch_workspace_size(const pyhst_tv_item *items, int32_t n_items,
+                                                const pyhst_tv_opts *opts) {
+    (void)opts;
+    if (!items || n_items < 1) return 0;
+    for (int s = 0; s < n_items; ++s) {
+        const pyhst_geometry &g = items[s].geom;
+        if (g.n_angles < 1 || g.n_bins < 1 || g.nx < 1 || g.ny < 1) return 0;
+    }
+    Plan P = make_plan(items, n_items);
+    return make_layout(P, items).bytes;
+}
+
+extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items, const pyhst_tv_opts *opts,
+                                    double *lipschitz_out, void *workspace, size_t ws_bytes, pyhst_stream_t stream) {
+    int rc = check_items(items, n_items);
+    if (rc) return rc;
+    if ((rc = check_tv_opts_b(opts))) return rc;
+    const Plan P = make_plan(items, n_items);
+    const Layout L = make_layout(P, items);
+    if (!workspace || ws_bytes < L.bytes || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", L.bytes);
+    if (P.px.size() > 0x7fffffff || P.bp.size() > 0x7fffffff)
+        return fail(PYHST_ERR_INVALID_ARG, "batch too large");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    const int n = n_items;
+
+    // ---- host tables
+    float *imgs = reinterpret_cast<float *>(ws + L.imgs);
+    float *sinos = reinterpret_cast<float *>(ws + L.sinos);
+    const size_t IT = P.img_total, ST = P.sino_total;
+    auto img = [&](int t, int s) { return imgs + (size_t)t * IT + P.img_off[s]; };
+    auto sin = [&](int t, int s) { return sinos + (size_t)t * ST + P.sino_off[s]; };
+    std::vector<TvSlice> tv(n);
+    std::vector<BatchSlice> ev(n), od(n), in(n), pw(n);
+    for (int s = 0; s < n; ++s) {
+        const pyhst_geometry &g = items[s].geom;
+        TvSlice &t = tv[s];
+        t.y = img(0, s); t.xa = img(1, s); t.xb = img(2, s); t.z = img(3, s); t.g = img(4, s);
+        t.p1a = img(5, s); t.p2a = img(6, s); t.p1b = img(7, s); t.p2b = img(8, s);
+        t.Axa = sin(0, s); t.Axb = sin(1, s); t.Ay = sin(2, s);
+        t.sino = items[s].sino;
+        t.x_user = items[s].x;
+        t.energy = items[s].energy;
+        t.nx = g.nx; t.ny = g.ny; t.M = g.n_angles * g.n_bins;
+        t.px_first = P.px_first[s];
+        t.sn_first = P.sn_first[s];
+        t.rep = P.rep[s];
+        BatchSlice b{};
+        b.tab = reinterpret_cast<const AngleInfo *>(ws + L.tab_off[s]);
+        b.n_angles = g.n_angles; b.n_bins = g.n_bins; b.nx = g.nx; b.ny = g.ny;
+        b.cx = g.cx; b.cy = g.cy; b.pixel_size = g.pixel_size;
+        b.proj_inT = img(9, s);
+        // gradient back-projection of the residual P y - sino
+        b.bp_a = t.Ay; b.bp_b = items[s].sino; b.bp_out = t.g;
+        ev[s] = b; ev[s].proj_in = t.xb; ev[s].proj_out = t.Axb;   // even iterations write xb, Axb
+        od[s] = b; od[s].proj_in = t.xa; od[s].proj_out = t.Axa;   // odd iterations write xa, Axa
+        in[s] = b; in[s].proj_in = t.xa; in[s].proj_out = t.Axa;   // warm start
+        pw[s] = b; pw[s].proj_in = t.z; pw[s].proj_out = t.Axa;    // power iteration
+        pw[s].bp_a = t.Axa; pw[s].bp_b = nullptr;
+    }
+    std::vector<int4> all;
+    auto append = [&](const std::vector<int4> &v) { size_t o = all.size(); all.insert(all.end(), v.begin(), v.end()); return o; };
+    const size_t o_bp = append(P.bp), o_proj = append(P.proj), o_tr = append(P.tr), o_px = append(P.px),
+                 o_sn = append(P.sn), o_bpr = append(P.bp_r), o_projr = append(P.proj_r), o_trr = append(P.tr_r),
+                 o_pxr = append(P.px_r), o_snr = append(P.sn_r);
+    // pageable host memory: each copy returns once its data are staged
+    cudaMemcpyAsync(ws + L.desc_even, ev.data(), sizeof(BatchSlice) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws + L.desc_odd, od.data(), sizeof(BatchSlice) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws + L.desc_init, in.data(), sizeof(BatchSlice) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws + L.desc_pow, pw.data(), sizeof(BatchSlice) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws + L.tvs, tv.data(), sizeof(TvSlice) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws + L.reps, P.reps.data(), sizeof(int) * P.reps.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws + L.items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice, st);
+    if ((rc = cuda_status("batch table upload"))) return rc;
+    for (int s = 0; s < n; ++s)
+        if ((rc = launch_angle_table(items[s].geom.angles, items[s].geom.axis, items[s].geom.n_angles,
+                                     reinterpret_cast<AngleInfo *>(ws + L.tab_off[s]), st)))
+            return rc;
+
+    const BatchSlice *D_even = reinterpret_cast<const BatchSlice *>(ws + L.desc_even);
+    const BatchSlice *D_odd = reinterpret_cast<const BatchSlice *>(ws + L.desc_odd);
+    const BatchSlice *D_init = reinterpret_cast<const BatchSlice *>(ws + L.desc_init);
+    const BatchSlice *D_pow = reinterpret_cast<const BatchSlice *>(ws + L.desc_pow);
+    const TvSlice *T = reinterpret_cast<const TvSlice *>(ws + L.tvs);
+    const int *R = reinterpret_cast<const int *>(ws + L.reps);
+    const int4 *I = reinterpret_cast<const int4 *>(ws + L.items);
+    double *sc_base = reinterpret_cast<double *>(ws + L.scal);
+    Scal sc;
+    sc.L = sc_base;
+    sc.ray = sc_base + n;
+    sc.invL = reinterpret_cast<float *>(sc_base + 2 * n);
+    sc.lam = sc.invL + n;
+    sc.invn = sc.lam + n;
+    double *part_px = reinterpret_cast<double *>(ws + L.part_px);
+    double *part_sn = reinterpret_cast<double *>(ws + L.part_sn);
+    const int npx = (int)P.px.size(), nsn = (int)P.sn.size(), nbp = (int)P.bp.size(), npr = (int)P.proj.size(),
+              ntr = (int)P.tr.size();
+    const dim3 tb(kBT);
+
+    // ---- step size: power iteration on the representatives, or the caller's L
+    if (opts->lipschitz == 0.0) {
+        const int npxr = (int)P.px_r.size(), nsnr = (int)P.sn_r.size();
+        b_fill_v<<<npxr, tb, 0, st>>>(T, I + o_pxr);
+        for (int it = 0; it < opts->n_power_iter; ++it) {
+            if ((rc = launch_project_batch(D_pow, I + o_projr, (int)P.proj_r.size(), I + o_trr, (int)P.tr_r.size(), st)))
+                return rc;
+            if ((rc = launch_backproject_batch(D_pow, I + o_bpr, (int)P.bp_r.size(), false, st))) return rc;
+            b_sqnorm_g<<<npxr, tb, 0, st>>>(T, I + o_pxr, part_px);
+            b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_px, sc, 0);
+            b_scale_v<<<npxr, tb, 0, st>>>(T, I + o_pxr, sc);
+        }
+        if ((rc = launch_project_batch(D_pow, I + o_projr, (int)P.proj_r.size(), I + o_trr, (int)P.tr_r.size(), st)))
+            return rc;
+        b_sqnorm_axa<<<nsnr, tb, 0, st>>>(T, I + o_snr, part_sn);
+        b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_sn, sc, 1);
+    }
+    b_set_step<<<(n + 127) / 128, 128, 0, st>>>(T, sc, opts->lipschitz, opts->beta, n);
+    if ((rc = cuda_status("step-size kernels"))) return rc;
+    if (lipschitz_out) cudaMemcpyAsync(lipschitz_out, sc.L, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+
+    // ---- start
+    b_copy_x<<<npx, tb, 0, st>>>(T, I + o_px, opts->warm_start ? 1 : 0, 0);
+    if (opts->warm_start)
+        if ((rc = launch_project_batch(D_init, I + o_proj, npr, I + o_tr, ntr, st))) return rc;
+    b_copy_sino_start<<<nsn, tb, 0, st>>>(T, I + o_sn, opts->warm_start ? 1 : 0);
+    if ((rc = cuda_status("batch start"))) return rc;
+
+    // ---- the iterations, captured in one graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    // the legacy default stream cannot be captured: launch directly there
+    const bool own_graph = cap == cudaStreamCaptureStatusNone && st != nullptr;
+    if (own_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cuda_status("graph capture begin");
+    double t = 1.0;
+    const bool identity = opts->beta == 0.0f;
+    for (int k = 0; k < opts->n_iter && !rc; ++k) {
+        const int par = k & 1;   // 0: x_new -> xb, 1: x_new -> xa
+        rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st);
+        if (rc) break;
+        b_grad_step<<<npx, tb, 0, st>>>(T, I + o_px, sc);
+        int pp = 0;
+        if (!identity) {
+            b_chambolle<true><<<npx, tb, 0, st>>>(T, I + o_px, sc, opts->tau, 0);
+            for (int m = 1; m < opts->n_inner; ++m) {
+                b_chambolle<false><<<npx, tb, 0, st>>>(T, I + o_px, sc, opts->tau, pp);
+                pp ^= 1;
+            }
+        }
+        b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, pp, par, identity);
+        rc = launch_project_batch(par ? D_odd : D_even, I + o_proj, npr, I + o_tr, ntr, st);
+        if (rc) break;
+        double w = 0.0;
+        if (opts->use_fista) {
+            const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+            w = (t - 1.0) / tn;
+            t = tn;
+        }
+        b_sino_update<<<nsn, tb, 0, st>>>(T, I + o_sn, (float)w, par, part_sn);
+        b_image_update<<<npx, tb, 0, st>>>(T, I + o_px, (float)w, par, part_px);
+        b_finalize_energy<<<n, tb, 0, st>>>(T, part_sn, part_px, opts->beta, opts->n_iter, k, n);
+        rc = cuda_status("batch iteration kernels");
+    }
+    if (own_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(PYHST_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(PYHST_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        e = cudaGraphLaunch(exec, st);
+        cudaGraphExecDestroy(exec);   // released once the launched graph completes
+        if (e != cudaSuccess) return fail(PYHST_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    } else if (rc) {
+        return rc;
+    }
+    // ---- result: the last iterate
+    b_copy_x<<<npx, tb, 0, st>>>(T, I + o_px, 2, (opts->n_iter - 1) & 1);
+    return cuda_status("batch result copy");
+}

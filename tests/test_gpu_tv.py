@@ -115,3 +115,75 @@ def test_tv_solve_energy_decreases_and_beats_fbp(P, cuda_device):
     err_tv = np.linalg.norm(x[0].cpu().numpy() - truth)
     err_fbp = np.linalg.norm(fbp[0].cpu().numpy() - truth)
     assert err_tv < 0.8 * err_fbp
+
+
+# ------------------------------------------------------------------ mixed batch
+def _mixed(P, dev):
+    """Five slices of three geometries: 48^2/40 angles, 64^2/24 angles and a
+    non-square 40 x 32 grid with 30 angles and an off-centre axis."""
+    out = []
+    specs = [(48, 48, 40, 0.0, 1), (64, 64, 24, 0.0, 2), (48, 48, 40, 0.0, 3), (40, 32, 30, 2.5, 4),
+             (64, 64, 24, 0.0, 5)]
+    geos = {}
+    for nx, ny, na, off, seed in specs:
+        key = (nx, ny, na, off)
+        if key not in geos:
+            ang = acq.uniform_angles(na)
+            nb = max(nx, ny) + 6
+            axis = torch.full((na,), (nb - 1) / 2.0 + off)
+            geos[key] = (P.Geometry(ang.to(dev), axis.to(dev), nb, nx, ny, 2.0 / max(nx, ny)), ang, axis, nb)
+        geo, ang, axis, nb = geos[key]
+        g = np.random.default_rng(seed)
+        img = np.zeros((ny, nx))
+        img[ny // 4: 3 * ny // 4, nx // 3: 2 * nx // 3] = 1.0
+        sino = P.pyhst_project(geo, torch.from_numpy(img.astype(np.float32)).to(dev))[0]
+        sino = (sino + 0.01 * torch.from_numpy(g.standard_normal(sino.shape).astype(np.float32)).to(dev)).contiguous()
+        out.append((geo, sino, ang, axis, nb))
+    return out
+
+
+def test_batch_matches_single_slice_solves(P, orc, cuda_device):
+    """With the same step size, every slice of a mixed batch equals its
+    single-slice solve bit for bit (same kernels), its energies agree to
+    1e-9, and it matches the FP64 oracle like the single-slice solver."""
+    items = _mixed(P, cuda_device)
+    L = 1.01 * max(orc.power_iteration(orc.Geometry(a.double().numpy(), ax.double().numpy(), nb, g.nx, g.ny,
+                                                    g.pixel_size), np.ones((g.ny, g.nx)), 40)[0]
+                   for g, _, a, ax, nb in items)
+    opts = P.TvOptions(beta=3e-3, n_iter=12, n_inner=8, lipschitz=L)
+    xs, es, lip = P.pyhst_tv_solve_batch([(g, s, None) for g, s, *_ in items], opts)
+    torch.cuda.synchronize()
+    for k, (g, s, a, ax, nb) in enumerate(items):
+        x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), opts)
+        assert torch.equal(xs[k], x1[0]), k
+        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
+        og = orc.Geometry(a.double().numpy(), ax.double().numpy(), nb, g.nx, g.ny, g.pixel_size)
+        xr, er = orc.fista(og, s.double().cpu().numpy(), 3e-3, L, 12, n_inner=8)
+        assert rel(xs[k].cpu().numpy(), xr) <= 1e-4
+        np.testing.assert_allclose(es[k].cpu().numpy(), er, rtol=1e-5)
+    assert torch.all(lip == L)
+
+
+def test_batch_step_size_per_geometry(P, cuda_device):
+    """Estimated L: one power iteration per distinct geometry, equal (to
+    float64 summation order) to the single-slice estimate."""
+    items = _mixed(P, cuda_device)
+    opts = P.TvOptions(beta=2e-3, n_iter=3, n_inner=5, n_power_iter=25)
+    _, _, lip = P.pyhst_tv_solve_batch([(g, s, None) for g, s, *_ in items], opts)
+    for k, (g, s, *_r) in enumerate(items):
+        _, _, l1 = P.pyhst_tv_solve(g, s[None].contiguous(), opts)
+        assert abs(lip[k].item() - l1.item()) <= 1e-6 * l1.item()
+    assert lip[0].item() == lip[2].item() and lip[1].item() == lip[4].item()
+
+
+@pytest.mark.parametrize("fista,beta,warm", [(False, 2e-3, False), (True, 0.0, False), (True, 4e-3, True)])
+def test_batch_variants(P, cuda_device, fista, beta, warm):
+    items = _mixed(P, cuda_device)
+    L = 5.0
+    opts = P.TvOptions(beta=beta, n_iter=9, n_inner=6, lipschitz=L, use_fista=fista, warm_start=warm)
+    x0s = [torch.rand((g.ny, g.nx), device=cuda_device) for g, *_ in items]
+    xs, es, _ = P.pyhst_tv_solve_batch([(g, s, x0.clone()) for (g, s, *_), x0 in zip(items, x0s)], opts)
+    for k, (g, s, *_r) in enumerate(items):
+        x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), opts, x=x0s[k][None].clone())
+        assert torch.equal(xs[k], x1[0]), k
+        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
