@@ -232,12 +232,14 @@ int pyhst_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
 /* One slice of a mixed-size batch: its own geometry (n_slices is ignored),
  * sinogram [n_angles][n_bins], iterate x [ny][nx] (in: start if warm_start,
- * out: result) and energy [n_iter] float64 (DEVICE, or NULL). */
+ * out: result), energy [n_iter] float64 (DEVICE, or NULL) and its own beta
+ * (>= 0; a negative value takes the options' beta). */
 typedef struct {
     pyhst_geometry geom;
     const float *sino;
     float *x;
     double *energy;
+    float beta;
 } pyhst_tv_item;
 
 /* pyhst_tv_solve for many slices of different sizes and angle sets at once

@@ -356,12 +356,15 @@ def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0
 
 def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace=None):
     """Eq. 3 for a mixed batch: ``slices`` is a list of (Geometry, sino
-    [n_angles, n_bins], x or None).  Returns (list of x, list of energy
-    [n_iter] float64 or None, lipschitz [n] float64)."""
+    [n_angles, n_bins], x or None[, beta]) (beta defaults to opts.beta).
+    Returns (list of x, list of energy [n_iter] float64 or None,
+    lipschitz [n] float64)."""
     items = (L.pyhst_tv_item * len(slices))()
     xs, es = [], []
     dev = None
-    for k, (geom, sino, x) in enumerate(slices):
+    for k, entry in enumerate(slices):
+        geom, sino, x = entry[:3]
+        beta = float(entry[3]) if len(entry) > 3 and entry[3] is not None else -1.0
         sino = _cuda(sino, "sino", (torch.float32,))
         if tuple(sino.shape[-2:]) != (geom.n_angles, geom.n_bins):
             raise ValueError(f"slice {k}: sinogram shape does not match its geometry")
@@ -370,7 +373,8 @@ def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace
             x = torch.zeros((geom.ny, geom.nx), dtype=torch.float32, device=dev)
         _cuda(x, "x", (torch.float32,))
         e = torch.empty((opts.n_iter,), dtype=torch.float64, device=dev) if energy else None
-        items[k] = L.pyhst_tv_item(geom.c(1), sino.data_ptr(), x.data_ptr(), e.data_ptr() if e is not None else None)
+        items[k] = L.pyhst_tv_item(geom.c(1), sino.data_ptr(), x.data_ptr(), e.data_ptr() if e is not None else None,
+                                   beta)
         xs.append(x)
         es.append(e)
     o = opts.c()

@@ -39,7 +39,8 @@ class pyhst_tv_opts(ctypes.Structure):
 
 
 class pyhst_tv_item(ctypes.Structure):
-    _fields_ = [("geom", pyhst_geometry), ("sino", c_void_p), ("x", c_void_p), ("energy", c_void_p)]
+    _fields_ = [("geom", pyhst_geometry), ("sino", c_void_p), ("x", c_void_p), ("energy", c_void_p),
+                ("beta", c_float)]
 
 
 # (name, restype, argtypes) of every exported entry point

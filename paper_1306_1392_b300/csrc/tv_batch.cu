@@ -35,6 +35,7 @@ struct TvSlice {
     int nx, ny, M;        // image size, sinogram elements
     int px_first, sn_first;
     int rep;              // representative slice of the geometry group (power iteration)
+    float beta;           // weight of TV in this slice's Eq. 3
 };
 
 struct Scal {
@@ -88,7 +89,7 @@ __global__ void b_chambolle(const TvSlice *__restrict__ d, const int4 *__restric
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
     int i, j;
-    if (!px_of(it, s, i, j)) return;
+    if (!px_of(it, s, i, j) || s.beta == 0.0f) return;   // beta = 0: the prox is the identity
     const int nx = s.nx, ny = s.ny;
     const float *P1 = parity ? s.p1b : s.p1a, *P2 = parity ? s.p2b : s.p2a;
     float *Q1 = parity ? s.p1a : s.p1b, *Q2 = parity ? s.p2a : s.p2b;
@@ -127,7 +128,7 @@ __global__ void b_prox_final(const TvSlice *__restrict__ d, const int4 *__restri
     if (!px_of(it, s, i, j)) return;
     const size_t k = (size_t)i * s.nx + j;
     float *xn = it_parity ? s.xa : s.xb;
-    if (identity) {
+    if (identity || s.beta == 0.0f) {
         xn[k] = s.z[k];
         return;
     }
@@ -180,7 +181,7 @@ __global__ void b_image_update(const TvSlice *__restrict__ d, const int4 *__rest
 
 // energy[k] of slice blockIdx.x from its partials, in a fixed order
 __global__ void b_finalize_energy(const TvSlice *__restrict__ d, const double *__restrict__ part_sn,
-                                  const double *__restrict__ part_px, float beta, int n_iter, int k, int n) {
+                                  const double *__restrict__ part_px, int n_iter, int k, int n) {
     const TvSlice s = d[blockIdx.x];
     (void)n;
     double a = 0.0, t = 0.0;
@@ -190,7 +191,7 @@ __global__ void b_finalize_energy(const TvSlice *__restrict__ d, const double *_
     for (int e = s.px_first + threadIdx.x; e < s.px_first + n_px; e += kBT) t += part_px[e];
     a = block_sum(a);
     t = block_sum(t);
-    if (threadIdx.x == 0 && s.energy) s.energy[(size_t)k] = 0.5 * a + (double)beta * t;
+    if (threadIdx.x == 0 && s.energy) s.energy[(size_t)k] = 0.5 * a + (double)s.beta * t;
 }
 
 // ||g||^2 partial of a slice's pixels (power iteration)
@@ -258,13 +259,13 @@ __global__ void b_fill_v(const TvSlice *__restrict__ d, const int4 *__restrict__
     s.z[(size_t)i * s.nx + j] = 1.0f;
 }
 
-__global__ void b_set_step(const TvSlice *__restrict__ d, Scal sc, double L_fixed, float beta, int n) {
+__global__ void b_set_step(const TvSlice *__restrict__ d, Scal sc, double L_fixed, int n) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const double L = L_fixed > 0.0 ? L_fixed : 1.01 * sc.ray[d[k].rep];
     sc.L[k] = L;
     sc.invL[k] = (float)(1.0 / L);
-    sc.lam[k] = (float)((double)beta / L);
+    sc.lam[k] = (float)((double)d[k].beta / L);
 }
 
 // start: xa = x_user (warm) or 0, y = xa; result: x_user = x of the last iteration
@@ -399,6 +400,7 @@ int check_items(const pyhst_tv_item *items, int n) {
         int rc = check_geometry(&g);
         if (rc) return fail(rc, "item %d: %s", s, pyhst_last_error());
         if (!items[s].sino || !items[s].x) return fail(PYHST_ERR_INVALID_ARG, "item %d: sino/x pointer is NULL", s);
+        if (!std::isfinite(items[s].beta)) return fail(PYHST_ERR_INVALID_ARG, "item %d: beta is not finite", s);
     }
     return PYHST_OK;
 }
@@ -469,6 +471,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         t.px_first = P.px_first[s];
         t.sn_first = P.sn_first[s];
         t.rep = P.rep[s];
+        t.beta = (items[s].beta >= 0.0f) ? items[s].beta : opts->beta;
         BatchSlice b{};
         b.tab = reinterpret_cast<const AngleInfo *>(ws + L.tab_off[s]);
         b.n_angles = g.n_angles; b.n_bins = g.n_bins; b.nx = g.nx; b.ny = g.ny;
@@ -538,7 +541,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         b_sqnorm_axa<<<nsnr, tb, 0, st>>>(T, I + o_snr, part_sn);
         b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_sn, sc, 1);
     }
-    b_set_step<<<(n + 127) / 128, 128, 0, st>>>(T, sc, opts->lipschitz, opts->beta, n);
+    b_set_step<<<(n + 127) / 128, 128, 0, st>>>(T, sc, opts->lipschitz, n);
     if ((rc = cuda_status("step-size kernels"))) return rc;
     if (lipschitz_out) cudaMemcpyAsync(lipschitz_out, sc.L, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
 
@@ -557,7 +560,8 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     if (own_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return cuda_status("graph capture begin");
     double t = 1.0;
-    const bool identity = opts->beta == 0.0f;
+    bool identity = true;   // no slice has a TV term: skip the Chambolle steps
+    for (int q = 0; q < n; ++q) identity = identity && tv[q].beta == 0.0f;
     for (int k = 0; k < opts->n_iter && !rc; ++k) {
         const int par = k & 1;   // 0: x_new -> xb, 1: x_new -> xa
         rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st);
@@ -582,7 +586,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         }
         b_sino_update<<<nsn, tb, 0, st>>>(T, I + o_sn, (float)w, par, part_sn);
         b_image_update<<<npx, tb, 0, st>>>(T, I + o_px, (float)w, par, part_px);
-        b_finalize_energy<<<n, tb, 0, st>>>(T, part_sn, part_px, opts->beta, opts->n_iter, k, n);
+        b_finalize_energy<<<n, tb, 0, st>>>(T, part_sn, part_px, opts->n_iter, k, n);
         rc = cuda_status("batch iteration kernels");
     }
     if (own_graph) {

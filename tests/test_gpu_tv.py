@@ -187,3 +187,17 @@ def test_batch_variants(P, cuda_device, fista, beta, warm):
         x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), opts, x=x0s[k][None].clone())
         assert torch.equal(xs[k], x1[0]), k
         np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
+
+
+def test_batch_per_item_beta(P, cuda_device):
+    """Each batch item may carry its own beta (0 included): every slice
+    equals its single-slice solve with that beta, bit for bit."""
+    items = _mixed(P, cuda_device)
+    betas = [1e-3, 0.0, 5e-3, 2e-3, None]
+    opts = P.TvOptions(beta=3e-3, n_iter=7, n_inner=6, lipschitz=6.0)
+    xs, es, _ = P.pyhst_tv_solve_batch([(g, s, None, b) for (g, s, *_), b in zip(items, betas)], opts)
+    for k, ((g, s, *_r), b) in enumerate(zip(items, betas)):
+        o1 = P.TvOptions(beta=3e-3 if b is None else b, n_iter=7, n_inner=6, lipschitz=6.0)
+        x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), o1)
+        assert torch.equal(xs[k], x1[0]), k
+        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
