@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the baseline sample")
     ap.add_argument("--no-tv", action="store_true", help="skip the reduced-dose TV measurement")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="mixed-precision FBP study (4096^2, 4000 angles; f32/f16/bf16 storage vs the FP64 oracle)")
+    ap.add_argument("--precision-slices", type=int, default=2, help="slices checked against the oracle")
     ap.add_argument("--kernel-case", choices=["backproject", "project", "filter"],
                     help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
     return ap.parse_args()
@@ -260,6 +263,61 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
             "learned_prox": "not built (the plain TV solve is the reported arm)"}
 
 
+# ------------------------------------------------------------------ precision study
+def run_precision_study(args):
+    """256 slices x 4096^2, 4000 angles, 4096 bins: FBP throughput with the
+    sinogram stored as float32 / float16 / bfloat16 (float32 arithmetic), and
+    the error of each against the FP64 oracle run on the exact float64 line
+    integrals, at sampled pixels of a few seeded slices."""
+    import numpy as np
+    import torch
+    import oracle as orc
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    orc.build()
+    dev = torch.device("cuda", 0)
+    n, na, ns = 4096, 4000, 256
+    ang = acq.uniform_angles(na)
+    geo = P.Geometry(ang.to(dev), torch.full((na,), (n - 1) / 2.0, device=dev), n, n, n, 2.0 / n)
+    p = torch.empty((ns, na, n), dtype=torch.float32, device=dev)
+    for z0 in range(0, ns, 16):
+        p[z0:z0 + 16] = acq.ellipsoid_sinograms(ns, n, na, seed=4000, device=dev, slices=range(z0, min(ns, z0 + 16)))
+    out = torch.empty((ns, n, n), dtype=torch.float32, device=dev)
+    check = [int(z) for z in np.linspace(ns // 5, 4 * ns // 5, args.precision_slices).round()]
+    rng = np.random.default_rng(7)
+    ii = rng.integers(0, n, 2000)
+    jj = rng.integers(0, n, 2000)
+    refs = {}
+    for z in check:
+        q = orc.ramlak_filter(acq.ellipsoid_sinograms(ns, n, na, seed=4000, slices=[z])[0].numpy())
+        refs[z] = orc.backproject_at(q, ang.double().numpy(), (n - 1) / 2.0, n, n, ii, jj, orc.fbp_weight(na, 2.0 / n))
+    res = {}
+    for kind, dt in (("f32_sino", torch.float32), ("f16_sino", torch.float16), ("bf16_sino", torch.bfloat16)):
+        stored = p.to(dt)
+        ws = torch.empty(P.pyhst_fbp_workspace_size(geo, ns, 0, 4), dtype=torch.uint8, device=dev)
+        P.pyhst_fbp(geo, stored, kind, out=out[:4], workspace=ws, slices=(0, 4))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.pyhst_fbp(geo, stored, kind, out=out, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        errs = []
+        for z in check:
+            g = out[z].cpu().numpy()[ii, jj].astype(np.float64)
+            r = refs[z]
+            errs.append((np.linalg.norm(g - r) / np.linalg.norm(r), np.abs(g - r).max() / np.abs(r).max()))
+        res[kind[:-5]] = {"rel_l2": max(e[0] for e in errs), "max_abs_over_max": max(e[1] for e in errs),
+                          "fbp_slices_per_s": ns / (ms * 1e-3), "gupd_per_s": ns * n * n * na / (ms * 1e-3) / 1e9,
+                          "input_bytes_per_slice": na * n * stored.element_size()}
+        del stored
+    print(json.dumps({"precision_study": res, "workload": "256 slices x 4096^2, 4000 angles over 180 deg, 4096 bins; "
+                      "exact line integrals of 200 random ellipsoids stored as f32/f16/bf16; float32 arithmetic",
+                      "reference": f"FP64 oracle on the exact float64 line integrals, {len(ii)} sampled pixels of "
+                                   f"slices {check}, worst slice reported"}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -459,6 +517,9 @@ def main():
     args = parse()
     if args.kernel_case:
         run_kernel_case(args)
+        return
+    if args.precision_study:
+        run_precision_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -270,3 +270,23 @@ def test_fbp_slice_range_in_place(P, cuda_device):
     part = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk, slices=(3, 8))
     torch.cuda.synchronize()
     assert torch.equal(full[3:8], part)
+
+
+@pytest.mark.parametrize("kind,dt", [("f32_sino", torch.float32), ("f16_sino", torch.float16)])
+def test_fbp_4096_geometry_sampled(P, orc, cuda_device, kind, dt):
+    """The mixed-precision workload's slice geometry (4096^2 grid, 4000
+    angles, 4096 bins, FFT length 8192): stored f32 / f16 sinogram, sampled
+    pixels against the oracle evaluated on the same stored values."""
+    n, na = 4096, 4000
+    p = acq.ellipsoid_sinograms(256, n, na, seed=4000, device=cuda_device, slices=[100])
+    stored = p.to(dt).contiguous()
+    ang = acq.uniform_angles(na)
+    geo = geometry(P, ang.numpy(), (n - 1) / 2.0, n, n, n, 2.0 / n, cuda_device)
+    got = P.pyhst_fbp(geo, stored, kind)
+    torch.cuda.synchronize()
+    q = orc.ramlak_filter(stored[0].double().cpu().numpy())
+    rng = np.random.default_rng(1)
+    ii = np.concatenate([rng.integers(0, n, 1200), [0, n - 1, n // 2]])
+    jj = np.concatenate([rng.integers(0, n, 1200), [n - 1, 0, n // 2]])
+    ref = orc.backproject_at(q, ang.double().numpy(), (n - 1) / 2.0, n, n, ii, jj, orc.fbp_weight(na, 2.0 / n))
+    close(got[0].cpu().numpy()[ii, jj], ref)
