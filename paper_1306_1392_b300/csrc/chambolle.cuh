@@ -1,0 +1,119 @@
+// Fused Chambolle steps for the TV prox (Eq. 2; Chambolle's dual fixed point):
+//   G = div p - z / lam,   p <- (p + tau grad G) / (1 + tau |grad G|)
+// with forward differences and Neumann boundary (grad is zero across the last
+// row/column, div = -grad^T).
+//
+// K steps on one 32 x 32 tile run in shared memory: the tile is loaded with a
+// halo of K pixels (a step reads its neighbours at distance one), every step
+// is computed over the whole loaded region, and after K steps the central
+// tile, whose dependence cone stayed inside the region, is written out.  The
+// loaded region is 64 wide (output 54 + halo 5 each side) so that warps of 32
+// columns fill it.  z/lam is formed once per launch; |grad G| and the
+// reciprocal of 1 + tau |grad G| use the hardware approximations (within two
+// ulp), and the rounding of every operation is spelled out (fmaf, __fmul_rn,
+// ...) so that all kernels built on this function give bit-identical results.
+#pragma once
+
+#include "common.cuh"
+
+namespace pyhst {
+
+constexpr int kChT = 54;                    // output tile
+constexpr int kChK = 5;                     // steps fused per launch
+constexpr int kChR = kChT + 2 * kChK;       // loaded region (64: two full warp rows)
+constexpr int kChW = kChR + 2;              // region + zero guard ring
+constexpr int kChThreads = 256;
+constexpr size_t kChSmem = sizeof(float) * 4 * kChW * kChW;   // dynamic shared memory per CTA
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
+                                               const float *__restrict__ p2, float *__restrict__ q1,
+                                               float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
+                                               int j0, int steps, bool first) {
+    // sz holds z / lam; threads as 32 columns x 8 rows
+    extern __shared__ __align__(16) float ch_smem[];
+    float(*sz)[kChW] = reinterpret_cast<float(*)[kChW]>(ch_smem);
+    float(*s1)[kChW] = sz + kChW;
+    float(*s2)[kChW] = s1 + kChW;
+    float(*sg)[kChW] = s2 + kChW;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int ri0 = i0 - kChK - 1, rj0 = j0 - kChK - 1;   // global coordinates of array cell (0, 0)
+    for (int r = ty; r < kChW; r += 8)
+        for (int c = tx; c < kChW; c += 32) {
+            const int gi = ri0 + r, gj = rj0 + c;
+            float vz = 0.0f, v1 = 0.0f, v2 = 0.0f;
+            if (r >= 1 && r <= kChR && c >= 1 && c <= kChR && gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
+                const size_t k = (size_t)gi * nx + gj;
+                vz = __fdiv_rn(z[k], lam);
+                if (!first) {
+                    v1 = p1[k];
+                    v2 = p2[k];
+                }
+            }
+            sz[r][c] = vz;
+            s1[r][c] = v1;
+            s2[r][c] = v2;
+            sg[r][c] = 0.0f;
+        }
+    __syncthreads();
+    // cells of the loaded region that lie inside the image
+    const int r_lo = max(1, -ri0), r_hi = min(kChR, ny - 1 - ri0);
+    const int c_lo = max(1, -rj0), c_hi = min(kChR, nx - 1 - rj0);
+    for (int st = 0; st < steps; ++st) {
+        for (int r = r_lo + ty; r <= r_hi; r += 8) {
+            const int gi = ri0 + r;
+            for (int c = c_lo + tx; c <= c_hi; c += 32) {
+                const int gj = rj0 + c;
+                float d = 0.0f;
+                if (gi + 1 < ny) d = __fadd_rn(d, s1[r][c]);
+                if (gi > 0) d = __fsub_rn(d, s1[r - 1][c]);
+                if (gj + 1 < nx) d = __fadd_rn(d, s2[r][c]);
+                if (gj > 0) d = __fsub_rn(d, s2[r][c - 1]);
+                sg[r][c] = __fsub_rn(d, sz[r][c]);
+            }
+        }
+        __syncthreads();
+        for (int r = r_lo + ty; r <= r_hi; r += 8) {
+            const int gi = ri0 + r;
+            for (int c = c_lo + tx; c <= c_hi; c += 32) {
+                const int gj = rj0 + c;
+                const float g0 = sg[r][c];
+                const float g1 = (gi + 1 < ny) ? __fsub_rn(sg[r + 1][c], g0) : 0.0f;
+                const float g2 = (gj + 1 < nx) ? __fsub_rn(sg[r][c + 1], g0) : 0.0f;
+                const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
+                s1[r][c] = __fmul_rn(fmaf(tau, g1, s1[r][c]), inv);
+                s2[r][c] = __fmul_rn(fmaf(tau, g2, s2[r][c]), inv);
+            }
+        }
+        __syncthreads();
+    }
+    for (int r = ty; r < kChT; r += 8)
+        for (int c = tx; c < kChT; c += 32) {
+            const int gi = i0 + r, gj = j0 + c;
+            if (gi < ny && gj < nx) {
+                const size_t k = (size_t)gi * nx + gj;
+                q1[k] = s1[r + kChK + 1][c + kChK + 1];
+                q2[k] = s2[r + kChK + 1][c + kChK + 1];
+            }
+        }
+}
+
+// Launch plan of n_inner steps: launch m runs steps_of(m) steps, the first
+// from a zero dual field; the result is in the "a" buffers if the number of
+// launches is odd, else in "b".
+__host__ __device__ inline int chambolle_launches(int n_inner) { return (n_inner + kChK - 1) / kChK; }
+__host__ __device__ inline int chambolle_steps(int n_inner, int m) {
+    return m + 1 < chambolle_launches(n_inner) ? kChK : n_inner - kChK * m;
+}
+
+}  // namespace pyhst

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <vector>
 
+#include "chambolle.cuh"
 #include "common.cuh"
 
 namespace pyhst {
@@ -145,37 +146,31 @@ __global__ void grad_step_kernel(const float *__restrict__ y, const float *__res
         z[off + i] = fmaf(-g[off + i], il, y[off + i]);
 }
 
-// One Chambolle step: G = div p - z / lam,  p <- (p + tau grad G) / (1 + tau |grad G|).
-template <bool kFirst>
-__global__ void chambolle_kernel(const float *__restrict__ z, const float *__restrict__ p1, const float *__restrict__ p2,
-                                 float *__restrict__ q1, float *__restrict__ q2, const float *__restrict__ lam,
-                                 float tau, int nx, int ny) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= ny || j >= nx) return;
-    const size_t off = (size_t)blockIdx.z * nx * ny;
-    const float l = lam[blockIdx.z];
-    const float *Z = z + off;
-    const float *P1 = p1 + off, *P2 = p2 + off;
-    auto G = [&](int r, int c) -> float {
-        float d = 0.0f;
-        if (!kFirst) {
-            const size_t k = (size_t)r * nx + c;
-            if (r + 1 < ny) d += P1[k];
-            if (r > 0) d -= P1[k - nx];
-            if (c + 1 < nx) d += P2[k];
-            if (c > 0) d -= P2[k - 1];
-        }
-        return d - Z[(size_t)r * nx + c] / l;
-    };
-    const float g0 = G(i, j);
-    const float g1 = (i + 1 < ny) ? G(i + 1, j) - g0 : 0.0f;
-    const float g2 = (j + 1 < nx) ? G(i, j + 1) - g0 : 0.0f;
-    const float den = 1.0f + tau * sqrtf(g1 * g1 + g2 * g2);
-    const size_t k = (size_t)i * nx + j;
-    const float a = kFirst ? 0.0f : P1[k], b = kFirst ? 0.0f : P2[k];
-    q1[off + k] = (a + tau * g1) / den;
-    q2[off + k] = (b + tau * g2) / den;
+// n_inner Chambolle steps in launches of up to kChK fused steps (see
+// chambolle.cuh): launch 0 starts from a zero field and writes the "a"
+// buffers, launch m > 0 reads a (m odd) or b and writes the other.
+__global__ void __launch_bounds__(kChThreads)
+chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, float *pb1, float *pb2,
+                       const float *__restrict__ lam, float tau, int nx, int ny, int m, int steps, int tiles_x) {
+    const size_t off = (size_t)blockIdx.y * nx * ny;
+    const bool odd = m & 1;
+    const float *s1 = (odd ? pa1 : pb1) + off, *s2 = (odd ? pa2 : pb2) + off;
+    float *d1 = (m == 0 || !odd ? pa1 : pb1) + off, *d2 = (m == 0 || !odd ? pa2 : pb2) + off;
+    chambolle_tile(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * kChT,
+                   (blockIdx.x % tiles_x) * kChT, steps, m == 0);
+}
+
+// Enqueue n_inner steps; returns through *final_a whether the result is in the a buffers.
+int launch_chambolle(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
+                     int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st) {
+    const int tx = (nx + kChT - 1) / kChT, ty = (ny + kChT - 1) / kChT;
+    const int L = chambolle_launches(n_inner);
+    cudaFuncSetAttribute(chambolle_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem);
+    for (int m = 0; m < L; ++m)
+        chambolle_fused_kernel<<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
+            z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, chambolle_steps(n_inner, m), tx);
+    *final_a = (L & 1) == 1;
+    return cuda_status("Chambolle kernels");
 }
 
 // x = z - lam div p
@@ -337,14 +332,10 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
         grad_step_kernel<<<eg, kRedThreads, 0, st>>>(y, gr, B.sc.invL, z, N);
         // prox of (beta/L) TV
         if (o->beta > 0.0f) {
-            float *pi1 = p1a, *pi2 = p2a, *po1 = p1b, *po2 = p2b;
-            chambolle_kernel<true><<<tgr, tb, 0, st>>>(z, nullptr, nullptr, pi1, pi2, B.sc.lam, o->tau, g->nx, g->ny);
-            for (int n = 1; n < o->n_inner; ++n) {
-                chambolle_kernel<false><<<tgr, tb, 0, st>>>(z, pi1, pi2, po1, po2, B.sc.lam, o->tau, g->nx, g->ny);
-                std::swap(pi1, po1);
-                std::swap(pi2, po2);
-            }
-            prox_final_kernel<<<tgr, tb, 0, st>>>(z, pi1, pi2, B.sc.lam, xn, g->nx, g->ny);
+            bool fa;
+            if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, B.sc.lam, o->tau, g->nx, g->ny, S, o->n_inner, &fa, st)))
+                return rc;
+            prox_final_kernel<<<tgr, tb, 0, st>>>(z, fa ? p1a : p1b, fa ? p2a : p2b, B.sc.lam, xn, g->nx, g->ny);
         } else {
             cudaMemcpyAsync(xn, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
         }
@@ -389,14 +380,10 @@ int tv_prox_enqueue(const float *z, int nx, int ny, int S, float lam, int n_inne
         return cuda_status("prox copy");
     }
     fill_lam<<<(S + 127) / 128, 128, 0, st>>>(lamd, lam, S);
-    float *pi1 = p1a, *pi2 = p2a, *po1 = p1b, *po2 = p2b;
-    chambolle_kernel<true><<<tgr, tb, 0, st>>>(z, nullptr, nullptr, pi1, pi2, lamd, tau, nx, ny);
-    for (int k = 1; k < n_inner; ++k) {
-        chambolle_kernel<false><<<tgr, tb, 0, st>>>(z, pi1, pi2, po1, po2, lamd, tau, nx, ny);
-        std::swap(pi1, po1);
-        std::swap(pi2, po2);
-    }
-    prox_final_kernel<<<tgr, tb, 0, st>>>(z, pi1, pi2, lamd, x, nx, ny);
+    bool fa;
+    int rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, S, n_inner, &fa, st);
+    if (rc) return rc;
+    prox_final_kernel<<<tgr, tb, 0, st>>>(z, fa ? p1a : p1b, fa ? p2a : p2b, lamd, x, nx, ny);
     return cuda_status("prox kernels");
 }
 

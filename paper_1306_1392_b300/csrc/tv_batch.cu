@@ -18,6 +18,7 @@
 #include <tuple>
 #include <vector>
 
+#include "chambolle.cuh"
 #include "common.cuh"
 
 namespace pyhst {
@@ -83,40 +84,17 @@ __global__ void b_grad_step(const TvSlice *__restrict__ d, const int4 *__restric
     s.z[k] = fmaf(-s.g[k], sc.invL[it.x], s.y[k]);
 }
 
-template <bool kFirst>
-__global__ void b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau,
-                            int parity) {
+// Launch m of the fused Chambolle steps (see chambolle.cuh) on 32 x 32 tile
+// (items[k].y, items[k].z) of slice items[k].x; slices with beta = 0 skip.
+__global__ void __launch_bounds__(kChThreads)
+b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    int i, j;
-    if (!px_of(it, s, i, j) || s.beta == 0.0f) return;   // beta = 0: the prox is the identity
-    const int nx = s.nx, ny = s.ny;
-    const float *P1 = parity ? s.p1b : s.p1a, *P2 = parity ? s.p2b : s.p2a;
-    float *Q1 = parity ? s.p1a : s.p1b, *Q2 = parity ? s.p2a : s.p2b;
-    if (kFirst) {   // the first step writes the "a" buffers from a zero field
-        Q1 = s.p1a;
-        Q2 = s.p2a;
-    }
-    const float l = sc.lam[it.x];
-    auto G = [&](int r, int c) -> float {
-        float dv = 0.0f;
-        if (!kFirst) {
-            const size_t k = (size_t)r * nx + c;
-            if (r + 1 < ny) dv += P1[k];
-            if (r > 0) dv -= P1[k - nx];
-            if (c + 1 < nx) dv += P2[k];
-            if (c > 0) dv -= P2[k - 1];
-        }
-        return dv - s.z[(size_t)r * nx + c] / l;
-    };
-    const float g0 = G(i, j);
-    const float g1 = (i + 1 < ny) ? G(i + 1, j) - g0 : 0.0f;
-    const float g2 = (j + 1 < nx) ? G(i, j + 1) - g0 : 0.0f;
-    const float den = 1.0f + tau * sqrtf(g1 * g1 + g2 * g2);
-    const size_t k = (size_t)i * nx + j;
-    const float a = kFirst ? 0.0f : P1[k], b = kFirst ? 0.0f : P2[k];
-    Q1[k] = (a + tau * g1) / den;
-    Q2[k] = (b + tau * g2) / den;
+    if (s.beta == 0.0f) return;
+    const bool odd = m & 1;
+    const float *s1 = odd ? s.p1a : s.p1b, *s2 = odd ? s.p2a : s.p2b;
+    float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
+    chambolle_tile(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * kChT, it.y * kChT, steps, m == 0);
 }
 
 // x_new = z - lam div p (p in the buffers of `parity`); with lam = 0, x_new = z
@@ -303,7 +281,7 @@ struct Plan {
     int n = 0;
     std::vector<int> rep;                       // representative of each slice
     std::vector<int> reps;                      // distinct representatives
-    std::vector<int4> bp, proj, tr, px, sn;     // all slices
+    std::vector<int4> bp, proj, tr, px, sn, ch; // all slices (ch: 32 x 32 Chambolle tiles)
     std::vector<int4> bp_r, proj_r, tr_r, px_r, sn_r;   // representatives only
     std::vector<size_t> img_off, sino_off;      // per slice, in floats
     size_t img_total = 0, sino_total = 0;
@@ -332,6 +310,9 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     auto &sn = rep_only ? P.sn_r : P.sn;
     const int M = g.n_angles * g.n_bins;
     for (int e = 0; e < (M + kSinoBlock - 1) / kSinoBlock; ++e) sn.push_back(make_int4(s, e, 0, 0));
+    if (!rep_only)
+        for (int y = 0; y < (g.ny + kChT - 1) / kChT; ++y)
+            for (int x = 0; x < (g.nx + kChT - 1) / kChT; ++x) P.ch.push_back(make_int4(s, x, y, 0));
 }
 
 Plan make_plan(const pyhst_tv_item *items, int n) {
@@ -379,7 +360,8 @@ Layout make_layout(const Plan &P, const pyhst_tv_item *items) {
     l.desc_pow = take(sizeof(BatchSlice) * P.n);
     l.tvs = take(sizeof(TvSlice) * P.n);
     l.reps = take(sizeof(int) * P.reps.size());
-    l.n_items_total = P.bp.size() + P.proj.size() + P.tr.size() + P.px.size() + P.sn.size() + P.bp_r.size() +
+    l.n_items_total = P.bp.size() + P.proj.size() + P.tr.size() + P.px.size() + P.sn.size() + P.ch.size() +
+                      P.bp_r.size() +
                       P.proj_r.size() + P.tr_r.size() + P.px_r.size() + P.sn_r.size();
     l.items = take(sizeof(int4) * l.n_items_total);
     for (int s = 0; s < P.n; ++s) l.tab_off.push_back(take(sizeof(AngleInfo) * items[s].geom.n_angles));
@@ -488,7 +470,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     std::vector<int4> all;
     auto append = [&](const std::vector<int4> &v) { size_t o = all.size(); all.insert(all.end(), v.begin(), v.end()); return o; };
     const size_t o_bp = append(P.bp), o_proj = append(P.proj), o_tr = append(P.tr), o_px = append(P.px),
-                 o_sn = append(P.sn), o_bpr = append(P.bp_r), o_projr = append(P.proj_r), o_trr = append(P.tr_r),
+                 o_sn = append(P.sn), o_ch = append(P.ch), o_bpr = append(P.bp_r), o_projr = append(P.proj_r), o_trr = append(P.tr_r),
                  o_pxr = append(P.px_r), o_snr = append(P.sn_r);
     // pageable host memory: each copy returns once its data are staged
     cudaMemcpyAsync(ws + L.desc_even, ev.data(), sizeof(BatchSlice) * n, cudaMemcpyHostToDevice, st);
@@ -521,7 +503,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     double *part_px = reinterpret_cast<double *>(ws + L.part_px);
     double *part_sn = reinterpret_cast<double *>(ws + L.part_sn);
     const int npx = (int)P.px.size(), nsn = (int)P.sn.size(), nbp = (int)P.bp.size(), npr = (int)P.proj.size(),
-              ntr = (int)P.tr.size();
+              ntr = (int)P.tr.size(), nch = (int)P.ch.size();
     const dim3 tb(kBT);
 
     // ---- step size: power iteration on the representatives, or the caller's L
@@ -552,6 +534,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     b_copy_sino_start<<<nsn, tb, 0, st>>>(T, I + o_sn, opts->warm_start ? 1 : 0);
     if ((rc = cuda_status("batch start"))) return rc;
 
+    cudaFuncSetAttribute(b_chambolle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem);
     // ---- the iterations, captured in one graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
@@ -567,13 +550,13 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st);
         if (rc) break;
         b_grad_step<<<npx, tb, 0, st>>>(T, I + o_px, sc);
-        int pp = 0;
+        int pp = 0;   // 0: the dual field ends in the "a" buffers
         if (!identity) {
-            b_chambolle<true><<<npx, tb, 0, st>>>(T, I + o_px, sc, opts->tau, 0);
-            for (int m = 1; m < opts->n_inner; ++m) {
-                b_chambolle<false><<<npx, tb, 0, st>>>(T, I + o_px, sc, opts->tau, pp);
-                pp ^= 1;
-            }
+            const int Lc = chambolle_launches(opts->n_inner);
+            for (int m = 0; m < Lc; ++m)
+                b_chambolle<<<nch, kChThreads, kChSmem, st>>>(T, I + o_ch, sc, opts->tau, m,
+                                                               chambolle_steps(opts->n_inner, m));
+            pp = (Lc & 1) ? 0 : 1;
         }
         b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, pp, par, identity);
         rc = launch_project_batch(par ? D_odd : D_even, I + o_proj, npr, I + o_tr, ntr, st);
