@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--precision-study", action="store_true",
                     help="mixed-precision FBP study (4096^2, 4000 angles; f32/f16/bf16 storage vs the FP64 oracle)")
     ap.add_argument("--precision-slices", type=int, default=2, help="slices checked against the oracle")
+    ap.add_argument("--tv-only", action="store_true", help="only the reduced-dose TV measurement (for profilers)")
     ap.add_argument("--kernel-case", choices=["backproject", "project", "filter"],
                     help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
     return ap.parse_args()
@@ -324,6 +325,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     import paper_1306_1392_b300 as P
+    from paper_1306_1392_b300.shard import reduce_throughput
     from synth import acquisition as acq
 
     dev = torch.device("cuda", local_rank)
@@ -366,13 +368,8 @@ def run_ours(args, rank, world, local_rank):
     fl_ms, fl_n = P.pyhst_profile_read("filter")
     slices_done = sum(min(((args.warmup + k) * S) % NZ + S, NZ) - ((args.warmup + k) * S) % NZ
                       for k in range(args.steps))
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    n_tot = torch.tensor([slices_done], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(n_tot, op=dist.ReduceOp.SUM)
-    ms_max = t.item()
-    value = n_tot.item() * UPD_PER_SLICE / (ms_max * 1e-3) / 1e9
+    ms_max, n_slices_all = reduce_throughput(ms, slices_done, device=dev)
+    value = n_slices_all * UPD_PER_SLICE / (ms_max * 1e-3) / 1e9
 
     # ---- end to end through the host-buffer C-ABI call (same metric)
     e2e = None
@@ -400,10 +397,8 @@ def run_ours(args, rank, world, local_rank):
             estep()
         e1.record()
         barrier()
-        ems = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps * S * UPD_PER_SLICE / (ems.item() * 1e-3) / 1e9, "unit": "Gupd/s",
+        ems, e_slices = reduce_throughput(e0.elapsed_time(e1), args.steps * S, device=dev)
+        e2e = {"value": e_slices * UPD_PER_SLICE / (ems * 1e-3) / 1e9, "unit": "Gupd/s",
                "h2d_bytes_per_step": int(host_raw.numel() * 2 + 2 * host_flat.numel() * 4),
                "d2h_bytes_per_step": int(host_out.numel() * 4),
                "call": "pyhst_fbp_host (pinned host in/out, 8-slice chunks double-buffered)"}
@@ -461,7 +456,7 @@ def run_ours(args, rank, world, local_rank):
                            "l2": f"inputs larger than L2: {S * N_ANG * N_BINS * 2 / 1e6:.0f} MB of raw counts "
                                  f"per step; the whole {NZ}-slice stack ({raw_gb:.1f} GB) resident",
                            "pad_len": 4096, "slices_per_pass": 4},
-                "fbp_slices_per_s": n_tot.item() / (ms_max * 1e-3),
+                "fbp_slices_per_s": n_slices_all / (ms_max * 1e-3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "tv": tv,
                 "gpu_launches": int(bp_n + fl_n + 3 * args.steps),
                 "clocks": clk.summary()}
@@ -520,6 +515,11 @@ def main():
         return
     if args.precision_study:
         run_precision_study(args)
+        return
+    if args.tv_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"tv": run_tv(torch.device("cuda", 0))}), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

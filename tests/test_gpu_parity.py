@@ -290,3 +290,18 @@ def test_fbp_4096_geometry_sampled(P, orc, cuda_device, kind, dt):
     jj = np.concatenate([rng.integers(0, n, 1200), [n - 1, 0, n // 2]])
     ref = orc.backproject_at(q, ang.double().numpy(), (n - 1) / 2.0, n, n, ii, jj, orc.fbp_weight(na, 2.0 / n))
     close(got[0].cpu().numpy()[ii, jj], ref)
+
+
+def test_fbp_shards_reassemble_the_volume(P, cuda_device):
+    """Each rank's contiguous share (computed here one after the other on one
+    GPU) equals the same slices of a single whole-stack call."""
+    from paper_1306_1392_b300.shard import fbp_shard
+    vol = acq.ellipsoid_volume(n_slices=7, n=64, n_angles=40, seed=61, n_ellipsoids=30)
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
+                   cuda_device)
+    raw, fl, dk = vol.raw.to(cuda_device), vol.flat.to(cuda_device), vol.dark.to(cuda_device)
+    full = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk)
+    parts = [fbp_shard(geo, raw, "u16_raw", fl, dk, world=3, rank=r) for r in range(3)]
+    torch.cuda.synchronize()
+    assert [p[:2] for p in parts] == [(0, 3), (3, 5), (5, 7)]
+    assert torch.equal(torch.cat([p[2] for p in parts]), full)
