@@ -54,6 +54,8 @@ def lib():
         L.orc_rof_gap.restype = D
         L.orc_energy.restype = D
         L.orc_power_iteration.restype = D
+        L.orc_cosine.restype = D
+        L.orc_ecohe.restype = D
         _lib = L
     return _lib
 
@@ -240,3 +242,34 @@ def fista(g: Geometry, sino, beta, L, n_iter, n_inner=20, tau=0.125, use_fista=T
     lib().orc_fista(ctypes.byref(gc), ps, D(beta), D(L), I64(n_iter), I64(n_inner), D(tau),
                     ctypes.c_int(1 if use_fista else 0), x.ctypes.data_as(PD), e.ctypes.data_as(PD))
     return x, e
+
+
+# ------------------------------------------------------------------ beta estimators (Sec. 4)
+def cosine(a, b):
+    a, pa = _c(a)
+    b, pb = _c(b)
+    return lib().orc_cosine(pa, pb, I64(a.size))
+
+
+def ecohe(I_beta, I_0):
+    """Eq. 11: Cos(I(beta) - I(0+), I(beta))."""
+    a, pa = _c(I_beta)
+    b, pb = _c(I_0)
+    return lib().orc_ecohe(pa, pb, I64(a.size))
+
+
+def cross_validation(g: Geometry, sino, held_out, betas, L, n_iter, n_inner=20, tau=0.125):
+    """Cross-validation estimator (Sec. 4): reconstruct without the projection
+    at angle index held_out, project the result at that angle, return the
+    squared distance to the held-out data for each beta, plus the images."""
+    keep = [a for a in range(len(g.angles)) if a != held_out]
+    gk = Geometry(g.angles[keep], g.axis[keep], g.n_bins, g.nx, g.ny, g.pixel_size, g.cx, g.cy)
+    sino = np.asarray(sino, dtype=np.float64)
+    errs, imgs = [], []
+    for b in betas:
+        x, _ = fista(gk, sino[keep], b, L, n_iter, n_inner=n_inner, tau=tau)
+        row = project(x, g.angles[held_out:held_out + 1], g.axis[held_out:held_out + 1], g.n_bins,
+                      g.pixel_size, g.cx, g.cy)[0]
+        errs.append(float(np.sum((row - sino[held_out]) ** 2)))
+        imgs.append(x)
+    return np.array(errs), imgs

@@ -392,3 +392,30 @@ void orc_fista(const orc_geom *g, const double *sino, double beta, double L,
     }
     free(y); free(xprev); free(z); free(grad); free(p1); free(p2); free(r);
 }
+
+/* ---------------------------------------------------------------------
+ * beta-selection estimators (Sec. 4, Eqs. 10-11).
+ * Cosine of the angle between two images: <a, b> / (||a|| ||b||)
+ * (NaN when either norm is zero).
+ * ------------------------------------------------------------------- */
+double orc_cosine(const double *a, const double *b, int64_t n)
+{
+    double ab = 0.0, aa = 0.0, bb = 0.0;
+    for (int64_t k = 0; k < n; k++) {
+        ab += a[k] * b[k];
+        aa += a[k] * a[k];
+        bb += b[k] * b[k];
+    }
+    if (aa == 0.0 || bb == 0.0) return NAN;
+    return ab / (sqrt(aa) * sqrt(bb));
+}
+
+/* Decoherence estimator (Eq. 11): E = Cos(I(beta) - I(0+), I(beta)). */
+double orc_ecohe(const double *I_beta, const double *I_0, int64_t n)
+{
+    double *d = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; k++) d[k] = I_beta[k] - I_0[k];
+    double c = orc_cosine(d, I_beta, n);
+    free(d);
+    return c;
+}

@@ -150,3 +150,34 @@ def test_fista_tv_recovers_piecewise_constant(orc):
     x0, _ = orc.fista(geo, y, 0.0, L, 150, n_inner=1)
     xb, _ = orc.fista(geo, y, 2e-3, L, 150, n_inner=20)
     assert np.linalg.norm(xb - xt) < 0.7 * np.linalg.norm(x0 - xt)
+
+
+def test_cosine_and_ecohe_closed_forms(orc):
+    """Cos of known vectors (orthogonal 0, parallel 1, 60 degrees 1/2), and
+    Eq. 11 on a scaled copy: I(beta) = c I(0+) gives sign((c - 1) c)."""
+    a = np.array([1.0, 0.0, 0.0])
+    assert orc.cosine(a, np.array([0.0, 2.0, 0.0])) == 0.0
+    assert orc.cosine(a, 3 * a) == pytest.approx(1.0, abs=1e-15)
+    assert orc.cosine(a, np.array([0.5, math.sqrt(3) / 2, 0.0])) == pytest.approx(0.5, abs=1e-15)
+    assert math.isnan(orc.cosine(a, np.zeros(3)))
+    g = np.random.default_rng(0)
+    I0 = g.standard_normal((9, 7))
+    assert orc.ecohe(0.5 * I0, I0) == pytest.approx(-1.0, abs=1e-14)
+    assert orc.ecohe(2.0 * I0, I0) == pytest.approx(1.0, abs=1e-14)
+    assert math.isnan(orc.ecohe(I0, I0))
+
+
+def test_cross_validation_is_zero_on_consistent_data(orc):
+    """Data generated by the projector itself from an image the solver can
+    reach: with beta = 0 and many iterations the held-out projection of the
+    reconstruction matches the held-out data (the estimator's zero)."""
+    n = 12
+    angles = np.arange(30) * math.pi / 30
+    geo = orc.Geometry(angles, (n - 1) / 2.0 + 2.0, n + 4, n, n, 0.1)
+    g = np.random.default_rng(1)
+    x_true = g.uniform(0, 1, (n, n))
+    y = geo.P(x_true)
+    L = 1.01 * orc.power_iteration(geo, np.ones((n, n)), 200)[0]
+    e1, _ = orc.cross_validation(geo, y, 7, [0.0], L, 1000, n_inner=1)
+    e3, _ = orc.cross_validation(geo, y, 7, [0.0], L, 3000, n_inner=1)
+    assert e3[0] < 1e-8 * np.sum(y[7] ** 2) and e3[0] < 0.1 * e1[0]   # -> 0 as the solve converges
