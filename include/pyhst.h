@@ -222,6 +222,23 @@ size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n_slices);
 int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
                   float tau, float *x, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
+/* Estimators of beta without ground truth (Sec. 4).  Reconstructs one slice
+ * (geometry g, n_slices ignored) for each of the n_beta values betas (HOST
+ * array; the first should be a very small beta, the paper's "0+") in one
+ * batched solve with options opts, leaving out the projection at angle index
+ * held_out (-1: use all projections), then returns, per beta:
+ *   x     [n_beta][ny][nx]  the reconstructions;
+ *   cv    [n_beta] float64 (DEVICE, or NULL; needs held_out >= 0): the
+ *         cross-validation error || P_k x - y_k ||^2 at the held-out angle k;
+ *   ecohe [n_beta] float64 (DEVICE, or NULL): Eq. 11,
+ *         Cos(I(beta) - I(betas[0]), I(beta)) (NaN for a zero difference).
+ * Workspace: pyhst_beta_scan_workspace_size. */
+size_t pyhst_beta_scan_workspace_size(const pyhst_geometry *g, int32_t n_beta, int32_t held_out,
+                                      const pyhst_tv_opts *opts);
+int pyhst_beta_scan(const pyhst_geometry *g, const float *sino, const float *betas, int32_t n_beta,
+                    int32_t held_out, const pyhst_tv_opts *opts, float *x, double *cv, double *ecohe,
+                    void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
 /* Opt-in per-kernel timing for measurement: while enabled (per host thread),
  * every launch of the back-projection, filter and projection kernels is
  * bracketed by CUDA events on its launch stream.  pyhst_profile_read waits for

@@ -26,7 +26,7 @@ from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SIN
 
 __all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_filter", "pyhst_fbp_host",
            "pyhst_profile_enable", "pyhst_profile_read", "pyhst_fbp_static", "pyhst_backproject", "pyhst_project",
-           "pyhst_tv_solve", "pyhst_tv_solve_batch", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
+           "pyhst_tv_solve", "pyhst_tv_solve_batch", "pyhst_beta_scan", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
            "pyhst_version", "library_path"]
 
 
@@ -384,6 +384,26 @@ def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace
     _check(L.lib.pyhst_tv_solve_batch(items, len(slices), ctypes.byref(o), _ptr(lip), _ptr(ws), ws.numel(),
                                       _stream()))
     return xs, es, lip
+
+
+def pyhst_beta_scan(geom: Geometry, sino: torch.Tensor, betas, opts: TvOptions, held_out: int = -1,
+                    workspace=None):
+    """Sec. 4 estimators over a beta grid: returns (x [n_beta, ny, nx],
+    cross-validation error [n_beta] float64 or None, E_cohe [n_beta] float64)."""
+    sino = _cuda(sino, "sino", (torch.float32,))
+    if tuple(sino.shape[-2:]) != (geom.n_angles, geom.n_bins):
+        raise ValueError("sinogram shape does not match the geometry")
+    nbeta = len(betas)
+    bh = (ctypes.c_float * nbeta)(*[float(b) for b in betas])
+    x = torch.empty((nbeta, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    cv = torch.empty((nbeta,), dtype=torch.float64, device=sino.device) if held_out >= 0 else None
+    ec = torch.empty((nbeta,), dtype=torch.float64, device=sino.device)
+    g, o = geom.c(1), opts.c()
+    need = L.lib.pyhst_beta_scan_workspace_size(ctypes.byref(g), nbeta, held_out, ctypes.byref(o))
+    ws = _workspace(need, sino.device, workspace)
+    _check(L.lib.pyhst_beta_scan(ctypes.byref(g), _ptr(sino), bh, nbeta, held_out, ctypes.byref(o), _ptr(x), _ptr(cv),
+                                 _ptr(ec), _ptr(ws), ws.numel(), _stream()))
+    return x, cv, ec
 
 
 def fbp_weight(n_angles: int, pixel_size: float) -> float:

@@ -74,6 +74,11 @@ SIGNATURES = [
                                                  ctypes.POINTER(pyhst_tv_opts)]),
     ("pyhst_tv_solve_batch", c_int32, [ctypes.POINTER(pyhst_tv_item), c_int32, ctypes.POINTER(pyhst_tv_opts),
                                        c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_beta_scan_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32,
+                                                  ctypes.POINTER(pyhst_tv_opts)]),
+    ("pyhst_beta_scan", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(c_float), c_int32, c_int32,
+                                  ctypes.POINTER(pyhst_tv_opts), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                  c_void_p]),
     ("pyhst_last_error", ctypes.c_char_p, []),
     ("pyhst_version", ctypes.c_char_p, []),
 ]

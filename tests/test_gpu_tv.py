@@ -201,3 +201,31 @@ def test_batch_per_item_beta(P, cuda_device):
         x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), o1)
         assert torch.equal(xs[k], x1[0]), k
         np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
+
+
+# ------------------------------------------------------------------ beta estimators (Sec. 4)
+@pytest.mark.parametrize("held_out", [5, 0, -1])
+def test_beta_scan_estimators_parity(P, orc, cuda_device, held_out):
+    """Cross-validation error and E_cohe (Eq. 11) over a beta grid against
+    the oracle's, with the same step size; the iterates as in the solver
+    parity tests."""
+    fs, geo, og = _foam_problem(P, orc, cuda_device, n=48, na=20, seed=13)
+    sino = fs.extra["sino"]
+    keep = [a for a in range(20) if a != held_out]
+    ogk = orc.Geometry(og.angles[keep], og.axis[keep], og.n_bins, og.nx, og.ny, og.pixel_size)
+    L = 1.01 * orc.power_iteration(ogk, np.ones((48, 48)), 30)[0]
+    betas = [1e-5, 5e-4, 2e-3, 8e-3]
+    opts = P.TvOptions(beta=0.0, n_iter=25, n_inner=10, lipschitz=L)
+    x, cv, ec = P.pyhst_beta_scan(geo, sino.to(cuda_device), betas, opts, held_out=held_out)
+    torch.cuda.synchronize()
+    if held_out >= 0:
+        cv_ref, imgs = orc.cross_validation(og, sino.double().numpy(), held_out, betas, L, 25, n_inner=10)
+        np.testing.assert_allclose(cv.cpu().numpy(), cv_ref, rtol=1e-4)
+    else:
+        assert cv is None
+        imgs = [orc.fista(og, sino.double().numpy(), b, L, 25, n_inner=10)[0] for b in betas]
+    for k in range(len(betas)):
+        assert rel(x[k].cpu().numpy(), imgs[k]) <= 1e-4
+    ec_ref = [orc.ecohe(im, imgs[0]) for im in imgs]
+    assert math.isnan(ec[0].item()) and math.isnan(ec_ref[0])
+    np.testing.assert_allclose(ec.cpu().numpy()[1:], ec_ref[1:], atol=2e-4)
