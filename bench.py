@@ -62,6 +62,8 @@ def parse():
                     help="mixed-precision FBP study (4096^2, 4000 angles; f32/f16/bf16 storage vs the FP64 oracle)")
     ap.add_argument("--precision-slices", type=int, default=2, help="slices checked against the oracle")
     ap.add_argument("--tv-only", action="store_true", help="only the reduced-dose TV measurement (for profilers)")
+    ap.add_argument("--beta-study", action="store_true",
+                    help="beta estimators (Sec. 4) on a 2048^2 foam with 150 projections vs its ground truth")
     ap.add_argument("--kernel-case", choices=["backproject", "project", "filter"],
                     help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
     return ap.parse_args()
@@ -319,6 +321,42 @@ def run_precision_study(args):
                                    f"slices {check}, worst slice reported"}), flush=True)
 
 
+# ------------------------------------------------------------------ beta estimators
+def run_beta_study(n=2048, n_angles=150, n_iter=200, seed=5150):
+    """The paper's validation setting (Sec. 4): a synthetic 2k x 2k phantom
+    with 150 projections; cross-validation and E_cohe over a beta grid in one
+    scan, against the ground-truth PSNR of each reconstruction."""
+    import numpy as np
+    import torch
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    dev = torch.device("cuda", 0)
+    fs = acq.foam_slice(n, n_angles, seed=seed, device=dev)
+    geo = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), n, n, n, fs.pixel_size)
+    betas = [1e-5] + [float(b) for b in np.logspace(-4, -1, 13)]
+    opts = P.TvOptions(beta=0.0, n_iter=n_iter, n_inner=20)
+    sino = fs.extra["sino"].to(dev)
+    P.pyhst_beta_scan(geo, sino, betas[:2], P.TvOptions(beta=0.0, n_iter=2, n_inner=20), held_out=n_angles // 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x, cv, ec = P.pyhst_beta_scan(geo, sino, betas, opts, held_out=n_angles // 2)
+    e1.record()
+    torch.cuda.synchronize()
+    truth = fs.truth.double().cpu().numpy()
+    ps = [psnr(x[k].double().cpu().numpy(), truth) for k in range(len(betas))]
+    cvv, ecv = cv.cpu().numpy(), ec.cpu().numpy()
+    k_gt, k_cv = int(np.argmax(ps[1:])) + 1, int(np.argmin(cvv[1:])) + 1
+    k_ec = int(np.nanargmin(np.abs(ecv[1:]))) + 1
+    print(json.dumps({"beta_study": {
+        "workload": f"foam phantom {n}^2, {n_angles} projections over 180 deg, Poisson 1e4 photons; "
+                    f"FISTA {n_iter} x Chambolle 20 per beta; held-out angle {n_angles // 2}",
+        "betas": betas, "psnr": ps, "cv": cvv.tolist(), "ecohe": ecv.tolist(),
+        "beta_best_psnr": betas[k_gt], "beta_min_cv": betas[k_cv], "beta_min_abs_ecohe": betas[k_ec],
+        "psnr_at": {"best": ps[k_gt], "min_cv": ps[k_cv], "min_abs_ecohe": ps[k_ec]},
+        "scan_s": e0.elapsed_time(e1) * 1e-3}}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -515,6 +553,9 @@ def main():
         return
     if args.precision_study:
         run_precision_study(args)
+        return
+    if args.beta_study:
+        run_beta_study()
         return
     if args.tv_only:
         import torch
