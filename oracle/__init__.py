@@ -273,3 +273,52 @@ def cross_validation(g: Geometry, sino, held_out, betas, L, n_iter, n_inner=20, 
         errs.append(float(np.sum((row - sino[held_out]) ** 2)))
         imgs.append(x)
     return np.array(errs), imgs
+
+
+# ------------------------------------------------------------------ preprocessing variants (Sec. 2.3)
+def flatfield(I, flats, pos, D):
+    """I [na, nz, nb], flats [nf, nz, nb], pos [na] (ignored for one flat),
+    D [nz, nb] -> r = (I - D) / (F(pos) - D)."""
+    I, pI = _c(I)
+    flats, pf = _c(flats)
+    na, nz, nb = I.shape
+    nf = flats.shape[0]
+    pos, pp = _c(np.zeros(na) if pos is None else pos)
+    D, pD = _c(D)
+    r = np.empty_like(I)
+    lib().orc_flatfield(pI, pf, I64(nf), pp, pD, I64(na), I64(nz), I64(nb), r.ctypes.data_as(PD))
+    return r
+
+
+def hotspot(r, threshold):
+    r, pr = _c(r)
+    out = np.empty_like(r)
+    na, nz, nb = r.shape
+    lib().orc_hotspot(pr, I64(na), I64(nz), I64(nb), D(threshold), out.ctypes.data_as(PD))
+    return out
+
+
+def neglog(r):
+    r, pr = _c(r)
+    p = np.empty_like(r)
+    lib().orc_log(pr, I64(r.size), p.ctypes.data_as(PD))
+    return p
+
+
+def ring(p, window):
+    """Ring filter of one sinogram p [na, nb] (returns a corrected copy)."""
+    p = np.array(p, dtype=np.float64, copy=True)
+    lib().orc_ring(p.ctypes.data_as(PD), I64(p.shape[0]), I64(p.shape[1]), I64(window))
+    return p
+
+
+def preprocess(I, flats, pos, D, hotspot_threshold=0.0, ring_window=0):
+    """Sec. 2.3 order: flat field, hot spots, -ln, rearrangement into
+    sinograms, ring filter.  Returns p [nz, na, nb]."""
+    r = flatfield(I, flats, pos, D)
+    if hotspot_threshold > 0:
+        r = hotspot(r, hotspot_threshold)
+    p = np.ascontiguousarray(neglog(r).transpose(1, 0, 2))
+    if ring_window > 0:
+        p = np.stack([ring(pz, ring_window) for pz in p])
+    return p

@@ -419,3 +419,102 @@ double orc_ecohe(const double *I_beta, const double *I_0, int64_t n)
     free(d);
     return c;
 }
+
+/* ---------------------------------------------------------------------
+ * Preprocessing variants (Sec. 2.3), on a raw stack I [na][nz][nb]
+ * (projection-major) in the paper's order: dark/flat correction with flats
+ * interpolated in time, hot-spot median filter, -ln, ring filter.
+ *
+ * Flat field: projection a uses F = (1 - w) flats[f0] + w flats[f0 + 1],
+ * f0 = floor(pos[a]), w = pos[a] - f0 (pos clamped to [0, nf - 1]; flats are
+ * [nf][nz][nb]); r = (I - D) / (F - D), r = 1 where F - D <= 0.
+ * ------------------------------------------------------------------- */
+void orc_flatfield(const double *I, const double *flats, int64_t nf, const double *pos, const double *D,
+                   int64_t na, int64_t nz, int64_t nb, double *r)
+{
+    for (int64_t a = 0; a < na; a++) {
+        double ps = nf > 1 ? pos[a] : 0.0;
+        if (ps < 0.0) ps = 0.0;
+        if (ps > (double)(nf - 1)) ps = (double)(nf - 1);
+        int64_t f0 = (int64_t)floor(ps);
+        if (f0 > nf - 2) f0 = nf > 1 ? nf - 2 : 0;
+        double w = ps - (double)f0;
+        for (int64_t z = 0; z < nz; z++)
+            for (int64_t b = 0; b < nb; b++) {
+                int64_t k = z * nb + b;
+                double F = flats[f0 * nz * nb + k];
+                if (nf > 1) F = (1.0 - w) * F + w * flats[(f0 + 1) * nz * nb + k];
+                double den = F - D[k];
+                r[(a * nz + z) * nb + b] = den > 0.0 ? (I[(a * nz + z) * nb + b] - D[k]) / den : 1.0;
+            }
+    }
+}
+
+static int cmp_double(const void *x, const void *y)
+{
+    double a = *(const double *)x, b = *(const double *)y;
+    return (a > b) - (a < b);
+}
+
+/* Hot-spot filter: in each projection, a pixel whose neighbours' median (the
+ * up to 8 pixels around it in the (z, b) plane that exist; for an even count
+ * the mean of the two middle values) is smaller than the pixel by more than
+ * `threshold` takes that median.  Neighbours are read from the input. */
+void orc_hotspot(const double *r, int64_t na, int64_t nz, int64_t nb, double threshold, double *out)
+{
+    for (int64_t a = 0; a < na; a++)
+        for (int64_t z = 0; z < nz; z++)
+            for (int64_t b = 0; b < nb; b++) {
+                double v[8];
+                int n = 0;
+                for (int dz = -1; dz <= 1; dz++)
+                    for (int db = -1; db <= 1; db++) {
+                        if (dz == 0 && db == 0) continue;
+                        int64_t zz = z + dz, bb = b + db;
+                        if (zz < 0 || zz >= nz || bb < 0 || bb >= nb) continue;
+                        v[n++] = r[(a * nz + zz) * nb + bb];
+                    }
+                double x = r[(a * nz + z) * nb + b];
+                double med = x;
+                if (n > 0) {
+                    qsort(v, n, sizeof(double), cmp_double);
+                    med = (n % 2) ? v[n / 2] : 0.5 * (v[n / 2 - 1] + v[n / 2]);
+                }
+                out[(a * nz + z) * nb + b] = (med < x - threshold) ? med : x;
+            }
+}
+
+/* p = -ln(max(r, 1e-6)) (absorption; same clamp as orc_normalise). */
+void orc_log(const double *r, int64_t n, double *p)
+{
+    for (int64_t k = 0; k < n; k++) p[k] = -log(r[k] < 1e-6 ? 1e-6 : r[k]);
+}
+
+/* Ring filter on one sinogram p [na][nb] (in place): s(b) = mean over angles,
+ * m(b) = mean of s over [b - h, b + h] inside [0, nb) with h = (window-1)/2,
+ * and p(a, b) -= s(b) - m(b) (the high-pass part of the angular mean). */
+void orc_ring(double *p, int64_t na, int64_t nb, int64_t window)
+{
+    double *sm = (double *)calloc(nb > 0 ? nb : 1, sizeof(double));
+    double *hp = (double *)calloc(nb > 0 ? nb : 1, sizeof(double));
+    int64_t h = (window - 1) / 2;
+    for (int64_t b = 0; b < nb; b++) {
+        double acc = 0.0;
+        for (int64_t a = 0; a < na; a++) acc += p[a * nb + b];
+        sm[b] = acc / (double)na;
+    }
+    for (int64_t b = 0; b < nb; b++) {
+        double acc = 0.0;
+        int64_t cnt = 0;
+        for (int64_t c = b - h; c <= b + h; c++)
+            if (c >= 0 && c < nb) {
+                acc += sm[c];
+                cnt++;
+            }
+        hp[b] = sm[b] - acc / (double)cnt;
+    }
+    for (int64_t a = 0; a < na; a++)
+        for (int64_t b = 0; b < nb; b++) p[a * nb + b] -= hp[b];
+    free(sm);
+    free(hp);
+}
