@@ -166,6 +166,36 @@ int pyhst_fbp_static(const pyhst_geometry *g, int input_type, const void *data,
                      const float *flat, const float *dark, int filter, int32_t pad_len,
                      float *out, pyhst_stream_t stream);
 
+/* Preprocessing variants of Sec. 2.3 for pyhst_fbp_pre. */
+typedef struct {
+    int32_t n_flats;          /* >= 1 flats acquired at different times                     */
+    const float *flats;       /* DEVICE [n_flats][n_slices][n_bins]                         */
+    const float *flat_pos;    /* DEVICE [n_angles]: position of each projection between the
+                                 flats (0 .. n_flats-1, clamped); the flat is the linear
+                                 interpolation there; NULL when n_flats == 1               */
+    float hotspot_threshold;  /* > 0: hot-spot median filter on r = (I - D) / (F - D): a pixel
+                                 whose neighbours' median (up to 8 pixels around it in the
+                                 (slice, bin) plane of its projection; mean of the two middle
+                                 values for an even count) is below r - threshold takes that
+                                 median.  0: off                                            */
+    int32_t ring_window;      /* odd >= 3: ring filter, subtracting from each sinogram the
+                                 high-pass part of its mean over angles (mean minus its
+                                 moving average over this many bins).  0: off               */
+} pyhst_preproc;
+
+/* pyhst_fbp with the preprocessing of Sec. 2.3, in the paper's order
+ * (dark/flat with flats interpolated in time, hot spots, -ln, sinograms, ring
+ * filter, then the Ram-Lak filter and back-projection).  Raw kinds only; data
+ * strides as in pyhst_fbp; dark [n_slices][n_bins]; the hot-spot filter reads
+ * the neighbouring detector rows of the stack (slices 0 .. n_slices-1 are the
+ * whole detector).  Workspace: pyhst_fbp_pre_workspace_size (slices_per_pass
+ * slices of filtered and of preprocessed rows). */
+size_t pyhst_fbp_pre_workspace_size(const pyhst_geometry *g, int32_t pad_len, int32_t slices_per_pass);
+int pyhst_fbp_pre(const pyhst_geometry *g, int input_type, const void *data,
+                  int64_t slice_stride, int64_t angle_stride, const float *dark,
+                  const pyhst_preproc *pre, int filter, int32_t pad_len, float *out,
+                  void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
 /* Back-projection (Sec. 2.3) of n_slices sinograms [n_slices][n_angles][n_bins]
  * into images [n_slices][ny][nx]:
  *     img[i][j] = weight * sum_a L(sino_a, t_a(i, j))

@@ -25,7 +25,7 @@ from ._lib import (PYHST_BF16_SINO, PYHST_F16_SINO, PYHST_F32_RAW, PYHST_F32_SIN
                    PYHST_U16_RAW)
 
 __all__ = ["Geometry", "TvOptions", "PyhstError", "pyhst_fbp", "pyhst_filter", "pyhst_fbp_host",
-           "pyhst_profile_enable", "pyhst_profile_read", "pyhst_fbp_static", "pyhst_backproject", "pyhst_project",
+           "pyhst_profile_enable", "pyhst_profile_read", "pyhst_fbp_static", "pyhst_fbp_pre", "pyhst_backproject", "pyhst_project",
            "pyhst_tv_solve", "pyhst_tv_solve_batch", "pyhst_beta_scan", "pyhst_tv_prox", "pyhst_workspace_size", "pyhst_fbp_workspace_size", "pyhst_fbp_host_workspace_size", "pyhst_tv_workspace_size", "pyhst_last_error",
            "pyhst_version", "library_path"]
 
@@ -271,6 +271,37 @@ def pyhst_fbp_static(geom: Geometry, data: torch.Tensor, kind: str, flat=None, d
     g = geom.c(ns)
     _check(L.lib.pyhst_fbp_static(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
                                   PYHST_RAMLAK, pad_len, _ptr(out), _stream()))
+    return out
+
+
+def pyhst_fbp_pre(geom: Geometry, data: torch.Tensor, kind: str, flats: torch.Tensor, dark: torch.Tensor,
+                  flat_pos: torch.Tensor = None, hotspot_threshold: float = 0.0, ring_window: int = 0,
+                  pad_len: int = 0, out=None, workspace=None, slices_per_pass: int = 4) -> torch.Tensor:
+    """FBP with the preprocessing of Sec. 2.3: data [n_angles, n_slices,
+    n_bins] raw counts, flats [n_flats, n_slices, n_bins] (or [n_slices,
+    n_bins] for one flat), flat_pos [n_angles] (more than one flat), dark
+    [n_slices, n_bins]."""
+    code, dt = _KINDS[kind]
+    if not kind.endswith("raw"):
+        raise ValueError("pyhst_fbp_pre needs raw counts")
+    _cuda(data, "data", (dt,))
+    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, "projections")
+    flats = _cuda(flats, "flats", (torch.float32,))
+    if flats.dim() == 2:
+        flats = flats.unsqueeze(0)
+    _cuda(dark, "dark", (torch.float32,))
+    if flat_pos is not None:
+        _cuda(flat_pos, "flat_pos", (torch.float32,))
+    if out is None:
+        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    pre = L.pyhst_preproc(int(flats.shape[0]), flats.data_ptr(), flat_pos.data_ptr() if flat_pos is not None else None,
+                          float(hotspot_threshold), int(ring_window))
+    ws = _workspace(L.lib.pyhst_fbp_pre_workspace_size(ctypes.byref(g), pad_len, slices_per_pass), data.device,
+                    workspace)
+    _check(L.lib.pyhst_fbp_pre(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(dark), ctypes.byref(pre),
+                               PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), ws.numel(), _stream()))
     return out
 
 

@@ -38,6 +38,11 @@ class pyhst_tv_opts(ctypes.Structure):
                 ("n_power_iter", c_int32)]
 
 
+class pyhst_preproc(ctypes.Structure):
+    _fields_ = [("n_flats", c_int32), ("flats", c_void_p), ("flat_pos", c_void_p), ("hotspot_threshold", c_float),
+                ("ring_window", c_int32)]
+
+
 class pyhst_tv_item(ctypes.Structure):
     _fields_ = [("geom", pyhst_geometry), ("sino", c_void_p), ("x", c_void_p), ("energy", c_void_p),
                 ("beta", c_float)]
@@ -79,6 +84,10 @@ SIGNATURES = [
     ("pyhst_beta_scan", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(c_float), c_int32, c_int32,
                                   ctypes.POINTER(pyhst_tv_opts), c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                   c_void_p]),
+    ("pyhst_fbp_pre_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32]),
+    ("pyhst_fbp_pre", c_int32, [ctypes.POINTER(pyhst_geometry), c_int32, c_void_p, c_int64, c_int64, c_void_p,
+                                ctypes.POINTER(pyhst_preproc), c_int32, c_int32, c_void_p, c_void_p, c_size_t,
+                                c_void_p]),
     ("pyhst_last_error", ctypes.c_char_p, []),
     ("pyhst_version", ctypes.c_char_p, []),
 ]

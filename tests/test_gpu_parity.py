@@ -305,3 +305,50 @@ def test_fbp_shards_reassemble_the_volume(P, cuda_device):
     torch.cuda.synchronize()
     assert [p[:2] for p in parts] == [(0, 3), (3, 5), (5, 7)]
     assert torch.equal(torch.cat([p[2] for p in parts]), full)
+
+
+# ------------------------------------------------------------------ preprocessing variants (Sec. 2.3)
+def test_fbp_pre_all_off_equals_fbp(P, cuda_device):
+    vol = acq.ellipsoid_volume(n_slices=5, n=80, n_angles=60, seed=71, n_ellipsoids=30)
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
+                   cuda_device)
+    raw, fl, dk = vol.raw.to(cuda_device), vol.flat.to(cuda_device), vol.dark.to(cuda_device)
+    a = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk)
+    b = P.pyhst_fbp_pre(geo, raw, "u16_raw", fl, dk)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_fbp_pre_flats_hotspots_rings_parity(P, orc, cuda_device):
+    """Three flats interpolated in time, hot pixels (ratio jumps of ~1.5 far
+    above the 0.2 threshold, so float32 and float64 decide alike) and a
+    detector column 5 % too sensitive (a ring): the GPU path against the
+    oracle's preprocessing, filter and back-projection."""
+    ns, n, na = 6, 96, 90
+    vol = acq.ellipsoid_volume(n_slices=ns, n=n, n_angles=na, seed=72, n_ellipsoids=40)
+    raw = vol.raw.to(torch.float64)
+    scale = torch.tensor([0.97, 1.0, 1.04], dtype=torch.float64)
+    pos = torch.linspace(0, 2, na, dtype=torch.float64)
+    f0 = torch.floor(pos).clamp(max=1)
+    w = pos - f0
+    s_a = (1 - w) * scale[f0.long()] + w * scale[f0.long() + 1]          # beam drift per projection
+    F_true = vol.flat.double() - vol.dark.double()
+    counts = (raw - vol.dark.double()[None]) * s_a[:, None, None] + vol.dark.double()[None]
+    counts[:, :, 37] = (counts[:, :, 37] - vol.dark.double()[None, :, 37]) * 1.05 + vol.dark.double()[None, :, 37]
+    g = np.random.default_rng(3)
+    for _ in range(25):
+        a, z, b = int(g.integers(0, na)), int(g.integers(0, ns)), int(g.integers(1, n - 1))
+        counts[a, z, b] = counts[a, z, b] * 2.5 + 20000
+    counts = counts.round().clamp(0, 65535)
+    raw16 = counts.to(torch.int32).to(torch.uint16)
+    flats = torch.stack([vol.dark.double() + F_true * s for s in scale]).float()
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), n, n, n, vol.pixel_size, cuda_device)
+    got = P.pyhst_fbp_pre(geo, raw16.to(cuda_device), "u16_raw", flats.to(cuda_device), vol.dark.to(cuda_device),
+                          flat_pos=pos.float().to(cuda_device), hotspot_threshold=0.2, ring_window=9)
+    torch.cuda.synchronize()
+    p = orc.preprocess(raw16.double().numpy(), flats.double().numpy(), pos.float().double().numpy(),
+                       vol.dark.double().numpy(), hotspot_threshold=0.2, ring_window=9)
+    for z in range(ns):
+        ref = orc.backproject(orc.ramlak_filter(p[z]), vol.angles.double().numpy(), vol.axis.double().numpy(), n, n,
+                              orc.fbp_weight(na, vol.pixel_size))
+        close(f64(got[z]), ref)
