@@ -62,6 +62,8 @@ def parse():
                     help="mixed-precision FBP study (4096^2, 4000 angles; f32/f16/bf16 storage vs the FP64 oracle)")
     ap.add_argument("--precision-slices", type=int, default=2, help="slices checked against the oracle")
     ap.add_argument("--tv-only", action="store_true", help="only the reduced-dose TV measurement (for profilers)")
+    ap.add_argument("--pre-study", action="store_true",
+                    help="cost of the Sec. 2.3 preprocessing variants on the batched-volume geometry")
     ap.add_argument("--beta-study", action="store_true",
                     help="beta estimators (Sec. 4) on a 2048^2 foam with 150 projections vs its ground truth")
     ap.add_argument("--kernel-case", choices=["backproject", "project", "filter"],
@@ -357,6 +359,38 @@ def run_beta_study(n=2048, n_angles=150, n_iter=200, seed=5150):
         "scan_s": e0.elapsed_time(e1) * 1e-3}}), flush=True)
 
 
+# ------------------------------------------------------------------ preprocessing cost
+def run_pre_study(ns=64):
+    """pyhst_fbp against pyhst_fbp_pre (three flats interpolated in time,
+    hot-spot filter, ring filter) on 64 slices of the batched-volume geometry."""
+    import torch
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    dev = torch.device("cuda", 0)
+    vol = acq.ellipsoid_volume(n_slices=ns, n=N_PIX, n_angles=N_ANG, seed=1000, device=dev)
+    geo = P.Geometry(vol.angles.to(dev), vol.axis.to(dev), N_BINS, N_PIX, N_PIX, vol.pixel_size)
+    flats = torch.stack([vol.flat * 0.99, vol.flat, vol.flat * 1.02])
+    pos = torch.linspace(0, 2, N_ANG, device=dev)
+    out = torch.empty((ns, N_PIX, N_PIX), device=dev)
+    runs = {"fbp": lambda: P.pyhst_fbp(geo, vol.raw, "u16_raw", vol.flat, vol.dark, out=out),
+            "fbp_pre_flats": lambda: P.pyhst_fbp_pre(geo, vol.raw, "u16_raw", flats, vol.dark, flat_pos=pos, out=out),
+            "fbp_pre_all": lambda: P.pyhst_fbp_pre(geo, vol.raw, "u16_raw", flats, vol.dark, flat_pos=pos,
+                                                   hotspot_threshold=0.2, ring_window=9, out=out)}
+    res = {}
+    for k, fn in runs.items():
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[k] = {"slices_per_s": ns / (ms * 1e-3), "gupd_per_s": ns * UPD_PER_SLICE / (ms * 1e-3) / 1e9}
+    print(json.dumps({"pre_study": res, "workload": f"{ns} slices of 2048^2, 2000 angles, 2048 bins, uint16 raw"}),
+          flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -553,6 +587,9 @@ def main():
         return
     if args.precision_study:
         run_precision_study(args)
+        return
+    if args.pre_study:
+        run_pre_study()
         return
     if args.beta_study:
         run_beta_study()
