@@ -55,6 +55,7 @@ def lib():
         L.orc_energy.restype = D
         L.orc_power_iteration.restype = D
         L.orc_cosine.restype = D
+        L.orc_patch_f.restype = D
         L.orc_ecohe.restype = D
         _lib = L
     return _lib
@@ -322,3 +323,71 @@ def preprocess(I, flats, pos, D, hotspot_threshold=0.0, ring_window=0):
     if ring_window > 0:
         p = np.stack([ring(pz, ring_window) for pz in p])
     return p
+
+
+# ------------------------------------------------------------------ overlapping patches (Eqs. 4-9, Algorithm 1)
+class _PatchProb(ctypes.Structure):
+    _fields_ = [("ny", I64), ("nx", I64), ("m", I64), ("stride", I64), ("nc", I64), ("D", PD), ("rho", D),
+                ("denoise", ctypes.c_int), ("g", ctypes.c_void_p)]
+
+
+def patch_grid(ny, nx, m, stride):
+    kr, kc = I64(), I64()
+    lib().orc_patch_grid(I64(ny), I64(nx), I64(m), I64(stride), ctypes.byref(kr), ctypes.byref(kc))
+    return kr.value, kc.value
+
+
+def dct_dictionary(m):
+    Dm = np.empty((m * m, m * m))
+    lib().orc_dct_dictionary(I64(m), Dm.ctypes.data_as(PD))
+    return Dm
+
+
+def patch_assemble(P, ny, nx, m, stride):
+    P, pp = _c(P)
+    X = np.empty((ny, nx))
+    lib().orc_patch_assemble(pp, I64(ny), I64(nx), I64(m), I64(stride), X.ctypes.data_as(PD))
+    return X
+
+
+def patch_sum(P, ny, nx, m, stride):
+    P, pp = _c(P)
+    S, Nv = np.empty((ny, nx)), np.empty((ny, nx))
+    lib().orc_patch_sum(pp, I64(ny), I64(nx), I64(m), I64(stride), S.ctypes.data_as(PD), Nv.ctypes.data_as(PD))
+    return S, Nv
+
+
+class PatchProblem:
+    """Eq. 8 on an ny x nx image: patch size m, stride, dictionary Dm [nc, m*m],
+    rho; geometry g (tomography) or None (denoising, Pi = identity)."""
+
+    def __init__(self, ny, nx, m, stride, Dm, rho, g: "Geometry" = None):
+        self.Dm = np.ascontiguousarray(Dm, dtype=np.float64)
+        self.g = g
+        self._gc = g._c() if g is not None else None
+        self.s = _PatchProb(ny, nx, m, stride, self.Dm.shape[0], self.Dm.ctypes.data_as(PD), rho,
+                            1 if g is None else 0,
+                            ctypes.cast(ctypes.pointer(self._gc), ctypes.c_void_p) if g is not None else None)
+        self.kr, self.kc = patch_grid(ny, nx, m, stride)
+        self.shape_w = (self.kr * self.kc, self.Dm.shape[0])
+
+    def f(self, W, y):
+        W, pw = _c(W)
+        y, py = _c(y)
+        return lib().orc_patch_f(ctypes.byref(self.s), pw, py)
+
+    def gradient(self, W, y):
+        W, pw = _c(W)
+        y, py = _c(y)
+        G = np.empty(self.shape_w)
+        lib().orc_patch_gradient(ctypes.byref(self.s), pw, py, G.ctypes.data_as(PD))
+        return G
+
+    def fista(self, y, beta, L, n_iter, use_fista=True, W0=None):
+        y, py = _c(y)
+        W = np.zeros(self.shape_w) if W0 is None else np.array(W0, dtype=np.float64, copy=True)
+        e = np.empty(n_iter)
+        X = np.empty((self.s.ny, self.s.nx))
+        lib().orc_patch_fista(ctypes.byref(self.s), py, D(beta), D(L), I64(n_iter), ctypes.c_int(1 if use_fista else 0),
+                              W.ctypes.data_as(PD), e.ctypes.data_as(PD), X.ctypes.data_as(PD))
+        return W, e, X

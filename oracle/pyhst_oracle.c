@@ -19,7 +19,10 @@
  *   - isotropic total variation (Eq. 2) and its proximal map by Chambolle's
  *     dual fixed point (the paper cites Chambolle 2004 for isotropic TV);
  *   - ISTA / FISTA (Sec. 3.1, after Eq. 3) on 1/2 ||y - P x||^2 + beta TV(x)
- *     (Eq. 3), with the energy of Eq. 3 recorded at every iteration.
+ *     (Eq. 3), with the energy of Eq. 3 recorded at every iteration;
+ *   - the overlapping-patch functional (Sec. 3.2.1, Eqs. 4-8), its gradient
+ *     (Eq. 9) computed with the steps of Algorithm 1, and ISTA/FISTA with L1
+ *     shrinkage on the patch coefficients.
  * Readings where the paper is silent (filter form, interpolation at the
  * detector edge, clamping of non-positive counts, TV step tau, start of the
  * dual field) are stated beside each function.
@@ -517,4 +520,250 @@ void orc_ring(double *p, int64_t na, int64_t nb, int64_t window)
         for (int64_t b = 0; b < nb; b++) p[a * nb + b] -= hp[b];
     free(sm);
     free(hp);
+}
+
+/* ---------------------------------------------------------------------
+ * Overlapping-patch functional (Sec. 3.2.1, Eqs. 4-9; Algorithm 1).
+ *
+ * Patches of m x m pixels sit on a grid: along an axis of n pixels the k-th
+ * patch starts at min(k * stride, n - m), k = 0 .. K-1, K = ceil((n - m) /
+ * stride) + 1, so they cover the image (Eq. 4).  The core of a pixel (Eqs.
+ * 5-6) is the patch whose centre start + (m-1)/2 is nearest in L1; on a
+ * product grid that is the nearest centre along each axis (ties: the lower
+ * index).  Patches P [N][m*m] (row-major inside the patch, N = Kr * Kc,
+ * patch index kr * Kc + kc) come from the coefficients W [N][Nc] and the
+ * dictionary D [Nc][m*m] as P = W D; the image takes each pixel from its core
+ * patch (Eq. 7).  f(W) = ||y - Pi x||^2 + rho sum_p sum_{i in p} (x_i - P_pi)^2
+ * (Eq. 8), F = f + beta ||W||_1.  Pi is the projector (scaled by the pixel
+ * size) or the identity (denoising).
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int64_t ny, nx, m, stride, kr, kc;
+} orc_patchgrid;
+
+static int64_t pg_count(int64_t n, int64_t m, int64_t stride)
+{
+    return (n - m + stride - 1) / stride + 1;
+}
+
+static int64_t pg_start(int64_t k, int64_t n, int64_t m, int64_t stride)
+{
+    int64_t r = k * stride;
+    return r > n - m ? n - m : r;
+}
+
+static int64_t pg_core(int64_t i, int64_t n, int64_t m, int64_t stride, int64_t K)
+{
+    int64_t best = 0;
+    double bd = 1e300;
+    for (int64_t k = 0; k < K; k++) {
+        double d = fabs((double)i - ((double)pg_start(k, n, m, stride) + 0.5 * (double)(m - 1)));
+        if (d < bd) {
+            bd = d;
+            best = k;
+        }
+    }
+    return best;
+}
+
+void orc_patch_grid(int64_t ny, int64_t nx, int64_t m, int64_t stride, int64_t *kr, int64_t *kc)
+{
+    *kr = pg_count(ny, m, stride);
+    *kc = pg_count(nx, m, stride);
+}
+
+/* orthonormal 2-D DCT-II basis of m x m patches: D [m*m][m*m], row u*m+v */
+void orc_dct_dictionary(int64_t m, double *D)
+{
+    for (int64_t u = 0; u < m; u++)
+        for (int64_t v = 0; v < m; v++)
+            for (int64_t a = 0; a < m; a++)
+                for (int64_t b = 0; b < m; b++) {
+                    double au = u ? sqrt(2.0 / m) : sqrt(1.0 / m);
+                    double av = v ? sqrt(2.0 / m) : sqrt(1.0 / m);
+                    D[(u * m + v) * m * m + a * m + b] =
+                        au * av * cos(M_PI * (2 * a + 1) * u / (2.0 * m)) * cos(M_PI * (2 * b + 1) * v / (2.0 * m));
+                }
+}
+
+/* C = A B with A [r][k], B [k][c] */
+static void matmul(const double *A, const double *B, int64_t r, int64_t k, int64_t c, double *C)
+{
+    for (int64_t i = 0; i < r; i++)
+        for (int64_t j = 0; j < c; j++) {
+            double acc = 0.0;
+            for (int64_t t = 0; t < k; t++) acc += A[i * k + t] * B[t * c + j];
+            C[i * c + j] = acc;
+        }
+}
+
+/* Eq. 7: x_j = P[core(j)][j - r_core(j)] */
+void orc_patch_assemble(const double *P, int64_t ny, int64_t nx, int64_t m, int64_t stride, double *X)
+{
+    int64_t kr = pg_count(ny, m, stride), kc = pg_count(nx, m, stride);
+    for (int64_t i = 0; i < ny; i++) {
+        int64_t pr = pg_core(i, ny, m, stride, kr), ri = pg_start(pr, ny, m, stride);
+        for (int64_t j = 0; j < nx; j++) {
+            int64_t pc = pg_core(j, nx, m, stride, kc), rj = pg_start(pc, nx, m, stride);
+            X[i * nx + j] = P[(pr * kc + pc) * m * m + (i - ri) * m + (j - rj)];
+        }
+    }
+}
+
+/* S_j = sum of the patches covering j, Nv_j = their number (Algorithm 1) */
+void orc_patch_sum(const double *P, int64_t ny, int64_t nx, int64_t m, int64_t stride, double *S, double *Nv)
+{
+    int64_t kr = pg_count(ny, m, stride), kc = pg_count(nx, m, stride);
+    for (int64_t k = 0; k < ny * nx; k++) S[k] = Nv[k] = 0.0;
+    for (int64_t a = 0; a < kr; a++)
+        for (int64_t b = 0; b < kc; b++) {
+            int64_t ri = pg_start(a, ny, m, stride), rj = pg_start(b, nx, m, stride);
+            for (int64_t u = 0; u < m; u++)
+                for (int64_t v = 0; v < m; v++) {
+                    S[(ri + u) * nx + rj + v] += P[(a * kc + b) * m * m + u * m + v];
+                    Nv[(ri + u) * nx + rj + v] += 1.0;
+                }
+        }
+}
+
+typedef struct {
+    int64_t ny, nx, m, stride, nc;
+    const double *D;        /* [nc][m*m] */
+    double rho;
+    int denoise;            /* 1: Pi = identity */
+    const orc_geom *g;      /* projector geometry when denoise == 0 */
+} orc_patchprob;
+
+static void pi_apply(const orc_patchprob *q, const double *x, double *y)
+{
+    if (q->denoise) memcpy(y, x, sizeof(double) * q->ny * q->nx);
+    else P_apply(q->g, x, y);
+}
+
+static void pit_apply(const orc_patchprob *q, const double *y, double *x)
+{
+    if (q->denoise) memcpy(x, y, sizeof(double) * q->ny * q->nx);
+    else PT_apply(q->g, y, x);
+}
+
+static int64_t data_size(const orc_patchprob *q)
+{
+    return q->denoise ? q->ny * q->nx : q->g->n_angles * q->g->n_bins;
+}
+
+/* f(W) of Eq. 8 (the smooth part) */
+double orc_patch_f(const orc_patchprob *q, const double *W, const double *y)
+{
+    int64_t kr = pg_count(q->ny, q->m, q->stride), kc = pg_count(q->nx, q->m, q->stride), N = kr * kc;
+    int64_t mm = q->m * q->m, n = q->ny * q->nx, md = data_size(q);
+    double *P = (double *)malloc(sizeof(double) * N * mm);
+    double *X = (double *)malloc(sizeof(double) * n);
+    double *r = (double *)malloc(sizeof(double) * md);
+    matmul(W, q->D, N, q->nc, mm, P);
+    orc_patch_assemble(P, q->ny, q->nx, q->m, q->stride, X);
+    pi_apply(q, X, r);
+    double f = 0.0;
+    for (int64_t k = 0; k < md; k++) f += (y[k] - r[k]) * (y[k] - r[k]);
+    double pen = 0.0;
+    for (int64_t a = 0; a < kr; a++)
+        for (int64_t b = 0; b < kc; b++) {
+            int64_t ri = pg_start(a, q->ny, q->m, q->stride), rj = pg_start(b, q->nx, q->m, q->stride);
+            for (int64_t u = 0; u < q->m; u++)
+                for (int64_t v = 0; v < q->m; v++) {
+                    double d = X[(ri + u) * q->nx + rj + v] - P[(a * kc + b) * mm + u * q->m + v];
+                    pen += d * d;
+                }
+        }
+    free(P); free(X); free(r);
+    return f + q->rho * pen;
+}
+
+/* Gradient of f (Eq. 9), computed with Algorithm 1's steps:
+ *   P = W D; X from the cores; R = Pi^T (Pi X - y); S, Nv;
+ *   P'_pi = [core(r_p + i) = p] (R + rho (Nv X - S))_{r_p+i} + rho (P_pi - X_{r_p+i});
+ *   G = 2 P' D^T.
+ * Reading: R carries the sign of Eq. 9 (Pi^T (Pi x - y)); Algorithm 1 prints
+ * Bp(data - Fp(X)), the opposite sign, which is not the gradient of Eq. 8. */
+void orc_patch_gradient(const orc_patchprob *q, const double *W, const double *y, double *G)
+{
+    int64_t kr = pg_count(q->ny, q->m, q->stride), kc = pg_count(q->nx, q->m, q->stride), N = kr * kc;
+    int64_t mm = q->m * q->m, n = q->ny * q->nx, md = data_size(q);
+    double *P = (double *)malloc(sizeof(double) * N * mm);
+    double *Pp = (double *)malloc(sizeof(double) * N * mm);
+    double *X = (double *)malloc(sizeof(double) * n);
+    double *R = (double *)malloc(sizeof(double) * n);
+    double *S = (double *)malloc(sizeof(double) * n);
+    double *Nv = (double *)malloc(sizeof(double) * n);
+    double *r = (double *)malloc(sizeof(double) * md);
+    double *DT = (double *)malloc(sizeof(double) * mm * q->nc);
+    matmul(W, q->D, N, q->nc, mm, P);
+    orc_patch_assemble(P, q->ny, q->nx, q->m, q->stride, X);
+    pi_apply(q, X, r);
+    for (int64_t k = 0; k < md; k++) r[k] -= y[k];
+    pit_apply(q, r, R);
+    orc_patch_sum(P, q->ny, q->nx, q->m, q->stride, S, Nv);
+    for (int64_t a = 0; a < kr; a++)
+        for (int64_t b = 0; b < kc; b++) {
+            int64_t p = a * kc + b;
+            int64_t ri = pg_start(a, q->ny, q->m, q->stride), rj = pg_start(b, q->nx, q->m, q->stride);
+            for (int64_t u = 0; u < q->m; u++)
+                for (int64_t v = 0; v < q->m; v++) {
+                    int64_t j = (ri + u) * q->nx + rj + v;
+                    double val = q->rho * (P[p * mm + u * q->m + v] - X[j]);
+                    int64_t cr = pg_core(ri + u, q->ny, q->m, q->stride, kr);
+                    int64_t cc = pg_core(rj + v, q->nx, q->m, q->stride, kc);
+                    if (cr == a && cc == b) val += R[j] + q->rho * (Nv[j] * X[j] - S[j]);
+                    Pp[p * mm + u * q->m + v] = val;
+                }
+        }
+    for (int64_t t = 0; t < q->nc; t++)
+        for (int64_t k = 0; k < mm; k++) DT[k * q->nc + t] = q->D[t * mm + k];
+    matmul(Pp, DT, N, mm, q->nc, G);
+    for (int64_t k = 0; k < N * q->nc; k++) G[k] *= 2.0;
+    free(P); free(Pp); free(X); free(R); free(S); free(Nv); free(r); free(DT);
+}
+
+/* ISTA/FISTA on F(W) = f(W) + beta ||W||_1 (Sec. 3.2.2): a gradient step of
+ * length 1/L, then the L1 shrinkage sign(v) max(|v| - beta/L, 0); FISTA
+ * momentum as in orc_fista.  W in: start, out: last iterate; energy[k] = F at
+ * iterate k; X receives the image of the last iterate. */
+void orc_patch_fista(const orc_patchprob *q, const double *y, double beta, double L, int64_t n_iter, int fista,
+                     double *W, double *energy, double *X)
+{
+    int64_t kr = pg_count(q->ny, q->m, q->stride), kc = pg_count(q->nx, q->m, q->stride);
+    int64_t nw = kr * kc * q->nc;
+    double *Y = (double *)malloc(sizeof(double) * nw);
+    double *Wp = (double *)malloc(sizeof(double) * nw);
+    double *G = (double *)malloc(sizeof(double) * nw);
+    memcpy(Y, W, sizeof(double) * nw);
+    memcpy(Wp, W, sizeof(double) * nw);
+    double t = 1.0;
+    for (int64_t k = 0; k < n_iter; k++) {
+        orc_patch_gradient(q, Y, y, G);
+        for (int64_t e = 0; e < nw; e++) {
+            double v = Y[e] - G[e] / L;
+            double a = fabs(v) - beta / L;
+            W[e] = a > 0.0 ? (v > 0.0 ? a : -a) : 0.0;
+        }
+        double tn = fista ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
+        double w = fista ? (t - 1.0) / tn : 0.0;
+        for (int64_t e = 0; e < nw; e++) {
+            Y[e] = W[e] + w * (W[e] - Wp[e]);
+            Wp[e] = W[e];
+        }
+        t = tn;
+        if (energy) {
+            double l1 = 0.0;
+            for (int64_t e = 0; e < nw; e++) l1 += fabs(W[e]);
+            energy[k] = orc_patch_f(q, W, y) + beta * l1;
+        }
+    }
+    if (X) {
+        int64_t mm = q->m * q->m, N = kr * kc;
+        double *P = (double *)malloc(sizeof(double) * N * mm);
+        matmul(W, q->D, N, q->nc, mm, P);
+        orc_patch_assemble(P, q->ny, q->nx, q->m, q->stride, X);
+        free(P);
+    }
+    free(Y); free(Wp); free(G);
 }
