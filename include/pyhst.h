@@ -303,6 +303,40 @@ size_t pyhst_tv_batch_workspace_size(const pyhst_tv_item *items, int32_t n_items
 int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items, const pyhst_tv_opts *opts,
                          double *lipschitz_out, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Learned proximal denoiser: a residual CNN that can replace the TV prox in
+ * the FISTA loop (Sec. 3.2 introduces learned priors with the patch
+ * dictionary; the network is a convolutional learned prior).
+ *
+ *   a_0 = z;  a_l = ReLU(conv3x3(a_{l-1}; W_l) + b_l), l = 1..7;
+ *   out = z + conv3x3(a_7; W_8) + b_8
+ *
+ * Channel widths 1, 32 x 7, 1; conv3x3 is cross-correlation with zero
+ * padding.  Weights and the hidden activations a_1..a_7 are bfloat16 (round
+ * to nearest even), sums float32 (the 32 -> 32 layers on the tensor cores),
+ * z, the biases and out float32.
+ *
+ * params: DEVICE float32 [pyhst_cnn_param_count()] in the order W_1, b_1,
+ * ..., W_8, b_8 with W_l [C_out][C_in][3][3] row-major (float32 master
+ * values; the call rounds the weights to bfloat16).
+ * ------------------------------------------------------------------------ */
+int64_t pyhst_cnn_param_count(void);
+
+/* Workspace of pyhst_cnn_forward for n_images of ny x nx:
+ * two bfloat16 activation buffers (64 bytes per pixel each) + packed
+ * weights.  0 for invalid sizes. */
+size_t pyhst_cnn_workspace_size(int32_t n_images, int32_t ny, int32_t nx);
+
+/* out [n_images][ny][nx] = network(z [n_images][ny][nx]), all DEVICE
+ * float32; out may equal z.  1 <= n_images <= 65535, 1 <= ny, nx <= 16384. */
+int pyhst_cnn_forward(const float *params, const float *z, float *out, int32_t n_images, int32_t ny, int32_t nx,
+                      void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* Error bits recorded on the current device by kernels whose bounded waits
+ * gave up (1: a tensor-core completion wait), since the last clear.  Reads
+ * the word synchronously; clear != 0 resets it. */
+int pyhst_device_status(uint32_t *flags, int32_t clear);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *pyhst_last_error(void);
 

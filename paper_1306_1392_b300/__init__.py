@@ -437,6 +437,33 @@ def pyhst_beta_scan(geom: Geometry, sino: torch.Tensor, betas, opts: TvOptions, 
     return x, cv, ec
 
 
+def pyhst_cnn_param_count() -> int:
+    return int(L.lib.pyhst_cnn_param_count())
+
+
+def pyhst_cnn_forward(params: torch.Tensor, z: torch.Tensor, out=None, workspace=None):
+    """Residual CNN prox on images z [n, ny, nx] (or [ny, nx]) with the flat
+    float32 parameter vector ``params`` (device)."""
+    params = _cuda(params, "params", (torch.float32,))
+    if params.numel() != pyhst_cnn_param_count():
+        raise ValueError(f"params must hold {pyhst_cnn_param_count()} values")
+    z3 = _stack3(_cuda(z, "z", (torch.float32,)), "z")
+    n, ny, nx = z3.shape
+    if out is None:
+        out = torch.empty_like(z3)
+    _cuda(out, "out", (torch.float32,))
+    ws = _workspace(L.lib.pyhst_cnn_workspace_size(n, ny, nx), z3.device, workspace)
+    _check(L.lib.pyhst_cnn_forward(_ptr(params), _ptr(z3), _ptr(out), n, ny, nx, _ptr(ws), ws.numel(), _stream()))
+    return out.view(z.shape)
+
+
+def pyhst_device_status(clear: bool = True) -> int:
+    """Error bits recorded by kernels whose bounded waits gave up (0: none)."""
+    v = ctypes.c_uint32(0)
+    _check(L.lib.pyhst_device_status(ctypes.byref(v), 1 if clear else 0))
+    return int(v.value)
+
+
 def fbp_weight(n_angles: int, pixel_size: float) -> float:
     """pi / (n_angles * s), the FBP angular weight over 180 degrees."""
     return math.pi / (n_angles * pixel_size)

@@ -79,6 +79,11 @@ SIGNATURES = [
                                                  ctypes.POINTER(pyhst_tv_opts)]),
     ("pyhst_tv_solve_batch", c_int32, [ctypes.POINTER(pyhst_tv_item), c_int32, ctypes.POINTER(pyhst_tv_opts),
                                        c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_cnn_param_count", c_int64, []),
+    ("pyhst_cnn_workspace_size", c_size_t, [c_int32, c_int32, c_int32]),
+    ("pyhst_cnn_forward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t,
+                                    c_void_p]),
+    ("pyhst_device_status", c_int32, [ctypes.POINTER(ctypes.c_uint32), c_int32]),
     ("pyhst_beta_scan_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32,
                                                   ctypes.POINTER(pyhst_tv_opts)]),
     ("pyhst_beta_scan", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(c_float), c_int32, c_int32,

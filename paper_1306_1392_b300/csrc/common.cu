@@ -67,7 +67,31 @@ int launch_angle_table(const float *angles, const float *axis, int n_angles, Ang
     return cuda_status("angle table");
 }
 
+// Error bits recorded by kernels whose bounded waits gave up (one word per
+// device; read and cleared by pyhst_device_status).
+__device__ unsigned int g_dev_status;
+
+unsigned *device_status_ptr() {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_dev_status) != cudaSuccess) return nullptr;
+    return static_cast<unsigned *>(p);
+}
+
 }  // namespace pyhst
+
+extern "C" int pyhst_device_status(uint32_t *flags, int32_t clear) {
+    if (!flags) return pyhst::fail(PYHST_ERR_INVALID_ARG, "flags pointer is NULL");
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, pyhst::g_dev_status, sizeof(v)) != cudaSuccess)
+        return pyhst::cuda_status("reading the device status word");
+    if (clear) {
+        const unsigned z = 0;
+        if (cudaMemcpyToSymbol(pyhst::g_dev_status, &z, sizeof(z)) != cudaSuccess)
+            return pyhst::cuda_status("clearing the device status word");
+    }
+    *flags = v;
+    return PYHST_OK;
+}
 
 extern "C" const char *pyhst_last_error(void) { return pyhst::g_err; }
 

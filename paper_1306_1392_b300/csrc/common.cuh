@@ -25,6 +25,8 @@ struct __align__(16) AngleInfo {
 int fail(int code, const char *fmt, ...);   // records the message, returns code
 int cuda_status(const char *what);          // PYHST_OK or PYHST_ERR_CUDA after a launch
 int check_geometry(const pyhst_geometry *g);
+// Device address of this device's status word (kernels OR error bits into it).
+unsigned *device_status_ptr();
 
 // ----------------------------------------------------------------- workspace
 constexpr size_t kAlign = 256;
