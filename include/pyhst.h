@@ -332,6 +332,44 @@ size_t pyhst_cnn_workspace_size(int32_t n_images, int32_t ny, int32_t nx);
 int pyhst_cnn_forward(const float *params, const float *z, float *out, int32_t n_images, int32_t ny, int32_t nx,
                       void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
+/* Training.  Workspace of pyhst_cnn_grad for n_images of ny x nx (all seven
+ * hidden activations are kept: ~9 x 64 bytes per pixel). */
+size_t pyhst_cnn_train_workspace_size(int32_t n_images, int32_t ny, int32_t nx);
+
+/* Loss = mean over every pixel of the batch of (network(z) - target)^2 and
+ * its gradient grad [pyhst_cnn_param_count()] (DEVICE float32, same layout
+ * as params), by the chain rule through the bf16 network (the rounding of
+ * stored values is differentiated as the identity; gradients of the hidden
+ * pre-activations are stored as bf16).  Weight gradients are summed over
+ * pixels in a fixed order (deterministic).  loss: DEVICE float64 or NULL. */
+int pyhst_cnn_grad(const float *params, const float *z, const float *target, int32_t n_images, int32_t ny,
+                   int32_t nx, float *grad, double *loss, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* One Adam step (Kingma & Ba 2015) on count DEVICE float32 values:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  step >= 1. */
+int pyhst_cnn_adam(float *params, const float *grad, float *m, float *v, int64_t count, int32_t step, float lr,
+                   float beta1, float beta2, float eps, pyhst_stream_t stream);
+
+/* FISTA/ISTA with the learned prox (plug-and-play): pyhst_tv_solve's
+ * iteration with x_k = network(z_k) in place of the TV prox of z_k, for the
+ * n_slices slices of g.  opts: n_iter, use_fista, warm_start, lipschitz and
+ * n_power_iter are used; beta, n_inner and tau are ignored.  energy [n_slices][n_iter]
+ * (DEVICE float64, or NULL) records the data term
+ * 1/2 ||sino - P x_k||^2.  Workspace: pyhst_pnp_workspace_size. */
+size_t pyhst_pnp_workspace_size(const pyhst_geometry *g);
+int pyhst_pnp_solve(const pyhst_geometry *g, const float *sino, const float *params, const pyhst_tv_opts *opts,
+                    float *x, double *energy, double *lipschitz_out, void *workspace, size_t ws_bytes,
+                    pyhst_stream_t stream);
+
+/* pyhst_tv_solve (without energies) that also copies the prox input
+ * z_k = y_k - (1/L) P^T (P y_k - sino) of iterations capture_iters[c]
+ * (HOST array, 1-based, each in [1, n_iter]) into capture + c n_slices ny nx
+ * (DEVICE float32).  Same workspace as pyhst_tv_solve. */
+int pyhst_tv_solve_capture(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts, float *x,
+                           int32_t n_capture, const int32_t *capture_iters, float *capture, void *workspace,
+                           size_t ws_bytes, pyhst_stream_t stream);
+
 /* Error bits recorded on the current device by kernels whose bounded waits
  * gave up (1: a tensor-core completion wait), since the last clear.  Reads
  * the word synchronously; clear != 0 resets it. */

@@ -145,3 +145,25 @@ def adam_step(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     vhat = v / (1.0 - beta2 ** step)
     return params - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
+
+
+def pnp_fista(geo, sino, params, L, n_iter, use_fista=True, x0=None):
+    """FISTA/ISTA with the network as the prox (plug-and-play): the steps of
+    the oracle's FISTA on Eq. 3 (gradient step of length 1/L on
+    1/2 ||sino - P x||^2, prox, momentum of Beck-Teboulle) with
+    x_k = forward(params, z_k) in place of the TV prox.  ``geo`` is an
+    oracle Geometry.  Returns (x, data term 1/2 ||sino - P x_k||^2 per
+    iteration)."""
+    sino = np.asarray(sino, dtype=np.float64)
+    x = np.zeros((geo.ny, geo.nx)) if x0 is None else np.array(x0, dtype=np.float64)
+    y, xprev, t = x.copy(), x.copy(), 1.0
+    energy = []
+    for _ in range(n_iter):
+        z = y - geo.PT(geo.P(y) - sino) / L
+        x, _, _ = forward(params, z, rounding=True)
+        tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t)) if use_fista else 1.0
+        w = (t - 1.0) / tn if use_fista else 0.0
+        y = x + w * (x - xprev)
+        xprev, t = x.copy(), tn
+        energy.append(0.5 * np.sum((sino - geo.P(x)) ** 2))
+    return x, np.array(energy)

@@ -361,9 +361,11 @@ double orc_power_iteration(const orc_geom *g, double *v, int64_t n_it)
  * energy[k] = Eq. 3 at x_{k+1} (k = 0 .. n_iter-1).  x is overwritten with
  * the last iterate.
  * ------------------------------------------------------------------- */
-void orc_fista(const orc_geom *g, const double *sino, double beta, double L,
-               int64_t n_iter, int64_t n_inner, double tau, int fista,
-               double *x, double *energy)
+/* as orc_fista; z_last (or NULL) receives the prox input z of the last
+ * iteration, y - (1/L) P^T (P y - sino) */
+void orc_fista_z(const orc_geom *g, const double *sino, double beta, double L,
+                 int64_t n_iter, int64_t n_inner, double tau, int fista,
+                 double *x, double *energy, double *z_last)
 {
     int64_t n = g->nx * g->ny, m = g->n_angles * g->n_bins;
     double *y = (double *)malloc(sizeof(double) * n);
@@ -393,7 +395,15 @@ void orc_fista(const orc_geom *g, const double *sino, double beta, double L,
         t = tn;
         if (energy) energy[k] = orc_energy(g, sino, x, beta);
     }
+    if (z_last) memcpy(z_last, z, sizeof(double) * n);
     free(y); free(xprev); free(z); free(grad); free(p1); free(p2); free(r);
+}
+
+void orc_fista(const orc_geom *g, const double *sino, double beta, double L,
+               int64_t n_iter, int64_t n_inner, double tau, int fista,
+               double *x, double *energy)
+{
+    orc_fista_z(g, sino, beta, L, n_iter, n_inner, tau, fista, x, energy, NULL);
 }
 
 /* ---------------------------------------------------------------------

@@ -371,6 +371,50 @@ def pyhst_tv_solve(geom: Geometry, sino: torch.Tensor, opts: TvOptions, x=None, 
     return x, e, lip
 
 
+def pyhst_tv_solve_capture(geom: Geometry, sino: torch.Tensor, opts: TvOptions, capture_iters, x=None,
+                           workspace=None):
+    """pyhst_tv_solve that also returns the prox inputs z_k of the given
+    (1-based) iterations: (x [n_slices, ny, nx], z [n_capture, n_slices, ny, nx])."""
+    sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")
+    ns = sino.shape[0]
+    if tuple(sino.shape[1:]) != (geom.n_angles, geom.n_bins):
+        raise ValueError("sinogram shape does not match the geometry")
+    if x is None:
+        x = torch.zeros((ns, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    _cuda(x, "x", (torch.float32,))
+    its = list(capture_iters)
+    cap = torch.empty((len(its), ns, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    arr = (ctypes.c_int32 * max(1, len(its)))(*its)
+    g, o = geom.c(ns), opts.c()
+    ws = _workspace(L.lib.pyhst_tv_workspace_size(ctypes.byref(g), ctypes.byref(o)), sino.device, workspace)
+    _check(L.lib.pyhst_tv_solve_capture(ctypes.byref(g), _ptr(sino), ctypes.byref(o), _ptr(x), len(its), arr,
+                                        _ptr(cap), _ptr(ws), ws.numel(), _stream()))
+    return x, cap
+
+
+def pyhst_pnp_solve(geom: Geometry, sino: torch.Tensor, params: torch.Tensor, opts: TvOptions, x=None,
+                    energy: bool = True, workspace=None):
+    """FISTA/ISTA with the learned prox for each slice; returns (x, data-term
+    energy [n_slices, n_iter] float64 or None, lipschitz [n_slices])."""
+    sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")
+    params = _cuda(params, "params", (torch.float32,))
+    if params.numel() != pyhst_cnn_param_count():
+        raise ValueError(f"params must hold {pyhst_cnn_param_count()} values")
+    ns = sino.shape[0]
+    if tuple(sino.shape[1:]) != (geom.n_angles, geom.n_bins):
+        raise ValueError("sinogram shape does not match the geometry")
+    if x is None:
+        x = torch.zeros((ns, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    _cuda(x, "x", (torch.float32,))
+    e = torch.empty((ns, opts.n_iter), dtype=torch.float64, device=sino.device) if energy else None
+    lip = torch.empty((ns,), dtype=torch.float64, device=sino.device)
+    g, o = geom.c(ns), opts.c()
+    ws = _workspace(L.lib.pyhst_pnp_workspace_size(ctypes.byref(g)), sino.device, workspace)
+    _check(L.lib.pyhst_pnp_solve(ctypes.byref(g), _ptr(sino), _ptr(params), ctypes.byref(o), _ptr(x), _ptr(e),
+                                 _ptr(lip), _ptr(ws), ws.numel(), _stream()))
+    return x, e, lip
+
+
 def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0.125, out=None, workspace=None):
     """prox of lam * TV (Eq. 2) for images z [n_slices, ny, nx] (or [ny, nx])."""
     z3 = _stack3(_cuda(z, "z", (torch.float32,)), "z")
@@ -455,6 +499,36 @@ def pyhst_cnn_forward(params: torch.Tensor, z: torch.Tensor, out=None, workspace
     ws = _workspace(L.lib.pyhst_cnn_workspace_size(n, ny, nx), z3.device, workspace)
     _check(L.lib.pyhst_cnn_forward(_ptr(params), _ptr(z3), _ptr(out), n, ny, nx, _ptr(ws), ws.numel(), _stream()))
     return out.view(z.shape)
+
+
+def pyhst_cnn_grad(params: torch.Tensor, z: torch.Tensor, target: torch.Tensor, grad=None, loss=None,
+                   workspace=None):
+    """Mean squared error of the network on the batch z [n, ny, nx] against
+    target and its gradient; returns (grad [param_count] float32, loss
+    [1] float64), both on the device."""
+    params = _cuda(params, "params", (torch.float32,))
+    z3 = _stack3(_cuda(z, "z", (torch.float32,)), "z")
+    t3 = _stack3(_cuda(target, "target", (torch.float32,)), "target")
+    if t3.shape != z3.shape:
+        raise ValueError("target must have the shape of z")
+    n, ny, nx = z3.shape
+    if grad is None:
+        grad = torch.empty_like(params)
+    if loss is None:
+        loss = torch.empty((1,), dtype=torch.float64, device=z3.device)
+    ws = _workspace(L.lib.pyhst_cnn_train_workspace_size(n, ny, nx), z3.device, workspace)
+    _check(L.lib.pyhst_cnn_grad(_ptr(params), _ptr(z3), _ptr(t3), n, ny, nx, _ptr(grad), _ptr(loss), _ptr(ws),
+                                ws.numel(), _stream()))
+    return grad, loss
+
+
+def pyhst_cnn_adam(params: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
+                   lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    """One Adam step in place on params, m, v (device float32)."""
+    for t, nm in ((params, "params"), (grad, "grad"), (m, "m"), (v, "v")):
+        _cuda(t, nm, (torch.float32,))
+    _check(L.lib.pyhst_cnn_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step), float(lr),
+                                float(beta1), float(beta2), float(eps), _stream()))
 
 
 def pyhst_device_status(clear: bool = True) -> int:

@@ -84,6 +84,17 @@ SIGNATURES = [
     ("pyhst_cnn_forward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t,
                                     c_void_p]),
     ("pyhst_device_status", c_int32, [ctypes.POINTER(ctypes.c_uint32), c_int32]),
+    ("pyhst_pnp_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry)]),
+    ("pyhst_pnp_solve", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, ctypes.POINTER(pyhst_tv_opts),
+                                  c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_tv_solve_capture", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(pyhst_tv_opts),
+                                         c_void_p, c_int32, ctypes.POINTER(c_int32), c_void_p, c_void_p, c_size_t,
+                                         c_void_p]),
+    ("pyhst_cnn_train_workspace_size", c_size_t, [c_int32, c_int32, c_int32]),
+    ("pyhst_cnn_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
+                                 c_void_p, c_size_t, c_void_p]),
+    ("pyhst_cnn_adam", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_float, c_float, c_float,
+                                 c_float, c_void_p]),
     ("pyhst_beta_scan_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), c_int32, c_int32,
                                                   ctypes.POINTER(pyhst_tv_opts)]),
     ("pyhst_beta_scan", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(c_float), c_int32, c_int32,

@@ -12,6 +12,7 @@
 //                          K = 9 taps x 32 input channels in 18 steps of 16
 //   layer 8   (32 -> 1) + residual: conv_last_kernel, CUDA cores
 #include <cmath>
+#include <utility>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -36,6 +37,9 @@ constexpr int64_t kNParams = kB8 + 1;          // 56097
 constexpr int kSliceBytes = 1024;
 constexpr int kLayerBytes = 18 * kSliceBytes;
 
+// kBwd packs the weights of the input-gradient convolution instead:
+// W'[o = cin][i = cout][t] = W[cout][cin][8 - t] (transposed, 180-degree flip).
+template <bool kBwd>
 __global__ void pack_mid_kernel(const float *__restrict__ params, __nv_bfloat16 *__restrict__ packed) {
     const int l = blockIdx.y;                                    // 0 .. kMid-1
     const int i = blockIdx.x * blockDim.x + threadIdx.x;         // element within the layer
@@ -43,8 +47,10 @@ __global__ void pack_mid_kernel(const float *__restrict__ params, __nv_bfloat16 
     const int slice = i >> 9, r = i & 511;
     const int t = slice >> 1, h = slice & 1;
     const int e = r & 7, row = (r >> 3) & 7, kc = (r >> 6) & 1, ng = r >> 7;
-    const int cout = ng * 8 + row, cin = 16 * h + 8 * kc + e;
-    const float w = params[kMid0 + l * kMidStride + ((int64_t)cout * kC + cin) * 9 + t];
+    const int o = ng * 8 + row, c = 16 * h + 8 * kc + e;        // output / input channel of this conv
+    const int64_t base = kMid0 + l * kMidStride;
+    const float w = kBwd ? params[base + ((int64_t)c * kC + o) * 9 + (8 - t)]
+                         : params[base + ((int64_t)o * kC + c) * 9 + t];
     packed[(size_t)l * (kLayerBytes / 2) + i] = __float2bfloat16_rn(w);
 }
 
@@ -114,9 +120,15 @@ constexpr int kInBytes = (kR + 2) * 4 * kXS * 16;  // 49,920
 constexpr int kMidSmem = 80 * 1024;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+// Forward: out = bf16(ReLU(conv(in) + bias)).  kBwd (input gradient of a
+// layer): out = bf16(conv'(in) masked by aux > 0), where in is the gradient
+// of the layer's pre-activation, conv' uses the transposed, flipped weights
+// and aux holds the previous layer's activations (the ReLU derivative).
+template <bool kBwd>
 __global__ void __launch_bounds__(256) conv_mid_kernel(const uint4 *__restrict__ in, uint4 *__restrict__ out,
                                                        const uint4 *__restrict__ wpack,
-                                                       const float *__restrict__ bias, int H, int W,
+                                                       const float *__restrict__ bias,
+                                                       const uint4 *__restrict__ aux, int H, int W,
                                                        unsigned *__restrict__ status) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *s_in = sm;
@@ -137,7 +149,7 @@ __global__ void __launch_bounds__(256) conv_mid_kernel(const uint4 *__restrict__
         tc::cp16(s_in + (size_t)i * 16, ok ? inb + ((size_t)(y * 4 + c) * W + x) : inb, ok ? 16u : 0u);
     }
     for (int i = tid; i < kLayerBytes / 16; i += 256) tc::cp16(s_w + (size_t)i * 16, wpack + i, 16u);
-    if (tid < kC) s_bias[tid] = bias[tid];
+    if (tid < kC) s_bias[tid] = kBwd ? 0.0f : bias[tid];
     __syncwarp();
     if (warp == 0) tc::tmem_alloc(&s_tmem, kR * kC);
     if (tid == 0) tc::bar_init(&s_bar, 1);
@@ -184,11 +196,21 @@ __global__ void __launch_bounds__(256) conv_mid_kernel(const uint4 *__restrict__
             float v[32];
             tc::tmem_ld32(tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * kC), v);
             if (x < W && y < H) {
+                const size_t rowoff = ((size_t)img * H + y) * 4 * W;
+                if (kBwd) {
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + s_bias[k], 0.0f);
-                uint4 *row = out + ((size_t)img * H + y) * 4 * W;
+                    for (int c = 0; c < 4; ++c) {
+                        float a[8];
+                        unpack8(aux[rowoff + (size_t)c * W + x], a);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) row[(size_t)c * W + x] = pack8(v + 8 * c);
+                        for (int k = 0; k < 8; ++k) v[8 * c + k] = a[k] > 0.0f ? v[8 * c + k] : 0.0f;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + s_bias[k], 0.0f);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) out[rowoff + (size_t)c * W + x] = pack8(v + 8 * c);
             }
         }
     }
@@ -231,6 +253,346 @@ __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict_
     out[o] = z[o] + (acc + params[kB8]);
 }
 
+bool cnn_sizes_ok(int n, int H, int W) { return n >= 1 && n <= 65535 && H >= 1 && W >= 1 && H <= 16384 && W <= 16384; }
+
+int set_smem_attrs() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
+    if (dev >= 0 && dev < 64 && done[dev]) return PYHST_OK;
+    if (cudaFuncSetAttribute(conv_mid_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMidSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(conv_mid_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMidSmem) !=
+            cudaSuccess)
+        return cuda_status("conv_mid_kernel shared-memory attribute");
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return PYHST_OK;
+}
+
+int launch_conv_mid(bool bwd, const uint4 *in, uint4 *out, const __nv_bfloat16 *packed_layer, const float *bias,
+                    const uint4 *aux, int n, int H, int W, unsigned *status, cudaStream_t st) {
+    const dim3 grid((W + 127) / 128, (H + kR - 1) / kR, n);
+    const uint4 *wp = reinterpret_cast<const uint4 *>(packed_layer);
+    if (bwd)
+        conv_mid_kernel<true><<<grid, 256, kMidSmem, st>>>(in, out, wp, bias, aux, H, W, status);
+    else
+        conv_mid_kernel<false><<<grid, 256, kMidSmem, st>>>(in, out, wp, bias, aux, H, W, status);
+    return cuda_status("conv_mid_kernel");
+}
+
+// Forward pass.  acts: NULL (activations ping-pong between act_a and act_b)
+// or 7 buffers that keep a_1 .. a_7 for the backward pass.
+int forward_pass(const float *params, const float *z, float *out, int n, int H, int W, __nv_bfloat16 *packed,
+                 uint4 *act_a, uint4 *act_b, uint4 *const *acts, cudaStream_t st) {
+    unsigned *status = device_status_ptr();
+    if (!status) return fail(PYHST_ERR_CUDA, "device status word unavailable");
+    int rc = set_smem_attrs();
+    if (rc) return rc;
+    pack_mid_kernel<false><<<dim3((18 * 512 + 255) / 256, kMid), 256, 0, st>>>(params, packed);
+    if ((rc = cuda_status("pack_mid_kernel"))) return rc;
+    uint4 *src = acts ? acts[0] : act_a;
+    conv_first_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(z, params, src, H, W);
+    if ((rc = cuda_status("conv_first_kernel"))) return rc;
+    for (int l = 0; l < kMid; ++l) {
+        uint4 *dst = acts ? acts[l + 1] : (src == act_a ? act_b : act_a);
+        if ((rc = launch_conv_mid(false, src, dst, packed + (size_t)l * (kLayerBytes / 2),
+                                  params + kMid0 + l * kMidStride + 9 * kC * kC, nullptr, n, H, W, status, st)))
+            return rc;
+        src = dst;
+    }
+    conv_last_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(src, z, params, out, H, W);
+    return cuda_status("conv_last_kernel");
+}
+
+
+// ----------------------------------------------------------------- training
+// Mean squared error over all pixels of the batch: d = out - target,
+// dout = (2/N) d, and FP64 partial sums of d^2 per block (fixed grid).
+constexpr int kLossBlocks = 592;
+
+__device__ __forceinline__ double block_sum256(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = l < 8 ? red[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ out, const float *__restrict__ target,
+                                                   size_t N, float scale, float *__restrict__ dout,
+                                                   double *__restrict__ part) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (size_t)gridDim.x * 256) {
+        const float d = out[i] - target[i];
+        dout[i] = scale * d;
+        acc += (double)d * (double)d;
+    }
+    acc = block_sum256(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) loss_final_kernel(const double *__restrict__ part, int nb, double invN,
+                                                         double *__restrict__ loss) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) acc += part[i];
+    acc = block_sum256(acc, red);
+    if (threadIdx.x == 0) *loss = acc * invN;
+}
+
+// Gradient of the last layer's input: dA_7[p][c] = sum_{u,v} W_8[c][u][v]
+// dout[p - (u-1, v-1)], masked by a_7 > 0 (the ReLU), stored as bf16 planes.
+__global__ void __launch_bounds__(128) conv_last_bwd_kernel(const float *__restrict__ dout,
+                                                            const uint4 *__restrict__ a7,
+                                                            const float *__restrict__ params,
+                                                            uint4 *__restrict__ dz, int H, int W) {
+    __shared__ float sw[9 * kC];
+    for (int i = threadIdx.x; i < 9 * kC; i += 128) {
+        const int c = i / 9, t = i % 9;
+        sw[t * kC + c] = bf16r(params[kW8 + i]);
+    }
+    __syncthreads();
+    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, img = blockIdx.z;
+    if (x >= W) return;
+    float d[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+        d[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dout[((size_t)img * H + yy) * W + xx] : 0.0f;
+    }
+    const size_t rowoff = ((size_t)img * H + y) * 4 * W;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float a[8], o[8];
+        unpack8(a7[rowoff + (size_t)c * W + x], a);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc = fmaf(sw[t * kC + 8 * c + k], d[t], acc);
+            o[k] = a[k] > 0.0f ? acc : 0.0f;
+        }
+        dz[rowoff + (size_t)c * W + x] = pack8(o);
+    }
+}
+
+// Weight gradients are sums over every pixel of the batch.  kGradCtas CTAs
+// each accumulate the tiles blockIdx.x, blockIdx.x + kGradCtas, ... in
+// registers and write one partial row; reduce_partials adds the rows in a
+// fixed order (deterministic).  Tiles: 8 rows x 32 pixels.
+constexpr int kGradCtas = 296;
+constexpr int kTR = 8, kTC = 32;
+constexpr int kPartRow = 9 * kC * kC + kC;        // 9248: the widest layer (W then b)
+constexpr int kGradSmem = ((kTR + 2) * (kTC + 2) * kC + kTR * kTC * kC) * 4;   // 76,288 B
+
+// stage bf16 planes of rows y0-1 .. y0+kTR, pixels x0-1 .. x0+kTC (halo 1,
+// zero outside) as float32 [kTR+2][kTC+2][32]
+__device__ __forceinline__ void stage_halo(const uint4 *__restrict__ src, float *dst, int img, int y0, int x0, int H,
+                                           int W) {
+    for (int i = threadIdx.x; i < (kTR + 2) * (kTC + 2) * 4; i += blockDim.x) {
+        const int c = i & 3, px = i >> 2, rr = px / (kTC + 2), cc = px % (kTC + 2);
+        const int y = y0 - 1 + rr, x = x0 - 1 + cc;
+        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (y >= 0 && y < H && x >= 0 && x < W) unpack8(src[(((size_t)img * H + y) * 4 + c) * W + x], v);
+        float4 *d = reinterpret_cast<float4 *>(dst + px * kC + 8 * c);
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+// the tile itself (no halo) as float32 [kTR][kTC][32]
+__device__ __forceinline__ void stage_tile(const uint4 *__restrict__ src, float *dst, int img, int y0, int x0, int H,
+                                           int W) {
+    for (int i = threadIdx.x; i < kTR * kTC * 4; i += blockDim.x) {
+        const int c = i & 3, px = i >> 2, rr = px / kTC, cc = px % kTC;
+        const int y = y0 + rr, x = x0 + cc;
+        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (y < H && x < W) unpack8(src[(((size_t)img * H + y) * 4 + c) * W + x], v);
+        float4 *d = reinterpret_cast<float4 *>(dst + px * kC + 8 * c);
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+// 32 -> 32 layer: gW[o][c][t] = sum_p dz[p][o] a[p + tap t][c], gb[o] = sum_p dz[p][o].
+// Thread: input channel c = lane, output channels 4 warp .. 4 warp + 3, all 9 taps.
+__global__ void __launch_bounds__(256) wgrad_mid_kernel(const uint4 *__restrict__ dz, const uint4 *__restrict__ act,
+                                                        int n, int H, int W, float *__restrict__ part) {
+    extern __shared__ float4 smg4[];
+    float *s_a = reinterpret_cast<float *>(smg4);
+    float *s_d = s_a + (kTR + 2) * (kTC + 2) * kC;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    float acc[4][9], accb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        accb[j] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[j][t] = 0.0f;
+    }
+    const int tx = (W + kTC - 1) / kTC, ty = (H + kTR - 1) / kTR;
+    const long total = (long)n * tx * ty;
+    for (long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int img = (int)(tile / ((long)tx * ty)), rem = (int)(tile % ((long)tx * ty));
+        const int y0 = (rem / tx) * kTR, x0 = (rem % tx) * kTC;
+        __syncthreads();
+        stage_halo(act, s_a, img, y0, x0, H, W);
+        stage_tile(dz, s_d, img, y0, x0, H, W);
+        __syncthreads();
+#pragma unroll 2
+        for (int p = 0; p < kTR * kTC; ++p) {
+            const int r = p / kTC, cc = p % kTC;
+            const float4 d = *reinterpret_cast<const float4 *>(s_d + p * kC + 4 * g);
+            accb[0] += d.x;
+            accb[1] += d.y;
+            accb[2] += d.z;
+            accb[3] += d.w;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float a = s_a[((r + t / 3) * (kTC + 2) + cc + t % 3) * kC + lane];
+                acc[0][t] = fmaf(d.x, a, acc[0][t]);
+                acc[1][t] = fmaf(d.y, a, acc[1][t]);
+                acc[2][t] = fmaf(d.z, a, acc[2][t]);
+                acc[3][t] = fmaf(d.w, a, acc[3][t]);
+            }
+        }
+    }
+    float *row = part + (size_t)blockIdx.x * kPartRow;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int o = 4 * g + j;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) row[(o * kC + lane) * 9 + t] = acc[j][t];
+        if (lane == 0) row[9 * kC * kC + o] = accb[j];
+    }
+}
+
+// First layer: gW_1[c][t] = sum_p dz_1[p][c] z[p + tap t], gb_1[c] = sum_p dz_1[p][c].
+// Last layer: gW_8[c][t] = sum_p dout[p] a_7[p + tap t][c], gb_8 = sum_p dout[p].
+// Thread: channel c = lane, tap t = warp (9 warps).
+template <bool kLast>
+__global__ void __launch_bounds__(288) wgrad_edge_kernel(const uint4 *__restrict__ planes, const float *__restrict__ img1,
+                                                         int n, int H, int W, float *__restrict__ part) {
+    extern __shared__ float4 smg4[];
+    float *s_p = reinterpret_cast<float *>(smg4);                  // planes: halo (last) or tile (first)
+    float *s_1 = s_p + (kTR + 2) * (kTC + 2) * kC;                 // one-channel image: tile (last) or halo (first)
+    const int c = threadIdx.x & 31, t = threadIdx.x >> 5, u = t / 3, v = t % 3;
+    float acc = 0.0f, accb = 0.0f;
+    const int tx = (W + kTC - 1) / kTC, ty = (H + kTR - 1) / kTR;
+    const long total = (long)n * tx * ty;
+    for (long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int im = (int)(tile / ((long)tx * ty)), rem = (int)(tile % ((long)tx * ty));
+        const int y0 = (rem / tx) * kTR, x0 = (rem % tx) * kTC;
+        __syncthreads();
+        if (kLast) {
+            stage_halo(planes, s_p, im, y0, x0, H, W);
+            for (int i = threadIdx.x; i < kTR * kTC; i += blockDim.x) {
+                const int y = y0 + i / kTC, x = x0 + i % kTC;
+                s_1[i] = (y < H && x < W) ? img1[((size_t)im * H + y) * W + x] : 0.0f;
+            }
+        } else {
+            stage_tile(planes, s_p, im, y0, x0, H, W);
+            for (int i = threadIdx.x; i < (kTR + 2) * (kTC + 2); i += blockDim.x) {
+                const int y = y0 - 1 + i / (kTC + 2), x = x0 - 1 + i % (kTC + 2);
+                s_1[i] = (y >= 0 && y < H && x >= 0 && x < W) ? img1[((size_t)im * H + y) * W + x] : 0.0f;
+            }
+        }
+        __syncthreads();
+        for (int p = 0; p < kTR * kTC; ++p) {
+            const int r = p / kTC, cc = p % kTC;
+            const int h = (r + u) * (kTC + 2) + cc + v;               // halo index of p + tap
+            if (kLast) {
+                const float d = s_1[p];
+                acc = fmaf(d, s_p[h * kC + c], acc);
+                accb += d;
+            } else {
+                const float d = s_p[p * kC + c];
+                acc = fmaf(d, s_1[h], acc);
+                accb += d;
+            }
+        }
+    }
+    float *row = part + (size_t)blockIdx.x * kPartRow;
+    row[c * 9 + t] = acc;
+    if (t == 0) {
+        if (kLast) {
+            if (c == 0) row[9 * kC] = accb;
+        } else {
+            row[9 * kC + c] = accb;
+        }
+    }
+}
+
+// grad[j] = sum over the partial rows b = 0 .. nb-1 of part[b][j], in order.
+__global__ void reduce_partials_kernel(const float *__restrict__ part, int nb, int len, float *__restrict__ grad) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += part[(size_t)b * kPartRow + j];
+    grad[j] = (float)acc;
+}
+
+// Adam (Kingma & Ba 2015): c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t).
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+struct TrainLayout {
+    size_t packed_f, packed_b, acts[7], dz[2], out, dout, part, loss_part, bytes;
+};
+
+TrainLayout train_layout(int n, int H, int W) {
+    TrainLayout l{};
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
+    const size_t act = (size_t)n * H * W * 64, img = (size_t)n * H * W * 4;
+    l.packed_f = take((size_t)kMid * kLayerBytes);
+    l.packed_b = take((size_t)kMid * kLayerBytes);
+    for (auto &a : l.acts) a = take(act);
+    for (auto &d : l.dz) d = take(act);
+    l.out = take(img);
+    l.dout = take(img);
+    l.part = take((size_t)kGradCtas * kPartRow * sizeof(float));
+    l.loss_part = take(kLossBlocks * sizeof(double));
+    l.bytes = off;
+    return l;
+}
+
+int set_grad_attrs() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
+    if (dev >= 0 && dev < 64 && done[dev]) return PYHST_OK;
+    if (cudaFuncSetAttribute(wgrad_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGradSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(wgrad_edge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGradSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(wgrad_edge_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGradSmem) !=
+            cudaSuccess)
+        return cuda_status("weight-gradient shared-memory attribute");
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return PYHST_OK;
+}
+
+int reduce_into(const float *part, int len, float *grad, cudaStream_t st) {
+    reduce_partials_kernel<<<(len + 255) / 256, 256, 0, st>>>(part, kGradCtas, len, grad);
+    return cuda_status("reduce_partials_kernel");
+}
+
 struct CnnLayout {
     size_t packed, act0, act1, bytes;
 };
@@ -247,43 +609,64 @@ CnnLayout cnn_layout(int n, int H, int W) {
     return l;
 }
 
-bool cnn_sizes_ok(int n, int H, int W) { return n >= 1 && n <= 65535 && H >= 1 && W >= 1 && H <= 16384 && W <= 16384; }
-
 }  // namespace
 
 int cnn_forward(const float *params, const float *z, float *out, int n, int H, int W, void *ws, cudaStream_t st) {
     const CnnLayout L = cnn_layout(n, H, W);
     char *base = static_cast<char *>(ws);
-    __nv_bfloat16 *packed = reinterpret_cast<__nv_bfloat16 *>(base + L.packed);
-    uint4 *a0 = reinterpret_cast<uint4 *>(base + L.act0), *a1 = reinterpret_cast<uint4 *>(base + L.act1);
+    return forward_pass(params, z, out, n, H, W, reinterpret_cast<__nv_bfloat16 *>(base + L.packed),
+                        reinterpret_cast<uint4 *>(base + L.act0), reinterpret_cast<uint4 *>(base + L.act1), nullptr,
+                        st);
+}
+
+int cnn_grad(const float *params, const float *z, const float *target, int n, int H, int W, float *grad,
+             double *loss, void *ws, cudaStream_t st) {
+    const TrainLayout L = train_layout(n, H, W);
+    char *base = static_cast<char *>(ws);
+    auto P = [&](size_t o) { return reinterpret_cast<uint4 *>(base + o); };
+    __nv_bfloat16 *packed_f = reinterpret_cast<__nv_bfloat16 *>(base + L.packed_f);
+    __nv_bfloat16 *packed_b = reinterpret_cast<__nv_bfloat16 *>(base + L.packed_b);
+    uint4 *acts[7];
+    for (int i = 0; i < 7; ++i) acts[i] = P(L.acts[i]);
+    float *out = reinterpret_cast<float *>(base + L.out), *dout = reinterpret_cast<float *>(base + L.dout);
+    float *part = reinterpret_cast<float *>(base + L.part);
+    double *lpart = reinterpret_cast<double *>(base + L.loss_part);
     unsigned *status = device_status_ptr();
     if (!status) return fail(PYHST_ERR_CUDA, "device status word unavailable");
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(conv_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMidSmem) != cudaSuccess)
-            return cuda_status("conv_mid_kernel shared-memory attribute");
-        attr_set[dev] = true;
-    }
-    pack_mid_kernel<<<dim3((18 * 512 + 255) / 256, kMid), 256, 0, st>>>(params, packed);
-    int rc = cuda_status("pack_mid_kernel");
+    int rc = set_grad_attrs();
     if (rc) return rc;
-    conv_first_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(z, params, a0, H, W);
-    if ((rc = cuda_status("conv_first_kernel"))) return rc;
-    uint4 *src = a0, *dst = a1;
-    for (int l = 0; l < kMid; ++l) {
-        conv_mid_kernel<<<dim3((W + 127) / 128, (H + kR - 1) / kR, n), 256, kMidSmem, st>>>(
-            src, dst, reinterpret_cast<const uint4 *>(packed + (size_t)l * (kLayerBytes / 2)),
-            params + kMid0 + l * kMidStride + 9 * kC * kC, H, W, status);
-        if ((rc = cuda_status("conv_mid_kernel"))) return rc;
-        uint4 *t = src;
-        src = dst;
-        dst = t;
+
+    if ((rc = forward_pass(params, z, out, n, H, W, packed_f, nullptr, nullptr, acts, st))) return rc;
+    const size_t N = (size_t)n * H * W;
+    loss_kernel<<<kLossBlocks, 256, 0, st>>>(out, target, N, (float)(2.0 / (double)N), dout, lpart);
+    if (loss) loss_final_kernel<<<1, 256, 0, st>>>(lpart, kLossBlocks, 1.0 / (double)N, loss);
+    pack_mid_kernel<true><<<dim3((18 * 512 + 255) / 256, kMid), 256, 0, st>>>(params, packed_b);
+    if ((rc = cuda_status("loss / packing kernels"))) return rc;
+
+    // layer 8
+    wgrad_edge_kernel<true><<<kGradCtas, 288, kGradSmem, st>>>(acts[6], dout, n, H, W, part);
+    if ((rc = cuda_status("wgrad_edge_kernel (last)"))) return rc;
+    if ((rc = reduce_into(part, 9 * kC + 1, grad + kW8, st))) return rc;
+    uint4 *dzc = P(L.dz[0]), *dzn = P(L.dz[1]);
+    conv_last_bwd_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(dout, acts[6], params, dzc, H, W);
+    if ((rc = cuda_status("conv_last_bwd_kernel"))) return rc;
+    // layers 7 .. 2 (mid index l: input a_{l+1} = acts[l])
+    for (int l = kMid - 1; l >= 0; --l) {
+        wgrad_mid_kernel<<<kGradCtas, 256, kGradSmem, st>>>(dzc, acts[l], n, H, W, part);
+        if ((rc = cuda_status("wgrad_mid_kernel"))) return rc;
+        if ((rc = reduce_into(part, kPartRow, grad + kMid0 + l * kMidStride, st))) return rc;
+        if ((rc = launch_conv_mid(true, dzc, dzn, packed_b + (size_t)l * (kLayerBytes / 2), nullptr, acts[l], n, H, W,
+                                  status, st)))
+            return rc;
+        std::swap(dzc, dzn);
     }
-    conv_last_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(src, z, params, out, H, W);
-    return cuda_status("conv_last_kernel");
+    // layer 1
+    wgrad_edge_kernel<false><<<kGradCtas, 288, kGradSmem, st>>>(dzc, z, n, H, W, part);
+    if ((rc = cuda_status("wgrad_edge_kernel (first)"))) return rc;
+    return reduce_into(part, 9 * kC + kC, grad + kW1, st);
 }
+
+size_t cnn_train_workspace_size(int n, int H, int W) { return cnn_sizes_ok(n, H, W) ? train_layout(n, H, W).bytes : 0; }
 
 size_t cnn_workspace_size(int n, int H, int W) { return cnn_sizes_ok(n, H, W) ? cnn_layout(n, H, W).bytes : 0; }
 
@@ -306,4 +689,32 @@ extern "C" int pyhst_cnn_forward(const float *params, const float *z, float *out
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
         return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
     return cnn_forward(params, z, out, n_images, ny, nx, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t pyhst_cnn_train_workspace_size(int32_t n_images, int32_t ny, int32_t nx) {
+    return cnn_train_workspace_size(n_images, ny, nx);
+}
+
+extern "C" int pyhst_cnn_grad(const float *params, const float *z, const float *target, int32_t n_images, int32_t ny,
+                              int32_t nx, float *grad, double *loss, void *workspace, size_t ws_bytes,
+                              pyhst_stream_t stream) {
+    if (!params || !z || !target || !grad) return fail(PYHST_ERR_INVALID_ARG, "params/z/target/grad pointer is NULL");
+    if (!cnn_sizes_ok(n_images, ny, nx))
+        return fail(PYHST_ERR_INVALID_ARG, "sizes %d x %d x %d outside [1, 65535] x [1, 16384]^2", n_images, ny, nx);
+    const size_t need = cnn_train_workspace_size(n_images, ny, nx);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    return cnn_grad(params, z, target, n_images, ny, nx, grad, loss, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pyhst_cnn_adam(float *params, const float *grad, float *m, float *v, int64_t count, int32_t step,
+                              float lr, float beta1, float beta2, float eps, pyhst_stream_t stream) {
+    if (!params || !grad || !m || !v) return fail(PYHST_ERR_INVALID_ARG, "params/grad/m/v pointer is NULL");
+    if (count < 1 || step < 1) return fail(PYHST_ERR_INVALID_ARG, "count and step must be >= 1");
+    if (!(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(PYHST_ERR_INVALID_ARG, "need lr > 0, 0 <= beta1, beta2 < 1, eps > 0");
+    const double c1 = 1.0 / (1.0 - std::pow((double)beta1, step)), c2 = 1.0 / (1.0 - std::pow((double)beta2, step));
+    adam_kernel<<<(unsigned)((count + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        params, grad, m, v, count, lr, beta1, beta2, eps, (float)c1, (float)c2);
+    return cuda_status("adam_kernel");
 }

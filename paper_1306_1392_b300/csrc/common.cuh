@@ -25,6 +25,10 @@ struct __align__(16) AngleInfo {
 int fail(int code, const char *fmt, ...);   // records the message, returns code
 int cuda_status(const char *what);          // PYHST_OK or PYHST_ERR_CUDA after a launch
 int check_geometry(const pyhst_geometry *g);
+// Residual CNN prox (cnn.cu): out = network(z) for n images of H x W.
+int cnn_forward(const float *params, const float *z, float *out, int n, int H, int W, void *ws, cudaStream_t st);
+size_t cnn_workspace_size(int n, int H, int W);
+
 // Device address of this device's status word (kernels OR error bits into it).
 unsigned *device_status_ptr();
 

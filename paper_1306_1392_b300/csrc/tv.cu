@@ -272,9 +272,20 @@ int check_tv_opts(const pyhst_tv_opts *o) {
     return PYHST_OK;
 }
 
+// Optional changes to the iteration: a learned prox in place of the TV prox
+// (the residual CNN of cnn.cu), and copies of the prox input z at chosen
+// iterations.
+struct SolveHooks {
+    const float *cnn_params = nullptr;     // non-NULL: x_k = CNN(z_k)
+    void *cnn_ws = nullptr;
+    int n_capture = 0;
+    const int32_t *capture_iters = nullptr; // host, 1-based iteration numbers
+    float *capture = nullptr;              // [n_capture][n_slices][ny][nx]
+};
+
 // Enqueue the whole solve on `st`.
 int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *o, float *x,
-                     double *energy, double *lip_out, void *ws, cudaStream_t st) {
+                     double *energy, double *lip_out, void *ws, cudaStream_t st, const SolveHooks &hk = SolveHooks()) {
     int rc;
     Bufs B = carve(g, ws);
     const int S = g->n_slices;
@@ -330,8 +341,13 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
         // gradient step: z = y - (1/L) P^T (P y - sino)
         if ((rc = launch_backproject(g, B.tab, BpSource{Ay, sino}, gr, s, st))) return rc;
         grad_step_kernel<<<eg, kRedThreads, 0, st>>>(y, gr, B.sc.invL, z, N);
-        // prox of (beta/L) TV
-        if (o->beta > 0.0f) {
+        for (int c = 0; c < hk.n_capture; ++c)
+            if (hk.capture_iters[c] == k + 1)
+                cudaMemcpyAsync(hk.capture + (size_t)c * N * S, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
+        // prox of (beta/L) TV, or the learned prox
+        if (hk.cnn_params) {
+            if ((rc = cnn_forward(hk.cnn_params, z, xn, S, g->ny, g->nx, hk.cnn_ws, st))) return rc;
+        } else if (o->beta > 0.0f) {
             bool fa;
             if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, B.sc.lam, o->tau, g->nx, g->ny, S, o->n_inner, &fa, st)))
                 return rc;
@@ -426,4 +442,66 @@ extern "C" int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_s
         return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
     return tv_prox_enqueue(z, nx, ny, n_slices, lam, n_inner, tau, x, workspace,
                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pyhst_tv_solve_capture(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts, float *x,
+                                      int32_t n_capture, const int32_t *capture_iters, float *capture,
+                                      void *workspace, size_t ws_bytes, pyhst_stream_t stream) {
+    using namespace pyhst;
+    int rc = check_geometry(g);
+    if (rc) return rc;
+    if ((rc = check_tv_opts(opts))) return rc;
+    if (!sino || !x) return fail(PYHST_ERR_INVALID_ARG, "sino/x pointer is NULL");
+    if (n_capture < 0 || (n_capture > 0 && (!capture_iters || !capture)))
+        return fail(PYHST_ERR_INVALID_ARG, "captures need iteration numbers and an output buffer");
+    for (int c = 0; c < n_capture; ++c)
+        if (capture_iters[c] < 1 || capture_iters[c] > opts->n_iter)
+            return fail(PYHST_ERR_INVALID_ARG, "capture iteration %d outside [1, n_iter]", capture_iters[c]);
+    const size_t need = tv_workspace_bytes(g, opts);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    SolveHooks hk;
+    hk.n_capture = n_capture;
+    hk.capture_iters = capture_iters;
+    hk.capture = capture;
+    return tv_solve_enqueue(g, sino, opts, x, nullptr, nullptr, workspace, reinterpret_cast<cudaStream_t>(stream), hk);
+}
+
+namespace {
+pyhst_tv_opts pnp_opts(const pyhst_tv_opts *o) {
+    pyhst_tv_opts r = *o;
+    r.beta = 0.0f;          // no functional: the energy is the data term 1/2 ||sino - P x||^2
+    r.n_inner = 1;
+    r.tau = 0.125f;
+    return r;
+}
+}  // namespace
+
+extern "C" size_t pyhst_pnp_workspace_size(const pyhst_geometry *g) {
+    using namespace pyhst;
+    if (!g || g->n_angles < 1 || g->n_bins < 1 || g->nx < 1 || g->ny < 1 || g->n_slices < 1) return 0;
+    const size_t c = cnn_workspace_size(g->n_slices, g->ny, g->nx);
+    if (!c) return 0;
+    return align_up(tv_workspace_bytes(g, nullptr)) + c;
+}
+
+extern "C" int pyhst_pnp_solve(const pyhst_geometry *g, const float *sino, const float *params,
+                               const pyhst_tv_opts *opts, float *x, double *energy, double *lipschitz_out,
+                               void *workspace, size_t ws_bytes, pyhst_stream_t stream) {
+    using namespace pyhst;
+    int rc = check_geometry(g);
+    if (rc) return rc;
+    if (!opts) return fail(PYHST_ERR_INVALID_ARG, "options are NULL");
+    const pyhst_tv_opts o = pnp_opts(opts);
+    if ((rc = check_tv_opts(&o))) return rc;
+    if (!sino || !x || !params) return fail(PYHST_ERR_INVALID_ARG, "sino/x/params pointer is NULL");
+    if (g->n_slices > 65535) return fail(PYHST_ERR_INVALID_ARG, "n_slices %d > 65535", g->n_slices);
+    const size_t need = pyhst_pnp_workspace_size(g);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    SolveHooks hk;
+    hk.cnn_params = params;
+    hk.cnn_ws = static_cast<char *>(workspace) + align_up(tv_workspace_bytes(g, nullptr));
+    return tv_solve_enqueue(g, sino, &o, x, energy, lipschitz_out, workspace, reinterpret_cast<cudaStream_t>(stream),
+                            hk);
 }

@@ -189,6 +189,28 @@ def foam_slice(n: int, n_angles: int, seed: int, photons: float = 1e4, device="c
     return sl
 
 
+def ellipse_slice(n: int, n_angles: int, seed: int, photons: float = 1e4, n_ellipses: int = 12, device="cpu",
+                  truth: bool = True, dtype=None) -> Slice:
+    """Reduced-dose slice of ``n_ellipses`` random additive ellipses (the
+    ellipse counterpart of foam_slice): exact line integrals, Poisson counts
+    at ``photons`` per bin, pre-normalised sinogram (float32)."""
+    device = torch.device(device)
+    dtype = dtype or (torch.float64 if device.type == "cpu" else torch.float32)
+    s = 2.0 / n
+    ang = uniform_angles(n_angles)
+    ax = torch.full((n_angles,), (n - 1) / 2.0, dtype=torch.float32)
+    ell = ph.random_ellipses(n_ellipses, seed).to(device=device, dtype=dtype)
+    p = ph.ellipse_sinogram(ell, ang.to(dtype=dtype, device=device),
+                            bin_offsets(ang, ax, n, s, dtype=dtype, device=device))
+    gen = torch.Generator(device=device).manual_seed(seed)
+    I = torch.poisson(photons * torch.exp(-p), generator=gen)
+    sino = -torch.log(torch.clamp(I, min=1.0) / photons)
+    sl = Slice(ang, ax, n, n, n, s, p=p,
+               truth=ph.ellipse_image(ell, n, n, s, ss=4, device=device) if truth else None)
+    sl.extra.update(sino=sino.to(torch.float32))
+    return sl
+
+
 def mixed_tv_batch_plan(n_slices: int = 128, seed: int = 3000):
     """Sizes of the reduced-dose batch: 256^2/512^2/1024^2 with 50/100/200
     angles (one tenth of the detector width), split 43/43/42 and shuffled."""

@@ -118,6 +118,18 @@ def ellipse_image(ell: Ellipses, nx: int, ny: int, s: float, ss: int = 1,
     return _box_mean(img, ss)
 
 
+def random_ellipses(n: int, seed: int, r_centres: float = 0.7, axes=(0.05, 0.4), density=(0.1, 0.6),
+                    dtype=torch.float64) -> Ellipses:
+    """``n`` ellipses with centres uniform in the disk r <= r_centres,
+    semi-axes U(axes), orientations U(0, pi) and densities U(density)
+    (additive where they overlap)."""
+    g = np.random.default_rng(seed)
+    rad = r_centres * np.sqrt(g.uniform(0, 1, n))
+    ang = g.uniform(0, 2 * np.pi, n)
+    return Ellipses.from_axes(rad * np.cos(ang), rad * np.sin(ang), g.uniform(*axes, n), g.uniform(*axes, n),
+                              g.uniform(0, np.pi, n), g.uniform(*density, n), dtype=dtype)
+
+
 def head_phantom(seed: int, dtype=torch.float64) -> Ellipses:
     """A seeded 10-ellipse head-like phantom on [-1,1]^2: a dense outer shell,
     a lower-density interior and eight small low-contrast features inside it.

@@ -120,3 +120,105 @@ def test_forward_rejects_bad_arguments():
     assert L.lib.pyhst_cnn_forward(p.data_ptr(), z.data_ptr(), z.data_ptr(), 0, 8, 8, None, 0, None) == -1
     ws = torch.empty(16, dtype=torch.uint8, device=dev)
     assert L.lib.pyhst_cnn_forward(p.data_ptr(), z.data_ptr(), z.data_ptr(), 1, 8, 8, ws.data_ptr(), 16, None) == -3
+
+
+def _layer_slices():
+    k, out = 0, []
+    for ws, bs in cnn.param_shapes():
+        nw, nb = int(np.prod(ws)), bs[0]
+        out.append(slice(k, k + nw + nb))
+        k += nw + nb
+    return out
+
+
+def test_gradient_matches_oracle_chain_rule():
+    """Batch of two 24 x 40 images (ragged against the 8 x 32 gradient
+    tiles and the 128-pixel convolution strips).  The GPU keeps the gradients
+    of hidden pre-activations in bf16 (2^-9 relative rounding each) and sums
+    in float32; the oracle differentiates the same bf16 network in FP64.
+    Bound per layer: relative L2 <= 2e-2 and cosine >= 0.999; a wrong tap,
+    channel or transpose would give an O(1) error."""
+    import paper_1306_1392_b300 as P
+    params = _dense_params(11)
+    g = np.random.default_rng(12)
+    n, h, w = 2, 24, 40
+    yy, xx = np.mgrid[0:h, 0:w]
+    z = (0.5 + 0.3 * np.sin(xx / 5.0) * np.cos(yy / 4.0) + 0.05 * g.standard_normal((n, h, w))).astype(np.float32)
+    t = (z + 0.1 * g.standard_normal((n, h, w))).astype(np.float32)
+    dev = torch.device("cuda:0")
+    grad, loss = P.pyhst_cnn_grad(torch.from_numpy(params).to(dev), torch.from_numpy(z).to(dev),
+                                  torch.from_numpy(t).to(dev))
+    torch.cuda.synchronize()
+    assert P.pyhst_device_status() == 0
+    grad = grad.cpu().numpy().astype(np.float64)
+    ref_l, ref_g = 0.0, np.zeros(params.size)
+    for i in range(n):
+        li, gi = cnn.loss_and_grad(params, z[i], t[i], rounding=True)
+        ref_l += li / n
+        ref_g += gi / n
+    assert loss.item() == pytest.approx(ref_l, rel=2e-3)
+    for sl in _layer_slices():
+        a, b = grad[sl], ref_g[sl]
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b), sl
+        assert np.vdot(a, b) >= 0.999 * np.linalg.norm(a) * np.linalg.norm(b), sl
+
+
+def test_adam_matches_oracle_and_descends():
+    import paper_1306_1392_b300 as P
+    dev = torch.device("cuda:0")
+    g = np.random.default_rng(13)
+    npar = P.pyhst_cnn_param_count()
+    p0 = g.standard_normal(npar).astype(np.float32)
+    gr = g.standard_normal(npar).astype(np.float32)
+    m0 = (0.1 * g.standard_normal(npar)).astype(np.float32)
+    v0 = (0.01 * g.uniform(0, 1, npar)).astype(np.float32)
+    pt, mt, vt = (torch.from_numpy(a.copy()).to(dev) for a in (p0, m0, v0))
+    P.pyhst_cnn_adam(pt, torch.from_numpy(gr).to(dev), mt, vt, 3, 1e-3)
+    # the kernel computes with the float32 values of lr, beta1, beta2, eps; the
+    # oracle takes the same values and sums exactly
+    f = lambda a: float(np.float32(a))
+    rp, rm, rv = cnn.adam_step(p0.astype(np.float64), gr.astype(np.float64), m0.astype(np.float64),
+                               v0.astype(np.float64), 3, f(1e-3), f(0.9), f(0.999), f(1e-8))
+    # two-term float32 sums: within a few units of 2^-24 of the operands
+    ulp = 2.0 ** -24
+    b1, b2 = f(0.9), f(0.999)
+    assert np.all(np.abs(mt.cpu().numpy() - rm) <= 4 * ulp * (b1 * np.abs(m0) + (1 - b1) * np.abs(gr)))
+    assert np.all(np.abs(vt.cpu().numpy() - rv) <= 4 * ulp * (b2 * v0 + (1 - b2) * gr.astype(np.float64) ** 2))
+    # the new parameter: one float32 rounding of p plus 1e-4 of the step
+    assert np.all(np.abs(pt.cpu().numpy() - rp) <= 2.0 ** -23 * np.abs(p0) + 1e-4 * np.abs(rp - p0))
+    # a few steps on one batch lower its loss
+    params = torch.from_numpy(init_params(3)).to(dev)
+    z = torch.rand((2, 32, 48), device=dev)
+    t = z + 0.1 * torch.sin(torch.arange(48, device=dev) / 3.0)
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    losses = []
+    for k in range(1, 21):
+        grad, loss = P.pyhst_cnn_grad(params, z, t)
+        losses.append(loss.item())
+        P.pyhst_cnn_adam(params, grad, m, v, k, 1e-3)
+    assert losses[-1] < 0.9 * losses[0]
+
+
+def test_pnp_solve_matches_oracle():
+    """FISTA with the network as prox, 3 iterations on a 48^2 foam with 16
+    angles, against the oracle's plug-and-play FISTA with the same L.  The
+    network's bf16 rounding flips (see the dense test) are the only source of
+    difference beyond float32 rounding: bound 5e-3 relative L2."""
+    import oracle as orc
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    dev = torch.device("cuda:0")
+    fs = acq.foam_slice(48, 16, seed=9, truth=False)
+    geo = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), fs.n_bins, fs.nx, fs.ny, fs.pixel_size)
+    og = orc.Geometry(fs.angles.double().numpy(), fs.axis.double().numpy(), fs.n_bins, fs.nx, fs.ny, fs.pixel_size)
+    L = 1.01 * orc.power_iteration(og, np.ones((fs.ny, fs.nx)), 30)[0]
+    params = init_params(21)
+    sino = fs.extra["sino"]
+    x, e, lip = P.pyhst_pnp_solve(geo, sino.to(dev), torch.from_numpy(params).to(dev),
+                                  P.TvOptions(beta=0.0, n_iter=3, lipschitz=L))
+    torch.cuda.synchronize()
+    assert P.pyhst_device_status() == 0
+    xr, er = cnn.pnp_fista(og, sino.double().numpy(), params, L, 3)
+    xg = x[0].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - xr) <= 5e-3 * np.linalg.norm(xr)
+    np.testing.assert_allclose(e[0].cpu().numpy(), er, rtol=1e-2)

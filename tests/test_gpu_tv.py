@@ -229,3 +229,19 @@ def test_beta_scan_estimators_parity(P, orc, cuda_device, held_out):
     ec_ref = [orc.ecohe(im, imgs[0]) for im in imgs]
     assert math.isnan(ec[0].item()) and math.isnan(ec_ref[0])
     np.testing.assert_allclose(ec.cpu().numpy()[1:], ec_ref[1:], atol=2e-4)
+
+
+def test_tv_solve_capture_matches_oracle_prox_inputs(P, orc, cuda_device):
+    """The captured prox inputs z_k of iterations 1, 4 and 9 equal the
+    oracle's (FISTA stopped after k iterations returns its last z), and the
+    run's iterate equals the plain solve's bit for bit."""
+    fs, geo, og = _foam_problem(P, orc, cuda_device, n=48, na=16, seed=5)
+    L = 1.01 * orc.power_iteration(og, np.ones((fs.ny, fs.nx)), 30)[0]
+    sino = fs.extra["sino"]
+    opts = P.TvOptions(beta=2e-3, n_iter=9, n_inner=20, lipschitz=L)
+    x, cap = P.pyhst_tv_solve_capture(geo, sino.to(cuda_device), opts, [1, 4, 9])
+    x1, _, _ = P.pyhst_tv_solve(geo, sino.to(cuda_device), opts, energy=False)
+    assert torch.equal(x, x1)
+    for c, k in enumerate((1, 4, 9)):
+        _, _, zr = orc.fista(og, sino.double().numpy(), 2e-3, L, k, n_inner=20, return_z=True)
+        assert rel(cap[c, 0].cpu().numpy(), zr) <= 1e-4

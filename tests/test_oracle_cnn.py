@@ -117,3 +117,38 @@ def test_adam_first_step_closed_form():
 
 def test_param_count():
     assert cnn.n_params() == 9 * 32 + 32 + 6 * (9 * 32 * 32 + 32) + 9 * 32 + 1 == init_params(0).size
+
+
+def test_pnp_with_identity_network_is_fista_without_penalty():
+    """A network whose residual branch is zero returns float32(z): the
+    plug-and-play loop is then FISTA on Eq. 3 with beta = 0 (whose prox is
+    the identity), up to that float32 rounding."""
+    import math
+    import oracle as orc
+    n, na, nb = 12, 9, 16
+    geo = orc.Geometry(np.arange(na) * math.pi / na, (nb - 1) / 2, nb, n, n, 0.5)
+    g = np.random.default_rng(6)
+    sino = geo.P(g.uniform(0, 1, (n, n))) + 0.01 * g.standard_normal((na, nb))
+    L = 1.01 * orc.power_iteration(geo, np.ones((n, n)), 50)[0]
+    p = np.zeros(cnn.n_params())
+    for use_fista in (True, False):
+        x, e = cnn.pnp_fista(geo, sino, p, L, 6, use_fista=use_fista)
+        xr, er = orc.fista(geo, sino, 0.0, L, 6, n_inner=1, use_fista=use_fista)
+        np.testing.assert_allclose(x, xr, rtol=1e-6, atol=1e-6 * np.abs(xr).max())
+        np.testing.assert_allclose(e, er, rtol=1e-5)
+
+
+def test_fista_returns_the_last_prox_input():
+    """beta = 0: the prox is the identity, so the last z is the iterate;
+    beta > 0: the iterate is the TV prox of the returned z."""
+    import math
+    import oracle as orc
+    n, na, nb = 10, 7, 14
+    geo = orc.Geometry(np.arange(na) * math.pi / na + 0.1, (nb - 1) / 2, nb, n, n, 0.5)
+    sino = geo.P(np.random.default_rng(7).uniform(0, 1, (n, n)))
+    L = 1.01 * orc.power_iteration(geo, np.ones((n, n)), 50)[0]
+    x, _, z = orc.fista(geo, sino, 0.0, L, 4, n_inner=1, return_z=True)
+    np.testing.assert_array_equal(x, z)
+    x, _, z = orc.fista(geo, sino, 0.02, L, 4, n_inner=15, return_z=True)
+    xp, _, _ = orc.tv_prox(z, 0.02 / L, 15)
+    np.testing.assert_array_equal(x, xp)
