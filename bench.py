@@ -265,7 +265,25 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
             "psnr_tv_mean": float(np.mean(ps_tv)), "psnr_fbp_mean": float(np.mean(ps_fbp)),
             "psnr_tv_by_size": {k: float(np.mean(v)) for k, v in by.items()},
             "energy_lower_at_end_fraction": mono, "beta": {str(k): v for k, v in TV_BETA.items()},
-            "learned_prox": "not built (the plain TV solve is the reported arm)"}
+            "learned_prox": run_learned_prox(dev)}
+
+
+PROX_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1306_1392_b300", "weights",
+                            "prox_cnn_foam512.npy")
+
+
+def run_learned_prox(dev, n_eval=64):
+    """Plain TV vs the learned solve (FBP, K_T FISTA-TV iterations, two ISTA
+    steps with the trained CNN prox) at equal PSNR on 64 held-out seeded
+    512^2 foams (100 angles, Poisson 1e4); everything event-timed on the GPU."""
+    import numpy as np
+    import torch
+    from paper_1306_1392_b300 import train_prox
+    params = torch.from_numpy(np.load(PROX_WEIGHTS).astype(np.float32)).to(dev)
+    r = train_prox.evaluate(params, dev, n_eval=n_eval, ks=(), tv_long=0, hybrid_kt=(40, 75, 100),
+                            tv_first=(20, 25, 30, 35, 40))
+    r["weights"] = "paper_1306_1392_b300/weights/prox_cnn_foam512.npy (train_prox.py)"
+    return r
 
 
 # ------------------------------------------------------------------ precision study

@@ -1,10 +1,10 @@
 // Residual CNN prox: forward pass.
 //
-// Activation layout (bfloat16, 32 channels): per image and row, four
-// "chunk planes" of 8 channels each, [row][chunk][x][8] -> 16 bytes per pixel
-// and chunk.  Eight consecutive pixels of one chunk plane are one tensor-core
-// core matrix (8 rows x 16 bytes), so the shifted windows of a 3x3
-// convolution are plain descriptor offsets into the staged rows.
+// Activation layout (bfloat16, 32 channels): NHWC, 64 bytes per pixel, read
+// and written as four 16-byte chunks of 8 channels.  Staged in shared memory
+// as 64-byte rows (one per pixel) in the tensor core's 64-byte swizzle, so the
+// shifted windows of a 3x3 convolution are plain descriptor offsets into the
+// staged image rows.
 //
 //   layer 1   (1 -> 32):  conv_first_kernel, CUDA cores (9 MACs per output)
 //   layers 2-7 (32 -> 32): conv_mid_kernel, tcgen05 implicit GEMM:
@@ -12,6 +12,7 @@
 //                          K = 9 taps x 32 input channels in 18 steps of 16
 //   layer 8   (32 -> 1) + residual: conv_last_kernel, CUDA cores
 #include <cmath>
+#include <algorithm>
 #include <utility>
 
 #include "common.cuh"
@@ -31,27 +32,30 @@ constexpr int64_t kB8 = kW8 + 9 * kC;
 constexpr int64_t kNParams = kB8 + 1;          // 56097
 
 // ----------------------------------------------------------------- packing
-// One 32 -> 32 layer as the B operand: 18 K-slices (tap t = 3u + v, half h:
-// input channels 16h .. 16h+15), each [4 groups of 8 output channels][2 core
-// matrices along K][8 rows][8 bf16] = 1 KB.
-constexpr int kSliceBytes = 1024;
-constexpr int kLayerBytes = 18 * kSliceBytes;
+// One 32 -> 32 layer as the B operand, arranged for row reuse: an input row
+// feeds output rows rho - 1, rho, rho + 1 through the kernel rows u = 2, 1, 0,
+// so the weights of the three kernel rows are stacked along N:
+// n = 32 j + c_out with u = 2 - j (N = 96).  Layout [v][n][32 input
+// channels]: one 64-byte row per (v, n), its 16-byte chunk c stored at chunk
+// c ^ ((row >> 1) & 3) (the tensor core's 64-byte swizzle, for a copy placed
+// at a 1024-byte aligned address).
+constexpr int kBRows = 3 * 96;
+constexpr int kLayerBytes = kBRows * 64;        // 18,432
 
 // kBwd packs the weights of the input-gradient convolution instead:
-// W'[o = cin][i = cout][t] = W[cout][cin][8 - t] (transposed, 180-degree flip).
+// W'[o = cin][i = cout][u][v] = W[cout][cin][2 - u][2 - v] (transposed, 180-degree flip).
 template <bool kBwd>
 __global__ void pack_mid_kernel(const float *__restrict__ params, __nv_bfloat16 *__restrict__ packed) {
     const int l = blockIdx.y;                                    // 0 .. kMid-1
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;         // element within the layer
-    if (i >= 18 * 512) return;
-    const int slice = i >> 9, r = i & 511;
-    const int t = slice >> 1, h = slice & 1;
-    const int e = r & 7, row = (r >> 3) & 7, kc = (r >> 6) & 1, ng = r >> 7;
-    const int o = ng * 8 + row, c = 16 * h + 8 * kc + e;        // output / input channel of this conv
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;         // logical element (v, n, c)
+    if (i >= kBRows * kC) return;
+    const int c = i & 31, row = i >> 5, v = row / 96, n = row % 96;
+    const int j = n >> 5, o = n & 31, u = 2 - j;                 // output channel o of this conv
     const int64_t base = kMid0 + l * kMidStride;
-    const float w = kBwd ? params[base + ((int64_t)c * kC + o) * 9 + (8 - t)]
-                         : params[base + ((int64_t)o * kC + c) * 9 + t];
-    packed[(size_t)l * (kLayerBytes / 2) + i] = __float2bfloat16_rn(w);
+    const float w = kBwd ? params[base + ((int64_t)c * kC + o) * 9 + (2 - u) * 3 + (2 - v)]
+                         : params[base + ((int64_t)o * kC + c) * 9 + u * 3 + v];
+    const int phys = row * kC + (((c >> 3) ^ ((row >> 1) & 3)) << 3) + (c & 7);
+    packed[(size_t)l * (kLayerBytes / 2) + phys] = __float2bfloat16_rn(w);
 }
 
 __device__ __forceinline__ uint4 pack8(const float *v) {
@@ -76,6 +80,11 @@ __device__ __forceinline__ void unpack8(uint4 u, float *v) {
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// 16-byte chunk c (channels 8c .. 8c+7) of pixel (img, y, x)
+__device__ __forceinline__ size_t act_idx(int img, int y, int x, int c, int H, int W) {
+    return (((size_t)img * H + y) * W + x) * 4 + c;
+}
+
 // ----------------------------------------------------------------- layer 1
 // One thread per pixel: 32 outputs from the 3x3 neighbourhood of z.
 __global__ void __launch_bounds__(128) conv_first_kernel(const float *__restrict__ z, const float *__restrict__ params,
@@ -95,7 +104,6 @@ __global__ void __launch_bounds__(128) conv_first_kernel(const float *__restrict
             const int yy = y + u - 1, xx = x + v - 1;
             nb[3 * u + v] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? zi[(size_t)yy * W + xx] : 0.0f;
         }
-    uint4 *row = act + ((size_t)img * H + y) * 4 * W;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float o[8];
@@ -107,118 +115,244 @@ __global__ void __launch_bounds__(128) conv_first_kernel(const float *__restrict
             for (int t = 0; t < 9; ++t) a = fmaf(sw[ch * 9 + t], nb[t], a);
             o[k] = fmaxf(a + sb[ch], 0.0f);
         }
-        row[(size_t)c * W + x] = pack8(o);
+        act[act_idx(img, y, x, c, H, W)] = pack8(o);
     }
 }
 
 // ----------------------------------------------------------------- layers 2-7
-constexpr int kR = 4;                              // output rows per CTA
+// Persistent and pipelined: one CTA per SM walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; a tile is kR output rows x 128 pixels.  Two
+// input buffers and two TMEM accumulator halves: while the tensor core runs
+// tile i, the CTA drains tile i-1 from TMEM (epilogue) and loads tile i+1.
+constexpr int kR = 8;                              // output rows per tile
 constexpr int kXS = 130;                           // staged pixels per row: 128 + halo
-constexpr int kInBytes = (kR + 2) * 4 * kXS * 16;  // 49,920
-// Every address a descriptor of this kernel can reach (with either reading
-// of LBO and SBO) lies below 80 KB; the allocation covers it.
-constexpr int kMidSmem = 80 * 1024;
+constexpr int kInBytes = ((kR + 2) * kXS * 64 + 1023) / 1024 * 1024;   // 84,992 per buffer
+constexpr int kMidSmem = 1024 + 2 * kInBytes + kLayerBytes;         // + alignment slack
+constexpr uint32_t kTmemCols = 2 * kR * kC;        // 512: two accumulator halves
 constexpr uint32_t kWaitLimit = 1u << 22;
+
+struct MidTiles {
+    int tx, ty, H, W;
+    long total;
+    __device__ void decode(long t, int &img, int &y0, int &x0) const {
+        const long per = (long)tx * ty;
+        img = (int)(t / per);
+        const int rem = (int)(t % per);
+        y0 = (rem / tx) * kR;
+        x0 = (rem % tx) * 128;
+    }
+};
+
+// MMA schedule of one tile (the same for every tile; built once per CTA).
+// Input row rho (staged row rho + 1) and kernel rows j_lo .. j_hi of a
+// K-slice (kernel column v, half h) update output rows rho - 1 + j_lo ..
+// rho - 1 + j_hi in one MMA of N = 32 (j_hi - j_lo + 1).  A first pass (kernel
+// row u = 0 of slice (v, h) = (0, 0)) initialises every output row; all later
+// MMAs accumulate.  The tile's output rows are split between kMmaWarps
+// issuing warps (each issuing thread has a long per-instruction latency, so
+// several issue in parallel into disjoint accumulator columns); an MMA whose
+// rows straddle two warps is split.
+struct MmaOp {
+    uint32_t a_off;    // A start, bytes from the staging buffer; bit 31: accumulate
+    uint32_t b_off;    // B start, bytes from the weights
+    uint32_t d_off;    // TMEM column offset within the accumulator half
+    uint32_t idesc;
+};
+constexpr int kMmaWarps = 4;
+constexpr int kRowsPerMmaWarp = kR / kMmaWarps;
+constexpr int kMaxOps = 32;                           // per issuing warp (25 for kR = 8)
+
+__device__ void build_schedule(MmaOp (*ops)[kMaxOps], int *count) {
+    for (int g = 0; g < kMmaWarps; ++g) count[g] = 0;
+    auto add = [&](int rho, int slice, int jlo, int jhi, bool acc) {
+        for (int g = 0; g < kMmaWarps; ++g) {
+            const int lo = max(jlo, g * kRowsPerMmaWarp - rho + 1);
+            const int hi = min(jhi, (g + 1) * kRowsPerMmaWarp - rho);
+            if (lo > hi || count[g] >= kMaxOps) continue;
+            const int v = slice >> 1, h = slice & 1;
+            MmaOp o;
+            o.a_off = (uint32_t)(((rho + 1) * kXS + v) * 64 + h * 32) | (acc ? 0x80000000u : 0u);
+            o.b_off = (uint32_t)((v * 96 + lo * 32) * 64 + h * 32);
+            o.d_off = (uint32_t)((rho - 1 + lo) * kC);
+            o.idesc = tc::idesc_bf16(128, 32 * (hi - lo + 1));
+            ops[g][count[g]++] = o;
+        }
+    };
+    for (int rho = -1; rho <= kR - 2; ++rho) add(rho, 0, 2, 2, false);
+    for (int slice = 0; slice < 6; ++slice)
+        for (int rho = -1; rho <= kR; ++rho) {
+            const int jlo = rho < 1 ? 1 - rho : 0;
+            const int jhi = min(slice == 0 ? 1 : 2, kR - rho);
+            if (jlo <= jhi) add(rho, slice, jlo, jhi, true);
+        }
+}
+
+constexpr int kWorkers = 256;                     // 8 worker warps after the issuing warps
+constexpr int kMidThreads = 32 * kMmaWarps + kWorkers;
 
 // Forward: out = bf16(ReLU(conv(in) + bias)).  kBwd (input gradient of a
 // layer): out = bf16(conv'(in) masked by aux > 0), where in is the gradient
 // of the layer's pre-activation, conv' uses the transposed, flipped weights
 // and aux holds the previous layer's activations (the ReLU derivative).
+//
+// Warps 0 .. kMmaWarps-1 issue the tensor-core work; the next 8 warps stage
+// tiles and drain the accumulators.  Per tile i (buffer and accumulator half
+// b = i & 1):
+//   loaded[b]  workers -> MMA warps: tile i staged and visible to the tensor core
+//   mma[b]     tcgen05.commit of every MMA warp -> workers: accumulators complete
+//   tfree[b]   workers -> MMA warps: accumulator half b read out
 template <bool kBwd>
-__global__ void __launch_bounds__(256) conv_mid_kernel(const uint4 *__restrict__ in, uint4 *__restrict__ out,
-                                                       const uint4 *__restrict__ wpack,
-                                                       const float *__restrict__ bias,
-                                                       const uint4 *__restrict__ aux, int H, int W,
-                                                       unsigned *__restrict__ status) {
-    extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *s_in = sm;
-    uint8_t *s_w = sm + kInBytes;
+__global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *__restrict__ in,
+                                                                  uint4 *__restrict__ out,
+                                                                  const uint4 *__restrict__ wpack,
+                                                                  const float *__restrict__ bias,
+                                                                  const uint4 *__restrict__ aux, MidTiles T,
+                                                                  unsigned *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t sm_raw[];
+    // swizzled operands need 1024-byte aligned shared addresses
+    uint8_t *sm = sm_raw + ((1024 - (tc::smem_u32(sm_raw) & 1023)) & 1023);
+    uint8_t *s_in[2] = {sm, sm + kInBytes};
+    uint8_t *s_w = sm + 2 * kInBytes;
     __shared__ float s_bias[kC];
-    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(16) MmaOp s_ops[kMmaWarps][kMaxOps];
+    __shared__ int s_nops[kMmaWarps];
+    __shared__ __align__(8) uint64_t bar_loaded[2], bar_mma[2], bar_tfree[2];
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kR, img = blockIdx.z;
-    const uint4 *inb = in + (size_t)img * H * 4 * W;
+    const long first = blockIdx.x, stride = gridDim.x;
+    const int n_my = first < T.total ? (int)((T.total - 1 - first) / stride + 1) : 0;
 
-    // stage rows y0-1 .. y0+kR, pixels x0-1 .. x0+128, zero outside the image
-    for (int i = tid; i < (kR + 2) * 4 * kXS; i += 256) {
-        const int px = i % kXS, rc = i / kXS, c = rc & 3, rr = rc >> 2;
-        const int y = y0 - 1 + rr, x = x0 - 1 + px;
-        const bool ok = y >= 0 && y < H && x >= 0 && x < W;
-        tc::cp16(s_in + (size_t)i * 16, ok ? inb + ((size_t)(y * 4 + c) * W + x) : inb, ok ? 16u : 0u);
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, kTmemCols);
+        if (lane == 0) {
+            build_schedule(s_ops, s_nops);
+            for (int b = 0; b < 2; ++b) {
+                tc::bar_init(&bar_loaded[b], kWorkers);
+                tc::bar_init(&bar_mma[b], kMmaWarps);
+                tc::bar_init(&bar_tfree[b], kWorkers);
+            }
+        }
+    } else if (warp >= kMmaWarps) {
+        const int w = tid - 32 * kMmaWarps;
+        for (int i = w; i < kLayerBytes / 16; i += kWorkers) tc::cp16(s_w + (size_t)i * 16, wpack + i, 16u);
+        if (w < kC) s_bias[w] = kBwd ? 0.0f : bias[w];
     }
-    for (int i = tid; i < kLayerBytes / 16; i += 256) tc::cp16(s_w + (size_t)i * 16, wpack + i, 16u);
-    if (tid < kC) s_bias[tid] = kBwd ? 0.0f : bias[tid];
-    __syncwarp();
-    if (warp == 0) tc::tmem_alloc(&s_tmem, kR * kC);
-    if (tid == 0) tc::bar_init(&s_bar, 1);
-    tc::cp_wait_all();
-    tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tm = s_tmem;
+    bool ok = true;
 
-    if (tid == 0) {
-        const uint32_t a0 = tc::smem_u32(s_in), b0 = tc::smem_u32(s_w);
-        constexpr uint32_t idesc = tc::idesc_bf16(128, kC);
-#pragma unroll 1
-        for (int r = 0; r < kR; ++r)
-#pragma unroll 1
-            for (int t = 0; t < 9; ++t) {
-                const int u = t / 3, v = t % 3;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t a = a0 + (uint32_t)((((r + u) * 4 + 2 * h) * kXS + v) * 16);
-                    const uint32_t b = b0 + (uint32_t)((2 * t + h) * kSliceBytes);
-                    tc::mma_bf16(tm + (uint32_t)(r * kC), tc::sdesc(a, kXS * 16, 128), tc::sdesc(b, 128, 256), idesc,
-                                 (t | h) != 0);
-                }
+    if (warp < kMmaWarps) {
+        // ---------------------------------------------------------- MMA warps
+        const uint32_t b0 = tc::smem_u32(s_w);
+        const uint64_t hi = tc::sdesc_sw64(0, 512);          // descriptor without its start address
+        for (int i = 0; i < n_my && ok; ++i) {
+            const int b = i & 1;
+            bool good = tc::bar_wait(&bar_loaded[b], (uint32_t)((i >> 1) & 1), kWaitLimit);
+            if (good && i >= 2) good = tc::bar_wait(&bar_tfree[b], (uint32_t)(((i >> 1) - 1) & 1), kWaitLimit);
+            ok = __all_sync(0xffffffffu, good);
+            if (!ok) break;
+            tc::fence_after();
+            const uint32_t a0 = tc::smem_u32(s_in[b]);
+            const uint32_t d0 = tm + (uint32_t)(b * kR * kC);
+            const int nops = s_nops[warp];
+#pragma unroll 4
+            for (int k = 0; k < nops; ++k) {
+                const MmaOp o = s_ops[warp][k];
+                if (lane == 0)
+                    tc::mma_bf16(d0 + o.d_off, hi | (uint64_t)((a0 + (o.a_off & 0x7FFFFFFFu)) >> 4),
+                                 hi | (uint64_t)((b0 + o.b_off) >> 4), o.idesc, (o.a_off >> 31) != 0);
             }
-        tc::mma_commit(&s_bar);
-    }
-    __syncwarp();
-    bool ok = __all_sync(0xffffffffu, tc::bar_wait(&s_bar, 0, kWaitLimit));
-    if (!ok) {
-        if (lane == 0) atomicOr(status, tc::kErrMmaTimeout);
-        // let the MMAs drain before freeing TMEM; skip the epilogue
-        tc::bar_wait(&s_bar, 0, kWaitLimit);
-        ok = false;
-    }
-    tc::fence_after();
-    if (ok) {
-        // warp w reads TMEM lanes 32 (w % 4) .. +31 (pixels), rows 2 (w / 4), +1
-        const int q = warp & 3, m = 32 * q + lane, x = x0 + m;
-#pragma unroll 1
-        for (int rr = 0; rr < 2; ++rr) {
-            const int r = 2 * (warp >> 2) + rr, y = y0 + r;
-            float v[32];
-            tc::tmem_ld32(tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * kC), v);
-            if (x < W && y < H) {
-                const size_t rowoff = ((size_t)img * H + y) * 4 * W;
-                if (kBwd) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        float a[8];
-                        unpack8(aux[rowoff + (size_t)c * W + x], a);
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) v[8 * c + k] = a[k] > 0.0f ? v[8 * c + k] : 0.0f;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + s_bias[k], 0.0f);
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) out[rowoff + (size_t)c * W + x] = pack8(v + 8 * c);
-            }
+            __syncwarp();
+            if (lane == 0) tc::mma_commit(&bar_mma[b]);
+            __syncwarp();
         }
+        if (!ok && lane == 0) atomicOr(status, tc::kErrMmaTimeout);
+    } else {
+        // ---------------------------------------------------------- workers
+        const int w = tid - 32 * kMmaWarps, ww = warp - kMmaWarps;   // worker warp 0 .. 7
+        const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31 (pixels)
+        const int r0 = (kR / 2) * (ww >> 2);               // output rows r0 .. r0 + kR/2 - 1
+        auto stage = [&](int i) {                          // tile i into buffer i & 1
+            int img, y0, x0;
+            T.decode(first + (long)i * stride, img, y0, x0);
+            uint8_t *buf = s_in[i & 1];
+            for (int e = w; e < (kR + 2) * kXS * 4; e += kWorkers) {
+                const int c = e & 3, qq = e >> 2, px = qq % kXS, rr = qq / kXS;
+                const int y = y0 - 1 + rr, x = x0 - 1 + px;
+                const bool in_img = y >= 0 && y < T.H && x >= 0 && x < T.W;
+                tc::cp16(buf + (size_t)qq * 64 + ((c ^ ((qq >> 1) & 3)) << 4),
+                         in_img ? in + act_idx(img, y, x, c, T.H, T.W) : in, in_img ? 16u : 0u);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        auto publish = [&](int i) {                        // staged tile i -> MMA warp
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            tc::fence_async_smem();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bar_loaded[i & 1]))
+                         : "memory");
+        };
+        if (n_my > 0) {
+            stage(0);
+            publish(0);
+        }
+        for (int i = 0; i <= n_my; ++i) {
+            if (i >= 1) {
+                const int j = i - 1;
+                ok = __all_sync(0xffffffffu, tc::bar_wait(&bar_mma[j & 1], (uint32_t)((j >> 1) & 1), kWaitLimit));
+                if (!ok) {
+                    if (lane == 0) atomicOr(status, tc::kErrMmaTimeout);
+                    break;
+                }
+                tc::fence_after();
+            }
+            if (i + 1 < n_my) stage(i + 1);                 // buffer of tile i-1: its MMAs are done
+            if (i >= 1) {
+                const int j = i - 1, bj = j & 1;
+                int img, y0, x0;
+                T.decode(first + (long)j * stride, img, y0, x0);
+                const int x = x0 + 32 * q + lane;
+#pragma unroll 1
+                for (int rr = 0; rr < kR / 2; ++rr) {
+                    const int r = r0 + rr, y = y0 + r;
+                    float v[32];
+                    tc::tmem_ld32(tm + ((uint32_t)(32 * q) << 16) + (uint32_t)((bj * kR + r) * kC), v);
+                    if (x < T.W && y < T.H) {
+                        const size_t px = act_idx(img, y, x, 0, T.H, T.W);
+                        if (kBwd) {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                float a[8];
+                                unpack8(aux[px + c], a);
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) v[8 * c + k] = a[k] > 0.0f ? v[8 * c + k] : 0.0f;
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + s_bias[k], 0.0f);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) out[px + c] = pack8(v + 8 * c);
+                    }
+                }
+                tc::fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bar_tfree[bj])) : "memory");
+            }
+            if (i + 1 < n_my) publish(i + 1);
+        }
+    }
+    // every thread gets here (all waits are bounded); drain before freeing TMEM
+    if (!__syncthreads_and(ok) && tid == 0) {
+        tc::bar_wait(&bar_mma[0], 0, kWaitLimit);
+        tc::bar_wait(&bar_mma[1], 0, kWaitLimit);
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_free(tm, kR * kC);
+        tc::tmem_free(tm, kTmemCols);
     }
 }
 
@@ -235,7 +369,7 @@ __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict_
     __syncthreads();
     const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, img = blockIdx.z;
     if (x >= W) return;
-    const uint4 *a = act + (size_t)img * H * 4 * W;
+
     float acc = 0.0f;
 #pragma unroll 1
     for (int t = 0; t < 9; ++t) {
@@ -244,7 +378,7 @@ __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict_
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             float v[8];
-            unpack8(a[((size_t)yy * 4 + c) * W + xx], v);
+            unpack8(act[act_idx(img, yy, xx, c, H, W)], v);
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc = fmaf(sw[t * kC + 8 * c + k], v[k], acc);
         }
@@ -269,14 +403,33 @@ int set_smem_attrs() {
     return PYHST_OK;
 }
 
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
 int launch_conv_mid(bool bwd, const uint4 *in, uint4 *out, const __nv_bfloat16 *packed_layer, const float *bias,
                     const uint4 *aux, int n, int H, int W, unsigned *status, cudaStream_t st) {
-    const dim3 grid((W + 127) / 128, (H + kR - 1) / kR, n);
+    MidTiles T;
+    T.tx = (W + 127) / 128;
+    T.ty = (H + kR - 1) / kR;
+    T.H = H;
+    T.W = W;
+    T.total = (long)n * T.tx * T.ty;
+    const int grid = (int)std::min<long>(T.total, sm_count());
     const uint4 *wp = reinterpret_cast<const uint4 *>(packed_layer);
     if (bwd)
-        conv_mid_kernel<true><<<grid, 256, kMidSmem, st>>>(in, out, wp, bias, aux, H, W, status);
+        conv_mid_kernel<true><<<grid, kMidThreads, kMidSmem, st>>>(in, out, wp, bias, aux, T, status);
     else
-        conv_mid_kernel<false><<<grid, 256, kMidSmem, st>>>(in, out, wp, bias, aux, H, W, status);
+        conv_mid_kernel<false><<<grid, kMidThreads, kMidSmem, st>>>(in, out, wp, bias, aux, T, status);
     return cuda_status("conv_mid_kernel");
 }
 
@@ -288,7 +441,7 @@ int forward_pass(const float *params, const float *z, float *out, int n, int H, 
     if (!status) return fail(PYHST_ERR_CUDA, "device status word unavailable");
     int rc = set_smem_attrs();
     if (rc) return rc;
-    pack_mid_kernel<false><<<dim3((18 * 512 + 255) / 256, kMid), 256, 0, st>>>(params, packed);
+    pack_mid_kernel<false><<<dim3((kBRows * kC + 255) / 256, kMid), 256, 0, st>>>(params, packed);
     if ((rc = cuda_status("pack_mid_kernel"))) return rc;
     uint4 *src = acts ? acts[0] : act_a;
     conv_first_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(z, params, src, H, W);
@@ -367,11 +520,11 @@ __global__ void __launch_bounds__(128) conv_last_bwd_kernel(const float *__restr
         const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
         d[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? dout[((size_t)img * H + yy) * W + xx] : 0.0f;
     }
-    const size_t rowoff = ((size_t)img * H + y) * 4 * W;
+    const size_t px = act_idx(img, y, x, 0, H, W);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float a[8], o[8];
-        unpack8(a7[rowoff + (size_t)c * W + x], a);
+        unpack8(a7[px + c], a);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             float acc = 0.0f;
@@ -379,7 +532,7 @@ __global__ void __launch_bounds__(128) conv_last_bwd_kernel(const float *__restr
             for (int t = 0; t < 9; ++t) acc = fmaf(sw[t * kC + 8 * c + k], d[t], acc);
             o[k] = a[k] > 0.0f ? acc : 0.0f;
         }
-        dz[rowoff + (size_t)c * W + x] = pack8(o);
+        dz[px + c] = pack8(o);
     }
 }
 
@@ -400,7 +553,7 @@ __device__ __forceinline__ void stage_halo(const uint4 *__restrict__ src, float 
         const int c = i & 3, px = i >> 2, rr = px / (kTC + 2), cc = px % (kTC + 2);
         const int y = y0 - 1 + rr, x = x0 - 1 + cc;
         float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (y >= 0 && y < H && x >= 0 && x < W) unpack8(src[(((size_t)img * H + y) * 4 + c) * W + x], v);
+        if (y >= 0 && y < H && x >= 0 && x < W) unpack8(src[act_idx(img, y, x, c, H, W)], v);
         float4 *d = reinterpret_cast<float4 *>(dst + px * kC + 8 * c);
         d[0] = make_float4(v[0], v[1], v[2], v[3]);
         d[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -414,7 +567,7 @@ __device__ __forceinline__ void stage_tile(const uint4 *__restrict__ src, float 
         const int c = i & 3, px = i >> 2, rr = px / kTC, cc = px % kTC;
         const int y = y0 + rr, x = x0 + cc;
         float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (y < H && x < W) unpack8(src[(((size_t)img * H + y) * 4 + c) * W + x], v);
+        if (y < H && x < W) unpack8(src[act_idx(img, y, x, c, H, W)], v);
         float4 *d = reinterpret_cast<float4 *>(dst + px * kC + 8 * c);
         d[0] = make_float4(v[0], v[1], v[2], v[3]);
         d[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -640,7 +793,7 @@ int cnn_grad(const float *params, const float *z, const float *target, int n, in
     const size_t N = (size_t)n * H * W;
     loss_kernel<<<kLossBlocks, 256, 0, st>>>(out, target, N, (float)(2.0 / (double)N), dout, lpart);
     if (loss) loss_final_kernel<<<1, 256, 0, st>>>(lpart, kLossBlocks, 1.0 / (double)N, loss);
-    pack_mid_kernel<true><<<dim3((18 * 512 + 255) / 256, kMid), 256, 0, st>>>(params, packed_b);
+    pack_mid_kernel<true><<<dim3((kBRows * kC + 255) / 256, kMid), 256, 0, st>>>(params, packed_b);
     if ((rc = cuda_status("loss / packing kernels"))) return rc;
 
     // layer 8

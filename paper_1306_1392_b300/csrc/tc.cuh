@@ -2,11 +2,12 @@
 // with operands in shared memory and the accumulator in tensor memory (TMEM),
 // mbarrier completion with bounded waits, cp.async staging.
 //
-// Operand layout used by every caller: K-major, no swizzle.  A "core matrix"
-// is 8 rows x 16 bytes stored as 128 contiguous bytes (row r at byte 16 r).
-// In the shared-memory descriptor, the leading-dimension byte offset (LBO) is
-// the distance between core matrices adjacent along K and the stride-dimension
-// byte offset (SBO) the distance between 8-row groups adjacent along M (or N).
+// Operand layouts are K-major.  Without swizzle, a "core matrix" is 8 rows x
+// 16 bytes stored as 128 contiguous bytes (row r at byte 16 r); the
+// leading-dimension byte offset (LBO) is the distance between core matrices
+// adjacent along K and the stride-dimension byte offset (SBO) the distance
+// between 8-row groups adjacent along M (or N).  The swizzled form used by
+// the convolutions is described at sdesc_sw64.
 #pragma once
 
 #include <cstdint>
@@ -29,6 +30,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
     d |= static_cast<uint64_t>(1) << 46;
     return d;
+}
+
+// K-major operand in the 64-byte swizzle: 64-byte rows (32 bf16 of K), 8-row
+// groups SBO bytes apart (512 for contiguous rows), 16-byte chunk c of a row
+// at chunk c ^ ((address >> 7) & 3).  Layout type 4 (bits 61-63); LBO unused.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr, uint32_t sbo) {
+    return sdesc(saddr, 16, sbo) | (static_cast<uint64_t>(4) << 61);
 }
 
 // Instruction descriptor of kind::f16 with bf16 A and B (both K-major) and an

@@ -76,8 +76,11 @@ def test_sparse_network_is_bit_exact(n, h, w):
         np.testing.assert_array_equal(out[i], ref)
 
 
-@pytest.mark.parametrize("seed,n,h,w", [(0, 1, 37, 150), (4, 2, 64, 300)])
+@pytest.mark.parametrize("seed,n,h,w", [(0, 1, 37, 150), (4, 2, 64, 300), (2, 3, 264, 384)])
 def test_integer_network_is_bit_exact(seed, n, h, w):
+    """The last case has 297 tiles of 8 rows x 128 pixels, more than two per
+    SM, so every stage of the pipelined tensor-core kernel (double-buffered
+    loads and accumulators, mbarrier phases beyond the first) is exercised."""
     params = _integer_params(seed)
     z = np.random.default_rng(seed).integers(0, 8, (n, h, w)).astype(np.float32)
     out = _run(params, z)
