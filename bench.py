@@ -175,12 +175,14 @@ def cpu_sample_fbp(orc, raw_slice, flat, dark, angles, axis, target_s):
     per_row = (time.perf_counter() - t0) / pilot
     R = int(max(4, min(n, (target_s - t_filter) / max(per_row, 1e-6))))
     # a whole slice is shorter than the target: repeat its back-projection
-    reps = max(1, int(round((target_s - t_filter) / max(per_row * n, 1e-6)))) if R == n else 1
+    # until the measured time reaches the target (at most 16 times)
     r0 = (n - R) // 2
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    reps, t_bp = 0, 0.0
+    while reps == 0 or (R == n and reps < 16 and t_bp + t_filter * reps < target_s):
+        t0 = time.perf_counter()
         orc.backproject(q, angles, axis, n, R, orc.fbp_weight(N_ANG, 2.0 / n), cy=cy - r0)
-    t_bp = time.perf_counter() - t0
+        t_bp += time.perf_counter() - t0
+        reps += 1
     secs = t_bp + t_filter * reps * R / n
     return reps * R * n * N_ANG, secs, R * reps, orc.num_threads()
 
