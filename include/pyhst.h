@@ -370,6 +370,59 @@ int pyhst_tv_solve_capture(const pyhst_geometry *g, const float *sino, const pyh
                            int32_t n_capture, const int32_t *capture_iters, float *capture, void *workspace,
                            size_t ws_bytes, pyhst_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Overlapping-patch prior (Sec. 3.2.1).  m x m patches on a grid of step
+ * `stride` (1 <= stride <= m <= 16): along an axis of n pixels patch k starts
+ * at min(k stride, n - m), k = 0 .. K-1, K = ceil((n - m) / stride) + 1, so
+ * the patches cover the image (Eq. 4).  The core of a pixel (Eqs. 5-6) is the
+ * patch with the nearest centre start + (m-1)/2 along each axis (ties to the
+ * lower index).  Coefficients W [N][n_atoms] (N = K_rows K_cols, patch index
+ * k_row K_cols + k_col), dictionary D [n_atoms][m m] (patch pixels
+ * row-major); patches P = W D; the image takes each pixel from its core
+ * patch (Eq. 7):  x_j = P[core(j)][j - r_core(j)].
+ *   f(W) = ||y - Pi x||^2 + rho sum_p sum_{i in p} (x_{r_p + i} - P_{p,i})^2   (Eq. 8)
+ *   F(W) = f(W) + beta ||W||_1
+ * Pi is the projector of `g` (pyhst_project's operator, one slice) or, with
+ * g = NULL, the identity (denoising; y is then an ny x nx image).
+ * All arrays are DEVICE float32 unless stated.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t ny, nx;        /* image size                                      */
+    int32_t m, stride;     /* patch size and grid step                         */
+    int32_t n_atoms;       /* dictionary size (n_atoms x m^2 <= 65536)         */
+    const float *dict;     /* DEVICE [n_atoms][m*m]                            */
+    float rho;             /* weight of the patch-agreement term (>= 0)        */
+} pyhst_patch_problem;
+
+/* Patches per axis (host, no GPU work); PYHST_ERR_INVALID_ARG for bad sizes. */
+int pyhst_patch_grid(int32_t ny, int32_t nx, int32_t m, int32_t stride, int32_t *k_rows, int32_t *k_cols);
+
+/* Workspace of the calls below (g: NULL for denoising). */
+size_t pyhst_patch_workspace_size(const pyhst_patch_problem *pp, const pyhst_geometry *g);
+
+/* x [ny][nx] = the image of the coefficients W (Eq. 7). */
+int pyhst_patch_image(const pyhst_patch_problem *pp, const float *W, float *x, void *workspace, size_t ws_bytes,
+                      pyhst_stream_t stream);
+
+/* G [N][n_atoms] = gradient of f at W (Eq. 9), computed with the steps of
+ * Algorithm 1 (P = W D, the image from the cores, R = Pi^T (Pi x - y), the
+ * patch sum S and cover count, the auxiliary patches P', G = 2 P' D^T).
+ * f_out: DEVICE float64 [1] or NULL, receives f(W) (Eq. 8). */
+int pyhst_patch_gradient(const pyhst_patch_problem *pp, const pyhst_geometry *g, const float *W, const float *y,
+                         float *G, double *f_out, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+
+/* ISTA / FISTA on F(W) (Sec. 3.2.2): a gradient step of length 1/L on f,
+ * then the L1 shrinkage sign(v) max(|v| - beta/L, 0), FISTA momentum of
+ * Beck-Teboulle.  lipschitz > 0: L; 0: L = 1.01 x the largest eigenvalue of
+ * f's (constant) Hessian by n_power_iter power iterations from W = 1.
+ * W [N][n_atoms] in: start, out: last iterate; x (or NULL) receives its
+ * image; energy: DEVICE float64 [n_iter] or NULL, F at every iterate;
+ * lipschitz_out: DEVICE float64 [1] or NULL. */
+int pyhst_patch_solve(const pyhst_patch_problem *pp, const pyhst_geometry *g, const float *y, float beta,
+                      double lipschitz, int32_t n_power_iter, int32_t n_iter, int32_t use_fista, float *W, float *x,
+                      double *energy, double *lipschitz_out, void *workspace, size_t ws_bytes,
+                      pyhst_stream_t stream);
+
 /* Error bits recorded on the current device by kernels whose bounded waits
  * gave up (1: a tensor-core completion wait), since the last clear.  Reads
  * the word synchronously; clear != 0 resets it. */

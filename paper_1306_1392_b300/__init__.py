@@ -531,6 +531,88 @@ def pyhst_cnn_adam(params: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v:
                                 float(beta1), float(beta2), float(eps), _stream()))
 
 
+@dataclass
+class PatchProblem:
+    """Overlapping-patch functional (Eq. 8): image ny x nx, m x m patches on a
+    grid of step ``stride``, dictionary ``dict`` [n_atoms, m*m] (device
+    float32), weight ``rho``."""
+    ny: int
+    nx: int
+    m: int
+    stride: int
+    dict: torch.Tensor
+    rho: float
+
+    def __post_init__(self):
+        _cuda(self.dict, "dict", (torch.float32,))
+        if self.dict.dim() != 2 or self.dict.shape[1] != self.m * self.m:
+            raise ValueError("dict must be [n_atoms, m*m]")
+        self.dict = self.dict.contiguous()
+
+    def c(self) -> L.pyhst_patch_problem:
+        return L.pyhst_patch_problem(self.ny, self.nx, self.m, self.stride, self.dict.shape[0],
+                                     self.dict.data_ptr(), self.rho)
+
+    def grid(self):
+        return pyhst_patch_grid(self.ny, self.nx, self.m, self.stride)
+
+    def coef_shape(self):
+        kr, kc = self.grid()
+        return (kr * kc, self.dict.shape[0])
+
+
+def pyhst_patch_grid(ny: int, nx: int, m: int, stride: int):
+    kr, kc = ctypes.c_int32(), ctypes.c_int32()
+    _check(L.lib.pyhst_patch_grid(ny, nx, m, stride, ctypes.byref(kr), ctypes.byref(kc)))
+    return kr.value, kc.value
+
+
+def _patch_ws(pp: PatchProblem, geom, device, workspace):
+    pc = pp.c()
+    gc = geom.c(1) if geom is not None else None
+    need = L.lib.pyhst_patch_workspace_size(ctypes.byref(pc), ctypes.byref(gc) if gc is not None else None)
+    return pc, gc, _workspace(need, device, workspace)
+
+
+def pyhst_patch_image(pp: PatchProblem, W: torch.Tensor, out=None, workspace=None):
+    """The image of the coefficients W [N, n_atoms] (Eq. 7)."""
+    W = _cuda(W, "W", (torch.float32,)).contiguous()
+    out = torch.empty((pp.ny, pp.nx), dtype=torch.float32, device=W.device) if out is None else out
+    pc, _, ws = _patch_ws(pp, None, W.device, workspace)
+    _check(L.lib.pyhst_patch_image(ctypes.byref(pc), _ptr(W), _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def pyhst_patch_gradient(pp: PatchProblem, geom, W: torch.Tensor, y: torch.Tensor, workspace=None):
+    """Gradient of Eq. 8 (Algorithm 1) at W and f(W); geom None: denoising.
+    Returns (G [N, n_atoms], f [1] float64)."""
+    W = _cuda(W, "W", (torch.float32,)).contiguous()
+    y = _cuda(y, "y", (torch.float32,)).contiguous()
+    G = torch.empty_like(W)
+    f = torch.empty((1,), dtype=torch.float64, device=W.device)
+    pc, gc, ws = _patch_ws(pp, geom, W.device, workspace)
+    _check(L.lib.pyhst_patch_gradient(ctypes.byref(pc), ctypes.byref(gc) if gc is not None else None, _ptr(W),
+                                      _ptr(y), _ptr(G), _ptr(f), _ptr(ws), ws.numel(), _stream()))
+    return G, f
+
+
+def pyhst_patch_solve(pp: PatchProblem, geom, y: torch.Tensor, beta: float, n_iter: int, lipschitz: float = 0.0,
+                      n_power_iter: int = 50, use_fista: bool = True, W=None, energy: bool = True, workspace=None):
+    """ISTA/FISTA on F(W) = f(W) + beta ||W||_1; returns (W, x, energy
+    [n_iter] float64 or None, L [1] float64)."""
+    y = _cuda(y, "y", (torch.float32,)).contiguous()
+    W = torch.zeros(pp.coef_shape(), dtype=torch.float32, device=y.device) if W is None else W
+    _cuda(W, "W", (torch.float32,))
+    x = torch.empty((pp.ny, pp.nx), dtype=torch.float32, device=y.device)
+    e = torch.empty((n_iter,), dtype=torch.float64, device=y.device) if energy else None
+    lip = torch.empty((1,), dtype=torch.float64, device=y.device)
+    pc, gc, ws = _patch_ws(pp, geom, y.device, workspace)
+    _check(L.lib.pyhst_patch_solve(ctypes.byref(pc), ctypes.byref(gc) if gc is not None else None, _ptr(y),
+                                   float(beta), float(lipschitz), int(n_power_iter), int(n_iter), int(bool(use_fista)),
+                                   _ptr(W), _ptr(x), _ptr(e), _ptr(lip), _ptr(ws), ws.numel(), _stream()))
+    return W, x, e, lip
+
+
 def pyhst_device_status(clear: bool = True) -> int:
     """Error bits recorded by kernels whose bounded waits gave up (0: none)."""
     v = ctypes.c_uint32(0)

@@ -32,6 +32,11 @@ class pyhst_geometry(ctypes.Structure):
                 ("cx", c_float), ("cy", c_float), ("pixel_size", c_float)]
 
 
+class pyhst_patch_problem(ctypes.Structure):
+    _fields_ = [("ny", c_int32), ("nx", c_int32), ("m", c_int32), ("stride", c_int32), ("n_atoms", c_int32),
+                ("dict", c_void_p), ("rho", c_float)]
+
+
 class pyhst_tv_opts(ctypes.Structure):
     _fields_ = [("beta", c_float), ("n_iter", c_int32), ("n_inner", c_int32), ("tau", c_float),
                 ("use_fista", c_int32), ("warm_start", c_int32), ("lipschitz", c_double),
@@ -84,6 +89,15 @@ SIGNATURES = [
     ("pyhst_cnn_forward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t,
                                     c_void_p]),
     ("pyhst_device_status", c_int32, [ctypes.POINTER(ctypes.c_uint32), c_int32]),
+    ("pyhst_patch_grid", c_int32, [c_int32, c_int32, c_int32, c_int32, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    ("pyhst_patch_workspace_size", c_size_t, [ctypes.POINTER(pyhst_patch_problem), ctypes.POINTER(pyhst_geometry)]),
+    ("pyhst_patch_image", c_int32, [ctypes.POINTER(pyhst_patch_problem), c_void_p, c_void_p, c_void_p, c_size_t,
+                                    c_void_p]),
+    ("pyhst_patch_gradient", c_int32, [ctypes.POINTER(pyhst_patch_problem), ctypes.POINTER(pyhst_geometry), c_void_p,
+                                       c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("pyhst_patch_solve", c_int32, [ctypes.POINTER(pyhst_patch_problem), ctypes.POINTER(pyhst_geometry), c_void_p,
+                                    c_float, c_double, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_size_t, c_void_p]),
     ("pyhst_pnp_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry)]),
     ("pyhst_pnp_solve", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, ctypes.POINTER(pyhst_tv_opts),
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

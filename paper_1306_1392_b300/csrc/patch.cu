@@ -1,0 +1,513 @@
+// Overlapping-patch prior (Sec. 3.2.1): the image of the coefficients
+// (Eq. 7), the gradient of Eq. 8 by the steps of Algorithm 1, and ISTA/FISTA
+// with L1 shrinkage on the coefficients.
+//
+// Per gradient evaluation at coefficients W [N][n_atoms]:
+//   synth_kernel     P = W D                          (N x m^2, float32 sums)
+//   image_kernel     x_j = P[core(j)][j - r], S_j = sum of covering patches,
+//                    Nv_j = their number
+//   (projector)      R = Pi^T (Pi x - y)  (or x - y for denoising)
+//   paux_kernel      P'_{p,i} = rho (P_{p,i} - x_{r_p+i})
+//                               + [core(r_p+i) = p] (R + rho (Nv x - S))_{r_p+i},
+//                    and the penalty sum_p sum_i (x_{r_p+i} - P_{p,i})^2
+//   gcoef_kernel     G = 2 P' D^T
+// Energies and norms are float64 block partials summed in a fixed order.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pyhst {
+namespace {
+
+constexpr int kPT = 256;            // threads of the element kernels
+constexpr int kPBlocks = 296;       // fixed grid of the reductions (partials are summed in order)
+
+struct PDims {
+    int ny, nx, m, stride, kr, kc, N, nc, mm;
+};
+
+int axis_count(int n, int m, int stride) { return (n - m + stride - 1) / stride + 1; }
+
+__host__ __device__ __forceinline__ int axis_start(int k, int n, int m, int stride) {
+    const int r = k * stride;
+    return r > n - m ? n - m : r;
+}
+
+// Core patch of every coordinate along one axis: the nearest centre
+// start + (m-1)/2, ties to the lower index (Eq. 6 on a product grid).
+void core_table(int n, int m, int stride, int K, std::vector<int> &core) {
+    core.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        double bd = 1e300;
+        for (int k = 0; k < K; ++k) {
+            const double d = std::fabs((double)i - ((double)axis_start(k, n, m, stride) + 0.5 * (m - 1)));
+            if (d < bd) {
+                bd = d;
+                core[i] = k;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[kPT / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = l < kPT / 32 ? red[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+// P[p][i] = sum_t W[p][t] D[t][i]; one thread per output, i fastest.
+__global__ void synth_kernel(const float *__restrict__ W, const float *__restrict__ D, float *__restrict__ P, PDims d) {
+    const size_t o = (size_t)blockIdx.x * kPT + threadIdx.x;
+    if (o >= (size_t)d.N * d.mm) return;
+    const int p = (int)(o / d.mm), i = (int)(o % d.mm);
+    const float *w = W + (size_t)p * d.nc;
+    float acc = 0.0f;
+    for (int t = 0; t < d.nc; ++t) acc = fmaf(w[t], D[(size_t)t * d.mm + i], acc);
+    P[o] = acc;
+}
+
+// Eq. 7 and the patch sums: one thread per pixel.
+__global__ void image_kernel(const float *__restrict__ P, const int *__restrict__ core_r,
+                             const int *__restrict__ core_c, PDims d, float *__restrict__ X, float *__restrict__ S,
+                             float *__restrict__ Nv) {
+    const int j = blockIdx.x * kPT + threadIdx.x;
+    if (j >= d.ny * d.nx) return;
+    const int i = j / d.nx, c = j % d.nx;
+    {
+        const int a = core_r[i], b = core_c[c];
+        const int ri = axis_start(a, d.ny, d.m, d.stride), rc = axis_start(b, d.nx, d.m, d.stride);
+        X[j] = P[((size_t)a * d.kc + b) * d.mm + (i - ri) * d.m + (c - rc)];
+    }
+    float s = 0.0f;
+    int nv = 0;
+    const int a0 = max(0, (i - d.m + 1 + d.stride - 1) / d.stride - 1);
+    const int b0 = max(0, (c - d.m + 1 + d.stride - 1) / d.stride - 1);
+    for (int a = a0; a < d.kr; ++a) {
+        const int ri = axis_start(a, d.ny, d.m, d.stride);
+        if (ri > i) break;
+        if (i >= ri + d.m) continue;
+        for (int b = b0; b < d.kc; ++b) {
+            const int rc = axis_start(b, d.nx, d.m, d.stride);
+            if (rc > c) break;
+            if (c >= rc + d.m) continue;
+            s += P[((size_t)a * d.kc + b) * d.mm + (i - ri) * d.m + (c - rc)];
+            ++nv;
+        }
+    }
+    S[j] = s;
+    Nv[j] = (float)nv;
+}
+
+// r = a - b (float32) and the float64 partial of sum r^2.
+__global__ void diff_kernel(const float *__restrict__ a, const float *__restrict__ b, float *__restrict__ r, size_t n,
+                            double *__restrict__ part) {
+    double acc = 0.0;
+    for (size_t k = (size_t)blockIdx.x * kPT + threadIdx.x; k < n; k += (size_t)gridDim.x * kPT) {
+        const float v = a[k] - (b ? b[k] : 0.0f);
+        if (r) r[k] = v;
+        acc += (double)v * (double)v;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// The auxiliary patches P' of Algorithm 1 and the penalty partials.
+__global__ void paux_kernel(const float *__restrict__ P, const float *__restrict__ X, const float *__restrict__ R,
+                            const float *__restrict__ S, const float *__restrict__ Nv, const int *__restrict__ core_r,
+                            const int *__restrict__ core_c, PDims d, float rho, float *__restrict__ Pp,
+                            double *__restrict__ part) {
+    double acc = 0.0;
+    const size_t total = (size_t)d.N * d.mm;
+    for (size_t o = (size_t)blockIdx.x * kPT + threadIdx.x; o < total; o += (size_t)gridDim.x * kPT) {
+        const int p = (int)(o / d.mm), i = (int)(o % d.mm);
+        const int a = p / d.kc, b = p % d.kc;
+        const int rr = axis_start(a, d.ny, d.m, d.stride) + i / d.m;
+        const int cc = axis_start(b, d.nx, d.m, d.stride) + i % d.m;
+        const size_t j = (size_t)rr * d.nx + cc;
+        const float x = X[j], pv = P[o];
+        float v = rho * (pv - x);
+        if (Pp) {
+            if (core_r[rr] == a && core_c[cc] == b) v += R[j] + rho * (Nv[j] * x - S[j]);
+            Pp[o] = v;
+        }
+        const double e = (double)x - (double)pv;
+        acc += e * e;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// G[p][t] = 2 sum_i P'[p][i] D[t][i]; Dt = D^T [mm][nc]; one thread per output.
+__global__ void gcoef_kernel(const float *__restrict__ Pp, const float *__restrict__ Dt, PDims d, float *__restrict__ G) {
+    const size_t o = (size_t)blockIdx.x * kPT + threadIdx.x;
+    if (o >= (size_t)d.N * d.nc) return;
+    const int p = (int)(o / d.nc), t = (int)(o % d.nc);
+    const float *pp = Pp + (size_t)p * d.mm;
+    float acc = 0.0f;
+    for (int i = 0; i < d.mm; ++i) acc = fmaf(pp[i], Dt[(size_t)i * d.nc + t], acc);
+    G[o] = 2.0f * acc;
+}
+
+__global__ void transpose_kernel(const float *__restrict__ D, float *__restrict__ Dt, int nc, int mm) {
+    const int o = blockIdx.x * kPT + threadIdx.x;
+    if (o >= nc * mm) return;
+    const int t = o / mm, i = o % mm;
+    Dt[(size_t)i * nc + t] = D[o];
+}
+
+// Scalars of a solve (device): L, and its float32 step and threshold.
+struct PScal {
+    double *L;       // [1]
+    float *invL;     // [1]
+    float *thr;      // [1] beta / L
+    double *acc;     // [4] scratch sums
+};
+
+// sum of part[0..n) (fixed order) into *out (scaled)
+__global__ void finalize_kernel(const double *__restrict__ part, int n, double scale, double *__restrict__ out) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += kPT) acc += part[k];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = acc * scale;
+}
+
+// f = data + rho pen (+ beta l1 when l1 != NULL) into out[slot]
+__global__ void energy_kernel(const double *__restrict__ pd, const double *__restrict__ pp,
+                              const double *__restrict__ pl, int n, double rho, double beta,
+                              double *__restrict__ out) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = threadIdx.x; k < n; k += kPT) {
+        a += pd[k];
+        b += pp[k];
+        if (pl) c += pl[k];
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    c = block_sum(c);
+    if (threadIdx.x == 0) *out = a + rho * b + beta * c;
+}
+
+// W = soft(Y - G / L, beta / L); Y = W + w (W - Wold); Wold = W; L1 partials of W.
+__global__ void fista_update_kernel(float *__restrict__ W, float *__restrict__ Y, float *__restrict__ Wold,
+                                    const float *__restrict__ G, size_t n, PScal sc, float w,
+                                    double *__restrict__ part) {
+    const float invL = *sc.invL, thr = *sc.thr;
+    double acc = 0.0;
+    for (size_t k = (size_t)blockIdx.x * kPT + threadIdx.x; k < n; k += (size_t)gridDim.x * kPT) {
+        const float v = Y[k] - G[k] * invL;
+        const float a = fabsf(v) - thr;
+        const float wn = a > 0.0f ? copysignf(a, v) : 0.0f;
+        W[k] = wn;
+        Y[k] = wn + w * (wn - Wold[k]);
+        Wold[k] = wn;
+        acc += fabs((double)wn);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// power iteration: v = h / ||h||, with ||h||^2 in *nrm (float64)
+__global__ void pnorm_kernel(const float *__restrict__ h, float *__restrict__ v, size_t n, const double *__restrict__ nrm2) {
+    const double s = 1.0 / sqrt(*nrm2);
+    for (size_t k = (size_t)blockIdx.x * kPT + threadIdx.x; k < n; k += (size_t)gridDim.x * kPT)
+        v[k] = (float)((double)h[k] * s);
+}
+
+__global__ void dot_kernel(const float *__restrict__ a, const float *__restrict__ b, size_t n, double *__restrict__ part) {
+    double acc = 0.0;
+    for (size_t k = (size_t)blockIdx.x * kPT + threadIdx.x; k < n; k += (size_t)gridDim.x * kPT)
+        acc += (double)a[k] * (double)b[k];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void set_step_kernel(const double *__restrict__ rq, double given, float beta, PScal sc) {
+    const double L = given > 0.0 ? given : 1.01 * *rq;
+    *sc.L = L;
+    *sc.invL = (float)(1.0 / L);
+    *sc.thr = (float)((double)beta / L);
+}
+
+__global__ void fill_f(float *__restrict__ v, float val, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * kPT + threadIdx.x; k < n; k += (size_t)gridDim.x * kPT) v[k] = val;
+}
+
+struct PLayout {
+    size_t core_r, core_c, P, Pp, X, R, S, Nv, Dt, sdata, tab, xt, zero, Y, Wold, G, V, part, scal, bytes;
+};
+
+struct PCtx {
+    PDims d;
+    const pyhst_patch_problem *pp;
+    const pyhst_geometry *g;
+    int *core_r, *core_c;
+    float *P, *Pp, *X, *R, *S, *Nv, *Dt, *sdata, *xt, *zero, *Y, *Wold, *G, *V;
+    AngleInfo *tab;
+    double *part;      // [4][kPBlocks]
+    PScal sc;
+    size_t M;          // data size
+};
+
+bool make_dims(const pyhst_patch_problem *pp, PDims &d) {
+    if (!pp || pp->ny < 1 || pp->nx < 1 || pp->m < 1 || pp->m > 16 || pp->stride < 1 || pp->stride > pp->m ||
+        pp->m > pp->ny || pp->m > pp->nx || pp->n_atoms < 1 || (int64_t)pp->n_atoms * pp->m * pp->m > 65536)
+        return false;
+    d.ny = pp->ny;
+    d.nx = pp->nx;
+    d.m = pp->m;
+    d.stride = pp->stride;
+    d.kr = axis_count(pp->ny, pp->m, pp->stride);
+    d.kc = axis_count(pp->nx, pp->m, pp->stride);
+    d.N = d.kr * d.kc;
+    d.nc = pp->n_atoms;
+    d.mm = pp->m * pp->m;
+    return true;
+}
+
+PLayout playout(const PDims &d, const pyhst_geometry *g) {
+    PLayout l{};
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
+    const size_t img = sizeof(float) * (size_t)d.ny * d.nx;
+    const size_t M = g ? (size_t)g->n_angles * g->n_bins : (size_t)d.ny * d.nx;
+    l.core_r = take(sizeof(int) * d.ny);
+    l.core_c = take(sizeof(int) * d.nx);
+    l.P = take(sizeof(float) * (size_t)d.N * d.mm);
+    l.Pp = take(sizeof(float) * (size_t)d.N * d.mm);
+    l.X = take(img);
+    l.R = take(img);
+    l.S = take(img);
+    l.Nv = take(img);
+    l.Dt = take(sizeof(float) * (size_t)d.nc * d.mm);
+    l.sdata = take(sizeof(float) * M);
+    l.zero = take(sizeof(float) * M);
+    if (g) {
+        pyhst_geometry g1 = *g;
+        g1.n_slices = 1;
+        l.tab = take(angle_table_bytes(g->n_angles));
+        l.xt = take(project_scratch_bytes(&g1));
+    }
+    const size_t coef = sizeof(float) * (size_t)d.N * d.nc;
+    l.Y = take(coef);
+    l.Wold = take(coef);
+    l.G = take(coef);
+    l.V = take(coef);
+    l.part = take(sizeof(double) * 4 * kPBlocks);
+    l.scal = take(64);
+    l.bytes = off;
+    return l;
+}
+
+int prepare(const pyhst_patch_problem *pp, const pyhst_geometry *g, void *ws, cudaStream_t st, PCtx &c) {
+    if (!make_dims(pp, c.d)) return fail(PYHST_ERR_INVALID_ARG, "patch problem sizes out of range");
+    const PLayout l = playout(c.d, g);
+    char *b = static_cast<char *>(ws);
+    c.pp = pp;
+    c.g = g;
+    c.core_r = reinterpret_cast<int *>(b + l.core_r);
+    c.core_c = reinterpret_cast<int *>(b + l.core_c);
+    c.P = reinterpret_cast<float *>(b + l.P);
+    c.Pp = reinterpret_cast<float *>(b + l.Pp);
+    c.X = reinterpret_cast<float *>(b + l.X);
+    c.R = reinterpret_cast<float *>(b + l.R);
+    c.S = reinterpret_cast<float *>(b + l.S);
+    c.Nv = reinterpret_cast<float *>(b + l.Nv);
+    c.Dt = reinterpret_cast<float *>(b + l.Dt);
+    c.sdata = reinterpret_cast<float *>(b + l.sdata);
+    c.zero = reinterpret_cast<float *>(b + l.zero);
+    c.tab = g ? reinterpret_cast<AngleInfo *>(b + l.tab) : nullptr;
+    c.xt = g ? reinterpret_cast<float *>(b + l.xt) : nullptr;
+    c.Y = reinterpret_cast<float *>(b + l.Y);
+    c.Wold = reinterpret_cast<float *>(b + l.Wold);
+    c.G = reinterpret_cast<float *>(b + l.G);
+    c.V = reinterpret_cast<float *>(b + l.V);
+    c.part = reinterpret_cast<double *>(b + l.part);
+    double *sc = reinterpret_cast<double *>(b + l.scal);
+    c.sc.L = sc;
+    c.sc.acc = sc + 1;
+    c.sc.invL = reinterpret_cast<float *>(sc + 5);
+    c.sc.thr = c.sc.invL + 1;
+    c.M = g ? (size_t)g->n_angles * g->n_bins : (size_t)c.d.ny * c.d.nx;
+    std::vector<int> cr, cc;
+    core_table(c.d.ny, c.d.m, c.d.stride, c.d.kr, cr);
+    core_table(c.d.nx, c.d.m, c.d.stride, c.d.kc, cc);
+    cudaMemcpyAsync(c.core_r, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c.core_c, cc.data(), sizeof(int) * cc.size(), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);   // the host tables are local
+    cudaMemsetAsync(c.zero, 0, sizeof(float) * c.M, st);
+    transpose_kernel<<<(c.d.nc * c.d.mm + kPT - 1) / kPT, kPT, 0, st>>>(pp->dict, c.Dt, c.d.nc, c.d.mm);
+    int rc = cuda_status("patch set-up");
+    if (rc) return rc;
+    if (g && (rc = launch_angle_table(g->angles, g->axis, g->n_angles, c.tab, st))) return rc;
+    return PYHST_OK;
+}
+
+int blocks_for(size_t n) { return (int)std::min<size_t>((n + kPT - 1) / kPT, 1u << 30); }
+
+// P = W D and the image (Eq. 7), patch sums and cover counts.
+int synth_image(PCtx &c, const float *W, cudaStream_t st) {
+    const size_t np = (size_t)c.d.N * c.d.mm;
+    synth_kernel<<<blocks_for(np), kPT, 0, st>>>(W, c.pp->dict, c.P, c.d);
+    image_kernel<<<blocks_for((size_t)c.d.ny * c.d.nx), kPT, 0, st>>>(c.P, c.core_r, c.core_c, c.d, c.X, c.S, c.Nv);
+    return cuda_status("patch synthesis");
+}
+
+// Evaluate at W: image, residual R, penalty; with G != NULL also the
+// gradient.  Partials: part[0] data, part[1] penalty.
+int evaluate(PCtx &c, const float *W, const float *y, float *G, cudaStream_t st) {
+    int rc = synth_image(c, W, st);
+    if (rc) return rc;
+    if (c.g) {
+        pyhst_geometry g1 = *c.g;
+        g1.n_slices = 1;
+        if ((rc = launch_project(&g1, c.tab, c.X, c.sdata, c.g->pixel_size, c.xt, st))) return rc;
+        diff_kernel<<<kPBlocks, kPT, 0, st>>>(c.sdata, y, nullptr, c.M, c.part);
+        if (G && (rc = launch_backproject(&g1, c.tab, BpSource{c.sdata, y}, c.R, c.g->pixel_size, st))) return rc;
+    } else {
+        diff_kernel<<<kPBlocks, kPT, 0, st>>>(c.X, y, c.R, c.M, c.part);
+    }
+    paux_kernel<<<kPBlocks, kPT, 0, st>>>(c.P, c.X, c.R, c.S, c.Nv, c.core_r, c.core_c, c.d, c.pp->rho,
+                                         G ? c.Pp : nullptr, c.part + kPBlocks);
+    if (G) gcoef_kernel<<<blocks_for((size_t)c.d.N * c.d.nc), kPT, 0, st>>>(c.Pp, c.Dt, c.d, G);
+    return cuda_status("patch gradient");
+}
+
+int check_common(const pyhst_patch_problem *pp, const pyhst_geometry *g, void *ws, size_t ws_bytes) {
+    PDims d;
+    if (!pp || !make_dims(pp, d))
+        return fail(PYHST_ERR_INVALID_ARG, "patch problem: need 1 <= stride <= m <= min(16, ny, nx), "
+                                           "n_atoms >= 1, n_atoms m^2 <= 65536");
+    if (!pp->dict) return fail(PYHST_ERR_INVALID_ARG, "dictionary pointer is NULL");
+    if (!(pp->rho >= 0.0f) || !std::isfinite(pp->rho)) return fail(PYHST_ERR_INVALID_ARG, "rho must be >= 0");
+    if (g) {
+        pyhst_geometry g1 = *g;
+        g1.n_slices = 1;
+        int rc = check_geometry(&g1);
+        if (rc) return rc;
+        if (g->nx != pp->nx || g->ny != pp->ny) return fail(PYHST_ERR_INVALID_ARG, "geometry image size differs");
+    }
+    const size_t need = playout(d, g).bytes;
+    if (!ws || ws_bytes < need || ((uintptr_t)ws % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    return PYHST_OK;
+}
+
+}  // namespace
+}  // namespace pyhst
+
+using namespace pyhst;
+
+extern "C" int pyhst_patch_grid(int32_t ny, int32_t nx, int32_t m, int32_t stride, int32_t *k_rows, int32_t *k_cols) {
+    if (!k_rows || !k_cols) return fail(PYHST_ERR_INVALID_ARG, "output pointers are NULL");
+    if (m < 1 || stride < 1 || stride > m || m > ny || m > nx)
+        return fail(PYHST_ERR_INVALID_ARG, "need 1 <= stride <= m <= min(ny, nx)");
+    *k_rows = axis_count(ny, m, stride);
+    *k_cols = axis_count(nx, m, stride);
+    return PYHST_OK;
+}
+
+extern "C" size_t pyhst_patch_workspace_size(const pyhst_patch_problem *pp, const pyhst_geometry *g) {
+    PDims d;
+    if (!pp || !make_dims(pp, d)) return 0;
+    return playout(d, g).bytes;
+}
+
+extern "C" int pyhst_patch_image(const pyhst_patch_problem *pp, const float *W, float *x, void *workspace,
+                                 size_t ws_bytes, pyhst_stream_t stream) {
+    int rc = check_common(pp, nullptr, workspace, ws_bytes);
+    if (rc) return rc;
+    if (!W || !x) return fail(PYHST_ERR_INVALID_ARG, "W/x pointer is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PCtx c;
+    if ((rc = prepare(pp, nullptr, workspace, st, c))) return rc;
+    if ((rc = synth_image(c, W, st))) return rc;
+    cudaMemcpyAsync(x, c.X, sizeof(float) * (size_t)c.d.ny * c.d.nx, cudaMemcpyDeviceToDevice, st);
+    return cuda_status("patch image copy");
+}
+
+extern "C" int pyhst_patch_gradient(const pyhst_patch_problem *pp, const pyhst_geometry *g, const float *W,
+                                    const float *y, float *G, double *f_out, void *workspace, size_t ws_bytes,
+                                    pyhst_stream_t stream) {
+    int rc = check_common(pp, g, workspace, ws_bytes);
+    if (rc) return rc;
+    if (!W || !y || !G) return fail(PYHST_ERR_INVALID_ARG, "W/y/G pointer is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PCtx c;
+    if ((rc = prepare(pp, g, workspace, st, c))) return rc;
+    if ((rc = evaluate(c, W, y, G, st))) return rc;
+    if (f_out) energy_kernel<<<1, kPT, 0, st>>>(c.part, c.part + kPBlocks, nullptr, kPBlocks, pp->rho, 0.0, f_out);
+    return cuda_status("patch energy");
+}
+
+extern "C" int pyhst_patch_solve(const pyhst_patch_problem *pp, const pyhst_geometry *g, const float *y, float beta,
+                                 double lipschitz, int32_t n_power_iter, int32_t n_iter, int32_t use_fista, float *W,
+                                 float *x, double *energy, double *lipschitz_out, void *workspace, size_t ws_bytes,
+                                 pyhst_stream_t stream) {
+    int rc = check_common(pp, g, workspace, ws_bytes);
+    if (rc) return rc;
+    if (!W || !y) return fail(PYHST_ERR_INVALID_ARG, "W/y pointer is NULL");
+    if (!(beta >= 0.0f) || !std::isfinite(beta)) return fail(PYHST_ERR_INVALID_ARG, "beta must be >= 0");
+    if (n_iter < 1) return fail(PYHST_ERR_INVALID_ARG, "n_iter must be >= 1");
+    if (!(lipschitz >= 0.0) || !std::isfinite(lipschitz))
+        return fail(PYHST_ERR_INVALID_ARG, "lipschitz must be >= 0 (0: estimate)");
+    if (lipschitz == 0.0 && n_power_iter < 1)
+        return fail(PYHST_ERR_INVALID_ARG, "n_power_iter must be >= 1 when lipschitz is estimated");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PCtx c;
+    if ((rc = prepare(pp, g, workspace, st, c))) return rc;
+    const size_t nw = (size_t)c.d.N * c.d.nc;
+
+    // ---- step size: the Hessian of f is constant; H v = grad f(v) at y = 0
+    if (lipschitz == 0.0) {
+        fill_f<<<kPBlocks, kPT, 0, st>>>(c.V, 1.0f, nw);
+        for (int it = 0; it < n_power_iter; ++it) {
+            if ((rc = evaluate(c, c.V, c.zero, c.G, st))) return rc;
+            dot_kernel<<<kPBlocks, kPT, 0, st>>>(c.G, c.G, nw, c.part + 2 * kPBlocks);
+            finalize_kernel<<<1, kPT, 0, st>>>(c.part + 2 * kPBlocks, kPBlocks, 1.0, c.sc.acc);
+            pnorm_kernel<<<kPBlocks, kPT, 0, st>>>(c.G, c.V, nw, c.sc.acc);
+        }
+        // Rayleigh quotient <v, H v> with ||v|| = 1
+        if ((rc = evaluate(c, c.V, c.zero, c.G, st))) return rc;
+        dot_kernel<<<kPBlocks, kPT, 0, st>>>(c.V, c.G, nw, c.part + 2 * kPBlocks);
+        finalize_kernel<<<1, kPT, 0, st>>>(c.part + 2 * kPBlocks, kPBlocks, 1.0, c.sc.acc + 1);
+    }
+    set_step_kernel<<<1, 1, 0, st>>>(c.sc.acc + 1, lipschitz, beta, c.sc);
+    if (lipschitz_out) cudaMemcpyAsync(lipschitz_out, c.sc.L, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if ((rc = cuda_status("patch step size"))) return rc;
+
+    // ---- ISTA / FISTA: Y = Wold = W
+    cudaMemcpyAsync(c.Y, W, sizeof(float) * nw, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c.Wold, W, sizeof(float) * nw, cudaMemcpyDeviceToDevice, st);
+    double t = 1.0;
+    for (int k = 0; k < n_iter; ++k) {
+        if ((rc = evaluate(c, c.Y, y, c.G, st))) return rc;
+        double w = 0.0;
+        if (use_fista) {
+            const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+            w = (t - 1.0) / tn;
+            t = tn;
+        }
+        fista_update_kernel<<<kPBlocks, kPT, 0, st>>>(W, c.Y, c.Wold, c.G, nw, c.sc, (float)w, c.part + 2 * kPBlocks);
+        if ((rc = cuda_status("patch update"))) return rc;
+        if (energy) {
+            if ((rc = evaluate(c, W, y, nullptr, st))) return rc;
+            energy_kernel<<<1, kPT, 0, st>>>(c.part, c.part + kPBlocks, c.part + 2 * kPBlocks, kPBlocks, pp->rho,
+                                             (double)beta, energy + k);
+        }
+    }
+    if (x) {
+        if ((rc = synth_image(c, W, st))) return rc;
+        cudaMemcpyAsync(x, c.X, sizeof(float) * (size_t)c.d.ny * c.d.nx, cudaMemcpyDeviceToDevice, st);
+    }
+    return cuda_status("patch solve");
+}
