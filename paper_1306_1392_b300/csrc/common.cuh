@@ -90,8 +90,13 @@ int bp_tiles(int nx, int ny, int *tx, int *ty);
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
                              cudaStream_t st);
 int proj_blocks(int n_angles, int n_bins, int *nb, int *na);
+// true: the 512-column staging variant of the projector (sparse angle sets)
+bool project_wide(int nx, int ny, int n_angles);
+// Sets the projector kernels' shared-memory attributes (call before a
+// stream capture that launches them).
+int set_proj_attr();
 int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
-                         const int4 *tr_items, int n_tr_items, cudaStream_t st);
+                         const int4 *tr_items, int n_tr_items, bool wide, cudaStream_t st);
 
 // ----------------------------------------------------------------- profiling
 // Opt-in per-launch timing (pyhst_profile_enable): events recorded on the

@@ -88,7 +88,12 @@ ScanLayout scan_layout(const pyhst_geometry *g, int n_beta, int held_out, const 
     l.batch_bytes = pyhst_tv_batch_workspace_size(items.data(), n_beta, opts);
     l.batch = take(l.batch_bytes);
     l.tab1 = take(sizeof(AngleInfo));
-    l.xt = take(sizeof(float) * (size_t)g->nx * g->ny * n_beta);
+    {
+        pyhst_geometry gk = *g;
+        gk.n_angles = 1;
+        gk.n_slices = n_beta;
+        l.xt = take(project_scratch_bytes(&gk));
+    }
     l.rows = take(sizeof(float) * (size_t)g->n_bins * n_beta);
     l.bytes = off;
     return l;

@@ -17,19 +17,22 @@
 // of 16 rows; for each chunk it stages the rectangle of pixels that its rays
 // can touch (for neighbouring angles their bands nearly coincide, so one
 // staged pixel serves about eight times more rays than a one-angle band
-// would).  The next chunk is loaded from L2 into registers (float4) while the
-// current one is walked, with one barrier per chunk.  If a group's band does
-// not fit the staging buffer (angles far apart) the CTA walks its angles one
-// at a time; the band width is convex in the row, so checking the first and
-// last chunks decides it.
+// would); only the columns of the band are loaded.  The next chunk is loaded
+// from L2 into registers (float4) while the current one is walked, with one
+// barrier per chunk.  The staging buffer holds 512 columns, enough for the
+// 8-angle bands of sparse angle sets (150 angles at 2048^2); if a group's band
+// still does not fit, the CTA walks 4, 2 or 1 angles at a time; the band width
+// is convex in the row, so checking the first and last chunks decides it.
+// When the grid would have few CTAs (few angles, few slices) the rows are
+// split into segments whose partial sinograms are added in a fixed order.
 //
 // x*(b, r) = X0 + b dX - r rho is computed in 32.32 fixed point (int64), so the
 // staged bands, computed with the same integers, provably contain every tap
 // (with one column to spare on each side).  Inside a chunk each ray follows
-// x* - L0 (L0: the chunk's first staged column) in 9.23 fixed point (int32),
-// re-anchored exactly at every chunk, so a row costs one integer add and the
-// error stays below 1e-6 pixel; the fraction becomes a float by placing its
-// bits in a mantissa.  Pairs of rays share paired float32 (f32x2) arithmetic.
+// x* - L0 (L0: the chunk's first staged column) in 9.23 fixed point (int32;
+// 10.22 for the 512-column variant), re-anchored exactly at every chunk, so a
+// row costs one integer add and the error stays below 2e-6 pixel; the
+// fraction becomes a float by placing its bits in a mantissa.  Pairs of rays share paired float32 (f32x2) arithmetic.
 // Rays that do not take part in a pass get zero weights and a fixed in-range
 // position, so the walk has no branches.  The weights
 // of the taps jc-1, jc, jc+1 (jc = round(x*), psi = x* - jc in [-1/2, 1/2)) are
@@ -37,6 +40,8 @@
 // no fourth pixel can have a non-zero weight since a >= 1/sqrt(2).
 #include <climits>
 #include <cmath>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -47,9 +52,12 @@ constexpr int kPThreads = 256;
 constexpr int kPG = 8;          // angles per group
 constexpr int kPB = 128;        // bins per CTA
 constexpr int kPR = 16;         // rows per staged chunk
-constexpr int kPW = 256;        // staged pixels per row (band capacity, multiple of 4)
+// Staged pixels per row (band capacity): 256 for dense angle sets, 512 for
+// sparse ones (image size / number of angles > 2), chosen per launch.
 constexpr int kPRays = kPG / 2; // rays per thread
-constexpr int kPVec = kPR * kPW / 4 / kPThreads;   // float4 staged per thread per chunk (4)
+template <int PW> __host__ __device__ constexpr int pvec() { return kPR * PW / 4 / kPThreads; }           // float4 per thread per chunk
+template <int PW> __host__ __device__ constexpr int psmem() { return 2 * kPR * PW * (int)sizeof(float); }  // double-buffered strip
+constexpr int kPTargetCtas = 148 * 3 * 4;   // below this, the rows are split into segments
 constexpr double kFix = 4294967296.0;   // 2^32
 
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int rows,
@@ -128,12 +136,16 @@ struct WalkArgs {
     bool vec;       // float4 staging allowed (16-byte aligned rows)
 };
 
-// Walk all rows of one array for the rays of the masked angles.
+// Walk the 16-row chunks [c_lo, c_hi) of one array for the rays of the
+// masked angles.  Only the band of each chunk is staged.
+template <int kPW>
 __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 acc[2],
-                                          float (*strip)[kPR][kPW], int *L0_s, int *H_s) {
+                                          float (*strip)[kPR][kPW], int *L0_s, int *H_s, int c_lo, int c_hi) {
+    constexpr int kPVec = pvec<kPW>();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int asub = lane >> 4;
-    const int n_chunks = (w.R + kPR - 1) / kPR;
+    const int n_chunks = c_hi - c_lo;       // chunks of this pass; chunk k is c_lo + k
+    if (n_chunks <= 0) return;
     long long X64[kPRays];          // x* + 1/2 at row 0, 32.32
     float aa[kPRays], t1[kPRays], c1[kPRays];
     bool act[kPRays];
@@ -147,14 +159,14 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         c1[k] = act[k] ? 1.0f : 0.0f;
     }
     float4 pre[kPVec];
-    auto load = [&](int c, int slot) {   // chunk c -> registers
-        const int r0 = c * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[slot];
+    auto load = [&](int k, int slot) {   // chunk c_lo + k -> registers (band columns only)
+        const int r0 = (c_lo + k) * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[slot], width = H_s[slot] - L0 + 4;
 #pragma unroll
         for (int v = 0; v < kPVec; ++v) {
             const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
             const int j = L0 + col;
             float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (rr < nr) {
+            if (rr < nr && col < width) {
                 const float *row = w.M + (size_t)(r0 + rr) * w.C;
                 if (w.vec) {
                     if (j >= 0 && j + 3 < w.C) val = __ldg(reinterpret_cast<const float4 *>(row + j));
@@ -168,17 +180,18 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
             pre[v] = val;
         }
     };
-    auto commit = [&](int sbuf) {
+    auto commit = [&](int sbuf, int slot) {
+        const int width = H_s[slot] - L0_s[slot] + 4;
 #pragma unroll
         for (int v = 0; v < kPVec; ++v) {
             const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
-            *reinterpret_cast<float4 *>(&strip[sbuf][rr][col]) = pre[v];
+            if (col < width) *reinterpret_cast<float4 *>(&strip[sbuf][rr][col]) = pre[v];
         }
     };
-    auto band = [&](int c, int slot) {
+    auto band = [&](int k, int slot) {
         if (warp == 0) {
             int L0, H;
-            const int r0 = c * kPR;
+            const int r0 = (c_lo + k) * kPR;
             chunk_band(rg, mask, w.b0, w.bhi, r0, min(r0 + kPR, w.R) - 1, L0, H);
             if (lane == 0) { L0_s[slot] = L0; H_s[slot] = H; }
         }
@@ -188,7 +201,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     if (n_chunks > 1) band(1, 1);
     __syncthreads();
     load(0, 0);
-    commit(0);
+    commit(0, 0);
     __syncthreads();
     const float2 m15 = make_float2(-1.5f, -1.5f);
     for (int c = 0; c < n_chunks; ++c) {
@@ -196,23 +209,28 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         const bool more = c + 1 < n_chunks;
         if (more) load(c + 1, (c + 1) % 3);
         if (c + 2 < n_chunks) band(c + 2, (c + 2) % 3);
-        const int r0 = c * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[c % 3];
-        // chunk anchors: x* + 1/2 - L0 in 9.23 fixed point (0 < value < 2^31)
+        const int r0 = (c_lo + c) * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[c % 3];
+        // chunk anchors: x* + 1/2 - L0 in fixed point with kFrac fraction bits
+        // (9.23 for 256-column bands, 10.22 for 512; 0 < value < 2^31);
+        // re-anchored from the exact 32.32 value at every chunk, so 16 rounded
+        // row steps add at most 2e-6 bins
+        constexpr int kFrac = kPW <= 256 ? 23 : 22;
         int x32[kPRays], r32[kPRays];
 #pragma unroll
         for (int k = 0; k < kPRays; ++k) {
             const long long rho = rg[asub + 2 * k].rho;
             const long long rel = X64[k] - (long long)r0 * rho - ((long long)L0 << 32);
-            x32[k] = act[k] ? (int)(rel >> 9) : (3 << 23);
-            r32[k] = act[k] ? (int)((rho + 256) >> 9) : 0;
+            x32[k] = act[k] ? (int)(rel >> (32 - kFrac)) : (3 << kFrac);
+            r32[k] = act[k] ? (int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0;
         }
         const float *S = &strip[cur][0][0];
         for (int rr = 0; rr < nr; ++rr, S += kPW) {
             float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
 #pragma unroll
             for (int k = 0; k < kPRays; ++k) {
-                const float *q = S + (x32[k] >> 23) - 1;
-                v[k] = __int_as_float((x32[k] & 0x7FFFFF) | 0x3F800000);   // 1 + frac in [1, 2)
+                const float *q = S + (x32[k] >> kFrac) - 1;
+                const int fr = x32[k] & ((1 << kFrac) - 1);
+                v[k] = __int_as_float((kFrac == 23 ? fr : fr << 1) | 0x3F800000);   // 1 + frac in [1, 2)
                 q0[k] = q[0];
                 q1[k] = q[1];
                 q2[k] = q[2];
@@ -231,18 +249,21 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                 acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
             }
         }
-        if (more) commit(cur ^ 1);
+        if (more) commit(cur ^ 1, (c + 1) % 3);
         __syncthreads();
     }
 }
 
-// One CTA: angles [g0, g0 + 8) x bins [b0, b0 + 128) of one slice; img/imgT
-// are that slice's image and its transpose, sino its sinogram.
+// One CTA: angles [g0, g0 + 8) x bins [b0, b0 + 128) of one slice, rows of
+// segment seg of nseg; img/imgT are that slice's image and its transpose,
+// sino its sinogram (or the segment's partial sinogram).
+template <int kPW>
 __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, const float *__restrict__ img,
                                          const float *__restrict__ imgT, float *__restrict__ sino, int n_angles,
                                          int n_bins, int nx, int ny, double cx, double cy, float scale, int g0,
-                                         int b0) {
-    __shared__ __align__(16) float strip[2][kPR][kPW];
+                                         int b0, int seg = 0, int nseg = 1) {
+    extern __shared__ __align__(16) float proj_smem[];
+    float (*strip)[kPR][kPW] = reinterpret_cast<float (*)[kPR][kPW]>(proj_smem);
     __shared__ RayGeom rg[kPG];
     __shared__ int L0_s[3], H_s[3];
     __shared__ int phase_mask[2], fits_s;
@@ -298,9 +319,11 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
         }
         __syncthreads();
         const int gs = fits_s;
+        const int nch = (w.R + kPR - 1) / kPR, per = (nch + nseg - 1) / nseg;
+        const int c_lo = seg * per, c_hi = min(nch, c_lo + per);
         for (int s0 = 0; s0 < kPG; s0 += gs) {
             const int m = mask_all & (((1 << gs) - 1) << s0);
-            if (m) walk_pass(w, rg, m, acc, strip, L0_s, H_s);
+            if (m) walk_pass(w, rg, m, acc, strip, L0_s, H_s, c_lo, c_hi);
         }
         __syncthreads();
     }
@@ -314,22 +337,38 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
     }
 }
 
+// blockIdx.z = slice * nseg + segment; with nseg > 1 the output is the
+// partial sinogram of the segment, part[slice][segment][angle][bin].
+template <int PW>
 __global__ void __launch_bounds__(kPThreads, 3)
 proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
             float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
-            float scale) {
-    const size_t img_off = (size_t)blockIdx.z * nx * ny;
-    proj_cta(tab, img + img_off, imgT + img_off, sino + (size_t)blockIdx.z * n_angles * n_bins, n_angles, n_bins,
-             nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB);
+            float scale, int nseg) {
+    const int slice = blockIdx.z / nseg, seg = blockIdx.z % nseg;
+    const size_t img_off = (size_t)slice * nx * ny;
+    proj_cta<PW>(tab, img + img_off, imgT + img_off, sino + (size_t)blockIdx.z * n_angles * n_bins, n_angles, n_bins,
+                 nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB, seg, nseg);
+}
+
+// sino[s][k] = sum over segments (in order) of part[s][seg][k]
+__global__ void proj_reduce_kernel(const float *__restrict__ part, float *__restrict__ sino, size_t per_slice,
+                                   int nseg) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= per_slice) return;
+    const float *p = part + (size_t)blockIdx.y * nseg * per_slice + k;
+    float acc = 0.0f;
+    for (int g = 0; g < nseg; ++g) acc += p[(size_t)g * per_slice];
+    sino[(size_t)blockIdx.y * per_slice + k] = acc;
 }
 
 // Mixed batch: CTA k projects angle group items[k].z, bin block items[k].y of slice items[k].x.
+template <int PW>
 __global__ void __launch_bounds__(kPThreads, 3)
 proj_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
-    proj_cta(s.tab, s.proj_in, s.proj_inT, s.proj_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy, s.pixel_size,
-             it.z * kPG, it.y * kPB);
+    proj_cta<PW>(s.tab, s.proj_in, s.proj_inT, s.proj_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
+                 s.pixel_size, it.z * kPG, it.y * kPB);
 }
 
 // Mixed batch transpose: CTA k moves 32 x 32 tile (items[k].y, items[k].z) of slice items[k].x.
@@ -352,6 +391,28 @@ __global__ void transpose_batch_kernel(const BatchSlice *__restrict__ slices, co
 
 }  // namespace
 
+// Sparse angle sets (image size / number of angles > 2) take the 512-column
+// staging buffer: their 8-angle bands rarely fit 256 columns.
+bool project_wide(int nx, int ny, int n_angles) { return (double)std::max(nx, ny) > 2.0 * n_angles; }
+
+int set_proj_attr() {
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
+    if (dev >= 0 && dev < 64 && done[dev]) return PYHST_OK;
+    if (cudaFuncSetAttribute(proj_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<256>()) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(proj_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<512>()) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(proj_batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<256>()) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(proj_batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<512>()) !=
+            cudaSuccess)
+        return cuda_status("projection kernel shared-memory attribute");
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return PYHST_OK;
+}
+
 int proj_blocks(int n_angles, int n_bins, int *nb, int *na) {
     *nb = (n_bins + kPB - 1) / kPB;
     *na = (n_angles + kPG - 1) / kPG;
@@ -359,20 +420,43 @@ int proj_blocks(int n_angles, int n_bins, int *nb, int *na) {
 }
 
 int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
-                         const int4 *tr_items, int n_tr_items, cudaStream_t st) {
+                         const int4 *tr_items, int n_tr_items, bool wide, cudaStream_t st) {
     if (n_tr_items > 0) {
         transpose_batch_kernel<<<n_tr_items, dim3(32, 8), 0, st>>>(slices, tr_items);
         int rc = cuda_status("batched transpose kernel");
         if (rc) return rc;
     }
     if (n_proj_items <= 0) return PYHST_OK;
+    int rc = set_proj_attr();
+    if (rc) return rc;
     ProfScope prof(kProfProject, st);
-    proj_batch_kernel<<<n_proj_items, kPThreads, 0, st>>>(slices, proj_items);
+    if (wide)
+        proj_batch_kernel<512><<<n_proj_items, kPThreads, psmem<512>(), st>>>(slices, proj_items);
+    else
+        proj_batch_kernel<256><<<n_proj_items, kPThreads, psmem<256>(), st>>>(slices, proj_items);
     return cuda_status("batched projection kernel");
 }
 
+// Row segments of one launch: enough CTAs to fill the GPU a few times, at
+// least 4 chunks (64 rows) per segment.
+int proj_segments(const pyhst_geometry *g) {
+    const long ctas = (long)((g->n_bins + kPB - 1) / kPB) * ((g->n_angles + kPG - 1) / kPG) * g->n_slices;
+    if (ctas >= kPTargetCtas) return 1;
+    const int cap = std::max(1, std::min(g->nx, g->ny) / (kPR * 4));
+    const int zcap = std::max(1, 65535 / std::max(1, g->n_slices));
+    return (int)std::max(1L, std::min<long>({(kPTargetCtas + ctas - 1) / ctas, (long)cap, (long)zcap}));
+}
+
+// Transposed image, then (with row segments) the partial sinograms; the
+// partials of a 1-slice call fit too, since callers also project single
+// slices of their geometry.
 size_t project_scratch_bytes(const pyhst_geometry *g) {
-    return align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices);
+    pyhst_geometry g1 = *g;
+    g1.n_slices = 1;
+    const int ns = proj_segments(g), n1 = proj_segments(&g1);
+    const size_t part = std::max((size_t)(ns > 1 ? ns : 0) * g->n_slices, (size_t)(n1 > 1 ? n1 : 0)) *
+                        (size_t)g->n_angles * g->n_bins;
+    return align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices) + align_up(sizeof(float) * part);
 }
 
 int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
@@ -382,11 +466,27 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     transpose_kernel<<<tg, tb, 0, st>>>(img, xt, g->ny, g->nx);
     int rc = cuda_status("transpose kernel");
     if (rc) return rc;
-    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG, g->n_slices);
-    ProfScope prof(kProfProject, st);
-    proj_kernel<<<grid, kPThreads, 0, st>>>(tab, img, xt, sino, g->n_angles, g->n_bins, g->nx, g->ny, g->cx,
-                                            g->cy, scale);
-    return cuda_status("projection kernel");
+    if ((rc = set_proj_attr())) return rc;
+    const int nseg = proj_segments(g);
+    float *part = xt + align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices) / sizeof(float);
+    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG, g->n_slices * nseg);
+    {
+        ProfScope prof(kProfProject, st);
+        float *dst = nseg > 1 ? part : sino;
+        if (project_wide(g->nx, g->ny, g->n_angles))
+            proj_kernel<512><<<grid, kPThreads, psmem<512>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
+                                                                    g->ny, g->cx, g->cy, scale, nseg);
+        else
+            proj_kernel<256><<<grid, kPThreads, psmem<256>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
+                                                                    g->ny, g->cx, g->cy, scale, nseg);
+    }
+    if ((rc = cuda_status("projection kernel"))) return rc;
+    if (nseg > 1) {
+        const size_t per = (size_t)g->n_angles * g->n_bins;
+        proj_reduce_kernel<<<dim3((unsigned)((per + 255) / 256), g->n_slices), 256, 0, st>>>(part, sino, per, nseg);
+        rc = cuda_status("projection segment sum");
+    }
+    return rc;
 }
 
 }  // namespace pyhst
@@ -403,7 +503,7 @@ extern "C" int pyhst_project(const pyhst_geometry *g, const float *img, float *s
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     Carver cv(workspace, ws_bytes);
     AngleInfo *tab = cv.take<AngleInfo>(g->n_angles);
-    float *xt = cv.take<float>((size_t)g->nx * g->ny * g->n_slices);
+    float *xt = cv.take<float>(project_scratch_bytes(g) / sizeof(float));
     if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, tab, st))) return rc;
     return launch_project(g, tab, img, sino, g->pixel_size, xt, st);
 }

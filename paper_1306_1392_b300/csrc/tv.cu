@@ -40,7 +40,7 @@ TvLayout tv_layout(const pyhst_geometry *g) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     l.tab = take(sizeof(AngleInfo) * g->n_angles);
-    l.xt = take(sizeof(float) * N * S);
+    l.xt = take(project_scratch_bytes(g));
     for (auto &o : l.img) o = take(sizeof(float) * N * S);
     for (auto &o : l.sino) o = take(sizeof(float) * M * S);
     l.scal = take(sizeof(double) * 4 * S);

@@ -286,6 +286,9 @@ struct Plan {
     std::vector<size_t> img_off, sino_off;      // per slice, in floats
     size_t img_total = 0, sino_total = 0;
     std::vector<int> px_first, sn_first;
+    // projector items of slices that take the 256-column variant come first
+    // (each slice uses the variant of its single-slice solve)
+    int proj_narrow = 0, proj_r_narrow = 0;
 };
 
 size_t up4(size_t v) { return (v + 63) / 64 * 64; }   // 256-byte multiples of floats
@@ -341,6 +344,12 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
         add_items(P, s, g, false);
     }
     for (int r : P.reps) add_items(P, r, items[r].geom, true);
+    auto narrow = [&](const int4 &it) {
+        const pyhst_geometry &g = items[it.x].geom;
+        return !project_wide(g.nx, g.ny, g.n_angles);
+    };
+    P.proj_narrow = (int)(std::stable_partition(P.proj.begin(), P.proj.end(), narrow) - P.proj.begin());
+    P.proj_r_narrow = (int)(std::stable_partition(P.proj_r.begin(), P.proj_r.end(), narrow) - P.proj_r.begin());
     return P;
 }
 
@@ -507,18 +516,25 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     const dim3 tb(kBT);
 
     // ---- step size: power iteration on the representatives, or the caller's L
+    if ((rc = set_proj_attr())) return rc;
+    // projector: the 256-column items, then the 512-column items
+    auto project = [&](const BatchSlice *D, size_t o_items, int n_items, int n_narrow, size_t o_tr, int n_tr) {
+        int r = launch_project_batch(D, I + o_items, n_narrow, I + o_tr, n_tr, false, st);
+        if (!r) r = launch_project_batch(D, I + o_items + n_narrow, n_items - n_narrow, nullptr, 0, true, st);
+        return r;
+    };
     if (opts->lipschitz == 0.0) {
         const int npxr = (int)P.px_r.size(), nsnr = (int)P.sn_r.size();
         b_fill_v<<<npxr, tb, 0, st>>>(T, I + o_pxr);
         for (int it = 0; it < opts->n_power_iter; ++it) {
-            if ((rc = launch_project_batch(D_pow, I + o_projr, (int)P.proj_r.size(), I + o_trr, (int)P.tr_r.size(), st)))
+            if ((rc = project(D_pow, o_projr, (int)P.proj_r.size(), P.proj_r_narrow, o_trr, (int)P.tr_r.size())))
                 return rc;
             if ((rc = launch_backproject_batch(D_pow, I + o_bpr, (int)P.bp_r.size(), false, st))) return rc;
             b_sqnorm_g<<<npxr, tb, 0, st>>>(T, I + o_pxr, part_px);
             b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_px, sc, 0);
             b_scale_v<<<npxr, tb, 0, st>>>(T, I + o_pxr, sc);
         }
-        if ((rc = launch_project_batch(D_pow, I + o_projr, (int)P.proj_r.size(), I + o_trr, (int)P.tr_r.size(), st)))
+        if ((rc = project(D_pow, o_projr, (int)P.proj_r.size(), P.proj_r_narrow, o_trr, (int)P.tr_r.size())))
             return rc;
         b_sqnorm_axa<<<nsnr, tb, 0, st>>>(T, I + o_snr, part_sn);
         b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_sn, sc, 1);
@@ -530,7 +546,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     // ---- start
     b_copy_x<<<npx, tb, 0, st>>>(T, I + o_px, opts->warm_start ? 1 : 0, 0);
     if (opts->warm_start)
-        if ((rc = launch_project_batch(D_init, I + o_proj, npr, I + o_tr, ntr, st))) return rc;
+        if ((rc = project(D_init, o_proj, npr, P.proj_narrow, o_tr, ntr))) return rc;
     b_copy_sino_start<<<nsn, tb, 0, st>>>(T, I + o_sn, opts->warm_start ? 1 : 0);
     if ((rc = cuda_status("batch start"))) return rc;
 
@@ -559,7 +575,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
             pp = (Lc & 1) ? 0 : 1;
         }
         b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, pp, par, identity);
-        rc = launch_project_batch(par ? D_odd : D_even, I + o_proj, npr, I + o_tr, ntr, st);
+        rc = project(par ? D_odd : D_even, o_proj, npr, P.proj_narrow, o_tr, ntr);
         if (rc) break;
         double w = 0.0;
         if (opts->use_fista) {

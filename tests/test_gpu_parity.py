@@ -53,6 +53,7 @@ CASES = [
     (1, 64, 64, 64, "zero", 0.0, 2),              # single angle
     (64, 96, 160, 40, "wide", -2.7, 3),           # angles beyond pi, negative angles
     (33, 300, 129, 257, "random", 10.0, 4),
+    (30, 1100, 1024, 1024, "random", 1.5, 5),     # few angles, large image: rows split into 16 segments
 ]
 
 
