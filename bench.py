@@ -296,7 +296,7 @@ def run_learned_prox(dev, n_eval=64):
 
 
 # ------------------------------------------------------------------ overlapping-patch prior
-def run_patch_study(n=2048, na=150, m=8, stride=4, k=12, n_iter=100, betas=(3e-4, 1e-3, 3e-3)):
+def run_patch_study(n=2048, na=150, m=8, stride=4, k=12, n_iter=400, betas=(3e-4, 1e-3, 3e-3)):
     """The paper's validation setting for the patch prior: a 2048^2 phantom
     (seeded foam), 150 projections, Gaussian white noise on the line
     integrals (sigma = 1 % of their maximum); 8x8 patches on a stride-4 grid,

@@ -3,14 +3,14 @@
 // with L1 shrinkage on the coefficients.
 //
 // Per gradient evaluation at coefficients W [N][n_atoms]:
-//   synth_kernel     P = W D                          (N x m^2, float32 sums)
+//   gemm_kernel      P = W D                          (N x m^2, float32 sums)
 //   image_kernel     x_j = P[core(j)][j - r], S_j = sum of covering patches,
 //                    Nv_j = their number
 //   (projector)      R = Pi^T (Pi x - y)  (or x - y for denoising)
 //   paux_kernel      P'_{p,i} = rho (P_{p,i} - x_{r_p+i})
 //                               + [core(r_p+i) = p] (R + rho (Nv x - S))_{r_p+i},
 //                    and the penalty sum_p sum_i (x_{r_p+i} - P_{p,i})^2
-//   gcoef_kernel     G = 2 P' D^T
+//   gemm_kernel      G = 2 P' D^T
 // Energies and norms are float64 block partials summed in a fixed order.
 #include <cmath>
 #include <vector>
@@ -22,6 +22,10 @@ namespace {
 
 constexpr int kPT = 256;            // threads of the element kernels
 constexpr int kPBlocks = 296;       // fixed grid of the reductions (partials are summed in order)
+constexpr int kPauxBlocks = 1184;   // fixed grid of the auxiliary-patch kernel (gathers: more warps in flight)
+// partial sums: data term, penalty, L1 norm, dot products
+constexpr int kOffData = 0, kOffPen = kPBlocks, kOffL1 = kOffPen + kPauxBlocks, kOffDot = kOffL1 + kPBlocks;
+constexpr int kPartTotal = kOffDot + kPBlocks;
 
 struct PDims {
     int ny, nx, m, stride, kr, kc, N, nc, mm;
@@ -65,15 +69,55 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-// P[p][i] = sum_t W[p][t] D[t][i]; one thread per output, i fastest.
-__global__ void synth_kernel(const float *__restrict__ W, const float *__restrict__ D, float *__restrict__ P, PDims d) {
-    const size_t o = (size_t)blockIdx.x * kPT + threadIdx.x;
-    if (o >= (size_t)d.N * d.mm) return;
-    const int p = (int)(o / d.mm), i = (int)(o % d.mm);
-    const float *w = W + (size_t)p * d.nc;
-    float acc = 0.0f;
-    for (int t = 0; t < d.nc; ++t) acc = fmaf(w[t], D[(size_t)t * d.mm + i], acc);
-    P[o] = acc;
+// C [M][N] = alpha A [M][K] B [K][N] (row-major, float32 sums in k order):
+// 64 x 64 output tiles, K in chunks of 16 staged in shared memory, each
+// thread 4 x 4 outputs.  Both patch products use it: P = W D (M = patches,
+// K = atoms, N = m^2) and G = 2 P' D^T (K = m^2, N = atoms).
+constexpr int kGT = 64, kGK = 16;
+
+__global__ void __launch_bounds__(256) gemm_kernel(const float *__restrict__ A, const float *__restrict__ B,
+                                                   float *__restrict__ C, int M, int N, int K, float alpha) {
+    __shared__ __align__(16) float As[kGK][kGT];     // A chunk, transposed: As[k][row]
+    __shared__ __align__(16) float Bs[kGK][kGT];
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kGK) {
+        for (int e = tid; e < kGT * kGK; e += 256) {
+            const int r = e / kGK, k = e % kGK;          // A: consecutive threads along k
+            const int gm = m0 + r, gk = k0 + k;
+            As[k][r] = (gm < M && gk < K) ? A[(size_t)gm * K + gk] : 0.0f;
+            const int kb = e / kGT, c = e % kGT;         // B: consecutive threads along n
+            const int gkb = k0 + kb, gn = n0 + c;
+            Bs[kb][c] = (gkb < K && gn < N) ? B[(size_t)gkb * N + gn] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kGK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][4 * tr]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][4 * tc]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + 4 * tr + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + 4 * tc + j;
+            if (gn < N) C[(size_t)gm * N + gn] = alpha * acc[i][j];
+        }
+    }
+}
+
+void gemm(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
+    gemm_kernel<<<dim3((M + kGT - 1) / kGT, (N + kGT - 1) / kGT), 256, 0, st>>>(A, B, C, M, N, K, alpha);
 }
 
 // Eq. 7 and the patch sums: one thread per pixel.
@@ -121,18 +165,21 @@ __global__ void diff_kernel(const float *__restrict__ a, const float *__restrict
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// The auxiliary patches P' of Algorithm 1 and the penalty partials.
+// The auxiliary patches P' of Algorithm 1 and the penalty partials.  A
+// block takes 256 / m^2 patches at a time (thread: one pixel of one patch).
 __global__ void paux_kernel(const float *__restrict__ P, const float *__restrict__ X, const float *__restrict__ R,
                             const float *__restrict__ S, const float *__restrict__ Nv, const int *__restrict__ core_r,
                             const int *__restrict__ core_c, PDims d, float rho, float *__restrict__ Pp,
                             double *__restrict__ part) {
     double acc = 0.0;
-    const size_t total = (size_t)d.N * d.mm;
-    for (size_t o = (size_t)blockIdx.x * kPT + threadIdx.x; o < total; o += (size_t)gridDim.x * kPT) {
-        const int p = (int)(o / d.mm), i = (int)(o % d.mm);
+    const int ppb = kPT / d.mm;                       // patches per pass of a block (m <= 16)
+    const int i = threadIdx.x % d.mm, sub = threadIdx.x / d.mm;
+    const int di = i / d.m, dj = i % d.m;
+    for (int p = blockIdx.x * ppb + sub; sub < ppb && p < d.N; p += gridDim.x * ppb) {
+        const size_t o = (size_t)p * d.mm + i;
         const int a = p / d.kc, b = p % d.kc;
-        const int rr = axis_start(a, d.ny, d.m, d.stride) + i / d.m;
-        const int cc = axis_start(b, d.nx, d.m, d.stride) + i % d.m;
+        const int rr = axis_start(a, d.ny, d.m, d.stride) + di;
+        const int cc = axis_start(b, d.nx, d.m, d.stride) + dj;
         const size_t j = (size_t)rr * d.nx + cc;
         const float x = X[j], pv = P[o];
         float v = rho * (pv - x);
@@ -145,17 +192,6 @@ __global__ void paux_kernel(const float *__restrict__ P, const float *__restrict
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
-}
-
-// G[p][t] = 2 sum_i P'[p][i] D[t][i]; Dt = D^T [mm][nc]; one thread per output.
-__global__ void gcoef_kernel(const float *__restrict__ Pp, const float *__restrict__ Dt, PDims d, float *__restrict__ G) {
-    const size_t o = (size_t)blockIdx.x * kPT + threadIdx.x;
-    if (o >= (size_t)d.N * d.nc) return;
-    const int p = (int)(o / d.nc), t = (int)(o % d.nc);
-    const float *pp = Pp + (size_t)p * d.mm;
-    float acc = 0.0f;
-    for (int i = 0; i < d.mm; ++i) acc = fmaf(pp[i], Dt[(size_t)i * d.nc + t], acc);
-    G[o] = 2.0f * acc;
 }
 
 __global__ void transpose_kernel(const float *__restrict__ D, float *__restrict__ Dt, int nc, int mm) {
@@ -181,16 +217,16 @@ __global__ void finalize_kernel(const double *__restrict__ part, int n, double s
     if (threadIdx.x == 0) *out = acc * scale;
 }
 
-// f = data + rho pen (+ beta l1 when l1 != NULL) into out[slot]
-__global__ void energy_kernel(const double *__restrict__ pd, const double *__restrict__ pp,
-                              const double *__restrict__ pl, int n, double rho, double beta,
+// f = data + rho pen (+ beta l1 when with_l1) into *out; part holds the
+// partials at kOffData, kOffPen, kOffL1
+__global__ void energy_kernel(const double *__restrict__ part, bool with_l1, double rho, double beta,
                               double *__restrict__ out) {
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int k = threadIdx.x; k < n; k += kPT) {
-        a += pd[k];
-        b += pp[k];
-        if (pl) c += pl[k];
+    for (int k = threadIdx.x; k < kPBlocks; k += kPT) {
+        a += part[kOffData + k];
+        if (with_l1) c += part[kOffL1 + k];
     }
+    for (int k = threadIdx.x; k < kPauxBlocks; k += kPT) b += part[kOffPen + k];
     a = block_sum(a);
     b = block_sum(b);
     c = block_sum(c);
@@ -253,7 +289,7 @@ struct PCtx {
     int *core_r, *core_c;
     float *P, *Pp, *X, *R, *S, *Nv, *Dt, *sdata, *xt, *zero, *Y, *Wold, *G, *V;
     AngleInfo *tab;
-    double *part;      // [4][kPBlocks]
+    double *part;      // [kPartTotal]
     PScal sc;
     size_t M;          // data size
 };
@@ -302,7 +338,7 @@ PLayout playout(const PDims &d, const pyhst_geometry *g) {
     l.Wold = take(coef);
     l.G = take(coef);
     l.V = take(coef);
-    l.part = take(sizeof(double) * 4 * kPBlocks);
+    l.part = take(sizeof(double) * kPartTotal);
     l.scal = take(64);
     l.bytes = off;
     return l;
@@ -356,8 +392,7 @@ int blocks_for(size_t n) { return (int)std::min<size_t>((n + kPT - 1) / kPT, 1u 
 
 // P = W D and the image (Eq. 7), patch sums and cover counts.
 int synth_image(PCtx &c, const float *W, cudaStream_t st) {
-    const size_t np = (size_t)c.d.N * c.d.mm;
-    synth_kernel<<<blocks_for(np), kPT, 0, st>>>(W, c.pp->dict, c.P, c.d);
+    gemm(W, c.pp->dict, c.P, c.d.N, c.d.mm, c.d.nc, 1.0f, st);
     image_kernel<<<blocks_for((size_t)c.d.ny * c.d.nx), kPT, 0, st>>>(c.P, c.core_r, c.core_c, c.d, c.X, c.S, c.Nv);
     return cuda_status("patch synthesis");
 }
@@ -376,9 +411,9 @@ int evaluate(PCtx &c, const float *W, const float *y, float *G, cudaStream_t st)
     } else {
         diff_kernel<<<kPBlocks, kPT, 0, st>>>(c.X, y, c.R, c.M, c.part);
     }
-    paux_kernel<<<kPBlocks, kPT, 0, st>>>(c.P, c.X, c.R, c.S, c.Nv, c.core_r, c.core_c, c.d, c.pp->rho,
-                                         G ? c.Pp : nullptr, c.part + kPBlocks);
-    if (G) gcoef_kernel<<<blocks_for((size_t)c.d.N * c.d.nc), kPT, 0, st>>>(c.Pp, c.Dt, c.d, G);
+    paux_kernel<<<kPauxBlocks, kPT, 0, st>>>(c.P, c.X, c.R, c.S, c.Nv, c.core_r, c.core_c, c.d, c.pp->rho,
+                                            G ? c.Pp : nullptr, c.part + kOffPen);
+    if (G) gemm(c.Pp, c.Dt, G, c.d.N, c.d.nc, c.d.mm, 2.0f, st);
     return cuda_status("patch gradient");
 }
 
@@ -445,7 +480,7 @@ extern "C" int pyhst_patch_gradient(const pyhst_patch_problem *pp, const pyhst_g
     PCtx c;
     if ((rc = prepare(pp, g, workspace, st, c))) return rc;
     if ((rc = evaluate(c, W, y, G, st))) return rc;
-    if (f_out) energy_kernel<<<1, kPT, 0, st>>>(c.part, c.part + kPBlocks, nullptr, kPBlocks, pp->rho, 0.0, f_out);
+    if (f_out) energy_kernel<<<1, kPT, 0, st>>>(c.part, false, pp->rho, 0.0, f_out);
     return cuda_status("patch energy");
 }
 
@@ -472,14 +507,14 @@ extern "C" int pyhst_patch_solve(const pyhst_patch_problem *pp, const pyhst_geom
         fill_f<<<kPBlocks, kPT, 0, st>>>(c.V, 1.0f, nw);
         for (int it = 0; it < n_power_iter; ++it) {
             if ((rc = evaluate(c, c.V, c.zero, c.G, st))) return rc;
-            dot_kernel<<<kPBlocks, kPT, 0, st>>>(c.G, c.G, nw, c.part + 2 * kPBlocks);
-            finalize_kernel<<<1, kPT, 0, st>>>(c.part + 2 * kPBlocks, kPBlocks, 1.0, c.sc.acc);
+            dot_kernel<<<kPBlocks, kPT, 0, st>>>(c.G, c.G, nw, c.part + kOffDot);
+            finalize_kernel<<<1, kPT, 0, st>>>(c.part + kOffDot, kPBlocks, 1.0, c.sc.acc);
             pnorm_kernel<<<kPBlocks, kPT, 0, st>>>(c.G, c.V, nw, c.sc.acc);
         }
         // Rayleigh quotient <v, H v> with ||v|| = 1
         if ((rc = evaluate(c, c.V, c.zero, c.G, st))) return rc;
-        dot_kernel<<<kPBlocks, kPT, 0, st>>>(c.V, c.G, nw, c.part + 2 * kPBlocks);
-        finalize_kernel<<<1, kPT, 0, st>>>(c.part + 2 * kPBlocks, kPBlocks, 1.0, c.sc.acc + 1);
+        dot_kernel<<<kPBlocks, kPT, 0, st>>>(c.V, c.G, nw, c.part + kOffDot);
+        finalize_kernel<<<1, kPT, 0, st>>>(c.part + kOffDot, kPBlocks, 1.0, c.sc.acc + 1);
     }
     set_step_kernel<<<1, 1, 0, st>>>(c.sc.acc + 1, lipschitz, beta, c.sc);
     if (lipschitz_out) cudaMemcpyAsync(lipschitz_out, c.sc.L, sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -497,12 +532,11 @@ extern "C" int pyhst_patch_solve(const pyhst_patch_problem *pp, const pyhst_geom
             w = (t - 1.0) / tn;
             t = tn;
         }
-        fista_update_kernel<<<kPBlocks, kPT, 0, st>>>(W, c.Y, c.Wold, c.G, nw, c.sc, (float)w, c.part + 2 * kPBlocks);
+        fista_update_kernel<<<kPBlocks, kPT, 0, st>>>(W, c.Y, c.Wold, c.G, nw, c.sc, (float)w, c.part + kOffL1);
         if ((rc = cuda_status("patch update"))) return rc;
         if (energy) {
             if ((rc = evaluate(c, W, y, nullptr, st))) return rc;
-            energy_kernel<<<1, kPT, 0, st>>>(c.part, c.part + kPBlocks, c.part + 2 * kPBlocks, kPBlocks, pp->rho,
-                                             (double)beta, energy + k);
+            energy_kernel<<<1, kPT, 0, st>>>(c.part, true, pp->rho, (double)beta, energy + k);
         }
     }
     if (x) {
