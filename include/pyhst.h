@@ -79,7 +79,14 @@ typedef enum {
     PYHST_BF16_SINO = 4  /* bfloat16 sinogram, converted to float32 on load  */
 } pyhst_input_t;
 
-typedef enum { PYHST_RAMLAK = 0 } pyhst_filter_t;
+/* Ramp filters, as spatial kernels h(n) (tau = 1 bin) applied by linear
+ * convolution along detector rows:
+ *   PYHST_RAMLAK       h(0) = 1/4, h(odd n) = -1/(pi n)^2, h(even n) = 0
+ *   PYHST_SHEPP_LOGAN  h(n) = -2 / (pi^2 (4 n^2 - 1))
+ *   PYHST_HANN         Ram-Lak smoothed by (1/4, 1/2, 1/4) (its spectrum times
+ *                      (1 + cos w) / 2)
+ * The paper does not name its filter; Ram-Lak is the default. */
+typedef enum { PYHST_RAMLAK = 0, PYHST_SHEPP_LOGAN = 1, PYHST_HANN = 2 } pyhst_filter_t;
 
 /* Operation selectors of pyhst_workspace_size(). */
 enum { PYHST_OP_FBP = 0, PYHST_OP_BACKPROJECT = 1, PYHST_OP_PROJECT = 2, PYHST_OP_TV_SOLVE = 3 };

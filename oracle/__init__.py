@@ -92,6 +92,18 @@ def ramlak_filter(p):
     return q
 
 
+FILTERS = {"ramlak": 0, "shepp-logan": 1, "hann": 2}
+
+
+def filter_rows(p, kind="ramlak"):
+    """Rows filtered with the spatial kernel of `kind` (ramlak, shepp-logan,
+    hann): q[m] = sum_k h(m-k) p[k]."""
+    p, pp = _c(p)
+    q = np.empty_like(p)
+    lib().orc_filter(pp, I64(p.shape[0]), I64(p.shape[1]), ctypes.c_int(FILTERS[kind]), q.ctypes.data_as(PD))
+    return q
+
+
 def _centre(n, c):
     return (n - 1) / 2.0 if c is None else float(c)
 

@@ -90,6 +90,33 @@ void orc_ramlak_filter(const double *p, int64_t n_rows, int64_t n_bins, double *
         }
 }
 
+/* Other ramp filters (the SURVEYed boundary's later filters), as spatial
+ * kernels of unit bin spacing applied by the same linear convolution:
+ *   kind 1, Shepp-Logan (Kak & Slaney): h(n) = -2 / (pi^2 (4 n^2 - 1));
+ *   kind 2, Hann: the Ram-Lak kernel smoothed by (1/4, 1/2, 1/4),
+ *           h(n) = h_RL(n)/2 + (h_RL(n-1) + h_RL(n+1))/4.
+ * kind 0 is Ram-Lak. */
+static double filter_kernel(int kind, int64_t n)
+{
+    switch (kind) {
+    case 1: return -2.0 / (M_PI * M_PI * (4.0 * (double)n * (double)n - 1.0));
+    case 2: return 0.5 * ramlak(n) + 0.25 * (ramlak(n - 1) + ramlak(n + 1));
+    default: return ramlak(n);
+    }
+}
+
+void orc_filter(const double *p, int64_t n_rows, int64_t n_bins, int kind, double *q)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n_rows; r++)
+        for (int64_t m = 0; m < n_bins; m++) {
+            double acc = 0.0;
+            for (int64_t k = 0; k < n_bins; k++)
+                acc += filter_kernel(kind, m - k) * p[r * n_bins + k];
+            q[r * n_bins + m] = acc;
+        }
+}
+
 /* Detector coordinate of pixel (row i, column j) at angle index a. */
 static double coord(int64_t i, int64_t j, double cth, double sth, double axis,
                     double cx, double cy)

@@ -152,9 +152,18 @@ _KINDS = {"u16_raw": (PYHST_U16_RAW, torch.uint16), "f32_raw": (PYHST_F32_RAW, t
           "bf16_sino": (PYHST_BF16_SINO, torch.bfloat16)}
 
 
+_FILTERS = {"ramlak": 0, "shepp-logan": 1, "hann": 2}
+
+
+def _filter_code(name: str) -> int:
+    if name not in _FILTERS:
+        raise ValueError(f"filter must be one of {sorted(_FILTERS)}")
+    return _FILTERS[name]
+
+
 def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
               pad_len: int = 0, out=None, workspace=None, ws_bytes: int = None,
-              slices_per_pass: int = 4, slices: tuple = None) -> torch.Tensor:
+              slices_per_pass: int = 4, slices: tuple = None, filter: str = "ramlak") -> torch.Tensor:
     """Filtered back-projection of every slice in ``data``.
 
     ``layout`` "projections": data [n_angles, n_slices, n_bins] (a raw
@@ -193,7 +202,7 @@ def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=Non
     fptr = ctypes.c_void_p(flat.data_ptr() + z0 * nb * 4) if raw else None
     kptr = ctypes.c_void_p(dark.data_ptr() + z0 * nb * 4) if raw else None
     _check(L.lib.pyhst_fbp(ctypes.byref(g), code, dptr, s_stride, a_stride, fptr, kptr,
-                           PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), nbytes, _stream()))
+                           _filter_code(filter), pad_len, _ptr(out), _ptr(ws), nbytes, _stream()))
     return out
 
 
@@ -212,8 +221,8 @@ def _layout(data, kind, layout):
 
 
 def pyhst_filter(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
-                 pad_len: int = 0, out=None, workspace=None) -> torch.Tensor:
-    """Normalised, Ram-Lak filtered sinograms q [n_slices, n_angles, n_bins]
+                 pad_len: int = 0, out=None, workspace=None, filter: str = "ramlak") -> torch.Tensor:
+    """Normalised, ramp-filtered (``filter``: ramlak, shepp-logan, hann) sinograms q [n_slices, n_angles, n_bins]
     (the first two steps of pyhst_fbp; same data conventions)."""
     code, dt = _KINDS[kind]
     _cuda(data, "data", (dt,))
@@ -226,13 +235,13 @@ def pyhst_filter(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=
     g = geom.c(ns)
     ws = _workspace(L.lib.pyhst_filter_workspace_size(ctypes.byref(g), pad_len), data.device, workspace)
     _check(L.lib.pyhst_filter(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
-                              PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), ws.numel(), _stream()))
+                              _filter_code(filter), pad_len, _ptr(out), _ptr(ws), ws.numel(), _stream()))
     return out
 
 
 def pyhst_fbp_host(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, out=None,
                    layout: str = None, pad_len: int = 0, slices_per_chunk: int = 16, workspace=None,
-                   device=None) -> torch.Tensor:
+                   device=None, filter: str = "ramlak") -> torch.Tensor:
     """pyhst_fbp on HOST tensors (pin them for overlap): chunks are streamed
     through the device by the library.  Returns the host output; the work is
     queued on the current stream (synchronise before reading it)."""
@@ -250,13 +259,13 @@ def pyhst_fbp_host(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dar
     need = L.lib.pyhst_fbp_host_workspace_size(ctypes.byref(g), code, pad_len, slices_per_chunk)
     ws = _workspace(need, device or geom.angles.device, workspace)
     _check(L.lib.pyhst_fbp_host(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
-                                PYHST_RAMLAK, pad_len, _ptr(out), slices_per_chunk, _ptr(ws), ws.numel(),
+                                _filter_code(filter), pad_len, _ptr(out), slices_per_chunk, _ptr(ws), ws.numel(),
                                 _stream()))
     return out
 
 
 def pyhst_fbp_static(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
-                     pad_len: int = 0, out=None) -> torch.Tensor:
+                     pad_len: int = 0, out=None, filter: str = "ramlak") -> torch.Tensor:
     """pyhst_fbp for callers that cannot allocate device scratch: the library
     uses its own fixed device array (see include/pyhst.h); calls that overlap
     on the GPU race on it."""
@@ -270,13 +279,14 @@ def pyhst_fbp_static(geom: Geometry, data: torch.Tensor, kind: str, flat=None, d
     _cuda(out, "out", (torch.float32,))
     g = geom.c(ns)
     _check(L.lib.pyhst_fbp_static(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
-                                  PYHST_RAMLAK, pad_len, _ptr(out), _stream()))
+                                  _filter_code(filter), pad_len, _ptr(out), _stream()))
     return out
 
 
 def pyhst_fbp_pre(geom: Geometry, data: torch.Tensor, kind: str, flats: torch.Tensor, dark: torch.Tensor,
                   flat_pos: torch.Tensor = None, hotspot_threshold: float = 0.0, ring_window: int = 0,
-                  pad_len: int = 0, out=None, workspace=None, slices_per_pass: int = 4) -> torch.Tensor:
+                  pad_len: int = 0, out=None, workspace=None, slices_per_pass: int = 4,
+                  filter: str = "ramlak") -> torch.Tensor:
     """FBP with the preprocessing of Sec. 2.3: data [n_angles, n_slices,
     n_bins] raw counts, flats [n_flats, n_slices, n_bins] (or [n_slices,
     n_bins] for one flat), flat_pos [n_angles] (more than one flat), dark
@@ -301,7 +311,7 @@ def pyhst_fbp_pre(geom: Geometry, data: torch.Tensor, kind: str, flats: torch.Te
     ws = _workspace(L.lib.pyhst_fbp_pre_workspace_size(ctypes.byref(g), pad_len, slices_per_pass), data.device,
                     workspace)
     _check(L.lib.pyhst_fbp_pre(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(dark), ctypes.byref(pre),
-                               PYHST_RAMLAK, pad_len, _ptr(out), _ptr(ws), ws.numel(), _stream()))
+                               _filter_code(filter), pad_len, _ptr(out), _ptr(ws), ws.numel(), _stream()))
     return out
 
 

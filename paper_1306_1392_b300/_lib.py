@@ -22,7 +22,7 @@ PYHST_ERR_TIMEOUT = -4
 PYHST_ERR_NUMERIC = -5
 
 PYHST_U16_RAW, PYHST_F32_RAW, PYHST_F32_SINO, PYHST_F16_SINO, PYHST_BF16_SINO = range(5)
-PYHST_RAMLAK = 0
+PYHST_RAMLAK, PYHST_SHEPP_LOGAN, PYHST_HANN = range(3)
 PYHST_OP_FBP, PYHST_OP_BACKPROJECT, PYHST_OP_PROJECT, PYHST_OP_TV_SOLVE = range(4)
 
 

@@ -19,7 +19,7 @@
 namespace pyhst {
 
 size_t filter_table_bytes(int P);
-int launch_filter_tables(int P, void *tables, cudaStream_t st);
+int launch_filter_tables(int P, int filter, void *tables, cudaStream_t st);
 int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angle_stride, const float *flat,
                   const float *dark, int z0, int n_slices_chunk, int n_angles, int n_bins, int P,
                   const void *tables, float *q, cudaStream_t st);
@@ -53,7 +53,7 @@ struct FbpPlan {
     AngleInfo *tab;
     void *tables;
     float *q;
-    int S, P;
+    int S, P, filter;
 };
 
 static int fbp_plan(const pyhst_geometry *g, int P, void *ws, size_t ws_bytes, FbpPlan *pl) {
@@ -73,7 +73,7 @@ static int fbp_plan(const pyhst_geometry *g, int P, void *ws, size_t ws_bytes, F
 static int fbp_prepare(const pyhst_geometry *g, const FbpPlan &pl, cudaStream_t st) {
     int rc = launch_angle_table(g->angles, g->axis, g->n_angles, pl.tab, st);
     if (rc) return rc;
-    return launch_filter_tables(pl.P, pl.tables, st);
+    return launch_filter_tables(pl.P, pl.filter, pl.tables, st);
 }
 
 // Reconstruct slices [0, g->n_slices) of `data` (z indices relative to data,
@@ -99,7 +99,7 @@ static int check_fbp_args(const pyhst_geometry *g, int kind, const void *data, c
     int rc = check_geometry(g);
     if (rc) return rc;
     if (kind < PYHST_U16_RAW || kind > PYHST_BF16_SINO) return fail(PYHST_ERR_INVALID_ARG, "unknown input kind %d", kind);
-    if (filter != PYHST_RAMLAK) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
+    if (filter < PYHST_RAMLAK || filter > PYHST_HANN) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
     if (!data || !out) return fail(PYHST_ERR_INVALID_ARG, "data/out pointer is NULL");
     const bool raw = kind == PYHST_U16_RAW || kind == PYHST_F32_RAW;
     if (raw && (!flat || !dark)) return fail(PYHST_ERR_INVALID_ARG, "raw input needs flat and dark fields");
@@ -170,6 +170,7 @@ extern "C" int pyhst_fbp(const pyhst_geometry *g, int input_type, const void *da
     if (rc) return rc;
     FbpPlan pl;
     if ((rc = fbp_plan(g, P, workspace, ws_bytes, &pl))) return rc;
+    pl.filter = filter;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if ((rc = fbp_prepare(g, pl, st))) return rc;
     return fbp_run(g, input_type, data, slice_stride, angle_stride, flat, dark, pl, out, st);
@@ -193,7 +194,7 @@ extern "C" int pyhst_filter(const pyhst_geometry *g, int input_type, const void 
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
         return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if ((rc = launch_filter_tables(P, workspace, st))) return rc;
+    if ((rc = launch_filter_tables(P, filter, workspace, st))) return rc;
     // at most 2^30 rows per launch (the kernel's grid is rows / 2)
     const int per = std::max(1, (1 << 30) / g->n_angles);
     for (int z0 = 0; z0 < g->n_slices; z0 += per) {
@@ -237,6 +238,7 @@ extern "C" int pyhst_fbp_host(const pyhst_geometry *g, int input_type, const voi
     const size_t plan_bytes = host_plan_bytes(g, P, S);
     FbpPlan pl;
     if ((rc = fbp_plan(&gs, P, workspace, plan_bytes, &pl))) return rc;
+    pl.filter = filter;
     Carver cv(static_cast<char *>(workspace) + plan_bytes, ws_bytes - plan_bytes);
     char *in[2];
     float *outb[2], *fl[2], *dk[2];

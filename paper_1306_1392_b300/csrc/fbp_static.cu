@@ -27,7 +27,7 @@
 namespace pyhst {
 
 size_t filter_table_bytes(int P);
-int launch_filter_tables(int P, void *tables, cudaStream_t st);
+int launch_filter_tables(int P, int filter, void *tables, cudaStream_t st);
 int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angle_stride, const float *flat,
                   const float *dark, int z0, int n_slices_chunk, int n_angles, int n_bins, int P,
                   const void *tables, float *q, cudaStream_t st);
@@ -74,7 +74,7 @@ extern "C" int pyhst_fbp_static(const pyhst_geometry *g, int input_type, const v
     if (rc) return rc;
     if (input_type < PYHST_U16_RAW || input_type > PYHST_BF16_SINO)
         return fail(PYHST_ERR_INVALID_ARG, "unknown input kind %d", input_type);
-    if (filter != PYHST_RAMLAK) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
+    if (filter < PYHST_RAMLAK || filter > PYHST_HANN) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
     if (!data || !out) return fail(PYHST_ERR_INVALID_ARG, "data/out pointer is NULL");
     const bool raw = input_type == PYHST_U16_RAW || input_type == PYHST_F32_RAW;
     if (raw && (!flat || !dark)) return fail(PYHST_ERR_INVALID_ARG, "raw input needs flat and dark fields");
@@ -98,7 +98,7 @@ extern "C" int pyhst_fbp_static(const pyhst_geometry *g, int input_type, const v
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, tab, st))) return rc;
-    if ((rc = launch_filter_tables(P, tables, st))) return rc;
+    if ((rc = launch_filter_tables(P, filter, tables, st))) return rc;
     const float weight = (float)(M_PI / ((double)g->n_angles * (double)g->pixel_size));
     for (int z0 = 0; z0 < g->n_slices; z0 += S) {
         const int n = std::min(S, g->n_slices - z0);

@@ -1,11 +1,13 @@
-// Flat/dark normalisation fused into the Ram-Lak ramp filter (Sec. 2.3).
+// Flat/dark normalisation fused into the ramp filter (Sec. 2.3).
 //
 // For each detector row (slice z, angle a) the kernel loads the raw values,
 // forms p = -ln((I - D) / (F - D)) (p = 0 where F - D <= 0; ratio clamped
-// below at 1e-6), zero-pads to P, convolves circularly with the Ram-Lak
-// kernel h periodised on [-P/2, P/2) and keeps the first n_bins outputs.  For
-// P >= 2 n_bins this is exactly the linear convolution
-//   q[m] = sum_k h(m - k) p[k],  h(0) = 1/4, h(odd n) = -1/(pi n)^2, h(even n) = 0.
+// below at 1e-6), zero-pads to P, convolves circularly with the filter's
+// spatial kernel h truncated to (-P/2, P/2) and keeps the first n_bins
+// outputs.  For P >= 2 n_bins this is exactly the linear convolution
+//   q[m] = sum_k h(m - k) p[k]
+// (Ram-Lak by default: h(0) = 1/4, h(odd n) = -1/(pi n)^2, h(even n) = 0;
+// Shepp-Logan and Hann below).
 //
 // Two real rows ride in one complex FFT (row A real, row B imaginary); since
 // the filter spectrum H is real and even, the inverse transform returns
@@ -33,13 +35,36 @@ __global__ void twiddle_kernel(int P, float2 *__restrict__ tw, double *__restric
 
 // H[k] = sum_{n=-P/2}^{P/2-1} h(n) cos(2 pi k n / P) = 1/4 + 2 sum_{odd n < P/2} h(n) cos(...)
 // stored at bit-reversed positions with the inverse-FFT factor 1/P folded in.
-__global__ void spectrum_kernel(int P, int logP, const double *__restrict__ costab,
+// Spatial kernels of the filters (tau = 1 bin), even in n:
+//   Ram-Lak      h(0) = 1/4, h(odd n) = -1/(pi n)^2, h(even n != 0) = 0   (DTFT |w| / 2 pi)
+//   Shepp-Logan  h(n) = -2 / (pi^2 (4 n^2 - 1))                           (DTFT |sin(w/2)| / pi)
+//   Hann         h(n) = h_RL(n) / 2 + (h_RL(n - 1) + h_RL(n + 1)) / 4       (DTFT |w| / 2 pi x (1 + cos w) / 2)
+__device__ __forceinline__ double ramlak_h(long long n) {
+    if (n < 0) n = -n;
+    if (n == 0) return 0.25;
+    return (n & 1) ? -1.0 / (M_PI * M_PI * (double)n * (double)n) : 0.0;
+}
+
+__device__ __forceinline__ double filter_h(int filter, long long n) {
+    switch (filter) {
+        case PYHST_SHEPP_LOGAN: return -2.0 / (M_PI * M_PI * (4.0 * (double)n * (double)n - 1.0));
+        case PYHST_HANN: return 0.5 * ramlak_h(n) + 0.25 * (ramlak_h(n - 1) + ramlak_h(n + 1));
+        default: return ramlak_h(n);
+    }
+}
+
+// H[k] = (h(0) + 2 sum_{n=1}^{P/2-1} h(n) cos(2 pi k n / P)) / P in float64:
+// the DFT of the kernel truncated to |n| < P/2 (which is all the linear
+// convolution of n_bins <= P/2 samples uses), with the 1/P of the inverse
+// transform folded in; stored in bit-reversed order.
+__global__ void spectrum_kernel(int P, int logP, int filter, const double *__restrict__ costab,
                                 float *__restrict__ hrev) {
     const int k = blockIdx.x;   // frequency 0..P/2
     double acc = 0.0;
-    for (int n = 1 + 2 * threadIdx.x; n < P / 2; n += 2 * blockDim.x) {
+    const int step = filter == PYHST_RAMLAK ? 2 : 1;   // Ram-Lak: odd n only
+    for (int n = 1 + step * threadIdx.x; n < P / 2; n += step * blockDim.x) {
         const long long m = ((long long)k * n) % P;
-        acc += -1.0 / (M_PI * M_PI * (double)n * (double)n) * costab[m];
+        acc += filter_h(filter, n) * costab[m];
     }
     __shared__ double red[256];
     red[threadIdx.x] = acc;
@@ -49,7 +74,7 @@ __global__ void spectrum_kernel(int P, int logP, const double *__restrict__ cost
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const float H = (float)((0.25 + 2.0 * red[0]) / (double)P);
+        const float H = (float)((filter_h(filter, 0) + 2.0 * red[0]) / (double)P);
         hrev[__brev(k) >> (32 - logP)] = H;
         if (k > 0 && k < P / 2) hrev[__brev(P - k) >> (32 - logP)] = H;
     }
@@ -161,7 +186,7 @@ size_t filter_table_bytes(int P) {
     return align_up(sizeof(float2) * (P / 2)) + align_up(sizeof(double) * P) + align_up(sizeof(float) * P);
 }
 
-int launch_filter_tables(int P, void *tables, cudaStream_t st) {
+int launch_filter_tables(int P, int filter, void *tables, cudaStream_t st) {
     Carver cv(tables, filter_table_bytes(P));
     float2 *tw = cv.take<float2>(P / 2);
     double *costab = cv.take<double>(P);
@@ -171,7 +196,7 @@ int launch_filter_tables(int P, void *tables, cudaStream_t st) {
     twiddle_kernel<<<(P + 255) / 256, 256, 0, st>>>(P, tw, costab);
     int rc = cuda_status("twiddle kernel");
     if (rc) return rc;
-    spectrum_kernel<<<P / 2 + 1, 256, 0, st>>>(P, logP, costab, hrev);
+    spectrum_kernel<<<P / 2 + 1, 256, 0, st>>>(P, logP, filter, costab, hrev);
     return cuda_status("filter spectrum kernel");
 }
 

@@ -20,7 +20,7 @@
 namespace pyhst {
 
 size_t filter_table_bytes(int P);
-int launch_filter_tables(int P, void *tables, cudaStream_t st);
+int launch_filter_tables(int P, int filter, void *tables, cudaStream_t st);
 int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angle_stride, const float *flat,
                   const float *dark, int z0, int n_slices_chunk, int n_angles, int n_bins, int P,
                   const void *tables, float *q, cudaStream_t st);
@@ -172,7 +172,7 @@ extern "C" int pyhst_fbp_pre(const pyhst_geometry *g, int input_type, const void
     if (rc) return rc;
     if (input_type != PYHST_U16_RAW && input_type != PYHST_F32_RAW)
         return fail(PYHST_ERR_INVALID_ARG, "pyhst_fbp_pre needs raw counts (PYHST_U16_RAW or PYHST_F32_RAW)");
-    if (filter != PYHST_RAMLAK) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
+    if (filter < PYHST_RAMLAK || filter > PYHST_HANN) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
     if (!data || !out || !dark || !pre || !pre->flats) return fail(PYHST_ERR_INVALID_ARG, "NULL pointer argument");
     if (pre->n_flats < 1 || (pre->n_flats > 1 && !pre->flat_pos))
         return fail(PYHST_ERR_INVALID_ARG, "n_flats >= 1, and flat_pos is needed for more than one flat");
@@ -198,7 +198,7 @@ extern "C" int pyhst_fbp_pre(const pyhst_geometry *g, int input_type, const void
     float *sbuf = cv.take<float>((size_t)S * g->n_bins);
     float *hp = cv.take<float>((size_t)S * g->n_bins);
     if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, tab, st))) return rc;
-    if ((rc = launch_filter_tables(P, tables, st))) return rc;
+    if ((rc = launch_filter_tables(P, filter, tables, st))) return rc;
 
     PreArgs A;
     A.data = data; A.ss = slice_stride; A.as = angle_stride;

@@ -353,3 +353,23 @@ def test_fbp_pre_flats_hotspots_rings_parity(P, orc, cuda_device):
         ref = orc.backproject(orc.ramlak_filter(p[z]), vol.angles.double().numpy(), vol.axis.double().numpy(), n, n,
                               orc.fbp_weight(na, vol.pixel_size))
         close(f64(got[z]), ref)
+
+
+@pytest.mark.parametrize("filt", ["shepp-logan", "hann", "ramlak"])
+@pytest.mark.parametrize("pad", [0, 2048])
+def test_fbp_filters(P, orc, cuda_device, filt, pad):
+    """The three ramp filters: FFT filter on the GPU (spectrum of the spatial
+    kernel formed in float64) against the oracle's direct-sum filter and
+    back-projection, on an ellipsoid sinogram with 77 bins (ragged) and two
+    paddings."""
+    p = acq.ellipsoid_sinograms(2, 77, 60, seed=9, n_ellipsoids=20).to(torch.float32)
+    ang = acq.uniform_angles(60).numpy()
+    geo = geometry(P, ang, 38.0, 77, 70, 64, 2 / 77, cuda_device)
+    got = P.pyhst_fbp(geo, p.to(cuda_device).contiguous(), "f32_sino", pad_len=pad, filter=filt)
+    q = P.pyhst_filter(geo, p.to(cuda_device).contiguous(), "f32_sino", pad_len=pad, filter=filt)
+    torch.cuda.synchronize()
+    for z in range(2):
+        qr = orc.filter_rows(p[z].double().numpy(), filt)
+        close(f64(q[z]), qr)
+        ref = orc.backproject(qr, ang.astype(np.float64), np.full(60, 38.0), 70, 64, orc.fbp_weight(60, 2 / 77))
+        close(f64(got[z]), ref)
