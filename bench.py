@@ -253,6 +253,12 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
         items.append((geos[n], fs.extra["sino"].to(dev).contiguous(), None, TV_BETA[n]))
         truths.append(fs.truth.double().cpu().numpy())
     opts = P.TvOptions(beta=1e-3, n_iter=n_iter, n_inner=n_inner, n_power_iter=50)
+    # autotune the Chambolle steps fused per launch for each slice size (results
+    # do not depend on it); outside the timed region
+    tuned = {}
+    for n in sorted(geos):
+        z = torch.randn((4, n, n), device=dev, generator=torch.Generator(device=dev).manual_seed(n))
+        tuned[str(n)] = P.pyhst_autotune_tv_prox(z, 0.01, n_inner)
     P.pyhst_tv_solve_batch(items, P.TvOptions(beta=1e-3, n_iter=2, n_inner=n_inner, n_power_iter=2))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -274,6 +280,7 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
             "psnr_tv_mean": float(np.mean(ps_tv)), "psnr_fbp_mean": float(np.mean(ps_fbp)),
             "psnr_tv_by_size": {k: float(np.mean(v)) for k, v in by.items()},
             "energy_lower_at_end_fraction": mono, "beta": {str(k): v for k, v in TV_BETA.items()},
+            "chambolle_steps_per_launch": tuned,
             "learned_prox": run_learned_prox(dev)}
 
 

@@ -296,6 +296,20 @@ typedef struct {
     float beta;
 } pyhst_tv_item;
 
+/* Autotuning of the TV prox.  The Chambolle steps run fused, several per
+ * launch on shared-memory tiles; the number fused per launch (2, 3, 4, 5, 6
+ * or 8) trades halo recomputation against launches and gives bit-identical
+ * results.  pyhst_autotune_tv_prox times every choice on the caller's z
+ * [n_slices][ny][nx] (DEVICE; workspace: pyhst_tv_prox_workspace_size),
+ * synchronizing `stream`, and records the fastest for images of ny x nx on
+ * the current device; pyhst_tv_prox, pyhst_tv_solve, pyhst_pnp_solve,
+ * pyhst_beta_scan and pyhst_tv_solve_batch (for its largest slice size) then
+ * use it.  pyhst_set_tv_prox_steps records a choice directly (0 clears it;
+ * the default is 5). */
+int pyhst_autotune_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
+                           float tau, void *workspace, size_t ws_bytes, int32_t *best_steps, pyhst_stream_t stream);
+int pyhst_set_tv_prox_steps(int32_t nx, int32_t ny, int32_t steps);
+
 /* pyhst_tv_solve for many slices of different sizes and angle sets at once
  * (same options for all): every stage of an iteration is one launch over the
  * whole batch, and the n_iter iterations are captured in one CUDA graph on

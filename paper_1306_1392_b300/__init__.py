@@ -439,6 +439,25 @@ def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0
     return out
 
 
+def pyhst_autotune_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0.125,
+                           workspace=None) -> int:
+    """Time the Chambolle steps fused per launch (2, 3, 4, 5, 6, 8; same
+    results) on z [n_slices, ny, nx] and record the fastest for ny x nx;
+    returns it."""
+    z3 = _stack3(_cuda(z, "z", (torch.float32,)), "z").contiguous()
+    ns, ny, nx = z3.shape
+    ws = _workspace(L.lib.pyhst_tv_prox_workspace_size(nx, ny, ns), z3.device, workspace)
+    best = ctypes.c_int32(0)
+    _check(L.lib.pyhst_autotune_tv_prox(_ptr(z3), nx, ny, ns, float(lam), int(n_inner), float(tau), _ptr(ws),
+                                        ws.numel(), ctypes.byref(best), _stream()))
+    return best.value
+
+
+def pyhst_set_tv_prox_steps(nx: int, ny: int, steps: int) -> None:
+    """Record the Chambolle steps fused per launch for ny x nx images (0: default)."""
+    _check(L.lib.pyhst_set_tv_prox_steps(nx, ny, steps))
+
+
 def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace=None):
     """Eq. 3 for a mixed batch: ``slices`` is a list of (Geometry, sino
     [n_angles, n_bins], x or None[, beta]) (beta defaults to opts.beta).

@@ -89,6 +89,9 @@ SIGNATURES = [
     ("pyhst_cnn_forward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t,
                                     c_void_p]),
     ("pyhst_device_status", c_int32, [ctypes.POINTER(ctypes.c_uint32), c_int32]),
+    ("pyhst_autotune_tv_prox", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_float, c_int32, c_float, c_void_p,
+                                         c_size_t, ctypes.POINTER(c_int32), c_void_p]),
+    ("pyhst_set_tv_prox_steps", c_int32, [c_int32, c_int32, c_int32]),
     ("pyhst_patch_grid", c_int32, [c_int32, c_int32, c_int32, c_int32, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     ("pyhst_patch_workspace_size", c_size_t, [ctypes.POINTER(pyhst_patch_problem), ctypes.POINTER(pyhst_geometry)]),
     ("pyhst_patch_image", c_int32, [ctypes.POINTER(pyhst_patch_problem), c_void_p, c_void_p, c_void_p, c_size_t,

@@ -3,12 +3,14 @@
 // with forward differences and Neumann boundary (grad is zero across the last
 // row/column, div = -grad^T).
 //
-// K steps on one 32 x 32 tile run in shared memory: the tile is loaded with a
-// halo of K pixels (a step reads its neighbours at distance one), every step
-// is computed over the whole loaded region, and after K steps the central
-// tile, whose dependence cone stayed inside the region, is written out.  The
-// loaded region is 64 wide (output 54 + halo 5 each side) so that warps of 32
-// columns fill it.  z/lam is formed once per launch; |grad G| and the
+// K steps on one tile run in shared memory: the tile is loaded with a halo of
+// K pixels (a step reads its neighbours at distance one), every step is
+// computed over the whole loaded region, and after K steps the central tile,
+// whose dependence cone stayed inside the region, is written out.  The loaded
+// region is 64 wide (output 64 - 2K + halo K each side) so that warps of 32
+// columns fill it.  K (2 .. 8) trades halo recomputation against launches;
+// every K gives bit-identical results, so it is a free tuning parameter
+// (chosen per image size by the autotuner, default 5).  z/lam is formed once per launch; |grad G| and the
 // reciprocal of 1 + tau |grad G| use the hardware approximations (within two
 // ulp), and the rounding of every operation is spelled out (fmaf, __fmul_rn,
 // ...) so that all kernels built on this function give bit-identical results.
@@ -18,10 +20,11 @@
 
 namespace pyhst {
 
-constexpr int kChT = 54;                    // output tile
-constexpr int kChK = 5;                     // steps fused per launch
-constexpr int kChR = kChT + 2 * kChK;       // loaded region (64: two full warp rows)
+constexpr int kChR = 64;                    // loaded region (two full warp rows)
 constexpr int kChW = kChR + 2;              // region + zero guard ring
+constexpr int kChKDefault = 5;              // steps fused per launch unless tuned
+__host__ __device__ constexpr int chambolle_tile_size(int K) { return kChR - 2 * K; }
+inline bool chambolle_k_supported(int K) { return K == 2 || K == 3 || K == 4 || K == 5 || K == 6 || K == 8; }
 constexpr int kChThreads = 256;
 constexpr size_t kChSmem = sizeof(float) * 4 * kChW * kChW;   // dynamic shared memory per CTA
 
@@ -36,6 +39,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+template <int kChK>
 __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
                                                const float *__restrict__ p2, float *__restrict__ q1,
                                                float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
@@ -97,6 +101,7 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
         }
         __syncthreads();
     }
+    constexpr int kChT = chambolle_tile_size(kChK);
     for (int r = ty; r < kChT; r += 8)
         for (int c = tx; c < kChT; c += 32) {
             const int gi = i0 + r, gj = j0 + c;
@@ -108,12 +113,27 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
         }
 }
 
-// Launch plan of n_inner steps: launch m runs steps_of(m) steps, the first
+// Launch plan of n_inner steps: launch m runs steps(m) steps, the first
 // from a zero dual field; the result is in the "a" buffers if the number of
 // launches is odd, else in "b".
-__host__ __device__ inline int chambolle_launches(int n_inner) { return (n_inner + kChK - 1) / kChK; }
-__host__ __device__ inline int chambolle_steps(int n_inner, int m) {
-    return m + 1 < chambolle_launches(n_inner) ? kChK : n_inner - kChK * m;
+__host__ __device__ inline int chambolle_launches(int n_inner, int K) { return (n_inner + K - 1) / K; }
+__host__ __device__ inline int chambolle_steps(int n_inner, int m, int K) {
+    return m + 1 < chambolle_launches(n_inner, K) ? K : n_inner - K * m;
 }
+
+// Steps fused per launch for an image size: the autotuned choice if there is
+// one (pyhst_autotune_tv_prox / pyhst_set_tv_prox_steps), else kChKDefault.
+int chambolle_k_for(int nx, int ny);
+
+// Instantiate F<K> for the supported K and call it (returns its status).
+#define PYHST_CHAMBOLLE_DISPATCH(K, F, ...)         \
+    switch (K) {                                    \
+        case 2: return F<2>(__VA_ARGS__);           \
+        case 3: return F<3>(__VA_ARGS__);           \
+        case 4: return F<4>(__VA_ARGS__);           \
+        case 6: return F<6>(__VA_ARGS__);           \
+        case 8: return F<8>(__VA_ARGS__);           \
+        default: return F<5>(__VA_ARGS__);          \
+    }
 
 }  // namespace pyhst

@@ -16,6 +16,9 @@
 // all-ones image (float64 norms), L = 1.01 * ||P v||^2 for the final unit v.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "chambolle.cuh"
@@ -146,9 +149,10 @@ __global__ void grad_step_kernel(const float *__restrict__ y, const float *__res
         z[off + i] = fmaf(-g[off + i], il, y[off + i]);
 }
 
-// n_inner Chambolle steps in launches of up to kChK fused steps (see
+// n_inner Chambolle steps in launches of up to K fused steps (see
 // chambolle.cuh): launch 0 starts from a zero field and writes the "a"
 // buffers, launch m > 0 reads a (m odd) or b and writes the other.
+template <int K>
 __global__ void __launch_bounds__(kChThreads)
 chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, float *pb1, float *pb2,
                        const float *__restrict__ lam, float tau, int nx, int ny, int m, int steps, int tiles_x) {
@@ -156,21 +160,33 @@ chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, floa
     const bool odd = m & 1;
     const float *s1 = (odd ? pa1 : pb1) + off, *s2 = (odd ? pa2 : pb2) + off;
     float *d1 = (m == 0 || !odd ? pa1 : pb1) + off, *d2 = (m == 0 || !odd ? pa2 : pb2) + off;
-    chambolle_tile(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * kChT,
-                   (blockIdx.x % tiles_x) * kChT, steps, m == 0);
+    constexpr int T = chambolle_tile_size(K);
+    chambolle_tile<K>(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * T,
+                      (blockIdx.x % tiles_x) * T, steps, m == 0);
 }
 
-// Enqueue n_inner steps; returns through *final_a whether the result is in the a buffers.
-int launch_chambolle(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
-                     int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st) {
-    const int tx = (nx + kChT - 1) / kChT, ty = (ny + kChT - 1) / kChT;
-    const int L = chambolle_launches(n_inner);
-    cudaFuncSetAttribute(chambolle_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem);
+template <int K>
+int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
+                       int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st) {
+    constexpr int T = chambolle_tile_size(K);
+    const int tx = (nx + T - 1) / T, ty = (ny + T - 1) / T;
+    const int L = chambolle_launches(n_inner, K);
+    cudaFuncSetAttribute(chambolle_fused_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem);
     for (int m = 0; m < L; ++m)
-        chambolle_fused_kernel<<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
-            z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, chambolle_steps(n_inner, m), tx);
+        chambolle_fused_kernel<K><<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
+            z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, chambolle_steps(n_inner, m, K), tx);
     *final_a = (L & 1) == 1;
     return cuda_status("Chambolle kernels");
+}
+
+// Enqueue n_inner steps with K fused steps per launch (K <= 0: the tuned or
+// default choice for the size); returns through *final_a whether the result
+// is in the a buffers.
+int launch_chambolle(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
+                     int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, int K = 0) {
+    if (K <= 0) K = chambolle_k_for(nx, ny);
+    PYHST_CHAMBOLLE_DISPATCH(K, launch_chambolle_k, z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, n_slices, n_inner,
+                             final_a, st)
 }
 
 // x = z - lam div p
@@ -504,4 +520,93 @@ extern "C" int pyhst_pnp_solve(const pyhst_geometry *g, const float *sino, const
     hk.cnn_ws = static_cast<char *>(workspace) + align_up(tv_workspace_bytes(g, nullptr));
     return tv_solve_enqueue(g, sino, &o, x, energy, lipschitz_out, workspace, reinterpret_cast<cudaStream_t>(stream),
                             hk);
+}
+
+namespace pyhst {
+
+// ----------------------------------------------------------------- autotuned K
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tune;   // (device, nx, ny) -> steps fused per launch
+
+int chambolle_k_for(int nx, int ny) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto f = g_tune.find(std::make_tuple(dev, nx, ny));
+    return f == g_tune.end() ? kChKDefault : f->second;
+}
+
+void chambolle_k_set(int nx, int ny, int K) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (K <= 0)
+        g_tune.erase(std::make_tuple(dev, nx, ny));
+    else
+        g_tune[std::make_tuple(dev, nx, ny)] = K;
+}
+
+}  // namespace pyhst
+
+extern "C" int pyhst_set_tv_prox_steps(int32_t nx, int32_t ny, int32_t steps) {
+    using namespace pyhst;
+    if (nx < 1 || ny < 1) return fail(PYHST_ERR_INVALID_ARG, "image size must be positive");
+    if (steps > 0 && !chambolle_k_supported(steps))
+        return fail(PYHST_ERR_INVALID_ARG, "steps per launch %d: supported 2, 3, 4, 5, 6, 8 (0 clears)", steps);
+    chambolle_k_set(nx, ny, steps);
+    return PYHST_OK;
+}
+
+extern "C" int pyhst_autotune_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam,
+                                      int32_t n_inner, float tau, void *workspace, size_t ws_bytes,
+                                      int32_t *best_steps, pyhst_stream_t stream) {
+    using namespace pyhst;
+    if (!z || !best_steps) return fail(PYHST_ERR_INVALID_ARG, "z/best_steps pointer is NULL");
+    if (nx < 1 || ny < 1 || n_slices < 1 || nx > 16384 || ny > 16384 || n_slices > 65535)
+        return fail(PYHST_ERR_INVALID_ARG, "image %d x %d x %d out of range", nx, ny, n_slices);
+    if (!(lam >= 0.0f) || !std::isfinite(lam)) return fail(PYHST_ERR_INVALID_ARG, "lam must be >= 0");
+    if (n_inner < 1) return fail(PYHST_ERR_INVALID_ARG, "n_inner must be >= 1");
+    if (!(tau > 0.0f && tau <= 0.25f)) return fail(PYHST_ERR_INVALID_ARG, "tau must be in (0, 1/4]");
+    const size_t need = tv_prox_workspace_bytes(nx, ny, n_slices);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t img = align_up(sizeof(float) * (size_t)nx * ny * n_slices);
+    char *b = static_cast<char *>(workspace);
+    float *p1a = reinterpret_cast<float *>(b), *p2a = reinterpret_cast<float *>(b + img);
+    float *p1b = reinterpret_cast<float *>(b + 2 * img), *p2b = reinterpret_cast<float *>(b + 3 * img);
+    float *lamd = reinterpret_cast<float *>(b + 4 * img);
+    fill_lam<<<(n_slices + 127) / 128, 128, 0, st>>>(lamd, lam, n_slices);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cand[] = {2, 3, 4, 5, 6, 8};
+    int best = kChKDefault;
+    float best_ms = 1e30f;
+    int rc = PYHST_OK;
+    for (int K : cand) {
+        bool fa;
+        if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, n_slices, n_inner, &fa, st, K))) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && !rc; ++r)
+            rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, n_slices, n_inner, &fa, st, K);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = cuda_status("autotune timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = K;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    chambolle_k_set(nx, ny, best);
+    *best_steps = best;
+    return PYHST_OK;
 }

@@ -84,8 +84,9 @@ __global__ void b_grad_step(const TvSlice *__restrict__ d, const int4 *__restric
     s.z[k] = fmaf(-s.g[k], sc.invL[it.x], s.y[k]);
 }
 
-// Launch m of the fused Chambolle steps (see chambolle.cuh) on 32 x 32 tile
+// Launch m of the fused Chambolle steps (see chambolle.cuh) on tile
 // (items[k].y, items[k].z) of slice items[k].x; slices with beta = 0 skip.
+template <int K>
 __global__ void __launch_bounds__(kChThreads)
 b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps) {
     const int4 it = items[blockIdx.x];
@@ -94,7 +95,30 @@ b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal 
     const bool odd = m & 1;
     const float *s1 = odd ? s.p1a : s.p1b, *s2 = odd ? s.p2a : s.p2b;
     float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
-    chambolle_tile(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * kChT, it.y * kChT, steps, m == 0);
+    constexpr int T = chambolle_tile_size(K);
+    chambolle_tile<K>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0);
+}
+
+template <int K>
+int b_chambolle_attr_k() {
+    return cudaFuncSetAttribute(b_chambolle<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem) ==
+                   cudaSuccess
+               ? PYHST_OK
+               : cuda_status("Chambolle kernel shared-memory attribute");
+}
+int b_chambolle_attr(int K) { PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_attr_k) }
+
+template <int K>
+int b_chambolle_launches_k(int nch, const TvSlice *T, const int4 *items, Scal sc, float tau, int n_inner,
+                           cudaStream_t st) {
+    const int Lc = chambolle_launches(n_inner, K);
+    for (int m = 0; m < Lc; ++m)
+        b_chambolle<K><<<nch, kChThreads, kChSmem, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K));
+    return cuda_status("batched Chambolle kernels");
+}
+int b_chambolle_launches(int K, int nch, const TvSlice *T, const int4 *items, Scal sc, float tau, int n_inner,
+                         cudaStream_t st) {
+    PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_launches_k, nch, T, items, sc, tau, n_inner, st)
 }
 
 // x_new = z - lam div p (p in the buffers of `parity`); with lam = 0, x_new = z
@@ -289,6 +313,7 @@ struct Plan {
     // projector items of slices that take the 256-column variant come first
     // (each slice uses the variant of its single-slice solve)
     int proj_narrow = 0, proj_r_narrow = 0;
+    int chK = 5;     // Chambolle steps fused per launch (tuned for the largest slice)
 };
 
 size_t up4(size_t v) { return (v + 63) / 64 * 64; }   // 256-byte multiples of floats
@@ -314,13 +339,18 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     const int M = g.n_angles * g.n_bins;
     for (int e = 0; e < (M + kSinoBlock - 1) / kSinoBlock; ++e) sn.push_back(make_int4(s, e, 0, 0));
     if (!rep_only)
-        for (int y = 0; y < (g.ny + kChT - 1) / kChT; ++y)
-            for (int x = 0; x < (g.nx + kChT - 1) / kChT; ++x) P.ch.push_back(make_int4(s, x, y, 0));
+        for (int y = 0; y < (g.ny + chambolle_tile_size(P.chK) - 1) / chambolle_tile_size(P.chK); ++y)
+            for (int x = 0; x < (g.nx + chambolle_tile_size(P.chK) - 1) / chambolle_tile_size(P.chK); ++x)
+                P.ch.push_back(make_int4(s, x, y, 0));
 }
 
 Plan make_plan(const pyhst_tv_item *items, int n) {
     Plan P;
     P.n = n;
+    int big = 0;
+    for (int s = 1; s < n; ++s)
+        if ((long)items[s].geom.nx * items[s].geom.ny > (long)items[big].geom.nx * items[big].geom.ny) big = s;
+    P.chK = chambolle_k_for(items[big].geom.nx, items[big].geom.ny);
     P.rep.resize(n);
     std::map<std::tuple<const void *, const void *, int, int, int, int, float, float, float>, int> groups;
     for (int s = 0; s < n; ++s) {
@@ -550,7 +580,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     b_copy_sino_start<<<nsn, tb, 0, st>>>(T, I + o_sn, opts->warm_start ? 1 : 0);
     if ((rc = cuda_status("batch start"))) return rc;
 
-    cudaFuncSetAttribute(b_chambolle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem);
+    if ((rc = b_chambolle_attr(P.chK))) return rc;
     // ---- the iterations, captured in one graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
@@ -568,10 +598,9 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         b_grad_step<<<npx, tb, 0, st>>>(T, I + o_px, sc);
         int pp = 0;   // 0: the dual field ends in the "a" buffers
         if (!identity) {
-            const int Lc = chambolle_launches(opts->n_inner);
-            for (int m = 0; m < Lc; ++m)
-                b_chambolle<<<nch, kChThreads, kChSmem, st>>>(T, I + o_ch, sc, opts->tau, m,
-                                                               chambolle_steps(opts->n_inner, m));
+            const int Lc = chambolle_launches(opts->n_inner, P.chK);
+            rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, sc, opts->tau, opts->n_inner, st);
+            if (rc) break;
             pp = (Lc & 1) ? 0 : 1;
         }
         b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, pp, par, identity);

@@ -245,3 +245,40 @@ def test_tv_solve_capture_matches_oracle_prox_inputs(P, orc, cuda_device):
     for c, k in enumerate((1, 4, 9)):
         _, _, zr = orc.fista(og, sino.double().numpy(), 2e-3, L, k, n_inner=20, return_z=True)
         assert rel(cap[c, 0].cpu().numpy(), zr) <= 1e-4
+
+
+def test_tv_prox_steps_per_launch_are_bit_identical(P, cuda_device):
+    """Every choice of Chambolle steps fused per launch gives the same bits
+    (the halo is recomputed with the same arithmetic); the autotuner picks one
+    of them and the prox then uses it."""
+    g = np.random.default_rng(3)
+    z = torch.from_numpy(g.standard_normal((3, 150, 133)).astype(np.float32)).to(cuda_device)
+    outs = {}
+    try:
+        for k in (2, 3, 4, 5, 6, 8):
+            P.pyhst_set_tv_prox_steps(133, 150, k)
+            outs[k] = P.pyhst_tv_prox(z, 0.4, 17)
+        for k, o in outs.items():
+            assert torch.equal(o, outs[5]), k
+        best = P.pyhst_autotune_tv_prox(z, 0.4, 17)
+        assert best in outs
+        assert torch.equal(P.pyhst_tv_prox(z, 0.4, 17), outs[5])
+        with pytest.raises(P.PyhstError):
+            P.pyhst_set_tv_prox_steps(133, 150, 7)
+    finally:
+        P.pyhst_set_tv_prox_steps(133, 150, 0)
+
+
+def test_batch_solve_with_tuned_steps_matches_default(P, cuda_device):
+    """The batched solver builds its Chambolle tiles for the tuned choice of
+    its largest slice; the result is the same bits as with the default."""
+    items = _mixed(P, cuda_device)
+    opts = P.TvOptions(beta=3e-3, n_iter=6, n_inner=7, lipschitz=50.0)
+    xs0, _, _ = P.pyhst_tv_solve_batch([(g, s, None) for g, s, *_ in items], opts, energy=False)
+    try:
+        P.pyhst_set_tv_prox_steps(64, 64, 3)
+        xs1, _, _ = P.pyhst_tv_solve_batch([(g, s, None) for g, s, *_ in items], opts, energy=False)
+    finally:
+        P.pyhst_set_tv_prox_steps(64, 64, 0)
+    for a, b in zip(xs0, xs1):
+        assert torch.equal(a, b)
