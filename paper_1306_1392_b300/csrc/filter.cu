@@ -15,7 +15,11 @@
 // decimation in frequency (natural order in, bit-reversed order out), the
 // spectrum is multiplied in bit-reversed order, and the inverse is decimation
 // in time (bit-reversed in, natural out), so no permutation pass is needed.
-// The whole padded row pair lives in shared memory (P * 8 bytes).
+// Consecutive radix-2 stages run fused three at a time in registers (the
+// same butterflies in the same order), so a 4096-point transform makes 4
+// shared-memory passes each way instead of 12.  The whole padded row pair
+// lives in shared memory (P * 8 bytes plus one pad slot per 16 elements).
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -102,10 +106,66 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// Shared-memory slot of element i: one pad slot per 16 elements, so the
+// stride-16 accesses of the last pass spread over all banks.
+__device__ __forceinline__ int slot(int i) { return i + (i >> 4); }
+
+// NST consecutive radix-2 stages (top, top-1, ..., top-NST+1 for the
+// decimation in frequency; lo, lo+1, ... for the decimation in time) fused in
+// registers: the 2^NST elements base + k 2^lo (k < 2^NST) are closed under
+// them.  Every butterfly and twiddle is the one the stage-by-stage radix-2
+// transform uses, in the same order, so the result is the same bits with a
+// quarter of the shared-memory passes.
+template <int NST, bool kDIF>
+__device__ __forceinline__ void fused_stages(float2 *z, const float2 *__restrict__ tw, int P, int logP, int lo) {
+    constexpr int G = 1 << NST;
+    const int top = lo + NST - 1, stride = 1 << lo, ngroups = P >> NST;
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const int base = (g & (stride - 1)) | ((g >> lo) << (top + 1));
+        float2 v[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) v[k] = z[slot(base + k * stride)];
+#pragma unroll
+        for (int t = 0; t < NST; ++t) {
+            const int sl = kDIF ? NST - 1 - t : t;      // stage within the group
+            const int s = lo + sl, hk = 1 << sl;
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                if (k & hk) continue;
+                const int i0 = base + k * stride;
+                const float2 w = tw[(i0 & ((1 << s) - 1)) << (logP - 1 - s)];
+                const float2 u = v[k];
+                if (kDIF) {
+                    const float2 b = v[k + hk];
+                    v[k] = make_float2(u.x + b.x, u.y + b.y);
+                    v[k + hk] = cmul(make_float2(u.x - b.x, u.y - b.y), w);
+                } else {
+                    const float2 t2 = cmul(v[k + hk], make_float2(w.x, -w.y));
+                    v[k] = make_float2(u.x + t2.x, u.y + t2.y);
+                    v[k + hk] = make_float2(u.x - t2.x, u.y - t2.y);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < G; ++k) z[slot(base + k * stride)] = v[k];
+    }
+}
+
+constexpr int kFuse = 3;   // radix-2 stages fused per shared-memory pass (8 elements per thread)
+
+template <bool kDIF>
+__device__ __forceinline__ void fused_pass(int nst, float2 *z, const float2 *__restrict__ tw, int P, int logP, int lo) {
+    switch (nst) {
+        case 3: fused_stages<3, kDIF>(z, tw, P, logP, lo); break;
+        case 2: fused_stages<2, kDIF>(z, tw, P, logP, lo); break;
+        default: fused_stages<1, kDIF>(z, tw, P, logP, lo); break;
+    }
+}
+
 // One CTA filters rows 2*blockIdx.x and 2*blockIdx.x+1 of the chunk; row r is
 // (slice z0 + r / n_angles, angle r % n_angles).
 template <int kKind>
-__global__ void filter_kernel(const void *__restrict__ data, int64_t slice_stride, int64_t angle_stride,
+__global__ void __launch_bounds__(1024) filter_kernel(const void *__restrict__ data, int64_t slice_stride, int64_t angle_stride,
                               const float *__restrict__ flat, const float *__restrict__ dark, int z0,
                               int n_rows, int n_angles, int n_bins, int P, int logP,
                               const float2 *__restrict__ tw, const float *__restrict__ hrev,
@@ -135,46 +195,30 @@ __global__ void filter_kernel(const void *__restrict__ data, int64_t slice_strid
                 vb = load_p<kKind>(data, baseB + k, FB, DB);
             }
         }
-        z[k] = make_float2(va, vb);
+        z[slot(k)] = make_float2(va, vb);
     }
     __syncthreads();
-    const int half = P >> 1;
-    // forward: decimation in frequency
-    for (int lh = logP - 1; lh >= 0; --lh) {
-        const int h = 1 << lh;
-        for (int bt = threadIdx.x; bt < half; bt += blockDim.x) {
-            const int j = bt & (h - 1);
-            const int i0 = ((bt >> lh) << (lh + 1)) | j;
-            const float2 u = z[i0], v = z[i0 + h];
-            z[i0] = make_float2(u.x + v.x, u.y + v.y);
-            z[i0 + h] = cmul(make_float2(u.x - v.x, u.y - v.y), tw[j << (logP - 1 - lh)]);
-        }
+    // forward: decimation in frequency, stages logP-1 .. 0 in passes of up to kFuse
+    for (int top = logP - 1; top >= 0; top -= kFuse) {
+        const int nst = min(kFuse, top + 1);
+        fused_pass<true>(nst, z, tw, P, logP, top - nst + 1);
         __syncthreads();
     }
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
         const float H = hrev[k];
-        const float2 v = z[k];
-        z[k] = make_float2(v.x * H, v.y * H);
+        const float2 v = z[slot(k)];
+        z[slot(k)] = make_float2(v.x * H, v.y * H);
     }
     __syncthreads();
-    // inverse: decimation in time with conjugate twiddles
-    for (int lh = 0; lh < logP; ++lh) {
-        const int h = 1 << lh;
-        for (int bt = threadIdx.x; bt < half; bt += blockDim.x) {
-            const int j = bt & (h - 1);
-            const int i0 = ((bt >> lh) << (lh + 1)) | j;
-            const float2 w = tw[j << (logP - 1 - lh)];
-            const float2 u = z[i0];
-            const float2 t = cmul(z[i0 + h], make_float2(w.x, -w.y));
-            z[i0] = make_float2(u.x + t.x, u.y + t.y);
-            z[i0 + h] = make_float2(u.x - t.x, u.y - t.y);
-        }
+    // inverse: decimation in time with conjugate twiddles, stages 0 .. logP-1
+    for (int lo = 0; lo < logP; lo += kFuse) {
+        fused_pass<false>(min(kFuse, logP - lo), z, tw, P, logP, lo);
         __syncthreads();
     }
     float *qA = q + (size_t)rA * n_bins;
     float *qB = q + (size_t)rB * n_bins;
     for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
-        const float2 v = z[k];
+        const float2 v = z[slot(k)];
         qA[k] = v.x;
         if (hasB) qB[k] = v.y;
     }
@@ -210,8 +254,8 @@ int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angl
     int logP = 0;
     while ((1 << logP) < P) ++logP;
     const int n_rows = n_slices_chunk * n_angles;
-    const int threads = P >= 2048 ? 512 : (P >= 256 ? P / 4 : 64);
-    const size_t smem = sizeof(float2) * P;
+    const int threads = std::min(1024, std::max(64, P / 8));   // one 8-element group per thread and pass
+    const size_t smem = sizeof(float2) * (P + P / 16);   // one pad slot per 16 elements
     const int grid = (n_rows + 1) / 2;
 #define PYHST_FILTER_CASE(K)                                                                          \
     case K: {                                                                                         \
