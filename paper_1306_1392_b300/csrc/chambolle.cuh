@@ -73,27 +73,39 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
     // cells of the loaded region that lie inside the image
     const int r_lo = max(1, -ri0), r_hi = min(kChR, ny - 1 - ri0);
     const int c_lo = max(1, -rj0), c_hi = min(kChR, nx - 1 - rj0);
+    // Boundary handling without branches in the cell loops: p1 stays exactly 0
+    // on the last image row and p2 on the last column (their forward
+    // differences are 0 there, and p starts at 0), and cells outside the image
+    // hold 0, so div p adds its four terms unconditionally (adding or
+    // subtracting 0 changes no bits); the forward differences of the last row
+    // and column are masked by multiplying with 0.
+    float m2c[(kChR + 31) / 32];                       // per column of this thread: gj + 1 < nx
+#pragma unroll
+    for (int q = 0; q < (kChR + 31) / 32; ++q) {
+        const int c = c_lo + tx + 32 * q;
+        m2c[q] = (rj0 + c + 1 < nx) ? 1.0f : 0.0f;
+    }
     for (int st = 0; st < steps; ++st) {
         for (int r = r_lo + ty; r <= r_hi; r += 8) {
-            const int gi = ri0 + r;
             for (int c = c_lo + tx; c <= c_hi; c += 32) {
-                const int gj = rj0 + c;
                 float d = 0.0f;
-                if (gi + 1 < ny) d = __fadd_rn(d, s1[r][c]);
-                if (gi > 0) d = __fsub_rn(d, s1[r - 1][c]);
-                if (gj + 1 < nx) d = __fadd_rn(d, s2[r][c]);
-                if (gj > 0) d = __fsub_rn(d, s2[r][c - 1]);
+                d = __fadd_rn(d, s1[r][c]);
+                d = __fsub_rn(d, s1[r - 1][c]);
+                d = __fadd_rn(d, s2[r][c]);
+                d = __fsub_rn(d, s2[r][c - 1]);
                 sg[r][c] = __fsub_rn(d, sz[r][c]);
             }
         }
         __syncthreads();
         for (int r = r_lo + ty; r <= r_hi; r += 8) {
-            const int gi = ri0 + r;
-            for (int c = c_lo + tx; c <= c_hi; c += 32) {
-                const int gj = rj0 + c;
+            const float m1 = (ri0 + r + 1 < ny) ? 1.0f : 0.0f;
+#pragma unroll
+            for (int q = 0; q < (kChR + 31) / 32; ++q) {
+                const int c = c_lo + tx + 32 * q;
+                if (c > c_hi) break;
                 const float g0 = sg[r][c];
-                const float g1 = (gi + 1 < ny) ? __fsub_rn(sg[r + 1][c], g0) : 0.0f;
-                const float g2 = (gj + 1 < nx) ? __fsub_rn(sg[r][c + 1], g0) : 0.0f;
+                const float g1 = __fmul_rn(m1, __fsub_rn(sg[r + 1][c], g0));
+                const float g2 = __fmul_rn(m2c[q], __fsub_rn(sg[r][c + 1], g0));
                 const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
                 s1[r][c] = __fmul_rn(fmaf(tau, g1, s1[r][c]), inv);
                 s2[r][c] = __fmul_rn(fmaf(tau, g2, s2[r][c]), inv);
