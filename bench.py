@@ -68,7 +68,8 @@ def parse():
                     help="cost of the Sec. 2.3 preprocessing variants on the batched-volume geometry")
     ap.add_argument("--beta-study", action="store_true",
                     help="beta estimators (Sec. 4) on a 2048^2 foam with 150 projections vs its ground truth")
-    ap.add_argument("--kernel-case", choices=["backproject", "project", "filter", "cnn"],
+    ap.add_argument("--kernel-case", choices=["backproject", "project", "filter", "cnn", "project-sparse", "tvprox",
+                                              "patch"],
                     help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
     return ap.parse_args()
 
@@ -649,6 +650,35 @@ def run_kernel_case(args):
         ws = torch.empty(P.pyhst_workspace_size(geo, P.PYHST_OP_PROJECT, S), dtype=torch.uint8, device=dev)
         fn = lambda: P.pyhst_project(geo, img, out=out, workspace=ws)
         upd = S * UPD_PER_SLICE
+    elif args.kernel_case == "project-sparse":
+        # one 2048^2 slice, 150 angles: the 512-column staging variant with row segments
+        ang150 = acq.uniform_angles(150).to(dev)
+        geo150 = P.Geometry(ang150, torch.full((150,), (N_BINS - 1) / 2.0, device=dev), N_BINS, N_PIX, N_PIX,
+                            2.0 / N_PIX)
+        img = torch.randn((1, N_PIX, N_PIX), device=dev, generator=g)
+        out = torch.empty((1, 150, N_BINS), device=dev)
+        ws = torch.empty(P.pyhst_workspace_size(geo150, P.PYHST_OP_PROJECT, 1), dtype=torch.uint8, device=dev)
+        fn = lambda: P.pyhst_project(geo150, img, out=out, workspace=ws)
+        upd = N_PIX * N_PIX * 150
+    elif args.kernel_case == "tvprox":
+        # 20 Chambolle steps on 16 images of 1024^2 (default fusion depth)
+        z = torch.randn((16, 1024, 1024), device=dev, generator=g)
+        out = torch.empty_like(z)
+        fn = lambda: P.pyhst_tv_prox(z, 0.05, 20, out=out)
+        upd = 16 * 1024 * 1024 * 20
+    elif args.kernel_case == "patch":
+        # one gradient of the overlapping-patch functional: 2048^2, 150 angles, 8x8 patches, stride 4, 144 atoms
+        import numpy as np
+        from synth.patches import overcomplete_dct
+        ang150 = acq.uniform_angles(150).to(dev)
+        geo150 = P.Geometry(ang150, torch.full((150,), (N_BINS - 1) / 2.0, device=dev), N_BINS, N_PIX, N_PIX,
+                            2.0 / N_PIX)
+        D = torch.from_numpy(overcomplete_dct(8, 12).astype(np.float32)).to(dev)
+        pp = P.PatchProblem(N_PIX, N_PIX, 8, 4, D, 1.0)
+        W = torch.randn(pp.coef_shape(), device=dev, generator=g)
+        y = torch.randn((150, N_BINS), device=dev, generator=g)
+        fn = lambda: P.pyhst_patch_gradient(pp, geo150, W, y)
+        upd = pp.coef_shape()[0]
     elif args.kernel_case == "cnn":
         # CNN prox forward pass on 16 images of 512^2 (seeded initial weights)
         from synth.cnn_init import init_params
