@@ -3,30 +3,41 @@
 // with forward differences and Neumann boundary (grad is zero across the last
 // row/column, div = -grad^T).
 //
-// K steps on one tile run in shared memory: the tile is loaded with a halo of
-// K pixels (a step reads its neighbours at distance one), every step is
+// K steps on one tile run on chip: the tile is loaded with a halo of K
+// pixels (a step reads its neighbours at distance one), every step is
 // computed over the whole loaded region, and after K steps the central tile,
 // whose dependence cone stayed inside the region, is written out.  The loaded
-// region is 64 wide (output 64 - 2K + halo K each side) so that warps of 32
-// columns fill it.  K (2 .. 8) trades halo recomputation against launches;
+// region is 64 x 64 (output 64 - 2K, halo K each side); outside it every field
+// reads as zero.  K (2 .. 8) trades halo recomputation against launches;
 // every K gives bit-identical results, so it is a free tuning parameter
-// (chosen per image size by the autotuner, default 5).  z/lam is formed once per launch; |grad G| and the
-// reciprocal of 1 + tau |grad G| use the hardware approximations (within two
-// ulp), and the rounding of every operation is spelled out (fmaf, __fmul_rn,
-// ...) so that all kernels built on this function give bit-identical results.
+// (chosen per image size by the autotuner, default 5).
+//
+// The fields live in registers: warp w holds region rows 8w+1 .. 8w+8 and
+// lane l the two columns 2l+1, 2l+2 of them (z / lam, p1, p2 and G for 16
+// cells per thread).  Horizontal neighbours come from the adjacent lane by a
+// shuffle, vertical ones from the thread's own rows, and only the first G row
+// and the last p1 row of each strip cross to the neighbouring warp, through
+// two small shared-memory arrays (two barriers per step).  z/lam is formed
+// once per launch; |grad G| and the reciprocal of 1 + tau |grad G| use the
+// hardware approximations (within two ulp), and the rounding of every
+// operation is spelled out (fmaf, __fmul_rn, ...) so that all kernels built on
+// this function give bit-identical results.
 #pragma once
 
 #include "common.cuh"
 
 namespace pyhst {
 
-constexpr int kChR = 64;                    // loaded region (two full warp rows)
-constexpr int kChW = kChR + 2;              // region + zero guard ring
+constexpr int kChR = 64;                    // loaded region side
+constexpr int kChRows = 8;                  // region rows per warp
 constexpr int kChKDefault = 5;              // steps fused per launch unless tuned
 __host__ __device__ constexpr int chambolle_tile_size(int K) { return kChR - 2 * K; }
 inline bool chambolle_k_supported(int K) { return K == 2 || K == 3 || K == 4 || K == 5 || K == 6 || K == 8; }
-constexpr int kChThreads = 256;
-constexpr size_t kChSmem = sizeof(float) * 4 * kChW * kChW;   // dynamic shared memory per CTA
+constexpr int kChThreads = 32 * kChR / kChRows;
+constexpr int kChMinBlocks = 3;             // register budget: three CTAs per SM
+// dynamic shared memory per CTA: the strips' last p1 rows and first G rows,
+// each with a zero guard row
+constexpr size_t kChSmem = sizeof(float) * 2 * (kChR / kChRows + 1) * kChR;
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float r;
@@ -39,24 +50,93 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// The K steps on the registers of one thread.  kEdge: the region touches the
+// image border, so cells outside the image keep p = 0 and G = 0, and the
+// forward differences across the last image row / column are multiplied by 0
+// (m1, m2); inside the image every such factor is 1 and is left out, which
+// changes no bits.
+template <bool kEdge>
+__device__ __forceinline__ void chambolle_steps_regs(float (&zl)[kChRows][2], float (&a1)[kChRows][2],
+                                                     float (&a2)[kChRows][2], float (*xp)[kChR],
+                                                     float (*xg)[kChR], float tau, int steps, unsigned in_mask,
+                                                     const float (&m1)[kChRows], const float (&m2)[2]) {
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int st = 0; st < steps; ++st) {
+        float G[kChRows][2];
+        const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);
+#pragma unroll
+        for (int i = 0; i < kChRows; ++i) {
+            float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
+            if (tx == 0) left = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float u = i > 0 ? a1[i - 1][j] : (j == 0 ? up.x : up.y);
+                const float l = j > 0 ? a2[i][0] : left;
+                float d = 0.0f;
+                d = __fadd_rn(d, a1[i][j]);
+                d = __fsub_rn(d, u);
+                d = __fadd_rn(d, a2[i][j]);
+                d = __fsub_rn(d, l);
+                G[i][j] = __fsub_rn(d, zl[i][j]);
+                if (kEdge && !((in_mask >> (2 * i + j)) & 1u)) G[i][j] = 0.0f;
+            }
+        }
+        *reinterpret_cast<float2 *>(&xg[w][2 * tx]) = make_float2(G[0][0], G[0][1]);
+        __syncthreads();
+        const float2 down = *reinterpret_cast<const float2 *>(&xg[w + 1][2 * tx]);
+#pragma unroll
+        for (int i = 0; i < kChRows; ++i) {
+            float right = __shfl_down_sync(0xffffffffu, G[i][0], 1);
+            if (tx == 31) right = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float g0 = G[i][j];
+                const float dn = i + 1 < kChRows ? G[i + 1][j] : (j == 0 ? down.x : down.y);
+                const float rt = j == 0 ? G[i][1] : right;
+                float g1 = __fsub_rn(dn, g0), g2 = __fsub_rn(rt, g0);
+                if (kEdge) {
+                    g1 = __fmul_rn(m1[i], g1);
+                    g2 = __fmul_rn(m2[j], g2);
+                }
+                const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
+                const float n1 = __fmul_rn(fmaf(tau, g1, a1[i][j]), inv);
+                const float n2 = __fmul_rn(fmaf(tau, g2, a2[i][j]), inv);
+                if (!kEdge || ((in_mask >> (2 * i + j)) & 1u)) {
+                    a1[i][j] = n1;
+                    a2[i][j] = n2;
+                }
+            }
+        }
+        *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
+        __syncthreads();
+    }
+}
+
 template <int kChK>
 __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
                                                const float *__restrict__ p2, float *__restrict__ q1,
                                                float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
                                                int j0, int steps, bool first) {
-    // sz holds z / lam; threads as 32 columns x 8 rows
     extern __shared__ __align__(16) float ch_smem[];
-    float(*sz)[kChW] = reinterpret_cast<float(*)[kChW]>(ch_smem);
-    float(*s1)[kChW] = sz + kChW;
-    float(*s2)[kChW] = s1 + kChW;
-    float(*sg)[kChW] = s2 + kChW;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int ri0 = i0 - kChK - 1, rj0 = j0 - kChK - 1;   // global coordinates of array cell (0, 0)
-    for (int r = ty; r < kChW; r += 8)
-        for (int c = tx; c < kChW; c += 32) {
-            const int gi = ri0 + r, gj = rj0 + c;
+    float(*xp)[kChR] = reinterpret_cast<float(*)[kChR]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
+    float(*xg)[kChR] = xp + (kChR / kChRows + 1);                       // xg[w]: first G row of strip w
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ri0 = i0 - kChK - 1, rj0 = j0 - kChK - 1;   // global coordinates of region cell (0, 0)
+    const int r0 = kChRows * w + 1, c0 = 2 * tx + 1;      // this thread's first region row and column
+    float zl[kChRows][2], a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
+    unsigned in_mask = 0;                                  // bit 2i + j: cell (i, j) inside the image
+#pragma unroll
+    for (int j = 0; j < 2; ++j) m2[j] = (rj0 + c0 + j + 1 < nx) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int i = 0; i < kChRows; ++i) {
+        const int gi = ri0 + r0 + i;
+        m1[i] = (gi + 1 < ny) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int gj = rj0 + c0 + j;
             float vz = 0.0f, v1 = 0.0f, v2 = 0.0f;
-            if (r >= 1 && r <= kChR && c >= 1 && c <= kChR && gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
+            if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
+                in_mask |= 1u << (2 * i + j);
                 const size_t k = (size_t)gi * nx + gj;
                 vz = __fdiv_rn(z[k], lam);
                 if (!first) {
@@ -64,63 +144,31 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
                     v2 = p2[k];
                 }
             }
-            sz[r][c] = vz;
-            s1[r][c] = v1;
-            s2[r][c] = v2;
-            sg[r][c] = 0.0f;
+            zl[i][j] = vz;
+            a1[i][j] = v1;
+            a2[i][j] = v2;
         }
+    }
+    if (w == 0) *reinterpret_cast<float2 *>(&xp[0][2 * tx]) = make_float2(0.0f, 0.0f);
+    if (w == kChR / kChRows - 1) *reinterpret_cast<float2 *>(&xg[kChR / kChRows][2 * tx]) = make_float2(0.0f, 0.0f);
+    *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
     __syncthreads();
-    // cells of the loaded region that lie inside the image
-    const int r_lo = max(1, -ri0), r_hi = min(kChR, ny - 1 - ri0);
-    const int c_lo = max(1, -rj0), c_hi = min(kChR, nx - 1 - rj0);
-    // Boundary handling without branches in the cell loops: p1 stays exactly 0
-    // on the last image row and p2 on the last column (their forward
-    // differences are 0 there, and p starts at 0), and cells outside the image
-    // hold 0, so div p adds its four terms unconditionally (adding or
-    // subtracting 0 changes no bits); the forward differences of the last row
-    // and column are masked by multiplying with 0.
-    float m2c[(kChR + 31) / 32];                       // per column of this thread: gj + 1 < nx
+    // the whole region inside the image and clear of its last row and column
+    const bool interior = ri0 + 1 >= 0 && ri0 + kChR + 1 < ny && rj0 + 1 >= 0 && rj0 + kChR + 1 < nx;
+    if (interior)
+        chambolle_steps_regs<false>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
+    else
+        chambolle_steps_regs<true>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
+    // write the central tile: region rows and columns kChK + 1 .. kChR - kChK
 #pragma unroll
-    for (int q = 0; q < (kChR + 31) / 32; ++q) {
-        const int c = c_lo + tx + 32 * q;
-        m2c[q] = (rj0 + c + 1 < nx) ? 1.0f : 0.0f;
-    }
-    for (int st = 0; st < steps; ++st) {
-        for (int r = r_lo + ty; r <= r_hi; r += 8) {
-            for (int c = c_lo + tx; c <= c_hi; c += 32) {
-                float d = 0.0f;
-                d = __fadd_rn(d, s1[r][c]);
-                d = __fsub_rn(d, s1[r - 1][c]);
-                d = __fadd_rn(d, s2[r][c]);
-                d = __fsub_rn(d, s2[r][c - 1]);
-                sg[r][c] = __fsub_rn(d, sz[r][c]);
-            }
-        }
-        __syncthreads();
-        for (int r = r_lo + ty; r <= r_hi; r += 8) {
-            const float m1 = (ri0 + r + 1 < ny) ? 1.0f : 0.0f;
+    for (int i = 0; i < kChRows; ++i)
 #pragma unroll
-            for (int q = 0; q < (kChR + 31) / 32; ++q) {
-                const int c = c_lo + tx + 32 * q;
-                if (c > c_hi) break;
-                const float g0 = sg[r][c];
-                const float g1 = __fmul_rn(m1, __fsub_rn(sg[r + 1][c], g0));
-                const float g2 = __fmul_rn(m2c[q], __fsub_rn(sg[r][c + 1], g0));
-                const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
-                s1[r][c] = __fmul_rn(fmaf(tau, g1, s1[r][c]), inv);
-                s2[r][c] = __fmul_rn(fmaf(tau, g2, s2[r][c]), inv);
-            }
-        }
-        __syncthreads();
-    }
-    constexpr int kChT = chambolle_tile_size(kChK);
-    for (int r = ty; r < kChT; r += 8)
-        for (int c = tx; c < kChT; c += 32) {
-            const int gi = i0 + r, gj = j0 + c;
-            if (gi < ny && gj < nx) {
+        for (int j = 0; j < 2; ++j) {
+            const int r = r0 + i, c = c0 + j, gi = ri0 + r, gj = rj0 + c;
+            if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && gi < ny && gj < nx) {
                 const size_t k = (size_t)gi * nx + gj;
-                q1[k] = s1[r + kChK + 1][c + kChK + 1];
-                q2[k] = s2[r + kChK + 1][c + kChK + 1];
+                q1[k] = a1[i][j];
+                q2[k] = a2[i][j];
             }
         }
 }

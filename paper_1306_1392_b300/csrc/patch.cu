@@ -69,55 +69,131 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-// C [M][N] = alpha A [M][K] B [K][N] (row-major, float32 sums in k order):
-// 64 x 64 output tiles, K in chunks of 16 staged in shared memory, each
-// thread 4 x 4 outputs.  Both patch products use it: P = W D (M = patches,
-// K = atoms, N = m^2) and G = 2 P' D^T (K = m^2, N = atoms).
-constexpr int kGT = 64, kGK = 16;
+// C [M][N] = alpha A [M][K] B [K][N] (row-major, float32 sums in k order).
+// Both patch products use it: P = W D (M = patches, K = atoms, N = m^2) and
+// G = 2 P' D^T (K = m^2, N = atoms).  The products are tall and skinny (N and
+// K of tens to hundreds), so a CTA of 16 x 16 threads takes 128 rows and all
+// of N at once when N <= 192 (16 * kTN columns), and A is read from HBM once.
+// Thread (tr, tc) owns rows {4 tr .. 4 tr + 3} and {64 + 4 tr .. 64 + 4 tr + 3}
+// and columns tc + 16 j (j < kTN), so its global stores are coalesced.  K runs
+// in chunks of 16, double-buffered in shared memory by asynchronous 4-byte
+// copies (any K, any alignment; out-of-range elements are zero-filled), the
+// next chunk in flight while the current one is multiplied.  The A chunk is
+// staged transposed (As[k][row]) with the row index XORed by 2k: the 16
+// threads of a half-warp that copy one row (16 consecutive k) then hit 16
+// different banks, and the float4 read of four rows becomes a read of a
+// permuted group of four (the permutation depends on the parity of k only).
+constexpr int kGM = 128, kGK = 16, kGThreads = 256, kGMaxTN = 12;
 
-__global__ void __launch_bounds__(256) gemm_kernel(const float *__restrict__ A, const float *__restrict__ B,
-                                                   float *__restrict__ C, int M, int N, int K, float alpha) {
-    __shared__ __align__(16) float As[kGK][kGT];     // A chunk, transposed: As[k][row]
-    __shared__ __align__(16) float Bs[kGK][kGT];
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+// One k of the product: four rows from each half of the swizzled A chunk
+// (kP: the in-group permutation of this k), kTN columns of B.
+template <int kTN, int kP>
+__device__ __forceinline__ void gemm_step(const float *__restrict__ a_row, const float *__restrict__ b_row, int tr,
+                                          int tc, int sw, float (&acc)[8][kTN]) {
+    const float4 a0 = *reinterpret_cast<const float4 *>(a_row + ((4 * tr) ^ sw));
+    const float4 a1 = *reinterpret_cast<const float4 *>(a_row + ((64 + 4 * tr) ^ sw));
+    const float x0[4] = {a0.x, a0.y, a0.z, a0.w}, x1[4] = {a1.x, a1.y, a1.z, a1.w};
+    float av[8], bv[kTN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        av[i] = x0[i ^ kP];
+        av[4 + i] = x1[i ^ kP];
+    }
+#pragma unroll
+    for (int j = 0; j < kTN; ++j) bv[j] = b_row[tc + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < kTN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+}
+
+template <int kTN>
+__global__ void __launch_bounds__(kGThreads, 2) gemm_kernel(const float *__restrict__ A, const float *__restrict__ B,
+                                                            float *__restrict__ C, int M, int N, int K, float alpha) {
+    constexpr int kBN = 16 * kTN;
+    constexpr int kAV = kGM * kGK / kGThreads;             // A elements per thread per chunk (8)
+    __shared__ __align__(16) float As[2][kGK][kGM];
+    __shared__ __align__(16) float Bs[2][kGK][kBN];
     const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
-    const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kGK) {
-        for (int e = tid; e < kGT * kGK; e += 256) {
-            const int r = e / kGK, k = e % kGK;          // A: consecutive threads along k
+    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kBN;
+    auto fetch = [&](int buf, int k0) {
+#pragma unroll
+        for (int v = 0; v < kAV; ++v) {
+            const int e = tid + v * kGThreads, r = e >> 4, k = e & 15;   // a half-warp copies one row's 16 k
             const int gm = m0 + r, gk = k0 + k;
-            As[k][r] = (gm < M && gk < K) ? A[(size_t)gm * K + gk] : 0.0f;
-            const int kb = e / kGT, c = e % kGT;         // B: consecutive threads along n
-            const int gkb = k0 + kb, gn = n0 + c;
-            Bs[kb][c] = (gkb < K && gn < N) ? B[(size_t)gkb * N + gn] : 0.0f;
+            const bool ok = gm < M && gk < K;
+            cp_async4(&As[buf][k][r ^ (2 * k)], ok ? A + (size_t)gm * K + gk : A, ok);
+        }
+#pragma unroll
+        for (int v = 0; v < kTN; ++v) {
+            const int e = tid + v * kGThreads, kb = e / kBN, c = e - kb * kBN;
+            const int gk = k0 + kb, gn = n0 + c;
+            const bool ok = gk < K && gn < N;
+            cp_async4(&Bs[buf][kb][c], ok ? B + (size_t)gk * N + gn : B, ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float acc[8][kTN] = {};
+    fetch(0, 0);
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += kGK, buf ^= 1) {
+        if (k0 + kGK < K) {
+            fetch(buf ^ 1, k0 + kGK);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kGK; ++k) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[k][4 * tr]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][4 * tc]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+#pragma unroll 2
+        for (int k = 0; k < kGK; k += 2) {
+            gemm_step<kTN, 0>(As[buf][k], Bs[buf][k], tr, tc, (2 * k) & ~3, acc);        // even k: rows in order
+            gemm_step<kTN, 2>(As[buf][k + 1], Bs[buf][k + 1], tr, tc, (2 * k + 2) & ~3, acc);  // odd k: pairs swapped
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + 4 * tr + i;
+    for (int i = 0; i < 8; ++i) {
+        const int gm = m0 + (i < 4 ? 4 * tr + i : 64 + 4 * tr + i - 4);
         if (gm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + 4 * tc + j;
+        for (int j = 0; j < kTN; ++j) {
+            const int gn = n0 + tc + 16 * j;
             if (gn < N) C[(size_t)gm * N + gn] = alpha * acc[i][j];
         }
     }
 }
 
+template <int kTN>
+void gemm_launch(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
+    gemm_kernel<kTN><<<dim3((M + kGM - 1) / kGM, (N + 16 * kTN - 1) / (16 * kTN)), kGThreads, 0, st>>>(A, B, C, M, N,
+                                                                                                       K, alpha);
+}
+
+// Column tile: all of N in one tile up to 16 * kGMaxTN columns, else tiles of 128.
+int gemm_tn(int N) { return N <= 16 * kGMaxTN ? (N + 15) / 16 : 8; }
+
 void gemm(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
-    gemm_kernel<<<dim3((M + kGT - 1) / kGT, (N + kGT - 1) / kGT), 256, 0, st>>>(A, B, C, M, N, K, alpha);
+    switch (gemm_tn(N)) {
+    case 1: gemm_launch<1>(A, B, C, M, N, K, alpha, st); break;
+    case 2: gemm_launch<2>(A, B, C, M, N, K, alpha, st); break;
+    case 3: gemm_launch<3>(A, B, C, M, N, K, alpha, st); break;
+    case 4: gemm_launch<4>(A, B, C, M, N, K, alpha, st); break;
+    case 5: gemm_launch<5>(A, B, C, M, N, K, alpha, st); break;
+    case 6: gemm_launch<6>(A, B, C, M, N, K, alpha, st); break;
+    case 7: gemm_launch<7>(A, B, C, M, N, K, alpha, st); break;
+    case 8: gemm_launch<8>(A, B, C, M, N, K, alpha, st); break;
+    case 9: gemm_launch<9>(A, B, C, M, N, K, alpha, st); break;
+    case 10: gemm_launch<10>(A, B, C, M, N, K, alpha, st); break;
+    case 11: gemm_launch<11>(A, B, C, M, N, K, alpha, st); break;
+    default: gemm_launch<12>(A, B, C, M, N, K, alpha, st); break;
+    }
 }
 
 // Eq. 7 and the patch sums: one thread per pixel.

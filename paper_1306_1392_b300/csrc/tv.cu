@@ -153,7 +153,7 @@ __global__ void grad_step_kernel(const float *__restrict__ y, const float *__res
 // chambolle.cuh): launch 0 starts from a zero field and writes the "a"
 // buffers, launch m > 0 reads a (m odd) or b and writes the other.
 template <int K>
-__global__ void __launch_bounds__(kChThreads)
+__global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, float *pb1, float *pb2,
                        const float *__restrict__ lam, float tau, int nx, int ny, int m, int steps, int tiles_x) {
     const size_t off = (size_t)blockIdx.y * nx * ny;

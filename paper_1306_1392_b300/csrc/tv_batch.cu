@@ -87,7 +87,7 @@ __global__ void b_grad_step(const TvSlice *__restrict__ d, const int4 *__restric
 // Launch m of the fused Chambolle steps (see chambolle.cuh) on tile
 // (items[k].y, items[k].z) of slice items[k].x; slices with beta = 0 skip.
 template <int K>
-__global__ void __launch_bounds__(kChThreads)
+__global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
