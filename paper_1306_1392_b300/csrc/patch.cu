@@ -39,18 +39,16 @@ __host__ __device__ __forceinline__ int axis_start(int k, int n, int m, int stri
 }
 
 // Core patch of every coordinate along one axis: the nearest centre
-// start + (m-1)/2, ties to the lower index (Eq. 6 on a product grid).
+// start + (m-1)/2, ties to the lower index (Eq. 6 on a product grid).  The
+// starts increase strictly with k, so along the axis the nearest centre only
+// moves forward: one pass, advancing while the next centre is strictly nearer.
 void core_table(int n, int m, int stride, int K, std::vector<int> &core) {
     core.assign(n, 0);
+    auto dist = [&](int i, int k) { return std::fabs((double)i - ((double)axis_start(k, n, m, stride) + 0.5 * (m - 1))); };
+    int k = 0;
     for (int i = 0; i < n; ++i) {
-        double bd = 1e300;
-        for (int k = 0; k < K; ++k) {
-            const double d = std::fabs((double)i - ((double)axis_start(k, n, m, stride) + 0.5 * (m - 1)));
-            if (d < bd) {
-                bd = d;
-                core[i] = k;
-            }
-        }
+        while (k + 1 < K && dist(i, k + 1) < dist(i, k)) ++k;
+        core[i] = k;
     }
 }
 
