@@ -85,6 +85,7 @@ struct BatchSlice {
     float *bp_out;
     const float *proj_in;
     float *proj_inT, *proj_out;
+    int proj_nseg;          // row segments of the projector (proj_segments of this geometry)
 };
 int bp_tiles(int nx, int ny, int *tx, int *ty);
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
@@ -92,6 +93,8 @@ int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_
 int proj_blocks(int n_angles, int n_bins, int *nb, int *na);
 // true: the 512-column staging variant of the projector (sparse angle sets)
 bool project_wide(int nx, int ny, int n_angles);
+// row segments of the projector's walks for a slice geometry (fixes the float32 summation order)
+int proj_segments(const pyhst_geometry *g);
 // Sets the projector kernels' shared-memory attributes (call before a
 // stream capture that launches them).
 int set_proj_attr();

@@ -140,7 +140,8 @@ struct WalkArgs {
 // masked angles.  Only the band of each chunk is staged.
 template <int kPW>
 __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 acc[2],
-                                          float (*strip)[kPR][kPW], int *L0_s, int *H_s, int c_lo, int c_hi) {
+                                          float2 (*tot)[kPThreads], float scale, int per, float (*strip)[kPR][kPW], int *L0_s,
+                                          int *H_s, int c_lo, int c_hi) {
     constexpr int kPVec = pvec<kPW>();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int asub = lane >> 4;
@@ -204,6 +205,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     commit(0, 0);
     __syncthreads();
     const float2 m15 = make_float2(-1.5f, -1.5f);
+    int seg_left = per - c_lo % per;       // chunks until the current row segment ends
     for (int c = 0; c < n_chunks; ++c) {
         const int cur = c & 1;
         const bool more = c + 1 < n_chunks;
@@ -249,19 +251,34 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                 acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
             }
         }
+        // end of a row segment: its scaled sum joins the total (in segment order)
+        if (--seg_left == 0 || !more) {
+            seg_left = per;
+            const float2 s2 = make_float2(scale, scale);
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                tot[p][tid] = add2(tot[p][tid], mul2(s2, acc[p]));
+                acc[p] = make_float2(0.0f, 0.0f);
+            }
+        }
         if (more) commit(cur ^ 1, (c + 1) % 3);
         __syncthreads();
     }
 }
 
-// One CTA: angles [g0, g0 + 8) x bins [b0, b0 + 128) of one slice, rows of
-// segment seg of nseg; img/imgT are that slice's image and its transpose,
-// sino its sinogram (or the segment's partial sinogram).
+// One CTA: angles [g0, g0 + 8) x bins [b0, b0 + 128) of one slice;
+// img/imgT are that slice's image and its transpose.  The rows of each walk
+// fall into nseg segments of equal chunk counts (the last one shorter), and
+// a ray's value is the sum, in segment order, of its scaled per-segment sums.
+// seg >= 0: this CTA walks segment seg only and writes that partial (the
+// partials are added in order afterwards); seg < 0: it walks all segments and
+// adds them itself.  Both give the same bits, so the segmentation (a
+// property of the slice geometry) and not the launch decides the rounding.
 template <int kPW>
 __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, const float *__restrict__ img,
                                          const float *__restrict__ imgT, float *__restrict__ sino, int n_angles,
                                          int n_bins, int nx, int ny, double cx, double cy, float scale, int g0,
-                                         int b0, int seg = 0, int nseg = 1) {
+                                         int b0, int seg, int nseg) {
     extern __shared__ __align__(16) float proj_smem[];
     float (*strip)[kPR][kPW] = reinterpret_cast<float (*)[kPR][kPW]>(proj_smem);
     __shared__ RayGeom rg[kPG];
@@ -284,7 +301,9 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
     if (tid < kPG && rg[tid].major >= 0) atomicOr(&phase_mask[rg[tid].major], 1 << tid);
     __syncthreads();
 
-    float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};   // rays (0,1), (2,3)
+    float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};   // rays (0,1), (2,3): segment sums
+    __shared__ float2 tot[2][kPThreads];    // per thread: scaled sums of its finished segments
+    tot[0][tid] = tot[1][tid] = make_float2(0.0f, 0.0f);
 
     for (int major = 0; major < 2; ++major) {
         const int mask_all = phase_mask[major];
@@ -320,31 +339,32 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
         __syncthreads();
         const int gs = fits_s;
         const int nch = (w.R + kPR - 1) / kPR, per = (nch + nseg - 1) / nseg;
-        const int c_lo = seg * per, c_hi = min(nch, c_lo + per);
+        const int c_lo = seg >= 0 ? seg * per : 0, c_hi = seg >= 0 ? min(nch, c_lo + per) : nch;
         for (int s0 = 0; s0 < kPG; s0 += gs) {
             const int m = mask_all & (((1 << gs) - 1) << s0);
-            if (m) walk_pass(w, rg, m, acc, strip, L0_s, H_s, c_lo, c_hi);
+            if (m) walk_pass(w, rg, m, acc, tot, scale, per, strip, L0_s, H_s, c_lo, c_hi);
         }
         __syncthreads();
     }
     if (b <= bhi) {
-        const float r[kPRays] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y};
+        const float r[kPRays] = {tot[0][tid].x, tot[0][tid].y, tot[1][tid].x, tot[1][tid].y};
 #pragma unroll
         for (int k = 0; k < kPRays; ++k) {
             const int a = g0 + asub + 2 * k;
-            if (a < n_angles) sino[(size_t)a * n_bins + b] = scale * r[k];
+            if (a < n_angles) sino[(size_t)a * n_bins + b] = r[k];
         }
     }
 }
 
-// blockIdx.z = slice * nseg + segment; with nseg > 1 the output is the
-// partial sinogram of the segment, part[slice][segment][angle][bin].
+// split: blockIdx.z = slice * nseg + segment, and the output is the partial
+// sinogram of the segment, part[slice][segment][angle][bin]; otherwise
+// blockIdx.z = slice and the CTA adds the segments itself.
 template <int PW>
 __global__ void __launch_bounds__(kPThreads, 3)
 proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
             float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
-            float scale, int nseg) {
-    const int slice = blockIdx.z / nseg, seg = blockIdx.z % nseg;
+            float scale, int nseg, int split) {
+    const int slice = split ? blockIdx.z / nseg : blockIdx.z, seg = split ? blockIdx.z % nseg : -1;
     const size_t img_off = (size_t)slice * nx * ny;
     proj_cta<PW>(tab, img + img_off, imgT + img_off, sino + (size_t)blockIdx.z * n_angles * n_bins, n_angles, n_bins,
                  nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB, seg, nseg);
@@ -368,7 +388,7 @@ proj_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict_
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
     proj_cta<PW>(s.tab, s.proj_in, s.proj_inT, s.proj_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
-                 s.pixel_size, it.z * kPG, it.y * kPB);
+                 s.pixel_size, it.z * kPG, it.y * kPB, -1, s.proj_nseg);
 }
 
 // Mixed batch transpose: CTA k moves 32 x 32 tile (items[k].y, items[k].z) of slice items[k].x.
@@ -437,24 +457,35 @@ int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n
     return cuda_status("batched projection kernel");
 }
 
-// Row segments of one launch: enough CTAs to fill the GPU a few times, at
-// least 4 chunks (64 rows) per segment.
+// Row segments of a slice geometry: when one slice gives few CTAs, enough
+// segments to fill the GPU a few times, at least 4 chunks (64 rows) each.
+// A property of the slice geometry alone (not of how many slices a call
+// holds), since the segments fix the order of the float32 sums.
 int proj_segments(const pyhst_geometry *g) {
-    const long ctas = (long)((g->n_bins + kPB - 1) / kPB) * ((g->n_angles + kPG - 1) / kPG) * g->n_slices;
+    const long ctas = (long)((g->n_bins + kPB - 1) / kPB) * ((g->n_angles + kPG - 1) / kPG);
     if (ctas >= kPTargetCtas) return 1;
     const int cap = std::max(1, std::min(g->nx, g->ny) / (kPR * 4));
-    const int zcap = std::max(1, 65535 / std::max(1, g->n_slices));
-    return (int)std::max(1L, std::min<long>({(kPTargetCtas + ctas - 1) / ctas, (long)cap, (long)zcap}));
+    return (int)std::max(1L, std::min<long>((kPTargetCtas + ctas - 1) / ctas, (long)cap));
 }
 
-// Transposed image, then (with row segments) the partial sinograms; the
+namespace {
+// Segments as separate CTAs (partials added afterwards) when the call has
+// few CTAs; otherwise each CTA adds its own segments (same bits).
+bool proj_split(const pyhst_geometry *g, int nseg) {
+    const long ctas = (long)((g->n_bins + kPB - 1) / kPB) * ((g->n_angles + kPG - 1) / kPG) * g->n_slices;
+    return nseg > 1 && ctas < kPTargetCtas && (long)g->n_slices * nseg <= 65535;
+}
+}  // namespace
+
+// Transposed image, then (for split launches) the partial sinograms; the
 // partials of a 1-slice call fit too, since callers also project single
 // slices of their geometry.
 size_t project_scratch_bytes(const pyhst_geometry *g) {
     pyhst_geometry g1 = *g;
     g1.n_slices = 1;
-    const int ns = proj_segments(g), n1 = proj_segments(&g1);
-    const size_t part = std::max((size_t)(ns > 1 ? ns : 0) * g->n_slices, (size_t)(n1 > 1 ? n1 : 0)) *
+    const int ns = proj_segments(g);
+    const size_t part = std::max(proj_split(g, ns) ? (size_t)ns * g->n_slices : 0,
+                                 proj_split(&g1, ns) ? (size_t)ns : 0) *
                         (size_t)g->n_angles * g->n_bins;
     return align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices) + align_up(sizeof(float) * part);
 }
@@ -468,20 +499,21 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     if (rc) return rc;
     if ((rc = set_proj_attr())) return rc;
     const int nseg = proj_segments(g);
+    const bool split = proj_split(g, nseg);
     float *part = xt + align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices) / sizeof(float);
-    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG, g->n_slices * nseg);
+    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG, g->n_slices * (split ? nseg : 1));
     {
         ProfScope prof(kProfProject, st);
-        float *dst = nseg > 1 ? part : sino;
+        float *dst = split ? part : sino;
         if (project_wide(g->nx, g->ny, g->n_angles))
             proj_kernel<512><<<grid, kPThreads, psmem<512>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
-                                                                    g->ny, g->cx, g->cy, scale, nseg);
+                                                                    g->ny, g->cx, g->cy, scale, nseg, split);
         else
             proj_kernel<256><<<grid, kPThreads, psmem<256>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
-                                                                    g->ny, g->cx, g->cy, scale, nseg);
+                                                                    g->ny, g->cx, g->cy, scale, nseg, split);
     }
     if ((rc = cuda_status("projection kernel"))) return rc;
-    if (nseg > 1) {
+    if (split) {
         const size_t per = (size_t)g->n_angles * g->n_bins;
         proj_reduce_kernel<<<dim3((unsigned)((per + 255) / 256), g->n_slices), 256, 0, st>>>(part, sino, per, nseg);
         rc = cuda_status("projection segment sum");

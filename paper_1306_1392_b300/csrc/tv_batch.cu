@@ -498,6 +498,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         b.n_angles = g.n_angles; b.n_bins = g.n_bins; b.nx = g.nx; b.ny = g.ny;
         b.cx = g.cx; b.cy = g.cy; b.pixel_size = g.pixel_size;
         b.proj_inT = img(9, s);
+        b.proj_nseg = proj_segments(&g);
         // gradient back-projection of the residual P y - sino
         b.bp_a = t.Ay; b.bp_b = items[s].sino; b.bp_out = t.g;
         ev[s] = b; ev[s].proj_in = t.xb; ev[s].proj_out = t.Axb;   // even iterations write xb, Axb

@@ -102,6 +102,32 @@ def test_project_parity(P, orc, cuda_device, case):
             close(f64(got[z]), ref)
 
 
+@pytest.mark.parametrize("na,ns,n_check", [(2000, 4, 24), (150, 1, 30)])
+def test_project_full_size_sampled_angles(P, orc, cuda_device, na, ns, n_check):
+    """The projector at full size: a 2048^2 grid with 2048 bins, either the
+    dense 2000-angle set in 4-slice launches (the back-projector's workload)
+    or 150 angles (the sparse variant: 512-column staging and row segments).
+    Each sinogram row depends on its own angle only, so sampled angles
+    (including the first, the last and those next to 45 and 135 degrees,
+    where the walk switches between rows and columns) are checked whole
+    against the oracle projecting just those angles."""
+    n = 2048
+    ang = (np.arange(na) * math.pi / na).astype(np.float32)
+    axis = np.full(na, (n - 1) / 2.0 + 0.37, np.float32)
+    geo = geometry(P, ang, axis, n, n, n, 2.0 / n, cuda_device)
+    g = torch.Generator(device=cuda_device).manual_seed(na)
+    img = torch.rand((ns, n, n), device=cuda_device, generator=g)
+    got = P.pyhst_project(geo, img)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(na)
+    near = [int(np.argmin(np.abs(ang - t))) + d for t in (math.pi / 4, 3 * math.pi / 4) for d in (-1, 0, 1)]
+    sel = sorted(set([0, na - 1] + [k for k in near if 0 <= k < na] + list(rng.choice(na, n_check, replace=False))))
+    for z in sorted({0, ns - 1}):
+        ref = orc.project(img[z].double().cpu().numpy(), ang[sel].astype(np.float64), axis[sel].astype(np.float64),
+                          n, geo.pixel_size)
+        close(f64(got[z][sel]), ref)
+
+
 def test_projector_pair_is_adjoint(P, cuda_device):
     """<P x, y> = <x, P^T y> for the GPU pair (float32 outputs, float64 dots)."""
     g = np.random.default_rng(9)

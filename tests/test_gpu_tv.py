@@ -40,6 +40,34 @@ def test_tv_prox_parity(P, orc, cuda_device, shape, lam, n_inner):
         assert rel(got[k], ref) <= 1e-5
 
 
+def test_tv_prox_full_size_sampled(P, orc, cuda_device):
+    """The prox at the size its kernel benchmark runs (16 x 1024^2, 20
+    steps, the autotuned steps per launch): sampled pixels against the
+    oracle's prox of a crop around each.  A step reads neighbours at
+    Chebyshev distance 1, so after n steps the crop's own borders have not
+    reached a pixel n + 3 away from them, and the crop gives the full
+    image's value there; pixels on the image border keep the true border."""
+    n, ns, n_inner, lam = 1024, 16, 20, 0.05
+    g = torch.Generator(device=cuda_device).manual_seed(11)
+    z = torch.randn((ns, n, n), device=cuda_device, generator=g)
+    P.pyhst_autotune_tv_prox(z, lam, n_inner)
+    got = P.pyhst_tv_prox(z, lam, n_inner).cpu().numpy()
+    zc = z.cpu().numpy()
+    rng = np.random.default_rng(3)
+    R = n_inner + 3
+    pts = list(zip(rng.integers(0, ns, 40), rng.integers(0, n, 40), rng.integers(0, n, 40)))
+    pts += [(0, 0, 0), (1, n - 1, n - 1), (2, 0, n - 1), (3, n - 1, 0), (4, n // 2, 0), (15, 0, n // 2),
+            (7, 53, 54), (8, 54, 107)]      # on tile seams of the fused kernel's output tiles
+    gv, rv = [], []
+    for s_, i, j in pts:
+        i0, i1, j0, j1 = max(0, i - R), min(n, i + R + 1), max(0, j - R), min(n, j + R + 1)
+        ref, _, _ = orc.tv_prox(zc[s_, i0:i1, j0:j1].astype(np.float64), lam, n_inner)
+        rv.append(ref[i - i0, j - j0])
+        gv.append(got[s_, i, j])
+    assert rel(gv, rv) <= 1e-5
+    P.pyhst_set_tv_prox_steps(n, n, 0)
+
+
 def test_tv_prox_zero_lambda_is_identity(P, cuda_device):
     z = torch.randn(1, 40, 30, device=cuda_device)
     torch.testing.assert_close(P.pyhst_tv_prox(z, 0.0), z, rtol=0, atol=0)
@@ -118,7 +146,7 @@ def test_tv_solve_energy_decreases_and_beats_fbp(P, cuda_device):
 
 
 # ------------------------------------------------------------------ mixed batch
-def _mixed(P, dev):
+def _mixed(P, orc, dev):
     """Five slices of three geometries: 48^2/40 angles, 64^2/24 angles and a
     non-square 40 x 32 grid with 30 angles and an off-centre axis."""
     out = []
@@ -136,9 +164,10 @@ def _mixed(P, dev):
         g = np.random.default_rng(seed)
         img = np.zeros((ny, nx))
         img[ny // 4: 3 * ny // 4, nx // 3: 2 * nx // 3] = 1.0
-        sino = P.pyhst_project(geo, torch.from_numpy(img.astype(np.float32)).to(dev))[0]
-        sino = (sino + 0.01 * torch.from_numpy(g.standard_normal(sino.shape).astype(np.float32)).to(dev)).contiguous()
-        out.append((geo, sino, ang, axis, nb))
+        # the oracle's projector makes the data (scaled like pyhst_project)
+        sino = orc.project(img, ang.double().numpy(), axis.double().numpy(), nb, scale=2.0 / max(nx, ny))
+        sino = (sino + 0.01 * g.standard_normal(sino.shape)).astype(np.float32)
+        out.append((geo, torch.from_numpy(sino).to(dev).contiguous(), ang, axis, nb))
     return out
 
 
@@ -146,7 +175,7 @@ def test_batch_matches_single_slice_solves(P, orc, cuda_device):
     """With the same step size, every slice of a mixed batch equals its
     single-slice solve bit for bit (same kernels), its energies agree to
     1e-9, and it matches the FP64 oracle like the single-slice solver."""
-    items = _mixed(P, cuda_device)
+    items = _mixed(P, orc, cuda_device)
     L = 1.01 * max(orc.power_iteration(orc.Geometry(a.double().numpy(), ax.double().numpy(), nb, g.nx, g.ny,
                                                     g.pixel_size), np.ones((g.ny, g.nx)), 40)[0]
                    for g, _, a, ax, nb in items)
@@ -164,10 +193,38 @@ def test_batch_matches_single_slice_solves(P, orc, cuda_device):
     assert torch.all(lip == L)
 
 
-def test_batch_step_size_per_geometry(P, cuda_device):
+def test_batch_at_benchmark_sizes(P, orc, cuda_device):
+    """One slice of each reduced-dose size (256^2 / 50, 512^2 / 100 and
+    1024^2 / 200 angles, bins = N, Poisson 1e4 foams) in one batched solve
+    with the benchmark's 20 Chambolle steps and tuned fusion depth: every
+    slice equals its single-slice solve bit for bit, and after 3 FISTA
+    iterations matches the oracle's FISTA with the same step size."""
+    items, ogs = [], []
+    for k, (n, na) in enumerate([(256, 50), (512, 100), (1024, 200)]):
+        fs = acq.foam_slice(n, na, seed=3000 + k, truth=False)
+        geo = P.Geometry(fs.angles.to(cuda_device), fs.axis.to(cuda_device), n, n, n, fs.pixel_size)
+        items.append((geo, fs.extra["sino"].to(cuda_device).contiguous(), fs.extra["sino"]))
+        ogs.append(orc.Geometry(fs.angles.double().numpy(), fs.axis.double().numpy(), n, n, n, fs.pixel_size))
+        z = torch.randn((2, n, n), device=cuda_device, generator=torch.Generator(device=cuda_device).manual_seed(n))
+        P.pyhst_autotune_tv_prox(z, 0.01, 20)
+    L = 1.01 * max(orc.power_iteration(og, np.ones((og.ny, og.nx)), 8)[0] for og in ogs)
+    opts = P.TvOptions(beta=1e-3, n_iter=3, n_inner=20, lipschitz=L)
+    xs, es, _ = P.pyhst_tv_solve_batch([(g, s, None) for g, s, _ in items], opts)
+    torch.cuda.synchronize()
+    for k, ((g, s, s_host), og) in enumerate(zip(items, ogs)):
+        x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), opts)
+        assert torch.equal(xs[k], x1[0]), k
+        xr, er = orc.fista(og, s_host.double().numpy(), 1e-3, L, 3, n_inner=20)
+        assert rel(xs[k].cpu().numpy(), xr) <= 1e-4
+        np.testing.assert_allclose(es[k].cpu().numpy(), er, rtol=1e-5)
+    for n in (256, 512, 1024):
+        P.pyhst_set_tv_prox_steps(n, n, 0)
+
+
+def test_batch_step_size_per_geometry(P, orc, cuda_device):
     """Estimated L: one power iteration per distinct geometry, equal (to
     float64 summation order) to the single-slice estimate."""
-    items = _mixed(P, cuda_device)
+    items = _mixed(P, orc, cuda_device)
     opts = P.TvOptions(beta=2e-3, n_iter=3, n_inner=5, n_power_iter=25)
     _, _, lip = P.pyhst_tv_solve_batch([(g, s, None) for g, s, *_ in items], opts)
     for k, (g, s, *_r) in enumerate(items):
@@ -177,8 +234,8 @@ def test_batch_step_size_per_geometry(P, cuda_device):
 
 
 @pytest.mark.parametrize("fista,beta,warm", [(False, 2e-3, False), (True, 0.0, False), (True, 4e-3, True)])
-def test_batch_variants(P, cuda_device, fista, beta, warm):
-    items = _mixed(P, cuda_device)
+def test_batch_variants(P, orc, cuda_device, fista, beta, warm):
+    items = _mixed(P, orc, cuda_device)
     L = 5.0
     opts = P.TvOptions(beta=beta, n_iter=9, n_inner=6, lipschitz=L, use_fista=fista, warm_start=warm)
     x0s = [torch.rand((g.ny, g.nx), device=cuda_device) for g, *_ in items]
@@ -189,10 +246,10 @@ def test_batch_variants(P, cuda_device, fista, beta, warm):
         np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
 
 
-def test_batch_per_item_beta(P, cuda_device):
+def test_batch_per_item_beta(P, orc, cuda_device):
     """Each batch item may carry its own beta (0 included): every slice
     equals its single-slice solve with that beta, bit for bit."""
-    items = _mixed(P, cuda_device)
+    items = _mixed(P, orc, cuda_device)
     betas = [1e-3, 0.0, 5e-3, 2e-3, None]
     opts = P.TvOptions(beta=3e-3, n_iter=7, n_inner=6, lipschitz=6.0)
     xs, es, _ = P.pyhst_tv_solve_batch([(g, s, None, b) for (g, s, *_), b in zip(items, betas)], opts)
@@ -269,10 +326,10 @@ def test_tv_prox_steps_per_launch_are_bit_identical(P, cuda_device):
         P.pyhst_set_tv_prox_steps(133, 150, 0)
 
 
-def test_batch_solve_with_tuned_steps_matches_default(P, cuda_device):
+def test_batch_solve_with_tuned_steps_matches_default(P, orc, cuda_device):
     """The batched solver builds its Chambolle tiles for the tuned choice of
     its largest slice; the result is the same bits as with the default."""
-    items = _mixed(P, cuda_device)
+    items = _mixed(P, orc, cuda_device)
     opts = P.TvOptions(beta=3e-3, n_iter=6, n_inner=7, lipschitz=50.0)
     xs0, _, _ = P.pyhst_tv_solve_batch([(g, s, None) for g, s, *_ in items], opts, energy=False)
     try:
