@@ -458,14 +458,28 @@ int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n
 }
 
 // Row segments of a slice geometry: when one slice gives few CTAs, enough
-// segments to fill the GPU a few times, at least 4 chunks (64 rows) each.
-// A property of the slice geometry alone (not of how many slices a call
-// holds), since the segments fix the order of the float32 sums.
+// segments to fill the GPU a few times (at least 4 waves of 3 CTAs per SM),
+// at least 4 chunks (64 rows) each; between that count and twice it, the one
+// whose last wave is fullest.  A property of the slice geometry alone (not of
+// how many slices a call holds), since the segments fix the order of the
+// float32 sums.
 int proj_segments(const pyhst_geometry *g) {
     const long ctas = (long)((g->n_bins + kPB - 1) / kPB) * ((g->n_angles + kPG - 1) / kPG);
     if (ctas >= kPTargetCtas) return 1;
-    const int cap = std::max(1, std::min(g->nx, g->ny) / (kPR * 4));
-    return (int)std::max(1L, std::min<long>((kPTargetCtas + ctas - 1) / ctas, (long)cap));
+    const long cap = std::max(1, std::min(g->nx, g->ny) / (kPR * 4));
+    const long lo = std::min(cap, (kPTargetCtas + ctas - 1) / ctas), hi = std::min(cap, 2 * lo);
+    constexpr long wave = kPTargetCtas / 4;
+    long best = lo;
+    double best_eff = 0.0;
+    for (long n = lo; n <= hi; ++n) {
+        const long c = ctas * n;
+        const double eff = (double)c / (double)(wave * ((c + wave - 1) / wave));
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = n;
+        }
+    }
+    return (int)std::max(1L, best);
 }
 
 namespace {
