@@ -3,19 +3,21 @@
 // with L1 shrinkage on the coefficients.
 //
 // Per gradient evaluation at coefficients W [N][n_atoms]:
-//   gemm_kernel      P = W D                          (N x m^2, float32 sums)
+//   gemm_tc_kernel   P = W D                          (N x m^2; tensor cores, split bf16)
 //   image_kernel     x_j = P[core(j)][j - r], S_j = sum of covering patches,
 //                    Nv_j = their number
 //   (projector)      R = Pi^T (Pi x - y)  (or x - y for denoising)
 //   paux_kernel      P'_{p,i} = rho (P_{p,i} - x_{r_p+i})
 //                               + [core(r_p+i) = p] (R + rho (Nv x - S))_{r_p+i},
 //                    and the penalty sum_p sum_i (x_{r_p+i} - P_{p,i})^2
-//   gemm_kernel      G = 2 P' D^T
+//   gemm_tc_kernel   G = 2 P' D^T
 // Energies and norms are float64 block partials summed in a fixed order.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace pyhst {
 namespace {
@@ -177,7 +179,7 @@ void gemm_launch(const float *A, const float *B, float *C, int M, int N, int K, 
 // Column tile: all of N in one tile up to 16 * kGMaxTN columns, else tiles of 128.
 int gemm_tn(int N) { return N <= 16 * kGMaxTN ? (N + 15) / 16 : 8; }
 
-void gemm(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
+void gemm_simt(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
     switch (gemm_tn(N)) {
     case 1: gemm_launch<1>(A, B, C, M, N, K, alpha, st); break;
     case 2: gemm_launch<2>(A, B, C, M, N, K, alpha, st); break;
@@ -192,6 +194,281 @@ void gemm(const float *A, const float *B, float *C, int M, int N, int K, float a
     case 11: gemm_launch<11>(A, B, C, M, N, K, alpha, st); break;
     default: gemm_launch<12>(A, B, C, M, N, K, alpha, st); break;
     }
+}
+
+// ---------------------------------------------------------------- tensor cores
+// The same product on the tensor cores (tcgen05, bf16 operands, float32
+// accumulation in tensor memory), accurate to float32 rounding: each operand
+// is split into three bf16 terms x = x1 + x2 + x3 (x1 = bf16(x),
+// x2 = bf16(x - x1), x3 = bf16(x - x1 - x2); 24 significant bits in all,
+// the subtractions are exact), and the six products x_i y_j with i + j <= 4
+// are accumulated (the three dropped ones are below 2^-24 of the result's
+// terms).  Persistent CTAs walk 128-row tiles of C: warp 0 issues the MMAs,
+// warps 1-8 read the accumulators back and store C (two warps per
+// tensor-memory lane quarter, alternate 32-column chunks), warps 9-16 stage A
+// in chunks of 32 k through a 4-stage ring (float32 loads issued two chunks
+// ahead into registers, split, K-major 8 x 16-byte core matrices).  B, with N
+// and K padded to multiples of 16, is split and staged once per CTA.  Two
+// accumulators let the read-back of one tile overlap the MMAs of the next.
+// Every wait is bounded; a wait that gives up sets the device status word.
+constexpr int kTcKC = 32;                          // k per ring stage
+constexpr int kTcStages = 4;
+constexpr int kTcProd = 256;                       // staging threads (warps 5-12)
+constexpr int kTcEpi = 256;                        // read-back threads (warps 1-8)
+constexpr int kTcThreads = 32 + kTcEpi + kTcProd;
+constexpr int kTcProd0 = 32 + kTcEpi;               // first staging thread
+constexpr int kTcSplit = 128 * kTcKC * 2;          // bytes of one bf16 term of a stage
+constexpr int kTcStage = 3 * kTcSplit;
+constexpr size_t kTcBMax = 96 * 1024;              // bytes of the staged B terms at most
+constexpr size_t kTcMinSmem = 120 * 1024;          // one CTA per SM (its tensor memory is 512 columns)
+constexpr uint32_t kTcWait = 1u << 22;
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c) {
+    a = __float2bfloat16_rn(x);
+    const float r = x - __bfloat162float(a);
+    b = __float2bfloat16_rn(r);
+    c = __float2bfloat16_rn(r - __bfloat162float(b));
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C, int M, int N, int K,
+               int NT, int Kp, float alpha, unsigned *__restrict__ status) {
+    extern __shared__ __align__(128) uint8_t tc_smem[];
+    uint8_t *ring = tc_smem;                                   // kTcStages x 3 terms x [128 rows][32 k]
+    uint8_t *bs = tc_smem + kTcStages * kTcStage;              // 3 terms x [NT rows][Kp k]
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], acc_full[2], acc_empty[2], drain;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles = (M + 127) / 128, nC = (Kp + kTcKC - 1) / kTcKC;
+    const int n_my = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t acc_stride = NT <= 128 ? 128u : 256u;
+    const uint32_t b_term = (uint32_t)NT * Kp * 2;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, 2 * acc_stride);
+        if (lane == 0) {
+            for (int s = 0; s < kTcStages; ++s) {
+                tc::bar_init(&full[s], kTcProd);
+                tc::bar_init(&empty[s], 1);
+            }
+            for (int b = 0; b < 2; ++b) {
+                tc::bar_init(&acc_full[b], 1);
+                tc::bar_init(&acc_empty[b], kTcEpi);
+            }
+            tc::bar_init(&drain, 1);
+        }
+    } else if (tid >= kTcProd0) {
+        // B [K][N] -> three bf16 terms, N-major rows of Kp k: element (n, k) at
+        // (n / 8) (16 Kp) + (k / 8) 128 + (n % 8) 16 + (k % 8) 2
+        for (int e = tid - kTcProd0; e < NT * Kp; e += kTcProd) {
+            const int n = e / Kp, k = e - n * Kp;
+            const float x = (n < N && k < K) ? B[(size_t)k * N + n] : 0.0f;
+            __nv_bfloat16 t[3];
+            split3(x, t[0], t[1], t[2]);
+            const uint32_t off = (uint32_t)(n >> 3) * (16u * Kp) + (uint32_t)(k >> 3) * 128u + (n & 7) * 16u + (k & 7) * 2u;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) *reinterpret_cast<__nv_bfloat16 *>(bs + j * b_term + off) = t[j];
+        }
+        tc::fence_async_smem();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tm = s_tmem;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ MMA issue
+        const uint32_t idesc = tc::idesc_bf16(128, NT);
+        const uint32_t ring0 = tc::smem_u32(ring), b0 = tc::smem_u32(bs);
+        constexpr int kA[6] = {0, 0, 1, 0, 1, 2}, kB[6] = {0, 1, 0, 2, 1, 0};
+        int q = 0;
+        for (int t = 0; t < n_my && ok; ++t) {
+            const int b = t & 1;
+            if (t >= 2) ok = __all_sync(0xffffffffu, tc::bar_wait(&acc_empty[b], (uint32_t)(((t >> 1) - 1) & 1), kTcWait));
+            if (!ok) break;
+            tc::fence_after();
+            const uint32_t d = tm + (uint32_t)b * acc_stride;
+            for (int c = 0; c < nC; ++c, ++q) {
+                const int s = q % kTcStages;
+                ok = __all_sync(0xffffffffu, tc::bar_wait(&full[s], (uint32_t)((q / kTcStages) & 1), kTcWait));
+                if (!ok) break;
+                tc::fence_after();
+                if (lane == 0) {
+                    for (int j = 0; j < kTcKC / 16; ++j) {
+                        const int kk = c * (kTcKC / 16) + j;        // k step (16 k) within Kp
+                        if (kk * 16 >= Kp) break;
+#pragma unroll
+                        for (int p = 0; p < 6; ++p) {
+                            const uint64_t da = tc::sdesc(ring0 + s * kTcStage + kA[p] * kTcSplit + j * 256, 128, 16 * kTcKC);
+                            const uint64_t db = tc::sdesc(b0 + kB[p] * b_term + kk * 256, 128, 16 * Kp);
+                            tc::mma_bf16(d, da, db, idesc, c > 0 || j > 0 || p > 0);
+                        }
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (lane == 0) tc::mma_commit(&acc_full[b]);
+            __syncwarp();
+        }
+        if (!ok && lane == 0) atomicOr(status, tc::kErrMmaTimeout);
+        // every MMA issued has finished before the tensor memory is freed
+        if (lane == 0) {
+            tc::mma_commit(&drain);
+            if (!tc::bar_wait(&drain, 0, kTcWait)) atomicOr(status, tc::kErrMmaTimeout);
+        }
+        __syncwarp();
+    } else if (tid < kTcProd0) {
+        // ------------------------------------------------------------ read-back
+        const int qd = warp & 3, half = (warp - 1) >> 2;      // lane quarter; even or odd column chunks
+        const bool cvec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+        for (int t = 0; t < n_my; ++t) {
+            const int b = t & 1;
+            ok = __all_sync(0xffffffffu, tc::bar_wait(&acc_full[b], (uint32_t)((t >> 1) & 1), kTcWait));
+            if (!ok) {
+                if (lane == 0) atomicOr(status, tc::kErrMmaTimeout);
+                break;
+            }
+            tc::fence_after();
+            const int row = (blockIdx.x + t * gridDim.x) * 128 + 32 * qd + lane;
+            float *crow = C + (size_t)row * N;
+            for (int j = half; j * 32 < NT; j += 2) {
+                float v[32];
+                tc::tmem_ld32(tm + ((uint32_t)(32 * qd) << 16) + (uint32_t)b * acc_stride + 32u * j, v);
+                if (row < M) {
+                    if (cvec && 32 * j + 32 <= N) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            *reinterpret_cast<float4 *>(crow + 32 * j + 4 * k) =
+                                make_float4(alpha * v[4 * k], alpha * v[4 * k + 1], alpha * v[4 * k + 2],
+                                            alpha * v[4 * k + 3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            const int col = 32 * j + k;
+                            if (col < N) crow[col] = alpha * v[k];
+                        }
+                    }
+                }
+            }
+            tc::fence_before();
+            bar_arrive(&acc_empty[b]);
+        }
+    } else {
+        // ------------------------------------------------------------ staging
+        const int pw = (tid - kTcProd0) >> 5, r8 = lane & 7, kq = lane >> 3;
+        const bool vec = (K & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+        const int total = n_my * nC;
+        // chunk q: tile q / nC of this CTA, k chunk q % nC.  Unit u of a chunk:
+        // 8 rows x 16 k; lane (r8, kq) holds row r8, k 4 kq .. 4 kq + 3.
+        auto fetch = [&](int q, float4 (&x)[4]) {
+            const int t = q / nC, c = q - t * nC;
+            const int m0 = (blockIdx.x + t * gridDim.x) * 128;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int unit = 4 * pw + u, rg = unit >> 1, kg = unit & 1;
+                const int row = m0 + 8 * rg + r8, k = c * kTcKC + 16 * kg + 4 * kq;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (row < M) {
+                    const float *src = A + (size_t)row * K + k;
+                    if (vec && k + 3 < K) {
+                        v = __ldg(reinterpret_cast<const float4 *>(src));
+                    } else {
+                        if (k < K) v.x = __ldg(src);
+                        if (k + 1 < K) v.y = __ldg(src + 1);
+                        if (k + 2 < K) v.z = __ldg(src + 2);
+                        if (k + 3 < K) v.w = __ldg(src + 3);
+                    }
+                }
+                x[u] = v;
+            }
+        };
+        float4 xa[4], xb[4], xc[4];
+        if (total > 0) fetch(0, xa);
+        if (total > 1) fetch(1, xb);
+        for (int q = 0; q < total; ++q) {
+            if (q + 2 < total) fetch(q + 2, xc);           // two chunks ahead
+            const int s = q % kTcStages;
+            if (q >= kTcStages) {
+                ok = __all_sync(0xffffffffu, tc::bar_wait(&empty[s], (uint32_t)(((q / kTcStages) - 1) & 1), kTcWait));
+                if (!ok) {
+                    if (lane == 0) atomicOr(status, tc::kErrMmaTimeout);
+                    break;
+                }
+                tc::fence_after();
+            }
+            uint8_t *st = ring + s * kTcStage;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int unit = 4 * pw + u, rg = unit >> 1, kg = unit & 1;
+                const float x[4] = {xa[u].x, xa[u].y, xa[u].z, xa[u].w};
+                __nv_bfloat16 h[3][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split3(x[i], h[0][i], h[1][i], h[2][i]);
+                const uint32_t off = rg * 512u + (uint32_t)(2 * kg + (kq >> 1)) * 128u + r8 * 16u + (kq & 1) * 8u;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    *reinterpret_cast<uint2 *>(st + j * kTcSplit + off) =
+                        make_uint2(pack_bf2(h[j][0], h[j][1]), pack_bf2(h[j][2], h[j][3]));
+            }
+            tc::fence_async_smem();
+            bar_arrive(&full[s]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xa[u] = xb[u];
+                xb[u] = xc[u];
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_free(tm, 2 * acc_stride);
+    }
+}
+
+int g_sm_count = 0;
+
+bool gemm_tc_fits(int N, int K) {
+    const int NT = (N + 15) & ~15, Kp = (K + 15) & ~15;
+    return N >= 1 && K >= 1 && NT <= 256 && (size_t)3 * NT * Kp * 2 <= kTcBMax;
+}
+
+void gemm_tc(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
+    const int NT = (N + 15) & ~15, Kp = (K + 15) & ~15;
+    const size_t smem = std::max(kTcMinSmem, (size_t)kTcStages * kTcStage + (size_t)3 * NT * Kp * 2);
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+        cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kTcStages * kTcStage + kTcBMax));
+    }
+    const int tiles = (M + 127) / 128;
+    gemm_tc_kernel<<<std::min(tiles, g_sm_count), kTcThreads, smem, st>>>(A, B, C, M, N, K, NT, Kp, alpha,
+                                                                         device_status_ptr());
+}
+
+// Shapes whose padded B fits the tensor-core kernel take it; the rest (more
+// than 256 columns, very long k) take the SIMT kernel.
+void gemm(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
+    if (M <= 0) return;
+    if (gemm_tc_fits(N, K))
+        gemm_tc(A, B, C, M, N, K, alpha, st);
+    else
+        gemm_simt(A, B, C, M, N, K, alpha, st);
 }
 
 // Eq. 7 and the patch sums: one thread per pixel.

@@ -14,7 +14,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-CASES = [((11, 9), 4, 3, 20), ((16, 16), 4, 2, 16), ((21, 34), 6, 4, 40), ((64, 64), 8, 4, 64)]
+# (shape, m, stride, atoms): the dictionary products run on the tensor cores
+# (split-bf16) when the padded B fits, else on the SIMT kernel (260 atoms:
+# G = 2 P' D^T has N = 260 > 256); m = 3 with 10 atoms gives k = 9 and 10
+# (scalar loads, one 16-k step in the last stage).
+CASES = [((11, 9), 4, 3, 20), ((16, 16), 4, 2, 16), ((21, 34), 6, 4, 40), ((64, 64), 8, 4, 64),
+         ((25, 19), 3, 2, 10), ((40, 36), 4, 2, 260), ((130, 70), 8, 4, 144)]
 
 
 def _problem(orc, shape, m, stride, nc, tomo, seed, rho=0.8):
