@@ -199,40 +199,47 @@ void gemm_simt(const float *A, const float *B, float *C, int M, int N, int K, fl
 // ---------------------------------------------------------------- tensor cores
 // The same product on the tensor cores (tcgen05, bf16 operands, float32
 // accumulation in tensor memory), accurate to float32 rounding: each operand
-// is split into three bf16 terms x = x1 + x2 + x3 (x1 = bf16(x),
-// x2 = bf16(x - x1), x3 = bf16(x - x1 - x2); 24 significant bits in all,
-// the subtractions are exact), and the six products x_i y_j with i + j <= 4
-// are accumulated (the three dropped ones are below 2^-24 of the result's
-// terms).  Persistent CTAs walk 128-row tiles of C: warp 0 issues the MMAs,
-// warps 1-8 read the accumulators back and store C (two warps per
-// tensor-memory lane quarter, alternate 32-column chunks), warps 9-16 stage A
-// in chunks of 32 k through a 4-stage ring (float32 loads issued two chunks
-// ahead into registers, split, K-major 8 x 16-byte core matrices).  B, with N
-// and K padded to multiples of 16, is split and staged once per CTA.  Two
-// accumulators let the read-back of one tile overlap the MMAs of the next.
-// Every wait is bounded; a wait that gives up sets the device status word.
+// is split exactly into three bf16 terms x = x1 + x2 + x3 (x1: the leading 8
+// significant bits of x, x2 the next 8 of the remainder, x3 the rest, which
+// has at most 8), and the six products x_i y_j with i + j <= 4 are
+// accumulated (the dropped ones are below 2^-22 of a term, about 1e-7 of the
+// result in practice).  For a padded N of 32 or 64 the B terms, stacked along
+// N, go in as one
+// operand: x1 [y1 y2 y3], x2 [y1 y2], x3 y1 are three MMAs of N = 3, 2 and 1
+// times the padded N into three column blocks of the accumulator, added in the
+// read-back (half the MMAs of one per product).  Persistent CTAs walk 128-row
+// tiles of C: warp 0
+// issues the MMAs; warps 1-8 read the accumulators back (two warps per
+// tensor-memory lane quarter, alternate 32-column chunks), transpose each
+// 32 x 32 block through shared memory and store C rows coalesced; warps 9-16
+// stage A in chunks of 32 k (float32 loads issued three chunks ahead into
+// registers, split, K-major 8 x 16-byte core matrices in a 4-stage ring).  B,
+// with N and K padded to multiples of 16, is split and staged once per CTA.
+// Two accumulators let the read-back of one tile overlap the MMAs of the
+// next.  Every wait is bounded; a wait that gives up sets the device status.
 constexpr int kTcKC = 32;                          // k per ring stage
 constexpr int kTcStages = 4;
-constexpr int kTcProd = 256;                       // staging threads (warps 5-12)
+constexpr int kTcProd = 256;                       // staging threads (warps 9-16)
 constexpr int kTcEpi = 256;                        // read-back threads (warps 1-8)
 constexpr int kTcThreads = 32 + kTcEpi + kTcProd;
-constexpr int kTcProd0 = 32 + kTcEpi;               // first staging thread
+constexpr int kTcProd0 = 32 + kTcEpi;              // first staging thread
 constexpr int kTcSplit = 128 * kTcKC * 2;          // bytes of one bf16 term of a stage
 constexpr int kTcStage = 3 * kTcSplit;
-constexpr size_t kTcBMax = 96 * 1024;              // bytes of the staged B terms at most
+constexpr int kTcEpiBytes = 8 * 32 * 33 * 4;       // a 32 x 33 transpose block per read-back warp
+constexpr size_t kTcBMax = 64 * 1024;              // bytes of the staged B terms at most
 constexpr size_t kTcMinSmem = 120 * 1024;          // one CTA per SM (its tensor memory is 512 columns)
 constexpr uint32_t kTcWait = 1u << 22;
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c) {
-    a = __float2bfloat16_rn(x);
-    const float r = x - __bfloat162float(a);
-    b = __float2bfloat16_rn(r);
-    c = __float2bfloat16_rn(r - __bfloat162float(b));
+// x = x1 + x2 + x3 exactly; each term's bf16 value is the high half of the word.
+__device__ __forceinline__ void split3(float x, uint32_t &a, uint32_t &b, uint32_t &c) {
+    a = __float_as_uint(x) & 0xFFFF0000u;
+    const float r = x - __uint_as_float(a);
+    b = __float_as_uint(r) & 0xFFFF0000u;
+    c = __float_as_uint(r - __uint_as_float(b));
 }
 
-__device__ __forceinline__ uint32_t pack_bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
+// high halves of two words -> one word of two bf16 (lo in the low half)
+__device__ __forceinline__ uint32_t pack_hi(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x7632); }
 
 __device__ __forceinline__ void bar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -243,13 +250,15 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
                int NT, int Kp, float alpha, unsigned *__restrict__ status) {
     extern __shared__ __align__(128) uint8_t tc_smem[];
     uint8_t *ring = tc_smem;                                   // kTcStages x 3 terms x [128 rows][32 k]
-    uint8_t *bs = tc_smem + kTcStages * kTcStage;              // 3 terms x [NT rows][Kp k]
+    float *epi = reinterpret_cast<float *>(tc_smem + kTcStages * kTcStage);   // 8 x [32][33]
+    uint8_t *bs = tc_smem + kTcStages * kTcStage + kTcEpiBytes;              // 3 terms x [NT rows][Kp k]
     __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], acc_full[2], acc_empty[2], drain;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles = (M + 127) / 128, nC = (Kp + kTcKC - 1) / kTcKC;
     const int n_my = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const uint32_t acc_stride = NT <= 128 ? 128u : 256u;
+    const bool stacked = NT == 32 || NT == 64;                  // B terms stacked along N (3 NT <= 256)
+    const uint32_t acc_stride = (NT <= 128 && !stacked) ? 128u : 256u;
     const uint32_t b_term = (uint32_t)NT * Kp * 2;
 
     if (warp == 0) {
@@ -267,15 +276,27 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
         }
     } else if (tid >= kTcProd0) {
         // B [K][N] -> three bf16 terms, N-major rows of Kp k: element (n, k) at
-        // (n / 8) (16 Kp) + (k / 8) 128 + (n % 8) 16 + (k % 8) 2
-        for (int e = tid - kTcProd0; e < NT * Kp; e += kTcProd) {
-            const int n = e / Kp, k = e - n * Kp;
-            const float x = (n < N && k < K) ? B[(size_t)k * N + n] : 0.0f;
-            __nv_bfloat16 t[3];
-            split3(x, t[0], t[1], t[2]);
-            const uint32_t off = (uint32_t)(n >> 3) * (16u * Kp) + (uint32_t)(k >> 3) * 128u + (n & 7) * 16u + (k & 7) * 2u;
+        // (n / 8) (16 Kp) + (k / 8) 128 + (n % 8) 16 + (k % 8) 2.  Consecutive
+        // threads read consecutive n (coalesced), eight loads in flight each.
+        constexpr int kU = 8;
+        for (int e0 = tid - kTcProd0; e0 < NT * Kp; e0 += kU * kTcProd) {
+            float x[kU];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) *reinterpret_cast<__nv_bfloat16 *>(bs + j * b_term + off) = t[j];
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + u * kTcProd, k = e / NT, n = e - k * NT;
+                x[u] = (e < NT * Kp && n < N && k < K) ? __ldg(B + (size_t)k * N + n) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + u * kTcProd, k = e / NT, n = e - k * NT;
+                if (e >= NT * Kp) break;
+                uint32_t t[3];
+                split3(x[u], t[0], t[1], t[2]);
+                const uint32_t off =
+                    (uint32_t)(n >> 3) * (16u * Kp) + (uint32_t)(k >> 3) * 128u + (n & 7) * 16u + (k & 7) * 2u;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) *reinterpret_cast<uint16_t *>(bs + j * b_term + off) = (uint16_t)(t[j] >> 16);
+            }
         }
         tc::fence_async_smem();
     }
@@ -288,6 +309,7 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
     if (warp == 0) {
         // ------------------------------------------------------------ MMA issue
         const uint32_t idesc = tc::idesc_bf16(128, NT);
+        const uint32_t idesc_s[3] = {tc::idesc_bf16(128, 3 * NT), tc::idesc_bf16(128, 2 * NT), idesc};
         const uint32_t ring0 = tc::smem_u32(ring), b0 = tc::smem_u32(bs);
         constexpr int kA[6] = {0, 0, 1, 0, 1, 2}, kB[6] = {0, 1, 0, 2, 1, 0};
         int q = 0;
@@ -306,11 +328,21 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
                     for (int j = 0; j < kTcKC / 16; ++j) {
                         const int kk = c * (kTcKC / 16) + j;        // k step (16 k) within Kp
                         if (kk * 16 >= Kp) break;
+                        if (stacked) {
+                            // x_i against the stacked terms y_1 .. y_(3-i): columns [0, (3 - i) NT)
+                            const uint64_t db = tc::sdesc(b0 + kk * 256, 128, 16 * Kp);
 #pragma unroll
-                        for (int p = 0; p < 6; ++p) {
-                            const uint64_t da = tc::sdesc(ring0 + s * kTcStage + kA[p] * kTcSplit + j * 256, 128, 16 * kTcKC);
-                            const uint64_t db = tc::sdesc(b0 + kB[p] * b_term + kk * 256, 128, 16 * Kp);
-                            tc::mma_bf16(d, da, db, idesc, c > 0 || j > 0 || p > 0);
+                            for (int i = 0; i < 3; ++i) {
+                                const uint64_t da = tc::sdesc(ring0 + s * kTcStage + i * kTcSplit + j * 256, 128, 16 * kTcKC);
+                                tc::mma_bf16(d, da, db, idesc_s[i], c > 0 || j > 0 || i > 0);
+                            }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < 6; ++p) {
+                                const uint64_t da = tc::sdesc(ring0 + s * kTcStage + kA[p] * kTcSplit + j * 256, 128, 16 * kTcKC);
+                                const uint64_t db = tc::sdesc(b0 + kB[p] * b_term + kk * 256, 128, 16 * Kp);
+                                tc::mma_bf16(d, da, db, idesc, c > 0 || j > 0 || p > 0);
+                            }
                         }
                     }
                     tc::mma_commit(&empty[s]);
@@ -331,7 +363,7 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
     } else if (tid < kTcProd0) {
         // ------------------------------------------------------------ read-back
         const int qd = warp & 3, half = (warp - 1) >> 2;      // lane quarter; even or odd column chunks
-        const bool cvec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+        float(*tb)[33] = reinterpret_cast<float(*)[33]>(epi + (warp - 1) * 32 * 33);
         for (int t = 0; t < n_my; ++t) {
             const int b = t & 1;
             ok = __all_sync(0xffffffffu, tc::bar_wait(&acc_full[b], (uint32_t)((t >> 1) & 1), kTcWait));
@@ -340,26 +372,28 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
                 break;
             }
             tc::fence_after();
-            const int row = (blockIdx.x + t * gridDim.x) * 128 + 32 * qd + lane;
-            float *crow = C + (size_t)row * N;
+            const int row0 = (blockIdx.x + t * gridDim.x) * 128 + 32 * qd;   // this warp's 32 rows
             for (int j = half; j * 32 < NT; j += 2) {
                 float v[32];
-                tc::tmem_ld32(tm + ((uint32_t)(32 * qd) << 16) + (uint32_t)b * acc_stride + 32u * j, v);
-                if (row < M) {
-                    if (cvec && 32 * j + 32 <= N) {
+                const uint32_t ta = tm + ((uint32_t)(32 * qd) << 16) + (uint32_t)b * acc_stride + 32u * j;
+                tc::tmem_ld32(ta, v);
+                if (stacked) {                                    // + x_i y_2 block + x_1 y_3 block
+                    float w[32];
+                    tc::tmem_ld32(ta + (uint32_t)NT, w);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            *reinterpret_cast<float4 *>(crow + 32 * j + 4 * k) =
-                                make_float4(alpha * v[4 * k], alpha * v[4 * k + 1], alpha * v[4 * k + 2],
-                                            alpha * v[4 * k + 3]);
-                    } else {
+                    for (int k = 0; k < 32; ++k) v[k] += w[k];
+                    tc::tmem_ld32(ta + 2u * NT, w);
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const int col = 32 * j + k;
-                            if (col < N) crow[col] = alpha * v[k];
-                        }
-                    }
+                    for (int k = 0; k < 32; ++k) v[k] += w[k];
                 }
+#pragma unroll
+                for (int k = 0; k < 32; ++k) tb[lane][k] = v[k];       // lane = row
+                __syncwarp();
+                const int col = 32 * j + lane;
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r)                            // lane = column
+                    if (row0 + r < M && col < N) C[(size_t)(row0 + r) * N + col] = alpha * tb[r][lane];
+                __syncwarp();
             }
             tc::fence_before();
             bar_arrive(&acc_empty[b]);
@@ -381,8 +415,8 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
                 float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (row < M) {
                     const float *src = A + (size_t)row * K + k;
-                    if (vec && k + 3 < K) {
-                        v = __ldg(reinterpret_cast<const float4 *>(src));
+                    if (vec) {
+                        if (k < K) v = __ldg(reinterpret_cast<const float4 *>(src));   // K % 4 == 0
                     } else {
                         if (k < K) v.x = __ldg(src);
                         if (k + 1 < K) v.y = __ldg(src + 1);
@@ -393,11 +427,12 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
                 x[u] = v;
             }
         };
-        float4 xa[4], xb[4], xc[4];
+        float4 xa[4], xb[4], xc[4], xd[4];
         if (total > 0) fetch(0, xa);
         if (total > 1) fetch(1, xb);
+        if (total > 2) fetch(2, xc);
         for (int q = 0; q < total; ++q) {
-            if (q + 2 < total) fetch(q + 2, xc);           // two chunks ahead
+            if (q + 3 < total) fetch(q + 3, xd);           // three chunks ahead
             const int s = q % kTcStages;
             if (q >= kTcStages) {
                 ok = __all_sync(0xffffffffu, tc::bar_wait(&empty[s], (uint32_t)(((q / kTcStages) - 1) & 1), kTcWait));
@@ -411,15 +446,16 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int unit = 4 * pw + u, rg = unit >> 1, kg = unit & 1;
-                const float x[4] = {xa[u].x, xa[u].y, xa[u].z, xa[u].w};
-                __nv_bfloat16 h[3][4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) split3(x[i], h[0][i], h[1][i], h[2][i]);
+                uint32_t h[3][4];
+                split3(xa[u].x, h[0][0], h[1][0], h[2][0]);
+                split3(xa[u].y, h[0][1], h[1][1], h[2][1]);
+                split3(xa[u].z, h[0][2], h[1][2], h[2][2]);
+                split3(xa[u].w, h[0][3], h[1][3], h[2][3]);
                 const uint32_t off = rg * 512u + (uint32_t)(2 * kg + (kq >> 1)) * 128u + r8 * 16u + (kq & 1) * 8u;
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     *reinterpret_cast<uint2 *>(st + j * kTcSplit + off) =
-                        make_uint2(pack_bf2(h[j][0], h[j][1]), pack_bf2(h[j][2], h[j][3]));
+                        make_uint2(pack_hi(h[j][0], h[j][1]), pack_hi(h[j][2], h[j][3]));
             }
             tc::fence_async_smem();
             bar_arrive(&full[s]);
@@ -427,6 +463,7 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
             for (int u = 0; u < 4; ++u) {
                 xa[u] = xb[u];
                 xb[u] = xc[u];
+                xc[u] = xd[u];
             }
         }
     }
@@ -447,14 +484,15 @@ bool gemm_tc_fits(int N, int K) {
 
 void gemm_tc(const float *A, const float *B, float *C, int M, int N, int K, float alpha, cudaStream_t st) {
     const int NT = (N + 15) & ~15, Kp = (K + 15) & ~15;
-    const size_t smem = std::max(kTcMinSmem, (size_t)kTcStages * kTcStage + (size_t)3 * NT * Kp * 2);
+    const size_t smem =
+        std::max(kTcMinSmem, (size_t)kTcStages * kTcStage + (size_t)kTcEpiBytes + (size_t)3 * NT * Kp * 2);
     if (g_sm_count == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (g_sm_count <= 0) g_sm_count = 1;
         cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kTcStages * kTcStage + kTcBMax));
+                             (int)(kTcStages * kTcStage + kTcEpiBytes + kTcBMax));
     }
     const int tiles = (M + 127) / 128;
     gemm_tc_kernel<<<std::min(tiles, g_sm_count), kTcThreads, smem, st>>>(A, B, C, M, N, K, NT, Kp, alpha,
