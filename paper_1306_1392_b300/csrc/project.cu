@@ -226,11 +226,11 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
             r32[k] = act[k] ? (int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0;
         }
         const float *S = &strip[cur][0][0];
-        for (int rr = 0; rr < nr; ++rr, S += kPW) {
+        auto row = [&](const float *Sr) {   // one staged row: three taps per ray
             float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
 #pragma unroll
             for (int k = 0; k < kPRays; ++k) {
-                const float *q = S + (x32[k] >> kFrac) - 1;
+                const float *q = Sr + (x32[k] >> kFrac) - 1;
                 const int fr = x32[k] & ((1 << kFrac) - 1);
                 v[k] = __int_as_float((kFrac == 23 ? fr : fr << 1) | 0x3F800000);   // 1 + frac in [1, 2)
                 q0[k] = q[0];
@@ -250,6 +250,12 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                 acc[p] = fma2(wc, make_float2(q1[k], q1[k + 1]), acc[p]);
                 acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
             }
+        };
+        if (nr == kPR) {                    // full chunk: rows at constant offsets
+#pragma unroll
+            for (int rr = 0; rr < kPR; ++rr) row(S + rr * kPW);
+        } else {
+            for (int rr = 0; rr < nr; ++rr) row(S + rr * kPW);
         }
         // end of a row segment: its scaled sum joins the total (in segment order)
         if (--seg_left == 0 || !more) {
