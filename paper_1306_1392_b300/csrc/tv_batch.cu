@@ -168,17 +168,26 @@ __global__ void b_image_update(const TvSlice *__restrict__ d, const int4 *__rest
     const TvSlice s = d[it.x];
     const float *xn = it_parity ? s.xa : s.xb, *xo = it_parity ? s.xb : s.xa;
     int i, j;
-    double acc = 0.0;
+    float tvp = 0.0f;
     if (px_of(it, s, i, j)) {
         const size_t k = (size_t)i * s.nx + j;
         const float v = xn[k];
         const float d1 = (i + 1 < s.ny) ? xn[k + s.nx] - v : 0.0f;
         const float d2 = (j + 1 < s.nx) ? xn[k + 1] - v : 0.0f;
-        acc = (double)sqrtf(d1 * d1 + d2 * d2);
+        tvp = sqrtf(d1 * d1 + d2 * d2);
         s.y[k] = fmaf(w, v - xo[k], v);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[px_slot(it, s)] = acc;
+    // TV partial: each warp's 32 terms in float32 (a fixed shuffle tree, relative
+    // error ~1e-7), the 8 warp sums in float64 in order (FP64 is scarce here)
+    for (int o = 16; o > 0; o >>= 1) tvp += __shfl_down_sync(0xffffffffu, tvp, o);
+    __shared__ float wsum[kBT / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = tvp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int q = 0; q < kBT / 32; ++q) acc += (double)wsum[q];
+        part[px_slot(it, s)] = acc;
+    }
 }
 
 // energy[k] of slice blockIdx.x from its partials, in a fixed order

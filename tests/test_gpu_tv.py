@@ -24,6 +24,14 @@ def P():
     return P
 
 
+# Batched and single-slice energies: the same float64 partials except that
+# the batched TV term adds each warp's 32 terms in float32 first (a fixed
+# tree, at most ~5 roundings of 2^-24 relative to that term, which is part
+# of E), so they agree to ~1e-7; the iterates themselves are compared bit
+# for bit.
+ENERGY_BATCH_RTOL = 1e-6
+
+
 def rel(a, b):
     a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
     return np.linalg.norm(a - b) / np.linalg.norm(b)
@@ -174,7 +182,8 @@ def _mixed(P, orc, dev):
 def test_batch_matches_single_slice_solves(P, orc, cuda_device):
     """With the same step size, every slice of a mixed batch equals its
     single-slice solve bit for bit (same kernels), its energies agree to
-    1e-9, and it matches the FP64 oracle like the single-slice solver."""
+    ENERGY_BATCH_RTOL, and it matches the FP64 oracle like the single-slice
+    solver."""
     items = _mixed(P, orc, cuda_device)
     L = 1.01 * max(orc.power_iteration(orc.Geometry(a.double().numpy(), ax.double().numpy(), nb, g.nx, g.ny,
                                                     g.pixel_size), np.ones((g.ny, g.nx)), 40)[0]
@@ -185,7 +194,7 @@ def test_batch_matches_single_slice_solves(P, orc, cuda_device):
     for k, (g, s, a, ax, nb) in enumerate(items):
         x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), opts)
         assert torch.equal(xs[k], x1[0]), k
-        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
+        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=ENERGY_BATCH_RTOL)
         og = orc.Geometry(a.double().numpy(), ax.double().numpy(), nb, g.nx, g.ny, g.pixel_size)
         xr, er = orc.fista(og, s.double().cpu().numpy(), 3e-3, L, 12, n_inner=8)
         assert rel(xs[k].cpu().numpy(), xr) <= 1e-4
@@ -243,7 +252,7 @@ def test_batch_variants(P, orc, cuda_device, fista, beta, warm):
     for k, (g, s, *_r) in enumerate(items):
         x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), opts, x=x0s[k][None].clone())
         assert torch.equal(xs[k], x1[0]), k
-        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
+        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=ENERGY_BATCH_RTOL)
 
 
 def test_batch_per_item_beta(P, orc, cuda_device):
@@ -257,7 +266,7 @@ def test_batch_per_item_beta(P, orc, cuda_device):
         o1 = P.TvOptions(beta=3e-3 if b is None else b, n_iter=7, n_inner=6, lipschitz=6.0)
         x1, e1, _ = P.pyhst_tv_solve(g, s[None].contiguous(), o1)
         assert torch.equal(xs[k], x1[0]), k
-        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=1e-9)
+        np.testing.assert_allclose(es[k].cpu().numpy(), e1[0].cpu().numpy(), rtol=ENERGY_BATCH_RTOL)
 
 
 # ------------------------------------------------------------------ beta estimators (Sec. 4)
