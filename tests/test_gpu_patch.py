@@ -64,6 +64,7 @@ def test_patch_gradient_matches_oracle(orc, shape, m, stride, nc, tomo):
     W = g.standard_normal(opp.shape_w).astype(np.float32)
     G, f = P.pyhst_patch_gradient(pp, geo, torch.from_numpy(W).cuda(), torch.from_numpy(y).cuda())
     Gr = opp.gradient(W.astype(np.float64), y.astype(np.float64))
+    assert P.pyhst_device_status() == 0             # the tensor-core product's waits all completed
     assert rel(G.cpu().numpy(), Gr) <= 1e-5
     assert f.item() == pytest.approx(opp.f(W.astype(np.float64), y.astype(np.float64)), rel=1e-5)
 
