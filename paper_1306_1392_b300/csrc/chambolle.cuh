@@ -112,11 +112,15 @@ __device__ __forceinline__ void chambolle_steps_regs(float (&zl)[kChRows][2], fl
     }
 }
 
+// xout == nullptr: write the dual field of the central tile to q1, q2.
+// Otherwise (the last launch of a prox) write the prox itself to xout,
+// x = z - lam div p: the divergence's four terms added in a fixed order,
+// those across the image border left out, then one fma.
 template <int kChK>
 __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
                                                const float *__restrict__ p2, float *__restrict__ q1,
                                                float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
-                                               int j0, int steps, bool first) {
+                                               int j0, int steps, bool first, float *__restrict__ xout = nullptr) {
     extern __shared__ __align__(16) float ch_smem[];
     float(*xp)[kChR] = reinterpret_cast<float(*)[kChR]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
     float(*xg)[kChR] = xp + (kChR / kChRows + 1);                       // xg[w]: first G row of strip w
@@ -160,6 +164,30 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
     else
         chambolle_steps_regs<true>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
     // write the central tile: region rows and columns kChK + 1 .. kChR - kChK
+    if (xout) {
+        const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
+#pragma unroll
+        for (int i = 0; i < kChRows; ++i) {
+            float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
+            if (tx == 0) left = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int r = r0 + i, c = c0 + j, gi = ri0 + r, gj = rj0 + c;
+                if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && gi < ny && gj < nx) {
+                    const size_t k = (size_t)gi * nx + gj;
+                    const float pu = i > 0 ? a1[i - 1][j] : (j == 0 ? up.x : up.y);
+                    const float pl = j > 0 ? a2[i][0] : left;
+                    float dv = 0.0f;
+                    if (gi + 1 < ny) dv += a1[i][j];
+                    if (gi > 0) dv -= pu;
+                    if (gj + 1 < nx) dv += a2[i][j];
+                    if (gj > 0) dv -= pl;
+                    xout[k] = fmaf(-lam, dv, z[k]);
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < kChRows; ++i)
 #pragma unroll

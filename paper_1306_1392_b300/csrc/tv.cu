@@ -155,55 +155,53 @@ __global__ void grad_step_kernel(const float *__restrict__ y, const float *__res
 template <int K>
 __global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, float *pb1, float *pb2,
-                       const float *__restrict__ lam, float tau, int nx, int ny, int m, int steps, int tiles_x) {
+                       const float *__restrict__ lam, float tau, int nx, int ny, int m, int steps, int tiles_x,
+                       float *__restrict__ x) {
     const size_t off = (size_t)blockIdx.y * nx * ny;
     const bool odd = m & 1;
     const float *s1 = (odd ? pa1 : pb1) + off, *s2 = (odd ? pa2 : pb2) + off;
     float *d1 = (m == 0 || !odd ? pa1 : pb1) + off, *d2 = (m == 0 || !odd ? pa2 : pb2) + off;
     constexpr int T = chambolle_tile_size(K);
     chambolle_tile<K>(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * T,
-                      (blockIdx.x % tiles_x) * T, steps, m == 0);
+                      (blockIdx.x % tiles_x) * T, steps, m == 0, x ? x + off : nullptr);
 }
 
 template <int K>
 int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
-                       int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st) {
+                       int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, float *x) {
     constexpr int T = chambolle_tile_size(K);
     const int tx = (nx + T - 1) / T, ty = (ny + T - 1) / T;
     const int L = chambolle_launches(n_inner, K);
-    cudaFuncSetAttribute(chambolle_fused_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem);
-    for (int m = 0; m < L; ++m)
-        chambolle_fused_kernel<K><<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
-            z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, chambolle_steps(n_inner, m, K), tx);
+    for (int m = 0; m < L; ++m) {
+        const int steps = chambolle_steps(n_inner, m, K);
+        if (m + 1 == L && x) {
+            // The prox x = z - lam div p of a tile reads p one row above and one
+            // column left of it, so the last launch takes the halo of K + 1 steps
+            // (tiles of 64 - 2 (K + 1)); its <= K steps give the same bits.
+            constexpr int T1 = chambolle_tile_size(K + 1);
+            const int tx1 = (nx + T1 - 1) / T1, ty1 = (ny + T1 - 1) / T1;
+            chambolle_fused_kernel<K + 1><<<dim3(tx1 * ty1, n_slices), kChThreads, kChSmem, st>>>(
+                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx1, x);
+        } else {
+            chambolle_fused_kernel<K><<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
+                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx, nullptr);
+        }
+    }
     *final_a = (L & 1) == 1;
     return cuda_status("Chambolle kernels");
 }
 
 // Enqueue n_inner steps with K fused steps per launch (K <= 0: the tuned or
-// default choice for the size); returns through *final_a whether the result
-// is in the a buffers.
+// default choice for the size); returns through *final_a whether the dual
+// field ends in the a buffers.  With x given, the last launch writes the prox
+// x = z - lam div p there instead of the dual field (the divergence with
+// the Neumann boundary of Eq. 2, then one fma).
 int launch_chambolle(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
-                     int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, int K = 0) {
+                     int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, int K = 0,
+                     float *x = nullptr) {
     if (K <= 0) K = chambolle_k_for(nx, ny);
     PYHST_CHAMBOLLE_DISPATCH(K, launch_chambolle_k, z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, n_slices, n_inner,
-                             final_a, st)
-}
-
-// x = z - lam div p
-__global__ void prox_final_kernel(const float *__restrict__ z, const float *__restrict__ p1,
-                                  const float *__restrict__ p2, const float *__restrict__ lam,
-                                  float *__restrict__ x, int nx, int ny) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= ny || j >= nx) return;
-    const size_t off = (size_t)blockIdx.z * nx * ny, k = (size_t)i * nx + j;
-    const float *P1 = p1 + off, *P2 = p2 + off;
-    float d = 0.0f;
-    if (i + 1 < ny) d += P1[k];
-    if (i > 0) d -= P1[k - nx];
-    if (j + 1 < nx) d += P2[k];
-    if (j > 0) d -= P2[k - 1];
-    x[off + k] = fmaf(-lam[blockIdx.z], d, z[off + k]);
+                             final_a, st, x)
 }
 
 // data partial of ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
@@ -312,7 +310,6 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
     float *Axa = B.sino[0], *Axb = B.sino[1], *Ay = B.sino[2];
     // reduction kernels always run kRedBlocks blocks per slice (every partial is written)
     const dim3 eg(kRedBlocks, S), sg(kRedBlocks, S);
-    const dim3 tb(32, 8), tgr((g->nx + 31) / 32, (g->ny + 7) / 8, S);
 
     if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, B.tab, st))) return rc;
 
@@ -365,9 +362,9 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
             if ((rc = cnn_forward(hk.cnn_params, z, xn, S, g->ny, g->nx, hk.cnn_ws, st))) return rc;
         } else if (o->beta > 0.0f) {
             bool fa;
-            if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, B.sc.lam, o->tau, g->nx, g->ny, S, o->n_inner, &fa, st)))
+            if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, B.sc.lam, o->tau, g->nx, g->ny, S, o->n_inner, &fa, st,
+                                       0, xn)))
                 return rc;
-            prox_final_kernel<<<tgr, tb, 0, st>>>(z, fa ? p1a : p1b, fa ? p2a : p2b, B.sc.lam, xn, g->nx, g->ny);
         } else {
             cudaMemcpyAsync(xn, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
         }
@@ -406,16 +403,14 @@ int tv_prox_enqueue(const float *z, int nx, int ny, int S, float lam, int n_inne
     const size_t n = (size_t)nx * ny * S;
     float *p1a = cv.take<float>(n), *p2a = cv.take<float>(n), *p1b = cv.take<float>(n), *p2b = cv.take<float>(n);
     float *lamd = cv.take<float>(S);
-    const dim3 tb(32, 8), tgr((nx + 31) / 32, (ny + 7) / 8, S);
     if (lam == 0.0f) {
         cudaMemcpyAsync(x, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
         return cuda_status("prox copy");
     }
     fill_lam<<<(S + 127) / 128, 128, 0, st>>>(lamd, lam, S);
     bool fa;
-    int rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, S, n_inner, &fa, st);
+    int rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, S, n_inner, &fa, st, 0, x);
     if (rc) return rc;
-    prox_final_kernel<<<tgr, tb, 0, st>>>(z, fa ? p1a : p1b, fa ? p2a : p2b, lamd, x, nx, ny);
     return cuda_status("prox kernels");
 }
 

@@ -88,15 +88,25 @@ __global__ void b_grad_step(const TvSlice *__restrict__ d, const int4 *__restric
 // (items[k].y, items[k].z) of slice items[k].x; slices with beta = 0 skip.
 template <int K>
 __global__ void __launch_bounds__(kChThreads, kChMinBlocks)
-b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps) {
+b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps,
+            int final_par) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    if (s.beta == 0.0f) return;
+    constexpr int T = chambolle_tile_size(K);
+    // final_par >= 0: the last launch, which writes x_new (parity as in b_prox_final)
+    float *xn = final_par < 0 ? nullptr : (final_par ? s.xa : s.xb);
+    if (s.beta == 0.0f) {                       // no TV term: x_new = z on this tile
+        if (xn)
+            for (int e = threadIdx.x; e < T * T; e += kChThreads) {
+                const int i = it.z * T + e / T, j = it.y * T + e % T;
+                if (i < s.ny && j < s.nx) xn[(size_t)i * s.nx + j] = s.z[(size_t)i * s.nx + j];
+            }
+        return;
+    }
     const bool odd = m & 1;
     const float *s1 = odd ? s.p1a : s.p1b, *s2 = odd ? s.p2a : s.p2b;
     float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
-    constexpr int T = chambolle_tile_size(K);
-    chambolle_tile<K>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0);
+    chambolle_tile<K>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0, xn);
 }
 
 template <int K>
@@ -109,16 +119,22 @@ int b_chambolle_attr_k() {
 int b_chambolle_attr(int K) { PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_attr_k) }
 
 template <int K>
-int b_chambolle_launches_k(int nch, const TvSlice *T, const int4 *items, Scal sc, float tau, int n_inner,
-                           cudaStream_t st) {
+int b_chambolle_launches_k(int nch, const TvSlice *T, const int4 *items, int nchf, const int4 *items_f, Scal sc,
+                           float tau, int n_inner, int par, cudaStream_t st) {
     const int Lc = chambolle_launches(n_inner, K);
-    for (int m = 0; m < Lc; ++m)
-        b_chambolle<K><<<nch, kChThreads, kChSmem, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K));
+    for (int m = 0; m + 1 < Lc; ++m)
+        b_chambolle<K><<<nch, kChThreads, kChSmem, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K), -1);
+    // the last launch writes x_new; it reads p one row above and one column left
+    // of its tiles, so it takes the halo of K + 1 steps (same bits)
+    b_chambolle<K + 1><<<nchf, kChThreads, kChSmem, st>>>(T, items_f, sc, tau, Lc - 1,
+                                                          chambolle_steps(n_inner, Lc - 1, K), par);
     return cuda_status("batched Chambolle kernels");
 }
-int b_chambolle_launches(int K, int nch, const TvSlice *T, const int4 *items, Scal sc, float tau, int n_inner,
-                         cudaStream_t st) {
-    PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_launches_k, nch, T, items, sc, tau, n_inner, st)
+// All launches of the Chambolle steps of one iteration; the last one writes
+// x_new (xa for par = 1, xb for par = 0) instead of the dual field.
+int b_chambolle_launches(int K, int nch, const TvSlice *T, const int4 *items, int nchf, const int4 *items_f, Scal sc,
+                         float tau, int n_inner, int par, cudaStream_t st) {
+    PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_launches_k, nch, T, items, nchf, items_f, sc, tau, n_inner, par, st)
 }
 
 // x_new = z - lam div p (p in the buffers of `parity`); with lam = 0, x_new = z
@@ -314,7 +330,8 @@ struct Plan {
     int n = 0;
     std::vector<int> rep;                       // representative of each slice
     std::vector<int> reps;                      // distinct representatives
-    std::vector<int4> bp, proj, tr, px, sn, ch; // all slices (ch: 32 x 32 Chambolle tiles)
+    std::vector<int4> bp, proj, tr, px, sn, ch; // all slices (ch: Chambolle tiles of 64 - 2 chK)
+    std::vector<int4> chf;                      // tiles of the last Chambolle launch (64 - 2 (chK + 1))
     std::vector<int4> bp_r, proj_r, tr_r, px_r, sn_r;   // representatives only
     std::vector<size_t> img_off, sino_off;      // per slice, in floats
     size_t img_total = 0, sino_total = 0;
@@ -347,10 +364,13 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     auto &sn = rep_only ? P.sn_r : P.sn;
     const int M = g.n_angles * g.n_bins;
     for (int e = 0; e < (M + kSinoBlock - 1) / kSinoBlock; ++e) sn.push_back(make_int4(s, e, 0, 0));
-    if (!rep_only)
-        for (int y = 0; y < (g.ny + chambolle_tile_size(P.chK) - 1) / chambolle_tile_size(P.chK); ++y)
-            for (int x = 0; x < (g.nx + chambolle_tile_size(P.chK) - 1) / chambolle_tile_size(P.chK); ++x)
-                P.ch.push_back(make_int4(s, x, y, 0));
+    if (!rep_only) {
+        const int t0 = chambolle_tile_size(P.chK), t1 = chambolle_tile_size(P.chK + 1);
+        for (int y = 0; y < (g.ny + t0 - 1) / t0; ++y)
+            for (int x = 0; x < (g.nx + t0 - 1) / t0; ++x) P.ch.push_back(make_int4(s, x, y, 0));
+        for (int y = 0; y < (g.ny + t1 - 1) / t1; ++y)
+            for (int x = 0; x < (g.nx + t1 - 1) / t1; ++x) P.chf.push_back(make_int4(s, x, y, 0));
+    }
 }
 
 Plan make_plan(const pyhst_tv_item *items, int n) {
@@ -409,6 +429,7 @@ Layout make_layout(const Plan &P, const pyhst_tv_item *items) {
     l.tvs = take(sizeof(TvSlice) * P.n);
     l.reps = take(sizeof(int) * P.reps.size());
     l.n_items_total = P.bp.size() + P.proj.size() + P.tr.size() + P.px.size() + P.sn.size() + P.ch.size() +
+                      P.chf.size() +
                       P.bp_r.size() +
                       P.proj_r.size() + P.tr_r.size() + P.px_r.size() + P.sn_r.size();
     l.items = take(sizeof(int4) * l.n_items_total);
@@ -519,7 +540,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     std::vector<int4> all;
     auto append = [&](const std::vector<int4> &v) { size_t o = all.size(); all.insert(all.end(), v.begin(), v.end()); return o; };
     const size_t o_bp = append(P.bp), o_proj = append(P.proj), o_tr = append(P.tr), o_px = append(P.px),
-                 o_sn = append(P.sn), o_ch = append(P.ch), o_bpr = append(P.bp_r), o_projr = append(P.proj_r), o_trr = append(P.tr_r),
+                 o_sn = append(P.sn), o_ch = append(P.ch), o_chf = append(P.chf), o_bpr = append(P.bp_r), o_projr = append(P.proj_r), o_trr = append(P.tr_r),
                  o_pxr = append(P.px_r), o_snr = append(P.sn_r);
     // pageable host memory: each copy returns once its data are staged
     cudaMemcpyAsync(ws + L.desc_even, ev.data(), sizeof(BatchSlice) * n, cudaMemcpyHostToDevice, st);
@@ -552,7 +573,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     double *part_px = reinterpret_cast<double *>(ws + L.part_px);
     double *part_sn = reinterpret_cast<double *>(ws + L.part_sn);
     const int npx = (int)P.px.size(), nsn = (int)P.sn.size(), nbp = (int)P.bp.size(), npr = (int)P.proj.size(),
-              ntr = (int)P.tr.size(), nch = (int)P.ch.size();
+              ntr = (int)P.tr.size(), nch = (int)P.ch.size(), nchf = (int)P.chf.size();
     const dim3 tb(kBT);
 
     // ---- step size: power iteration on the representatives, or the caller's L
@@ -606,14 +627,13 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st);
         if (rc) break;
         b_grad_step<<<npx, tb, 0, st>>>(T, I + o_px, sc);
-        int pp = 0;   // 0: the dual field ends in the "a" buffers
-        if (!identity) {
-            const int Lc = chambolle_launches(opts->n_inner, P.chK);
-            rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, sc, opts->tau, opts->n_inner, st);
+        if (!identity) {                        // the last Chambolle launch writes x_new
+            rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, nchf, I + o_chf, sc, opts->tau, opts->n_inner, par,
+                                      st);
             if (rc) break;
-            pp = (Lc & 1) ? 0 : 1;
+        } else {
+            b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, 0, par, 1);
         }
-        b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, pp, par, identity);
         rc = project(par ? D_odd : D_even, o_proj, npr, P.proj_narrow, o_tr, ntr);
         if (rc) break;
         double w = 0.0;
