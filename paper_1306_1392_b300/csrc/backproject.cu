@@ -70,11 +70,14 @@ __device__ __forceinline__ StageInfo stage_info(const AngleInfo *tab, int a, int
 
 // One CTA: the 64 x 64 tile at (X0, Y0) of one slice.  A (and B in residual
 // mode) are that slice's rows, out its image.
+// With ystep given, out receives the gradient step z = ystep - invL * g of
+// g = weight * back-projection, rounded as a separate pass would round it.
 template <bool kResidual>
 __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const float *__restrict__ A,
                                         const float *__restrict__ B, float *__restrict__ out, int n_angles,
                                         int n_bins, int nx, int ny, double cx, double cy, float weight,
-                                        int X0, int Y0) {
+                                        int X0, int Y0, const float *__restrict__ ystep = nullptr,
+                                        float invL = 0.0f) {
     __shared__ __align__(16) float2 win[2][kNA * kW];
     __shared__ StageInfo info[3][kNA];
 
@@ -169,8 +172,14 @@ __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const
             const int y = Y0 + py + 4 * ry;
             const int x0 = X0 + px + 16 * rp;
             if (y < ny) {
-                if (x0 < nx) out[(size_t)y * nx + x0] = weight * acc[ry][rp].x;
-                if (x0 + 8 < nx) out[(size_t)y * nx + x0 + 8] = weight * acc[ry][rp].y;
+                const size_t k = (size_t)y * nx + x0;
+                if (ystep) {
+                    if (x0 < nx) out[k] = fmaf(-(weight * acc[ry][rp].x), invL, ystep[k]);
+                    if (x0 + 8 < nx) out[k + 8] = fmaf(-(weight * acc[ry][rp].y), invL, ystep[k + 8]);
+                } else {
+                    if (x0 < nx) out[k] = weight * acc[ry][rp].x;
+                    if (x0 + 8 < nx) out[k + 8] = weight * acc[ry][rp].y;
+                }
             }
         }
 }
@@ -179,12 +188,13 @@ template <bool kResidual>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
           const float *__restrict__ srcB, float *__restrict__ img, int n_angles, int n_bins,
-          int nx, int ny, double cx, double cy, float weight, int tiles_x) {
+          int nx, int ny, double cx, double cy, float weight, int tiles_x, const float *__restrict__ ystep,
+          const float *__restrict__ invL) {
     const int slice = blockIdx.y;
-    const size_t sino_off = (size_t)slice * n_angles * n_bins;
-    bp_tile<kResidual>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + (size_t)slice * nx * ny,
+    const size_t sino_off = (size_t)slice * n_angles * n_bins, img_off = (size_t)slice * nx * ny;
+    bp_tile<kResidual>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + img_off,
                        n_angles, n_bins, nx, ny, cx, cy, weight, (blockIdx.x % tiles_x) * kTX,
-                       (blockIdx.x / tiles_x) * kTY);
+                       (blockIdx.x / tiles_x) * kTY, ystep ? ystep + img_off : nullptr, ystep ? invL[slice] : 0.0f);
 }
 
 // Mixed batch: CTA k reconstructs tile (items[k].y, items[k].z) of slice items[k].x.
@@ -194,7 +204,7 @@ bp_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ 
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
     bp_tile<kResidual>(s.tab, s.bp_a, s.bp_b, s.bp_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
-                       weight_scale * s.pixel_size, it.y * kTX, it.z * kTY);
+                       weight_scale * s.pixel_size, it.y * kTX, it.z * kTY, s.bp_y, s.bp_y ? *s.bp_invL : 0.0f);
 }
 
 }  // namespace
@@ -225,10 +235,10 @@ int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource s
     ProfScope prof(kProfBackproject, st);
     if (src.b)
         bp_kernel<true><<<grid, kThreads, 0, st>>>(tab, src.a, src.b, img, g->n_angles, g->n_bins, g->nx,
-                                                   g->ny, g->cx, g->cy, weight, tiles_x);
+                                                   g->ny, g->cx, g->cy, weight, tiles_x, src.y, src.invL);
     else
         bp_kernel<false><<<grid, kThreads, 0, st>>>(tab, src.a, nullptr, img, g->n_angles, g->n_bins,
-                                                    g->nx, g->ny, g->cx, g->cy, weight, tiles_x);
+                                                    g->nx, g->ny, g->cx, g->cy, weight, tiles_x, src.y, src.invL);
     return cuda_status("back-projection kernel");
 }
 

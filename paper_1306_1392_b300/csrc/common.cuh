@@ -60,6 +60,10 @@ int launch_angle_table(const float *angles, const float *axis, int n_angles, Ang
 struct BpSource {
     const float *a;          // [n_slices][n_angles][n_bins]
     const float *b;          // NULL, or subtracted from a
+    // gradient step in the epilogue: with y given, img receives
+    // z = y - invL[slice] * (weight * back-projection) instead
+    const float *y = nullptr;
+    const float *invL = nullptr;
 };
 int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img,
                        float weight, cudaStream_t st);
@@ -86,6 +90,8 @@ struct BatchSlice {
     const float *proj_in;
     float *proj_inT, *proj_out;
     int proj_nseg;          // row segments of the projector (proj_segments of this geometry)
+    const float *bp_y;      // NULL, or the gradient step: bp_out = bp_y - *bp_invL * back-projection
+    const float *bp_invL;
 };
 int bp_tiles(int nx, int ny, int *tx, int *ty);
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,

@@ -10,7 +10,8 @@
 // projects x_k (which the energy needs anyway) and carries P y_{k+1} =
 // P x_k + w_k (P x_k - P x_{k-1}) by linearity in sinogram space, so the
 // gradient step back-projects the residual P y_k - sino directly (the
-// back-projector subtracts while staging its rows).  Reductions (energy,
+// back-projector subtracts while staging its rows and writes z = y_k - g/L
+// itself), and the last Chambolle launch writes x_k.  Reductions (energy,
 // norms) are float64, per block then in fixed order: bitwise reproducible.
 // L comes from the caller or from power iteration on P^T P started from the
 // all-ones image (float64 norms), L = 1.01 * ||P v||^2 for the final unit v.
@@ -138,15 +139,6 @@ __global__ void scale_kernel(const float *__restrict__ w, const float *__restric
 __global__ void fill_kernel(float *__restrict__ v, float val, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         v[i] = val;
-}
-
-// z = y - g / L
-__global__ void grad_step_kernel(const float *__restrict__ y, const float *__restrict__ g,
-                                 const float *__restrict__ invL, float *__restrict__ z, size_t n) {
-    const size_t off = (size_t)blockIdx.y * n;
-    const float il = invL[blockIdx.y];
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        z[off + i] = fmaf(-g[off + i], il, y[off + i]);
 }
 
 // n_inner Chambolle steps in launches of up to K fused steps (see
@@ -352,8 +344,7 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
     double t = 1.0;
     for (int k = 0; k < o->n_iter; ++k) {
         // gradient step: z = y - (1/L) P^T (P y - sino)
-        if ((rc = launch_backproject(g, B.tab, BpSource{Ay, sino}, gr, s, st))) return rc;
-        grad_step_kernel<<<eg, kRedThreads, 0, st>>>(y, gr, B.sc.invL, z, N);
+        if ((rc = launch_backproject(g, B.tab, BpSource{Ay, sino, y, B.sc.invL}, z, s, st))) return rc;
         for (int c = 0; c < hk.n_capture; ++c)
             if (hk.capture_iters[c] == k + 1)
                 cudaMemcpyAsync(hk.capture + (size_t)c * N * S, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);

@@ -1,8 +1,9 @@
 // Mixed-size batch of TV-penalised solves (Eq. 3 by ISTA/FISTA, Sec. 3.1).
 //
 // Slices of different sizes and angle sets run together: every stage of an
-// outer iteration (gradient back-projection, gradient step, each Chambolle
-// step, prox end, projection, momentum and energy) is ONE launch over the
+// outer iteration (gradient back-projection with the gradient step in its
+// epilogue, each Chambolle launch, the last of which writes the prox,
+// projection, momentum and energy) is ONE launch over the
 // whole batch, each CTA taking a (slice, tile) work item from a list built on
 // the host, with per-slice descriptors in device memory.  The n_iter
 // iterations are captured in one CUDA graph and launched once (unless the
@@ -73,15 +74,6 @@ __device__ __forceinline__ bool px_of(const int4 it, const TvSlice &s, int &i, i
     j = it.y * 32 + (threadIdx.x & 31);
     i = it.z * 8 + (threadIdx.x >> 5);
     return i < s.ny && j < s.nx;
-}
-
-__global__ void b_grad_step(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc) {
-    const int4 it = items[blockIdx.x];
-    const TvSlice s = d[it.x];
-    int i, j;
-    if (!px_of(it, s, i, j)) return;
-    const size_t k = (size_t)i * s.nx + j;
-    s.z[k] = fmaf(-s.g[k], sc.invL[it.x], s.y[k]);
 }
 
 // Launch m of the fused Chambolle steps (see chambolle.cuh) on tile
@@ -533,6 +525,13 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         b.bp_a = t.Ay; b.bp_b = items[s].sino; b.bp_out = t.g;
         ev[s] = b; ev[s].proj_in = t.xb; ev[s].proj_out = t.Axb;   // even iterations write xb, Axb
         od[s] = b; od[s].proj_in = t.xa; od[s].proj_out = t.Axa;   // odd iterations write xa, Axa
+        // the iterations' back-projection ends in the gradient step z = y - invL g
+        const float *invL_s = reinterpret_cast<const float *>(reinterpret_cast<double *>(ws + L.scal) + 2 * n) + s;
+        for (BatchSlice *e : {&ev[s], &od[s]}) {
+            e->bp_out = t.z;
+            e->bp_y = t.y;
+            e->bp_invL = invL_s;
+        }
         in[s] = b; in[s].proj_in = t.xa; in[s].proj_out = t.Axa;   // warm start
         pw[s] = b; pw[s].proj_in = t.z; pw[s].proj_out = t.Axa;    // power iteration
         pw[s].bp_a = t.Axa; pw[s].bp_b = nullptr;
@@ -626,7 +625,6 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         const int par = k & 1;   // 0: x_new -> xb, 1: x_new -> xa
         rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st);
         if (rc) break;
-        b_grad_step<<<npx, tb, 0, st>>>(T, I + o_px, sc);
         if (!identity) {                        // the last Chambolle launch writes x_new
             rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, nchf, I + o_chf, sc, opts->tau, opts->n_inner, par,
                                       st);
