@@ -114,6 +114,36 @@ def test_dense_network_within_bf16_rounding(n, h, w):
         assert np.linalg.norm(out[i] - ref) <= 2e-3 * np.linalg.norm(ref)
 
 
+def test_trained_network_full_size_sampled():
+    """The configuration the learned solve runs: the trained weights on a
+    64 x 512^2 stack.  Each output pixel depends on z within 8 pixels (eight
+    3 x 3 layers; the oracle pin test_receptive_field_is_eight_pixels), so
+    the oracle runs the network on the 17 x 17 crop around each sampled pixel
+    (or the part of it inside the image) and gives the full image's value.
+    Same bounds as the dense test, over the samples."""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    params = np.load(os.path.join(root, "paper_1306_1392_b300", "weights", "prox_cnn_foam512.npy")).astype(np.float32)
+    n, h, w = 64, 512, 512
+    g = np.random.default_rng(12)
+    yy, xx = np.mgrid[0:h, 0:w]
+    base = 0.5 + 0.3 * np.sin(xx / 23.0) * np.cos(yy / 17.0)
+    z = (base[None] + 0.05 * g.standard_normal((n, h, w))).astype(np.float32)
+    out = _run(params, z)
+    pts = list(zip(g.integers(0, n, 120), g.integers(0, h, 120), g.integers(0, w, 120)))
+    pts += [(0, 0, 0), (1, h - 1, w - 1), (2, 0, w - 1), (63, h - 1, 0), (5, 127, 128), (6, 255, 256)]
+    rg, rr, og, orf = [], [], [], []
+    for s_, i, j in pts:
+        i0, i1, j0, j1 = max(0, i - 8), min(h, i + 9), max(0, j - 8), min(w, j + 9)
+        ref, _, _ = cnn.forward(params, z[s_, i0:i1, j0:j1], rounding=True)
+        v = ref[i - i0, j - j0]
+        og.append(out[s_, i, j]); orf.append(v)
+        rg.append(out[s_, i, j] - z[s_, i, j]); rr.append(v - z[s_, i, j])
+    rg, rr, og, orf = (np.asarray(a, np.float64) for a in (rg, rr, og, orf))
+    assert np.linalg.norm(rg - rr) <= 1e-2 * np.linalg.norm(rr)
+    assert np.linalg.norm(og - orf) <= 2e-3 * np.linalg.norm(orf)
+
+
 def test_forward_rejects_bad_arguments():
     import paper_1306_1392_b300 as P
     from paper_1306_1392_b300 import _lib as L
