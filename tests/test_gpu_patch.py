@@ -88,6 +88,34 @@ def test_patch_solve_matches_oracle(orc, fista, tomo):
     np.testing.assert_allclose(e.cpu().numpy(), er, rtol=1e-5)
 
 
+def test_patch_gradient_full_size(orc):
+    """The patch study's configuration: a 2048^2 image, 150 angles over
+    180 degrees, 8 x 8 patches at stride 4 (261,121 patches), the 144-atom
+    over-complete DCT: Algorithm 1's gradient and f (Eq. 8) for seeded
+    coefficients against the oracle's, same bounds as the small cases (the
+    oracle's gradient takes ~20-30 s here)."""
+    import paper_1306_1392_b300 as P
+    from synth.patches import overcomplete_dct
+    n, na, m, stride = 2048, 150, 8, 4
+    dev = torch.device("cuda:0")
+    ang = (np.arange(na) * math.pi / na).astype(np.float32)
+    ax = np.full(na, (n - 1) / 2.0, np.float32)
+    geo = P.Geometry(torch.from_numpy(ang).to(dev), torch.from_numpy(ax).to(dev), n, n, n, 2.0 / n)
+    ogeo = orc.Geometry(ang.astype(np.float64), ax.astype(np.float64), n, n, n, 2.0 / n)
+    Dm = overcomplete_dct(m, 12).astype(np.float32)
+    pp = P.PatchProblem(n, n, m, stride, torch.from_numpy(Dm).to(dev), 1.0)
+    opp = orc.PatchProblem(n, n, m, stride, Dm.astype(np.float64), 1.0, g=ogeo)
+    g = np.random.default_rng(31)
+    W = g.standard_normal(opp.shape_w).astype(np.float32)
+    y = g.standard_normal((na, n)).astype(np.float32)
+    G, f = P.pyhst_patch_gradient(pp, geo, torch.from_numpy(W).to(dev), torch.from_numpy(y).to(dev))
+    torch.cuda.synchronize()
+    assert P.pyhst_device_status() == 0
+    Wd, yd = W.astype(np.float64), y.astype(np.float64)
+    assert rel(G.cpu().numpy(), opp.gradient(Wd, yd)) <= 1e-5
+    assert f.item() == pytest.approx(opp.f(Wd, yd), rel=1e-5)
+
+
 def _power(opp, y, iters=300):
     """Largest eigenvalue of f's constant Hessian (H v = grad f(v) - grad f(0))."""
     g0 = opp.gradient(np.zeros(opp.shape_w), y)
