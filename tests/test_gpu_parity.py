@@ -381,6 +381,44 @@ def test_fbp_pre_flats_hotspots_rings_parity(P, orc, cuda_device):
         close(f64(got[z]), ref)
 
 
+def test_fbp_pre_full_size_sampled(P, orc, cuda_device):
+    """The preprocessing study's configuration (Sec. 2.3: three flats
+    interpolated by projection position, hot-spot median with threshold 0.2,
+    ring filter of window 9) on the batched-volume geometry (2048^2, 2000
+    angles, 2048 bins, uint16, an 8-slice stack in one call): sampled pixels
+    of two slices against the oracle's preprocessing of the stack, filter and
+    back-projection at those pixels."""
+    n, na, ns = 2048, 2000, 8
+    vol = acq.ellipsoid_volume(n_slices=ns, n=n, n_angles=na, seed=1100, device=cuda_device)
+    dev = cuda_device
+    scale = torch.tensor([0.97, 1.0, 1.04], dtype=torch.float32, device=dev)
+    pos = torch.linspace(0, 2, na, dtype=torch.float32, device=dev)
+    f0 = torch.floor(pos).clamp(max=1)
+    w = pos - f0
+    s_a = (1 - w) * scale[f0.long()] + w * scale[f0.long() + 1]        # beam drift per projection
+    dark, flat = vol.dark.to(dev).float(), vol.flat.to(dev).float()
+    counts = (vol.raw.to(dev).float() - dark[None]) * s_a[:, None, None] + dark[None]
+    counts[:, :, 1001] = (counts[:, :, 1001] - dark[None, :, 1001]) * 1.05 + dark[None, :, 1001]   # a ring
+    g = np.random.default_rng(5)
+    hot = (torch.from_numpy(g.integers(0, na, 400)).to(dev), torch.from_numpy(g.integers(0, ns, 400)).to(dev),
+           torch.from_numpy(g.integers(1, n - 1, 400)).to(dev))
+    counts[hot] = counts[hot] * 2.5 + 20000
+    raw16 = counts.round().clamp(0, 65535).to(torch.int32).to(torch.uint16)
+    flats = torch.stack([dark + (flat - dark) * sc for sc in scale])
+    geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), n, n, n, vol.pixel_size, dev)
+    got = P.pyhst_fbp_pre(geo, raw16, "u16_raw", flats, dark, flat_pos=pos, hotspot_threshold=0.2, ring_window=9)
+    torch.cuda.synchronize()
+    p = orc.preprocess(raw16.cpu().double().numpy(), flats.cpu().double().numpy(), pos.cpu().double().numpy(),
+                       dark.cpu().double().numpy(), hotspot_threshold=0.2, ring_window=9)
+    rng = np.random.default_rng(1)
+    for z in (1, 6):
+        ii = np.concatenate([rng.integers(0, n, 800), [0, n - 1, n // 2]])
+        jj = np.concatenate([rng.integers(0, n, 800), [0, n - 1, 1001]])
+        ref = orc.backproject_at(orc.ramlak_filter(p[z]), vol.angles.double().numpy(), vol.axis.double().numpy(),
+                                 n, n, ii, jj, orc.fbp_weight(na, vol.pixel_size))
+        close(got[z].cpu().double().numpy()[ii, jj], ref)
+
+
 @pytest.mark.parametrize("filt", ["shepp-logan", "hann", "ramlak"])
 @pytest.mark.parametrize("pad", [0, 2048])
 def test_fbp_filters(P, orc, cuda_device, filt, pad):
