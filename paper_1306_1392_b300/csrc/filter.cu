@@ -84,22 +84,25 @@ __global__ void spectrum_kernel(int P, int logP, int filter, const double *__res
     }
 }
 
+// Raw value of sample idx as float (counts, or the pre-normalised sinogram).
 template <int kKind>
-__device__ __forceinline__ float load_p(const void *data, int64_t idx, float F, float D) {
+__device__ __forceinline__ float load_raw(const void *data, int64_t idx) {
+    if (kKind == PYHST_U16_RAW) return (float)static_cast<const uint16_t *>(data)[idx];
+    if (kKind == PYHST_F32_RAW || kKind == PYHST_F32_SINO) return static_cast<const float *>(data)[idx];
+    if (kKind == PYHST_F16_SINO) return __half2float(static_cast<const __half *>(data)[idx]);
+    return __bfloat162float(static_cast<const __nv_bfloat16 *>(data)[idx]);
+}
+// p = -ln((I - D) / (F - D)) for counts (0 where F - D <= 0, ratio clamped
+// below at 1e-6); the value itself for sinogram kinds.
+template <int kKind>
+__device__ __forceinline__ float to_p(float v, float F, float D) {
     if (kKind == PYHST_U16_RAW || kKind == PYHST_F32_RAW) {
-        const float I = (kKind == PYHST_U16_RAW) ? (float)static_cast<const uint16_t *>(data)[idx]
-                                                 : static_cast<const float *>(data)[idx];
         const float den = F - D;
         if (!(den > 0.0f)) return 0.0f;
-        const float r = fmaxf((I - D) / den, 1e-6f);
+        const float r = fmaxf((v - D) / den, 1e-6f);
         return -logf(r);
-    } else if (kKind == PYHST_F32_SINO) {
-        return static_cast<const float *>(data)[idx];
-    } else if (kKind == PYHST_F16_SINO) {
-        return __half2float(static_cast<const __half *>(data)[idx]);
-    } else {
-        return __bfloat162float(static_cast<const __nv_bfloat16 *>(data)[idx]);
     }
+    return v;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -177,23 +180,50 @@ __global__ void __launch_bounds__(1024) filter_kernel(const void *__restrict__ d
     const int zB = z0 + rB / n_angles, aB = rB % n_angles;
     const int64_t baseA = (int64_t)zA * slice_stride + (int64_t)aA * angle_stride;
     const int64_t baseB = (int64_t)zB * slice_stride + (int64_t)aB * angle_stride;
-    const bool raw = (kKind == PYHST_U16_RAW || kKind == PYHST_F32_RAW);
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    constexpr bool raw = (kKind == PYHST_U16_RAW || kKind == PYHST_F32_RAW);
+    // The thread's first four samples (and their flat / dark values) are all
+    // loaded before any is used; this covers [0, n_bins) whenever n_bins <=
+    // 4 blockDim (P = 2^k >= 2 n_bins with blockDim = P / 8 up to P = 8192);
+    // the tail loop takes any remaining samples and the zero padding.
+    constexpr int kJ = 4;
+    float IA[kJ], IB[kJ], FA[kJ], DA[kJ], FB[kJ], DB[kJ];
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
+        IA[j] = IB[j] = FA[j] = DA[j] = FB[j] = DB[j] = 0.0f;
+        if (k < n_bins) {
+            IA[j] = load_raw<kKind>(data, baseA + k);
+            if (raw) {
+                FA[j] = flat[(size_t)zA * n_bins + k];
+                DA[j] = dark[(size_t)zA * n_bins + k];
+            }
+            if (hasB) {
+                IB[j] = load_raw<kKind>(data, baseB + k);
+                if (raw) {
+                    FB[j] = flat[(size_t)zB * n_bins + k];
+                    DB[j] = dark[(size_t)zB * n_bins + k];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kJ; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
         float va = 0.0f, vb = 0.0f;
         if (k < n_bins) {
-            float FA = 0.0f, DA = 0.0f, FB = 0.0f, DB = 0.0f;
-            if (raw) {
-                FA = flat[(size_t)zA * n_bins + k];
-                DA = dark[(size_t)zA * n_bins + k];
-            }
-            va = load_p<kKind>(data, baseA + k, FA, DA);
-            if (hasB) {
-                if (raw) {
-                    FB = flat[(size_t)zB * n_bins + k];
-                    DB = dark[(size_t)zB * n_bins + k];
-                }
-                vb = load_p<kKind>(data, baseB + k, FB, DB);
-            }
+            va = to_p<kKind>(IA[j], FA[j], DA[j]);
+            if (hasB) vb = to_p<kKind>(IB[j], FB[j], DB[j]);
+        }
+        if (k < P) z[slot(k)] = make_float2(va, vb);
+    }
+    for (int k = threadIdx.x + kJ * blockDim.x; k < P; k += blockDim.x) {
+        float va = 0.0f, vb = 0.0f;
+        if (k < n_bins) {
+            va = to_p<kKind>(load_raw<kKind>(data, baseA + k), raw ? flat[(size_t)zA * n_bins + k] : 0.0f,
+                             raw ? dark[(size_t)zA * n_bins + k] : 0.0f);
+            if (hasB)
+                vb = to_p<kKind>(load_raw<kKind>(data, baseB + k), raw ? flat[(size_t)zB * n_bins + k] : 0.0f,
+                                 raw ? dark[(size_t)zB * n_bins + k] : 0.0f);
         }
         z[slot(k)] = make_float2(va, vb);
     }
