@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(kPThreads, 3)
 proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
             float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
             float scale, int nseg, int split) {
-    const int slice = split ? blockIdx.z / nseg : blockIdx.z, seg = split ? blockIdx.z % nseg : -1;
+    const int bz = (int)blockIdx.z;
+    const int slice = split ? bz / nseg : bz, seg = split ? bz % nseg : -1;
     const size_t img_off = (size_t)slice * nx * ny;
     proj_cta<PW>(tab, img + img_off, imgT + img_off, sino + (size_t)blockIdx.z * n_angles * n_bins, n_angles, n_bins,
                  nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB, seg, nseg);
