@@ -428,7 +428,11 @@ int pyhst_patch_image(const pyhst_patch_problem *pp, const float *W, float *x, v
 /* G [N][n_atoms] = gradient of f at W (Eq. 9), computed with the steps of
  * Algorithm 1 (P = W D, the image from the cores, R = Pi^T (Pi x - y), the
  * patch sum S and cover count, the auxiliary patches P', G = 2 P' D^T).
- * f_out: DEVICE float64 [1] or NULL, receives f(W) (Eq. 8). */
+ * f_out: DEVICE float64 [1] or NULL, receives f(W) (Eq. 8).  The two
+ * dictionary products run on the tensor cores with both operands split into
+ * three bf16 terms (float32 accuracy) when the padded dictionary side fits
+ * (<= 256 columns); a completion wait there that gives up sets bit 1 of
+ * pyhst_device_status. */
 int pyhst_patch_gradient(const pyhst_patch_problem *pp, const pyhst_geometry *g, const float *W, const float *y,
                          float *G, double *f_out, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
