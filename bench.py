@@ -290,15 +290,16 @@ PROX_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1
 
 
 def run_learned_prox(dev, n_eval=64):
-    """Plain TV vs the learned solve (FBP, K_T FISTA-TV iterations, two ISTA
-    steps with the trained CNN prox) at equal PSNR on 64 held-out seeded
-    512^2 foams (100 angles, Poisson 1e4); everything event-timed on the GPU."""
+    """Plain TV vs the learned solve (FBP, K_T FISTA-TV iterations, K_L ISTA
+    steps with the trained CNN prox; the fastest (K_T, K_L) of a small grid
+    that reaches plain TV's PSNR) at equal PSNR on 64 held-out seeded 512^2
+    foams (100 angles, Poisson 1e4); everything event-timed on the GPU."""
     import numpy as np
     import torch
     from paper_1306_1392_b300 import train_prox
     params = torch.from_numpy(np.load(PROX_WEIGHTS).astype(np.float32)).to(dev)
     r = train_prox.evaluate(params, dev, n_eval=n_eval, ks=(), tv_long=0, hybrid_kt=(40, 75, 100),
-                            tv_first=(20, 25, 30, 35, 40))
+                            tv_first=(25, 28, 30, 35, 40), learned_steps=(2, 3, 4, 5))
     r["weights"] = "paper_1306_1392_b300/weights/prox_cnn_foam512.npy (train_prox.py)"
     return r
 

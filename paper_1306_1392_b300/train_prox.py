@@ -171,8 +171,12 @@ def train(inputs, targets, steps: int, batch: int = 16, crop: int = 128, lr: flo
 
 def evaluate(params, dev, n_eval: int = 64, ks=(1, 2, 3, 5), n_iter_tv: int = 200,
              L: float = None, variants=(("ista", False),), tv_long: int = 1000,
-             hybrid_kl=(0,), hybrid_kt=(30, 40, 50, 75, 100), tv_first=(20, 25, 30, 35, 40)):
-    """Plain TV vs the learned prox on held-out seeded foams (even seeds)."""
+             hybrid_kl=(0,), hybrid_kt=(30, 40, 50, 75, 100), tv_first=(20, 25, 30, 35, 40),
+             learned_steps=(1, 2)):
+    """Plain TV vs the learned prox on held-out seeded foams (even seeds).
+    The learned solve is FBP, K_T FISTA-TV iterations (tv_first), then K_L
+    ISTA steps with the network as the prox (learned_steps); the fastest
+    (K_T, K_L) whose mean PSNR reaches plain TV's is reported as equal_psnr."""
     from . import TvOptions, pyhst_fbp, pyhst_pnp_solve, pyhst_tv_solve
     geo = geometry(dev)
     if L is None:
@@ -241,7 +245,7 @@ def evaluate(params, dev, n_eval: int = 64, ks=(1, 2, 3, 5), n_iter_tv: int = 20
             ps = float(np.mean([psnr(x[i].double().cpu().numpy(), truth[i]) for i in range(n_eval)]))
             res["pnp"].append({"variant": f"ista{KL}+tv" if KL else "fbp+tv", "n_iter": KT,
                                "s_per_slice": t / n_eval, "psnr_mean": ps})
-    for KL in (1, 2):
+    for KL in learned_steps:
         for KT in tv_first:
             (x, _, _), t = timed(lambda: tv_then_learned(KT, KL))
             ps = float(np.mean([psnr(x[i].double().cpu().numpy(), truth[i]) for i in range(n_eval)]))
