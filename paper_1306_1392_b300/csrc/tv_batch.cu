@@ -61,7 +61,11 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-// Partial-sum slots: a slice's pixel items (32 x 8) and sinogram items are
+// Pixel work items are 32 columns x kPxRows rows; thread t of a CTA takes
+// column t % 32 and rows t / 32 + 8 r (r < kPxRows / 8).
+constexpr int kPxRows = 32;
+
+// Partial-sum slots: a slice's pixel items (32 x kPxRows) and sinogram items are
 // numbered from its px_first / sn_first in the order the host lists them, so
 // that work lists over any subset of slices write the same slots.
 __device__ __forceinline__ int px_slot(const int4 it, const TvSlice &s) {
@@ -69,12 +73,13 @@ __device__ __forceinline__ int px_slot(const int4 it, const TvSlice &s) {
 }
 __device__ __forceinline__ int sn_slot(const int4 it, const TvSlice &s) { return s.sn_first + it.y; }
 
-// pixel (i, j) of a 32 x 8 work item; false if outside the slice
-__device__ __forceinline__ bool px_of(const int4 it, const TvSlice &s, int &i, int &j) {
+// pixel (i, j) of row group r of a pixel work item; false if outside the slice
+__device__ __forceinline__ bool px_of(const int4 it, const TvSlice &s, int r, int &i, int &j) {
     j = it.y * 32 + (threadIdx.x & 31);
-    i = it.z * 8 + (threadIdx.x >> 5);
+    i = it.z * kPxRows + (threadIdx.x >> 5) + 8 * r;
     return i < s.ny && j < s.nx;
 }
+__device__ __forceinline__ int px_items(const TvSlice &s) { return ((s.nx + 31) / 32) * ((s.ny + kPxRows - 1) / kPxRows); }
 
 // Launch m of the fused Chambolle steps (see chambolle.cuh) on tile
 // (items[k].y, items[k].z) of slice items[k].x; slices with beta = 0 skip.
@@ -134,21 +139,23 @@ __global__ void b_prox_final(const TvSlice *__restrict__ d, const int4 *__restri
                              int it_parity, int identity) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    int i, j;
-    if (!px_of(it, s, i, j)) return;
-    const size_t k = (size_t)i * s.nx + j;
     float *xn = it_parity ? s.xa : s.xb;
-    if (identity || s.beta == 0.0f) {
-        xn[k] = s.z[k];
-        return;
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (!px_of(it, s, r, i, j)) continue;
+        const size_t k = (size_t)i * s.nx + j;
+        if (identity || s.beta == 0.0f) {
+            xn[k] = s.z[k];
+            continue;
+        }
+        const float *P1 = parity ? s.p1b : s.p1a, *P2 = parity ? s.p2b : s.p2a;
+        float dv = 0.0f;
+        if (i + 1 < s.ny) dv += P1[k];
+        if (i > 0) dv -= P1[k - s.nx];
+        if (j + 1 < s.nx) dv += P2[k];
+        if (j > 0) dv -= P2[k - 1];
+        xn[k] = fmaf(-sc.lam[it.x], dv, s.z[k]);
     }
-    const float *P1 = parity ? s.p1b : s.p1a, *P2 = parity ? s.p2b : s.p2a;
-    float dv = 0.0f;
-    if (i + 1 < s.ny) dv += P1[k];
-    if (i > 0) dv -= P1[k - s.nx];
-    if (j + 1 < s.nx) dv += P2[k];
-    if (j > 0) dv -= P2[k - 1];
-    xn[k] = fmaf(-sc.lam[it.x], dv, s.z[k]);
 }
 
 // data partial ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
@@ -175,18 +182,20 @@ __global__ void b_image_update(const TvSlice *__restrict__ d, const int4 *__rest
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
     const float *xn = it_parity ? s.xa : s.xb, *xo = it_parity ? s.xb : s.xa;
-    int i, j;
     float tvp = 0.0f;
-    if (px_of(it, s, i, j)) {
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (!px_of(it, s, r, i, j)) continue;
         const size_t k = (size_t)i * s.nx + j;
         const float v = xn[k];
         const float d1 = (i + 1 < s.ny) ? xn[k + s.nx] - v : 0.0f;
         const float d2 = (j + 1 < s.nx) ? xn[k + 1] - v : 0.0f;
-        tvp = sqrtf(d1 * d1 + d2 * d2);
+        tvp += sqrtf(d1 * d1 + d2 * d2);
         s.y[k] = fmaf(w, v - xo[k], v);
     }
-    // TV partial: each warp's 32 terms in float32 (a fixed shuffle tree, relative
-    // error ~1e-7), the 8 warp sums in float64 in order (FP64 is scarce here)
+    // TV partial: each thread's terms and then each warp's in float32 (fixed
+    // order and shuffle tree, relative error ~1e-7), the 8 warp sums in
+    // float64 in order (FP64 is scarce here)
     for (int o = 16; o > 0; o >>= 1) tvp += __shfl_down_sync(0xffffffffu, tvp, o);
     __shared__ float wsum[kBT / 32];
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = tvp;
@@ -206,7 +215,7 @@ __global__ void b_finalize_energy(const TvSlice *__restrict__ d, const double *_
     double a = 0.0, t = 0.0;
     for (int e = s.sn_first + threadIdx.x; e < s.sn_first + (s.M + kSinoBlock - 1) / kSinoBlock; e += kBT)
         a += part_sn[e];
-    const int n_px = ((s.nx + 31) / 32) * ((s.ny + 7) / 8);
+    const int n_px = px_items(s);
     for (int e = s.px_first + threadIdx.x; e < s.px_first + n_px; e += kBT) t += part_px[e];
     a = block_sum(a);
     t = block_sum(t);
@@ -217,11 +226,12 @@ __global__ void b_finalize_energy(const TvSlice *__restrict__ d, const double *_
 __global__ void b_sqnorm_g(const TvSlice *__restrict__ d, const int4 *__restrict__ items, double *__restrict__ part) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    int i, j;
     double acc = 0.0;
-    if (px_of(it, s, i, j)) {
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (!px_of(it, s, r, i, j)) continue;
         const float v = s.g[(size_t)i * s.nx + j];
-        acc = (double)v * (double)v;
+        acc += (double)v * (double)v;
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) part[px_slot(it, s)] = acc;
@@ -248,7 +258,7 @@ __global__ void b_finalize_norm(const TvSlice *__restrict__ d, const int *__rest
     const TvSlice s = d[r];
     double a = 0.0;
     if (mode == 0) {
-        const int n_px = ((s.nx + 31) / 32) * ((s.ny + 7) / 8);
+        const int n_px = px_items(s);
         for (int e = s.px_first + threadIdx.x; e < s.px_first + n_px; e += kBT) a += part[e];
     } else {
         for (int e = s.sn_first + threadIdx.x; e < s.sn_first + (s.M + kSinoBlock - 1) / kSinoBlock; e += kBT)
@@ -264,18 +274,21 @@ __global__ void b_finalize_norm(const TvSlice *__restrict__ d, const int *__rest
 __global__ void b_scale_v(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    int i, j;
-    if (!px_of(it, s, i, j)) return;
-    const size_t k = (size_t)i * s.nx + j;
-    s.z[k] = s.g[k] * sc.invn[it.x];
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (!px_of(it, s, r, i, j)) continue;
+        const size_t k = (size_t)i * s.nx + j;
+        s.z[k] = s.g[k] * sc.invn[it.x];
+    }
 }
 
 __global__ void b_fill_v(const TvSlice *__restrict__ d, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    int i, j;
-    if (!px_of(it, s, i, j)) return;
-    s.z[(size_t)i * s.nx + j] = 1.0f;
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (px_of(it, s, r, i, j)) s.z[(size_t)i * s.nx + j] = 1.0f;
+    }
 }
 
 __global__ void b_set_step(const TvSlice *__restrict__ d, Scal sc, double L_fixed, int n) {
@@ -291,18 +304,20 @@ __global__ void b_set_step(const TvSlice *__restrict__ d, Scal sc, double L_fixe
 __global__ void b_copy_x(const TvSlice *__restrict__ d, const int4 *__restrict__ items, int mode, int it_parity) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    int i, j;
-    if (!px_of(it, s, i, j)) return;
-    const size_t k = (size_t)i * s.nx + j;
-    if (mode == 0) {           // cold start
-        s.xa[k] = 0.0f;
-        s.y[k] = 0.0f;
-    } else if (mode == 1) {    // warm start
-        const float v = s.x_user[k];
-        s.xa[k] = v;
-        s.y[k] = v;
-    } else {                   // result
-        s.x_user[k] = it_parity ? s.xa[k] : s.xb[k];
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (!px_of(it, s, r, i, j)) continue;
+        const size_t k = (size_t)i * s.nx + j;
+        if (mode == 0) {           // cold start
+            s.xa[k] = 0.0f;
+            s.y[k] = 0.0f;
+        } else if (mode == 1) {    // warm start
+            const float v = s.x_user[k];
+            s.xa[k] = v;
+            s.y[k] = v;
+        } else {                   // result
+            s.x_user[k] = it_parity ? s.xa[k] : s.xb[k];
+        }
     }
 }
 
@@ -351,7 +366,7 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     for (int y = 0; y < (g.ny + 31) / 32; ++y)
         for (int x = 0; x < (g.nx + 31) / 32; ++x) tr.push_back(make_int4(s, x, y, 0));
     auto &px = rep_only ? P.px_r : P.px;
-    for (int y = 0; y < (g.ny + 7) / 8; ++y)
+    for (int y = 0; y < (g.ny + kPxRows - 1) / kPxRows; ++y)
         for (int x = 0; x < (g.nx + 31) / 32; ++x) px.push_back(make_int4(s, x, y, 0));
     auto &sn = rep_only ? P.sn_r : P.sn;
     const int M = g.n_angles * g.n_bins;
