@@ -86,37 +86,57 @@ __device__ __forceinline__ size_t act_idx(int img, int y, int x, int c, int H, i
 }
 
 // ----------------------------------------------------------------- layer 1
-// One thread per pixel: 32 outputs from the 3x3 neighbourhood of z.
+// One thread per pixel: 32 outputs from the 3x3 neighbourhood of z.  The
+// CTA's 128 output pixels (64 B each, contiguous in NHWC) pass through shared
+// memory so that the global stores are consecutive 16-byte words.
 __global__ void __launch_bounds__(128) conv_first_kernel(const float *__restrict__ z, const float *__restrict__ params,
                                                          uint4 *__restrict__ act, int H, int W) {
-    __shared__ float sw[9 * kC], sb[kC];
-    for (int i = threadIdx.x; i < 9 * kC; i += 128) sw[i] = bf16r(params[kW1 + i]);
+    __shared__ __align__(16) float sw[9 * kC];         // [tap][channel]: four weights per 16-byte read
+    __shared__ float sb[kC];
+    __shared__ __align__(16) uint4 so[4][129];          // [chunk][pixel], one pad word per chunk row
+    for (int i = threadIdx.x; i < 9 * kC; i += 128) {
+        const int ch = i / 9, t = i - 9 * ch;           // params hold W_1[ch][0][t]
+        sw[t * kC + ch] = bf16r(params[kW1 + i]);
+    }
     if (threadIdx.x < kC) sb[threadIdx.x] = params[kB1 + threadIdx.x];
     __syncthreads();
-    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, img = blockIdx.z;
-    if (x >= W) return;
-    const float *zi = z + (size_t)img * H * W;
-    float nb[9];
+    const int x0 = blockIdx.x * 128, x = x0 + threadIdx.x, y = blockIdx.y, img = blockIdx.z;
+    if (x < W) {
+        const float *zi = z + (size_t)img * H * W;
+        float nb[9];
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
+        for (int u = 0; u < 3; ++u)
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const int yy = y + u - 1, xx = x + v - 1;
-            nb[3 * u + v] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? zi[(size_t)yy * W + xx] : 0.0f;
+            for (int v = 0; v < 3; ++v) {
+                const int yy = y + u - 1, xx = x + v - 1;
+                nb[3 * u + v] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? zi[(size_t)yy * W + xx] : 0.0f;
+            }
+        float a[kC];                                     // per channel, taps summed in order 0 .. 8
+#pragma unroll
+        for (int ch = 0; ch < kC; ++ch) a[ch] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+#pragma unroll
+            for (int q = 0; q < kC / 4; ++q) {
+                const float4 w = *reinterpret_cast<const float4 *>(&sw[t * kC + 4 * q]);
+                a[4 * q] = fmaf(w.x, nb[t], a[4 * q]);
+                a[4 * q + 1] = fmaf(w.y, nb[t], a[4 * q + 1]);
+                a[4 * q + 2] = fmaf(w.z, nb[t], a[4 * q + 2]);
+                a[4 * q + 3] = fmaf(w.w, nb[t], a[4 * q + 3]);
+            }
         }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float o[8];
+        for (int c = 0; c < 4; ++c) {
+            float o[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int ch = 8 * c + k;
-            float a = 0.0f;
-#pragma unroll
-            for (int t = 0; t < 9; ++t) a = fmaf(sw[ch * 9 + t], nb[t], a);
-            o[k] = fmaxf(a + sb[ch], 0.0f);
+            for (int k = 0; k < 8; ++k) o[k] = fmaxf(a[8 * c + k] + sb[8 * c + k], 0.0f);
+            so[c][threadIdx.x] = pack8(o);
         }
-        act[act_idx(img, y, x, c, H, W)] = pack8(o);
     }
+    __syncthreads();
+    const int npx = min(128, W - x0);
+    uint4 *dst = act + act_idx(img, y, x0, 0, H, W);
+    for (int e = threadIdx.x; e < 4 * npx; e += 128) dst[e] = so[e & 3][e >> 2];
 }
 
 // ----------------------------------------------------------------- layers 2-7
@@ -358,16 +378,30 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
 
 // ----------------------------------------------------------------- layer 8
 // One thread per pixel: r = sum over 3x3 x 32 of bf16(W_8) a_7, out = z + r + b_8.
+// The CTA's three input rows (130 pixels each, 64 B per pixel) are staged in
+// shared memory channel-chunk-major, s[row][chunk][pixel], by coalesced
+// 16-byte copies, so that a warp's reads of one (tap, chunk) are 32
+// consecutive 16-byte words.  The sum runs over taps, then chunks, then
+// channels, as before the staging (same bits).
 __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict__ act, const float *__restrict__ z,
                                                         const float *__restrict__ params, float *__restrict__ out,
                                                         int H, int W) {
-    __shared__ float sw[9 * kC];
+    __shared__ __align__(16) float sw[9 * kC];         // [tap][channel]
+    __shared__ __align__(16) uint4 srow[3][4][130];
+    const int x0 = blockIdx.x * 128, y = blockIdx.y, img = blockIdx.z;
     for (int i = threadIdx.x; i < 9 * kC; i += 128) {
         const int c = i / 9, t = i % 9;                    // params hold W_8[0][c][t]
         sw[t * kC + c] = bf16r(params[kW8 + i]);
     }
+    for (int e = threadIdx.x; e < 3 * 130 * 4; e += 128) {   // asynchronous copies, all in flight at once
+        const int rr = e / 520, rem = e - rr * 520, px = rem >> 2, c = rem & 3;
+        const int yy = y - 1 + rr, xx = x0 - 1 + px;
+        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        tc::cp16(&srow[rr][c][px], in ? act + act_idx(img, yy, xx, c, H, W) : act, in ? 16u : 0u);
+    }
+    tc::cp_wait_all();
     __syncthreads();
-    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, img = blockIdx.z;
+    const int x = x0 + threadIdx.x;
     if (x >= W) return;
 
     float acc = 0.0f;
@@ -378,9 +412,12 @@ __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict_
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             float v[8];
-            unpack8(act[act_idx(img, yy, xx, c, H, W)], v);
+            unpack8(srow[t / 3][c][threadIdx.x + t % 3], v);
+            const float4 w0 = *reinterpret_cast<const float4 *>(&sw[t * kC + 8 * c]);
+            const float4 w1 = *reinterpret_cast<const float4 *>(&sw[t * kC + 8 * c + 4]);
+            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc = fmaf(sw[t * kC + 8 * c + k], v[k], acc);
+            for (int k = 0; k < 8; ++k) acc = fmaf(w[k], v[k], acc);
         }
     }
     const size_t o = ((size_t)img * H + y) * W + x;
