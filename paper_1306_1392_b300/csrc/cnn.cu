@@ -393,11 +393,16 @@ __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict_
         const int c = i / 9, t = i % 9;                    // params hold W_8[0][c][t]
         sw[t * kC + c] = bf16r(params[kW8 + i]);
     }
-    for (int e = threadIdx.x; e < 3 * 130 * 4; e += 128) {   // asynchronous copies, all in flight at once
-        const int rr = e / 520, rem = e - rr * 520, px = rem >> 2, c = rem & 3;
-        const int yy = y - 1 + rr, xx = x0 - 1 + px;
-        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-        tc::cp16(&srow[rr][c][px], in ? act + act_idx(img, yy, xx, c, H, W) : act, in ? 16u : 0u);
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr) {                          // asynchronous copies, all in flight at once
+        const int yy = y - 1 + rr;
+        const bool row_in = yy >= 0 && yy < H;
+        const uint4 *src_row = act + act_idx(img, row_in ? yy : 0, 0, 0, H, W);
+        for (int e = threadIdx.x; e < 130 * 4; e += 128) {   // e = 4 px + c: consecutive 16-byte words
+            const int px = e >> 2, c = e & 3, xx = x0 - 1 + px;
+            const bool in = row_in && xx >= 0 && xx < W;
+            tc::cp16(&srow[rr][c][px], in ? src_row + 4 * xx + c : act, in ? 16u : 0u);
+        }
     }
     tc::cp_wait_all();
     __syncthreads();
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict_
     if (x >= W) return;
 
     float acc = 0.0f;
-#pragma unroll 1
+#pragma unroll
     for (int t = 0; t < 9; ++t) {
         const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
         if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
@@ -436,6 +441,11 @@ int set_smem_attrs() {
         cudaFuncSetAttribute(conv_mid_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMidSmem) !=
             cudaSuccess)
         return cuda_status("conv_mid_kernel shared-memory attribute");
+    // the last layer's 26 KB of staged rows per 128-pixel CTA: ask for the
+    // largest shared-memory carve-out so that eight CTAs fit on an SM
+    if (cudaFuncSetAttribute(conv_last_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return cuda_status("conv_last_kernel carve-out attribute");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return PYHST_OK;
 }
