@@ -131,6 +131,23 @@ __device__ __forceinline__ float add_rd(float a, float b) {
     return r;
 }
 
+// A float64 sum fed in float32 runs of 8 terms (relative error ~5e-7 per
+// run): one float64 add per 8 terms, FP64 throughput being scarce here.
+struct RunSum {
+    double acc = 0.0;
+    float run = 0.0f;
+    int n = 0;
+    __device__ __forceinline__ void add(float v) {
+        run += v;
+        if (++n == 8) {
+            acc += (double)run;
+            run = 0.0f;
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ double total() const { return acc + (double)run; }
+};
+
 // Paired float32 arithmetic (sm_100+ f32x2): two lanes of work per instruction.
 __device__ __forceinline__ float2 add2_rd(float2 a, float2 b) {
     float2 d;

@@ -69,23 +69,6 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-// A float64 sum fed in float32 runs of 8 terms (relative error ~5e-7 per
-// run): one float64 add per 8 terms, FP64 throughput being scarce here.
-struct RunSum {
-    double acc = 0.0;
-    float run = 0.0f;
-    int n = 0;
-    __device__ __forceinline__ void add(float v) {
-        run += v;
-        if (++n == 8) {
-            acc += (double)run;
-            run = 0.0f;
-            n = 0;
-        }
-    }
-    __device__ __forceinline__ double total() const { return acc + (double)run; }
-};
-
 // C [M][N] = alpha A [M][K] B [K][N] (row-major, float32 sums in k order).
 // Both patch products use it: P = W D (M = patches, K = atoms, N = m^2) and
 // G = 2 P' D^T (K = m^2, N = atoms).  The products are tall and skinny (N and

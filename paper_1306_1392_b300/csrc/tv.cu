@@ -201,14 +201,14 @@ __global__ void sino_update_kernel(const float *__restrict__ axn, const float *_
                                    const float *__restrict__ b, float *__restrict__ ay, float w, size_t n,
                                    double *__restrict__ part) {
     const size_t off = (size_t)blockIdx.y * n;
-    double acc = 0.0;
+    RunSum rs;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float v = axn[off + i];
         const float d = v - b[off + i];
-        acc += (double)d * (double)d;
+        rs.add(d * d);
         ay[off + i] = fmaf(w, v - axo[off + i], v);
     }
-    acc = block_sum(acc);
+    const double acc = block_sum(rs.total());
     if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
 }
 
@@ -218,16 +218,17 @@ __global__ void image_update_kernel(const float *__restrict__ xn, const float *_
                                     double *__restrict__ part) {
     const size_t n = (size_t)nx * ny, off = (size_t)blockIdx.y * n;
     const float *X = xn + off;
-    double acc = 0.0;
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(k / nx), j = (int)(k - (size_t)i * nx);
-        const float v = X[k];
-        const float d1 = (i + 1 < ny) ? X[k + nx] - v : 0.0f;
-        const float d2 = (j + 1 < nx) ? X[k + 1] - v : 0.0f;
-        acc += (double)sqrtf(d1 * d1 + d2 * d2);
-        y[off + k] = fmaf(w, v - xo[off + k], v);
-    }
-    acc = block_sum(acc);
+    RunSum rs;
+    for (int i = blockIdx.x; i < ny; i += gridDim.x)      // block: rows; threads: columns
+        for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+            const size_t k = (size_t)i * nx + j;
+            const float v = X[k];
+            const float d1 = (i + 1 < ny) ? X[k + nx] - v : 0.0f;
+            const float d2 = (j + 1 < nx) ? X[k + 1] - v : 0.0f;
+            rs.add(sqrtf(d1 * d1 + d2 * d2));
+            y[off + k] = fmaf(w, v - xo[off + k], v);
+        }
+    const double acc = block_sum(rs.total());
     if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
 }
 

@@ -164,15 +164,15 @@ __global__ void b_sino_update(const TvSlice *__restrict__ d, const int4 *__restr
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
     const float *axn = it_parity ? s.Axa : s.Axb, *axo = it_parity ? s.Axb : s.Axa;
-    double acc = 0.0;
+    RunSum rs;
     const int base = it.y * kSinoBlock;
     for (int e = base + threadIdx.x; e < min(base + kSinoBlock, s.M); e += kBT) {
         const float v = axn[e];
         const float r = v - s.sino[e];
-        acc += (double)r * (double)r;
+        rs.add(r * r);
         s.Ay[e] = fmaf(w, v - axo[e], v);
     }
-    acc = block_sum(acc);
+    const double acc = block_sum(rs.total());
     if (threadIdx.x == 0) part[sn_slot(it, s)] = acc;
 }
 
