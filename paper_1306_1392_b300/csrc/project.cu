@@ -29,8 +29,8 @@
 // x*(b, r) = X0 + b dX - r rho is computed in 32.32 fixed point (int64), so the
 // staged bands, computed with the same integers, provably contain every tap
 // (with one column to spare on each side).  Inside a chunk each ray follows
-// x* - L0 (L0: the chunk's first staged column) in 9.23 fixed point (int32;
-// 10.22 for the 512-column variant), re-anchored exactly at every chunk, so a
+// x* - L0 (L0: the chunk's first staged column) in unsigned 9.23 fixed point
+// (both band widths), re-anchored exactly at every chunk, so a
 // row costs one integer add and the error stays below 2e-6 pixel; the
 // fraction becomes a float by placing its bits in a mantissa.  Pairs of rays share paired float32 (f32x2) arithmetic.
 // Rays that do not take part in a pass get zero weights and a fixed in-range
@@ -148,7 +148,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     const int n_chunks = c_hi - c_lo;       // chunks of this pass; chunk k is c_lo + k
     if (n_chunks <= 0) return;
     long long X64[kPRays];          // x* + 1/2 at row 0, 32.32
-    float aa[kPRays], t1[kPRays], c1[kPRays];
+    float aa[kPRays], m1[kPRays], t1[kPRays], c1[kPRays];
     bool act[kPRays];
 #pragma unroll
     for (int k = 0; k < kPRays; ++k) {
@@ -156,6 +156,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         act[k] = ((mask >> (asub + 2 * k)) & 1) && w.b <= w.bhi;
         X64[k] = g.X0 + (long long)w.b * g.dX + (1LL << 31);
         aa[k] = act[k] ? g.a : 0.0f;          // inactive: all three weights 0
+        m1[k] = -1.5f * aa[k];
         t1[k] = act[k] ? 1.0f - g.a : -1.0f;
         c1[k] = act[k] ? 1.0f : 0.0f;
     }
@@ -204,7 +205,6 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     load(0, 0);
     commit(0, 0);
     __syncthreads();
-    const float2 m15 = make_float2(-1.5f, -1.5f);
     int seg_left = per - c_lo % per;       // chunks until the current row segment ends
     for (int c = 0; c < n_chunks; ++c) {
         const int cur = c & 1;
@@ -212,18 +212,18 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         if (more) load(c + 1, (c + 1) % 3);
         if (c + 2 < n_chunks) band(c + 2, (c + 2) % 3);
         const int r0 = (c_lo + c) * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[c % 3];
-        // chunk anchors: x* + 1/2 - L0 in fixed point with kFrac fraction bits
-        // (9.23 for 256-column bands, 10.22 for 512; 0 < value < 2^31);
+        // chunk anchors: x* + 1/2 - L0 in unsigned 9.23 fixed point (the band
+        // keeps it inside (2.5, kPW - 5.5), so below 2^32 for both widths);
         // re-anchored from the exact 32.32 value at every chunk, so 16 rounded
-        // row steps add at most 2e-6 bins
-        constexpr int kFrac = kPW <= 256 ? 23 : 22;
-        int x32[kPRays], r32[kPRays];
+        // row steps add at most 1e-6 bins
+        constexpr int kFrac = 23;
+        unsigned x32[kPRays], r32[kPRays];
 #pragma unroll
         for (int k = 0; k < kPRays; ++k) {
             const long long rho = rg[asub + 2 * k].rho;
             const long long rel = X64[k] - (long long)r0 * rho - ((long long)L0 << 32);
-            x32[k] = act[k] ? (int)(rel >> (32 - kFrac)) : (3 << kFrac);
-            r32[k] = act[k] ? (int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0;
+            x32[k] = act[k] ? (unsigned)(rel >> (32 - kFrac)) : (3u << kFrac);
+            r32[k] = act[k] ? (unsigned)(int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0u;
         }
         const float *S = &strip[cur][0][0];
         auto row = [&](const float *Sr) {   // one staged row: three taps per ray
@@ -231,8 +231,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
 #pragma unroll
             for (int k = 0; k < kPRays; ++k) {
                 const float *q = Sr + (x32[k] >> kFrac) - 1;
-                const int fr = x32[k] & ((1 << kFrac) - 1);
-                v[k] = __int_as_float((kFrac == 23 ? fr : fr << 1) | 0x3F800000);   // 1 + frac in [1, 2)
+                v[k] = __uint_as_float((x32[k] & 0x7FFFFFu) | 0x3F800000u);   // 1 + frac in [1, 2)
                 q0[k] = q[0];
                 q1[k] = q[1];
                 q2[k] = q[2];
@@ -241,10 +240,11 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 const int k = 2 * p;
-                const float2 ps = add2(make_float2(v[k], v[k + 1]), m15);       // psi in [-1/2, 1/2)
-                const float2 ap = mul2(make_float2(aa[k], aa[k + 1]), ps);
+                // a psi = a (1 + frac) - 3a/2, psi in [-1/2, 1/2)
+                const float2 ap = fma2(make_float2(aa[k], aa[k + 1]), make_float2(v[k], v[k + 1]),
+                                       make_float2(m1[k], m1[k + 1]));
                 const float2 wl = make_float2(__saturatef(t1[k] - ap.x), __saturatef(t1[k + 1] - ap.y));
-                const float2 wc = make_float2(fmaf(-aa[k], fabsf(ps.x), c1[k]), fmaf(-aa[k + 1], fabsf(ps.y), c1[k + 1]));
+                const float2 wc = make_float2(c1[k] - fabsf(ap.x), c1[k + 1] - fabsf(ap.y));
                 const float2 wr = make_float2(__saturatef(t1[k] + ap.x), __saturatef(t1[k + 1] + ap.y));
                 acc[p] = fma2(wl, make_float2(q0[k], q0[k + 1]), acc[p]);
                 acc[p] = fma2(wc, make_float2(q1[k], q1[k + 1]), acc[p]);
