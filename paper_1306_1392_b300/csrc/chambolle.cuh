@@ -34,7 +34,7 @@ constexpr int kChKDefault = 5;              // steps fused per launch unless tun
 __host__ __device__ constexpr int chambolle_tile_size(int K) { return kChR - 2 * K; }
 inline bool chambolle_k_supported(int K) { return K == 2 || K == 3 || K == 4 || K == 5 || K == 6 || K == 8; }
 constexpr int kChThreads = 32 * kChR / kChRows;
-constexpr int kChMinBlocks = 3;             // register budget: three CTAs per SM
+constexpr int kChMinBlocks = 4;             // register budget: four CTAs per SM (64 registers)
 // dynamic shared memory per CTA: the strips' last p1 rows and first G rows,
 // each with a zero guard row
 constexpr size_t kChSmem = sizeof(float) * 2 * (kChR / kChRows + 1) * kChR;
