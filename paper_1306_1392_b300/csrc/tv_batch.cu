@@ -63,7 +63,7 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Pixel work items are 32 columns x kPxRows rows; thread t of a CTA takes
 // column t % 32 and rows t / 32 + 8 r (r < kPxRows / 8).
-constexpr int kPxRows = 32;
+constexpr int kPxRows = 64;
 
 // Partial-sum slots: a slice's pixel items (32 x kPxRows) and sinogram items are
 // numbered from its px_first / sn_first in the order the host lists them, so
@@ -140,6 +140,7 @@ __global__ void b_prox_final(const TvSlice *__restrict__ d, const int4 *__restri
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
     float *xn = it_parity ? s.xa : s.xb;
+#pragma unroll
     for (int r = 0; r < kPxRows / 8; ++r) {
         int i, j;
         if (!px_of(it, s, r, i, j)) continue;
@@ -183,6 +184,7 @@ __global__ void b_image_update(const TvSlice *__restrict__ d, const int4 *__rest
     const TvSlice s = d[it.x];
     const float *xn = it_parity ? s.xa : s.xb, *xo = it_parity ? s.xb : s.xa;
     float tvp = 0.0f;
+#pragma unroll
     for (int r = 0; r < kPxRows / 8; ++r) {
         int i, j;
         if (!px_of(it, s, r, i, j)) continue;
@@ -227,6 +229,7 @@ __global__ void b_sqnorm_g(const TvSlice *__restrict__ d, const int4 *__restrict
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
     double acc = 0.0;
+#pragma unroll
     for (int r = 0; r < kPxRows / 8; ++r) {
         int i, j;
         if (!px_of(it, s, r, i, j)) continue;
@@ -274,6 +277,7 @@ __global__ void b_finalize_norm(const TvSlice *__restrict__ d, const int *__rest
 __global__ void b_scale_v(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
+#pragma unroll
     for (int r = 0; r < kPxRows / 8; ++r) {
         int i, j;
         if (!px_of(it, s, r, i, j)) continue;
@@ -285,6 +289,7 @@ __global__ void b_scale_v(const TvSlice *__restrict__ d, const int4 *__restrict_
 __global__ void b_fill_v(const TvSlice *__restrict__ d, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
+#pragma unroll
     for (int r = 0; r < kPxRows / 8; ++r) {
         int i, j;
         if (px_of(it, s, r, i, j)) s.z[(size_t)i * s.nx + j] = 1.0f;
@@ -304,6 +309,7 @@ __global__ void b_set_step(const TvSlice *__restrict__ d, Scal sc, double L_fixe
 __global__ void b_copy_x(const TvSlice *__restrict__ d, const int4 *__restrict__ items, int mode, int it_parity) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
+#pragma unroll
     for (int r = 0; r < kPxRows / 8; ++r) {
         int i, j;
         if (!px_of(it, s, r, i, j)) continue;
