@@ -62,7 +62,7 @@ def parse():
                     help="overlapping-patch prior on a 2048^2 phantom with 150 projections (Sec. 3.2.1)")
     ap.add_argument("--precision-study", action="store_true",
                     help="mixed-precision FBP study (4096^2, 4000 angles; f32/f16/bf16 storage vs the FP64 oracle)")
-    ap.add_argument("--precision-slices", type=int, default=2, help="slices checked against the oracle")
+    ap.add_argument("--precision-slices", type=int, default=4, help="slices checked against the oracle")
     ap.add_argument("--tv-only", action="store_true", help="only the reduced-dose TV measurement (for profilers)")
     ap.add_argument("--pre-study", action="store_true",
                     help="cost of the Sec. 2.3 preprocessing variants on the batched-volume geometry")
