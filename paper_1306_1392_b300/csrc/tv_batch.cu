@@ -422,6 +422,22 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
     };
     P.proj_narrow = (int)(std::stable_partition(P.proj.begin(), P.proj.end(), narrow) - P.proj.begin());
     P.proj_r_narrow = (int)(std::stable_partition(P.proj_r.begin(), P.proj_r.end(), narrow) - P.proj_r.begin());
+    // Longest items first: CTAs start roughly in list order, so the long
+    // items of the large slices run early and the short ones fill the last
+    // wave.  A CTA's result does not depend on its place in the list.
+    auto longest_first = [](std::vector<int4>::iterator b, std::vector<int4>::iterator e, auto cost) {
+        std::stable_sort(b, e, [&](const int4 &u, const int4 &v) { return cost(u) > cost(v); });
+    };
+    auto bp_cost = [&](const int4 &it) { return items[it.x].geom.n_angles; };       // angles per output tile
+    auto proj_cost = [&](const int4 &it) {                                           // rows walked per ray
+        return std::max(items[it.x].geom.nx, items[it.x].geom.ny);
+    };
+    longest_first(P.bp.begin(), P.bp.end(), bp_cost);
+    longest_first(P.bp_r.begin(), P.bp_r.end(), bp_cost);
+    longest_first(P.proj.begin(), P.proj.begin() + P.proj_narrow, proj_cost);
+    longest_first(P.proj.begin() + P.proj_narrow, P.proj.end(), proj_cost);
+    longest_first(P.proj_r.begin(), P.proj_r.begin() + P.proj_r_narrow, proj_cost);
+    longest_first(P.proj_r.begin() + P.proj_r_narrow, P.proj_r.end(), proj_cost);
     return P;
 }
 
