@@ -297,6 +297,46 @@ def test_beta_scan_estimators_parity(P, orc, cuda_device, held_out):
     np.testing.assert_allclose(ec.cpu().numpy()[1:], ec_ref[1:], atol=2e-4)
 
 
+def test_beta_scan_full_size_properties(P, cuda_device):
+    """The scan at the size of the Sec. 4 study (2048^2 foam, 150
+    projections, angle 75 held out), a few iterations per beta.  Properties
+    that hold at any size: each reconstruction equals, bit for bit, the
+    single-slice solve of the 149 kept projections with its beta and the same
+    step size; the cross-validation error is the squared distance between
+    the held-out row and that reconstruction's projection at the held-out
+    angle; E_cohe is Cos(x_b - x_0, x_b) of the returned reconstructions."""
+    dev = cuda_device
+    n, na, h = 2048, 150, 75
+    fs = acq.foam_slice(n, na, seed=5150, device=dev, truth=False)
+    sino = fs.extra["sino"].to(dev)
+    ang, ax = fs.angles.to(dev), fs.axis.to(dev)
+    keep = torch.tensor([a for a in range(na) if a != h], device=dev)
+    geo = P.Geometry(ang, ax, n, n, n, fs.pixel_size)
+    geo_k = P.Geometry(ang[keep].contiguous(), ax[keep].contiguous(), n, n, n, fs.pixel_size)
+    geo_h = P.Geometry(ang[h:h + 1].contiguous(), ax[h:h + 1].contiguous(), n, n, n, fs.pixel_size)
+    sino_k = sino[keep].contiguous()
+    _, _, lip = P.pyhst_tv_solve(geo_k, sino_k[None], P.TvOptions(beta=1e-3, n_iter=1, n_inner=1, n_power_iter=30),
+                                 energy=False)
+    L = lip.item()
+    betas = [1e-5, 1e-3, 1e-2]
+    opts = P.TvOptions(beta=0.0, n_iter=4, n_inner=20, lipschitz=L)
+    x, cv, ec = P.pyhst_beta_scan(geo, sino, betas, opts, held_out=h)
+    torch.cuda.synchronize()
+    for k, b in enumerate(betas):
+        x1, _, _ = P.pyhst_tv_solve(geo_k, sino_k[None], P.TvOptions(beta=b, n_iter=4, n_inner=20, lipschitz=L),
+                                    energy=False)
+        assert torch.equal(x[k], x1[0]), k
+    rows = P.pyhst_project(geo_h, x)[:, 0, :].double()
+    cv_ref = ((rows - sino[h].double()[None]) ** 2).sum(dim=1).cpu().numpy()
+    np.testing.assert_allclose(cv.cpu().numpy(), cv_ref, rtol=1e-9)
+    xd = x.double()
+    for k in range(1, len(betas)):
+        d = xd[k] - xd[0]
+        cos = (d * xd[k]).sum() / (d.norm() * xd[k].norm())
+        assert abs(ec[k].item() - cos.item()) <= 1e-9
+    assert math.isnan(ec[0].item())
+
+
 def test_tv_solve_capture_matches_oracle_prox_inputs(P, orc, cuda_device):
     """The captured prox inputs z_k of iterations 1, 4 and 9 equal the
     oracle's (FISTA stopped after k iterations returns its last z), and the
