@@ -90,7 +90,7 @@ void orc_ramlak_filter(const double *p, int64_t n_rows, int64_t n_bins, double *
         }
 }
 
-/* Other ramp filters (the SURVEYed boundary's later filters), as spatial
+/* Other ramp filters (the C boundary's Shepp-Logan and Hann options), as spatial
  * kernels of unit bin spacing applied by the same linear convolution:
  *   kind 1, Shepp-Logan (Kak & Slaney): h(n) = -2 / (pi^2 (4 n^2 - 1));
  *   kind 2, Hann: the Ram-Lak kernel smoothed by (1/4, 1/2, 1/4),
