@@ -253,8 +253,8 @@ size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_tv_opts *opt
  * by n_inner steps of Chambolle's dual fixed point from a zero dual field
  * (the TV prox inside pyhst_tv_solve; on its own it is the denoising case of
  * the paper's functional, where the projection operator is the identity,
- * Sec. 3.2.1).  z, x: [n_slices][ny][nx] float32 (x may not alias z).
- * lam = 0 copies z. */
+ * Sec. 3.2.1).  z, x: [n_slices][ny][nx] float32; x must not overlap z
+ * (PYHST_ERR_INVALID_ARG).  lam = 0 copies z. */
 size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n_slices);
 int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
                   float tau, float *x, void *workspace, size_t ws_bytes, pyhst_stream_t stream);

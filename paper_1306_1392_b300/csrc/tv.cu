@@ -440,6 +440,11 @@ extern "C" int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_s
     if (!(lam >= 0.0f) || !std::isfinite(lam)) return fail(PYHST_ERR_INVALID_ARG, "lam must be >= 0");
     if (n_inner < 1) return fail(PYHST_ERR_INVALID_ARG, "n_inner must be >= 1");
     if (!(tau > 0.0f && tau <= 0.25f)) return fail(PYHST_ERR_INVALID_ARG, "tau must be in (0, 1/4]");
+    {   // every launch reads z around its tiles while the last one writes x
+        const uintptr_t bytes = sizeof(float) * (size_t)nx * ny * n_slices;
+        const uintptr_t xa = reinterpret_cast<uintptr_t>(x), za = reinterpret_cast<uintptr_t>(z);
+        if (xa < za + bytes && za < xa + bytes) return fail(PYHST_ERR_INVALID_ARG, "x overlaps z");
+    }
     const size_t need = tv_prox_workspace_bytes(nx, ny, n_slices);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
         return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
