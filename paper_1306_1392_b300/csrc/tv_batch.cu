@@ -14,6 +14,7 @@
 // size is estimated once per distinct geometry (same angle/axis arrays, sizes,
 // centre and pixel size) by power iteration on one representative slice.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <map>
 #include <tuple>
@@ -478,7 +479,11 @@ int check_items(const pyhst_tv_item *items, int n) {
         pyhst_geometry g = items[s].geom;
         g.n_slices = 1;
         int rc = check_geometry(&g);
-        if (rc) return fail(rc, "item %d: %s", s, pyhst_last_error());
+        if (rc) {
+            char inner[512];   // the message is formatted into the same per-thread buffer
+            snprintf(inner, sizeof inner, "%s", pyhst_last_error());
+            return fail(rc, "item %d: %s", s, inner);
+        }
         if (!items[s].sino || !items[s].x) return fail(PYHST_ERR_INVALID_ARG, "item %d: sino/x pointer is NULL", s);
         if (!std::isfinite(items[s].beta)) return fail(PYHST_ERR_INVALID_ARG, "item %d: beta is not finite", s);
     }

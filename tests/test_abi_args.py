@@ -78,3 +78,94 @@ def test_binding_refuses_host_tensors():
         P.pyhst_tv_prox(torch.zeros((8, 8)), 0.1)
     with pytest.raises(TypeError, match="CUDA tensor"):
         P.pyhst_cnn_forward(torch.zeros(P.pyhst_cnn_param_count()), torch.zeros((1, 8, 8)))
+
+
+def _geom(L, **kw):
+    d = dict(n_angles=180, n_bins=256, nx=256, ny=256, n_slices=1, angles=8, axis=8, cx=127.5, cy=127.5,
+             pixel_size=2 / 256)
+    d.update(kw)
+    return L.pyhst_geometry(**d)
+
+
+def _opts(L, **kw):
+    d = dict(beta=0.1, n_iter=5, n_inner=20, tau=0.125, use_fista=1, warm_start=0, lipschitz=0.0, n_power_iter=10)
+    d.update(kw)
+    return L.pyhst_tv_opts(**d)
+
+
+def test_tv_batch_argument_checks(L):
+    o = _opts(L)
+    items = (L.pyhst_tv_item * 2)()
+    for it in items:
+        it.geom, it.sino, it.x, it.energy, it.beta = _geom(L), 1024, 2048, None, -1.0
+    call = lambda n=2, wsb=BIG: L.lib.pyhst_tv_solve_batch(items, n, ctypes.byref(o), None, 256, wsb, None)
+    E = L.PYHST_ERR_INVALID_ARG
+    assert call(n=0) == E
+    items[1].sino = None
+    assert call() == E and L.lib.pyhst_last_error().decode().startswith("item 1:")
+    items[1].sino = 1024
+    items[1].beta = float("nan")
+    assert call() == E
+    items[1].beta = -1.0
+    items[1].geom = _geom(L, nx=0)
+    assert call() == E
+    assert L.lib.pyhst_last_error().decode() == "item 1: image 0 x 256 outside [1, 16384]^2"
+    items[1].geom = _geom(L)
+    assert call(wsb=64) == L.PYHST_ERR_WORKSPACE
+
+
+def test_beta_scan_argument_checks(L):
+    g, o = _geom(L), _opts(L)
+    betas = (ctypes.c_float * 3)(1e-5, 1e-3, 1e-2)
+    call = lambda b=betas, n=3, held=5, cv=None: L.lib.pyhst_beta_scan(ctypes.byref(g), 1024, b, n, held,
+                                                                       ctypes.byref(o), 2048, cv, None, 256, BIG,
+                                                                       None)
+    E = L.PYHST_ERR_INVALID_ARG
+    assert call(n=0) == E
+    assert call(held=180) == E and call(held=-2) == E       # an angle index of the 180, or -1
+    assert call(held=-1, cv=4096) == E                      # cross-validation needs a held-out angle
+    assert call(b=None) == E
+    assert call(b=(ctypes.c_float * 3)(1e-5, -1e-3, 1e-2)) == E
+
+
+def test_cnn_training_argument_checks(L):
+    E = L.PYHST_ERR_INVALID_ARG
+    assert L.lib.pyhst_cnn_grad(256, 512, 768, 0, 64, 64, 1024, None, 2048, BIG, None) == E
+    assert L.lib.pyhst_cnn_grad(256, None, 768, 1, 64, 64, 1024, None, 2048, BIG, None) == E
+    adam = lambda count=100, step=1, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8: L.lib.pyhst_cnn_adam(
+        256, 512, 768, 1024, count, step, lr, b1, b2, eps, None)
+    assert adam(step=0) == E and adam(count=0) == E
+    assert adam(lr=0.0) == E and adam(b1=1.0) == E and adam(b2=1.0) == E and adam(eps=0.0) == E
+
+
+def test_patch_argument_checks(L):
+    E = L.PYHST_ERR_INVALID_ARG
+    pp = lambda **kw: L.pyhst_patch_problem(**{**dict(ny=64, nx=64, m=8, stride=4, n_atoms=64, dict=4096,
+                                                      rho=1.0), **kw})
+    image = lambda p, wsb=BIG: L.lib.pyhst_patch_image(ctypes.byref(p) if p else None, 256, 512, 1024, wsb, None)
+    assert image(None) == E
+    assert image(pp(n_atoms=2048)) == E          # n_atoms x m^2 above 65536
+    assert image(pp(m=32, stride=4)) == E        # patches above 16 x 16
+    assert image(pp(rho=-1.0)) == E
+    assert image(pp(dict=None)) == E
+    assert image(pp(), wsb=16) == L.PYHST_ERR_WORKSPACE
+    gp = _geom(L, nx=64, ny=64, n_bins=64)
+    solve = lambda beta=0.1, n_iter=5: L.lib.pyhst_patch_solve(ctypes.byref(pp()), ctypes.byref(gp), 256, beta, 0.0,
+                                                               10, n_iter, 1, 512, None, None, None, 1024, BIG, None)
+    assert solve(n_iter=0) == E and solve(beta=-0.1) == E
+    other = _geom(L, nx=128, ny=128, n_bins=64)
+    assert L.lib.pyhst_patch_gradient(ctypes.byref(pp()), ctypes.byref(other), 256, 512, 768, None, 1024, BIG,
+                                      None) == E
+
+
+def test_capture_pnp_profile_and_tuning_checks(L):
+    g, o = _geom(L), _opts(L)
+    E = L.PYHST_ERR_INVALID_ARG
+    iters = (ctypes.c_int32 * 2)(1, 9)                    # 9 > n_iter = 5
+    assert L.lib.pyhst_tv_solve_capture(ctypes.byref(g), 1024, ctypes.byref(o), 2048, 2, iters, 4096, 256, BIG,
+                                        None) == E
+    assert L.lib.pyhst_pnp_solve(ctypes.byref(g), 1024, None, ctypes.byref(o), 2048, None, None, 256, BIG,
+                                 None) == E
+    d, n = ctypes.c_double(), ctypes.c_int64()
+    assert L.lib.pyhst_profile_read(b"nonsense", ctypes.byref(d), ctypes.byref(n)) == E
+    assert L.lib.pyhst_set_tv_prox_steps(64, 64, 7) == E   # supported: 2, 3, 4, 5, 6, 8
