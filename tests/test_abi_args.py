@@ -169,3 +169,23 @@ def test_capture_pnp_profile_and_tuning_checks(L):
     d, n = ctypes.c_double(), ctypes.c_int64()
     assert L.lib.pyhst_profile_read(b"nonsense", ctypes.byref(d), ctypes.byref(n)) == E
     assert L.lib.pyhst_set_tv_prox_steps(64, 64, 7) == E   # supported: 2, 3, 4, 5, 6, 8
+
+
+def test_fbp_pre_and_host_argument_checks(L):
+    g = _geom(L, n_slices=2)
+    E = L.PYHST_ERR_INVALID_ARG
+    ok = dict(n_flats=2, flats=4096, flat_pos=8192, hotspot_threshold=0.0, ring_window=0)
+    pre = lambda kind=0, wsb=BIG, **kw: L.lib.pyhst_fbp_pre(
+        ctypes.byref(g), kind, 256, 256, 512, 8, ctypes.byref(L.pyhst_preproc(**{**ok, **kw})), 0, 0, 512, 1024,
+        wsb, None)
+    assert pre(kind=L.PYHST_F32_SINO) == E              # raw counts only
+    assert pre(n_flats=0, flats=None, flat_pos=None) == E
+    assert pre(flats=None) == E
+    assert pre(hotspot_threshold=-1.0) == E
+    assert pre(ring_window=2) == E                      # 0 or odd >= 3
+    assert pre(wsb=16) == L.PYHST_ERR_WORKSPACE
+    assert L.lib.pyhst_fbp_pre(ctypes.byref(g), 0, 256, 256, 512, 8, None, 0, 0, 512, 1024, BIG, None) == E
+    host = lambda data=256, flat=8, spc=16, wsb=BIG: L.lib.pyhst_fbp_host(
+        ctypes.byref(g), 0, data, 256, 512, flat, 8, 0, 0, 4096, spc, 1024, wsb, None)
+    assert host(spc=0) == E and host(data=None) == E and host(flat=None) == E
+    assert host(wsb=16) == L.PYHST_ERR_WORKSPACE
