@@ -188,3 +188,26 @@ def test_fbp_single_slice_workload_quality(orc):
     mse = np.mean((img - truth)[disk] ** 2)
     psnr = 10 * math.log10((truth.max() - truth.min()) ** 2 / mse)
     assert psnr > 24.0, psnr
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_backproject_at_equals_full_backprojection(orc, case):
+    """The spot-check back-projection (used by every full-size parity test)
+    evaluates the same sum as the whole-image back-projection at every pixel
+    of small non-square, off-centre geometries with per-angle axes, so a
+    swapped row/column or a wrong centre in it shows up here."""
+    g = np.random.default_rng(300 + case)
+    nx, ny = ((23, 17), (31, 12), (9, 40))[case]
+    na, nb = int(g.integers(5, 30)), int(g.integers(20, 50))
+    angles = g.uniform(0, math.pi, na)
+    axis = (nb - 1) / 2.0 + g.uniform(-4, 4, na)
+    cx, cy = (nx - 1) / 2 + g.uniform(-3, 3), (ny - 1) / 2 + g.uniform(-3, 3)
+    q = g.standard_normal((na, nb))
+    w = float(g.uniform(0.5, 2.0))
+    full = orc.backproject(q, angles, axis, nx, ny, w, cx, cy)
+    ii, jj = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    at = orc.backproject_at(q, angles, axis, nx, ny, ii.ravel(), jj.ravel(), w, cx, cy)
+    np.testing.assert_allclose(at, full.ravel(), rtol=0, atol=1e-14 * np.abs(full).max())
+    # and both equal the transpose of the dense hat-function matrix
+    A = _dense_A(angles, axis, nb, nx, ny, cx, cy)
+    np.testing.assert_allclose(at, w * (A.T @ q.ravel()), rtol=0, atol=1e-12 * np.abs(full).max())

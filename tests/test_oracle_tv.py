@@ -181,3 +181,51 @@ def test_cross_validation_is_zero_on_consistent_data(orc):
     e1, _ = orc.cross_validation(geo, y, 7, [0.0], L, 1000, n_inner=1)
     e3, _ = orc.cross_validation(geo, y, 7, [0.0], L, 3000, n_inner=1)
     assert e3[0] < 1e-8 * np.sum(y[7] ** 2) and e3[0] < 0.1 * e1[0]   # -> 0 as the solve converges
+
+
+def _np_tv(x):
+    """Eq. 2 written with numpy differences (Neumann: zero past the last row
+    and column), independent of the oracle's loops."""
+    d1 = np.zeros_like(x)
+    d2 = np.zeros_like(x)
+    d1[:-1, :] = np.diff(x, axis=0)
+    d2[:, :-1] = np.diff(x, axis=1)
+    return np.sqrt(d1 ** 2 + d2 ** 2).sum()
+
+
+def test_energy_closed_forms(orc):
+    """Eq. 3 at points where it is known exactly: E(0) = 1/2 ||y||^2 for any
+    beta (TV(0) = 0); for data y = P x_t of a ramp x_t = a j the data term
+    vanishes and E(x_t) = beta |a| ny (nx - 1), the ramp's total variation."""
+    geo = _tiny_geometry(orc, n=10, na=7, nb=16, seed=9)
+    g = np.random.default_rng(11)
+    y = g.standard_normal((7, 16))
+    for beta in (0.0, 0.37, 5.0):
+        assert orc.energy(geo, y, np.zeros((10, 10)), beta) == pytest.approx(0.5 * np.sum(y ** 2), rel=1e-15)
+    a = -1.3
+    xt = a * np.arange(10)[None, :] * np.ones((10, 1))
+    yt = geo.P(xt)
+    for beta in (0.0, 0.25, 3.0):
+        assert orc.energy(geo, yt, xt, beta) == pytest.approx(beta * abs(a) * 10 * 9, rel=1e-13, abs=1e-13)
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_energy_equals_dense_system(orc, case):
+    """Eq. 3 against the dense hat-function system matrix built entry by
+    entry (off-centre, per-angle axes) and a numpy TV: a dropped 1/2, a
+    misplaced beta, a sign flip in the residual or a missing pixel-size
+    scale of the projector changes the value."""
+    from test_oracle_pipeline import _dense_A
+    g = np.random.default_rng(40 + case)
+    nx, ny = ((7, 9), (11, 6), (8, 8))[case]
+    na, nb = int(g.integers(3, 9)), int(g.integers(8, 15))
+    angles = g.uniform(0, math.pi, na)
+    axis = (nb - 1) / 2.0 + g.uniform(-1.5, 1.5, na)
+    s = float(g.uniform(0.05, 0.5))
+    geo = orc.Geometry(angles, axis, nb, nx, ny, s)
+    A = s * _dense_A(angles, axis, nb, nx, ny, (nx - 1) / 2.0, (ny - 1) / 2.0)
+    x = g.standard_normal((ny, nx))
+    y = g.standard_normal((na, nb)) + 3.0
+    beta = float(g.uniform(0.1, 2.0))
+    ref = 0.5 * np.sum((y.ravel() - A @ x.ravel()) ** 2) + beta * _np_tv(x)
+    assert orc.energy(geo, y, x, beta) == pytest.approx(ref, rel=1e-13)
