@@ -174,25 +174,11 @@ def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=Non
     ``slices=(z0, z1)`` reconstructs only that range of the stack (read in
     place); ``out`` then holds z1 - z0 slices.
     """
-    code, dt = _KINDS[kind]
-    _cuda(data, "data", (dt,))
-    raw = kind.endswith("raw")
-    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
-    if na != geom.n_angles or nb != geom.n_bins:
-        raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
-    if raw:
-        _cuda(flat, "flat", (torch.float32,))
-        _cuda(dark, "dark", (torch.float32,))
-        if flat.shape != (ns, nb) or dark.shape != (ns, nb):
-            raise ValueError("flat/dark must be [n_slices, n_bins]")
+    code, raw, data, ns, na, nb, s_stride, a_stride = _fbp_inputs(geom, data, kind, flat, dark, layout)
     z0, z1 = (0, ns) if slices is None else slices
     if not 0 <= z0 < z1 <= ns:
         raise ValueError(f"slice range {slices} outside [0, {ns}]")
-    if out is None:
-        out = torch.empty((z1 - z0, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
-    _cuda(out, "out", (torch.float32,))
-    if out.numel() < (z1 - z0) * geom.ny * geom.nx:
-        raise ValueError("out is too small")
+    out = _fbp_out(geom, out, z1 - z0, data.device)
     g = geom.c(z1 - z0)
     need = L.lib.pyhst_fbp_workspace_size(ctypes.byref(g), pad_len, slices_per_pass)
     ws = _workspace(need, data.device, workspace)
@@ -203,6 +189,43 @@ def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=Non
     kptr = ctypes.c_void_p(dark.data_ptr() + z0 * nb * 4) if raw else None
     _check(L.lib.pyhst_fbp(ctypes.byref(g), code, dptr, s_stride, a_stride, fptr, kptr,
                            _filter_code(filter), pad_len, _ptr(out), _ptr(ws), nbytes, _stream()))
+    return out
+
+
+def _fbp_inputs(geom, data, kind, flat, dark, layout):
+    """Checks shared by the FBP entry points: data of the kind's dtype on the
+    geometry's device and of its shape; flat/dark float32 [n_slices, n_bins]
+    on that device for raw kinds."""
+    if kind not in _KINDS:
+        raise ValueError(f"kind must be one of {sorted(_KINDS)}")
+    code, dt = _KINDS[kind]
+    _cuda(data, "data", (dt,))
+    if geom.angles.device != data.device:
+        raise ValueError(f"geometry tensors on {geom.angles.device}, data on {data.device}")
+    raw = kind.endswith("raw")
+    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
+    if na != geom.n_angles or nb != geom.n_bins:
+        raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
+    if raw:
+        for t, nm in ((flat, "flat"), (dark, "dark")):
+            _cuda(t, nm, (torch.float32,))
+            if t.device != data.device:
+                raise ValueError(f"{nm} is on {t.device}, data on {data.device}")
+            if tuple(t.shape) != (ns, nb):
+                raise ValueError("flat/dark must be [n_slices, n_bins]")
+    return code, raw, data, ns, na, nb, s_stride, a_stride
+
+
+def _fbp_out(geom, out, n_slices, device):
+    """The output stack [n_slices, ny, nx] float32 on ``device`` (allocated
+    when None; a caller's tensor must hold every slice)."""
+    if out is None:
+        return torch.empty((n_slices, geom.ny, geom.nx), dtype=torch.float32, device=device)
+    _cuda(out, "out", (torch.float32,))
+    if out.device != device:
+        raise ValueError(f"out is on {out.device}, data on {device}")
+    if out.numel() < n_slices * geom.ny * geom.nx:
+        raise ValueError(f"out holds {out.numel()} floats, {n_slices} slices of {geom.ny} x {geom.nx} need more")
     return out
 
 
@@ -269,16 +292,11 @@ def pyhst_fbp_static(geom: Geometry, data: torch.Tensor, kind: str, flat=None, d
     """pyhst_fbp for callers that cannot allocate device scratch: the library
     uses its own fixed device array (see include/pyhst.h); calls that overlap
     on the GPU race on it."""
-    code, dt = _KINDS[kind]
-    _cuda(data, "data", (dt,))
-    data, ns, na, nb, s_stride, a_stride = _layout(data, kind, layout)
-    if na != geom.n_angles or nb != geom.n_bins:
-        raise ValueError(f"data shape {tuple(data.shape)} does not match the geometry")
-    if out is None:
-        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=data.device)
-    _cuda(out, "out", (torch.float32,))
+    code, raw, data, ns, na, nb, s_stride, a_stride = _fbp_inputs(geom, data, kind, flat, dark, layout)
+    out = _fbp_out(geom, out, ns, data.device)
     g = geom.c(ns)
-    _check(L.lib.pyhst_fbp_static(ctypes.byref(g), code, _ptr(data), s_stride, a_stride, _ptr(flat), _ptr(dark),
+    _check(L.lib.pyhst_fbp_static(ctypes.byref(g), code, _ptr(data), s_stride, a_stride,
+                                  _ptr(flat) if raw else None, _ptr(dark) if raw else None,
                                   _filter_code(filter), pad_len, _ptr(out), _stream()))
     return out
 

@@ -25,6 +25,19 @@ struct __align__(16) AngleInfo {
 int fail(int code, const char *fmt, ...);   // records the message, returns code
 int cuda_status(const char *what);          // PYHST_OK or PYHST_ERR_CUDA after a launch
 int check_geometry(const pyhst_geometry *g);
+// Argument checks of the FBP entry points (fbp.cu): geometry, input kind,
+// filter, pointers, flat/dark for raw kinds, and the pad length (*P = 0 is
+// replaced by the default power of two >= max(64, 2 n_bins)).
+int check_fbp_args(const pyhst_geometry *g, int kind, const void *data, const float *flat, const float *dark,
+                   int filter, int *P, const void *out);
+bool valid_pad(int P, int n_bins);
+// Slices per filter/back-projection pass: the back-projector's grid has one
+// row per slice (at most 65535) and the filter's grid one CTA per two of the
+// pass's rows (at most 2^30 rows).
+inline int max_slices_per_pass(int n_angles) {
+    const int by_rows = (1 << 30) / (n_angles > 0 ? n_angles : 1);
+    return by_rows < 1 ? 1 : (by_rows < 65535 ? by_rows : 65535);
+}
 // Residual CNN prox (cnn.cu): out = network(z) for n images of H x W.
 int cnn_forward(const float *params, const float *z, float *out, int n, int H, int W, void *ws, cudaStream_t st);
 size_t cnn_workspace_size(int n, int H, int W);

@@ -33,7 +33,7 @@ int default_pad(int n_bins) {
     return P;
 }
 
-static bool valid_pad(int P, int n_bins) { return P >= 2 * n_bins && P <= 16384 && !(P & (P - 1)) && P >= 64; }
+bool valid_pad(int P, int n_bins) { return P >= 2 * n_bins && P <= 16384 && !(P & (P - 1)) && P >= 64; }
 
 static size_t q_slice_bytes(const pyhst_geometry *g) { return sizeof(float) * (size_t)g->n_angles * g->n_bins; }
 
@@ -61,7 +61,7 @@ static int fbp_plan(const pyhst_geometry *g, int P, void *ws, size_t ws_bytes, F
     if (!ws || ((uintptr_t)ws % kAlign) || ws_bytes < fixed + align_up(per))
         return fail(PYHST_ERR_WORKSPACE, "workspace needs at least %zu bytes, 256-byte aligned", fixed + align_up(per));
     const size_t room = ws_bytes - fixed;
-    pl->S = (int)std::min<size_t>((size_t)g->n_slices, std::max<size_t>(1, room / per));
+    pl->S = (int)std::min<size_t>({(size_t)g->n_slices, std::max<size_t>(1, room / per), (size_t)max_slices_per_pass(g->n_angles)});
     pl->P = P;
     Carver cv(ws, ws_bytes);
     pl->tab = cv.take<AngleInfo>(g->n_angles);
@@ -94,7 +94,7 @@ static int fbp_run(const pyhst_geometry *g, int kind, const void *data, int64_t 
     return PYHST_OK;
 }
 
-static int check_fbp_args(const pyhst_geometry *g, int kind, const void *data, const float *flat,
+int check_fbp_args(const pyhst_geometry *g, int kind, const void *data, const float *flat,
                           const float *dark, int filter, int *P, const void *out) {
     int rc = check_geometry(g);
     if (rc) return rc;

@@ -31,7 +31,6 @@ int launch_filter_tables(int P, int filter, void *tables, cudaStream_t st);
 int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angle_stride, const float *flat,
                   const float *dark, int z0, int n_slices_chunk, int n_angles, int n_bins, int P,
                   const void *tables, float *q, cudaStream_t st);
-int default_pad(int n_bins);
 
 namespace {
 
@@ -70,17 +69,9 @@ extern "C" int pyhst_fbp_static(const pyhst_geometry *g, int input_type, const v
                                 int64_t angle_stride, const float *flat, const float *dark, int filter,
                                 int32_t pad_len, float *out, pyhst_stream_t stream) {
     using namespace pyhst;
-    int rc = check_geometry(g);
+    int P = pad_len;
+    int rc = check_fbp_args(g, input_type, data, flat, dark, filter, &P, out);
     if (rc) return rc;
-    if (input_type < PYHST_U16_RAW || input_type > PYHST_BF16_SINO)
-        return fail(PYHST_ERR_INVALID_ARG, "unknown input kind %d", input_type);
-    if (filter < PYHST_RAMLAK || filter > PYHST_HANN) return fail(PYHST_ERR_INVALID_ARG, "unknown filter %d", filter);
-    if (!data || !out) return fail(PYHST_ERR_INVALID_ARG, "data/out pointer is NULL");
-    const bool raw = input_type == PYHST_U16_RAW || input_type == PYHST_F32_RAW;
-    if (raw && (!flat || !dark)) return fail(PYHST_ERR_INVALID_ARG, "raw input needs flat and dark fields");
-    const int P = pad_len == 0 ? default_pad(g->n_bins) : pad_len;
-    if (P < 2 * g->n_bins || P > 16384 || (P & (P - 1)) || P < 64)
-        return fail(PYHST_ERR_INVALID_ARG, "pad_len %d: need a power of two in [max(64, 2 n_bins), 16384]", P);
     // scratch: angle table | FFT tables | filtered rows of S slices
     const size_t tab_b = angle_table_bytes(g->n_angles), fft_b = filter_table_bytes(P);
     const size_t per = sizeof(float) * (size_t)g->n_angles * g->n_bins;
@@ -88,7 +79,8 @@ extern "C" int pyhst_fbp_static(const pyhst_geometry *g, int input_type, const v
         return fail(PYHST_ERR_INVALID_ARG,
                     "pyhst_fbp_static: %d angles x %d bins (pad %d) need %zu bytes of scratch, above its fixed %zu",
                     g->n_angles, g->n_bins, P, tab_b + fft_b + per, kFbpStaticBytes);
-    const int S = (int)std::min<size_t>((size_t)g->n_slices, (kFbpStaticBytes - tab_b - fft_b) / per);
+    const int S = (int)std::min<size_t>({(size_t)g->n_slices, (kFbpStaticBytes - tab_b - fft_b) / per,
+                                         (size_t)max_slices_per_pass(g->n_angles)});
     void *base = nullptr;
     if ((rc = static_scratch(&base))) return rc;
     char *b = static_cast<char *>(base);

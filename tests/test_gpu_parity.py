@@ -299,10 +299,11 @@ def test_fbp_slice_range_in_place(P, cuda_device):
     assert torch.equal(full[3:8], part)
 
 
-@pytest.mark.parametrize("kind,dt", [("f32_sino", torch.float32), ("f16_sino", torch.float16)])
+@pytest.mark.parametrize("kind,dt", [("f32_sino", torch.float32), ("f16_sino", torch.float16),
+                                     ("bf16_sino", torch.bfloat16)])
 def test_fbp_4096_geometry_sampled(P, orc, cuda_device, kind, dt):
     """The mixed-precision workload's slice geometry (4096^2 grid, 4000
-    angles, 4096 bins, FFT length 8192): stored f32 / f16 sinogram, sampled
+    angles, 4096 bins, FFT length 8192): stored f32 / f16 / bf16 sinogram, sampled
     pixels against the oracle evaluated on the same stored values."""
     n, na = 4096, 4000
     p = acq.ellipsoid_sinograms(256, n, na, seed=4000, device=cuda_device, slices=[100])

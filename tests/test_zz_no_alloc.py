@@ -2,32 +2,23 @@
 
 It serves callers that cannot allocate device memory (a framework that owns
 every device allocation, an acquisition loop that may not call cudaMalloc
-while it runs): the scratch is a fixed array inside the library.  The test
-calls it through the C ABI twice in a row, on different inputs, and checks
-each result against pyhst_fbp (the workspace entry point) within the float32
-tolerance of the other parity tests.  This file is collected last.
+while it runs): the scratch is a fixed array inside the library.  The GPU
+tests call it through the C ABI twice in a row, on different inputs, and
+check each result against pyhst_fbp (the workspace entry point): both run the
+same kernels on each slice, so the results are equal bit for bit, including
+a geometry whose filtered rows need two passes through the fixed scratch.
+This file is collected last.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
 from synth import acquisition as acq
 
-REL_L2 = 1e-5
-MAX_ABS = 1e-4
-
 
 def _geometry(P, vol, dev):
     return P.Geometry(vol.angles.to(dev), vol.axis.to(dev), vol.n_bins, vol.nx, vol.ny, vol.pixel_size)
-
-
-def _close(got, ref):
-    got, ref = got.double().cpu().numpy(), ref.double().cpu().numpy()
-    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    mx = np.abs(got - ref).max() / np.abs(ref).max()
-    assert rel <= REL_L2 and mx <= MAX_ABS, (rel, mx)
 
 
 def test_static_entry_rejects_oversized_geometry():
@@ -43,6 +34,34 @@ def test_static_entry_rejects_oversized_geometry():
     assert "static" in L.lib.pyhst_last_error().decode()
 
 
+def test_static_entry_shares_the_fbp_argument_checks():
+    """Host-side checks (no GPU needed): raw kinds without flat or dark, an
+    unknown kind or filter, and a pad length below 2 n_bins are refused with
+    the same messages as pyhst_fbp, before anything runs."""
+    from paper_1306_1392_b300 import _lib as L
+    g = L.pyhst_geometry(100, 64, 32, 32, 2, 8, 8, 15.5, 15.5, 0.1)
+    for kind, flat, dark, filt, pad, what in ((L.PYHST_U16_RAW, None, 8, L.PYHST_RAMLAK, 0, "flat and dark"),
+                                              (L.PYHST_F32_RAW, 8, None, L.PYHST_RAMLAK, 0, "flat and dark"),
+                                              (17, None, None, L.PYHST_RAMLAK, 0, "input kind"),
+                                              (L.PYHST_F32_SINO, None, None, 9, 0, "filter"),
+                                              (L.PYHST_F32_SINO, None, None, L.PYHST_RAMLAK, 64, "pad_len")):
+        rc_s = L.lib.pyhst_fbp_static(ctypes.byref(g), kind, 8, 6400, 64, flat, dark, filt, pad, 8, None)
+        msg_s = L.lib.pyhst_last_error().decode()
+        rc_w = L.lib.pyhst_fbp(ctypes.byref(g), kind, 8, 6400, 64, flat, dark, filt, pad, 8, None, 0, None)
+        msg_w = L.lib.pyhst_last_error().decode()
+        assert rc_s == rc_w == L.PYHST_ERR_INVALID_ARG, (what, rc_s, rc_w)
+        assert what in msg_s and msg_s == msg_w, (msg_s, msg_w)
+
+
+def _c_call(L, geo, kind, data, s_stride, a_stride, fl, dk, out, ns):
+    g = geo.c(ns)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    rc = L.lib.pyhst_fbp_static(ctypes.byref(g), kind, ptr(data), s_stride, a_stride, ptr(fl), ptr(dk),
+                                L.PYHST_RAMLAK, 0, ptr(out), stream)
+    assert rc == 0, L.lib.pyhst_last_error().decode()
+
+
 @pytest.mark.gpu
 def test_static_entry_matches_workspace_entry_twice(cuda_device):
     import paper_1306_1392_b300 as P
@@ -54,12 +73,54 @@ def test_static_entry_matches_workspace_entry_twice(cuda_device):
         raw, fl, dk = vol.raw.to(dev), vol.flat.to(dev), vol.dark.to(dev)
         ref = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk)
         out = torch.full((ns, 160, 160), float("nan"), device=dev)
-        g = geo.c(ns)
-        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-        rc = L.lib.pyhst_fbp_static(ctypes.byref(g), L.PYHST_U16_RAW, ctypes.c_void_p(raw.data_ptr()), 160,
-                                    ns * 160, ctypes.c_void_p(fl.data_ptr()), ctypes.c_void_p(dk.data_ptr()),
-                                    L.PYHST_RAMLAK, 0, ctypes.c_void_p(out.data_ptr()), stream)
-        assert rc == 0, L.lib.pyhst_last_error().decode()
+        _c_call(L, geo, L.PYHST_U16_RAW, raw, 160, ns * 160, fl, dk, out, ns)
         torch.cuda.synchronize()
-        assert torch.isfinite(out).all()
-        _close(out, ref)
+        assert torch.equal(out, ref)
+
+
+@pytest.mark.gpu
+def test_static_entry_multi_pass_matches_workspace_entry(cuda_device):
+    """2000 angles x 1024 bins: 8.2 MB of filtered rows per slice, so the
+    32 MiB scratch holds 4 slices and 6 slices take two passes (4 + 2); the
+    second pass reuses the filtered-row area and writes at a slice offset.
+    Called through the C ABI and through the Python binding, twice in a row
+    on different stacks."""
+    import paper_1306_1392_b300 as P
+    from paper_1306_1392_b300 import _lib as L
+    dev = cuda_device
+    n, na, ns = 1024, 2000, 6
+    per = 4 * na * n
+    assert L.lib.pyhst_fbp_static_max_bytes() // per == 4
+    for seed in (53, 54):
+        vol = acq.ellipsoid_volume(n_slices=ns, n=n, n_angles=na, seed=seed, device=dev, n_ellipsoids=40)
+        geo = _geometry(P, vol, dev)
+        raw, fl, dk = vol.raw.to(dev), vol.flat.to(dev), vol.dark.to(dev)
+        ref = P.pyhst_fbp(geo, raw, "u16_raw", fl, dk)
+        out = torch.full((ns, n, n), float("nan"), device=dev)
+        _c_call(L, geo, L.PYHST_U16_RAW, raw, n, ns * n, fl, dk, out, ns)
+        out2 = P.pyhst_fbp_static(geo, raw, "u16_raw", fl, dk)
+        torch.cuda.synchronize()
+        assert torch.isfinite(ref).all()
+        assert torch.equal(out, ref)
+        assert torch.equal(out2, ref)
+
+
+@pytest.mark.gpu
+def test_static_binding_refuses_bad_tensors(cuda_device):
+    """The binding refuses, before any launch, flat/dark that are on the host,
+    of the wrong dtype or shape, and an output too short for the stack."""
+    import paper_1306_1392_b300 as P
+    dev = cuda_device
+    vol = acq.ellipsoid_volume(n_slices=2, n=64, n_angles=40, seed=55, n_ellipsoids=10)
+    geo = _geometry(P, vol, dev)
+    raw, fl, dk = vol.raw.to(dev), vol.flat.to(dev), vol.dark.to(dev)
+    with pytest.raises(TypeError):
+        P.pyhst_fbp_static(geo, raw, "u16_raw", vol.flat, dk)
+    with pytest.raises(TypeError):
+        P.pyhst_fbp_static(geo, raw, "u16_raw", fl, dk.double())
+    with pytest.raises(ValueError):
+        P.pyhst_fbp_static(geo, raw, "u16_raw", fl[:1], dk)
+    with pytest.raises(TypeError):
+        P.pyhst_fbp_static(geo, raw, "u16_raw", fl, None)
+    with pytest.raises(ValueError):
+        P.pyhst_fbp_static(geo, raw, "u16_raw", fl, dk, out=torch.empty((1, 64, 64), device=dev))
