@@ -235,8 +235,9 @@ def test_tv_solve_full_iteration_count(P, orc, cuda_device):
     benchmark's full count, 200 FISTA iterations x 20 Chambolle steps with the
     benchmark's beta for that size, through the batched solver, against the
     oracle's FISTA with the same step size.  float32 rounding compounds over
-    the iterations; the measured drift at 200 iterations (printed) stays
-    inside the iterative bar: iterate relative L2 <= 1e-4, every energy of the
+    the iterations, but the drift measured at 200 iterations on a B300
+    (iterate 4.9e-7 relative L2, energies 2.0e-7) is well inside the float32
+    bar, which holds here: iterate relative L2 <= 1e-5, every energy of the
     history within 1e-5 relative."""
     n, na, beta = 256, 50, 1.7783e-3
     fs = acq.foam_slice(n, na, seed=3000, truth=False)
@@ -252,7 +253,7 @@ def test_tv_solve_full_iteration_count(P, orc, cuda_device):
     re = np.abs(es[0].cpu().numpy() - er) / np.abs(er)
     print(f"\n200 x 20 iterations at 256^2 / 50 angles: iterate rel L2 {rx:.3e}, "
           f"energy rel error max {re.max():.3e}, last {re[-1]:.3e}")
-    assert rx <= 1e-4
+    assert rx <= 1e-5
     assert re.max() <= 1e-5
 
 
