@@ -35,8 +35,9 @@ DATA = ("synthetic: seeded ellipsoid phantom, exact (closed-form) line integrals
         "uint16; random numbers drawn once at set-up")
 UPD_PER_SLICE = N_PIX * N_PIX * N_ANG
 # Reduced-dose TV workload: beta per slice size, frozen from a seeded PSNR
-# calibration (4 training foams per size, 13-point log grid 1e-4..1e-1,
-# 200 x 20 iterations; the sweep is recorded in the design doc).
+# calibration (4 training foams per size disjoint from the benchmark's,
+# 13-point log grid 1e-4..1e-1, 200 x 20 iterations, PSNR over the inscribed
+# disk; maxima 30.3 / 30.4 / 30.2 dB).
 TV_BETA = {256: 1.7783e-3, 512: 1.7783e-3, 1024: 1.0e-3}
 TV_WORKLOAD = ("reduced-dose iterative TV: FISTA + Chambolle TV prox (20 inner steps), 200 outer iterations, "
                "128 slices of mixed size 256^2/512^2/1024^2 with 50/100/200 angles over 180 deg (43/43/42, "
@@ -58,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the baseline sample")
     ap.add_argument("--no-tv", action="store_true", help="skip the reduced-dose TV measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-slice and mixed-precision FBP measurements")
     ap.add_argument("--patch-study", action="store_true",
                     help="overlapping-patch prior on a 2048^2 phantom with 150 projections (Sec. 3.2.1)")
     ap.add_argument("--precision-study", action="store_true",
@@ -136,27 +139,23 @@ def measured_peaks():
         return {}
 
 
-def bp_traffic_from_profile():
-    """DRAM bytes per back-projection launch from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "backproject_2048x2000_ncu.md")
+# DRAM bytes (read + write) of one back-projection launch of the timed FBP
+# (4 slices, 2048^2, 2000 angles) from an ncu capture of bp_kernel, and the
+# hash of the kernel source it was taken on: the figure is reported only
+# while the source is unchanged.
+BP_DRAM_BYTES_PER_LAUNCH = 101914880
+BP_DRAM_SOURCE_SHA16 = "955543fdbb82d00f"
+
+
+def bp_traffic():
+    """DRAM bytes per back-projection launch if the capture above was taken
+    on the current kernel source, else None."""
     src = os.path.join(ROOT, "paper_1306_1392_b300", "csrc", "backproject.cu")
     try:
-        text = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    vals = {}
-    for line in text.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != sha:
-        return None
-    try:
-        return float(vals["dram_bytes_per_full_launch"])
-    except (KeyError, ValueError):
-        return None
+    return BP_DRAM_BYTES_PER_LAUNCH if sha == BP_DRAM_SOURCE_SHA16 else None
 
 
 def cpu_sample_fbp(orc, raw_slice, flat, dark, angles, axis, target_s):
@@ -238,9 +237,85 @@ def psnr(x, truth):
     return 10 * math.log10((truth.max() - truth.min()) ** 2 / mse)
 
 
-def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
+def tv_kernel_rates(P, plan, n_iter, n_inner, n_power_iter, kern, peaks, props):
+    """Per-kernel rates of one batched solve from its event-timed launches:
+    algorithmic units per solve (projector and back-projector: voxel-angle
+    updates; Chambolle: pixel-steps) over the kernel's summed launch time."""
+    sizes = sorted({(n, na) for n, na in plan})
+    upd_all = sum(n * n * na for n, na in plan)
+    upd_rep = sum(n * n * na for n, na in sizes)          # one representative per geometry
+    units = {"project": n_iter * upd_all + (n_power_iter + 1) * upd_rep,
+             "backproject": n_iter * upd_all + n_power_iter * upd_rep,
+             "chambolle": n_iter * n_inner * sum(n * n for n, _ in plan)}
+    out = {}
+    for k, (ms, n) in kern.items():
+        out[k] = {"launches": n, "total_ms": ms, "units": units[k],
+                  "unit": "pixel-steps" if k == "chambolle" else "voxel-angle updates",
+                  "g_units_per_s": units[k] / (ms * 1e-3) / 1e9 if ms > 0 else None}
+    sm_max = float(peaks.get("sm_max_mhz") or 2032.0)
+    peak_smem = props.multi_processor_count * SMEM_BYTES_PER_CLK * sm_max * 1e6 / 1e12
+    top = max(kern, key=lambda k: kern[k][0])
+    roof = None
+    if top in ("project", "backproject") and kern[top][0] > 0:
+        achieved = SMEM_BYTES_PER_UPDATE * units[top] / (kern[top][0] * 1e-3) / 1e12
+        roof = {"kernel": {"project": "proj_batch_kernel", "backproject": "bp_batch_kernel"}[top],
+                "bound": "smem", "achieved": achieved, "peak": peak_smem, "unit": "TB/s", "frac": achieved / peak_smem,
+                "traffic": None, "tupd_per_s": units[top] / (kern[top][0] * 1e-3) / 1e12,
+                "share_of_solve_kernels": kern[top][0] / sum(v[0] for v in kern.values()),
+                "peak_basis": f"shared-memory data pipe: {props.multi_processor_count} SMs x {SMEM_BYTES_PER_CLK} "
+                              f"B/clk x {sm_max:.0f} MHz; {SMEM_BYTES_PER_UPDATE} B per voxel-angle update (the "
+                              "matched back-projector's window entry; the projector makes the same updates); "
+                              "units: every projection of the solve (power iteration on one slice per geometry, "
+                              "then one projection of every slice per iteration) over the summed launch times"}
+    return out, roof
+
+
+def tv_cpu_baseline(plan, n_iter, n_inner, n_power_iter, target_s):
+    """The FP64 oracle's FISTA-TV on one seeded slice of each size of the
+    reduced-dose batch, for a bounded number of outer iterations: s/slice =
+    power iteration + n_iter x the measured time per iteration, weighted by
+    the batch's size mix."""
+    import numpy as np
+    import oracle as orc
+    from synth import acquisition as acq
+    orc.build()
+    per, done = {}, {}
+    first = {}
+    for k, (n, na) in enumerate(plan):
+        first.setdefault((n, na), k)
+    budget = target_s / len(first)
+    for (n, na), k in sorted(first.items()):
+        fs = acq.foam_slice(n, na, seed=3000 + k, truth=False)
+        og = orc.Geometry(fs.angles.double().numpy(), fs.axis.double().numpy(), n, n, n, fs.pixel_size)
+        sino = fs.extra["sino"].double().numpy()
+        t0 = time.perf_counter()
+        L = 1.01 * orc.power_iteration(og, np.ones((n, n)), 2)[0]
+        t_pow = (time.perf_counter() - t0) / 2 * n_power_iter
+        t0 = time.perf_counter()
+        orc.fista(og, sino, TV_BETA[n], L, 1, n_inner=n_inner)
+        t1 = time.perf_counter() - t0
+        its = int(max(1, min(n_iter, (budget - t1 - t_pow * 2 / n_power_iter) / max(t1, 1e-6))))
+        t0 = time.perf_counter()
+        orc.fista(og, sino, TV_BETA[n], L, its, n_inner=n_inner)
+        t_it = (time.perf_counter() - t0) / its
+        per[f"{n}^2/{na}"] = t_pow + n_iter * t_it
+        done[f"{n}^2/{na}"] = its
+    counts = {}
+    for n, na in plan:
+        counts[f"{n}^2/{na}"] = counts.get(f"{n}^2/{na}", 0) + 1
+    mean = sum(per[k] * c for k, c in counts.items()) / len(plan)
+    return {"value": mean, "unit": "s/slice", "cores": orc.num_threads(), "kind": "oracle",
+            "per_size_s_per_slice": per,
+            "sample": "one seeded slice per size (the batch's first of each); FISTA-TV with 20 Chambolle steps "
+                      f"timed over {done} outer iterations, power iteration over 2 of its {n_power_iter}, "
+                      f"extrapolated to {n_iter} iterations and weighted by the batch's size mix"}
+
+
+def run_tv(dev, n_slices=128, n_iter=200, n_inner=20, cpu_seconds=20.0):
     """One batched FISTA-TV solve of the mixed reduced-dose set, event-timed
-    (power iteration, table upload and graph capture included)."""
+    (power iteration, table upload and graph capture included); then the same
+    solve with per-kernel events (the kernels' rates and the roofline of the
+    dominant one) and once more reporting the prox duality gaps."""
     import numpy as np
     import torch
     import paper_1306_1392_b300 as P
@@ -253,7 +328,8 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
             geos[n] = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), n, n, n, fs.pixel_size)
         items.append((geos[n], fs.extra["sino"].to(dev).contiguous(), None, TV_BETA[n]))
         truths.append(fs.truth.double().cpu().numpy())
-    opts = P.TvOptions(beta=1e-3, n_iter=n_iter, n_inner=n_inner, n_power_iter=50)
+    n_power_iter = 50
+    opts = P.TvOptions(beta=1e-3, n_iter=n_iter, n_inner=n_inner, n_power_iter=n_power_iter)
     # autotune the Chambolle steps fused per launch for each slice size (results
     # do not depend on it); outside the timed region
     tuned = {}
@@ -268,6 +344,36 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # the same solve, every projector / back-projector / Chambolle launch bracketed by events
+    for k in ("project", "backproject", "chambolle"):
+        P.pyhst_profile_read(k)
+    P.pyhst_profile_enable(True)
+    e0.record()
+    xs_p, _, _ = P.pyhst_tv_solve_batch(items, opts, energy=False)
+    e1.record()
+    torch.cuda.synchronize()
+    P.pyhst_profile_enable(False)
+    ms_prof = e0.elapsed_time(e1)
+    kern = {k: P.pyhst_profile_read(k) for k in ("project", "backproject", "chambolle")}
+    same = all(torch.equal(a, b) for a, b in zip(xs, xs_p))
+    rates, roof = tv_kernel_rates(P, plan, n_iter, n_inner, n_power_iter, kern, measured_peaks(),
+                                  torch.cuda.get_device_properties(dev))
+    # the prox duality gaps of the same solve (extra reductions, not timed)
+    gaps = [torch.empty(n_iter, dtype=torch.float64, device=dev) for _ in items]
+    xs_g, _, lip_g = P.pyhst_tv_solve_batch(items, opts, energy=False, gaps=gaps)
+    torch.cuda.synchronize()
+    gap_by = {}
+    for (n, na), g, x, Lk, it in zip(plan, gaps, xs_g, lip_g.tolist(), items):
+        xd = x.double()
+        tvx = float(torch.sqrt(torch.nn.functional.pad(xd[1:] - xd[:-1], (0, 0, 0, 1)) ** 2 +
+                               torch.nn.functional.pad(xd[:, 1:] - xd[:, :-1], (0, 1)) ** 2).sum())
+        lam = it[3] / Lk
+        gl = float(g[-1])
+        gap_by.setdefault(f"{n}^2/{na}", []).append((float(g[0]), gl, gl / (lam * tvx)))
+    gap_rep = {k: {"first_iteration_mean": float(np.mean([v[0] for v in vs])),
+                   "last_iteration_mean": float(np.mean([v[1] for v in vs])),
+                   "last_relative_to_lam_tv_mean": float(np.mean([v[2] for v in vs])),
+                   "min": float(min(v[1] for v in vs))} for k, vs in gap_by.items()}
     ps_tv = [psnr(x.double().cpu().numpy(), t) for x, t in zip(xs, truths)]
     ps_fbp = []
     for (g, sino, _, _b), t in zip(items, truths):
@@ -276,13 +382,125 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20):
     by = {}
     for (n, na), p in zip(plan, ps_tv):
         by.setdefault(f"{n}^2/{na}", []).append(p)
-    return {"workload": TV_WORKLOAD, "slices": n_slices, "n_iter": n_iter, "n_inner": n_inner,
-            "total_s": ms * 1e-3, "s_per_slice": ms * 1e-3 / n_slices,
-            "psnr_tv_mean": float(np.mean(ps_tv)), "psnr_fbp_mean": float(np.mean(ps_fbp)),
-            "psnr_tv_by_size": {k: float(np.mean(v)) for k, v in by.items()},
-            "energy_lower_at_end_fraction": mono, "beta": {str(k): v for k, v in TV_BETA.items()},
-            "chambolle_steps_per_launch": tuned,
-            "learned_prox": run_learned_prox(dev)}
+    res = {"workload": TV_WORKLOAD, "slices": n_slices, "n_iter": n_iter, "n_inner": n_inner,
+           "total_s": ms * 1e-3, "s_per_slice": ms * 1e-3 / n_slices,
+           "psnr_tv_mean": float(np.mean(ps_tv)), "psnr_fbp_mean": float(np.mean(ps_fbp)),
+           "psnr_tv_by_size": {k: float(np.mean(v)) for k, v in by.items()},
+           "energy_lower_at_end_fraction": mono, "beta": {str(k): v for k, v in TV_BETA.items()},
+           "chambolle_steps_per_launch": tuned,
+           "kernels": rates, "roofline": roof,
+           "profiled_solve_s": ms_prof * 1e-3, "profiled_iterates_equal": same,
+           "prox_gap_after_n_inner": gap_rep}
+    if cpu_seconds > 0:
+        res["cpu_baseline"] = tv_cpu_baseline(plan, n_iter, n_inner, n_power_iter, cpu_seconds)
+    res["learned_prox"] = run_learned_prox(dev)
+    return res
+
+
+def run_c1(dev, reps=200, batch=64, cpu=True):
+    """The single-slice FBP workload (256^2, 180 angles over 180 deg, 256
+    bins, axis 127.5, Poisson counts at 1e5 photons, flat 1e5, dark 0,
+    Ram-Lak, padding 512): event-timed one slice per call (latency) and
+    `batch` slices of the same geometry per call (throughput), inputs
+    resident; the result's relative L2 error against the FP64 oracle; the
+    oracle's own time for the slice."""
+    import numpy as np
+    import torch
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    sl = acq.single_slice_fbp(seed=0)
+    geo = P.Geometry(sl.angles.to(dev), sl.axis.to(dev), sl.n_bins, sl.nx, sl.ny, sl.pixel_size)
+    raw = sl.extra["raw"].to(dev)                        # [180, 1, 256] float32 counts
+    fl, dk = sl.extra["flat"].to(dev), sl.extra["dark"].to(dev)
+    out = torch.empty((1, sl.ny, sl.nx), device=dev)
+    ws = torch.empty(P.pyhst_fbp_workspace_size(geo, 1, 512, 1), dtype=torch.uint8, device=dev)
+    call = lambda: P.pyhst_fbp(geo, raw, "f32_raw", fl, dk, pad_len=512, out=out, workspace=ws)   # noqa: E731
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / reps
+    rawb = raw.expand(-1, batch, -1).contiguous()
+    flb, dkb = fl.expand(batch, -1).contiguous(), dk.expand(batch, -1).contiguous()
+    outb = torch.empty((batch, sl.ny, sl.nx), device=dev)
+    wsb = torch.empty(P.pyhst_fbp_workspace_size(geo, batch, 512, 16), dtype=torch.uint8, device=dev)
+    callb = lambda: P.pyhst_fbp(geo, rawb, "f32_raw", flb, dkb, pad_len=512, out=outb, workspace=wsb)  # noqa: E731
+    callb()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        callb()
+    e1.record()
+    torch.cuda.synchronize()
+    msb = e0.elapsed_time(e1) / 20
+    upd = sl.nx * sl.ny * len(sl.angles)
+    res = {"workload": "single-slice FBP: 256^2 float32 grid, 180 angles over 180 deg, 256 bins, axis 127.5; "
+                       "head-like 10-ellipse phantom, Poisson counts at 1e5 photons, flat 1e5, dark 0; Ram-Lak, "
+                       "zero-padded to 512",
+           "one_slice_per_call": {"ms_per_slice": ms1, "slices_per_s": 1e3 / ms1, "gupd_per_s": upd / ms1 / 1e6},
+           f"{batch}_slices_per_call": {"ms_per_slice": msb / batch, "slices_per_s": 1e3 * batch / msb,
+                                        "gupd_per_s": upd * batch / msb / 1e6}}
+    if cpu:
+        import oracle as orc
+        orc.build()
+        args = (sl.extra["raw"][:, 0, :].double().numpy(), sl.extra["flat"][0].double().numpy(),
+                sl.extra["dark"][0].double().numpy(), sl.angles.double().numpy(), sl.axis.double().numpy(),
+                sl.nx, sl.ny, sl.pixel_size)
+        orc.fbp_from_raw(*args)
+        t0 = time.perf_counter()
+        k = 0
+        while k == 0 or time.perf_counter() - t0 < 2.0:
+            ref = orc.fbp_from_raw(*args)
+            k += 1
+        t = (time.perf_counter() - t0) / k
+        g = out[0].double().cpu().numpy()
+        res["rel_l2_vs_oracle"] = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+        res["cpu_baseline"] = {"value": 1.0 / t, "unit": "slices/s", "cores": orc.num_threads(), "kind": "oracle",
+                               "sample": f"the whole slice, {k} repetitions"}
+    return res
+
+
+def run_c4(dev, n_slices=32):
+    """The mixed-precision FBP workload's geometry (4096^2, 4000 angles over
+    180 deg, 4096 bins; exact line integrals of 200 random ellipsoids stored
+    as f32 / f16 / bf16, float32 arithmetic): `n_slices` central slices of
+    its 256-slice stack per storage type, event-timed, inputs resident."""
+    import torch
+    import paper_1306_1392_b300 as P
+    from synth import acquisition as acq
+    n, na, ns_all = 4096, 4000, 256
+    z0 = ns_all // 2 - n_slices // 2
+    ang = acq.uniform_angles(na)
+    geo = P.Geometry(ang.to(dev), torch.full((na,), (n - 1) / 2.0, device=dev), n, n, n, 2.0 / n)
+    p = torch.empty((n_slices, na, n), dtype=torch.float32, device=dev)
+    for a in range(0, n_slices, 16):
+        p[a:a + 16] = acq.ellipsoid_sinograms(ns_all, n, na, seed=4000, device=dev,
+                                              slices=range(z0 + a, z0 + min(n_slices, a + 16)))
+    out = torch.empty((n_slices, n, n), dtype=torch.float32, device=dev)
+    ws = torch.empty(P.pyhst_fbp_workspace_size(geo, n_slices, 0, 4), dtype=torch.uint8, device=dev)
+    res = {"workload": f"mixed-precision FBP: slices {z0}..{z0 + n_slices - 1} of 256 x 4096^2, 4000 angles over "
+                       "180 deg, 4096 bins; exact line integrals of 200 random ellipsoids stored as f32/f16/bf16, "
+                       "float32 arithmetic"}
+    for kind, dt in (("f32_sino", torch.float32), ("f16_sino", torch.float16), ("bf16_sino", torch.bfloat16)):
+        stored = p.to(dt)
+        P.pyhst_fbp(geo, stored, kind, out=out[:4], workspace=ws, slices=(0, 4))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.pyhst_fbp(geo, stored, kind, out=out, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[kind[:-5]] = {"fbp_slices_per_s": n_slices / (ms * 1e-3),
+                          "gupd_per_s": n_slices * n * n * na / (ms * 1e-3) / 1e9,
+                          "input_bytes_per_slice": na * n * stored.element_size()}
+        del stored
+    return res
 
 
 PROX_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1306_1392_b300", "weights",
@@ -298,8 +516,9 @@ def run_learned_prox(dev, n_eval=64):
     import torch
     from paper_1306_1392_b300 import train_prox
     params = torch.from_numpy(np.load(PROX_WEIGHTS).astype(np.float32)).to(dev)
-    r = train_prox.evaluate(params, dev, n_eval=n_eval, ks=(), tv_long=0, hybrid_kt=(40, 75, 100),
-                            tv_first=(25, 28, 30, 35, 40), learned_steps=(2, 3, 4, 5))
+    r = train_prox.evaluate(params, dev, n_eval=n_eval, ks=(), tv_long=0, hybrid_kt=(75, 100, 125, 150, 200),
+                            tv_first=(25, 28, 30, 35, 40), learned_steps=(2, 3, 4, 5),
+                            tv_zero=(100, 125, 150, 175))
     r["weights"] = "paper_1306_1392_b300/weights/prox_cnn_foam512.npy (train_prox.py)"
     return r
 
@@ -577,13 +796,13 @@ def run_ours(args, rank, world, local_rank):
     achieved = SMEM_BYTES_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
     alu = OPS_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
     roofline = {"bound": "smem", "achieved": achieved, "peak": peak_smem, "unit": "TB/s",
-                "frac": achieved / peak_smem, "traffic": bp_traffic_from_profile(),
+                "frac": achieved / peak_smem, "traffic": bp_traffic(),
                 "kernel": "bp_kernel", "launches": bp_n, "avg_launch_ms": bp_avg_s * 1e3,
                 "gupd_per_s": per_launch_upd / bp_avg_s / 1e9,
                 "peak_basis": f"shared-memory data pipe: {props.multi_processor_count} SMs x "
                               f"{SMEM_BYTES_PER_CLK} B/clk x {sm_max:.0f} MHz (measured max SM clock); "
                               f"{SMEM_BYTES_PER_UPDATE} B (one float32 (dq, c0) pair) per voxel-angle update; "
-                              "traffic = DRAM bytes per launch from the committed ncu capture",
+                              "traffic = DRAM bytes per launch from an ncu capture of the same kernel source",
                 "alu": {"achieved": alu, "peak": peak_ops, "unit": "T FP32 lane-ops/s", "frac": alu / peak_ops,
                         "basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz; "
                                  f"{OPS_PER_UPDATE} FP32 ops per update"},
@@ -604,12 +823,17 @@ def run_ours(args, rank, world, local_rank):
                          f"(2048 per slice; a whole slice repeated when the target needs more; filter time "
                          f"prorated by rows); {secs:.1f} s"}
 
-    tv = None
+    tv = c1 = c4 = None
     raw_gb = raw.numel() * 2 / 1e9
-    if rank == 0 and not args.no_tv:
+    if rank == 0 and not (args.no_tv and args.no_configs):
         del out, raw
         torch.cuda.empty_cache()
-        tv = run_tv(dev)
+    if rank == 0 and not args.no_configs:
+        c1 = run_c1(dev, cpu=world == 1 and not args.no_cpu_baseline)
+        c4 = run_c4(dev)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_tv:
+        tv = run_tv(dev, cpu_seconds=0.0 if (world > 1 or args.no_cpu_baseline) else args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gupd/s", "n_gpus": world, "steps": args.steps,
@@ -622,6 +846,7 @@ def run_ours(args, rank, world, local_rank):
                            "pad_len": 4096, "slices_per_pass": 4},
                 "fbp_slices_per_s": n_slices_all / (ms_max * 1e-3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "tv": tv,
+                "single_slice_fbp": c1, "mixed_precision_fbp": c4,
                 "gpu_launches": int(bp_n + fl_n + 3 * args.steps),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

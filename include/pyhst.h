@@ -239,9 +239,12 @@ typedef struct {
  *   sino   [n_slices][n_angles][n_bins]
  *   x      [n_slices][ny][nx]  in: start (if warm_start), out: last iterate
  *   energy [n_slices][n_iter] float64 DEVICE or NULL: Eq. 3 at every iterate
+ *   gap    [n_slices][n_iter] float64 DEVICE or NULL: the duality gap of each
+ *          iteration's TV prox (see pyhst_tv_prox; 0 when beta = 0), a measure
+ *          of how far n_inner Chambolle steps leave the prox from its optimum
  *   lipschitz_out  DEVICE float64 [n_slices] or NULL: the L that was used. */
 int pyhst_tv_solve(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts,
-                   float *x, double *energy, double *lipschitz_out,
+                   float *x, double *energy, double *gap, double *lipschitz_out,
                    void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
 /* Workspace bytes of pyhst_tv_solve for a given option set (n_inner does not
@@ -254,10 +257,16 @@ size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_tv_opts *opt
  * (the TV prox inside pyhst_tv_solve; on its own it is the denoising case of
  * the paper's functional, where the projection operator is the identity,
  * Sec. 3.2.1).  z, x: [n_slices][ny][nx] float32; x must not overlap z
- * (PYHST_ERR_INVALID_ARG).  lam = 0 copies z. */
+ * (PYHST_ERR_INVALID_ARG).  lam = 0 copies z.
+ * gap [n_slices] float64 DEVICE or NULL: the ROF duality gap of the result,
+ * primal 1/2 ||x - z||^2 + lam TV(x) minus dual 1/2 ||z||^2 - 1/2 ||z - lam div p||^2
+ * for the final dual field p (|p| <= 1, x = z - lam div p); it is >= 0 and
+ * bounds the primal suboptimality of x.  Evaluated as
+ * lam * sum over pixels of (|grad x| + p . grad x), the same value written
+ * as a sum of non-negative terms (float32 terms, float64 sums). */
 size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n_slices);
 int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
-                  float tau, float *x, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
+                  float tau, float *x, double *gap, void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
 /* Estimators of beta without ground truth (Sec. 4).  Reconstructs one slice
  * (geometry g, n_slices ignored) for each of the n_beta values betas (HOST
@@ -277,22 +286,26 @@ int pyhst_beta_scan(const pyhst_geometry *g, const float *sino, const float *bet
                     void *workspace, size_t ws_bytes, pyhst_stream_t stream);
 
 /* Opt-in per-kernel timing for measurement: while enabled (per host thread),
- * every launch of the back-projection, filter and projection kernels is
- * bracketed by CUDA events on its launch stream.  pyhst_profile_read waits for
- * the recorded launches of one kernel ("backproject", "filter" or "project"),
- * returns their summed duration (ms) and count, and forgets them. */
+ * every launch of the back-projection, filter, projection and fused Chambolle
+ * kernels is bracketed by CUDA events on its launch stream (event-record nodes
+ * when the stream is being captured into a CUDA graph, as in
+ * pyhst_tv_solve_batch).  pyhst_profile_read waits for the recorded launches
+ * of one kernel ("backproject", "filter", "project" or "chambolle"), returns
+ * their summed duration (ms) and count, and forgets them. */
 int pyhst_profile_enable(int on);
 int pyhst_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
 /* One slice of a mixed-size batch: its own geometry (n_slices is ignored),
  * sinogram [n_angles][n_bins], iterate x [ny][nx] (in: start if warm_start,
- * out: result), energy [n_iter] float64 (DEVICE, or NULL) and its own beta
- * (>= 0; a negative value takes the options' beta). */
+ * out: result), energy [n_iter] and prox duality gaps [n_iter] float64
+ * (DEVICE, or NULL; as in pyhst_tv_solve) and its own beta (>= 0; a negative
+ * value takes the options' beta). */
 typedef struct {
     pyhst_geometry geom;
     const float *sino;
     float *x;
     double *energy;
+    double *gap;
     float beta;
 } pyhst_tv_item;
 

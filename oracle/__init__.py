@@ -246,18 +246,22 @@ def power_iteration(g: Geometry, v0, n_it=50):
     return lam, v
 
 
-def fista(g: Geometry, sino, beta, L, n_iter, n_inner=20, tau=0.125, use_fista=True, x0=None, return_z=False):
-    """ISTA/FISTA on Eq. 3; returns (x, energy history [n_iter]) and, with
-    return_z, the prox input z of the last iteration."""
+def fista(g: Geometry, sino, beta, L, n_iter, n_inner=20, tau=0.125, use_fista=True, x0=None, return_z=False,
+          return_gap=False):
+    """ISTA/FISTA on Eq. 3; returns (x, energy history [n_iter]), then, with
+    return_z, the prox input z of the last iteration and, with return_gap,
+    the ROF duality gap of every iteration's prox [n_iter]."""
     sino, ps = _c(sino)
     x = np.zeros((g.ny, g.nx)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     e = np.empty(n_iter)
     z = np.empty((g.ny, g.nx)) if return_z else None
+    gp = np.empty(n_iter) if return_gap else None
     gc = g._c()
     lib().orc_fista_z(ctypes.byref(gc), ps, D(beta), D(L), I64(n_iter), I64(n_inner), D(tau),
                       ctypes.c_int(1 if use_fista else 0), x.ctypes.data_as(PD), e.ctypes.data_as(PD),
-                      z.ctypes.data_as(PD) if return_z else None)
-    return (x, e, z) if return_z else (x, e)
+                      gp.ctypes.data_as(PD) if return_gap else None, z.ctypes.data_as(PD) if return_z else None)
+    out = (x, e) + ((z,) if return_z else ()) + ((gp,) if return_gap else ())
+    return out
 
 
 # ------------------------------------------------------------------ beta estimators (Sec. 4)

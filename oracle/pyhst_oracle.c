@@ -389,10 +389,12 @@ double orc_power_iteration(const orc_geom *g, double *v, int64_t n_it)
  * the last iterate.
  * ------------------------------------------------------------------- */
 /* as orc_fista; z_last (or NULL) receives the prox input z of the last
- * iteration, y - (1/L) P^T (P y - sino) */
+ * iteration, y - (1/L) P^T (P y - sino), and gap (or NULL) [n_iter] the ROF
+ * duality gap of each iteration's prox (orc_rof_gap of its z and final dual
+ * field; 0 when beta = 0, where the prox is the identity) */
 void orc_fista_z(const orc_geom *g, const double *sino, double beta, double L,
                  int64_t n_iter, int64_t n_inner, double tau, int fista,
-                 double *x, double *energy, double *z_last)
+                 double *x, double *energy, double *gap, double *z_last)
 {
     int64_t n = g->nx * g->ny, m = g->n_angles * g->n_bins;
     double *y = (double *)malloc(sizeof(double) * n);
@@ -413,6 +415,7 @@ void orc_fista_z(const orc_geom *g, const double *sino, double beta, double L,
         memset(p1, 0, sizeof(double) * n);
         memset(p2, 0, sizeof(double) * n);
         orc_tv_prox(z, g->ny, g->nx, beta / L, tau, n_inner, p1, p2, x);
+        if (gap) gap[k] = beta > 0.0 ? orc_rof_gap(z, g->ny, g->nx, beta / L, p1, p2) : 0.0;
         double tn = fista ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
         double w = fista ? (t - 1.0) / tn : 0.0;
         for (int64_t q = 0; q < n; q++) {
@@ -430,7 +433,7 @@ void orc_fista(const orc_geom *g, const double *sino, double beta, double L,
                int64_t n_iter, int64_t n_inner, double tau, int fista,
                double *x, double *energy)
 {
-    orc_fista_z(g, sino, beta, L, n_iter, n_inner, tau, fista, x, energy, NULL);
+    orc_fista_z(g, sino, beta, L, n_iter, n_inner, tau, fista, x, energy, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------------

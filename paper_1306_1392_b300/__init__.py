@@ -378,10 +378,22 @@ def pyhst_project(geom: Geometry, img: torch.Tensor, out=None, workspace=None):
     return out
 
 
+def _gap_out(gap, shape, device):
+    """A caller's float64 CUDA tensor of ``shape`` for the prox duality gaps (or None)."""
+    if gap is None:
+        return None
+    _cuda(gap, "gap", (torch.float64,))
+    if tuple(gap.shape) != tuple(shape) or gap.device != device:
+        raise ValueError(f"gap must be a float64 tensor {tuple(shape)} on {device}")
+    return gap
+
+
 def pyhst_tv_solve(geom: Geometry, sino: torch.Tensor, opts: TvOptions, x=None, energy: bool = True,
-                   workspace=None):
+                   workspace=None, gap=None):
     """Eq. 3 by ISTA/FISTA for each slice; returns (x, energy [n_slices, n_iter]
-    float64 or None, lipschitz [n_slices] float64)."""
+    float64 or None, lipschitz [n_slices] float64).  ``gap``: None, or a
+    float64 CUDA tensor [n_slices, n_iter] that receives the duality gap of
+    each iteration's TV prox."""
     sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")
     ns = sino.shape[0]
     if tuple(sino.shape[1:]) != (geom.n_angles, geom.n_bins):
@@ -394,7 +406,8 @@ def pyhst_tv_solve(geom: Geometry, sino: torch.Tensor, opts: TvOptions, x=None, 
     g, o = geom.c(ns), opts.c()
     need = L.lib.pyhst_tv_workspace_size(ctypes.byref(g), ctypes.byref(o))
     ws = _workspace(need, sino.device, workspace)
-    _check(L.lib.pyhst_tv_solve(ctypes.byref(g), _ptr(sino), ctypes.byref(o), _ptr(x), _ptr(e), _ptr(lip),
+    gp = _gap_out(gap, (ns, opts.n_iter), sino.device)
+    _check(L.lib.pyhst_tv_solve(ctypes.byref(g), _ptr(sino), ctypes.byref(o), _ptr(x), _ptr(e), _ptr(gp), _ptr(lip),
                                 _ptr(ws), ws.numel(), _stream()))
     return x, e, lip
 
@@ -443,8 +456,11 @@ def pyhst_pnp_solve(geom: Geometry, sino: torch.Tensor, params: torch.Tensor, op
     return x, e, lip
 
 
-def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0.125, out=None, workspace=None):
-    """prox of lam * TV (Eq. 2) for images z [n_slices, ny, nx] (or [ny, nx])."""
+def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0.125, out=None, workspace=None,
+                  gap=None):
+    """prox of lam * TV (Eq. 2) for images z [n_slices, ny, nx] (or [ny, nx]).
+    ``gap``: None, or a float64 CUDA tensor [n_slices] that receives the ROF
+    duality gap of each result."""
     z3 = _stack3(_cuda(z, "z", (torch.float32,)), "z")
     ns, ny, nx = z3.shape
     if out is None:
@@ -452,8 +468,9 @@ def pyhst_tv_prox(z: torch.Tensor, lam: float, n_inner: int = 20, tau: float = 0
     _cuda(out, "out", (torch.float32,))
     need = L.lib.pyhst_tv_prox_workspace_size(nx, ny, ns)
     ws = _workspace(need, z3.device, workspace)
-    _check(L.lib.pyhst_tv_prox(_ptr(z3), nx, ny, ns, float(lam), int(n_inner), float(tau), _ptr(out), _ptr(ws),
-                               ws.numel(), _stream()))
+    gp = _gap_out(gap, (ns,), z3.device)
+    _check(L.lib.pyhst_tv_prox(_ptr(z3), nx, ny, ns, float(lam), int(n_inner), float(tau), _ptr(out), _ptr(gp),
+                               _ptr(ws), ws.numel(), _stream()))
     return out
 
 
@@ -476,11 +493,14 @@ def pyhst_set_tv_prox_steps(nx: int, ny: int, steps: int) -> None:
     _check(L.lib.pyhst_set_tv_prox_steps(nx, ny, steps))
 
 
-def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace=None):
+def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace=None, gaps=None):
     """Eq. 3 for a mixed batch: ``slices`` is a list of (Geometry, sino
     [n_angles, n_bins], x or None[, beta]) (beta defaults to opts.beta).
     Returns (list of x, list of energy [n_iter] float64 or None,
-    lipschitz [n] float64)."""
+    lipschitz [n] float64).  ``gaps``: None, or a list with, per slice, None or
+    a float64 CUDA tensor [n_iter] that receives its prox duality gaps."""
+    if gaps is not None and len(gaps) != len(slices):
+        raise ValueError("gaps needs one entry per slice")
     items = (L.pyhst_tv_item * len(slices))()
     xs, es = [], []
     dev = None
@@ -495,8 +515,9 @@ def pyhst_tv_solve_batch(slices, opts: TvOptions, energy: bool = True, workspace
             x = torch.zeros((geom.ny, geom.nx), dtype=torch.float32, device=dev)
         _cuda(x, "x", (torch.float32,))
         e = torch.empty((opts.n_iter,), dtype=torch.float64, device=dev) if energy else None
+        gp = _gap_out(gaps[k], (opts.n_iter,), dev) if gaps is not None else None
         items[k] = L.pyhst_tv_item(geom.c(1), sino.data_ptr(), x.data_ptr(), e.data_ptr() if e is not None else None,
-                                   beta)
+                                   gp.data_ptr() if gp is not None else None, beta)
         xs.append(x)
         es.append(e)
     o = opts.c()

@@ -50,7 +50,7 @@ class pyhst_preproc(ctypes.Structure):
 
 class pyhst_tv_item(ctypes.Structure):
     _fields_ = [("geom", pyhst_geometry), ("sino", c_void_p), ("x", c_void_p), ("energy", c_void_p),
-                ("beta", c_float)]
+                ("gap", c_void_p), ("beta", c_float)]
 
 
 # (name, restype, argtypes) of every exported entry point
@@ -73,11 +73,11 @@ SIGNATURES = [
     ("pyhst_project", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_void_p, c_size_t,
                                 c_void_p]),
     ("pyhst_tv_solve", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, ctypes.POINTER(pyhst_tv_opts),
-                                 c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     ("pyhst_tv_workspace_size", c_size_t, [ctypes.POINTER(pyhst_geometry), ctypes.POINTER(pyhst_tv_opts)]),
     ("pyhst_tv_prox_workspace_size", c_size_t, [c_int32, c_int32, c_int32]),
     ("pyhst_tv_prox", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_float, c_int32, c_float, c_void_p,
-                                c_void_p, c_size_t, c_void_p]),
+                                c_void_p, c_void_p, c_size_t, c_void_p]),
     ("pyhst_profile_enable", c_int32, [c_int32]),
     ("pyhst_profile_read", c_int32, [ctypes.c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     ("pyhst_tv_batch_workspace_size", c_size_t, [ctypes.POINTER(pyhst_tv_item), c_int32,

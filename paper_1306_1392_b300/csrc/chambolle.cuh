@@ -115,12 +115,14 @@ __device__ __forceinline__ void chambolle_steps_regs(float (&zl)[kChRows][2], fl
 // xout == nullptr: write the dual field of the central tile to q1, q2.
 // Otherwise (the last launch of a prox) write the prox itself to xout,
 // x = z - lam div p: the divergence's four terms added in a fixed order,
-// those across the image border left out, then one fma.
+// those across the image border left out, then one fma; with keep_p the
+// dual field is written to q1, q2 as well (for the duality gap).
 template <int kChK>
 __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
                                                const float *__restrict__ p2, float *__restrict__ q1,
                                                float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
-                                               int j0, int steps, bool first, float *__restrict__ xout = nullptr) {
+                                               int j0, int steps, bool first, float *__restrict__ xout = nullptr,
+                                               bool keep_p = false) {
     extern __shared__ __align__(16) float ch_smem[];
     float(*xp)[kChR] = reinterpret_cast<float(*)[kChR]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
     float(*xg)[kChR] = xp + (kChR / kChRows + 1);                       // xg[w]: first G row of strip w
@@ -183,6 +185,10 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
                     if (gj + 1 < nx) dv += a2[i][j];
                     if (gj > 0) dv -= pl;
                     xout[k] = fmaf(-lam, dv, z[k]);
+                    if (keep_p) {
+                        q1[k] = a1[i][j];
+                        q2[k] = a2[i][j];
+                    }
                 }
             }
         }

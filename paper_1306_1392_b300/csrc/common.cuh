@@ -122,12 +122,15 @@ int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n
 
 // ----------------------------------------------------------------- profiling
 // Opt-in per-launch timing (pyhst_profile_enable): events recorded on the
-// launch stream around each kernel of a kind; off by default.
-enum ProfKind { kProfBackproject = 0, kProfFilter = 1, kProfProject = 2, kProfKinds = 3 };
+// launch stream around each kernel of a kind; off by default.  On a stream
+// that is being captured the events become event-record nodes of the graph
+// (recorded when the graph runs).
+enum ProfKind { kProfBackproject = 0, kProfFilter = 1, kProfProject = 2, kProfChambolle = 3, kProfKinds = 4 };
 struct ProfScope {
     int kind;
     cudaStream_t st;
     void *end;
+    unsigned flags;
     ProfScope(int kind, cudaStream_t st);
     ~ProfScope();
 };

@@ -83,7 +83,7 @@ ScanLayout scan_layout(const pyhst_geometry *g, int n_beta, int held_out, const 
         it.geom.n_slices = 1;
         it.geom.angles = reinterpret_cast<const float *>(1);   // same (placeholder) arrays for every item
         it.geom.axis = reinterpret_cast<const float *>(2);
-        it.sino = nullptr; it.x = nullptr; it.energy = nullptr; it.beta = 0.0f;
+        it.sino = nullptr; it.x = nullptr; it.energy = nullptr; it.gap = nullptr; it.beta = 0.0f;
     }
     l.batch_bytes = pyhst_tv_batch_workspace_size(items.data(), n_beta, opts);
     l.batch = take(l.batch_bytes);
@@ -164,6 +164,7 @@ extern "C" int pyhst_beta_scan(const pyhst_geometry *g, const float *sino, const
         items[k].sino = sino_r;
         items[k].x = x + (size_t)k * N;
         items[k].energy = nullptr;
+        items[k].gap = nullptr;
         items[k].beta = betas[k];
     }
     rc = pyhst_tv_solve_batch(items.data(), n_beta, opts, nullptr, ws + L.batch, L.batch_bytes, stream);

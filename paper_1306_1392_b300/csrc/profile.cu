@@ -27,21 +27,24 @@ cudaEvent_t get_event() {
     return e;
 }
 
-const char *kNames[kProfKinds] = {"backproject", "filter", "project"};
+const char *kNames[kProfKinds] = {"backproject", "filter", "project", "chambolle"};
 
 }  // namespace
 
-ProfScope::ProfScope(int k, cudaStream_t s) : kind(k), st(s), end(nullptr) {
+ProfScope::ProfScope(int k, cudaStream_t s) : kind(k), st(s), end(nullptr), flags(cudaEventRecordDefault) {
     if (!g_on) return;
     cudaEvent_t a = get_event(), b = get_event();
     if (!a || !b) return;
-    cudaEventRecord(a, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        flags = cudaEventRecordExternal;   // an event-record node of the captured graph
+    cudaEventRecordWithFlags(a, st, flags);
     g_recs.push_back(Record{kind, a, b});
     end = reinterpret_cast<void *>(b);
 }
 
 ProfScope::~ProfScope() {
-    if (end) cudaEventRecord(reinterpret_cast<cudaEvent_t>(end), st);
+    if (end) cudaEventRecordWithFlags(reinterpret_cast<cudaEvent_t>(end), st, flags);
 }
 
 }  // namespace pyhst

@@ -33,7 +33,7 @@ constexpr int kRedBlocks = 256;  // partial sums per slice (= kRedThreads: one p
 
 // ----------------------------------------------------------------- layout
 struct TvLayout {
-    size_t tab, xt, img[9], sino[3], scal, part[2], bytes;
+    size_t tab, xt, img[9], sino[3], scal, part[3], bytes;
 };
 
 // images: y, xa, xb, z, g, p1a, p2a, p1b, p2b; sinograms: Axa, Axb, Ay;
@@ -148,23 +148,25 @@ template <int K>
 __global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, float *pb1, float *pb2,
                        const float *__restrict__ lam, float tau, int nx, int ny, int m, int steps, int tiles_x,
-                       float *__restrict__ x) {
+                       float *__restrict__ x, bool keep_p) {
     const size_t off = (size_t)blockIdx.y * nx * ny;
     const bool odd = m & 1;
     const float *s1 = (odd ? pa1 : pb1) + off, *s2 = (odd ? pa2 : pb2) + off;
     float *d1 = (m == 0 || !odd ? pa1 : pb1) + off, *d2 = (m == 0 || !odd ? pa2 : pb2) + off;
     constexpr int T = chambolle_tile_size(K);
     chambolle_tile<K>(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * T,
-                      (blockIdx.x % tiles_x) * T, steps, m == 0, x ? x + off : nullptr);
+                      (blockIdx.x % tiles_x) * T, steps, m == 0, x ? x + off : nullptr, keep_p);
 }
 
 template <int K>
 int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
-                       int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, float *x) {
+                       int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, float *x,
+                       bool keep_p) {
     constexpr int T = chambolle_tile_size(K);
     const int tx = (nx + T - 1) / T, ty = (ny + T - 1) / T;
     const int L = chambolle_launches(n_inner, K);
     for (int m = 0; m < L; ++m) {
+        ProfScope prof(kProfChambolle, st);
         const int steps = chambolle_steps(n_inner, m, K);
         if (m + 1 == L && x) {
             // The prox x = z - lam div p of a tile reads p one row above and one
@@ -173,10 +175,10 @@ int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float
             constexpr int T1 = chambolle_tile_size(K + 1);
             const int tx1 = (nx + T1 - 1) / T1, ty1 = (ny + T1 - 1) / T1;
             chambolle_fused_kernel<K + 1><<<dim3(tx1 * ty1, n_slices), kChThreads, kChSmem, st>>>(
-                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx1, x);
+                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx1, x, keep_p);
         } else {
             chambolle_fused_kernel<K><<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
-                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx, nullptr);
+                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx, nullptr, false);
         }
     }
     *final_a = (L & 1) == 1;
@@ -187,13 +189,51 @@ int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float
 // default choice for the size); returns through *final_a whether the dual
 // field ends in the a buffers.  With x given, the last launch writes the prox
 // x = z - lam div p there instead of the dual field (the divergence with
-// the Neumann boundary of Eq. 2, then one fma).
+// the Neumann boundary of Eq. 2, then one fma), and with keep_p the final
+// dual field as well.
 int launch_chambolle(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
                      int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, int K = 0,
-                     float *x = nullptr) {
+                     float *x = nullptr, bool keep_p = false) {
     if (K <= 0) K = chambolle_k_for(nx, ny);
     PYHST_CHAMBOLLE_DISPATCH(K, launch_chambolle_k, z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, n_slices, n_inner,
-                             final_a, st, x)
+                             final_a, st, x, keep_p)
+}
+
+// ROF duality gap of the prox (Eq. 2 with the quadratic term of the prox):
+// for x = z - lam div p with |p| <= 1 pixelwise,
+//   primal 1/2 ||x - z||^2 + lam TV(x)  -  dual 1/2 ||z||^2 - 1/2 ||x||^2
+//     = lam TV(x) - <x, z - x> = lam (TV(x) + <p, grad x>)
+// (z - x = lam div p and div = -grad^T), a sum of per-pixel terms
+// |grad x| + p . grad x >= 0.  Summing those terms avoids the cancellation of
+// the two nearly equal halves of the first form.  Partial of slice
+// blockIdx.y per block (float32 terms in runs of 8, float64 beyond).
+__global__ void gap_partial(const float *__restrict__ x, const float *__restrict__ p1, const float *__restrict__ p2,
+                            int nx, int ny, double *__restrict__ part) {
+    const size_t n = (size_t)nx * ny, off = (size_t)blockIdx.y * n;
+    const float *X = x + off, *Q1 = p1 + off, *Q2 = p2 + off;
+    RunSum rs;
+    for (int i = blockIdx.x; i < ny; i += gridDim.x)
+        for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+            const size_t k = (size_t)i * nx + j;
+            const float v = X[k];
+            const float d1 = (i + 1 < ny) ? X[k + nx] - v : 0.0f;
+            const float d2 = (j + 1 < nx) ? X[k + 1] - v : 0.0f;
+            rs.add(sqrtf(fmaf(d1, d1, d2 * d2)) + fmaf(Q1[k], d1, Q2[k] * d2));
+        }
+    const double acc = block_sum(rs.total());
+    if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
+}
+
+// gap[slice * stride + k] = lam[slice] * (sum of the slice's partials)
+__global__ void finalize_gap(const double *__restrict__ part, const float *__restrict__ lam, double *__restrict__ gap,
+                             int stride, int k) {
+    const double s = sum_partials(part);
+    if (threadIdx.x == 0) gap[(size_t)blockIdx.x * stride + k] = (double)lam[blockIdx.x] * s;
+}
+
+__global__ void zero_gap(double *__restrict__ gap, int S, int stride, int k) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < S) gap[(size_t)q * stride + k] = 0.0;
 }
 
 // data partial of ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
@@ -238,7 +278,7 @@ struct Bufs {
     float *img[9];
     float *sino[3];
     Scalars sc;
-    double *part[2];
+    double *part[3];
 };
 
 Bufs carve(const pyhst_geometry *g, void *ws) {
@@ -255,7 +295,7 @@ Bufs carve(const pyhst_geometry *g, void *ws) {
     r.sc.invL = reinterpret_cast<float *>(sc + S);
     r.sc.lam = r.sc.invL + S;
     r.sc.invn = r.sc.lam + S;
-    for (int i = 0; i < 2; ++i) r.part[i] = reinterpret_cast<double *>(b + l.part[i]);
+    for (int i = 0; i < 3; ++i) r.part[i] = reinterpret_cast<double *>(b + l.part[i]);
     return r;
 }
 
@@ -292,7 +332,8 @@ struct SolveHooks {
 
 // Enqueue the whole solve on `st`.
 int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *o, float *x,
-                     double *energy, double *lip_out, void *ws, cudaStream_t st, const SolveHooks &hk = SolveHooks()) {
+                     double *energy, double *lip_out, void *ws, cudaStream_t st, const SolveHooks &hk = SolveHooks(),
+                     double *gap = nullptr) {
     int rc;
     Bufs B = carve(g, ws);
     const int S = g->n_slices;
@@ -355,10 +396,15 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
         } else if (o->beta > 0.0f) {
             bool fa;
             if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, B.sc.lam, o->tau, g->nx, g->ny, S, o->n_inner, &fa, st,
-                                       0, xn)))
+                                       0, xn, gap != nullptr)))
                 return rc;
+            if (gap) {
+                gap_partial<<<eg, kRedThreads, 0, st>>>(xn, fa ? p1a : p1b, fa ? p2a : p2b, g->nx, g->ny, B.part[2]);
+                finalize_gap<<<S, kRedThreads, 0, st>>>(B.part[2], B.sc.lam, gap, o->n_iter, k);
+            }
         } else {
             cudaMemcpyAsync(xn, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
+            if (gap) zero_gap<<<(S + 127) / 128, 128, 0, st>>>(gap, S, o->n_iter, k);   // the identity prox
         }
         if ((rc = cuda_status("prox kernels"))) return rc;
         if ((rc = launch_project(g, B.tab, xn, Axn, s, B.xt, st))) return rc;
@@ -381,7 +427,8 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
 
 size_t tv_prox_workspace_bytes(int nx, int ny, int n_slices) {
     if (nx < 1 || ny < 1 || n_slices < 1) return 0;
-    return 4 * align_up(sizeof(float) * (size_t)nx * ny * n_slices) + align_up(sizeof(float) * n_slices);
+    return 4 * align_up(sizeof(float) * (size_t)nx * ny * n_slices) + align_up(sizeof(float) * n_slices) +
+           align_up(sizeof(double) * kRedBlocks * n_slices);
 }
 
 __global__ void fill_lam(float *lam, float v, int n) {
@@ -390,19 +437,25 @@ __global__ void fill_lam(float *lam, float v, int n) {
 }
 
 int tv_prox_enqueue(const float *z, int nx, int ny, int S, float lam, int n_inner, float tau, float *x, void *ws,
-                    cudaStream_t st) {
+                    cudaStream_t st, double *gap = nullptr) {
     Carver cv(ws, tv_prox_workspace_bytes(nx, ny, S));
     const size_t n = (size_t)nx * ny * S;
     float *p1a = cv.take<float>(n), *p2a = cv.take<float>(n), *p1b = cv.take<float>(n), *p2b = cv.take<float>(n);
     float *lamd = cv.take<float>(S);
+    double *part = cv.take<double>((size_t)kRedBlocks * S);
     if (lam == 0.0f) {
         cudaMemcpyAsync(x, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+        if (gap) zero_gap<<<(S + 127) / 128, 128, 0, st>>>(gap, S, 1, 0);   // the identity prox
         return cuda_status("prox copy");
     }
     fill_lam<<<(S + 127) / 128, 128, 0, st>>>(lamd, lam, S);
     bool fa;
-    int rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, S, n_inner, &fa, st, 0, x);
+    int rc = launch_chambolle(z, p1a, p2a, p1b, p2b, lamd, tau, nx, ny, S, n_inner, &fa, st, 0, x, gap != nullptr);
     if (rc) return rc;
+    if (gap) {
+        gap_partial<<<dim3(kRedBlocks, S), kRedThreads, 0, st>>>(x, fa ? p1a : p1b, fa ? p2a : p2b, nx, ny, part);
+        finalize_gap<<<S, kRedThreads, 0, st>>>(part, lamd, gap, 1, 0);
+    }
     return cuda_status("prox kernels");
 }
 
@@ -413,7 +466,7 @@ extern "C" size_t pyhst_tv_workspace_size(const pyhst_geometry *g, const pyhst_t
 }
 
 extern "C" int pyhst_tv_solve(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts, float *x,
-                              double *energy, double *lipschitz_out, void *workspace, size_t ws_bytes,
+                              double *energy, double *gap, double *lipschitz_out, void *workspace, size_t ws_bytes,
                               pyhst_stream_t stream) {
     using namespace pyhst;
     int rc = check_geometry(g);
@@ -424,7 +477,7 @@ extern "C" int pyhst_tv_solve(const pyhst_geometry *g, const float *sino, const 
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
         return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
     return tv_solve_enqueue(g, sino, opts, x, energy, lipschitz_out, workspace,
-                            reinterpret_cast<cudaStream_t>(stream));
+                            reinterpret_cast<cudaStream_t>(stream), SolveHooks(), gap);
 }
 
 extern "C" size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n_slices) {
@@ -432,7 +485,8 @@ extern "C" size_t pyhst_tv_prox_workspace_size(int32_t nx, int32_t ny, int32_t n
 }
 
 extern "C" int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_slices, float lam, int32_t n_inner,
-                             float tau, float *x, void *workspace, size_t ws_bytes, pyhst_stream_t stream) {
+                             float tau, float *x, double *gap, void *workspace, size_t ws_bytes,
+                             pyhst_stream_t stream) {
     using namespace pyhst;
     if (!z || !x) return fail(PYHST_ERR_INVALID_ARG, "z/x pointer is NULL");
     if (nx < 1 || ny < 1 || n_slices < 1 || nx > 16384 || ny > 16384 || n_slices > 65535)
@@ -449,7 +503,7 @@ extern "C" int pyhst_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_s
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
         return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
     return tv_prox_enqueue(z, nx, ny, n_slices, lam, n_inner, tau, x, workspace,
-                           reinterpret_cast<cudaStream_t>(stream));
+                           reinterpret_cast<cudaStream_t>(stream), gap);
 }
 
 extern "C" int pyhst_tv_solve_capture(const pyhst_geometry *g, const float *sino, const pyhst_tv_opts *opts, float *x,

@@ -35,6 +35,7 @@ struct TvSlice {
     const float *sino;
     float *x_user;
     double *energy;
+    double *gap;          // NULL, or the prox's duality gap per iteration
     int nx, ny, M;        // image size, sinogram elements
     int px_first, sn_first;
     int rep;              // representative slice of the geometry group (power iteration)
@@ -87,7 +88,7 @@ __device__ __forceinline__ int px_items(const TvSlice &s) { return ((s.nx + 31) 
 template <int K>
 __global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps,
-            int final_par) {
+            int final_par, int keep_p) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
     constexpr int T = chambolle_tile_size(K);
@@ -104,7 +105,9 @@ b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal 
     const bool odd = m & 1;
     const float *s1 = odd ? s.p1a : s.p1b, *s2 = odd ? s.p2a : s.p2b;
     float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
-    chambolle_tile<K>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0, xn);
+    // keep_p: the last launch also writes the final dual field of slices that report the gap
+    chambolle_tile<K>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0, xn,
+                      keep_p && s.gap != nullptr);
 }
 
 template <int K>
@@ -118,21 +121,69 @@ int b_chambolle_attr(int K) { PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_attr_k) }
 
 template <int K>
 int b_chambolle_launches_k(int nch, const TvSlice *T, const int4 *items, int nchf, const int4 *items_f, Scal sc,
-                           float tau, int n_inner, int par, cudaStream_t st) {
+                           float tau, int n_inner, int par, int keep_p, cudaStream_t st) {
     const int Lc = chambolle_launches(n_inner, K);
-    for (int m = 0; m + 1 < Lc; ++m)
-        b_chambolle<K><<<nch, kChThreads, kChSmem, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K), -1);
+    for (int m = 0; m + 1 < Lc; ++m) {
+        ProfScope prof(kProfChambolle, st);
+        b_chambolle<K><<<nch, kChThreads, kChSmem, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K), -1, 0);
+    }
     // the last launch writes x_new; it reads p one row above and one column left
     // of its tiles, so it takes the halo of K + 1 steps (same bits)
-    b_chambolle<K + 1><<<nchf, kChThreads, kChSmem, st>>>(T, items_f, sc, tau, Lc - 1,
-                                                          chambolle_steps(n_inner, Lc - 1, K), par);
+    {
+        ProfScope prof(kProfChambolle, st);
+        b_chambolle<K + 1><<<nchf, kChThreads, kChSmem, st>>>(T, items_f, sc, tau, Lc - 1,
+                                                              chambolle_steps(n_inner, Lc - 1, K), par, keep_p);
+    }
     return cuda_status("batched Chambolle kernels");
 }
 // All launches of the Chambolle steps of one iteration; the last one writes
-// x_new (xa for par = 1, xb for par = 0) instead of the dual field.
+// x_new (xa for par = 1, xb for par = 0) instead of the dual field, and with
+// keep_p the final dual field too (in the a buffers when the number of
+// launches is odd) for the slices that report the duality gap.
 int b_chambolle_launches(int K, int nch, const TvSlice *T, const int4 *items, int nchf, const int4 *items_f, Scal sc,
-                         float tau, int n_inner, int par, cudaStream_t st) {
-    PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_launches_k, nch, T, items, nchf, items_f, sc, tau, n_inner, par, st)
+                         float tau, int n_inner, int par, int keep_p, cudaStream_t st) {
+    PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_launches_k, nch, T, items, nchf, items_f, sc, tau, n_inner, par, keep_p,
+                             st)
+}
+
+// Duality-gap partial of a pixel item (the prox's gap, lam * sum of
+// |grad x| + p . grad x over the slice, as in pyhst_tv_prox): x_new of
+// it_parity, the final dual field in the a buffers (pa_final) or b.
+__global__ void b_gap_partial(const TvSlice *__restrict__ d, const int4 *__restrict__ items, int it_parity,
+                              int pa_final, double *__restrict__ part) {
+    const int4 it = items[blockIdx.x];
+    const TvSlice s = d[it.x];
+    if (!s.gap || s.beta == 0.0f) {             // uniform over the CTA
+        if (threadIdx.x == 0) part[px_slot(it, s)] = 0.0;
+        return;
+    }
+    const float *xn = it_parity ? s.xa : s.xb;
+    const float *Q1 = pa_final ? s.p1a : s.p1b, *Q2 = pa_final ? s.p2a : s.p2b;
+    RunSum rs;
+#pragma unroll
+    for (int r = 0; r < kPxRows / 8; ++r) {
+        int i, j;
+        if (!px_of(it, s, r, i, j)) continue;
+        const size_t k = (size_t)i * s.nx + j;
+        const float v = xn[k];
+        const float d1 = (i + 1 < s.ny) ? xn[k + s.nx] - v : 0.0f;
+        const float d2 = (j + 1 < s.nx) ? xn[k + 1] - v : 0.0f;
+        rs.add(sqrtf(fmaf(d1, d1, d2 * d2)) + fmaf(Q1[k], d1, Q2[k] * d2));
+    }
+    const double acc = block_sum(rs.total());
+    if (threadIdx.x == 0) part[px_slot(it, s)] = acc;
+}
+
+// gap[k] of slice blockIdx.x: lam times its partials in a fixed order (0 for beta = 0)
+__global__ void b_finalize_gap(const TvSlice *__restrict__ d, const double *__restrict__ part, Scal sc, int k) {
+    const TvSlice s = d[blockIdx.x];
+    if (!s.gap) return;                          // uniform over the CTA
+    double t = 0.0;
+    const int n_px = px_items(s);
+    if (s.beta != 0.0f)
+        for (int e = s.px_first + threadIdx.x; e < s.px_first + n_px; e += kBT) t += part[e];
+    t = block_sum(t);
+    if (threadIdx.x == 0) s.gap[(size_t)k] = s.beta == 0.0f ? 0.0 : (double)sc.lam[blockIdx.x] * t;
 }
 
 // x_new = z - lam div p (p in the buffers of `parity`); with lam = 0, x_new = z
@@ -443,7 +494,8 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
 }
 
 struct Layout {
-    size_t desc_even, desc_odd, desc_init, desc_pow, tvs, reps, items, tabs, imgs, sinos, scal, part_px, part_sn, bytes;
+    size_t desc_even, desc_odd, desc_init, desc_pow, tvs, reps, items, tabs, imgs, sinos, scal, part_px, part_sn,
+        part_gap, bytes;
     size_t n_items_total;
     std::vector<size_t> tab_off;
 };
@@ -469,6 +521,7 @@ Layout make_layout(const Plan &P, const pyhst_tv_item *items) {
     l.scal = take(sizeof(double) * P.n * 2 + sizeof(float) * P.n * 3);
     l.part_px = take(sizeof(double) * P.px.size());
     l.part_sn = take(sizeof(double) * P.sn.size());
+    l.part_gap = take(sizeof(double) * P.px.size());
     l.bytes = off;
     return l;
 }
@@ -552,6 +605,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         t.sino = items[s].sino;
         t.x_user = items[s].x;
         t.energy = items[s].energy;
+        t.gap = items[s].gap;
         t.nx = g.nx; t.ny = g.ny; t.M = g.n_angles * g.n_bins;
         t.px_first = P.px_first[s];
         t.sn_first = P.sn_first[s];
@@ -613,6 +667,10 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     sc.invn = sc.lam + n;
     double *part_px = reinterpret_cast<double *>(ws + L.part_px);
     double *part_sn = reinterpret_cast<double *>(ws + L.part_sn);
+    double *part_gap = reinterpret_cast<double *>(ws + L.part_gap);
+    bool any_gap = false;
+    for (int q = 0; q < n; ++q) any_gap = any_gap || items[q].gap != nullptr;
+    const int pa_final = (chambolle_launches(opts->n_inner, P.chK) - 1) % 2 == 0;
     const int npx = (int)P.px.size(), nsn = (int)P.sn.size(), nbp = (int)P.bp.size(), npr = (int)P.proj.size(),
               ntr = (int)P.tr.size(), nch = (int)P.ch.size(), nchf = (int)P.chf.size();
     const dim3 tb(kBT);
@@ -669,11 +727,13 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         if (rc) break;
         if (!identity) {                        // the last Chambolle launch writes x_new
             rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, nchf, I + o_chf, sc, opts->tau, opts->n_inner, par,
-                                      st);
+                                      any_gap ? 1 : 0, st);
             if (rc) break;
+            if (any_gap) b_gap_partial<<<npx, tb, 0, st>>>(T, I + o_px, par, pa_final, part_gap);
         } else {
             b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, 0, par, 1);
         }
+        if (any_gap) b_finalize_gap<<<n, tb, 0, st>>>(T, part_gap, sc, k);
         rc = project(par ? D_odd : D_even, o_proj, npr, P.proj_narrow, o_tr, ntr);
         if (rc) break;
         double w = 0.0;

@@ -100,8 +100,8 @@ def test_tv_argument_checks(L):
     for k, v in [("beta", -1.0), ("n_iter", 0), ("n_inner", 0), ("tau", 0.0), ("tau", 0.3), ("lipschitz", -2.0),
                  ("n_power_iter", 0)]:
         o = L.pyhst_tv_opts(**{**ok, k: v})
-        rc = L.lib.pyhst_tv_solve(ctypes.byref(g), 8, ctypes.byref(o), 8, None, None, 256, 1 << 30, None)
+        rc = L.lib.pyhst_tv_solve(ctypes.byref(g), 8, ctypes.byref(o), 8, None, None, None, 256, 1 << 30, None)
         assert rc == L.PYHST_ERR_INVALID_ARG, (k, v)
     o = L.pyhst_tv_opts(**ok)
-    assert L.lib.pyhst_tv_solve(ctypes.byref(g), 8, ctypes.byref(o), 8, None, None, 256, 64, None) == \
+    assert L.lib.pyhst_tv_solve(ctypes.byref(g), 8, ctypes.byref(o), 8, None, None, None, 256, 64, None) == \
         L.PYHST_ERR_WORKSPACE

@@ -15,11 +15,8 @@ def L():
     return L
 
 
-def _prox(L, z=256, nx=64, ny=64, ns=1, lam=0.1, n_inner=20, tau=0.125, x=1 << 20, ws=1024, wsb=BIG):
-    f = L.lib.pyhst_tv_prox
-    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
-                  ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
-    return f(z, nx, ny, ns, lam, n_inner, tau, x, ws, wsb, None)
+def _prox(L, z=256, nx=64, ny=64, ns=1, lam=0.1, n_inner=20, tau=0.125, x=1 << 20, ws=1024, wsb=BIG, gap=None):
+    return L.lib.pyhst_tv_prox(z, nx, ny, ns, lam, n_inner, tau, x, gap, ws, wsb, None)
 
 
 def test_tv_prox_argument_checks(L):
@@ -44,9 +41,7 @@ def test_tv_prox_rejects_overlapping_output(L):
 
 
 def test_cnn_forward_argument_checks(L):
-    f = L.lib.pyhst_cnn_forward
-    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    f = L.lib.pyhst_cnn_forward      # argument types as the binding declares them
     E = L.PYHST_ERR_INVALID_ARG
     assert f(256, 512, 1024, 0, 64, 64, 2048, BIG, None) == E
     assert f(256, 512, 1024, 1, 16385, 64, 2048, BIG, None) == E
@@ -59,7 +54,6 @@ def test_patch_grid_counts_and_checks(L):
     (host arithmetic only): 2048^2 with 8 x 8 patches at stride 4 gives the
     511 x 511 = 261,121 patches of the patch study."""
     f = L.lib.pyhst_patch_grid
-    f.argtypes = [ctypes.c_int32] * 4 + [ctypes.POINTER(ctypes.c_int32)] * 2
     kr, kc = ctypes.c_int32(), ctypes.c_int32()
     assert f(2048, 2048, 8, 4, ctypes.byref(kr), ctypes.byref(kc)) == 0
     assert (kr.value, kc.value) == (511, 511)

@@ -415,3 +415,78 @@ def test_batch_solve_with_tuned_steps_matches_default(P, orc, cuda_device):
         P.pyhst_set_tv_prox_steps(64, 64, 0)
     for a, b in zip(xs0, xs1):
         assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------------ ROF duality gap of the prox
+# The gap is primal minus dual, two nearly equal quantities; float32 rounding
+# of the dual field moves it by about 1e-7 of the TV term lam TV(x) that
+# the reduction sums, so the gap is compared with the oracle's within
+# GAP_TOL * lam TV(x) (and printed as a plain relative error as well).
+GAP_TOL = 1e-5
+
+
+@pytest.mark.parametrize("shape,lam,n_inner", [((64, 64), 0.3, 20), ((77, 100), 0.05, 20), ((31, 9), 1.5, 7),
+                                               ((200, 160), 0.1, 60)])
+def test_tv_prox_gap_parity(P, orc, cuda_device, shape, lam, n_inner):
+    g = np.random.default_rng(sum(shape) + 1)
+    z = g.standard_normal((2,) + shape).astype(np.float32)
+    gap = torch.empty(2, dtype=torch.float64, device=cuda_device)
+    x = P.pyhst_tv_prox(torch.from_numpy(z).to(cuda_device), lam, n_inner, gap=gap).cpu().numpy()
+    gap = gap.cpu().numpy()
+    for k in range(2):
+        xr, p1, p2 = orc.tv_prox(z[k].astype(np.float64), lam, n_inner)
+        gr = orc.rof_gap(z[k].astype(np.float64), lam, p1, p2)
+        scale = lam * orc.tv(xr)
+        print(f"\nprox gap {shape} lam {lam} n {n_inner}: gpu {gap[k]:.6e} oracle {gr:.6e} "
+              f"rel {abs(gap[k] - gr) / gr:.2e} (of lam TV {abs(gap[k] - gr) / scale:.2e})")
+        assert gap[k] >= 0
+        assert abs(gap[k] - gr) <= GAP_TOL * scale
+        assert rel(x[k], xr) <= 1e-5
+
+
+def test_tv_prox_gap_decreases_with_inner_steps(P, cuda_device):
+    g = torch.Generator(device=cuda_device).manual_seed(5)
+    z = torch.randn((3, 96, 80), device=cuda_device, generator=g)
+    gaps = []
+    for n_inner in (5, 20, 80, 320):
+        gp = torch.empty(3, dtype=torch.float64, device=cuda_device)
+        P.pyhst_tv_prox(z, 0.2, n_inner, gap=gp)
+        gaps.append(gp.cpu().numpy())
+    gaps = np.array(gaps)
+    assert np.all(gaps > 0)
+    assert np.all(np.diff(gaps, axis=0) < 0), gaps
+    gz = torch.empty(3, dtype=torch.float64, device=cuda_device)
+    P.pyhst_tv_prox(z, 0.0, 5, gap=gz)
+    assert torch.all(gz == 0)
+
+
+@pytest.mark.parametrize("fista,beta", [(True, 2e-3), (False, 5e-3), (True, 0.0)])
+def test_tv_solve_gap_history_parity(P, orc, cuda_device, fista, beta):
+    """The gap of every iteration's prox in pyhst_tv_solve against the
+    oracle FISTA's, and the batched solver's equal to the single-slice
+    solver's (different reduction order: 1e-6 relative)."""
+    fs, geo, og = _foam_problem(P, orc, cuda_device)
+    L = 1.01 * orc.power_iteration(og, np.ones((fs.ny, fs.nx)), 30)[0]
+    sino = fs.extra["sino"]
+    n_iter = 15
+    opts = P.TvOptions(beta=beta, n_iter=n_iter, n_inner=20, lipschitz=L, use_fista=fista)
+    gap = torch.empty((1, n_iter), dtype=torch.float64, device=cuda_device)
+    x, e, _ = P.pyhst_tv_solve(geo, sino.to(cuda_device), opts, gap=gap)
+    xr, er, gr = orc.fista(og, sino.double().numpy(), beta, L, n_iter, n_inner=20, use_fista=fista, return_gap=True)
+    gap = gap[0].cpu().numpy()
+    gb = torch.empty(n_iter, dtype=torch.float64, device=cuda_device)
+    xs, _, _ = P.pyhst_tv_solve_batch([(geo, sino.to(cuda_device).contiguous(), None)], opts, gaps=[gb])
+    gb = gb.cpu().numpy()
+    assert torch.equal(xs[0], x[0])
+    if beta == 0.0:
+        assert np.all(gap == 0) and np.all(gr == 0) and np.all(gb == 0)
+        return
+    # lam TV(x_k) of every iterate, from the oracle's energies: E - 1/2 ||P x - y||^2 is beta TV
+    scale = np.array([(beta / L) * orc.tv(orc.fista(og, sino.double().numpy(), beta, L, k + 1, n_inner=20,
+                                                    use_fista=fista)[0]) for k in (0, n_iter - 1)])
+    err = np.abs(gap - gr)
+    print(f"\nsolve gaps fista={fista}: rel max {np.max(err / gr):.2e}, of lam TV {err.max() / scale.min():.2e}; "
+          f"batch vs single rel {np.max(np.abs(gb - gap) / gap):.2e}")
+    assert np.all(gap >= 0)
+    assert err.max() <= GAP_TOL * scale.min()
+    np.testing.assert_allclose(gb, gap, rtol=1e-6)

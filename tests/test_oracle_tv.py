@@ -229,3 +229,52 @@ def test_energy_equals_dense_system(orc, case):
     beta = float(g.uniform(0.1, 2.0))
     ref = 0.5 * np.sum((y.ravel() - A @ x.ravel()) ** 2) + beta * _np_tv(x)
     assert orc.energy(geo, y, x, beta) == pytest.approx(ref, rel=1e-13)
+
+
+def _np_grad(x):
+    d1 = np.zeros_like(x)
+    d2 = np.zeros_like(x)
+    d1[:-1, :] = np.diff(x, axis=0)
+    d2[:, :-1] = np.diff(x, axis=1)
+    return d1, d2
+
+
+def test_rof_gap_equals_sum_of_nonnegative_terms(orc):
+    """For x = z - lam div p with |p| <= 1, primal minus dual of the ROF
+    problem equals lam * sum(|grad x| + p . grad x) (expand the squares and
+    use div = -grad^T), a sum of terms that are each >= 0 by Cauchy-Schwarz.
+    Checked with numpy differences on random feasible dual fields, so a
+    wrong sign, a dropped 1/2 or a wrong lam in the oracle's gap fails."""
+    g = np.random.default_rng(21)
+    for ny, nx, lam in ((9, 13, 0.4), (20, 7, 2.5), (16, 16, 0.05)):
+        z = g.standard_normal((ny, nx))
+        p1, p2 = g.standard_normal((2, ny, nx))
+        r = np.maximum(1.0, np.hypot(p1, p2)) / g.uniform(0.2, 1.0, (ny, nx))
+        p1, p2 = p1 / r, p2 / r
+        assert np.all(np.hypot(p1, p2) <= 1.0)
+        d1, d2 = _np_grad(z - lam * orc.div(p1, p2))
+        terms = np.hypot(d1, d2) + p1 * d1 + p2 * d2
+        assert terms.min() >= -1e-12
+        assert orc.rof_gap(z, lam, p1, p2) == pytest.approx(lam * terms.sum(), rel=1e-12)
+
+
+def test_fista_gap_history(orc):
+    """The gap history of the solver's proxes: non-negative, zero without a
+    penalty, its last entry equal to the gap of the prox recomputed from the
+    last prox input, and (first iteration, same z) smaller with more inner
+    steps."""
+    geo = _tiny_geometry(orc, n=16, na=6, nb=24, seed=2)
+    g = np.random.default_rng(22)
+    xt = np.zeros((16, 16))
+    xt[4:12, 5:11] = 1.0
+    y = geo.P(xt) + 0.02 * g.standard_normal((6, 24))
+    L = 1.01 * orc.power_iteration(geo, g.standard_normal((16, 16)), 100)[0]
+    beta = 0.02
+    x, e, z, gp = orc.fista(geo, y, beta, L, 12, n_inner=20, return_z=True, return_gap=True)
+    assert np.all(gp >= 0) and np.all(gp > 0)
+    _, p1, p2 = orc.tv_prox(z, beta / L, 20)
+    assert gp[-1] == pytest.approx(orc.rof_gap(z, beta / L, p1, p2), rel=1e-13)
+    _, _, g0 = orc.fista(geo, y, 0.0, L, 5, n_inner=20, return_gap=True)
+    assert np.all(g0 == 0)
+    first = [orc.fista(geo, y, beta, L, 1, n_inner=m, return_gap=True)[2][0] for m in (2, 8, 32, 128)]
+    assert all(b < a for a, b in zip(first, first[1:])), first
