@@ -323,6 +323,22 @@ int pyhst_autotune_tv_prox(const float *z, int32_t nx, int32_t ny, int32_t n_sli
                            float tau, void *workspace, size_t ws_bytes, int32_t *best_steps, pyhst_stream_t stream);
 int pyhst_set_tv_prox_steps(int32_t nx, int32_t ny, int32_t steps);
 
+/* Autotuning of the back-projector.  Each CTA stages the filtered rows of a
+ * block of angles at a time; the block size (8, 16 or 24 angles) trades
+ * barriers and set-up per angle against the padding slots of a last, partial
+ * block, and gives identical results (every pixel sums its angles in the same
+ * order).  pyhst_autotune_backproject times every choice on the caller's
+ * sinograms sino [n_slices][n_angles][n_bins] (DEVICE; img receives the
+ * back-projection, workspace as pyhst_backproject's), synchronizing `stream`,
+ * and records the fastest for (nx, ny, n_angles) on the current device;
+ * pyhst_backproject, the FBP entry points, the TV solvers and
+ * pyhst_tv_solve_batch (for its geometry with the most updates) then use it.
+ * pyhst_set_backproject_block records a choice directly (0 clears it; the
+ * default is 16). */
+int pyhst_autotune_backproject(const pyhst_geometry *g, const float *sino, float *img, void *workspace,
+                               size_t ws_bytes, int32_t *best, pyhst_stream_t stream);
+int pyhst_set_backproject_block(int32_t nx, int32_t ny, int32_t n_angles, int32_t angles_per_block);
+
 /* pyhst_tv_solve for many slices of different sizes and angle sets at once
  * (same options for all): every stage of an iteration is one launch over the
  * whole batch, and the n_iter iterations are captured in one CUDA graph on
@@ -463,8 +479,20 @@ int pyhst_patch_solve(const pyhst_patch_problem *pp, const pyhst_geometry *g, co
 
 /* Error bits recorded on the current device by kernels whose bounded waits
  * gave up (1: a tensor-core completion wait), since the last clear.  Reads
- * the word synchronously; clear != 0 resets it. */
+ * the word synchronously; clear != 0 resets it.  A kernel whose wait gave up
+ * stops issuing work, waits (with the default limit) for the tensor-core
+ * operations it already issued, frees its tensor memory and returns; its
+ * output is then incomplete. */
 int pyhst_device_status(uint32_t *flags, int32_t clear);
+
+/* Failure detection (the paper has no counterpart): number of polls after
+ * which the pipeline waits of the tensor-core kernels (CNN convolutions,
+ * patch products) give up; a negative value restores the default (2^22
+ * polls, far longer than any healthy wait), 0 makes every such wait give up
+ * without polling, so that tests can exercise the give-up path and
+ * pyhst_device_status without a GPU fault.  Process-wide; takes effect at the
+ * next launch.  PYHST_ERR_INVALID_ARG above 2^32 - 1. */
+int pyhst_set_wait_limit(int64_t polls);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *pyhst_last_error(void);

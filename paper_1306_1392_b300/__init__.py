@@ -688,6 +688,37 @@ def pyhst_device_status(clear: bool = True) -> int:
     return int(v.value)
 
 
+def pyhst_autotune_backproject(geom: Geometry, sino: torch.Tensor, out=None, workspace=None) -> int:
+    """Time the back-projector's angle blocks (8, 16, 24 angles; identical
+    results) on sino [n_slices, n_angles, n_bins] and record the fastest for
+    the geometry; returns it."""
+    sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")
+    ns = sino.shape[0]
+    if tuple(sino.shape[1:]) != (geom.n_angles, geom.n_bins):
+        raise ValueError("sinogram shape does not match the geometry")
+    if out is None:
+        out = torch.empty((ns, geom.ny, geom.nx), dtype=torch.float32, device=sino.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    ws = _workspace(L.lib.pyhst_workspace_size(ctypes.byref(g), PYHST_OP_BACKPROJECT), sino.device, workspace)
+    best = ctypes.c_int32(0)
+    _check(L.lib.pyhst_autotune_backproject(ctypes.byref(g), _ptr(sino), _ptr(out), _ptr(ws), ws.numel(),
+                                            ctypes.byref(best), _stream()))
+    return int(best.value)
+
+
+def pyhst_set_backproject_block(nx: int, ny: int, n_angles: int, angles_per_block: int) -> None:
+    """Record the back-projector's angle block for a geometry (0 clears)."""
+    _check(L.lib.pyhst_set_backproject_block(int(nx), int(ny), int(n_angles), int(angles_per_block)))
+
+
+def pyhst_set_wait_limit(polls: int = -1) -> None:
+    """Polls after which the tensor-core kernels' pipeline waits give up
+    (negative: the default; 0: give up without polling); for tests of
+    failure detection."""
+    _check(L.lib.pyhst_set_wait_limit(int(polls)))
+
+
 def fbp_weight(n_angles: int, pixel_size: float) -> float:
     """pi / (n_angles * s), the FBP angular weight over 180 degrees."""
     return math.pi / (n_angles * pixel_size)

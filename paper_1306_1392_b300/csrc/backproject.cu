@@ -26,6 +26,9 @@
 // from L2 while the current block is computed, with one barrier per block.
 #include <climits>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -35,10 +38,12 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kTX = 64, kTY = 64;   // CTA output tile (x, y)
 constexpr int kRX = 4, kRY = 4;     // pixels per thread: x stride 8, y stride 4 (warp: 32 x 16)
-constexpr int kNA = 16;             // angles staged per block
 constexpr int kW = 96;              // window entries per angle: ceil(hypot(63, 63)) + 4, rounded up
-constexpr int kFill = kNA * kW / kThreads;   // window entries each thread fills per block (6)
-static_assert(kNA % (kThreads / 32) == 0 && kW % 32 == 0, "fill mapping");
+// Angles staged per block (NA): 8, 16 or 24, a tuning parameter (the
+// per-pixel sums run over the angles in the same order for every NA, and the
+// padding slots of a last, partial block add +0, so results are identical);
+// each thread fills NA * kW / kThreads window entries per block.
+static_assert(kW % 32 == 0, "fill mapping");
 
 struct __align__(16) StageInfo {
     float base;   // u at the tile origin
@@ -72,12 +77,14 @@ __device__ __forceinline__ StageInfo stage_info(const AngleInfo *tab, int a, int
 // mode) are that slice's rows, out its image.
 // With ystep given, out receives the gradient step z = ystep - invL * g of
 // g = weight * back-projection, rounded as a separate pass would round it.
-template <bool kResidual>
+template <int kNA, bool kResidual>
 __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const float *__restrict__ A,
                                         const float *__restrict__ B, float *__restrict__ out, int n_angles,
                                         int n_bins, int nx, int ny, double cx, double cy, float weight,
                                         int X0, int Y0, const float *__restrict__ ystep = nullptr,
                                         float invL = 0.0f) {
+    static_assert(kNA % (kThreads / 32) == 0, "fill mapping");
+    constexpr int kFill = kNA * kW / kThreads;   // window entries each thread fills per block
     __shared__ __align__(16) float2 win[2][kNA * kW];
     __shared__ StageInfo info[3][kNA];
 
@@ -184,7 +191,7 @@ __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const
         }
 }
 
-template <bool kResidual>
+template <int kNA, bool kResidual>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
           const float *__restrict__ srcB, float *__restrict__ img, int n_angles, int n_bins,
@@ -192,19 +199,41 @@ bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
           const float *__restrict__ invL) {
     const int slice = blockIdx.y;
     const size_t sino_off = (size_t)slice * n_angles * n_bins, img_off = (size_t)slice * nx * ny;
-    bp_tile<kResidual>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + img_off,
+    bp_tile<kNA, kResidual>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + img_off,
                        n_angles, n_bins, nx, ny, cx, cy, weight, (blockIdx.x % tiles_x) * kTX,
                        (blockIdx.x / tiles_x) * kTY, ystep ? ystep + img_off : nullptr, ystep ? invL[slice] : 0.0f);
 }
 
 // Mixed batch: CTA k reconstructs tile (items[k].y, items[k].z) of slice items[k].x.
-template <bool kResidual>
+template <int kNA, bool kResidual>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items, float weight_scale) {
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
-    bp_tile<kResidual>(s.tab, s.bp_a, s.bp_b, s.bp_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
+    bp_tile<kNA, kResidual>(s.tab, s.bp_a, s.bp_b, s.bp_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
                        weight_scale * s.pixel_size, it.y * kTX, it.z * kTY, s.bp_y, s.bp_y ? *s.bp_invL : 0.0f);
+}
+
+template <int kNA>
+int launch_bp_batch_na(const BatchSlice *slices, const int4 *items, int n_items, bool residual, cudaStream_t st) {
+    if (residual)
+        bp_batch_kernel<kNA, true><<<n_items, kThreads, 0, st>>>(slices, items, 1.0f);
+    else
+        bp_batch_kernel<kNA, false><<<n_items, kThreads, 0, st>>>(slices, items, 1.0f);
+    return cuda_status("batched back-projection kernel");
+}
+
+template <int kNA>
+int launch_bp_na(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img, float weight, dim3 grid,
+                 int tiles_x, cudaStream_t st) {
+    if (src.b)
+        bp_kernel<kNA, true><<<grid, kThreads, 0, st>>>(tab, src.a, src.b, img, g->n_angles, g->n_bins, g->nx,
+                                                        g->ny, g->cx, g->cy, weight, tiles_x, src.y, src.invL);
+    else
+        bp_kernel<kNA, false><<<grid, kThreads, 0, st>>>(tab, src.a, nullptr, img, g->n_angles, g->n_bins,
+                                                         g->nx, g->ny, g->cx, g->cy, weight, tiles_x, src.y,
+                                                         src.invL);
+    return cuda_status("back-projection kernel");
 }
 
 }  // namespace
@@ -215,34 +244,108 @@ int bp_tiles(int nx, int ny, int *tx, int *ty) {
     return *tx * *ty;
 }
 
+bool bp_block_supported(int na) { return na == 8 || na == 16 || na == 24; }
+
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
-                             cudaStream_t st) {
+                             cudaStream_t st, int angle_block) {
     if (n_items <= 0) return PYHST_OK;
     ProfScope prof(kProfBackproject, st);
-    if (residual)
-        bp_batch_kernel<true><<<n_items, kThreads, 0, st>>>(slices, items, 1.0f);
-    else
-        bp_batch_kernel<false><<<n_items, kThreads, 0, st>>>(slices, items, 1.0f);
-    return cuda_status("batched back-projection kernel");
+    switch (angle_block) {
+        case 8: return launch_bp_batch_na<8>(slices, items, n_items, residual, st);
+        case 24: return launch_bp_batch_na<24>(slices, items, n_items, residual, st);
+        default: return launch_bp_batch_na<16>(slices, items, n_items, residual, st);
+    }
 }
 
 int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img,
-                       float weight, cudaStream_t st) {
+                       float weight, cudaStream_t st, int angle_block) {
     const int tiles_x = (g->nx + kTX - 1) / kTX;
     const int tiles_y = (g->ny + kTY - 1) / kTY;
     dim3 grid(tiles_x * tiles_y, g->n_slices);
     if (grid.y > 65535) return fail(PYHST_ERR_INVALID_ARG, "too many slices in one call (%d)", g->n_slices);
+    if (angle_block <= 0) angle_block = bp_block_for(g->nx, g->ny, g->n_angles);
     ProfScope prof(kProfBackproject, st);
-    if (src.b)
-        bp_kernel<true><<<grid, kThreads, 0, st>>>(tab, src.a, src.b, img, g->n_angles, g->n_bins, g->nx,
-                                                   g->ny, g->cx, g->cy, weight, tiles_x, src.y, src.invL);
-    else
-        bp_kernel<false><<<grid, kThreads, 0, st>>>(tab, src.a, nullptr, img, g->n_angles, g->n_bins,
-                                                    g->nx, g->ny, g->cx, g->cy, weight, tiles_x, src.y, src.invL);
-    return cuda_status("back-projection kernel");
+    switch (angle_block) {
+        case 8: return launch_bp_na<8>(g, tab, src, img, weight, grid, tiles_x, st);
+        case 24: return launch_bp_na<24>(g, tab, src, img, weight, grid, tiles_x, st);
+        default: return launch_bp_na<16>(g, tab, src, img, weight, grid, tiles_x, st);
+    }
+}
+
+namespace {
+std::mutex g_bp_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_bp_tune;   // (device, nx, ny, n_angles) -> angles per block
+}  // namespace
+
+int bp_block_for(int nx, int ny, int n_angles) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_bp_tune_mu);
+    auto it = g_bp_tune.find(std::make_tuple(dev, nx, ny, n_angles));
+    return it == g_bp_tune.end() ? 16 : it->second;
 }
 
 }  // namespace pyhst
+
+extern "C" int pyhst_set_backproject_block(int32_t nx, int32_t ny, int32_t n_angles, int32_t angles_per_block) {
+    using namespace pyhst;
+    if (nx < 1 || ny < 1 || n_angles < 1) return fail(PYHST_ERR_INVALID_ARG, "image %d x %d, %d angles", nx, ny, n_angles);
+    if (angles_per_block != 0 && !bp_block_supported(angles_per_block))
+        return fail(PYHST_ERR_INVALID_ARG, "angles per block %d: need 8, 16 or 24 (0 clears)", angles_per_block);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_bp_tune_mu);
+    const auto key = std::make_tuple(dev, (int)nx, (int)ny, (int)n_angles);
+    if (angles_per_block == 0)
+        g_bp_tune.erase(key);
+    else
+        g_bp_tune[key] = angles_per_block;
+    return PYHST_OK;
+}
+
+extern "C" int pyhst_autotune_backproject(const pyhst_geometry *g, const float *sino, float *img, void *workspace,
+                                          size_t ws_bytes, int32_t *best, pyhst_stream_t stream) {
+    using namespace pyhst;
+    int rc = check_geometry(g);
+    if (rc) return rc;
+    if (!sino || !img) return fail(PYHST_ERR_INVALID_ARG, "sino/img pointer is NULL");
+    const size_t need = pyhst_workspace_size(g, PYHST_OP_BACKPROJECT);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv(workspace, ws_bytes);
+    AngleInfo *tab = cv.take<AngleInfo>(g->n_angles);
+    if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, tab, st))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_status("autotune events");
+    }
+    int pick = 16;
+    float best_ms = 1e30f;
+    for (int na : {8, 16, 24}) {
+        if ((rc = launch_backproject(g, tab, BpSource{sino, nullptr}, img, 1.0f, st, na))) break;   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && !rc; ++r) rc = launch_backproject(g, tab, BpSource{sino, nullptr}, img, 1.0f, st, na);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = cuda_status("autotune timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            pick = na;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best) *best = pick;
+    return pyhst_set_backproject_block(g->nx, g->ny, g->n_angles, pick);
+}
 
 extern "C" int pyhst_backproject(const pyhst_geometry *g, const float *sino, float *img, float weight,
                                  void *workspace, size_t ws_bytes, pyhst_stream_t stream) {

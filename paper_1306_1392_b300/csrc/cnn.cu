@@ -149,7 +149,6 @@ constexpr int kXS = 130;                           // staged pixels per row: 128
 constexpr int kInBytes = ((kR + 2) * kXS * 64 + 1023) / 1024 * 1024;   // 84,992 per buffer
 constexpr int kMidSmem = 1024 + 2 * kInBytes + kLayerBytes;         // + alignment slack
 constexpr uint32_t kTmemCols = 2 * kR * kC;        // 512: two accumulator halves
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct MidTiles {
     int tx, ty, H, W;
@@ -227,7 +226,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
                                                                   const uint4 *__restrict__ wpack,
                                                                   const float *__restrict__ bias,
                                                                   const uint4 *__restrict__ aux, MidTiles T,
-                                                                  unsigned *__restrict__ status) {
+                                                                  unsigned *__restrict__ status,
+                                                                  uint32_t wait_limit) {
     extern __shared__ __align__(1024) uint8_t sm_raw[];
     // swizzled operands need 1024-byte aligned shared addresses
     uint8_t *sm = sm_raw + ((1024 - (tc::smem_u32(sm_raw) & 1023)) & 1023);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
     __shared__ float s_bias[kC];
     __shared__ __align__(16) MmaOp s_ops[kMmaWarps][kMaxOps];
     __shared__ int s_nops[kMmaWarps];
-    __shared__ __align__(8) uint64_t bar_loaded[2], bar_mma[2], bar_tfree[2];
+    __shared__ __align__(8) uint64_t bar_loaded[2], bar_mma[2], bar_tfree[2], bar_drain[kMmaWarps];
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
                 tc::bar_init(&bar_mma[b], kMmaWarps);
                 tc::bar_init(&bar_tfree[b], kWorkers);
             }
+            for (int g = 0; g < kMmaWarps; ++g) tc::bar_init(&bar_drain[g], 1);
         }
     } else if (warp >= kMmaWarps) {
         const int w = tid - 32 * kMmaWarps;
@@ -270,8 +271,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
         const uint64_t hi = tc::sdesc_sw64(0, 512);          // descriptor without its start address
         for (int i = 0; i < n_my && ok; ++i) {
             const int b = i & 1;
-            bool good = tc::bar_wait(&bar_loaded[b], (uint32_t)((i >> 1) & 1), kWaitLimit);
-            if (good && i >= 2) good = tc::bar_wait(&bar_tfree[b], (uint32_t)(((i >> 1) - 1) & 1), kWaitLimit);
+            bool good = tc::bar_wait(&bar_loaded[b], (uint32_t)((i >> 1) & 1), wait_limit);
+            if (good && i >= 2) good = tc::bar_wait(&bar_tfree[b], (uint32_t)(((i >> 1) - 1) & 1), wait_limit);
             ok = __all_sync(0xffffffffu, good);
             if (!ok) break;
             tc::fence_after();
@@ -290,6 +291,14 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
             __syncwarp();
         }
         if (!ok && lane == 0) atomicOr(status, tc::kErrMmaTimeout);
+        // every MMA this warp issued has finished before the tensor memory is
+        // freed: a commit tracks all of the issuing thread's earlier MMAs (the
+        // wait keeps the default limit even when the pipeline waits are lowered)
+        if (lane == 0) {
+            tc::mma_commit(&bar_drain[warp]);
+            if (!tc::bar_wait(&bar_drain[warp], 0, kDefaultWaitLimit)) atomicOr(status, tc::kErrMmaTimeout);
+        }
+        __syncwarp();
     } else {
         // ---------------------------------------------------------- workers
         const int w = tid - 32 * kMmaWarps, ww = warp - kMmaWarps;   // worker warp 0 .. 7
@@ -321,7 +330,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
         for (int i = 0; i <= n_my; ++i) {
             if (i >= 1) {
                 const int j = i - 1;
-                ok = __all_sync(0xffffffffu, tc::bar_wait(&bar_mma[j & 1], (uint32_t)((j >> 1) & 1), kWaitLimit));
+                ok = __all_sync(0xffffffffu, tc::bar_wait(&bar_mma[j & 1], (uint32_t)((j >> 1) & 1), wait_limit));
                 if (!ok) {
                     if (lane == 0) atomicOr(status, tc::kErrMmaTimeout);
                     break;
@@ -363,11 +372,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
             if (i + 1 < n_my) publish(i + 1);
         }
     }
-    // every thread gets here (all waits are bounded); drain before freeing TMEM
-    if (!__syncthreads_and(ok) && tid == 0) {
-        tc::bar_wait(&bar_mma[0], 0, kWaitLimit);
-        tc::bar_wait(&bar_mma[1], 0, kWaitLimit);
-    }
+    // every thread gets here (all waits are bounded; the MMA warps have drained
+    // their tensor-core work, and the workers' copies were waited for before
+    // each publish, so none is in flight)
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -474,9 +481,11 @@ int launch_conv_mid(bool bwd, const uint4 *in, uint4 *out, const __nv_bfloat16 *
     const int grid = (int)std::min<long>(T.total, sm_count());
     const uint4 *wp = reinterpret_cast<const uint4 *>(packed_layer);
     if (bwd)
-        conv_mid_kernel<true><<<grid, kMidThreads, kMidSmem, st>>>(in, out, wp, bias, aux, T, status);
+        conv_mid_kernel<true><<<grid, kMidThreads, kMidSmem, st>>>(in, out, wp, bias, aux, T, status,
+                                                                   pipeline_wait_limit());
     else
-        conv_mid_kernel<false><<<grid, kMidThreads, kMidSmem, st>>>(in, out, wp, bias, aux, T, status);
+        conv_mid_kernel<false><<<grid, kMidThreads, kMidSmem, st>>>(in, out, wp, bias, aux, T, status,
+                                                                    pipeline_wait_limit());
     return cuda_status("conv_mid_kernel");
 }
 

@@ -3,6 +3,9 @@
 #include <cstdio>
 #include <cmath>
 
+#include <atomic>
+#include <cstdint>
+
 #include "common.cuh"
 
 namespace pyhst {
@@ -77,7 +80,21 @@ unsigned *device_status_ptr() {
     return static_cast<unsigned *>(p);
 }
 
+std::atomic<int64_t> g_wait_limit{-1};
+
+uint32_t pipeline_wait_limit() {
+    const int64_t v = g_wait_limit.load(std::memory_order_relaxed);
+    return v < 0 ? kDefaultWaitLimit : (uint32_t)v;
+}
+
 }  // namespace pyhst
+
+extern "C" int pyhst_set_wait_limit(int64_t polls) {
+    if (polls > (int64_t)UINT32_MAX) return pyhst::fail(PYHST_ERR_INVALID_ARG, "wait limit %lld beyond 2^32 - 1",
+                                                        (long long)polls);
+    pyhst::g_wait_limit.store(polls < 0 ? -1 : polls, std::memory_order_relaxed);
+    return PYHST_OK;
+}
 
 extern "C" int pyhst_device_status(uint32_t *flags, int32_t clear) {
     if (!flags) return pyhst::fail(PYHST_ERR_INVALID_ARG, "flags pointer is NULL");

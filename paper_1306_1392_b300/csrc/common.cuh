@@ -44,6 +44,12 @@ size_t cnn_workspace_size(int n, int H, int W);
 
 // Device address of this device's status word (kernels OR error bits into it).
 unsigned *device_status_ptr();
+// Polls after which the pipeline waits of the tensor-core kernels give up
+// (pyhst_set_wait_limit; kDefaultWaitLimit unless lowered for a test).  The
+// waits that drain in-flight tensor-core work before TMEM is freed always use
+// kDefaultWaitLimit.
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
+uint32_t pipeline_wait_limit();
 
 // ----------------------------------------------------------------- workspace
 constexpr size_t kAlign = 256;
@@ -78,8 +84,14 @@ struct BpSource {
     const float *y = nullptr;
     const float *invL = nullptr;
 };
+// angle_block: angles staged per block (8, 16, 24); <= 0 takes the tuned or
+// default choice for the geometry (bp_block_for).
 int launch_backproject(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img,
-                       float weight, cudaStream_t st);
+                       float weight, cudaStream_t st, int angle_block = 0);
+bool bp_block_supported(int na);
+// Angles per block for images of ny x nx and n_angles angles: the autotuned
+// choice (pyhst_autotune_backproject / pyhst_set_backproject_block), else 16.
+int bp_block_for(int nx, int ny, int n_angles);
 
 // Projector: img [n_slices][ny][nx] -> sino [n_slices][n_angles][n_bins],
 // scaled by `scale`; `xt` is scratch for the transposed slice stack
@@ -108,7 +120,7 @@ struct BatchSlice {
 };
 int bp_tiles(int nx, int ny, int *tx, int *ty);
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
-                             cudaStream_t st);
+                             cudaStream_t st, int angle_block = 16);
 int proj_blocks(int n_angles, int n_bins, int *nb, int *na);
 // true: the 512-column staging variant of the projector (sparse angle sets)
 bool project_wide(int nx, int ny, int n_angles);

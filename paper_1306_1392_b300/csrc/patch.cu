@@ -228,7 +228,6 @@ constexpr int kTcStage = 3 * kTcSplit;
 constexpr int kTcEpiBytes = 8 * 32 * 33 * 4;       // a 32 x 33 transpose block per read-back warp
 constexpr size_t kTcBMax = 64 * 1024;              // bytes of the staged B terms at most
 constexpr size_t kTcMinSmem = 120 * 1024;          // one CTA per SM (its tensor memory is 512 columns)
-constexpr uint32_t kTcWait = 1u << 22;
 
 // x = x1 + x2 + x3 exactly; each term's bf16 value is the high half of the word.
 __device__ __forceinline__ void split3(float x, uint32_t &a, uint32_t &b, uint32_t &c) {
@@ -247,7 +246,7 @@ __device__ __forceinline__ void bar_arrive(uint64_t *bar) {
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C, int M, int N, int K,
-               int NT, int Kp, float alpha, unsigned *__restrict__ status) {
+               int NT, int Kp, float alpha, unsigned *__restrict__ status, uint32_t kTcWait) {
     extern __shared__ __align__(128) uint8_t tc_smem[];
     uint8_t *ring = tc_smem;                                   // kTcStages x 3 terms x [128 rows][32 k]
     float *epi = reinterpret_cast<float *>(tc_smem + kTcStages * kTcStage);   // 8 x [32][33]
@@ -357,7 +356,7 @@ gemm_tc_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
         // every MMA issued has finished before the tensor memory is freed
         if (lane == 0) {
             tc::mma_commit(&drain);
-            if (!tc::bar_wait(&drain, 0, kTcWait)) atomicOr(status, tc::kErrMmaTimeout);
+            if (!tc::bar_wait(&drain, 0, kDefaultWaitLimit)) atomicOr(status, tc::kErrMmaTimeout);
         }
         __syncwarp();
     } else if (tid < kTcProd0) {
@@ -496,7 +495,8 @@ void gemm_tc(const float *A, const float *B, float *C, int M, int N, int K, floa
     }
     const int tiles = (M + 127) / 128;
     gemm_tc_kernel<<<std::min(tiles, g_sm_count), kTcThreads, smem, st>>>(A, B, C, M, N, K, NT, Kp, alpha,
-                                                                         device_status_ptr());
+                                                                         device_status_ptr(),
+                                                                         pipeline_wait_limit());
 }
 
 // Shapes whose padded B fits the tensor-core kernel take it; the rest (more

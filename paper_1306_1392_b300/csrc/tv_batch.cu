@@ -405,6 +405,7 @@ struct Plan {
     // (each slice uses the variant of its single-slice solve)
     int proj_narrow = 0, proj_r_narrow = 0;
     int chK = 5;     // Chambolle steps fused per launch (tuned for the largest slice)
+    int bpNA = 16;   // back-projector angles per block (tuned for the geometry with the most updates)
 };
 
 size_t up4(size_t v) { return (v + 63) / 64 * 64; }   // 256-byte multiples of floats
@@ -445,6 +446,16 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
     for (int s = 1; s < n; ++s)
         if ((long)items[s].geom.nx * items[s].geom.ny > (long)items[big].geom.nx * items[big].geom.ny) big = s;
     P.chK = chambolle_k_for(items[big].geom.nx, items[big].geom.ny);
+    {   // the back-projector's angle block: that of the geometry (size, angle count) with the most updates
+        std::map<std::tuple<int, int, int>, double> work;
+        for (int s = 0; s < n; ++s) {
+            const pyhst_geometry &g = items[s].geom;
+            work[std::make_tuple(g.nx, g.ny, g.n_angles)] += (double)g.nx * g.ny * g.n_angles;
+        }
+        auto top = std::max_element(work.begin(), work.end(),
+                                    [](const auto &a, const auto &b) { return a.second < b.second; });
+        P.bpNA = bp_block_for(std::get<0>(top->first), std::get<1>(top->first), std::get<2>(top->first));
+    }
     P.rep.resize(n);
     std::map<std::tuple<const void *, const void *, int, int, int, int, float, float, float>, int> groups;
     for (int s = 0; s < n; ++s) {
@@ -689,7 +700,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         for (int it = 0; it < opts->n_power_iter; ++it) {
             if ((rc = project(D_pow, o_projr, (int)P.proj_r.size(), P.proj_r_narrow, o_trr, (int)P.tr_r.size())))
                 return rc;
-            if ((rc = launch_backproject_batch(D_pow, I + o_bpr, (int)P.bp_r.size(), false, st))) return rc;
+            if ((rc = launch_backproject_batch(D_pow, I + o_bpr, (int)P.bp_r.size(), false, st, P.bpNA))) return rc;
             b_sqnorm_g<<<npxr, tb, 0, st>>>(T, I + o_pxr, part_px);
             b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_px, sc, 0);
             b_scale_v<<<npxr, tb, 0, st>>>(T, I + o_pxr, sc);
@@ -723,7 +734,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     for (int q = 0; q < n; ++q) identity = identity && tv[q].beta == 0.0f;
     for (int k = 0; k < opts->n_iter && !rc; ++k) {
         const int par = k & 1;   // 0: x_new -> xb, 1: x_new -> xa
-        rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st);
+        rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st, P.bpNA);
         if (rc) break;
         if (!identity) {                        // the last Chambolle launch writes x_new
             rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, nchf, I + o_chf, sc, opts->tau, opts->n_inner, par,

@@ -255,3 +255,36 @@ def test_pnp_solve_matches_oracle():
     xg = x[0].cpu().numpy().astype(np.float64)
     assert np.linalg.norm(xg - xr) <= 5e-3 * np.linalg.norm(xr)
     np.testing.assert_allclose(e[0].cpu().numpy(), er, rtol=1e-2)
+
+
+def test_wait_give_up_is_reported_and_the_next_call_succeeds():
+    """Failure detection without a GPU fault.  With the tensor-core kernels'
+    pipeline waits set to give up without polling, the first wait of a
+    16 x 256^2 forward pass runs out: the kernel stops issuing
+    work, drains the tensor-core operations it already issued (that wait keeps
+    the default limit), frees its tensor memory and returns, and the device
+    status word carries bit 1.  With the default limit restored, the next
+    call is bit-exact against the oracle and sets no bit."""
+    import paper_1306_1392_b300 as P
+    dev = torch.device("cuda:0")
+    params = _integer_params(7)
+    pd = torch.from_numpy(params).to(dev)
+    g = np.random.default_rng(7)
+    zbig = torch.from_numpy(g.integers(0, 8, (16, 256, 256)).astype(np.float32)).to(dev)
+    P.pyhst_device_status(clear=True)
+    hit = 0
+    try:
+        P.pyhst_set_wait_limit(0)
+        for _ in range(2):
+            P.pyhst_cnn_forward(pd, zbig)
+            torch.cuda.synchronize()
+            hit |= P.pyhst_device_status(clear=True)
+            if hit:
+                break
+    finally:
+        P.pyhst_set_wait_limit(-1)
+    assert hit & 1
+    z = g.integers(0, 8, (1, 40, 200)).astype(np.float32)
+    out = _run(params, z)                       # asserts the status word is clear again
+    ref, _, _ = cnn.forward(params, z[0], rounding=True)
+    np.testing.assert_array_equal(out[0], ref)

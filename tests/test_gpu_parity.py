@@ -438,3 +438,50 @@ def test_fbp_filters(P, orc, cuda_device, filt, pad):
         close(f64(q[z]), qr)
         ref = orc.backproject(qr, ang.astype(np.float64), np.full(60, 38.0), 70, 64, orc.fbp_weight(60, 2 / 77))
         close(f64(got[z]), ref)
+
+
+# ------------------------------------------------------------------ autotuned back-projector block
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3], (50, 256, 256, 256, "uniform", 0.0, 7),
+                                  (100, 512, 512, 512, "uniform", 0.0, 8)])
+def test_backproject_angle_blocks_are_identical(P, orc, cuda_device, case):
+    """Every angle block (8, 16, 24 angles staged per CTA) gives the same
+    bits, within the oracle bar; the autotuner picks one of them and the
+    tuned call still gives the same bits."""
+    na, nb, nx, ny, kind, off, seed = case
+    g, ang, axis, geo = _case(P, cuda_device, *case)
+    sino = torch.from_numpy(g.standard_normal((2, na, nb)).astype(np.float32)).to(cuda_device)
+    outs = {}
+    try:
+        for blk in (8, 16, 24):
+            P.pyhst_set_backproject_block(nx, ny, na, blk)
+            outs[blk] = P.pyhst_backproject(geo, sino, 0.37)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[8], outs[16]) and torch.equal(outs[24], outs[16])
+        best = P.pyhst_autotune_backproject(geo, sino)
+        assert best in (8, 16, 24)
+        assert torch.equal(P.pyhst_backproject(geo, sino, 0.37), outs[16])
+    finally:
+        P.pyhst_set_backproject_block(nx, ny, na, 0)
+    ref = orc.backproject(sino[0].double().cpu().numpy(), ang.astype(np.float64), axis.astype(np.float64), nx, ny,
+                          0.37)
+    close(f64(outs[16][0]), ref)
+
+
+def test_tv_batch_with_tuned_back_projector_block(P, cuda_device):
+    """The batched solver takes the block of its geometry with the most
+    updates; its iterates are bitwise those of the default block."""
+    dev = cuda_device
+    items = []
+    for k, (n, na) in enumerate([(256, 50), (128, 30), (256, 50)]):
+        fs = acq.foam_slice(n, na, seed=900 + k, truth=False)
+        geo = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), n, n, n, fs.pixel_size)
+        items.append((geo, fs.extra["sino"].to(dev).contiguous(), None))
+    opts = P.TvOptions(beta=2e-3, n_iter=6, n_inner=10, lipschitz=50.0)
+    xs0, _, _ = P.pyhst_tv_solve_batch(items, opts)
+    try:
+        P.pyhst_set_backproject_block(256, 256, 50, 8)
+        xs1, _, _ = P.pyhst_tv_solve_batch(items, opts)
+    finally:
+        P.pyhst_set_backproject_block(256, 256, 50, 0)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(xs0, xs1))

@@ -155,3 +155,36 @@ def test_patch_rejects_bad_arguments():
 def ctypes_byref(s):
     import ctypes
     return ctypes.byref(s)
+
+
+def test_product_wait_give_up_is_reported_and_the_next_call_succeeds(orc):
+    """As for the CNN: with pipeline waits that give up without polling the
+    tensor-core patch product gives up, drains its issued operations, frees its tensor memory
+    and records bit 1; with the default limit the next gradient matches the
+    oracle and sets no bit."""
+    import paper_1306_1392_b300 as P
+    dev = torch.device("cuda:0")
+    gen = np.random.default_rng(3)
+    Dm = (gen.standard_normal((96, 64)) / 8).astype(np.float32)
+    pp = P.PatchProblem(400, 400, 8, 4, torch.from_numpy(Dm).to(dev), 0.8)
+    W = torch.from_numpy(gen.standard_normal(pp.coef_shape()).astype(np.float32)).to(dev)
+    y = torch.from_numpy(gen.standard_normal((400, 400)).astype(np.float32)).to(dev)
+    P.pyhst_device_status(clear=True)
+    hit = 0
+    try:
+        P.pyhst_set_wait_limit(0)
+        for _ in range(2):
+            P.pyhst_patch_gradient(pp, None, W, y)
+            torch.cuda.synchronize()
+            hit |= P.pyhst_device_status(clear=True)
+            if hit:
+                break
+    finally:
+        P.pyhst_set_wait_limit(-1)
+    assert hit & 1
+    G, _ = P.pyhst_patch_gradient(pp, None, W, y)
+    torch.cuda.synchronize()
+    assert P.pyhst_device_status(clear=True) == 0
+    opp = orc.PatchProblem(400, 400, 8, 4, Dm.astype(np.float64), float(np.float32(0.8)))
+    Gr = opp.gradient(W.cpu().double().numpy(), y.cpu().double().numpy())
+    assert np.linalg.norm(G.cpu().numpy() - Gr) / np.linalg.norm(Gr) <= 1e-5
