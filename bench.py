@@ -332,10 +332,16 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20, cpu_seconds=20.0):
     opts = P.TvOptions(beta=1e-3, n_iter=n_iter, n_inner=n_inner, n_power_iter=n_power_iter)
     # autotune the Chambolle steps fused per launch for each slice size (results
     # do not depend on it); outside the timed region
-    tuned = {}
+    tuned, tuned_bp, tuned_pw = {}, {}, {}
     for n in sorted(geos):
         z = torch.randn((4, n, n), device=dev, generator=torch.Generator(device=dev).manual_seed(n))
         tuned[str(n)] = P.pyhst_autotune_tv_prox(z, 0.01, n_inner)
+        # the back-projector's angle block for this geometry (identical results), on 16 of its sinograms
+        sinos = torch.stack([it[1] for it in items if it[0] is geos[n]][:16]).contiguous()
+        tuned_bp[str(n)] = P.pyhst_autotune_backproject(geos[n], sinos)
+        # and the projector's staging width (identical results), on 16 images of that size
+        imgs = torch.rand((16, n, n), device=dev, generator=torch.Generator(device=dev).manual_seed(n + 1))
+        tuned_pw[str(n)] = P.pyhst_autotune_project(geos[n], imgs)
     P.pyhst_tv_solve_batch(items, P.TvOptions(beta=1e-3, n_iter=2, n_inner=n_inner, n_power_iter=2))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -387,7 +393,8 @@ def run_tv(dev, n_slices=128, n_iter=200, n_inner=20, cpu_seconds=20.0):
            "psnr_tv_mean": float(np.mean(ps_tv)), "psnr_fbp_mean": float(np.mean(ps_fbp)),
            "psnr_tv_by_size": {k: float(np.mean(v)) for k, v in by.items()},
            "energy_lower_at_end_fraction": mono, "beta": {str(k): v for k, v in TV_BETA.items()},
-           "chambolle_steps_per_launch": tuned,
+           "chambolle_steps_per_launch": tuned, "backproject_angles_per_block": tuned_bp,
+           "project_staging_columns": tuned_pw,
            "kernels": rates, "roofline": roof,
            "profiled_solve_s": ms_prof * 1e-3, "profiled_iterates_equal": same,
            "prox_gap_after_n_inner": gap_rep}

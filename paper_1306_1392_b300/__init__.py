@@ -707,6 +707,30 @@ def pyhst_autotune_backproject(geom: Geometry, sino: torch.Tensor, out=None, wor
     return int(best.value)
 
 
+def pyhst_autotune_project(geom: Geometry, img: torch.Tensor, out=None, workspace=None) -> int:
+    """Time the projector's staging widths (256, 512 columns; identical
+    results) on img [n_slices, ny, nx] and record the faster for the
+    geometry; returns it."""
+    img = _stack3(_cuda(img, "img", (torch.float32,)), "img")
+    ns = img.shape[0]
+    if tuple(img.shape[1:]) != (geom.ny, geom.nx):
+        raise ValueError("image shape does not match the geometry")
+    if out is None:
+        out = torch.empty((ns, geom.n_angles, geom.n_bins), dtype=torch.float32, device=img.device)
+    _cuda(out, "out", (torch.float32,))
+    g = geom.c(ns)
+    ws = _workspace(L.lib.pyhst_workspace_size(ctypes.byref(g), PYHST_OP_PROJECT), img.device, workspace)
+    best = ctypes.c_int32(0)
+    _check(L.lib.pyhst_autotune_project(ctypes.byref(g), _ptr(img), _ptr(out), _ptr(ws), ws.numel(),
+                                        ctypes.byref(best), _stream()))
+    return int(best.value)
+
+
+def pyhst_set_project_staging(nx: int, ny: int, n_angles: int, width: int) -> None:
+    """Record the projector's staging width (256 or 512) for a geometry (0 clears)."""
+    _check(L.lib.pyhst_set_project_staging(int(nx), int(ny), int(n_angles), int(width)))
+
+
 def pyhst_set_backproject_block(nx: int, ny: int, n_angles: int, angles_per_block: int) -> None:
     """Record the back-projector's angle block for a geometry (0 clears)."""
     _check(L.lib.pyhst_set_backproject_block(int(nx), int(ny), int(n_angles), int(angles_per_block)))

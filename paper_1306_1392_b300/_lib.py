@@ -93,6 +93,9 @@ SIGNATURES = [
     ("pyhst_autotune_backproject", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_void_p, c_size_t,
                                              ctypes.POINTER(c_int32), c_void_p]),
     ("pyhst_set_backproject_block", c_int32, [c_int32, c_int32, c_int32, c_int32]),
+    ("pyhst_autotune_project", c_int32, [ctypes.POINTER(pyhst_geometry), c_void_p, c_void_p, c_void_p, c_size_t,
+                                         ctypes.POINTER(c_int32), c_void_p]),
+    ("pyhst_set_project_staging", c_int32, [c_int32, c_int32, c_int32, c_int32]),
     ("pyhst_autotune_tv_prox", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_float, c_int32, c_float, c_void_p,
                                          c_size_t, ctypes.POINTER(c_int32), c_void_p]),
     ("pyhst_set_tv_prox_steps", c_int32, [c_int32, c_int32, c_int32]),

@@ -112,59 +112,78 @@ __device__ __forceinline__ void chambolle_steps_regs(float (&zl)[kChRows][2], fl
     }
 }
 
-// xout == nullptr: write the dual field of the central tile to q1, q2.
-// Otherwise (the last launch of a prox) write the prox itself to xout,
-// x = z - lam div p: the divergence's four terms added in a fixed order,
-// those across the image border left out, then one fma; with keep_p the
-// dual field is written to q1, q2 as well (for the duality gap).
-template <int kChK>
-__device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
-                                               const float *__restrict__ p2, float *__restrict__ q1,
-                                               float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
-                                               int j0, int steps, bool first, float *__restrict__ xout = nullptr,
-                                               bool keep_p = false) {
+// One tile's K steps.  kEdge: the loaded region touches the image border or
+// its last row or column (see chambolle_tile); otherwise every cell of the
+// region is inside the image, so the loads, the steps and the stores need no
+// bounds checks and address the image by constant row offsets.
+template <int kChK, bool kEdge>
+__device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z, const float *__restrict__ p1,
+                                                    const float *__restrict__ p2, float *__restrict__ q1,
+                                                    float *__restrict__ q2, float lam, float inv_lam, float tau,
+                                                    int nx, int ny, int ri0, int rj0, int steps, bool first,
+                                                    float *__restrict__ xout, bool keep_p) {
     extern __shared__ __align__(16) float ch_smem[];
     float(*xp)[kChR] = reinterpret_cast<float(*)[kChR]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
     float(*xg)[kChR] = xp + (kChR / kChRows + 1);                       // xg[w]: first G row of strip w
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int ri0 = i0 - kChK - 1, rj0 = j0 - kChK - 1;   // global coordinates of region cell (0, 0)
     const int r0 = kChRows * w + 1, c0 = 2 * tx + 1;      // this thread's first region row and column
     float zl[kChRows][2], a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
     unsigned in_mask = 0;                                  // bit 2i + j: cell (i, j) inside the image
+    if (!kEdge) {
+        const size_t base = (size_t)(ri0 + r0) * nx + (size_t)(rj0 + c0);
+        const float *zr = z + base;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) m2[j] = (rj0 + c0 + j + 1 < nx) ? 1.0f : 0.0f;
+        for (int i = 0; i < kChRows; ++i, zr += nx) {
+            m1[i] = 1.0f;
+            zl[i][0] = __fmul_rn(zr[0], inv_lam);
+            zl[i][1] = __fmul_rn(zr[1], inv_lam);
+        }
+        if (first) {
 #pragma unroll
-    for (int i = 0; i < kChRows; ++i) {
-        const int gi = ri0 + r0 + i;
-        m1[i] = (gi + 1 < ny) ? 1.0f : 0.0f;
+            for (int i = 0; i < kChRows; ++i) a1[i][0] = a1[i][1] = a2[i][0] = a2[i][1] = 0.0f;
+        } else {
+            const float *r1 = p1 + base, *r2 = p2 + base;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int gj = rj0 + c0 + j;
-            float vz = 0.0f, v1 = 0.0f, v2 = 0.0f;
-            if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
-                in_mask |= 1u << (2 * i + j);
-                const size_t k = (size_t)gi * nx + gj;
-                vz = __fdiv_rn(z[k], lam);
-                if (!first) {
-                    v1 = p1[k];
-                    v2 = p2[k];
-                }
+            for (int i = 0; i < kChRows; ++i, r1 += nx, r2 += nx) {
+                a1[i][0] = r1[0];
+                a1[i][1] = r1[1];
+                a2[i][0] = r2[0];
+                a2[i][1] = r2[1];
             }
-            zl[i][j] = vz;
-            a1[i][j] = v1;
-            a2[i][j] = v2;
+        }
+        m2[0] = m2[1] = 1.0f;
+        in_mask = 0xFFFFu;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) m2[j] = (rj0 + c0 + j + 1 < nx) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int i = 0; i < kChRows; ++i) {
+            const int gi = ri0 + r0 + i;
+            m1[i] = (gi + 1 < ny) ? 1.0f : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int gj = rj0 + c0 + j;
+                float vz = 0.0f, v1 = 0.0f, v2 = 0.0f;
+                if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
+                    in_mask |= 1u << (2 * i + j);
+                    const size_t k = (size_t)gi * nx + gj;
+                    vz = __fmul_rn(z[k], inv_lam);
+                    if (!first) {
+                        v1 = p1[k];
+                        v2 = p2[k];
+                    }
+                }
+                zl[i][j] = vz;
+                a1[i][j] = v1;
+                a2[i][j] = v2;
+            }
         }
     }
     if (w == 0) *reinterpret_cast<float2 *>(&xp[0][2 * tx]) = make_float2(0.0f, 0.0f);
     if (w == kChR / kChRows - 1) *reinterpret_cast<float2 *>(&xg[kChR / kChRows][2 * tx]) = make_float2(0.0f, 0.0f);
     *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
     __syncthreads();
-    // the whole region inside the image and clear of its last row and column
-    const bool interior = ri0 + 1 >= 0 && ri0 + kChR + 1 < ny && rj0 + 1 >= 0 && rj0 + kChR + 1 < nx;
-    if (interior)
-        chambolle_steps_regs<false>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
-    else
-        chambolle_steps_regs<true>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
+    chambolle_steps_regs<kEdge>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
     // write the central tile: region rows and columns kChK + 1 .. kChR - kChK
     if (xout) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
@@ -175,15 +194,16 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int r = r0 + i, c = c0 + j, gi = ri0 + r, gj = rj0 + c;
-                if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && gi < ny && gj < nx) {
+                // inside the image the region is clear of the border: all four divergence terms exist
+                if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && (!kEdge || (gi < ny && gj < nx))) {
                     const size_t k = (size_t)gi * nx + gj;
                     const float pu = i > 0 ? a1[i - 1][j] : (j == 0 ? up.x : up.y);
                     const float pl = j > 0 ? a2[i][0] : left;
                     float dv = 0.0f;
-                    if (gi + 1 < ny) dv += a1[i][j];
-                    if (gi > 0) dv -= pu;
-                    if (gj + 1 < nx) dv += a2[i][j];
-                    if (gj > 0) dv -= pl;
+                    if (!kEdge || gi + 1 < ny) dv += a1[i][j];
+                    if (!kEdge || gi > 0) dv -= pu;
+                    if (!kEdge || gj + 1 < nx) dv += a2[i][j];
+                    if (!kEdge || gj > 0) dv -= pl;
                     xout[k] = fmaf(-lam, dv, z[k]);
                     if (keep_p) {
                         q1[k] = a1[i][j];
@@ -199,12 +219,38 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int r = r0 + i, c = c0 + j, gi = ri0 + r, gj = rj0 + c;
-            if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && gi < ny && gj < nx) {
+            if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && (!kEdge || (gi < ny && gj < nx))) {
                 const size_t k = (size_t)gi * nx + gj;
                 q1[k] = a1[i][j];
                 q2[k] = a2[i][j];
             }
         }
+}
+
+// K steps on the tile whose output corner is (i0, j0): the region loaded is
+// rows i0 - K - 1 + 1 .. i0 - K - 1 + 64 and the same columns.
+// xout == nullptr: write the dual field of the central tile to q1, q2.
+// Otherwise (the last launch of a prox) write the prox itself to xout,
+// x = z - lam div p: the divergence's four terms added in a fixed order,
+// those across the image border left out, then one fma; with keep_p the
+// dual field is written to q1, q2 as well (for the duality gap).
+// z / lam is formed as z times the correctly rounded reciprocal of lam.
+template <int kChK>
+__device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
+                                               const float *__restrict__ p2, float *__restrict__ q1,
+                                               float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
+                                               int j0, int steps, bool first, float *__restrict__ xout = nullptr,
+                                               bool keep_p = false) {
+    const int ri0 = i0 - kChK - 1, rj0 = j0 - kChK - 1;   // global coordinates of region cell (0, 0)
+    const float inv_lam = __frcp_rn(lam);
+    // the whole region inside the image and clear of its last row and column
+    const bool interior = ri0 + 1 >= 0 && ri0 + kChR + 1 < ny && rj0 + 1 >= 0 && rj0 + kChR + 1 < nx;
+    if (interior)
+        chambolle_tile_body<kChK, false>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps, first, xout,
+                                         keep_p);
+    else
+        chambolle_tile_body<kChK, true>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps, first, xout,
+                                        keep_p);
 }
 
 // Launch plan of n_inner steps: launch m runs steps(m) steps, the first

@@ -96,8 +96,9 @@ int bp_block_for(int nx, int ny, int n_angles);
 // Projector: img [n_slices][ny][nx] -> sino [n_slices][n_angles][n_bins],
 // scaled by `scale`; `xt` is scratch for the transposed slice stack
 // ([n_slices][nx][ny] floats).
+// staging: 256 or 512 columns; <= 0 takes the tuned or rule-based choice (project_wide)
 int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
-                   float scale, float *xt, cudaStream_t st);
+                   float scale, float *xt, cudaStream_t st, int staging = 0);
 size_t project_scratch_bytes(const pyhst_geometry *g);
 
 // ----------------------------------------------------------------- mixed batches
@@ -122,7 +123,8 @@ int bp_tiles(int nx, int ny, int *tx, int *ty);
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
                              cudaStream_t st, int angle_block = 16);
 int proj_blocks(int n_angles, int n_bins, int *nb, int *na);
-// true: the 512-column staging variant of the projector (sparse angle sets)
+// true: the 512-column staging variant of the projector (the autotuned choice
+// for the geometry, else for sparse angle sets); either gives the same bits
 bool project_wide(int nx, int ny, int n_angles);
 // row segments of the projector's walks for a slice geometry (fixes the float32 summation order)
 int proj_segments(const pyhst_geometry *g);

@@ -42,6 +42,9 @@
 #include <cmath>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -127,6 +130,47 @@ __device__ __forceinline__ void chunk_band(const RayGeom *rg, int mask, int b0, 
     }
     L0 = lo & ~3;   // float4-aligned start
     H = hi;
+}
+
+// Chunks [out[0], out[1]) outside of which no ray of the masked angles has a
+// tap inside the array's columns [0, C) (warp 0; result in lane 0): on the
+// rows outside, every tap reads a zero staged outside the image and adds an
+// exact zero, so skipping them changes no bits.  The range is widened by
+// margins (3 columns, 2 rows, one chunk), never narrowed.
+__device__ __forceinline__ void chunk_clip(const RayGeom *rg, int mask, int b0, int bhi, int R, int C, int *out) {
+    const int lane = threadIdx.x & 31;
+    int lo = INT_MAX, hi = INT_MIN;
+    if (lane < kPG && ((mask >> lane) & 1)) {
+        const RayGeom g = rg[lane];
+        // x*(b, r) = A_b - r rho over the bins b0 .. bhi: its extremes are at the end bins
+        const double A0 = (double)(g.X0 + (long long)b0 * g.dX) / kFix;
+        const double A1 = (double)(g.X0 + (long long)bhi * g.dX) / kFix;
+        const double rho = (double)g.rho / kFix, amax = fmax(A0, A1), amin = fmin(A0, A1);
+        double rl = 0.0, rh = (double)(R - 1);
+        if (rho > 0.0) {
+            rh = fmin(rh, (amax + 3.0) / rho);
+            rl = fmax(rl, (amin - C - 2.0) / rho);
+        } else if (rho < 0.0) {
+            rl = fmax(rl, (amax + 3.0) / rho);
+            rh = fmin(rh, (amin - C - 2.0) / rho);
+        } else if (amax < -3.0 || amin > C + 2.0) {
+            rl = 1.0;
+            rh = 0.0;
+        }
+        if (rl <= rh) {
+            lo = (int)floor(rl) - 2;
+            hi = (int)ceil(rh) + 2;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+        const int nch = (R + kPR - 1) / kPR;
+        out[0] = lo == INT_MAX ? 0 : max(0, lo / kPR);
+        out[1] = hi == INT_MIN ? 0 : min(nch, hi / kPR + 1);
+    }
 }
 
 struct WalkArgs {
@@ -289,7 +333,7 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
     float (*strip)[kPR][kPW] = reinterpret_cast<float (*)[kPR][kPW]>(proj_smem);
     __shared__ RayGeom rg[kPG];
     __shared__ int L0_s[3], H_s[3];
-    __shared__ int phase_mask[2], fits_s;
+    __shared__ int phase_mask[2], fits_s, clip_s[2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = b0 + 16 * warp + (lane & 15);
@@ -348,7 +392,13 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
         const int c_lo = seg >= 0 ? seg * per : 0, c_hi = seg >= 0 ? min(nch, c_lo + per) : nch;
         for (int s0 = 0; s0 < kPG; s0 += gs) {
             const int m = mask_all & (((1 << gs) - 1) << s0);
-            if (m) walk_pass(w, rg, m, acc, tot, scale, per, strip, L0_s, H_s, c_lo, c_hi);
+            if (!m) continue;
+            // only the chunks where some ray of the subset meets the image
+            if (warp == 0) chunk_clip(rg, m, b0, bhi, w.R, w.C, clip_s);
+            __syncthreads();
+            const int cl = max(c_lo, clip_s[0]), ch = min(c_hi, clip_s[1]);
+            __syncthreads();
+            walk_pass(w, rg, m, acc, tot, scale, per, strip, L0_s, H_s, cl, ch);
         }
         __syncthreads();
     }
@@ -418,9 +468,27 @@ __global__ void transpose_batch_kernel(const BatchSlice *__restrict__ slices, co
 
 }  // namespace
 
-// Sparse angle sets (image size / number of angles > 2) take the 512-column
-// staging buffer: their 8-angle bands rarely fit 256 columns.
-bool project_wide(int nx, int ny, int n_angles) { return (double)std::max(nx, ny) > 2.0 * n_angles; }
+// Staging width: the autotuned choice for the geometry (pyhst_autotune_project,
+// pyhst_set_project_staging) if there is one; else sparse angle sets (image
+// size / number of angles > 2) take the 512-column staging buffer, since
+// their 8-angle bands rarely fit 256 columns.  Both widths walk every ray
+// with the same fixed-point positions and sum order, so the choice changes
+// no bits.
+namespace {
+std::mutex g_pw_mu;
+std::map<std::tuple<int, int, int, int>, int> g_pw_tune;   // (device, nx, ny, n_angles) -> 256 or 512
+}  // namespace
+
+bool project_wide(int nx, int ny, int n_angles) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_pw_mu);
+        auto it = g_pw_tune.find(std::make_tuple(dev, nx, ny, n_angles));
+        if (it != g_pw_tune.end()) return it->second == 512;
+    }
+    return (double)std::max(nx, ny) > 2.0 * n_angles;
+}
 
 int set_proj_attr() {
     static bool done[64] = {};
@@ -512,7 +580,7 @@ size_t project_scratch_bytes(const pyhst_geometry *g) {
 }
 
 int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
-                   float scale, float *xt, cudaStream_t st) {
+                   float scale, float *xt, cudaStream_t st, int staging) {
     if (g->n_slices > 65535) return fail(PYHST_ERR_INVALID_ARG, "too many slices in one call (%d)", g->n_slices);
     dim3 tb(32, 8), tg((g->nx + 31) / 32, (g->ny + 31) / 32, g->n_slices);
     transpose_kernel<<<tg, tb, 0, st>>>(img, xt, g->ny, g->nx);
@@ -526,7 +594,8 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     {
         ProfScope prof(kProfProject, st);
         float *dst = split ? part : sino;
-        if (project_wide(g->nx, g->ny, g->n_angles))
+        const bool wide = staging > 0 ? staging == 512 : project_wide(g->nx, g->ny, g->n_angles);
+        if (wide)
             proj_kernel<512><<<grid, kPThreads, psmem<512>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
                                                                     g->ny, g->cx, g->cy, scale, nseg, split);
         else
@@ -543,6 +612,67 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
 }
 
 }  // namespace pyhst
+
+extern "C" int pyhst_set_project_staging(int32_t nx, int32_t ny, int32_t n_angles, int32_t width) {
+    using namespace pyhst;
+    if (nx < 1 || ny < 1 || n_angles < 1) return fail(PYHST_ERR_INVALID_ARG, "image %d x %d, %d angles", nx, ny, n_angles);
+    if (width != 0 && width != 256 && width != 512)
+        return fail(PYHST_ERR_INVALID_ARG, "staging width %d: need 256 or 512 (0 clears)", width);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_pw_mu);
+    const auto key = std::make_tuple(dev, (int)nx, (int)ny, (int)n_angles);
+    if (width == 0)
+        g_pw_tune.erase(key);
+    else
+        g_pw_tune[key] = width;
+    return PYHST_OK;
+}
+
+extern "C" int pyhst_autotune_project(const pyhst_geometry *g, const float *img, float *sino, void *workspace,
+                                      size_t ws_bytes, int32_t *best, pyhst_stream_t stream) {
+    using namespace pyhst;
+    int rc = check_geometry(g);
+    if (rc) return rc;
+    if (!img || !sino) return fail(PYHST_ERR_INVALID_ARG, "img/sino pointer is NULL");
+    const size_t need = pyhst_workspace_size(g, PYHST_OP_PROJECT);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign))
+        return fail(PYHST_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv(workspace, ws_bytes);
+    AngleInfo *tab = cv.take<AngleInfo>(g->n_angles);
+    float *xt = cv.take<float>(project_scratch_bytes(g) / sizeof(float));
+    if ((rc = launch_angle_table(g->angles, g->axis, g->n_angles, tab, st))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_status("autotune events");
+    }
+    int pick = project_wide(g->nx, g->ny, g->n_angles) ? 512 : 256;
+    float best_ms = 1e30f;
+    for (int width : {256, 512}) {
+        if ((rc = launch_project(g, tab, img, sino, g->pixel_size, xt, st, width))) break;   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && !rc; ++r) rc = launch_project(g, tab, img, sino, g->pixel_size, xt, st, width);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = cuda_status("autotune timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            pick = width;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best) *best = pick;
+    return pyhst_set_project_staging(g->nx, g->ny, g->n_angles, pick);
+}
 
 extern "C" int pyhst_project(const pyhst_geometry *g, const float *img, float *sino, void *workspace,
                              size_t ws_bytes, pyhst_stream_t stream) {

@@ -485,3 +485,28 @@ def test_tv_batch_with_tuned_back_projector_block(P, cuda_device):
         P.pyhst_set_backproject_block(256, 256, 50, 0)
     torch.cuda.synchronize()
     assert all(torch.equal(a, b) for a, b in zip(xs0, xs1))
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[5], (50, 256, 256, 256, "uniform", 0.0, 7),
+                                  (200, 1024, 1024, 1024, "uniform", 0.0, 9)])
+def test_project_staging_widths_are_identical(P, orc, cuda_device, case):
+    """Both staging widths of the projector (256 and 512 columns) give the
+    same bits, within the oracle bar; the autotuner picks one of them."""
+    na, nb, nx, ny, kind, off, seed = case
+    g, ang, axis, geo = _case(P, cuda_device, *case)
+    img = torch.from_numpy(g.standard_normal((2, ny, nx)).astype(np.float32)).to(cuda_device)
+    outs = {}
+    try:
+        for width in (256, 512):
+            P.pyhst_set_project_staging(nx, ny, na, width)
+            outs[width] = P.pyhst_project(geo, img)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[256], outs[512])
+        best = P.pyhst_autotune_project(geo, img)
+        assert best in (256, 512)
+        assert torch.equal(P.pyhst_project(geo, img), outs[256])
+    finally:
+        P.pyhst_set_project_staging(nx, ny, na, 0)
+    ref = orc.project(img[0].double().cpu().numpy(), ang.astype(np.float64), axis.astype(np.float64), nb,
+                      geo.pixel_size)
+    close(f64(outs[256][0]), ref)
