@@ -340,13 +340,13 @@ int pyhst_autotune_backproject(const pyhst_geometry *g, const float *sino, float
 int pyhst_set_backproject_block(int32_t nx, int32_t ny, int32_t n_angles, int32_t angles_per_block);
 
 /* Autotuning of the projector.  A CTA stages, per 16 image rows, the band of
- * columns its rays cross, in a buffer of 256 or 512 columns (a band that does
- * not fit is walked in smaller angle subsets); the width trades shared memory
- * and staging work against those extra walks, and gives identical results
- * (every ray is walked with the same fixed-point positions, in the same row
- * order).  pyhst_autotune_project times both widths on the caller's images
+ * columns its rays cross, in a buffer of 256, 384 or 512 columns (a band that
+ * does not fit is walked in smaller angle subsets); the width trades shared
+ * memory and staging work against those extra walks, and gives identical
+ * results (every ray is walked with the same fixed-point positions, in the
+ * same row order).  pyhst_autotune_project times every width on the caller's images
  * img [n_slices][ny][nx] (DEVICE; sino receives the projection, workspace as
- * pyhst_project's), synchronizing `stream`, and records the faster for
+ * pyhst_project's), synchronizing `stream`, and records the fastest for
  * (nx, ny, n_angles) on the current device; pyhst_project, the TV solvers and
  * pyhst_tv_solve_batch (per slice geometry) then use it.
  * pyhst_set_project_staging records a choice directly (0 clears it; the

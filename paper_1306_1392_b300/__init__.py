@@ -708,8 +708,8 @@ def pyhst_autotune_backproject(geom: Geometry, sino: torch.Tensor, out=None, wor
 
 
 def pyhst_autotune_project(geom: Geometry, img: torch.Tensor, out=None, workspace=None) -> int:
-    """Time the projector's staging widths (256, 512 columns; identical
-    results) on img [n_slices, ny, nx] and record the faster for the
+    """Time the projector's staging widths (256, 384, 512 columns; identical
+    results) on img [n_slices, ny, nx] and record the fastest for the
     geometry; returns it."""
     img = _stack3(_cuda(img, "img", (torch.float32,)), "img")
     ns = img.shape[0]
@@ -727,7 +727,7 @@ def pyhst_autotune_project(geom: Geometry, img: torch.Tensor, out=None, workspac
 
 
 def pyhst_set_project_staging(nx: int, ny: int, n_angles: int, width: int) -> None:
-    """Record the projector's staging width (256 or 512) for a geometry (0 clears)."""
+    """Record the projector's staging width (256, 384 or 512) for a geometry (0 clears)."""
     _check(L.lib.pyhst_set_project_staging(int(nx), int(ny), int(n_angles), int(width)))
 
 

@@ -96,7 +96,7 @@ int bp_block_for(int nx, int ny, int n_angles);
 // Projector: img [n_slices][ny][nx] -> sino [n_slices][n_angles][n_bins],
 // scaled by `scale`; `xt` is scratch for the transposed slice stack
 // ([n_slices][nx][ny] floats).
-// staging: 256 or 512 columns; <= 0 takes the tuned or rule-based choice (project_wide)
+// staging: 256, 384 or 512 columns; <= 0 takes the tuned or rule-based choice (project_width)
 int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
                    float scale, float *xt, cudaStream_t st, int staging = 0);
 size_t project_scratch_bytes(const pyhst_geometry *g);
@@ -123,16 +123,17 @@ int bp_tiles(int nx, int ny, int *tx, int *ty);
 int launch_backproject_batch(const BatchSlice *slices, const int4 *items, int n_items, bool residual,
                              cudaStream_t st, int angle_block = 16);
 int proj_blocks(int n_angles, int n_bins, int *nb, int *na);
-// true: the 512-column staging variant of the projector (the autotuned choice
-// for the geometry, else for sparse angle sets); either gives the same bits
-bool project_wide(int nx, int ny, int n_angles);
+// Staging width of the projector for a geometry: 256, 384 or 512 columns (the
+// autotuned choice, else 512 for sparse angle sets and 256 otherwise); every
+// width gives the same bits
+int project_width(int nx, int ny, int n_angles);
 // row segments of the projector's walks for a slice geometry (fixes the float32 summation order)
 int proj_segments(const pyhst_geometry *g);
 // Sets the projector kernels' shared-memory attributes (call before a
 // stream capture that launches them).
 int set_proj_attr();
 int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
-                         const int4 *tr_items, int n_tr_items, bool wide, cudaStream_t st);
+                         const int4 *tr_items, int n_tr_items, int width, cudaStream_t st);
 
 // ----------------------------------------------------------------- profiling
 // Opt-in per-launch timing (pyhst_profile_enable): events recorded on the

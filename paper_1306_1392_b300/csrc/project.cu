@@ -468,26 +468,26 @@ __global__ void transpose_batch_kernel(const BatchSlice *__restrict__ slices, co
 
 }  // namespace
 
-// Staging width: the autotuned choice for the geometry (pyhst_autotune_project,
-// pyhst_set_project_staging) if there is one; else sparse angle sets (image
-// size / number of angles > 2) take the 512-column staging buffer, since
-// their 8-angle bands rarely fit 256 columns.  Both widths walk every ray
-// with the same fixed-point positions and sum order, so the choice changes
-// no bits.
+// Staging width (256, 384 or 512 columns): the autotuned choice for the
+// geometry (pyhst_autotune_project, pyhst_set_project_staging) if there is
+// one; else sparse angle sets (image size / number of angles > 2) take 512
+// columns, since their 8-angle bands rarely fit 256, and the others 256.
+// Every width walks every ray with the same fixed-point positions and sum
+// order, so the choice changes no bits.
 namespace {
 std::mutex g_pw_mu;
 std::map<std::tuple<int, int, int, int>, int> g_pw_tune;   // (device, nx, ny, n_angles) -> 256 or 512
 }  // namespace
 
-bool project_wide(int nx, int ny, int n_angles) {
+int project_width(int nx, int ny, int n_angles) {
     int dev = 0;
     cudaGetDevice(&dev);
     {
         std::lock_guard<std::mutex> lk(g_pw_mu);
         auto it = g_pw_tune.find(std::make_tuple(dev, nx, ny, n_angles));
-        if (it != g_pw_tune.end()) return it->second == 512;
+        if (it != g_pw_tune.end()) return it->second;
     }
-    return (double)std::max(nx, ny) > 2.0 * n_angles;
+    return (double)std::max(nx, ny) > 2.0 * n_angles ? 512 : 256;
 }
 
 int set_proj_attr() {
@@ -497,9 +497,13 @@ int set_proj_attr() {
     if (dev >= 0 && dev < 64 && done[dev]) return PYHST_OK;
     if (cudaFuncSetAttribute(proj_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<256>()) !=
             cudaSuccess ||
+        cudaFuncSetAttribute(proj_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<384>()) !=
+            cudaSuccess ||
         cudaFuncSetAttribute(proj_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<512>()) !=
             cudaSuccess ||
         cudaFuncSetAttribute(proj_batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<256>()) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(proj_batch_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<384>()) !=
             cudaSuccess ||
         cudaFuncSetAttribute(proj_batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<512>()) !=
             cudaSuccess)
@@ -515,7 +519,7 @@ int proj_blocks(int n_angles, int n_bins, int *nb, int *na) {
 }
 
 int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
-                         const int4 *tr_items, int n_tr_items, bool wide, cudaStream_t st) {
+                         const int4 *tr_items, int n_tr_items, int width, cudaStream_t st) {
     if (n_tr_items > 0) {
         transpose_batch_kernel<<<n_tr_items, dim3(32, 8), 0, st>>>(slices, tr_items);
         int rc = cuda_status("batched transpose kernel");
@@ -525,8 +529,10 @@ int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n
     int rc = set_proj_attr();
     if (rc) return rc;
     ProfScope prof(kProfProject, st);
-    if (wide)
+    if (width == 512)
         proj_batch_kernel<512><<<n_proj_items, kPThreads, psmem<512>(), st>>>(slices, proj_items);
+    else if (width == 384)
+        proj_batch_kernel<384><<<n_proj_items, kPThreads, psmem<384>(), st>>>(slices, proj_items);
     else
         proj_batch_kernel<256><<<n_proj_items, kPThreads, psmem<256>(), st>>>(slices, proj_items);
     return cuda_status("batched projection kernel");
@@ -594,9 +600,12 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     {
         ProfScope prof(kProfProject, st);
         float *dst = split ? part : sino;
-        const bool wide = staging > 0 ? staging == 512 : project_wide(g->nx, g->ny, g->n_angles);
-        if (wide)
+        const int width = staging > 0 ? staging : project_width(g->nx, g->ny, g->n_angles);
+        if (width == 512)
             proj_kernel<512><<<grid, kPThreads, psmem<512>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
+                                                                    g->ny, g->cx, g->cy, scale, nseg, split);
+        else if (width == 384)
+            proj_kernel<384><<<grid, kPThreads, psmem<384>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
                                                                     g->ny, g->cx, g->cy, scale, nseg, split);
         else
             proj_kernel<256><<<grid, kPThreads, psmem<256>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
@@ -616,8 +625,8 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
 extern "C" int pyhst_set_project_staging(int32_t nx, int32_t ny, int32_t n_angles, int32_t width) {
     using namespace pyhst;
     if (nx < 1 || ny < 1 || n_angles < 1) return fail(PYHST_ERR_INVALID_ARG, "image %d x %d, %d angles", nx, ny, n_angles);
-    if (width != 0 && width != 256 && width != 512)
-        return fail(PYHST_ERR_INVALID_ARG, "staging width %d: need 256 or 512 (0 clears)", width);
+    if (width != 0 && width != 256 && width != 384 && width != 512)
+        return fail(PYHST_ERR_INVALID_ARG, "staging width %d: need 256, 384 or 512 (0 clears)", width);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
     std::lock_guard<std::mutex> lk(g_pw_mu);
@@ -648,9 +657,9 @@ extern "C" int pyhst_autotune_project(const pyhst_geometry *g, const float *img,
         if (e0) cudaEventDestroy(e0);
         return cuda_status("autotune events");
     }
-    int pick = project_wide(g->nx, g->ny, g->n_angles) ? 512 : 256;
+    int pick = project_width(g->nx, g->ny, g->n_angles);
     float best_ms = 1e30f;
-    for (int width : {256, 512}) {
+    for (int width : {256, 384, 512}) {
         if ((rc = launch_project(g, tab, img, sino, g->pixel_size, xt, st, width))) break;   // warm-up
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && !rc; ++r) rc = launch_project(g, tab, img, sino, g->pixel_size, xt, st, width);

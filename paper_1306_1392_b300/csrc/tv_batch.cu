@@ -401,9 +401,9 @@ struct Plan {
     std::vector<size_t> img_off, sino_off;      // per slice, in floats
     size_t img_total = 0, sino_total = 0;
     std::vector<int> px_first, sn_first;
-    // projector items of slices that take the 256-column variant come first
-    // (each slice uses the variant of its single-slice solve)
-    int proj_narrow = 0, proj_r_narrow = 0;
+    // projector items grouped by staging width (256, 384, 512 columns; each
+    // slice uses the width of its single-slice solve): counts per group
+    int proj_cnt[3] = {0, 0, 0}, proj_r_cnt[3] = {0, 0, 0};
     int chK = 5;     // Chambolle steps fused per launch (tuned for the largest slice)
     int bpNA = 16;   // back-projector angles per block (tuned for the geometry with the most updates)
 };
@@ -479,12 +479,25 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
         add_items(P, s, g, false);
     }
     for (int r : P.reps) add_items(P, r, items[r].geom, true);
-    auto narrow = [&](const int4 &it) {
+    auto width_group = [&](const int4 &it) {
         const pyhst_geometry &g = items[it.x].geom;
-        return !project_wide(g.nx, g.ny, g.n_angles);
+        const int w = project_width(g.nx, g.ny, g.n_angles);
+        return w == 256 ? 0 : (w == 384 ? 1 : 2);
     };
-    P.proj_narrow = (int)(std::stable_partition(P.proj.begin(), P.proj.end(), narrow) - P.proj.begin());
-    P.proj_r_narrow = (int)(std::stable_partition(P.proj_r.begin(), P.proj_r.end(), narrow) - P.proj_r.begin());
+    for (auto *v : {&P.proj, &P.proj_r}) {
+        std::vector<int> grp(v->size());
+        for (size_t q = 0; q < v->size(); ++q) grp[q] = width_group((*v)[q]);
+        std::vector<size_t> ord(v->size());
+        for (size_t q = 0; q < ord.size(); ++q) ord[q] = q;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return grp[a] < grp[b]; });
+        std::vector<int4> sorted(v->size());
+        int *cnt = v == &P.proj ? P.proj_cnt : P.proj_r_cnt;
+        for (size_t q = 0; q < ord.size(); ++q) {
+            sorted[q] = (*v)[ord[q]];
+            ++cnt[grp[ord[q]]];
+        }
+        v->swap(sorted);
+    }
     // Longest items first: CTAs start roughly in list order, so the long
     // items of the large slices run early and the short ones fill the last
     // wave.  A CTA's result does not depend on its place in the list.
@@ -497,10 +510,10 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
     };
     longest_first(P.bp.begin(), P.bp.end(), bp_cost);
     longest_first(P.bp_r.begin(), P.bp_r.end(), bp_cost);
-    longest_first(P.proj.begin(), P.proj.begin() + P.proj_narrow, proj_cost);
-    longest_first(P.proj.begin() + P.proj_narrow, P.proj.end(), proj_cost);
-    longest_first(P.proj_r.begin(), P.proj_r.begin() + P.proj_r_narrow, proj_cost);
-    longest_first(P.proj_r.begin() + P.proj_r_narrow, P.proj_r.end(), proj_cost);
+    for (int k = 0, o = 0, orr = 0; k < 3; o += P.proj_cnt[k], orr += P.proj_r_cnt[k], ++k) {
+        longest_first(P.proj.begin() + o, P.proj.begin() + o + P.proj_cnt[k], proj_cost);
+        longest_first(P.proj_r.begin() + orr, P.proj_r.begin() + orr + P.proj_r_cnt[k], proj_cost);
+    }
     return P;
 }
 
@@ -688,24 +701,25 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
 
     // ---- step size: power iteration on the representatives, or the caller's L
     if ((rc = set_proj_attr())) return rc;
-    // projector: the 256-column items, then the 512-column items
-    auto project = [&](const BatchSlice *D, size_t o_items, int n_items, int n_narrow, size_t o_tr, int n_tr) {
-        int r = launch_project_batch(D, I + o_items, n_narrow, I + o_tr, n_tr, false, st);
-        if (!r) r = launch_project_batch(D, I + o_items + n_narrow, n_items - n_narrow, nullptr, 0, true, st);
+    // projector: the transposes, then the items of each staging width (256, 384, 512 columns)
+    auto project = [&](const BatchSlice *D, size_t o_items, const int *cnt, size_t o_tr, int n_tr) {
+        int r = launch_project_batch(D, I + o_items, cnt[0], I + o_tr, n_tr, 256, st);
+        if (!r) r = launch_project_batch(D, I + o_items + cnt[0], cnt[1], nullptr, 0, 384, st);
+        if (!r) r = launch_project_batch(D, I + o_items + cnt[0] + cnt[1], cnt[2], nullptr, 0, 512, st);
         return r;
     };
     if (opts->lipschitz == 0.0) {
         const int npxr = (int)P.px_r.size(), nsnr = (int)P.sn_r.size();
         b_fill_v<<<npxr, tb, 0, st>>>(T, I + o_pxr);
         for (int it = 0; it < opts->n_power_iter; ++it) {
-            if ((rc = project(D_pow, o_projr, (int)P.proj_r.size(), P.proj_r_narrow, o_trr, (int)P.tr_r.size())))
+            if ((rc = project(D_pow, o_projr, P.proj_r_cnt, o_trr, (int)P.tr_r.size())))
                 return rc;
             if ((rc = launch_backproject_batch(D_pow, I + o_bpr, (int)P.bp_r.size(), false, st, P.bpNA))) return rc;
             b_sqnorm_g<<<npxr, tb, 0, st>>>(T, I + o_pxr, part_px);
             b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_px, sc, 0);
             b_scale_v<<<npxr, tb, 0, st>>>(T, I + o_pxr, sc);
         }
-        if ((rc = project(D_pow, o_projr, (int)P.proj_r.size(), P.proj_r_narrow, o_trr, (int)P.tr_r.size())))
+        if ((rc = project(D_pow, o_projr, P.proj_r_cnt, o_trr, (int)P.tr_r.size())))
             return rc;
         b_sqnorm_axa<<<nsnr, tb, 0, st>>>(T, I + o_snr, part_sn);
         b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_sn, sc, 1);
@@ -717,7 +731,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     // ---- start
     b_copy_x<<<npx, tb, 0, st>>>(T, I + o_px, opts->warm_start ? 1 : 0, 0);
     if (opts->warm_start)
-        if ((rc = project(D_init, o_proj, npr, P.proj_narrow, o_tr, ntr))) return rc;
+        if ((rc = project(D_init, o_proj, P.proj_cnt, o_tr, ntr))) return rc;
     b_copy_sino_start<<<nsn, tb, 0, st>>>(T, I + o_sn, opts->warm_start ? 1 : 0);
     if ((rc = cuda_status("batch start"))) return rc;
 
@@ -745,7 +759,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
             b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, 0, par, 1);
         }
         if (any_gap) b_finalize_gap<<<n, tb, 0, st>>>(T, part_gap, sc, k);
-        rc = project(par ? D_odd : D_even, o_proj, npr, P.proj_narrow, o_tr, ntr);
+        rc = project(par ? D_odd : D_even, o_proj, P.proj_cnt, o_tr, ntr);
         if (rc) break;
         double w = 0.0;
         if (opts->use_fista) {

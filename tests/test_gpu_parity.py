@@ -490,23 +490,46 @@ def test_tv_batch_with_tuned_back_projector_block(P, cuda_device):
 @pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[5], (50, 256, 256, 256, "uniform", 0.0, 7),
                                   (200, 1024, 1024, 1024, "uniform", 0.0, 9)])
 def test_project_staging_widths_are_identical(P, orc, cuda_device, case):
-    """Both staging widths of the projector (256 and 512 columns) give the
-    same bits, within the oracle bar; the autotuner picks one of them."""
+    """Every staging width of the projector (256, 384 and 512 columns) gives
+    the same bits, within the oracle bar; the autotuner picks one of them."""
     na, nb, nx, ny, kind, off, seed = case
     g, ang, axis, geo = _case(P, cuda_device, *case)
     img = torch.from_numpy(g.standard_normal((2, ny, nx)).astype(np.float32)).to(cuda_device)
     outs = {}
     try:
-        for width in (256, 512):
+        for width in (256, 384, 512):
             P.pyhst_set_project_staging(nx, ny, na, width)
             outs[width] = P.pyhst_project(geo, img)
         torch.cuda.synchronize()
-        assert torch.equal(outs[256], outs[512])
+        assert torch.equal(outs[256], outs[512]) and torch.equal(outs[384], outs[512])
         best = P.pyhst_autotune_project(geo, img)
-        assert best in (256, 512)
+        assert best in (256, 384, 512)
         assert torch.equal(P.pyhst_project(geo, img), outs[256])
     finally:
         P.pyhst_set_project_staging(nx, ny, na, 0)
     ref = orc.project(img[0].double().cpu().numpy(), ang.astype(np.float64), axis.astype(np.float64), nb,
                       geo.pixel_size)
     close(f64(outs[256][0]), ref)
+
+
+def test_tv_batch_with_three_projector_widths(P, cuda_device):
+    """Slices whose geometries take different staging widths run in one
+    batched solve (one projector launch per width); the iterates are bitwise
+    those of the batch with every slice at the default width."""
+    dev = cuda_device
+    items, sizes = [], [(256, 50), (128, 30), (192, 40)]
+    for k, (n, na) in enumerate(sizes):
+        fs = acq.foam_slice(n, na, seed=950 + k, truth=False)
+        geo = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), n, n, n, fs.pixel_size)
+        items.append((geo, fs.extra["sino"].to(dev).contiguous(), None))
+    opts = P.TvOptions(beta=2e-3, n_iter=5, n_inner=10, lipschitz=40.0)
+    xs0, _, _ = P.pyhst_tv_solve_batch(items, opts)
+    try:
+        for (n, na), w in zip(sizes, (256, 384, 512)):
+            P.pyhst_set_project_staging(n, n, na, w)
+        xs1, _, _ = P.pyhst_tv_solve_batch(items, opts)
+    finally:
+        for n, na in sizes:
+            P.pyhst_set_project_staging(n, n, na, 0)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(xs0, xs1))
