@@ -61,6 +61,7 @@ constexpr int kPRays = kPG / 2; // rays per thread
 template <int PW> __host__ __device__ constexpr int pvec() { return kPR * PW / 4 / kPThreads; }           // float4 per thread per chunk
 template <int PW> __host__ __device__ constexpr int psmem() { return 2 * kPR * PW * (int)sizeof(float); }  // double-buffered strip
 constexpr int kPTargetCtas = 148 * 3 * 4;   // below this, the rows are split into segments
+constexpr int kPBandWin = 128;              // chunks whose bands are computed at once (1 KB of shared memory)
 constexpr double kFix = 4294967296.0;   // 2^32
 
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int rows,
@@ -181,11 +182,13 @@ struct WalkArgs {
 };
 
 // Walk the 16-row chunks [c_lo, c_hi) of one array for the rays of the
-// masked angles.  Only the band of each chunk is staged.
+// masked angles.  Only the band of each chunk is staged.  The bands of up to
+// kPBandWin chunks are computed at once by all threads (the same integer
+// bounds as chunk_band) before those chunks are walked.
 template <int kPW>
 __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 acc[2],
-                                          float2 (*tot)[kPThreads], float scale, int per, float (*strip)[kPR][kPW], int *L0_s,
-                                          int *H_s, int c_lo, int c_hi) {
+                                          float2 (*tot)[kPThreads], float scale, int per, float (*strip)[kPR][kPW],
+                                          int2 *bands, int c_lo, int c_hi) {
     constexpr int kPVec = pvec<kPW>();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int asub = lane >> 4;
@@ -205,8 +208,10 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         c1[k] = act[k] ? 1.0f : 0.0f;
     }
     float4 pre[kPVec];
-    auto load = [&](int k, int slot) {   // chunk c_lo + k -> registers (band columns only)
-        const int r0 = (c_lo + k) * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[slot], width = H_s[slot] - L0 + 4;
+    int win0 = 0;                          // first chunk (relative to c_lo) of the current band window
+    auto load = [&](int k) {   // chunk c_lo + k -> registers (band columns only)
+        const int2 bd = bands[k - win0];
+        const int r0 = (c_lo + k) * kPR, nr = min(kPR, w.R - r0), L0 = bd.x & ~3, width = bd.y - L0 + 4;
 #pragma unroll
         for (int v = 0; v < kPVec; ++v) {
             const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
@@ -226,93 +231,104 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
             pre[v] = val;
         }
     };
-    auto commit = [&](int sbuf, int slot) {
-        const int width = H_s[slot] - L0_s[slot] + 4;
+    auto commit = [&](int sbuf, int k) {
+        const int2 bd = bands[k - win0];
+        const int width = bd.y - (bd.x & ~3) + 4;
 #pragma unroll
         for (int v = 0; v < kPVec; ++v) {
             const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
             if (col < width) *reinterpret_cast<float4 *>(&strip[sbuf][rr][col]) = pre[v];
         }
     };
-    auto band = [&](int k, int slot) {
-        if (warp == 0) {
-            int L0, H;
-            const int r0 = (c_lo + k) * kPR;
-            chunk_band(rg, mask, w.b0, w.bhi, r0, min(r0 + kPR, w.R) - 1, L0, H);
-            if (lane == 0) { L0_s[slot] = L0; H_s[slot] = H; }
+    // bands of chunks [win0, win0 + n), all threads at once: min / max over the
+    // masked angles of the end bins' positions at the chunk's first and last rows
+    auto bands_for = [&](int n) {
+        for (int k = tid; k < n; k += kPThreads) bands[k] = make_int2(INT_MAX, INT_MIN);
+        __syncthreads();
+        for (int idx = tid; idx < n * kPG; idx += kPThreads) {
+            const int k = idx / kPG, a = idx % kPG;
+            if (!((mask >> a) & 1)) continue;
+            const RayGeom g = rg[a];
+            const int r_first = (c_lo + win0 + k) * kPR, r_last = min(r_first + kPR, w.R) - 1;
+            const long long p = g.X0 + (long long)w.b0 * g.dX, q = g.X0 + (long long)w.bhi * g.dX;
+            const long long u = (long long)r_first * g.rho, v = (long long)r_last * g.rho;
+            const long long mn = min(min(p - u, q - u), min(p - v, q - v));
+            const long long mx = max(max(p - u, q - u), max(p - v, q - v));
+            atomicMin(&bands[k].x, hi32(mn) - 2);
+            atomicMax(&bands[k].y, hi32(mx) + 3);
         }
+        __syncthreads();
     };
-    // prologue
-    band(0, 0);
-    if (n_chunks > 1) band(1, 1);
-    __syncthreads();
-    load(0, 0);
-    commit(0, 0);
-    __syncthreads();
     int seg_left = per - c_lo % per;       // chunks until the current row segment ends
-    for (int c = 0; c < n_chunks; ++c) {
-        const int cur = c & 1;
-        const bool more = c + 1 < n_chunks;
-        if (more) load(c + 1, (c + 1) % 3);
-        if (c + 2 < n_chunks) band(c + 2, (c + 2) % 3);
-        const int r0 = (c_lo + c) * kPR, nr = min(kPR, w.R - r0), L0 = L0_s[c % 3];
-        // chunk anchors: x* + 1/2 - L0 in unsigned 9.23 fixed point (the band
-        // keeps it inside (2.5, kPW - 5.5), so below 2^32 for both widths);
-        // re-anchored from the exact 32.32 value at every chunk, so 16 rounded
-        // row steps add at most 1e-6 bins
-        constexpr int kFrac = 23;
-        unsigned x32[kPRays], r32[kPRays];
-#pragma unroll
-        for (int k = 0; k < kPRays; ++k) {
-            const long long rho = rg[asub + 2 * k].rho;
-            const long long rel = X64[k] - (long long)r0 * rho - ((long long)L0 << 32);
-            x32[k] = act[k] ? (unsigned)(rel >> (32 - kFrac)) : (3u << kFrac);
-            r32[k] = act[k] ? (unsigned)(int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0u;
-        }
-        const float *S = &strip[cur][0][0];
-        auto row = [&](const float *Sr) {   // one staged row: three taps per ray
-            float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
+    for (; win0 < n_chunks; win0 += kPBandWin) {
+        const int win_end = min(n_chunks, win0 + kPBandWin);
+        bands_for(win_end - win0);
+        load(win0);
+        commit(0, win0);
+        __syncthreads();
+        for (int c = win0; c < win_end; ++c) {
+            const int cur = (c - win0) & 1;
+            const bool more = c + 1 < win_end;
+            if (more) load(c + 1);
+            const int r0 = (c_lo + c) * kPR, nr = min(kPR, w.R - r0), L0 = bands[c - win0].x & ~3;
+            // chunk anchors: x* + 1/2 - L0 in unsigned 9.23 fixed point (the band
+            // keeps it inside (2.5, kPW - 5.5), so below 2^32 for both widths);
+            // re-anchored from the exact 32.32 value at every chunk, so 16 rounded
+            // row steps add at most 1e-6 bins
+            constexpr int kFrac = 23;
+            unsigned x32[kPRays], r32[kPRays];
 #pragma unroll
             for (int k = 0; k < kPRays; ++k) {
-                const float *q = Sr + (x32[k] >> kFrac) - 1;
-                v[k] = __uint_as_float((x32[k] & 0x7FFFFFu) | 0x3F800000u);   // 1 + frac in [1, 2)
-                q0[k] = q[0];
-                q1[k] = q[1];
-                q2[k] = q[2];
-                x32[k] -= r32[k];
+                const long long rho = rg[asub + 2 * k].rho;
+                const long long rel = X64[k] - (long long)r0 * rho - ((long long)L0 << 32);
+                x32[k] = act[k] ? (unsigned)(rel >> (32 - kFrac)) : (3u << kFrac);
+                r32[k] = act[k] ? (unsigned)(int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0u;
             }
+            const float *S = &strip[cur][0][0];
+            auto row = [&](const float *Sr) {   // one staged row: three taps per ray
+                float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const int k = 2 * p;
-                // a psi = a (1 + frac) - 3a/2, psi in [-1/2, 1/2)
-                const float2 ap = fma2(make_float2(aa[k], aa[k + 1]), make_float2(v[k], v[k + 1]),
-                                       make_float2(m1[k], m1[k + 1]));
-                const float2 wl = make_float2(__saturatef(t1[k] - ap.x), __saturatef(t1[k + 1] - ap.y));
-                const float2 wc = make_float2(c1[k] - fabsf(ap.x), c1[k + 1] - fabsf(ap.y));
-                const float2 wr = make_float2(__saturatef(t1[k] + ap.x), __saturatef(t1[k + 1] + ap.y));
-                acc[p] = fma2(wl, make_float2(q0[k], q0[k + 1]), acc[p]);
-                acc[p] = fma2(wc, make_float2(q1[k], q1[k + 1]), acc[p]);
-                acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
+                for (int k = 0; k < kPRays; ++k) {
+                    const float *q = Sr + (x32[k] >> kFrac) - 1;
+                    v[k] = __uint_as_float((x32[k] & 0x7FFFFFu) | 0x3F800000u);   // 1 + frac in [1, 2)
+                    q0[k] = q[0];
+                    q1[k] = q[1];
+                    q2[k] = q[2];
+                    x32[k] -= r32[k];
+                }
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int k = 2 * p;
+                    // a psi = a (1 + frac) - 3a/2, psi in [-1/2, 1/2)
+                    const float2 ap = fma2(make_float2(aa[k], aa[k + 1]), make_float2(v[k], v[k + 1]),
+                                           make_float2(m1[k], m1[k + 1]));
+                    const float2 wl = make_float2(__saturatef(t1[k] - ap.x), __saturatef(t1[k + 1] - ap.y));
+                    const float2 wc = make_float2(c1[k] - fabsf(ap.x), c1[k + 1] - fabsf(ap.y));
+                    const float2 wr = make_float2(__saturatef(t1[k] + ap.x), __saturatef(t1[k + 1] + ap.y));
+                    acc[p] = fma2(wl, make_float2(q0[k], q0[k + 1]), acc[p]);
+                    acc[p] = fma2(wc, make_float2(q1[k], q1[k + 1]), acc[p]);
+                    acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
+                }
+            };
+            if (nr == kPR) {                    // full chunk: rows at constant offsets
+#pragma unroll
+                for (int rr = 0; rr < kPR; ++rr) row(S + rr * kPW);
+            } else {
+                for (int rr = 0; rr < nr; ++rr) row(S + rr * kPW);
             }
-        };
-        if (nr == kPR) {                    // full chunk: rows at constant offsets
+            // end of a row segment: its scaled sum joins the total (in segment order)
+            if (--seg_left == 0 || c + 1 == n_chunks) {
+                seg_left = per;
+                const float2 s2 = make_float2(scale, scale);
 #pragma unroll
-            for (int rr = 0; rr < kPR; ++rr) row(S + rr * kPW);
-        } else {
-            for (int rr = 0; rr < nr; ++rr) row(S + rr * kPW);
+                for (int p = 0; p < 2; ++p) {
+                    tot[p][tid] = add2(tot[p][tid], mul2(s2, acc[p]));
+                    acc[p] = make_float2(0.0f, 0.0f);
+                }
+            }
+            if (more) commit(cur ^ 1, c + 1);
+            __syncthreads();
         }
-        // end of a row segment: its scaled sum joins the total (in segment order)
-        if (--seg_left == 0 || !more) {
-            seg_left = per;
-            const float2 s2 = make_float2(scale, scale);
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                tot[p][tid] = add2(tot[p][tid], mul2(s2, acc[p]));
-                acc[p] = make_float2(0.0f, 0.0f);
-            }
-        }
-        if (more) commit(cur ^ 1, (c + 1) % 3);
-        __syncthreads();
     }
 }
 
@@ -332,7 +348,7 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
     extern __shared__ __align__(16) float proj_smem[];
     float (*strip)[kPR][kPW] = reinterpret_cast<float (*)[kPR][kPW]>(proj_smem);
     __shared__ RayGeom rg[kPG];
-    __shared__ int L0_s[3], H_s[3];
+    __shared__ int2 bands_s[kPBandWin];
     __shared__ int phase_mask[2], fits_s, clip_s[2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -398,7 +414,7 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
             __syncthreads();
             const int cl = max(c_lo, clip_s[0]), ch = min(c_hi, clip_s[1]);
             __syncthreads();
-            walk_pass(w, rg, m, acc, tot, scale, per, strip, L0_s, H_s, cl, ch);
+            walk_pass(w, rg, m, acc, tot, scale, per, strip, bands_s, cl, ch);
         }
         __syncthreads();
     }

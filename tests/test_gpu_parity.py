@@ -54,6 +54,7 @@ CASES = [
     (64, 96, 160, 40, "wide", -2.7, 3),           # angles beyond pi, negative angles
     (33, 300, 129, 257, "random", 10.0, 4),
     (30, 1100, 1024, 1024, "random", 1.5, 5),     # few angles, large image: rows split into 16 segments
+    (24, 2400, 96, 2300, "random", -4.0, 10),     # tall image: a walk of 144 chunks (two band windows)
 ]
 
 
