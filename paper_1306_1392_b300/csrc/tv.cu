@@ -8,10 +8,10 @@
 //
 // Each iteration makes one projection and one back-projection: the solver
 // projects x_k (which the energy needs anyway) and carries P y_{k+1} =
-// P x_k + w_k (P x_k - P x_{k-1}) by linearity in sinogram space, so the
-// gradient step back-projects the residual P y_k - sino directly (the
-// back-projector subtracts while staging its rows and writes z = y_k - g/L
-// itself), and the last Chambolle launch writes x_k.  Reductions (energy,
+// P x_k + w_k (P x_k - P x_{k-1}) by linearity in sinogram space, keeping
+// the residual P y_{k+1} - sino (formed by the update kernel), so the
+// gradient step back-projects that residual directly (the back-projector
+// writes z = y_k - g/L itself), and the last Chambolle launch writes x_k.  Reductions (energy,
 // norms) are float64, per block then in fixed order: bitwise reproducible.
 // L comes from the caller or from power iteration on P^T P started from the
 // all-ones image (float64 norms), L = 1.01 * ||P v||^2 for the final unit v.
@@ -36,7 +36,7 @@ struct TvLayout {
     size_t tab, xt, img[9], sino[3], scal, part[3], bytes;
 };
 
-// images: y, xa, xb, z, g, p1a, p2a, p1b, p2b; sinograms: Axa, Axb, Ay;
+// images: y, xa, xb, z, g, p1a, p2a, p1b, p2b; sinograms: Axa, Axb, Ry (the residual P y - sino);
 // scalars per slice: L (double), invL, lam, invnorm (float)
 TvLayout tv_layout(const pyhst_geometry *g) {
     TvLayout l{};
@@ -134,6 +134,12 @@ __global__ void scale_kernel(const float *__restrict__ w, const float *__restric
     const float s = invn[blockIdx.y];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         v[off + i] = w[off + i] * s;
+}
+
+// r = a - b (element-wise, all slices)
+__global__ void diff_kernel(const float *__restrict__ a, const float *__restrict__ b, float *__restrict__ r, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        r[i] = a[i] - b[i];
 }
 
 __global__ void fill_kernel(float *__restrict__ v, float val, size_t n) {
@@ -236,17 +242,20 @@ __global__ void zero_gap(double *__restrict__ gap, int S, int stride, int k) {
     if (q < S) gap[(size_t)q * stride + k] = 0.0;
 }
 
-// data partial of ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
+// data partial of ||Axn - b||^2 and the residual of the next y,
+// ry = Ay - b with Ay = Axn + w (Axn - Axo) rounded to float32 first; the
+// gradient step back-projects ry
 __global__ void sino_update_kernel(const float *__restrict__ axn, const float *__restrict__ axo,
-                                   const float *__restrict__ b, float *__restrict__ ay, float w, size_t n,
+                                   const float *__restrict__ b, float *__restrict__ ry, float w, size_t n,
                                    double *__restrict__ part) {
     const size_t off = (size_t)blockIdx.y * n;
     RunSum rs;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float v = axn[off + i];
-        const float d = v - b[off + i];
+        const float v = axn[off + i], bi = b[off + i];
+        const float d = v - bi;
         rs.add(d * d);
-        ay[off + i] = fmaf(w, v - axo[off + i], v);
+        const float ay = fmaf(w, v - axo[off + i], v);
+        ry[off + i] = ay - bi;
     }
     const double acc = block_sum(rs.total());
     if (threadIdx.x == 0) part[blockIdx.y * kRedBlocks + blockIdx.x] = acc;
@@ -341,7 +350,7 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
     const float s = g->pixel_size;
     float *y = B.img[0], *xa = B.img[1], *xb = B.img[2], *z = B.img[3], *gr = B.img[4];
     float *p1a = B.img[5], *p2a = B.img[6], *p1b = B.img[7], *p2b = B.img[8];
-    float *Axa = B.sino[0], *Axb = B.sino[1], *Ay = B.sino[2];
+    float *Axa = B.sino[0], *Axb = B.sino[1], *Ry = B.sino[2];
     // reduction kernels always run kRedBlocks blocks per slice (every partial is written)
     const dim3 eg(kRedBlocks, S), sg(kRedBlocks, S);
 
@@ -380,13 +389,13 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
         cudaMemsetAsync(Axo, 0, sizeof(float) * M * S, st);
     }
     cudaMemcpyAsync(y, xo, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(Ay, Axo, sizeof(float) * M * S, cudaMemcpyDeviceToDevice, st);
+    diff_kernel<<<256, 256, 0, st>>>(Axo, sino, Ry, M * S);   // P y_1 - sino
     if ((rc = cuda_status("solver start"))) return rc;
 
     double t = 1.0;
     for (int k = 0; k < o->n_iter; ++k) {
         // gradient step: z = y - (1/L) P^T (P y - sino)
-        if ((rc = launch_backproject(g, B.tab, BpSource{Ay, sino, y, B.sc.invL}, z, s, st))) return rc;
+        if ((rc = launch_backproject(g, B.tab, BpSource{Ry, nullptr, y, B.sc.invL}, z, s, st))) return rc;
         for (int c = 0; c < hk.n_capture; ++c)
             if (hk.capture_iters[c] == k + 1)
                 cudaMemcpyAsync(hk.capture + (size_t)c * N * S, z, sizeof(float) * N * S, cudaMemcpyDeviceToDevice, st);
@@ -414,7 +423,7 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
             w = (t - 1.0) / tn;
             t = tn;
         }
-        sino_update_kernel<<<sg, kRedThreads, 0, st>>>(Axn, Axo, sino, Ay, (float)w, M, B.part[0]);
+        sino_update_kernel<<<sg, kRedThreads, 0, st>>>(Axn, Axo, sino, Ry, (float)w, M, B.part[0]);
         image_update_kernel<<<eg, kRedThreads, 0, st>>>(xn, xo, y, (float)w, g->nx, g->ny, B.part[1]);
         finalize_energy<<<S, kRedThreads, 0, st>>>(B.part[0], B.part[1], o->beta, energy, o->n_iter, k);
         if ((rc = cuda_status("update kernels"))) return rc;

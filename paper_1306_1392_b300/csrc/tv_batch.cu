@@ -31,7 +31,7 @@ constexpr int kSinoBlock = 1024;    // sinogram elements per work item (4 per th
 
 struct TvSlice {
     float *y, *xa, *xb, *z, *g, *p1a, *p2a, *p1b, *p2b;
-    float *Axa, *Axb, *Ay;
+    float *Axa, *Axb, *Ry;   // P x of the two iterates; Ry = P y - sino
     const float *sino;
     float *x_user;
     double *energy;
@@ -211,7 +211,7 @@ __global__ void b_prox_final(const TvSlice *__restrict__ d, const int4 *__restri
     }
 }
 
-// data partial ||Axn - b||^2 and Ay = Axn + w (Axn - Axo)
+// data partial ||Axn - b||^2 and Ry = Ay - b, Ay = Axn + w (Axn - Axo) rounded first
 __global__ void b_sino_update(const TvSlice *__restrict__ d, const int4 *__restrict__ items, float w, int it_parity,
                               double *__restrict__ part) {
     const int4 it = items[blockIdx.x];
@@ -220,10 +220,11 @@ __global__ void b_sino_update(const TvSlice *__restrict__ d, const int4 *__restr
     RunSum rs;
     const int base = it.y * kSinoBlock;
     for (int e = base + threadIdx.x; e < min(base + kSinoBlock, s.M); e += kBT) {
-        const float v = axn[e];
-        const float r = v - s.sino[e];
+        const float v = axn[e], b = s.sino[e];
+        const float r = v - b;
         rs.add(r * r);
-        s.Ay[e] = fmaf(w, v - axo[e], v);
+        const float ay = fmaf(w, v - axo[e], v);
+        s.Ry[e] = ay - b;
     }
     const double acc = block_sum(rs.total());
     if (threadIdx.x == 0) part[sn_slot(it, s)] = acc;
@@ -386,7 +387,7 @@ __global__ void b_copy_sino_start(const TvSlice *__restrict__ d, const int4 *__r
     for (int e = base + threadIdx.x; e < min(base + kSinoBlock, s.M); e += kBT) {
         const float v = warm ? s.Axa[e] : 0.0f;
         s.Axa[e] = v;
-        s.Ay[e] = v;
+        s.Ry[e] = v - s.sino[e];
     }
 }
 
@@ -625,7 +626,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         TvSlice &t = tv[s];
         t.y = img(0, s); t.xa = img(1, s); t.xb = img(2, s); t.z = img(3, s); t.g = img(4, s);
         t.p1a = img(5, s); t.p2a = img(6, s); t.p1b = img(7, s); t.p2b = img(8, s);
-        t.Axa = sin(0, s); t.Axb = sin(1, s); t.Ay = sin(2, s);
+        t.Axa = sin(0, s); t.Axb = sin(1, s); t.Ry = sin(2, s);
         t.sino = items[s].sino;
         t.x_user = items[s].x;
         t.energy = items[s].energy;
@@ -641,8 +642,8 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         b.cx = g.cx; b.cy = g.cy; b.pixel_size = g.pixel_size;
         b.proj_inT = img(9, s);
         b.proj_nseg = proj_segments(&g);
-        // gradient back-projection of the residual P y - sino
-        b.bp_a = t.Ay; b.bp_b = items[s].sino; b.bp_out = t.g;
+        // gradient back-projection of the residual P y - sino (formed by the update kernels)
+        b.bp_a = t.Ry; b.bp_b = nullptr; b.bp_out = t.g;
         ev[s] = b; ev[s].proj_in = t.xb; ev[s].proj_out = t.Axb;   // even iterations write xb, Axb
         od[s] = b; od[s].proj_in = t.xa; od[s].proj_out = t.Axa;   // odd iterations write xa, Axa
         // the iterations' back-projection ends in the gradient step z = y - invL g
@@ -748,7 +749,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     for (int q = 0; q < n; ++q) identity = identity && tv[q].beta == 0.0f;
     for (int k = 0; k < opts->n_iter && !rc; ++k) {
         const int par = k & 1;   // 0: x_new -> xb, 1: x_new -> xa
-        rc = launch_backproject_batch(D_even, I + o_bp, nbp, true, st, P.bpNA);
+        rc = launch_backproject_batch(D_even, I + o_bp, nbp, false, st, P.bpNA);
         if (rc) break;
         if (!identity) {                        // the last Chambolle launch writes x_new
             rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, nchf, I + o_chf, sc, opts->tau, opts->n_inner, par,
