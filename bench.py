@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--slices-per-step", type=int, default=64)
+    ap.add_argument("--slices-per-pass", type=int, default=16,
+                    help="slices filtered and back-projected per pass of pyhst_fbp (the workspace holds their "
+                         "filtered rows); 16 slices give 16,384 back-projection CTAs, 36.9 waves of 444")
     ap.add_argument("--volume-slices", type=int, default=N_SLICES)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -725,7 +728,8 @@ def run_ours(args, rank, world, local_rank):
     raw, flat, dark = vol.raw, vol.flat, vol.dark
     geo = P.Geometry(vol.angles.to(dev), vol.axis.to(dev), N_BINS, N_PIX, N_PIX, vol.pixel_size)
     out = torch.empty((NZ, N_PIX, N_PIX), dtype=torch.float32, device=dev)
-    ws = torch.empty(P.pyhst_fbp_workspace_size(geo, S, 0, 4), dtype=torch.uint8, device=dev)
+    SP = max(1, min(args.slices_per_pass, S))
+    ws = torch.empty(P.pyhst_fbp_workspace_size(geo, S, 0, SP), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
     def step(k):
@@ -797,7 +801,7 @@ def run_ours(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz") or 2032.0)
     peak_ops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12      # T FP32 lane-ops/s
-    per_launch_upd = min(4, S) * UPD_PER_SLICE
+    per_launch_upd = SP * UPD_PER_SLICE
     bp_avg_s = bp_ms / max(1, bp_n) * 1e-3
     peak_smem = props.multi_processor_count * SMEM_BYTES_PER_CLK * sm_max * 1e6 / 1e12   # TB/s
     achieved = SMEM_BYTES_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
@@ -850,7 +854,7 @@ def run_ours(args, rank, world, local_rank):
                            "parallelism": f"slice shards, {world} GPU(s), no collective on the data path",
                            "l2": f"inputs larger than L2: {S * N_ANG * N_BINS * 2 / 1e6:.0f} MB of raw counts "
                                  f"per step; the whole {NZ}-slice stack ({raw_gb:.1f} GB) resident",
-                           "pad_len": 4096, "slices_per_pass": 4},
+                           "pad_len": 4096, "slices_per_pass": SP},
                 "fbp_slices_per_s": n_slices_all / (ms_max * 1e-3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "tv": tv,
                 "single_slice_fbp": c1, "mixed_precision_fbp": c4,

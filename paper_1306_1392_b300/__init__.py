@@ -163,14 +163,16 @@ def _filter_code(name: str) -> int:
 
 def pyhst_fbp(geom: Geometry, data: torch.Tensor, kind: str, flat=None, dark=None, layout: str = None,
               pad_len: int = 0, out=None, workspace=None, ws_bytes: int = None,
-              slices_per_pass: int = 4, slices: tuple = None, filter: str = "ramlak") -> torch.Tensor:
+              slices_per_pass: int = 16, slices: tuple = None, filter: str = "ramlak") -> torch.Tensor:
     """Filtered back-projection of every slice in ``data``.
 
     ``layout`` "projections": data [n_angles, n_slices, n_bins] (a raw
     radiography stack, read in place through strides); "sinograms": data
     [n_slices, n_angles, n_bins].  Default: projections for raw kinds,
     sinograms otherwise.  flat/dark [n_slices, n_bins] float32 for raw kinds.
-    Without a ``workspace`` one is allocated for ``slices_per_pass`` slices.
+    Without a ``workspace`` one is allocated for ``slices_per_pass`` slices
+    (their filtered rows; more slices per pass fill the back-projector's last
+    wave of CTAs better).
     ``slices=(z0, z1)`` reconstructs only that range of the stack (read in
     place); ``out`` then holds z1 - z0 slices.
     """

@@ -26,6 +26,11 @@ int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angl
 size_t tv_workspace_bytes(const pyhst_geometry *g, const pyhst_tv_opts *o);
 
 static constexpr int kFbpDefaultChunk = 4;
+// The host-streamed FBP filters and back-projects each copied chunk in one
+// pass of up to this many slices (a 2048^2 slice is 1024 back-projection
+// CTAs: 8 slices make 18.4 waves of 444, so the partly filled last wave
+// costs less than with 4).
+static constexpr int kFbpHostPass = 16;
 
 int default_pad(int n_bins) {
     int P = 64;
@@ -121,7 +126,7 @@ static size_t host_chunk_field_bytes(const pyhst_geometry *g, int S) {
 static size_t host_plan_bytes(const pyhst_geometry *g, int P, int S) {
     pyhst_geometry gc = *g;
     gc.n_slices = S;
-    return fbp_fixed_bytes(&gc, P) + align_up(q_slice_bytes(&gc) * std::min(S, kFbpDefaultChunk));
+    return fbp_fixed_bytes(&gc, P) + align_up(q_slice_bytes(&gc) * std::min(S, kFbpHostPass));
 }
 static size_t fbp_host_bytes(const pyhst_geometry *g, int kind, int P, int S) {
     return host_plan_bytes(g, P, S) +

@@ -238,9 +238,9 @@ def test_fbp_padding_lengths_agree(P, orc, cuda_device, pad):
 def test_fbp_full_size_volume_sampled(P, orc, cuda_device):
     """The batched-volume workload's slice geometry (2048^2 grid, 2000 angles,
     2048 bins, uint16 raw with flat/dark) in the launch configuration the
-    benchmark times (chunks of 4 slices): sampled pixels of 2 slices of an
-    8-slice stack against the oracle evaluated at those pixels."""
-    n, na, ns = 2048, 2000, 8
+    benchmark times (passes of 16 slices): sampled pixels of 2 slices of a
+    16-slice stack against the oracle evaluated at those pixels."""
+    n, na, ns = 2048, 2000, 16
     vol = acq.ellipsoid_volume(n_slices=ns, n=n, n_angles=na, seed=1000, device=cuda_device, slices=[2, 5])
     geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), n, n, n, vol.pixel_size, cuda_device)
     got = P.pyhst_fbp(geo, vol.raw, "u16_raw", vol.flat, vol.dark)
