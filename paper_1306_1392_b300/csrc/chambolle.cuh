@@ -13,8 +13,8 @@
 // (chosen per image size by the autotuner, default 5).
 //
 // The fields live in registers: warp w holds region rows 8w+1 .. 8w+8 and
-// lane l the two columns 2l+1, 2l+2 of them (z / lam, p1, p2 and G for 16
-// cells per thread).  Horizontal neighbours come from the adjacent lane by a
+// lane l the two columns 2l+1, 2l+2 of them (p1, p2 and G for 16 cells per
+// thread; z / lam, read once per cell and step, in shared memory).  Horizontal neighbours come from the adjacent lane by a
 // shuffle, vertical ones from the thread's own rows, and only the first G row
 // and the last p1 row of each strip cross to the neighbouring warp, through
 // two small shared-memory arrays (two barriers per step).  z/lam is formed
@@ -36,8 +36,10 @@ inline bool chambolle_k_supported(int K) { return K == 2 || K == 3 || K == 4 || 
 constexpr int kChThreads = 32 * kChR / kChRows;
 constexpr int kChMinBlocks = 4;             // register budget: four CTAs per SM (64 registers)
 // dynamic shared memory per CTA: the strips' last p1 rows and first G rows,
-// each with a zero guard row
-constexpr size_t kChSmem = sizeof(float) * 2 * (kChR / kChRows + 1) * kChR;
+// each with a zero guard row, then z / lam of the region (as float2 pairs of
+// a thread's two columns)
+constexpr size_t kChExchange = sizeof(float) * 2 * (kChR / kChRows + 1) * kChR;
+constexpr size_t kChSmem = kChExchange + sizeof(float) * kChR * kChR;
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float r;
@@ -55,58 +57,74 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // forward differences across the last image row / column are multiplied by 0
 // (m1, m2); inside the image every such factor is 1 and is left out, which
 // changes no bits.
+//
+// Rows stream through a step: G of row i is formed from the dual field as it
+// was at the start of the step (row i - 1 is updated only after G of row i
+// exists), then row i - 1 is updated from G of rows i - 1 and i, so only two
+// rows of G are live.  Each cell's operations and their order are those of
+// the step as written above.
 template <bool kEdge>
-__device__ __forceinline__ void chambolle_steps_regs(float (&zl)[kChRows][2], float (&a1)[kChRows][2],
+__device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChR / 2], float (&a1)[kChRows][2],
                                                      float (&a2)[kChRows][2], float (*xp)[kChR],
                                                      float (*xg)[kChR], float tau, int steps, unsigned in_mask,
                                                      const float (&m1)[kChRows], const float (&m2)[2]) {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // G of row i (old dual field)
+    auto form_g = [&](int i, float u0, float u1, float (&G)[2]) {
+        float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
+        if (tx == 0) left = 0.0f;
+        const float2 zz = zs[kChRows * w + i][tx];   // z / lam of the thread's two cells of row i
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float u = j == 0 ? u0 : u1;
+            const float l = j > 0 ? a2[i][0] : left;
+            float d = 0.0f;
+            d = __fadd_rn(d, a1[i][j]);
+            d = __fsub_rn(d, u);
+            d = __fadd_rn(d, a2[i][j]);
+            d = __fsub_rn(d, l);
+            G[j] = __fsub_rn(d, j == 0 ? zz.x : zz.y);
+            if (kEdge && !((in_mask >> (2 * i + j)) & 1u)) G[j] = 0.0f;
+        }
+    };
+    // update row i from G of rows i and i + 1
+    auto update = [&](int i, const float (&G)[2], float dn0, float dn1) {
+        float right = __shfl_down_sync(0xffffffffu, G[0], 1);
+        if (tx == 31) right = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float g0 = G[j];
+            const float dn = j == 0 ? dn0 : dn1;
+            const float rt = j == 0 ? G[1] : right;
+            float g1 = __fsub_rn(dn, g0), g2 = __fsub_rn(rt, g0);
+            if (kEdge) {
+                g1 = __fmul_rn(m1[i], g1);
+                g2 = __fmul_rn(m2[j], g2);
+            }
+            const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
+            const float n1 = __fmul_rn(fmaf(tau, g1, a1[i][j]), inv);
+            const float n2 = __fmul_rn(fmaf(tau, g2, a2[i][j]), inv);
+            if (!kEdge || ((in_mask >> (2 * i + j)) & 1u)) {
+                a1[i][j] = n1;
+                a2[i][j] = n2;
+            }
+        }
+    };
     for (int st = 0; st < steps; ++st) {
-        float G[kChRows][2];
-        const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);
+        const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
+        float Gp[2], Gc[2];
+        form_g(0, up.x, up.y, Gp);
+        *reinterpret_cast<float2 *>(&xg[w][2 * tx]) = make_float2(Gp[0], Gp[1]);
 #pragma unroll
-        for (int i = 0; i < kChRows; ++i) {
-            float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
-            if (tx == 0) left = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float u = i > 0 ? a1[i - 1][j] : (j == 0 ? up.x : up.y);
-                const float l = j > 0 ? a2[i][0] : left;
-                float d = 0.0f;
-                d = __fadd_rn(d, a1[i][j]);
-                d = __fsub_rn(d, u);
-                d = __fadd_rn(d, a2[i][j]);
-                d = __fsub_rn(d, l);
-                G[i][j] = __fsub_rn(d, zl[i][j]);
-                if (kEdge && !((in_mask >> (2 * i + j)) & 1u)) G[i][j] = 0.0f;
-            }
+        for (int i = 1; i < kChRows; ++i) {
+            form_g(i, a1[i - 1][0], a1[i - 1][1], Gc);
+            update(i - 1, Gp, Gc[0], Gc[1]);
+            Gp[0] = Gc[0];
+            Gp[1] = Gc[1];
         }
-        *reinterpret_cast<float2 *>(&xg[w][2 * tx]) = make_float2(G[0][0], G[0][1]);
         __syncthreads();
-        const float2 down = *reinterpret_cast<const float2 *>(&xg[w + 1][2 * tx]);
-#pragma unroll
-        for (int i = 0; i < kChRows; ++i) {
-            float right = __shfl_down_sync(0xffffffffu, G[i][0], 1);
-            if (tx == 31) right = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float g0 = G[i][j];
-                const float dn = i + 1 < kChRows ? G[i + 1][j] : (j == 0 ? down.x : down.y);
-                const float rt = j == 0 ? G[i][1] : right;
-                float g1 = __fsub_rn(dn, g0), g2 = __fsub_rn(rt, g0);
-                if (kEdge) {
-                    g1 = __fmul_rn(m1[i], g1);
-                    g2 = __fmul_rn(m2[j], g2);
-                }
-                const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
-                const float n1 = __fmul_rn(fmaf(tau, g1, a1[i][j]), inv);
-                const float n2 = __fmul_rn(fmaf(tau, g2, a2[i][j]), inv);
-                if (!kEdge || ((in_mask >> (2 * i + j)) & 1u)) {
-                    a1[i][j] = n1;
-                    a2[i][j] = n2;
-                }
-            }
-        }
+        const float2 down = *reinterpret_cast<const float2 *>(&xg[w + 1][2 * tx]);   // G row below the strip
+        update(kChRows - 1, Gp, down.x, down.y);
         *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
         __syncthreads();
     }
@@ -125,9 +143,10 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
     extern __shared__ __align__(16) float ch_smem[];
     float(*xp)[kChR] = reinterpret_cast<float(*)[kChR]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
     float(*xg)[kChR] = xp + (kChR / kChRows + 1);                       // xg[w]: first G row of strip w
+    float2(*zs)[kChR / 2] = reinterpret_cast<float2(*)[kChR / 2]>(ch_smem + kChExchange / sizeof(float));
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = kChRows * w + 1, c0 = 2 * tx + 1;      // this thread's first region row and column
-    float zl[kChRows][2], a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
+    float a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
     unsigned in_mask = 0;                                  // bit 2i + j: cell (i, j) inside the image
     if (!kEdge) {
         const size_t base = (size_t)(ri0 + r0) * nx + (size_t)(rj0 + c0);
@@ -135,8 +154,7 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
 #pragma unroll
         for (int i = 0; i < kChRows; ++i, zr += nx) {
             m1[i] = 1.0f;
-            zl[i][0] = __fmul_rn(zr[0], inv_lam);
-            zl[i][1] = __fmul_rn(zr[1], inv_lam);
+            zs[kChRows * w + i][tx] = make_float2(__fmul_rn(zr[0], inv_lam), __fmul_rn(zr[1], inv_lam));
         }
         if (first) {
 #pragma unroll
@@ -160,30 +178,32 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
         for (int i = 0; i < kChRows; ++i) {
             const int gi = ri0 + r0 + i;
             m1[i] = (gi + 1 < ny) ? 1.0f : 0.0f;
+            float vz[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int gj = rj0 + c0 + j;
-                float vz = 0.0f, v1 = 0.0f, v2 = 0.0f;
+                float v1 = 0.0f, v2 = 0.0f;
+                vz[j] = 0.0f;
                 if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
                     in_mask |= 1u << (2 * i + j);
                     const size_t k = (size_t)gi * nx + gj;
-                    vz = __fmul_rn(z[k], inv_lam);
+                    vz[j] = __fmul_rn(z[k], inv_lam);
                     if (!first) {
                         v1 = p1[k];
                         v2 = p2[k];
                     }
                 }
-                zl[i][j] = vz;
                 a1[i][j] = v1;
                 a2[i][j] = v2;
             }
+            zs[kChRows * w + i][tx] = make_float2(vz[0], vz[1]);
         }
     }
     if (w == 0) *reinterpret_cast<float2 *>(&xp[0][2 * tx]) = make_float2(0.0f, 0.0f);
     if (w == kChR / kChRows - 1) *reinterpret_cast<float2 *>(&xg[kChR / kChRows][2 * tx]) = make_float2(0.0f, 0.0f);
     *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
     __syncthreads();
-    chambolle_steps_regs<kEdge>(zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
+    chambolle_steps_regs<kEdge>(zs, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
     // write the central tile: region rows and columns kChK + 1 .. kChR - kChK
     if (xout) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
