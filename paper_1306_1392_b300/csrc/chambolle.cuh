@@ -14,7 +14,8 @@
 //
 // The fields live in registers: warp w holds region rows 8w+1 .. 8w+8 and
 // lane l the two columns 2l+1, 2l+2 of them (p1, p2 and G for 16 cells per
-// thread; z / lam, read once per cell and step, in shared memory).  Horizontal neighbours come from the adjacent lane by a
+// thread; z / lam, read once per cell and step, in shared memory or in
+// registers, a per-kernel choice).  Horizontal neighbours come from the adjacent lane by a
 // shuffle, vertical ones from the thread's own rows, and only the first G row
 // and the last p1 row of each strip cross to the neighbouring warp, through
 // two small shared-memory arrays (two barriers per step).  z/lam is formed
@@ -36,10 +37,12 @@ inline bool chambolle_k_supported(int K) { return K == 2 || K == 3 || K == 4 || 
 constexpr int kChThreads = 32 * kChR / kChRows;
 constexpr int kChMinBlocks = 4;             // register budget: four CTAs per SM (64 registers)
 // dynamic shared memory per CTA: the strips' last p1 rows and first G rows,
-// each with a zero guard row, then z / lam of the region (as float2 pairs of
-// a thread's two columns)
+// each with a zero guard row, then (kChSmem) z / lam of the region as float2
+// pairs of a thread's two columns; kChSmemRegs when z / lam stays in
+// registers (see chambolle_tile)
 constexpr size_t kChExchange = sizeof(float) * 2 * (kChR / kChRows + 1) * kChR;
 constexpr size_t kChSmem = kChExchange + sizeof(float) * kChR * kChR;
+constexpr size_t kChSmemRegs = kChExchange;
 
 __device__ __forceinline__ float sqrt_approx(float x) {
     float r;
@@ -63,17 +66,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // exists), then row i - 1 is updated from G of rows i - 1 and i, so only two
 // rows of G are live.  Each cell's operations and their order are those of
 // the step as written above.
-template <bool kEdge>
-__device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChR / 2], float (&a1)[kChRows][2],
-                                                     float (&a2)[kChRows][2], float (*xp)[kChR],
-                                                     float (*xg)[kChR], float tau, int steps, unsigned in_mask,
-                                                     const float (&m1)[kChRows], const float (&m2)[2]) {
+template <bool kEdge, bool kZsSmem>
+__device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChR / 2], const float (&zl)[kChRows][2],
+                                                     float (&a1)[kChRows][2], float (&a2)[kChRows][2],
+                                                     float (*xp)[kChR], float (*xg)[kChR], float tau, int steps,
+                                                     unsigned in_mask, const float (&m1)[kChRows],
+                                                     const float (&m2)[2]) {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     // G of row i (old dual field)
     auto form_g = [&](int i, float u0, float u1, float (&G)[2]) {
         float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
         if (tx == 0) left = 0.0f;
-        const float2 zz = zs[kChRows * w + i][tx];   // z / lam of the thread's two cells of row i
+        float2 zz;                                   // z / lam of the thread's two cells of row i
+        if constexpr (kZsSmem)
+            zz = zs[kChRows * w + i][tx];
+        else
+            zz = make_float2(zl[i][0], zl[i][1]);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const float u = j == 0 ? u0 : u1;
@@ -134,7 +142,7 @@ __device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChR / 2
 // its last row or column (see chambolle_tile); otherwise every cell of the
 // region is inside the image, so the loads, the steps and the stores need no
 // bounds checks and address the image by constant row offsets.
-template <int kChK, bool kEdge>
+template <int kChK, bool kEdge, bool kZsSmem>
 __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z, const float *__restrict__ p1,
                                                     const float *__restrict__ p2, float *__restrict__ q1,
                                                     float *__restrict__ q2, float lam, float inv_lam, float tau,
@@ -146,7 +154,16 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
     float2(*zs)[kChR / 2] = reinterpret_cast<float2(*)[kChR / 2]>(ch_smem + kChExchange / sizeof(float));
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = kChRows * w + 1, c0 = 2 * tx + 1;      // this thread's first region row and column
-    float a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
+    float zl[kChRows][2], a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
+    // z / lam of the thread's cells (i, 0) and (i, 1)
+    auto put_zl = [&](int i, float v0, float v1) {
+        if constexpr (kZsSmem) {
+            zs[kChRows * w + i][tx] = make_float2(v0, v1);
+        } else {
+            zl[i][0] = v0;
+            zl[i][1] = v1;
+        }
+    };
     unsigned in_mask = 0;                                  // bit 2i + j: cell (i, j) inside the image
     if (!kEdge) {
         const size_t base = (size_t)(ri0 + r0) * nx + (size_t)(rj0 + c0);
@@ -154,7 +171,7 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
 #pragma unroll
         for (int i = 0; i < kChRows; ++i, zr += nx) {
             m1[i] = 1.0f;
-            zs[kChRows * w + i][tx] = make_float2(__fmul_rn(zr[0], inv_lam), __fmul_rn(zr[1], inv_lam));
+            put_zl(i, __fmul_rn(zr[0], inv_lam), __fmul_rn(zr[1], inv_lam));
         }
         if (first) {
 #pragma unroll
@@ -196,14 +213,14 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
                 a1[i][j] = v1;
                 a2[i][j] = v2;
             }
-            zs[kChRows * w + i][tx] = make_float2(vz[0], vz[1]);
+            put_zl(i, vz[0], vz[1]);
         }
     }
     if (w == 0) *reinterpret_cast<float2 *>(&xp[0][2 * tx]) = make_float2(0.0f, 0.0f);
     if (w == kChR / kChRows - 1) *reinterpret_cast<float2 *>(&xg[kChR / kChRows][2 * tx]) = make_float2(0.0f, 0.0f);
     *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
     __syncthreads();
-    chambolle_steps_regs<kEdge>(zs, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
+    chambolle_steps_regs<kEdge, kZsSmem>(zs, zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
     // write the central tile: region rows and columns kChK + 1 .. kChR - kChK
     if (xout) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
@@ -254,8 +271,12 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
 // x = z - lam div p: the divergence's four terms added in a fixed order,
 // those across the image border left out, then one fma; with keep_p the
 // dual field is written to q1, q2 as well (for the duality gap).
-// z / lam is formed as z times the correctly rounded reciprocal of lam.
-template <int kChK>
+// z / lam is formed as z times the correctly rounded reciprocal of lam, and
+// kept in shared memory (kZsSmem; dynamic shared memory kChSmem) or in
+// registers (kChSmemRegs): the same bits either way.  Measured on the B300,
+// shared memory is faster for the single-slice kernels (no spills at 64
+// registers) and registers for the batched kernel.
+template <int kChK, bool kZsSmem = true>
 __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, const float *__restrict__ p1,
                                                const float *__restrict__ p2, float *__restrict__ q1,
                                                float *__restrict__ q2, float lam, float tau, int nx, int ny, int i0,
@@ -266,11 +287,11 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
     // the whole region inside the image and clear of its last row and column
     const bool interior = ri0 + 1 >= 0 && ri0 + kChR + 1 < ny && rj0 + 1 >= 0 && rj0 + kChR + 1 < nx;
     if (interior)
-        chambolle_tile_body<kChK, false>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps, first, xout,
-                                         keep_p);
+        chambolle_tile_body<kChK, false, kZsSmem>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps,
+                                                  first, xout, keep_p);
     else
-        chambolle_tile_body<kChK, true>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps, first, xout,
-                                        keep_p);
+        chambolle_tile_body<kChK, true, kZsSmem>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps,
+                                                 first, xout, keep_p);
 }
 
 // Launch plan of n_inner steps: launch m runs steps(m) steps, the first

@@ -106,13 +106,14 @@ b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal 
     const float *s1 = odd ? s.p1a : s.p1b, *s2 = odd ? s.p2a : s.p2b;
     float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
     // keep_p: the last launch also writes the final dual field of slices that report the gap
-    chambolle_tile<K>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0, xn,
-                      keep_p && s.gap != nullptr);
+    // z / lam in registers: faster than shared memory for this kernel on the B300 (same bits)
+    chambolle_tile<K, false>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0,
+                             xn, keep_p && s.gap != nullptr);
 }
 
 template <int K>
 int b_chambolle_attr_k() {
-    return cudaFuncSetAttribute(b_chambolle<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmem) ==
+    return cudaFuncSetAttribute(b_chambolle<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChSmemRegs) ==
                    cudaSuccess
                ? PYHST_OK
                : cuda_status("Chambolle kernel shared-memory attribute");
@@ -125,13 +126,13 @@ int b_chambolle_launches_k(int nch, const TvSlice *T, const int4 *items, int nch
     const int Lc = chambolle_launches(n_inner, K);
     for (int m = 0; m + 1 < Lc; ++m) {
         ProfScope prof(kProfChambolle, st);
-        b_chambolle<K><<<nch, kChThreads, kChSmem, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K), -1, 0);
+        b_chambolle<K><<<nch, kChThreads, kChSmemRegs, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K), -1, 0);
     }
     // the last launch writes x_new; it reads p one row above and one column left
     // of its tiles, so it takes the halo of K + 1 steps (same bits)
     {
         ProfScope prof(kProfChambolle, st);
-        b_chambolle<K + 1><<<nchf, kChThreads, kChSmem, st>>>(T, items_f, sc, tau, Lc - 1,
+        b_chambolle<K + 1><<<nchf, kChThreads, kChSmemRegs, st>>>(T, items_f, sc, tau, Lc - 1,
                                                               chambolle_steps(n_inner, Lc - 1, K), par, keep_p);
     }
     return cuda_status("batched Chambolle kernels");
