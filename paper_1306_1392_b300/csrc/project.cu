@@ -17,9 +17,10 @@
 // of 16 rows; for each chunk it stages the rectangle of pixels that its rays
 // can touch (for neighbouring angles their bands nearly coincide, so one
 // staged pixel serves about eight times more rays than a one-angle band
-// would); only the columns of the band are loaded.  The next chunk is loaded
-// from L2 into registers (float4) while the current one is walked, with one
-// barrier per chunk.  The staging buffer holds 512 columns, enough for the
+// would); only the columns of the band are loaded.  The next chunk is copied
+// from L2 into the other half of a double buffer by asynchronous 16-byte
+// copies (cp.async, no registers held) while the current one is walked, with
+// one barrier per chunk.  The staging buffer holds 512 columns, enough for the
 // 8-angle bands of sparse angle sets (150 angles at 2048^2); if a group's band
 // still does not fit, the CTA walks 4, 2 or 1 angles at a time; the band width
 // is convex in the row, so checking the first and last chunks decides it.
@@ -207,39 +208,37 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         t1[k] = act[k] ? 1.0f - g.a : -1.0f;
         c1[k] = act[k] ? 1.0f : 0.0f;
     }
-    float4 pre[kPVec];
     int win0 = 0;                          // first chunk (relative to c_lo) of the current band window
-    auto load = [&](int k) {   // chunk c_lo + k -> registers (band columns only)
+    // chunk c_lo + k -> strip[sbuf], band columns only, by asynchronous copies
+    // (a source size of 0 fills zeros outside the array); completed by the
+    // wait before the next barrier
+    auto load = [&](int k, int sbuf) {
         const int2 bd = bands[k - win0];
         const int r0 = (c_lo + k) * kPR, nr = min(kPR, w.R - r0), L0 = bd.x & ~3, width = bd.y - L0 + 4;
 #pragma unroll
         for (int v = 0; v < kPVec; ++v) {
             const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
             const int j = L0 + col;
-            float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (rr < nr && col < width) {
+            if (col < width) {
+                const uint32_t dst = smem_addr(&strip[sbuf][rr][col]);
                 const float *row = w.M + (size_t)(r0 + rr) * w.C;
                 if (w.vec) {
-                    if (j >= 0 && j + 3 < w.C) val = __ldg(reinterpret_cast<const float4 *>(row + j));
+                    const bool in = rr < nr && j >= 0 && j + 3 < w.C;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
+                                 "l"(in ? row + j : w.M), "r"(in ? 16u : 0u) : "memory");
                 } else {
-                    if ((unsigned)j < (unsigned)w.C) val.x = __ldg(row + j);
-                    if ((unsigned)(j + 1) < (unsigned)w.C) val.y = __ldg(row + j + 1);
-                    if ((unsigned)(j + 2) < (unsigned)w.C) val.z = __ldg(row + j + 2);
-                    if ((unsigned)(j + 3) < (unsigned)w.C) val.w = __ldg(row + j + 3);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool in = rr < nr && (unsigned)(j + q) < (unsigned)w.C;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * q),
+                                     "l"(in ? row + j + q : w.M), "r"(in ? 4u : 0u) : "memory");
+                    }
                 }
             }
-            pre[v] = val;
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto commit = [&](int sbuf, int k) {
-        const int2 bd = bands[k - win0];
-        const int width = bd.y - (bd.x & ~3) + 4;
-#pragma unroll
-        for (int v = 0; v < kPVec; ++v) {
-            const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
-            if (col < width) *reinterpret_cast<float4 *>(&strip[sbuf][rr][col]) = pre[v];
-        }
-    };
+    auto wait_loads = [] { asm volatile("cp.async.wait_group 0;" ::: "memory"); };
     // bands of chunks [win0, win0 + n), all threads at once: min / max over the
     // masked angles of the end bins' positions at the chunk's first and last rows
     auto bands_for = [&](int n) {
@@ -263,13 +262,13 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     for (; win0 < n_chunks; win0 += kPBandWin) {
         const int win_end = min(n_chunks, win0 + kPBandWin);
         bands_for(win_end - win0);
-        load(win0);
-        commit(0, win0);
+        load(win0, 0);
+        wait_loads();
         __syncthreads();
         for (int c = win0; c < win_end; ++c) {
             const int cur = (c - win0) & 1;
             const bool more = c + 1 < win_end;
-            if (more) load(c + 1);
+            if (more) load(c + 1, cur ^ 1);   // the barrier that ended chunk c - 1 freed that buffer
             const int r0 = (c_lo + c) * kPR, nr = min(kPR, w.R - r0), L0 = bands[c - win0].x & ~3;
             // chunk anchors: x* + 1/2 - L0 in unsigned 9.23 fixed point (the band
             // keeps it inside (2.5, kPW - 5.5), so below 2^32 for both widths);
@@ -326,7 +325,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                     acc[p] = make_float2(0.0f, 0.0f);
                 }
             }
-            if (more) commit(cur ^ 1, c + 1);
+            if (more) wait_loads();
             __syncthreads();
         }
     }
