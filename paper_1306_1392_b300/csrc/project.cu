@@ -13,27 +13,31 @@
 // A CTA takes a group of 8 consecutive angles and 128 consecutive bins (1024
 // rays, 4 per thread).  A warp holds 16 consecutive bins of two neighbouring
 // angles, so the pixels its lanes read in one row span at most ~26 words of
-// shared memory (one wavefront per load).  The CTA walks its array in chunks
-// of 16 rows; for each chunk it stages the rectangle of pixels that its rays
-// can touch (for neighbouring angles their bands nearly coincide, so one
-// staged pixel serves about eight times more rays than a one-angle band
-// would); only the columns of the band are loaded.  The next chunk is copied
-// from L2 into the other half of a double buffer by asynchronous 16-byte
-// copies (cp.async, no registers held) while the current one is walked, with
-// one barrier per chunk.  The staging buffer holds 512 columns, enough for the
-// 8-angle bands of sparse angle sets (150 angles at 2048^2); if a group's band
-// still does not fit, the CTA walks 4, 2 or 1 angles at a time; the band width
-// is convex in the row, so checking the first and last chunks decides it.
+// shared memory (one wavefront per load).  The CTA walks its array in blocks
+// of 32 rows (256-column staging) or 16 rows (384 or 512 columns); for each
+// block it stages the rectangle of pixels that its rays can touch (for
+// neighbouring angles their bands nearly coincide, so one staged pixel serves
+// about eight times more rays than a one-angle band would); only the columns
+// of the band are loaded.  The next block is copied from L2 into the other
+// half of a double buffer by asynchronous 16-byte copies (cp.async, no
+// registers held) while the current one is walked, with one barrier per
+// block.  The staging buffer holds up to 512 columns, enough for the 8-angle
+// bands of sparse angle sets (150 angles at 2048^2); if a group's band still
+// does not fit, the CTA walks 4, 2 or 1 angles at a time; the band width is
+// convex in the row, so checking the first and last blocks decides it.
 // When the grid would have few CTAs (few angles, few slices) the rows are
 // split into segments whose partial sinograms are added in a fixed order.
 //
 // x*(b, r) = X0 + b dX - r rho is computed in 32.32 fixed point (int64), so the
 // staged bands, computed with the same integers, provably contain every tap
-// (with one column to spare on each side).  Inside a chunk each ray follows
-// x* - L0 (L0: the chunk's first staged column) in unsigned 9.23 fixed point
-// (both band widths), re-anchored exactly at every chunk, so a
-// row costs one integer add and the error stays below 2e-6 pixel; the
-// fraction becomes a float by placing its bits in a mantissa.  Pairs of rays share paired float32 (f32x2) arithmetic.
+// (with one column to spare on each side).  Inside a 32-row chunk each ray
+// follows x* - L0 (L0: the first staged column of the current block) in
+// unsigned 9.23 fixed point (every band width), re-anchored exactly at every
+// chunk and moved by whole columns between a chunk's two blocks, so a row
+// costs one integer add and the error stays below 2e-6 pixel (31 steps
+// rounded by at most 2^-24 each, plus the anchor's truncation below 2^-23);
+// the fraction becomes a float by placing its bits in a mantissa.  Pairs of
+// rays share paired float32 (f32x2) arithmetic.
 // Rays that do not take part in a pass get zero weights and a fixed in-range
 // position, so the walk has no branches.  The weights
 // of the taps jc-1, jc, jc+1 (jc = round(x*), psi = x* - jc in [-1/2, 1/2)) are
@@ -55,12 +59,16 @@ namespace {
 constexpr int kPThreads = 256;
 constexpr int kPG = 8;          // angles per group
 constexpr int kPB = 128;        // bins per CTA
-constexpr int kPR = 16;         // rows per staged chunk
+constexpr int kPR = 32;         // rows per chunk (the unit of re-anchoring, clipping and row segments)
 // Staged pixels per row (band capacity): 256 for dense angle sets, 512 for
 // sparse ones (image size / number of angles > 2), chosen per launch.
 constexpr int kPRays = kPG / 2; // rays per thread
-template <int PW> __host__ __device__ constexpr int pvec() { return kPR * PW / 4 / kPThreads; }           // float4 per thread per chunk
-template <int PW> __host__ __device__ constexpr int psmem() { return 2 * kPR * PW * (int)sizeof(float); }  // double-buffered strip
+// Rows per staged block: a whole chunk for the 256-column staging (whose
+// double buffer then still allows 3 CTAs per SM), half a chunk for the wider
+// ones.  The arithmetic is per chunk, so the bits do not depend on it.
+template <int PW> __host__ __device__ constexpr int prows() { return PW == 256 ? kPR : kPR / 2; }
+template <int PW> __host__ __device__ constexpr int pvec() { return prows<PW>() * PW / 4 / kPThreads; }   // copies per thread per block
+template <int PW> __host__ __device__ constexpr int psmem() { return 2 * prows<PW>() * PW * (int)sizeof(float); }  // double-buffered strip
 constexpr int kPTargetCtas = 148 * 3 * 4;   // below this, the rows are split into segments
 constexpr int kPBandWin = 128;              // chunks whose bands are computed at once (1 KB of shared memory)
 constexpr double kFix = 4294967296.0;   // 2^32
@@ -182,21 +190,25 @@ struct WalkArgs {
     bool vec;       // float4 staging allowed (16-byte aligned rows)
 };
 
-// Walk the 16-row chunks [c_lo, c_hi) of one array for the rays of the
-// masked angles.  Only the band of each chunk is staged.  The bands of up to
-// kPBandWin chunks are computed at once by all threads (the same integer
-// bounds as chunk_band) before those chunks are walked.
+// Walk the chunks [c_lo, c_hi) of one array for the rays of the masked
+// angles, staged in blocks of prows rows (one or two per chunk).  Only the
+// band of each block is staged.  The bands of up to kPBandWin blocks are
+// computed at once by all threads (the same integer bounds as chunk_band)
+// before those blocks are walked.
 template <int kPW>
 __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 acc[2],
-                                          float2 (*tot)[kPThreads], float scale, int per, float (*strip)[kPR][kPW],
-                                          int2 *bands, int c_lo, int c_hi) {
-    constexpr int kPVec = pvec<kPW>();
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+                                          float2 (*tot)[kPThreads], float scale, int per,
+                                          float (*strip)[prows<kPW>()][kPW], int2 *bands, int c_lo, int c_hi) {
+    constexpr int kPVec = pvec<kPW>(), kRows = prows<kPW>(), kSub = kPR / kRows;   // kSub blocks per chunk
+    constexpr int kFrac = 23;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int asub = lane >> 4;
-    const int n_chunks = c_hi - c_lo;       // chunks of this pass; chunk k is c_lo + k
-    if (n_chunks <= 0) return;
+    if (c_hi <= c_lo) return;
+    const int row0 = c_lo * kPR, r_end = min(w.R, c_hi * kPR);   // rows of this pass
+    const int n_blocks = (r_end - row0 + kRows - 1) / kRows;       // block k: rows row0 + k kRows, ...
     long long X64[kPRays];          // x* + 1/2 at row 0, 32.32
     float aa[kPRays], m1[kPRays], t1[kPRays], c1[kPRays];
+    unsigned r32[kPRays];           // rho in 9.23 fixed point (0: ray not in this pass)
     bool act[kPRays];
 #pragma unroll
     for (int k = 0; k < kPRays; ++k) {
@@ -207,14 +219,15 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         m1[k] = -1.5f * aa[k];
         t1[k] = act[k] ? 1.0f - g.a : -1.0f;
         c1[k] = act[k] ? 1.0f : 0.0f;
+        r32[k] = act[k] ? (unsigned)(int)((g.rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0u;
     }
-    int win0 = 0;                          // first chunk (relative to c_lo) of the current band window
-    // chunk c_lo + k -> strip[sbuf], band columns only, by asynchronous copies
+    int win0 = 0;                          // first block of the current band window
+    // block k -> strip[sbuf], band columns only, by asynchronous copies
     // (a source size of 0 fills zeros outside the array); completed by the
     // wait before the next barrier
     auto load = [&](int k, int sbuf) {
         const int2 bd = bands[k - win0];
-        const int r0 = (c_lo + k) * kPR, nr = min(kPR, w.R - r0), L0 = bd.x & ~3, width = bd.y - L0 + 4;
+        const int r0 = row0 + k * kRows, nr = min(kRows, r_end - r0), L0 = bd.x & ~3, width = bd.y - L0 + 4;
 #pragma unroll
         for (int v = 0; v < kPVec; ++v) {
             const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
@@ -239,8 +252,8 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto wait_loads = [] { asm volatile("cp.async.wait_group 0;" ::: "memory"); };
-    // bands of chunks [win0, win0 + n), all threads at once: min / max over the
-    // masked angles of the end bins' positions at the chunk's first and last rows
+    // bands of blocks [win0, win0 + n), all threads at once: min / max over the
+    // masked angles of the end bins' positions at the block's first and last rows
     auto bands_for = [&](int n) {
         for (int k = tid; k < n; k += kPThreads) bands[k] = make_int2(INT_MAX, INT_MIN);
         __syncthreads();
@@ -248,7 +261,7 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
             const int k = idx / kPG, a = idx % kPG;
             if (!((mask >> a) & 1)) continue;
             const RayGeom g = rg[a];
-            const int r_first = (c_lo + win0 + k) * kPR, r_last = min(r_first + kPR, w.R) - 1;
+            const int r_first = row0 + (win0 + k) * kRows, r_last = min(r_first + kRows, r_end) - 1;
             const long long p = g.X0 + (long long)w.b0 * g.dX, q = g.X0 + (long long)w.bhi * g.dX;
             const long long u = (long long)r_first * g.rho, v = (long long)r_last * g.rho;
             const long long mn = min(min(p - u, q - u), min(p - v, q - v));
@@ -258,9 +271,17 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         }
         __syncthreads();
     };
+    // Ray positions x* + 1/2 - L0 in unsigned 9.23 fixed point (the block's
+    // band keeps them inside (2.5, kPW - 5.5), so below 2^32 for every
+    // width), anchored from the exact 32.32 value at the first row of every
+    // chunk, so 32 rounded row steps add at most 2e-6 bins.  A chunk's second
+    // block moves them by the change of L0, an exact integer; L0 only shifts
+    // the integer part, so the bits do not depend on the blocking.
+    unsigned x32[kPRays];
+    int L0_prev = 0;
     int seg_left = per - c_lo % per;       // chunks until the current row segment ends
-    for (; win0 < n_chunks; win0 += kPBandWin) {
-        const int win_end = min(n_chunks, win0 + kPBandWin);
+    for (; win0 < n_blocks; win0 += kPBandWin) {
+        const int win_end = min(n_blocks, win0 + kPBandWin);
         bands_for(win_end - win0);
         load(win0, 0);
         wait_loads();
@@ -268,21 +289,20 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
         for (int c = win0; c < win_end; ++c) {
             const int cur = (c - win0) & 1;
             const bool more = c + 1 < win_end;
-            if (more) load(c + 1, cur ^ 1);   // the barrier that ended chunk c - 1 freed that buffer
-            const int r0 = (c_lo + c) * kPR, nr = min(kPR, w.R - r0), L0 = bands[c - win0].x & ~3;
-            // chunk anchors: x* + 1/2 - L0 in unsigned 9.23 fixed point (the band
-            // keeps it inside (2.5, kPW - 5.5), so below 2^32 for both widths);
-            // re-anchored from the exact 32.32 value at every chunk, so 16 rounded
-            // row steps add at most 1e-6 bins
-            constexpr int kFrac = 23;
-            unsigned x32[kPRays], r32[kPRays];
+            if (more) load(c + 1, cur ^ 1);   // the barrier that ended block c - 1 freed that buffer
+            const int r0 = row0 + c * kRows, nr = min(kRows, r_end - r0), L0 = bands[c - win0].x & ~3;
+            if (kSub == 1 || c % kSub == 0) {
 #pragma unroll
-            for (int k = 0; k < kPRays; ++k) {
-                const long long rho = rg[asub + 2 * k].rho;
-                const long long rel = X64[k] - (long long)r0 * rho - ((long long)L0 << 32);
-                x32[k] = act[k] ? (unsigned)(rel >> (32 - kFrac)) : (3u << kFrac);
-                r32[k] = act[k] ? (unsigned)(int)((rho + (1LL << (31 - kFrac))) >> (32 - kFrac)) : 0u;
+                for (int k = 0; k < kPRays; ++k) {
+                    const long long rel = X64[k] - (long long)r0 * rg[asub + 2 * k].rho - ((long long)L0 << 32);
+                    x32[k] = act[k] ? (unsigned)(rel >> (32 - kFrac)) : (3u << kFrac);
+                }
+            } else {
+                const unsigned d = (unsigned)(L0_prev - L0) << kFrac;
+#pragma unroll
+                for (int k = 0; k < kPRays; ++k) x32[k] += act[k] ? d : 0u;
             }
+            L0_prev = L0;
             const float *S = &strip[cur][0][0];
             auto row = [&](const float *Sr) {   // one staged row: three taps per ray
                 float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
@@ -309,14 +329,16 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                     acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
                 }
             };
-            if (nr == kPR) {                    // full chunk: rows at constant offsets
+            if (nr == kRows) {                  // full block: rows at constant offsets
 #pragma unroll
-                for (int rr = 0; rr < kPR; ++rr) row(S + rr * kPW);
+                for (int rr = 0; rr < kRows; ++rr) row(S + rr * kPW);
             } else {
                 for (int rr = 0; rr < nr; ++rr) row(S + rr * kPW);
             }
-            // end of a row segment: its scaled sum joins the total (in segment order)
-            if (--seg_left == 0 || c + 1 == n_chunks) {
+            // end of a chunk that ends a row segment: its scaled sum joins the
+            // total (in segment order)
+            const bool last = c + 1 == n_blocks;
+            if ((kSub == 1 || c % kSub == kSub - 1 || last) && (--seg_left == 0 || last)) {
                 seg_left = per;
                 const float2 s2 = make_float2(scale, scale);
 #pragma unroll
@@ -345,7 +367,7 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
                                          int n_bins, int nx, int ny, double cx, double cy, float scale, int g0,
                                          int b0, int seg, int nseg) {
     extern __shared__ __align__(16) float proj_smem[];
-    float (*strip)[kPR][kPW] = reinterpret_cast<float (*)[kPR][kPW]>(proj_smem);
+    float (*strip)[prows<kPW>()][kPW] = reinterpret_cast<float (*)[prows<kPW>()][kPW]>(proj_smem);
     __shared__ RayGeom rg[kPG];
     __shared__ int2 bands_s[kPBandWin];
     __shared__ int phase_mask[2], fits_s, clip_s[2];
@@ -380,20 +402,22 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
         w.b0 = b0; w.bhi = bhi; w.b = b;
         w.vec = (w.C % 4 == 0) && ((reinterpret_cast<uintptr_t>(w.M) & 15) == 0);
         // Largest subset of consecutive angles (8, 4, 2, 1) whose bands fit:
-        // the band of rows [r, r + 15] has a width convex in r, every chunk
-        // lies within the range of the first and last 16-row windows, and the
-        // float4 alignment of a chunk's start adds at most 3 columns.  A
-        // single angle always fits (127 sqrt 2 + 16 + 8 < 256).
+        // the band of rows [r, r + n - 1] (n rows per staged block) has a
+        // width convex in r, every block lies within the range of the first
+        // and last n-row windows, and the float4 alignment of a block's start
+        // adds at most 3 columns.  A single angle always fits
+        // (127 sqrt 2 + 32 + 8 < 256).
         if (warp == 0) {
             int gs = kPG;
-            const int last0 = max(0, w.R - kPR);
+            constexpr int kRows = prows<kPW>();
+            const int last0 = max(0, w.R - kRows);
             for (; gs > 1; gs >>= 1) {
                 bool ok = true;
                 for (int s0 = 0; s0 < kPG; s0 += gs) {
                     const int m = mask_all & (((1 << gs) - 1) << s0);
                     if (!m) continue;
                     int L0a, Ha, L0b, Hb;
-                    chunk_band(rg, m, b0, bhi, 0, min(kPR, w.R) - 1, L0a, Ha);
+                    chunk_band(rg, m, b0, bhi, 0, min(kRows, w.R) - 1, L0a, Ha);
                     chunk_band(rg, m, b0, bhi, last0, w.R - 1, L0b, Hb);
                     ok = ok && (Ha - L0a + 4 <= kPW) && (Hb - L0b + 4 <= kPW);
                 }
@@ -555,14 +579,14 @@ int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n
 
 // Row segments of a slice geometry: when one slice gives few CTAs, enough
 // segments to fill the GPU a few times (at least 4 waves of 3 CTAs per SM),
-// at least 4 chunks (64 rows) each; between that count and twice it, the one
+// at least 2 chunks (64 rows) each; between that count and twice it, the one
 // whose last wave is fullest.  A property of the slice geometry alone (not of
 // how many slices a call holds), since the segments fix the order of the
 // float32 sums.
 int proj_segments(const pyhst_geometry *g) {
     const long ctas = (long)((g->n_bins + kPB - 1) / kPB) * ((g->n_angles + kPG - 1) / kPG);
     if (ctas >= kPTargetCtas) return 1;
-    const long cap = std::max(1, std::min(g->nx, g->ny) / (kPR * 4));
+    const long cap = std::max(1, std::min(g->nx, g->ny) / (kPR * 2));
     const long lo = std::min(cap, (kPTargetCtas + ctas - 1) / ctas), hi = std::min(cap, 2 * lo);
     constexpr long wave = kPTargetCtas / 4;
     long best = lo;
