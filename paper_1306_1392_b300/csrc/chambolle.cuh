@@ -20,28 +20,34 @@
 // and the last p1 row of each strip cross to the neighbouring warp, through
 // two small shared-memory arrays (two barriers per step).  z/lam is formed
 // once per launch; |grad G| and the reciprocal of 1 + tau |grad G| use the
-// hardware approximations (within two ulp), and the rounding of every
-// operation is spelled out (fmaf, __fmul_rn, ...) so that all kernels built on
-// this function give bit-identical results.
+// hardware approximations (within two ulp).  A thread's two cells of a row
+// are computed together by paired float32 instructions (f32x2; each half
+// rounds as the scalar operation would), and the rounding of every operation
+// is spelled out (fma2, mul2, ...) so that all kernels built on this function
+// give bit-identical results.
 #pragma once
 
 #include "common.cuh"
 
 namespace pyhst {
 
-constexpr int kChR = 64;                    // loaded region side
 constexpr int kChRows = 8;                  // region rows per warp
+constexpr int kChWarps = 8;                 // warps per CTA (16, a 128 x 64 region, measured slower)
+constexpr int kChRH = kChRows * kChWarps;   // loaded region: rows
+constexpr int kChRW = 64;                   // loaded region: columns (two per lane)
 constexpr int kChKDefault = 5;              // steps fused per launch unless tuned
-__host__ __device__ constexpr int chambolle_tile_size(int K) { return kChR - 2 * K; }
+// output tile of K fused steps: the region less a halo of K on each side
+__host__ __device__ constexpr int chambolle_tile_h(int K) { return kChRH - 2 * K; }
+__host__ __device__ constexpr int chambolle_tile_w(int K) { return kChRW - 2 * K; }
 inline bool chambolle_k_supported(int K) { return K == 2 || K == 3 || K == 4 || K == 5 || K == 6 || K == 8; }
-constexpr int kChThreads = 32 * kChR / kChRows;
-constexpr int kChMinBlocks = 4;             // register budget: four CTAs per SM (64 registers)
+constexpr int kChThreads = 32 * kChWarps;
+constexpr int kChMinBlocks = 1024 / kChThreads;   // register budget: 64 registers a thread (1024 threads per SM)
 // dynamic shared memory per CTA: the strips' last p1 rows and first G rows,
 // each with a zero guard row, then (kChSmem) z / lam of the region as float2
 // pairs of a thread's two columns; kChSmemRegs when z / lam stays in
 // registers (see chambolle_tile)
-constexpr size_t kChExchange = sizeof(float) * 2 * (kChR / kChRows + 1) * kChR;
-constexpr size_t kChSmem = kChExchange + sizeof(float) * kChR * kChR;
+constexpr size_t kChExchange = sizeof(float) * 2 * (kChWarps + 1) * kChRW;
+constexpr size_t kChSmem = kChExchange + sizeof(float) * kChRH * kChRW;
 constexpr size_t kChSmemRegs = kChExchange;
 
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -67,73 +73,71 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // rows of G are live.  Each cell's operations and their order are those of
 // the step as written above.
 template <bool kEdge, bool kZsSmem>
-__device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChR / 2], const float (&zl)[kChRows][2],
-                                                     float (&a1)[kChRows][2], float (&a2)[kChRows][2],
-                                                     float (*xp)[kChR], float (*xg)[kChR], float tau, int steps,
+__device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChRW / 2], const float2 (&zl)[kChRows],
+                                                     float2 (&a1)[kChRows], float2 (&a2)[kChRows],
+                                                     float (*xp)[kChRW], float (*xg)[kChRW], float tau, int steps,
                                                      unsigned in_mask, const float (&m1)[kChRows],
-                                                     const float (&m2)[2]) {
+                                                     const float2 m2) {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // G of row i (old dual field)
-    auto form_g = [&](int i, float u0, float u1, float (&G)[2]) {
-        float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
+    const float2 tau2 = make_float2(tau, tau), one2 = make_float2(1.0f, 1.0f);
+    auto in_cell = [&](int i, int j) { return ((in_mask >> (2 * i + j)) & 1u) != 0u; };
+    // G of row i (old dual field); u: p1 of the row above
+    auto form_g = [&](int i, float2 u) {
+        float left = __shfl_up_sync(0xffffffffu, a2[i].y, 1);
         if (tx == 0) left = 0.0f;
-        float2 zz;                                   // z / lam of the thread's two cells of row i
-        if constexpr (kZsSmem)
-            zz = zs[kChRows * w + i][tx];
-        else
-            zz = make_float2(zl[i][0], zl[i][1]);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const float u = j == 0 ? u0 : u1;
-            const float l = j > 0 ? a2[i][0] : left;
-            float d = 0.0f;
-            d = __fadd_rn(d, a1[i][j]);
-            d = __fsub_rn(d, u);
-            d = __fadd_rn(d, a2[i][j]);
-            d = __fsub_rn(d, l);
-            G[j] = __fsub_rn(d, j == 0 ? zz.x : zz.y);
-            if (kEdge && !((in_mask >> (2 * i + j)) & 1u)) G[j] = 0.0f;
+        const float2 zz = kZsSmem ? zs[kChRows * w + i][tx] : zl[i];   // z / lam of the thread's two cells
+        float2 d = sub2(a1[i], u);
+        d = add2(d, a2[i]);
+        d = sub2(d, make_float2(left, a2[i].x));
+        float2 G = sub2(d, zz);
+        if (kEdge) {
+            if (!in_cell(i, 0)) G.x = 0.0f;
+            if (!in_cell(i, 1)) G.y = 0.0f;
         }
+        return G;
     };
     // update row i from G of rows i and i + 1
-    auto update = [&](int i, const float (&G)[2], float dn0, float dn1) {
-        float right = __shfl_down_sync(0xffffffffu, G[0], 1);
+    auto update = [&](int i, float2 G, float2 dn) {
+        float right = __shfl_down_sync(0xffffffffu, G.x, 1);
         if (tx == 31) right = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const float g0 = G[j];
-            const float dn = j == 0 ? dn0 : dn1;
-            const float rt = j == 0 ? G[1] : right;
-            float g1 = __fsub_rn(dn, g0), g2 = __fsub_rn(rt, g0);
-            if (kEdge) {
-                g1 = __fmul_rn(m1[i], g1);
-                g2 = __fmul_rn(m2[j], g2);
+        float2 g1 = sub2(dn, G), g2 = sub2(make_float2(G.y, right), G);
+        if (kEdge) {
+            g1 = mul2(make_float2(m1[i], m1[i]), g1);
+            g2 = mul2(m2, g2);
+        }
+        const float2 s = fma2(g1, g1, mul2(g2, g2));
+        const float2 den = fma2(tau2, make_float2(sqrt_approx(s.x), sqrt_approx(s.y)), one2);
+        const float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+        const float2 n1 = mul2(fma2(tau2, g1, a1[i]), inv);
+        const float2 n2 = mul2(fma2(tau2, g2, a2[i]), inv);
+        if (!kEdge) {
+            a1[i] = n1;
+            a2[i] = n2;
+        } else {
+            if (in_cell(i, 0)) {
+                a1[i].x = n1.x;
+                a2[i].x = n2.x;
             }
-            const float inv = rcp_approx(fmaf(tau, sqrt_approx(fmaf(g1, g1, __fmul_rn(g2, g2))), 1.0f));
-            const float n1 = __fmul_rn(fmaf(tau, g1, a1[i][j]), inv);
-            const float n2 = __fmul_rn(fmaf(tau, g2, a2[i][j]), inv);
-            if (!kEdge || ((in_mask >> (2 * i + j)) & 1u)) {
-                a1[i][j] = n1;
-                a2[i][j] = n2;
+            if (in_cell(i, 1)) {
+                a1[i].y = n1.y;
+                a2[i].y = n2.y;
             }
         }
     };
     for (int st = 0; st < steps; ++st) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
-        float Gp[2], Gc[2];
-        form_g(0, up.x, up.y, Gp);
-        *reinterpret_cast<float2 *>(&xg[w][2 * tx]) = make_float2(Gp[0], Gp[1]);
+        float2 Gp = form_g(0, up);
+        *reinterpret_cast<float2 *>(&xg[w][2 * tx]) = Gp;
 #pragma unroll
         for (int i = 1; i < kChRows; ++i) {
-            form_g(i, a1[i - 1][0], a1[i - 1][1], Gc);
-            update(i - 1, Gp, Gc[0], Gc[1]);
-            Gp[0] = Gc[0];
-            Gp[1] = Gc[1];
+            const float2 Gc = form_g(i, a1[i - 1]);
+            update(i - 1, Gp, Gc);
+            Gp = Gc;
         }
         __syncthreads();
         const float2 down = *reinterpret_cast<const float2 *>(&xg[w + 1][2 * tx]);   // G row below the strip
-        update(kChRows - 1, Gp, down.x, down.y);
-        *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
+        update(kChRows - 1, Gp, down);
+        *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = a1[kChRows - 1];
         __syncthreads();
     }
 }
@@ -149,19 +153,19 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
                                                     int nx, int ny, int ri0, int rj0, int steps, bool first,
                                                     float *__restrict__ xout, bool keep_p) {
     extern __shared__ __align__(16) float ch_smem[];
-    float(*xp)[kChR] = reinterpret_cast<float(*)[kChR]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
-    float(*xg)[kChR] = xp + (kChR / kChRows + 1);                       // xg[w]: first G row of strip w
-    float2(*zs)[kChR / 2] = reinterpret_cast<float2(*)[kChR / 2]>(ch_smem + kChExchange / sizeof(float));
+    float(*xp)[kChRW] = reinterpret_cast<float(*)[kChRW]>(ch_smem);   // xp[w + 1]: last p1 row of strip w
+    float(*xg)[kChRW] = xp + (kChWarps + 1);                            // xg[w]: first G row of strip w
+    float2(*zs)[kChRW / 2] = reinterpret_cast<float2(*)[kChRW / 2]>(ch_smem + kChExchange / sizeof(float));
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = kChRows * w + 1, c0 = 2 * tx + 1;      // this thread's first region row and column
-    float zl[kChRows][2], a1[kChRows][2], a2[kChRows][2], m1[kChRows], m2[2];
+    float2 zl[kChRows], a1[kChRows], a2[kChRows], m2;
+    float m1[kChRows];
     // z / lam of the thread's cells (i, 0) and (i, 1)
     auto put_zl = [&](int i, float v0, float v1) {
         if constexpr (kZsSmem) {
             zs[kChRows * w + i][tx] = make_float2(v0, v1);
         } else {
-            zl[i][0] = v0;
-            zl[i][1] = v1;
+            zl[i] = make_float2(v0, v1);
         }
     };
     unsigned in_mask = 0;                                  // bit 2i + j: cell (i, j) inside the image
@@ -175,27 +179,24 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
         }
         if (first) {
 #pragma unroll
-            for (int i = 0; i < kChRows; ++i) a1[i][0] = a1[i][1] = a2[i][0] = a2[i][1] = 0.0f;
+            for (int i = 0; i < kChRows; ++i) a1[i] = a2[i] = make_float2(0.0f, 0.0f);
         } else {
             const float *r1 = p1 + base, *r2 = p2 + base;
 #pragma unroll
             for (int i = 0; i < kChRows; ++i, r1 += nx, r2 += nx) {
-                a1[i][0] = r1[0];
-                a1[i][1] = r1[1];
-                a2[i][0] = r2[0];
-                a2[i][1] = r2[1];
+                a1[i] = make_float2(r1[0], r1[1]);
+                a2[i] = make_float2(r2[0], r2[1]);
             }
         }
-        m2[0] = m2[1] = 1.0f;
+        m2 = make_float2(1.0f, 1.0f);
         in_mask = 0xFFFFu;
     } else {
-#pragma unroll
-        for (int j = 0; j < 2; ++j) m2[j] = (rj0 + c0 + j + 1 < nx) ? 1.0f : 0.0f;
+        m2 = make_float2((rj0 + c0 + 1 < nx) ? 1.0f : 0.0f, (rj0 + c0 + 2 < nx) ? 1.0f : 0.0f);
 #pragma unroll
         for (int i = 0; i < kChRows; ++i) {
             const int gi = ri0 + r0 + i;
             m1[i] = (gi + 1 < ny) ? 1.0f : 0.0f;
-            float vz[2];
+            float vz[2], v1s[2], v2s[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int gj = rj0 + c0 + j;
@@ -210,41 +211,46 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
                         v2 = p2[k];
                     }
                 }
-                a1[i][j] = v1;
-                a2[i][j] = v2;
+                v1s[j] = v1;
+                v2s[j] = v2;
             }
+            a1[i] = make_float2(v1s[0], v1s[1]);
+            a2[i] = make_float2(v2s[0], v2s[1]);
             put_zl(i, vz[0], vz[1]);
         }
     }
     if (w == 0) *reinterpret_cast<float2 *>(&xp[0][2 * tx]) = make_float2(0.0f, 0.0f);
-    if (w == kChR / kChRows - 1) *reinterpret_cast<float2 *>(&xg[kChR / kChRows][2 * tx]) = make_float2(0.0f, 0.0f);
-    *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = make_float2(a1[kChRows - 1][0], a1[kChRows - 1][1]);
+    if (w == kChWarps - 1) *reinterpret_cast<float2 *>(&xg[kChWarps][2 * tx]) = make_float2(0.0f, 0.0f);
+    *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = a1[kChRows - 1];
     __syncthreads();
     chambolle_steps_regs<kEdge, kZsSmem>(zs, zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
-    // write the central tile: region rows and columns kChK + 1 .. kChR - kChK
+    // write the central tile: region rows kChK + 1 .. kChRH - kChK, columns kChK + 1 .. kChRW - kChK
     if (xout) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
 #pragma unroll
         for (int i = 0; i < kChRows; ++i) {
-            float left = __shfl_up_sync(0xffffffffu, a2[i][1], 1);
+            float left = __shfl_up_sync(0xffffffffu, a2[i].y, 1);
             if (tx == 0) left = 0.0f;
+            const float a1r[2] = {a1[i].x, a1[i].y}, a2r[2] = {a2[i].x, a2[i].y};
+            const float2 pu2 = i > 0 ? a1[i - 1] : up;
+            const float pur[2] = {pu2.x, pu2.y};
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int r = r0 + i, c = c0 + j, gi = ri0 + r, gj = rj0 + c;
                 // inside the image the region is clear of the border: all four divergence terms exist
-                if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && (!kEdge || (gi < ny && gj < nx))) {
+                if (r > kChK && r <= kChRH - kChK && c > kChK && c <= kChRW - kChK && (!kEdge || (gi < ny && gj < nx))) {
                     const size_t k = (size_t)gi * nx + gj;
-                    const float pu = i > 0 ? a1[i - 1][j] : (j == 0 ? up.x : up.y);
-                    const float pl = j > 0 ? a2[i][0] : left;
+                    const float pu = pur[j];
+                    const float pl = j > 0 ? a2r[0] : left;
                     float dv = 0.0f;
-                    if (!kEdge || gi + 1 < ny) dv += a1[i][j];
+                    if (!kEdge || gi + 1 < ny) dv += a1r[j];
                     if (!kEdge || gi > 0) dv -= pu;
-                    if (!kEdge || gj + 1 < nx) dv += a2[i][j];
+                    if (!kEdge || gj + 1 < nx) dv += a2r[j];
                     if (!kEdge || gj > 0) dv -= pl;
                     xout[k] = fmaf(-lam, dv, z[k]);
                     if (keep_p) {
-                        q1[k] = a1[i][j];
-                        q2[k] = a2[i][j];
+                        q1[k] = a1r[j];
+                        q2[k] = a2r[j];
                     }
                 }
             }
@@ -256,16 +262,16 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int r = r0 + i, c = c0 + j, gi = ri0 + r, gj = rj0 + c;
-            if (r > kChK && r <= kChR - kChK && c > kChK && c <= kChR - kChK && (!kEdge || (gi < ny && gj < nx))) {
+            if (r > kChK && r <= kChRH - kChK && c > kChK && c <= kChRW - kChK && (!kEdge || (gi < ny && gj < nx))) {
                 const size_t k = (size_t)gi * nx + gj;
-                q1[k] = a1[i][j];
-                q2[k] = a2[i][j];
+                q1[k] = j == 0 ? a1[i].x : a1[i].y;
+                q2[k] = j == 0 ? a2[i].x : a2[i].y;
             }
         }
 }
 
 // K steps on the tile whose output corner is (i0, j0): the region loaded is
-// rows i0 - K - 1 + 1 .. i0 - K - 1 + 64 and the same columns.
+// rows i0 - K .. i0 - K - 1 + kChRH and columns j0 - K .. j0 - K - 1 + kChRW.
 // xout == nullptr: write the dual field of the central tile to q1, q2.
 // Otherwise (the last launch of a prox) write the prox itself to xout,
 // x = z - lam div p: the divergence's four terms added in a fixed order,
@@ -285,7 +291,7 @@ __device__ __forceinline__ void chambolle_tile(const float *__restrict__ z, cons
     const int ri0 = i0 - kChK - 1, rj0 = j0 - kChK - 1;   // global coordinates of region cell (0, 0)
     const float inv_lam = __frcp_rn(lam);
     // the whole region inside the image and clear of its last row and column
-    const bool interior = ri0 + 1 >= 0 && ri0 + kChR + 1 < ny && rj0 + 1 >= 0 && rj0 + kChR + 1 < nx;
+    const bool interior = ri0 + 1 >= 0 && ri0 + kChRH + 1 < ny && rj0 + 1 >= 0 && rj0 + kChRW + 1 < nx;
     if (interior)
         chambolle_tile_body<kChK, false, kZsSmem>(z, p1, p2, q1, q2, lam, inv_lam, tau, nx, ny, ri0, rj0, steps,
                                                   first, xout, keep_p);

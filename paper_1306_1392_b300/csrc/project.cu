@@ -228,23 +228,53 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     auto load = [&](int k, int sbuf) {
         const int2 bd = bands[k - win0];
         const int r0 = row0 + k * kRows, nr = min(kRows, r_end - r0), L0 = bd.x & ~3, width = bd.y - L0 + 4;
-#pragma unroll
-        for (int v = 0; v < kPVec; ++v) {
-            const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
-            const int j = L0 + col;
+        if constexpr ((4 * kPThreads) % kPW == 0) {
+            // a thread copies the same 4 columns of rows rr0, rr0 + kStep, ...
+            constexpr int kStep = 4 * kPThreads / kPW;
+            const int col = (4 * tid) % kPW, rr0 = (4 * tid) / kPW, j = L0 + col;
             if (col < width) {
-                const uint32_t dst = smem_addr(&strip[sbuf][rr][col]);
-                const float *row = w.M + (size_t)(r0 + rr) * w.C;
+                uint32_t dst = smem_addr(&strip[sbuf][rr0][col]);
+                const float *src = w.M + (size_t)(r0 + rr0) * w.C + j;
+                const size_t src_step = (size_t)kStep * w.C;
                 if (w.vec) {
-                    const bool in = rr < nr && j >= 0 && j + 3 < w.C;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
-                                 "l"(in ? row + j : w.M), "r"(in ? 16u : 0u) : "memory");
+                    const bool jin = j >= 0 && j + 3 < w.C;
+#pragma unroll
+                    for (int v = 0; v < kPVec; ++v, dst += kStep * kPW * 4, src += src_step) {
+                        const bool in = jin && rr0 + v * kStep < nr;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
+                                     "l"(in ? src : w.M), "r"(in ? 16u : 0u) : "memory");
+                    }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const bool in = rr < nr && (unsigned)(j + q) < (unsigned)w.C;
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * q),
-                                     "l"(in ? row + j + q : w.M), "r"(in ? 4u : 0u) : "memory");
+                    for (int v = 0; v < kPVec; ++v, dst += kStep * kPW * 4, src += src_step) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const bool in = rr0 + v * kStep < nr && (unsigned)(j + q) < (unsigned)w.C;
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * q),
+                                         "l"(in ? src + q : w.M), "r"(in ? 4u : 0u) : "memory");
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < kPVec; ++v) {
+                const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
+                const int j = L0 + col;
+                if (col < width) {
+                    const uint32_t dst = smem_addr(&strip[sbuf][rr][col]);
+                    const float *row = w.M + (size_t)(r0 + rr) * w.C;
+                    if (w.vec) {
+                        const bool in = rr < nr && j >= 0 && j + 3 < w.C;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
+                                     "l"(in ? row + j : w.M), "r"(in ? 16u : 0u) : "memory");
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const bool in = rr < nr && (unsigned)(j + q) < (unsigned)w.C;
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * q),
+                                         "l"(in ? row + j + q : w.M), "r"(in ? 4u : 0u) : "memory");
+                        }
                     }
                 }
             }

@@ -159,17 +159,17 @@ chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, floa
     const bool odd = m & 1;
     const float *s1 = (odd ? pa1 : pb1) + off, *s2 = (odd ? pa2 : pb2) + off;
     float *d1 = (m == 0 || !odd ? pa1 : pb1) + off, *d2 = (m == 0 || !odd ? pa2 : pb2) + off;
-    constexpr int T = chambolle_tile_size(K);
-    chambolle_tile<K>(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * T,
-                      (blockIdx.x % tiles_x) * T, steps, m == 0, x ? x + off : nullptr, keep_p);
+    constexpr int Th = chambolle_tile_h(K), Tw = chambolle_tile_w(K);
+    chambolle_tile<K>(z + off, s1, s2, d1, d2, lam[blockIdx.y], tau, nx, ny, (blockIdx.x / tiles_x) * Th,
+                      (blockIdx.x % tiles_x) * Tw, steps, m == 0, x ? x + off : nullptr, keep_p);
 }
 
 template <int K>
 int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
                        int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, float *x,
                        bool keep_p) {
-    constexpr int T = chambolle_tile_size(K);
-    const int tx = (nx + T - 1) / T, ty = (ny + T - 1) / T;
+    constexpr int Th = chambolle_tile_h(K), Tw = chambolle_tile_w(K);
+    const int tx = (nx + Tw - 1) / Tw, ty = (ny + Th - 1) / Th;
     const int L = chambolle_launches(n_inner, K);
     for (int m = 0; m < L; ++m) {
         ProfScope prof(kProfChambolle, st);
@@ -177,9 +177,9 @@ int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float
         if (m + 1 == L && x) {
             // The prox x = z - lam div p of a tile reads p one row above and one
             // column left of it, so the last launch takes the halo of K + 1 steps
-            // (tiles of 64 - 2 (K + 1)); its <= K steps give the same bits.
-            constexpr int T1 = chambolle_tile_size(K + 1);
-            const int tx1 = (nx + T1 - 1) / T1, ty1 = (ny + T1 - 1) / T1;
+            // (tiles two rows and columns smaller); its <= K steps give the same bits.
+            constexpr int Th1 = chambolle_tile_h(K + 1), Tw1 = chambolle_tile_w(K + 1);
+            const int tx1 = (nx + Tw1 - 1) / Tw1, ty1 = (ny + Th1 - 1) / Th1;
             chambolle_fused_kernel<K + 1><<<dim3(tx1 * ty1, n_slices), kChThreads, kChSmem, st>>>(
                 z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx1, x, keep_p);
         } else {

@@ -91,13 +91,13 @@ b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal 
             int final_par, int keep_p) {
     const int4 it = items[blockIdx.x];
     const TvSlice s = d[it.x];
-    constexpr int T = chambolle_tile_size(K);
+    constexpr int Th = chambolle_tile_h(K), Tw = chambolle_tile_w(K);
     // final_par >= 0: the last launch, which writes x_new (parity as in b_prox_final)
     float *xn = final_par < 0 ? nullptr : (final_par ? s.xa : s.xb);
     if (s.beta == 0.0f) {                       // no TV term: x_new = z on this tile
         if (xn)
-            for (int e = threadIdx.x; e < T * T; e += kChThreads) {
-                const int i = it.z * T + e / T, j = it.y * T + e % T;
+            for (int e = threadIdx.x; e < Th * Tw; e += kChThreads) {
+                const int i = it.z * Th + e / Tw, j = it.y * Tw + e % Tw;
                 if (i < s.ny && j < s.nx) xn[(size_t)i * s.nx + j] = s.z[(size_t)i * s.nx + j];
             }
         return;
@@ -107,7 +107,7 @@ b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal 
     float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
     // keep_p: the last launch also writes the final dual field of slices that report the gap
     // z / lam in registers: faster than shared memory for this kernel on the B300 (same bits)
-    chambolle_tile<K, false>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * T, it.y * T, steps, m == 0,
+    chambolle_tile<K, false>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * Th, it.y * Tw, steps, m == 0,
                              xn, keep_p && s.gap != nullptr);
 }
 
@@ -397,8 +397,8 @@ struct Plan {
     int n = 0;
     std::vector<int> rep;                       // representative of each slice
     std::vector<int> reps;                      // distinct representatives
-    std::vector<int4> bp, proj, tr, px, sn, ch; // all slices (ch: Chambolle tiles of 64 - 2 chK)
-    std::vector<int4> chf;                      // tiles of the last Chambolle launch (64 - 2 (chK + 1))
+    std::vector<int4> bp, proj, tr, px, sn, ch; // all slices (ch: Chambolle tiles of chK fused steps)
+    std::vector<int4> chf;                      // tiles of the last Chambolle launch (chK + 1 steps of halo)
     std::vector<int4> bp_r, proj_r, tr_r, px_r, sn_r;   // representatives only
     std::vector<size_t> img_off, sino_off;      // per slice, in floats
     size_t img_total = 0, sino_total = 0;
@@ -433,11 +433,12 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     const int M = g.n_angles * g.n_bins;
     for (int e = 0; e < (M + kSinoBlock - 1) / kSinoBlock; ++e) sn.push_back(make_int4(s, e, 0, 0));
     if (!rep_only) {
-        const int t0 = chambolle_tile_size(P.chK), t1 = chambolle_tile_size(P.chK + 1);
-        for (int y = 0; y < (g.ny + t0 - 1) / t0; ++y)
-            for (int x = 0; x < (g.nx + t0 - 1) / t0; ++x) P.ch.push_back(make_int4(s, x, y, 0));
-        for (int y = 0; y < (g.ny + t1 - 1) / t1; ++y)
-            for (int x = 0; x < (g.nx + t1 - 1) / t1; ++x) P.chf.push_back(make_int4(s, x, y, 0));
+        const int h0 = chambolle_tile_h(P.chK), w0 = chambolle_tile_w(P.chK);
+        const int h1 = chambolle_tile_h(P.chK + 1), w1 = chambolle_tile_w(P.chK + 1);
+        for (int y = 0; y < (g.ny + h0 - 1) / h0; ++y)
+            for (int x = 0; x < (g.nx + w0 - 1) / w0; ++x) P.ch.push_back(make_int4(s, x, y, 0));
+        for (int y = 0; y < (g.ny + h1 - 1) / h1; ++y)
+            for (int x = 0; x < (g.nx + w1 - 1) / w1; ++x) P.chf.push_back(make_int4(s, x, y, 0));
     }
 }
 
