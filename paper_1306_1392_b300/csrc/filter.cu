@@ -105,8 +105,13 @@ __device__ __forceinline__ float to_p(float v, float F, float D) {
     return v;
 }
 
+// The transform's arithmetic is written with the rounding intrinsics
+// (__fadd_rn, __fmul_rn, fmaf), which the compiler never contracts into
+// other operations: the register-fused passes therefore give the bits of the
+// pass-by-pass transform, where every stage's results went through shared
+// memory.
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+    return make_float2(fmaf(a.x, b.x, -__fmul_rn(a.y, b.y)), fmaf(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 
 // Shared-memory slot of element i: one pad slot per 16 elements, so the
@@ -119,6 +124,41 @@ __device__ __forceinline__ int slot(int i) { return i + (i >> 4); }
 // them.  Every butterfly and twiddle is the one the stage-by-stage radix-2
 // transform uses, in the same order, so the result is the same bits with a
 // quarter of the shared-memory passes.
+// The NST stages on the registers of one group: v[k] holds element
+// base + k 2^lo.
+template <int NST, bool kDIF>
+__device__ __forceinline__ void group_stages(float2 (&v)[1 << NST], const float2 *__restrict__ tw, int logP, int lo,
+                                             int base) {
+    constexpr int G = 1 << NST;
+    const int stride = 1 << lo, b0 = base & (stride - 1);
+#pragma unroll
+    for (int t = 0; t < NST; ++t) {
+        const int sl = kDIF ? NST - 1 - t : t;      // stage within the group
+        const int s = lo + sl, hk = 1 << sl;
+        // the butterfly of element base + k 2^lo at stage s takes twiddle
+        // ((base + k 2^lo) mod 2^s) 2^(logP-1-s) = (b0 + (k mod 2^sl) 2^lo) 2^(logP-1-s):
+        // 2^sl distinct entries, each loaded once
+        float2 wt[G / 2];
+#pragma unroll
+        for (int m = 0; m < hk; ++m) wt[m] = tw[(b0 + m * stride) << (logP - 1 - s)];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            if (k & hk) continue;
+            const float2 w = wt[k & (hk - 1)];
+            const float2 u = v[k];
+            if (kDIF) {
+                const float2 b = v[k + hk];
+                v[k] = make_float2(__fadd_rn(u.x, b.x), __fadd_rn(u.y, b.y));
+                v[k + hk] = cmul(make_float2(__fsub_rn(u.x, b.x), __fsub_rn(u.y, b.y)), w);
+            } else {
+                const float2 t2 = cmul(v[k + hk], make_float2(w.x, -w.y));
+                v[k] = make_float2(__fadd_rn(u.x, t2.x), __fadd_rn(u.y, t2.y));
+                v[k + hk] = make_float2(__fsub_rn(u.x, t2.x), __fsub_rn(u.y, t2.y));
+            }
+        }
+    }
+}
+
 template <int NST, bool kDIF>
 __device__ __forceinline__ void fused_stages(float2 *z, const float2 *__restrict__ tw, int P, int logP, int lo) {
     constexpr int G = 1 << NST;
@@ -128,27 +168,7 @@ __device__ __forceinline__ void fused_stages(float2 *z, const float2 *__restrict
         float2 v[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) v[k] = z[slot(base + k * stride)];
-#pragma unroll
-        for (int t = 0; t < NST; ++t) {
-            const int sl = kDIF ? NST - 1 - t : t;      // stage within the group
-            const int s = lo + sl, hk = 1 << sl;
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                if (k & hk) continue;
-                const int i0 = base + k * stride;
-                const float2 w = tw[(i0 & ((1 << s) - 1)) << (logP - 1 - s)];
-                const float2 u = v[k];
-                if (kDIF) {
-                    const float2 b = v[k + hk];
-                    v[k] = make_float2(u.x + b.x, u.y + b.y);
-                    v[k + hk] = cmul(make_float2(u.x - b.x, u.y - b.y), w);
-                } else {
-                    const float2 t2 = cmul(v[k + hk], make_float2(w.x, -w.y));
-                    v[k] = make_float2(u.x + t2.x, u.y + t2.y);
-                    v[k + hk] = make_float2(u.x - t2.x, u.y - t2.y);
-                }
-            }
-        }
+        group_stages<NST, kDIF>(v, tw, logP, lo, base);
 #pragma unroll
         for (int k = 0; k < G; ++k) z[slot(base + k * stride)] = v[k];
     }
@@ -167,7 +187,7 @@ __device__ __forceinline__ void fused_pass(int nst, float2 *z, const float2 *__r
 
 // One CTA filters rows 2*blockIdx.x and 2*blockIdx.x+1 of the chunk; row r is
 // (slice z0 + r / n_angles, angle r % n_angles).
-template <int kKind>
+template <int kKind, bool kFused>
 __global__ void __launch_bounds__(1024) filter_kernel(const void *__restrict__ data, int64_t slice_stride, int64_t angle_stride,
                               const float *__restrict__ flat, const float *__restrict__ dark, int z0,
                               int n_rows, int n_angles, int n_bins, int P, int logP,
@@ -181,10 +201,101 @@ __global__ void __launch_bounds__(1024) filter_kernel(const void *__restrict__ d
     const int64_t baseA = (int64_t)zA * slice_stride + (int64_t)aA * angle_stride;
     const int64_t baseB = (int64_t)zB * slice_stride + (int64_t)aB * angle_stride;
     constexpr bool raw = (kKind == PYHST_U16_RAW || kKind == PYHST_F32_RAW);
+    if (kFused) {
+        // One 8-element group per thread (blockDim = P / 8).  The first
+        // forward pass (stages logP-1 .. logP-3) works on the elements
+        // tid + j P/8, which are the samples the thread loads; the last
+        // inverse pass (logP-3 .. logP-1) on the same elements, which it
+        // stores; and the last forward pass (2, 1, 0), the spectrum and the
+        // first inverse pass (0, 1, 2) on eight consecutive elements.  So these
+        // run in registers: six shared-memory passes in all, with the
+        // butterflies of the pass-by-pass transform in the same order.
+        const int S = P / 8, tid = threadIdx.x;
+        float2 v[8];
+        {
+            // all samples of the thread (and their flat / dark values) are
+            // loaded before any is used; P >= 2 n_bins, so j >= 4 is padding
+            constexpr int kJ = 4;
+            float IA[kJ], IB[kJ], FA[kJ], DA[kJ], FB[kJ], DB[kJ];
+#pragma unroll
+            for (int j = 0; j < kJ; ++j) {
+                const int k = tid + j * S;
+                IA[j] = IB[j] = FA[j] = DA[j] = FB[j] = DB[j] = 0.0f;
+                if (k < n_bins) {
+                    IA[j] = load_raw<kKind>(data, baseA + k);
+                    if (raw) {
+                        FA[j] = flat[(size_t)zA * n_bins + k];
+                        DA[j] = dark[(size_t)zA * n_bins + k];
+                    }
+                    if (hasB) {
+                        IB[j] = load_raw<kKind>(data, baseB + k);
+                        if (raw) {
+                            FB[j] = flat[(size_t)zB * n_bins + k];
+                            DB[j] = dark[(size_t)zB * n_bins + k];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = tid + j * S;
+                float va = 0.0f, vb = 0.0f;
+                if (j < kJ && k < n_bins) {
+                    va = to_p<kKind>(IA[j], FA[j], DA[j]);
+                    if (hasB) vb = to_p<kKind>(IB[j], FB[j], DB[j]);
+                }
+                v[j] = make_float2(va, vb);
+            }
+        }
+        // forward: decimation in frequency
+        group_stages<3, true>(v, tw, logP, logP - 3, tid);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) z[slot(tid + j * S)] = v[j];
+        __syncthreads();
+        for (int top = logP - 4; top >= 3; top -= kFuse) {
+            const int nst = min(kFuse, top - 2);
+            fused_pass<true>(nst, z, tw, P, logP, top - nst + 1);
+            __syncthreads();
+        }
+        {
+            const int base = 8 * tid;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = z[slot(base + k)];
+            group_stages<3, true>(v, tw, logP, 0, base);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float H = hrev[base + k];
+                v[k] = make_float2(__fmul_rn(v[k].x, H), __fmul_rn(v[k].y, H));
+            }
+            // inverse: decimation in time with conjugate twiddles
+            group_stages<3, false>(v, tw, logP, 0, base);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) z[slot(base + k)] = v[k];
+        }
+        __syncthreads();
+        for (int lo = 3; lo <= logP - 4; lo += kFuse) {
+            fused_pass<false>(min(kFuse, logP - 3 - lo), z, tw, P, logP, lo);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = z[slot(tid + j * S)];
+        group_stages<3, false>(v, tw, logP, logP - 3, tid);
+        float *qA = q + (size_t)rA * n_bins;
+        float *qB = q + (size_t)rB * n_bins;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = tid + j * S;
+            if (k < n_bins) {
+                qA[k] = v[j].x;
+                if (hasB) qB[k] = v[j].y;
+            }
+        }
+        return;
+    }
+    // Other lengths: the pass-by-pass transform through shared memory.
     // The thread's first four samples (and their flat / dark values) are all
     // loaded before any is used; this covers [0, n_bins) whenever n_bins <=
-    // 4 blockDim (P = 2^k >= 2 n_bins with blockDim = P / 8 up to P = 8192);
-    // the tail loop takes any remaining samples and the zero padding.
+    // 4 blockDim; the tail loop takes any remaining samples and the zero padding.
     constexpr int kJ = 4;
     float IA[kJ], IB[kJ], FA[kJ], DA[kJ], FB[kJ], DB[kJ];
 #pragma unroll
@@ -237,7 +348,7 @@ __global__ void __launch_bounds__(1024) filter_kernel(const void *__restrict__ d
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
         const float H = hrev[k];
         const float2 v = z[slot(k)];
-        z[slot(k)] = make_float2(v.x * H, v.y * H);
+        z[slot(k)] = make_float2(__fmul_rn(v.x, H), __fmul_rn(v.y, H));
     }
     __syncthreads();
     // inverse: decimation in time with conjugate twiddles, stages 0 .. logP-1
@@ -287,13 +398,15 @@ int launch_filter(int kind, const void *data, int64_t slice_stride, int64_t angl
     const int threads = std::min(1024, std::max(64, P / 8));   // one 8-element group per thread and pass
     const size_t smem = sizeof(float2) * (P + P / 16);   // one pad slot per 16 elements
     const int grid = (n_rows + 1) / 2;
-#define PYHST_FILTER_CASE(K)                                                                          \
-    case K: {                                                                                         \
-        if (smem > 48 * 1024)                                                                         \
-            cudaFuncSetAttribute(filter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        filter_kernel<K><<<grid, threads, smem, st>>>(data, slice_stride, angle_stride, flat, dark, z0,   \
-                                                      n_rows, n_angles, n_bins, P, logP, tw, hrev, q); \
-        break;                                                                                        \
+    // register-fused passes when a thread holds exactly one 8-element group
+    const bool fused = threads * 8 == P;
+#define PYHST_FILTER_CASE(K)                                                                             \
+    case K: {                                                                                            \
+        auto kern = fused ? filter_kernel<K, true> : filter_kernel<K, false>;                            \
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        kern<<<grid, threads, smem, st>>>(data, slice_stride, angle_stride, flat, dark, z0, n_rows, n_angles, \
+                                          n_bins, P, logP, tw, hrev, q);                                 \
+        break;                                                                                           \
     }
     ProfScope prof(kProfFilter, st);
     switch (kind) {
