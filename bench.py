@@ -59,6 +59,7 @@ def parse():
                          "filtered rows); 16 slices give 16,384 back-projection CTAs, 36.9 waves of 444")
     ap.add_argument("--volume-slices", type=int, default=N_SLICES)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=16, help="largest chunk of the host-buffer call, in slices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the baseline sample")
     ap.add_argument("--no-tv", action="store_true", help="skip the reduced-dose TV measurement")
@@ -773,7 +774,7 @@ def run_ours(args, rank, world, local_rank):
         host_flat = flat[z0:z0 + S].cpu().pin_memory()
         host_dark = dark[z0:z0 + S].cpu().pin_memory()
         host_out = torch.empty((S, N_PIX, N_PIX), dtype=torch.float32, pin_memory=True)
-        chunk = 8
+        chunk = args.e2e_chunk
         hws = torch.empty(P.pyhst_fbp_host_workspace_size(geo, "u16_raw", S, 0, chunk), dtype=torch.uint8,
                           device=dev)
 
@@ -794,7 +795,8 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": e_slices * UPD_PER_SLICE / (ems * 1e-3) / 1e9, "unit": "Gupd/s",
                "h2d_bytes_per_step": int(host_raw.numel() * 2 + 2 * host_flat.numel() * 4),
                "d2h_bytes_per_step": int(host_out.numel() * 4),
-               "call": "pyhst_fbp_host (pinned host in/out, 8-slice chunks double-buffered)"}
+               "call": f"pyhst_fbp_host (pinned host in/out, chunks of up to {chunk} slices ramped 1, 4, .. at "
+                       "both ends, double-buffered)"}
 
     # ---- roofline of the back-projection kernel (dominant)
     peaks = measured_peaks()

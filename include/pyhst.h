@@ -136,10 +136,13 @@ int pyhst_filter(const pyhst_geometry *g, int input_type, const void *data,
 
 /* pyhst_fbp with HOST input and output: host_data (strides as in pyhst_fbp),
  * host_flat/host_dark [n_slices][n_bins] and host_out [n_slices][ny][nx] are
- * host memory (page-locked for the copies to overlap compute).  Chunks of
- * slices_per_chunk slices are copied to the device on an internal stream,
+ * host memory (page-locked for the copies to overlap compute).  Chunks of at
+ * most slices_per_chunk slices are copied to the device on an internal stream,
  * reconstructed on `stream` and copied back on a second internal stream, with
- * two buffers of each so that copies overlap compute.  The internal streams
+ * two buffers of each so that copies overlap compute; the chunks grow from one
+ * slice (1, 4, 16, ...) at the start and shrink back to one at the end, so
+ * that only one slice's copy in and one slice's copy back are not overlapped.
+ * Each slice's result does not depend on the chunking.  The internal streams
  * start after the work already queued on `stream`, and the call's completion
  * is ordered on `stream` (synchronise it before reading host_out).  The
  * workspace (pyhst_fbp_host_workspace_size) holds the FBP scratch and the

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pyhst {
@@ -212,6 +214,25 @@ extern "C" int pyhst_filter(const pyhst_geometry *g, int input_type, const void 
 }
 
 // ------------------------------------------------------------------ host-streamed FBP
+// Chunk sizes of a host-streamed call on n slices with chunks of at most S:
+// 1, 4, 16, ... (below S) at both ends and chunks of S between (a shorter one
+// first), so that the first compute waits only for one slice's copy and the
+// last copy back is one slice's, while every other copy is smaller than the
+// compute it overlaps (a slice's copies take about a tenth of its FBP).
+static std::vector<int> host_chunks(int n, int S) {
+    std::vector<int> head;
+    int left = n;
+    for (int c = 1; c < S && left > 2 * c; c *= 4) {
+        head.push_back(c);
+        left -= 2 * c;
+    }
+    std::vector<int> out = head;
+    if (left % S) out.push_back(left % S);
+    for (int k = 0; k < left / S; ++k) out.push_back(S);
+    out.insert(out.end(), head.rbegin(), head.rend());
+    return out;
+}
+
 extern "C" size_t pyhst_fbp_host_workspace_size(const pyhst_geometry *g, int input_type, int32_t pad_len,
                                                 int32_t slices_per_chunk) {
     if (!g || g->n_angles < 1 || g->n_bins < 1 || g->nx < 1 || g->ny < 1 || g->n_slices < 1) return 0;
@@ -287,8 +308,9 @@ extern "C" int pyhst_fbp_host(const pyhst_geometry *g, int input_type, const voi
     cudaStreamWaitEvent(d2h, start, 0);
     rc = fbp_prepare(&gs, pl, st);
     const char *src = static_cast<const char *>(host_data);
-    for (int i = 0, z0 = 0; !rc && z0 < g->n_slices; ++i, z0 += S) {
-        const int b = i & 1, n = std::min(S, g->n_slices - z0);
+    const std::vector<int> chunks = host_chunks(g->n_slices, S);
+    for (int i = 0, z0 = 0; !rc && i < (int)chunks.size(); z0 += chunks[i], ++i) {
+        const int b = i & 1, n = chunks[i];
         if (i >= 2) cudaStreamWaitEvent(h2d, done[b], 0);   // compute has finished reading in[b]
         int64_t dss, das;                                     // strides of the device chunk
         if (slice_stride == nb) {

@@ -272,11 +272,12 @@ def test_filter_only_parity(P, orc, cuda_device):
         close(f64(q[z]), ref)
 
 
-@pytest.mark.parametrize("chunk", [1, 3, 8])
-def test_fbp_host_pipeline_matches_device_call(P, cuda_device, chunk):
+@pytest.mark.parametrize("n_slices,chunk", [(7, 1), (7, 3), (7, 8), (40, 16)])
+def test_fbp_host_pipeline_matches_device_call(P, cuda_device, n_slices, chunk):
     """pyhst_fbp_host on pinned host buffers gives bitwise the device call's
-    slices, for chunk sizes that do and do not divide the stack."""
-    vol = acq.ellipsoid_volume(n_slices=7, n=128, n_angles=90, seed=31, n_ellipsoids=40)
+    slices, for chunk sizes that do and do not divide the stack (40 slices in
+    chunks of up to 16: 1, 4, 14, 16, 4, 1)."""
+    vol = acq.ellipsoid_volume(n_slices=n_slices, n=128, n_angles=90, seed=31, n_ellipsoids=40)
     geo = geometry(P, vol.angles.numpy(), vol.axis.numpy(), vol.n_bins, vol.nx, vol.ny, vol.pixel_size,
                    cuda_device)
     dev_out = P.pyhst_fbp(geo, vol.raw.to(cuda_device), "u16_raw", vol.flat.to(cuda_device),
