@@ -41,7 +41,9 @@ constexpr int kRX = 4, kRY = 4;     // pixels per thread: x stride 8, y stride 4
 constexpr int kW = 96;              // window entries per angle: ceil(hypot(63, 63)) + 4, rounded up
 // Angles staged per block (NA): 8, 16 or 24, a tuning parameter (the
 // per-pixel sums run over the angles in the same order for every NA, and the
-// padding slots of a last, partial block add +0, so results are identical);
+// padding slots of a last, partial block add +0 -- or, in the kPartial
+// instantiation, are not walked: a sum that starts at +0 is never -0, so
+// adding +0 changes no bit -- so results are identical);
 // each thread fills NA * kW / kThreads window entries per block.
 static_assert(kW % 32 == 0, "fill mapping");
 
@@ -77,7 +79,7 @@ __device__ __forceinline__ StageInfo stage_info(const AngleInfo *tab, int a, int
 // mode) are that slice's rows, out its image.
 // With ystep given, out receives the gradient step z = ystep - invL * g of
 // g = weight * back-projection, rounded as a separate pass would round it.
-template <int kNA, bool kResidual>
+template <int kNA, bool kResidual, bool kPartial>
 __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const float *__restrict__ A,
                                         const float *__restrict__ B, float *__restrict__ out, int n_angles,
                                         int n_bins, int nx, int ny, double cx, double cy, float weight,
@@ -149,8 +151,11 @@ __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const
             info[(blk + 2) % 3][tid] = stage_info(tab, (blk + 2) * kNA + tid, n_angles, X0, Y0, cx, cy);
         const StageInfo *ib = info[blk % 3];
         const uint32_t wbase = smem_addr(win[cur]) - (kMagicBits << 3);
+        // kPartial: the last block walks its real angles only (a loop with a
+        // run-time bound, slower on geometries without a partial block)
+        const int na_blk = kPartial ? min(kNA, n_angles - blk * kNA) : kNA;
 #pragma unroll 2
-        for (int a = 0; a < kNA; ++a) {
+        for (int a = 0; a < na_blk; ++a) {
             const StageInfo si = ib[a];
             const uint32_t wb = wbase + (uint32_t)(a * kW * 8);
             const float r0 = fmaf(fpy, si.sf, fmaf(fpx, si.cf, si.base));
@@ -191,7 +196,7 @@ __device__ __forceinline__ void bp_tile(const AngleInfo *__restrict__ tab, const
         }
 }
 
-template <int kNA, bool kResidual>
+template <int kNA, bool kResidual, bool kPartial>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
           const float *__restrict__ srcB, float *__restrict__ img, int n_angles, int n_bins,
@@ -199,18 +204,19 @@ bp_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ srcA,
           const float *__restrict__ invL) {
     const int slice = blockIdx.y;
     const size_t sino_off = (size_t)slice * n_angles * n_bins, img_off = (size_t)slice * nx * ny;
-    bp_tile<kNA, kResidual>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + img_off,
+    bp_tile<kNA, kResidual, kPartial>(tab, srcA + sino_off, kResidual ? srcB + sino_off : nullptr, img + img_off,
                        n_angles, n_bins, nx, ny, cx, cy, weight, (blockIdx.x % tiles_x) * kTX,
                        (blockIdx.x / tiles_x) * kTY, ystep ? ystep + img_off : nullptr, ystep ? invL[slice] : 0.0f);
 }
 
-// Mixed batch: CTA k reconstructs tile (items[k].y, items[k].z) of slice items[k].x.
+// Mixed batch: CTA k reconstructs tile (items[k].y, items[k].z) of slice items[k].x
+// (the slices' angle counts differ, so the partial last blocks are walked short).
 template <int kNA, bool kResidual>
 __global__ void __launch_bounds__(kThreads, 3)
 bp_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items, float weight_scale) {
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
-    bp_tile<kNA, kResidual>(s.tab, s.bp_a, s.bp_b, s.bp_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
+    bp_tile<kNA, kResidual, true>(s.tab, s.bp_a, s.bp_b, s.bp_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
                        weight_scale * s.pixel_size, it.y * kTX, it.z * kTY, s.bp_y, s.bp_y ? *s.bp_invL : 0.0f);
 }
 
@@ -223,16 +229,28 @@ int launch_bp_batch_na(const BatchSlice *slices, const int4 *items, int n_items,
     return cuda_status("batched back-projection kernel");
 }
 
+template <int kNA, bool kPartial>
+void launch_bp_na_p(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img, float weight,
+                    dim3 grid, int tiles_x, cudaStream_t st) {
+    if (src.b)
+        bp_kernel<kNA, true, kPartial><<<grid, kThreads, 0, st>>>(tab, src.a, src.b, img, g->n_angles, g->n_bins,
+                                                                  g->nx, g->ny, g->cx, g->cy, weight, tiles_x, src.y,
+                                                                  src.invL);
+    else
+        bp_kernel<kNA, false, kPartial><<<grid, kThreads, 0, st>>>(tab, src.a, nullptr, img, g->n_angles, g->n_bins,
+                                                                   g->nx, g->ny, g->cx, g->cy, weight, tiles_x,
+                                                                   src.y, src.invL);
+}
+
+// The short walk of a partial last block only where there is one: its loop
+// bound is a run-time value, which costs a little on full blocks.
 template <int kNA>
 int launch_bp_na(const pyhst_geometry *g, const AngleInfo *tab, BpSource src, float *img, float weight, dim3 grid,
                  int tiles_x, cudaStream_t st) {
-    if (src.b)
-        bp_kernel<kNA, true><<<grid, kThreads, 0, st>>>(tab, src.a, src.b, img, g->n_angles, g->n_bins, g->nx,
-                                                        g->ny, g->cx, g->cy, weight, tiles_x, src.y, src.invL);
+    if (g->n_angles % kNA)
+        launch_bp_na_p<kNA, true>(g, tab, src, img, weight, grid, tiles_x, st);
     else
-        bp_kernel<kNA, false><<<grid, kThreads, 0, st>>>(tab, src.a, nullptr, img, g->n_angles, g->n_bins,
-                                                         g->nx, g->ny, g->cx, g->cy, weight, tiles_x, src.y,
-                                                         src.invL);
+        launch_bp_na_p<kNA, false>(g, tab, src, img, weight, grid, tiles_x, st);
     return cuda_status("back-projection kernel");
 }
 
