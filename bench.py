@@ -75,6 +75,7 @@ def parse():
                     help="cost of the Sec. 2.3 preprocessing variants on the batched-volume geometry")
     ap.add_argument("--beta-study", action="store_true",
                     help="beta estimators (Sec. 4) on a 2048^2 foam with 150 projections vs its ground truth")
+    ap.add_argument("--kernel-slices", type=int, default=4, help="slices per launch of --kernel-case")
     ap.add_argument("--kernel-case", choices=["backproject", "project", "filter", "cnn", "project-sparse", "tvprox",
                                               "patch"],
                     help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
@@ -143,23 +144,26 @@ def measured_peaks():
         return {}
 
 
-# DRAM bytes (read + write) of one back-projection launch of the timed FBP
-# (4 slices, 2048^2, 2000 angles) from an ncu capture of bp_kernel, and the
-# hash of the kernel source it was taken on: the figure is reported only
-# while the source is unchanged.
-BP_DRAM_BYTES_PER_LAUNCH = 100360704
-BP_DRAM_SOURCE_SHA16 = "9eee8825a94d8f28"
+# DRAM bytes (read + write) of one back-projection launch of BP_DRAM_SLICES
+# slices (2048^2, 2000 angles) from an ncu capture of bp_kernel, and the hash
+# of the kernel source it was taken on: the figure is reported only while the
+# source is unchanged.
+BP_DRAM_BYTES = 502970368
+BP_DRAM_SLICES = 16
+BP_DRAM_SOURCE_SHA16 = "28dcc8ce9243e080"
 
 
-def bp_traffic():
-    """DRAM bytes per back-projection launch if the capture above was taken
-    on the current kernel source, else None."""
+def bp_traffic(slices):
+    """DRAM bytes per back-projection launch of `slices` slices if the capture
+    above was taken on the current kernel source (scaled by the slice count:
+    every slice reads its own filtered rows and writes its own image), else
+    None."""
     src = os.path.join(ROOT, "paper_1306_1392_b300", "csrc", "backproject.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return BP_DRAM_BYTES_PER_LAUNCH if sha == BP_DRAM_SOURCE_SHA16 else None
+    return BP_DRAM_BYTES * slices // BP_DRAM_SLICES if sha == BP_DRAM_SOURCE_SHA16 else None
 
 
 def cpu_sample_fbp(orc, raw_slice, flat, dark, angles, axis, target_s):
@@ -809,7 +813,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = SMEM_BYTES_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
     alu = OPS_PER_UPDATE * per_launch_upd / bp_avg_s / 1e12
     roofline = {"bound": "smem", "achieved": achieved, "peak": peak_smem, "unit": "TB/s",
-                "frac": achieved / peak_smem, "traffic": bp_traffic(),
+                "frac": achieved / peak_smem, "traffic": bp_traffic(SP),
                 "kernel": "bp_kernel", "launches": bp_n, "avg_launch_ms": bp_avg_s * 1e3,
                 "gupd_per_s": per_launch_upd / bp_avg_s / 1e9,
                 "peak_basis": f"shared-memory data pipe: {props.multi_processor_count} SMs x "
@@ -866,14 +870,15 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_kernel_case(args):
-    """A few launches of one kernel on the workload's slice geometry (4-slice
-    launch as in the timed FBP), inputs resident: a small, fixed case for
-    profilers.  Prints one JSON line with the event-timed launches."""
+    """A few launches of one kernel on the workload's slice geometry
+    (--kernel-slices slices per launch, 4 by default; the timed FBP's passes
+    hold 16), inputs resident: a small, fixed case for profilers.  Prints one
+    JSON line with the event-timed launches."""
     import torch
     import paper_1306_1392_b300 as P
     from synth import acquisition as acq
     dev = torch.device("cuda", 0)
-    S = 4
+    S = args.kernel_slices
     ang = acq.uniform_angles(N_ANG).to(dev)
     geo = P.Geometry(ang, torch.full((N_ANG,), (N_BINS - 1) / 2.0, device=dev), N_BINS, N_PIX, N_PIX, 2.0 / N_PIX)
     g = torch.Generator(device=dev).manual_seed(5)

@@ -27,13 +27,22 @@
 namespace pyhst {
 namespace {
 
+// tw[k] = exp(-2 pi i k / P) for k < P/2, rounded to float from float64; the
+// second quarter is formed as -i times the first (exact), so that
+// tw[k + P/4] = -i tw[k] holds bit for bit (the transform derives half of its
+// twiddles that way).
 __global__ void twiddle_kernel(int P, float2 *__restrict__ tw, double *__restrict__ costab) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P) {
         double s, c;
         sincospi(2.0 * (double)k / (double)P, &s, &c);
         costab[k] = c;
-        if (k < P / 2) tw[k] = make_float2((float)c, (float)-s);   // exp(-2 pi i k / P)
+        if (k < P / 2) {
+            const int j = k % (P / 4);
+            sincospi(2.0 * (double)j / (double)P, &s, &c);
+            const float2 w = make_float2((float)c, (float)-s);
+            tw[k] = k < P / 4 ? w : make_float2(w.y, -w.x);
+        }
     }
 }
 
@@ -137,10 +146,14 @@ __device__ __forceinline__ void group_stages(float2 (&v)[1 << NST], const float2
         const int s = lo + sl, hk = 1 << sl;
         // the butterfly of element base + k 2^lo at stage s takes twiddle
         // ((base + k 2^lo) mod 2^s) 2^(logP-1-s) = (b0 + (k mod 2^sl) 2^lo) 2^(logP-1-s):
-        // 2^sl distinct entries, each loaded once
+        // 2^sl distinct entries.  The upper half of them lie P/4 further in
+        // the table, and tw[k + P/4] = -i tw[k] exactly (both rounded from
+        // float64 values of opposite signs), so those are formed, not loaded.
         float2 wt[G / 2];
 #pragma unroll
-        for (int m = 0; m < hk; ++m) wt[m] = tw[(b0 + m * stride) << (logP - 1 - s)];
+        for (int m = 0; m < (hk + 1) / 2; ++m) wt[m] = tw[(b0 + m * stride) << (logP - 1 - s)];
+#pragma unroll
+        for (int m = (hk + 1) / 2; m < hk; ++m) wt[m] = make_float2(wt[m - hk / 2].y, -wt[m - hk / 2].x);
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             if (k & hk) continue;
