@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--beta-study", action="store_true",
                     help="beta estimators (Sec. 4) on a 2048^2 foam with 150 projections vs its ground truth")
     ap.add_argument("--kernel-slices", type=int, default=4, help="slices per launch of --kernel-case")
-    ap.add_argument("--kernel-case", choices=["backproject", "project", "filter", "cnn", "project-sparse", "tvprox",
+    ap.add_argument("--kernel-case", choices=["backproject", "project", "filter", "cnn", "project-sparse", "project-tv", "tvprox",
                                               "patch"],
                     help="run only a few launches of one kernel at the workload's slice geometry (for profilers)")
     return ap.parse_args()
@@ -904,6 +904,16 @@ def run_kernel_case(args):
         ws = torch.empty(P.pyhst_workspace_size(geo150, P.PYHST_OP_PROJECT, 1), dtype=torch.uint8, device=dev)
         fn = lambda: P.pyhst_project(geo150, img, out=out, workspace=ws)
         upd = N_PIX * N_PIX * 150
+    elif args.kernel_case == "project-tv":
+        # the reduced-dose TV batch's largest geometry: 42 slices of 1024^2, 200 angles, 1024 bins
+        n, na, ns = 1024, 200, 42
+        angt = acq.uniform_angles(na).to(dev)
+        geot = P.Geometry(angt, torch.full((na,), (n - 1) / 2.0, device=dev), n, n, n, 2.0 / n)
+        img = torch.randn((ns, n, n), device=dev, generator=g)
+        out = torch.empty((ns, na, n), device=dev)
+        ws = torch.empty(P.pyhst_workspace_size(geot, P.PYHST_OP_PROJECT, ns), dtype=torch.uint8, device=dev)
+        fn = lambda: P.pyhst_project(geot, img, out=out, workspace=ws)
+        upd = ns * n * n * na
     elif args.kernel_case == "tvprox":
         # 20 Chambolle steps on 16 images of 1024^2 (default fusion depth)
         z = torch.randn((16, 1024, 1024), device=dev, generator=g)
