@@ -162,51 +162,49 @@ struct MidTiles {
     }
 };
 
-// MMA schedule of one tile (the same for every tile; built once per CTA).
-// Input row rho (staged row rho + 1) and kernel rows j_lo .. j_hi of a
-// K-slice (kernel column v, half h) update output rows rho - 1 + j_lo ..
-// rho - 1 + j_hi in one MMA of N = 32 (j_hi - j_lo + 1).  A first pass (kernel
-// row u = 0 of slice (v, h) = (0, 0)) initialises every output row; all later
-// MMAs accumulate.  The tile's output rows are split between kMmaWarps
-// issuing warps (each issuing thread has a long per-instruction latency, so
-// several issue in parallel into disjoint accumulator columns); an MMA whose
-// rows straddle two warps is split.
-struct MmaOp {
-    uint32_t a_off;    // A start, bytes from the staging buffer; bit 31: accumulate
-    uint32_t b_off;    // B start, bytes from the weights
-    uint32_t d_off;    // TMEM column offset within the accumulator half
-    uint32_t idesc;
-};
-constexpr int kMmaWarps = 4;
+// MMA schedule of one tile (the same for every tile).  Input row rho
+// (staged row rho + 1) and kernel rows j_lo .. j_hi of a K-slice (kernel
+// column v, half h) update output rows rho - 1 + j_lo .. rho - 1 + j_hi in one
+// MMA of N = 32 (j_hi - j_lo + 1).  A first pass (kernel row u = 0 of slice
+// (v, h) = (0, 0)) initialises every output row; all later MMAs accumulate.
+// The tile's output rows are split between kMmaWarps issuing warps, which
+// issue in parallel into disjoint accumulator columns; an MMA whose rows
+// straddle two warps is split.  The schedule is unrolled at compile time for
+// each issuing warp: every offset is a constant, so the issuing thread sends a
+// tile's MMAs back to back (a table of MMAs in shared memory cost it a load and
+// the address arithmetic per MMA: measured 16 % slower over a forward pass,
+// same bits).
+constexpr int kMmaWarps = 2;
 constexpr int kRowsPerMmaWarp = kR / kMmaWarps;
-constexpr int kMaxOps = 32;                           // per issuing warp (25 for kR = 8)
 
-__device__ void build_schedule(MmaOp (*ops)[kMaxOps], int *count) {
-    for (int g = 0; g < kMmaWarps; ++g) count[g] = 0;
-    auto add = [&](int rho, int slice, int jlo, int jhi, bool acc) {
-        for (int g = 0; g < kMmaWarps; ++g) {
-            const int lo = max(jlo, g * kRowsPerMmaWarp - rho + 1);
-            const int hi = min(jhi, (g + 1) * kRowsPerMmaWarp - rho);
-            if (lo > hi || count[g] >= kMaxOps) continue;
-            const int v = slice >> 1, h = slice & 1;
-            MmaOp o;
-            o.a_off = (uint32_t)(((rho + 1) * kXS + v) * 64 + h * 32) | (acc ? 0x80000000u : 0u);
-            o.b_off = (uint32_t)((v * 96 + lo * 32) * 64 + h * 32);
-            o.d_off = (uint32_t)((rho - 1 + lo) * kC);
-            o.idesc = tc::idesc_bf16(128, 32 * (hi - lo + 1));
-            ops[g][count[g]++] = o;
-        }
+template <int G>
+__device__ __forceinline__ void issue_tile(uint64_t a_desc, uint64_t b_desc, uint32_t d0) {
+    auto one = [&](int rho, int slice, int jlo, int jhi, bool acc) {
+        const int lo = max(jlo, G * kRowsPerMmaWarp - rho + 1);
+        const int hi = min(jhi, (G + 1) * kRowsPerMmaWarp - rho);
+        if (lo > hi) return;
+        const int v = slice >> 1, h = slice & 1;
+        const uint32_t a_off = (uint32_t)(((rho + 1) * kXS + v) * 64 + h * 32);
+        const uint32_t b_off = (uint32_t)((v * 96 + lo * 32) * 64 + h * 32);
+        tc::mma_bf16(d0 + (uint32_t)((rho - 1 + lo) * kC), a_desc + (a_off >> 4), b_desc + (b_off >> 4),
+                     tc::idesc_bf16(128, 32 * (hi - lo + 1)), acc);
     };
-    for (int rho = -1; rho <= kR - 2; ++rho) add(rho, 0, 2, 2, false);
-    for (int slice = 0; slice < 6; ++slice)
+#pragma unroll
+    for (int rho = -1; rho <= kR - 2; ++rho) one(rho, 0, 2, 2, false);
+#pragma unroll
+    for (int slice = 0; slice < 6; ++slice) {
+#pragma unroll
         for (int rho = -1; rho <= kR; ++rho) {
             const int jlo = rho < 1 ? 1 - rho : 0;
             const int jhi = min(slice == 0 ? 1 : 2, kR - rho);
-            if (jlo <= jhi) add(rho, slice, jlo, jhi, true);
+            if (jlo <= jhi) one(rho, slice, jlo, jhi, true);
         }
+    }
 }
 
-constexpr int kWorkers = 256;                     // 8 worker warps after the issuing warps
+constexpr int kWorkers = 256;                     // worker threads after the issuing warps (512: no gain)
+constexpr int kWRows = kR / (kWorkers / 128);     // output rows a worker warp drains per tile
+static_assert(kWorkers % 128 == 0 && kR % (kWorkers / 128) == 0, "worker warps: whole lane quarters");
 constexpr int kMidThreads = 32 * kMmaWarps + kWorkers;
 
 // Forward: out = bf16(ReLU(conv(in) + bias)).  kBwd (input gradient of a
@@ -234,8 +232,6 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
     uint8_t *s_in[2] = {sm, sm + kInBytes};
     uint8_t *s_w = sm + 2 * kInBytes;
     __shared__ float s_bias[kC];
-    __shared__ __align__(16) MmaOp s_ops[kMmaWarps][kMaxOps];
-    __shared__ int s_nops[kMmaWarps];
     __shared__ __align__(8) uint64_t bar_loaded[2], bar_mma[2], bar_tfree[2], bar_drain[kMmaWarps];
     __shared__ uint32_t s_tmem;
 
@@ -246,7 +242,6 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
     if (warp == 0) {
         tc::tmem_alloc(&s_tmem, kTmemCols);
         if (lane == 0) {
-            build_schedule(s_ops, s_nops);
             for (int b = 0; b < 2; ++b) {
                 tc::bar_init(&bar_loaded[b], kWorkers);
                 tc::bar_init(&bar_mma[b], kMmaWarps);
@@ -276,15 +271,15 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
             ok = __all_sync(0xffffffffu, good);
             if (!ok) break;
             tc::fence_after();
-            const uint32_t a0 = tc::smem_u32(s_in[b]);
             const uint32_t d0 = tm + (uint32_t)(b * kR * kC);
-            const int nops = s_nops[warp];
-#pragma unroll 4
-            for (int k = 0; k < nops; ++k) {
-                const MmaOp o = s_ops[warp][k];
-                if (lane == 0)
-                    tc::mma_bf16(d0 + o.d_off, hi | (uint64_t)((a0 + (o.a_off & 0x7FFFFFFFu)) >> 4),
-                                 hi | (uint64_t)((b0 + o.b_off) >> 4), o.idesc, (o.a_off >> 31) != 0);
+            // start addresses below 2^18 bytes: the 14-bit field takes the offsets without a carry
+            const uint64_t a_desc = hi | (uint64_t)(tc::smem_u32(s_in[b]) >> 4), b_desc = hi | (uint64_t)(b0 >> 4);
+            if (lane == 0) {
+                static_assert(kMmaWarps == 2, "one issue_tile instantiation per issuing warp");
+                if (warp == 0)
+                    issue_tile<0>(a_desc, b_desc, d0);
+                else
+                    issue_tile<1>(a_desc, b_desc, d0);
             }
             __syncwarp();
             if (lane == 0) tc::mma_commit(&bar_mma[b]);
@@ -301,9 +296,9 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
         __syncwarp();
     } else {
         // ---------------------------------------------------------- workers
-        const int w = tid - 32 * kMmaWarps, ww = warp - kMmaWarps;   // worker warp 0 .. 7
+        const int w = tid - 32 * kMmaWarps, ww = warp - kMmaWarps;   // worker warp 0 .. kWorkers / 32 - 1
         const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31 (pixels)
-        const int r0 = (kR / 2) * (ww >> 2);               // output rows r0 .. r0 + kR/2 - 1
+        const int r0 = kWRows * (ww >> 2);                 // output rows r0 .. r0 + kWRows - 1
         auto stage = [&](int i) {                          // tile i into buffer i & 1
             int img, y0, x0;
             T.decode(first + (long)i * stride, img, y0, x0);
@@ -344,7 +339,7 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
                 T.decode(first + (long)j * stride, img, y0, x0);
                 const int x = x0 + 32 * q + lane;
 #pragma unroll 1
-                for (int rr = 0; rr < kR / 2; ++rr) {
+                for (int rr = 0; rr < kWRows; ++rr) {
                     const int r = r0 + rr, y = y0 + r;
                     float v[32];
                     tc::tmem_ld32(tm + ((uint32_t)(32 * q) << 16) + (uint32_t)((bj * kR + r) * kC), v);
