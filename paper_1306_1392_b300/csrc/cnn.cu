@@ -10,7 +10,7 @@
 //   layers 2-7 (32 -> 32): conv_mid_kernel, tcgen05 implicit GEMM:
 //                          M = 128 pixels of one row, N = 32 output channels,
 //                          K = 9 taps x 32 input channels in 18 steps of 16
-//   layer 8   (32 -> 1) + residual: conv_last_kernel, CUDA cores
+//   layer 8   (32 -> 1) + residual: conv_last_rows_kernel, CUDA cores
 #include <cmath>
 #include <algorithm>
 #include <utility>
@@ -379,57 +379,88 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
 }
 
 // ----------------------------------------------------------------- layer 8
-// One thread per pixel: r = sum over 3x3 x 32 of bf16(W_8) a_7, out = z + r + b_8.
-// The CTA's three input rows (130 pixels each, 64 B per pixel) are staged in
-// shared memory channel-chunk-major, s[row][chunk][pixel], by coalesced
-// 16-byte copies, so that a warp's reads of one (tap, chunk) are 32
-// consecutive 16-byte words.  The sum runs over taps, then chunks, then
-// channels, as before the staging (same bits).
-__global__ void __launch_bounds__(128) conv_last_kernel(const uint4 *__restrict__ act, const float *__restrict__ z,
-                                                        const float *__restrict__ params, float *__restrict__ out,
-                                                        int H, int W) {
-    __shared__ __align__(16) float sw[9 * kC];         // [tap][channel]
-    __shared__ __align__(16) uint4 srow[3][4][130];
-    const int x0 = blockIdx.x * 128, y = blockIdx.y, img = blockIdx.z;
-    for (int i = threadIdx.x; i < 9 * kC; i += 128) {
-        const int c = i / 9, t = i % 9;                    // params hold W_8[0][c][t]
+// r = sum over 3x3 x 32 of bf16(W_8) a_7, out = z + r + b_8.
+// Layer 8, several output rows per CTA: a CTA of 128 threads reconstructs
+// kLR rows x 128 pixels; its kLR + 2 input rows are staged once (the
+// single-row kernel above stages three rows per output row).  A thread owns
+// one column: each staged 8-channel chunk it unpacks feeds up to three of its
+// output rows (kernel rows u = 0, 1, 2), the 24 weights of a (kernel column,
+// chunk) pair stay in registers while it walks the rows, and channel pairs
+// accumulate in paired float32 (two partial sums per row, added at the end).
+template <int kLR>
+__global__ void __launch_bounds__(128) conv_last_rows_kernel(const uint4 *__restrict__ act,
+                                                             const float *__restrict__ z,
+                                                             const float *__restrict__ params,
+                                                             float *__restrict__ out, int H, int W) {
+    extern __shared__ __align__(16) uint4 srows[];                 // [kLR + 2][4][130]
+    __shared__ __align__(16) float sw[9 * kC];                      // [tap][channel]
+    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kLR, img = blockIdx.z, tid = threadIdx.x;
+    for (int i = tid; i < 9 * kC; i += 128) {
+        const int c = i / 9, t = i % 9;                              // params hold W_8[0][c][t]
         sw[t * kC + c] = bf16r(params[kW8 + i]);
     }
-#pragma unroll
-    for (int rr = 0; rr < 3; ++rr) {                          // asynchronous copies, all in flight at once
-        const int yy = y - 1 + rr;
+    for (int rr = 0; rr < kLR + 2; ++rr) {                           // asynchronous copies, all in flight at once
+        const int yy = y0 - 1 + rr;
         const bool row_in = yy >= 0 && yy < H;
         const uint4 *src_row = act + act_idx(img, row_in ? yy : 0, 0, 0, H, W);
-        for (int e = threadIdx.x; e < 130 * 4; e += 128) {   // e = 4 px + c: consecutive 16-byte words
+        for (int e = tid; e < 130 * 4; e += 128) {                  // e = 4 px + c: consecutive 16-byte words
             const int px = e >> 2, c = e & 3, xx = x0 - 1 + px;
             const bool in = row_in && xx >= 0 && xx < W;
-            tc::cp16(&srow[rr][c][px], in ? src_row + 4 * xx + c : act, in ? 16u : 0u);
+            tc::cp16(&srows[(rr * 4 + c) * 130 + px], in ? src_row + 4 * xx + c : act, in ? 16u : 0u);
         }
     }
     tc::cp_wait_all();
     __syncthreads();
-    const int x = x0 + threadIdx.x;
+    const int x = x0 + tid;
     if (x >= W) return;
-
-    float acc = 0.0f;
+    float2 acc[kLR];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    for (int r = 0; r < kLR; ++r) acc[r] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const int xx = x + v - 1;
+        if (xx < 0 || xx >= W) continue;                            // taps outside the image add nothing
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float v[8];
-            unpack8(srow[t / 3][c][threadIdx.x + t % 3], v);
-            const float4 w0 = *reinterpret_cast<const float4 *>(&sw[t * kC + 8 * c]);
-            const float4 w1 = *reinterpret_cast<const float4 *>(&sw[t * kC + 8 * c + 4]);
-            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float2 wt[3][4];                                         // kernel rows u = 0, 1, 2
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc = fmaf(w[k], v[k], acc);
+            for (int u = 0; u < 3; ++u) {
+                const float4 w0 = *reinterpret_cast<const float4 *>(&sw[(3 * u + v) * kC + 8 * c]);
+                const float4 w1 = *reinterpret_cast<const float4 *>(&sw[(3 * u + v) * kC + 8 * c + 4]);
+                wt[u][0] = make_float2(w0.x, w0.y);
+                wt[u][1] = make_float2(w0.z, w0.w);
+                wt[u][2] = make_float2(w1.x, w1.y);
+                wt[u][3] = make_float2(w1.z, w1.w);
+            }
+#pragma unroll
+            for (int rr = 0; rr < kLR + 2; ++rr) {
+                const int yy = y0 - 1 + rr;
+                if (yy < 0 || yy >= H) continue;
+                float p[8];
+                unpack8(srows[(rr * 4 + c) * 130 + tid + v], p);
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int r = rr - u;                            // output row y0 + r reads row yy at kernel row u
+                    if (r < 0 || r >= kLR) continue;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[r] = fma2(wt[u][k], make_float2(p[2 * k], p[2 * k + 1]), acc[r]);
+                }
+            }
         }
     }
-    const size_t o = ((size_t)img * H + y) * W + x;
-    out[o] = z[o] + (acc + params[kB8]);
+    const float b8 = params[kB8];
+#pragma unroll
+    for (int r = 0; r < kLR; ++r) {
+        const int y = y0 + r;
+        if (y >= H) break;
+        const size_t o = ((size_t)img * H + y) * W + x;
+        out[o] = z[o] + ((acc[r].x + acc[r].y) + b8);
+    }
 }
+template <int kLR> constexpr int last_rows_smem() { return (kLR + 2) * 4 * 130 * 16; }
+// rows per CTA: 4 (49.9 KB of staged rows, four CTAs per SM; 2 was slower, the
+// one-row kernel it replaced 4 % slower over a forward pass)
+constexpr int kLastRows = 4;
 
 bool cnn_sizes_ok(int n, int H, int W) { return n >= 1 && n <= 65535 && H >= 1 && W >= 1 && H <= 16384 && W <= 16384; }
 
@@ -443,11 +474,9 @@ int set_smem_attrs() {
         cudaFuncSetAttribute(conv_mid_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMidSmem) !=
             cudaSuccess)
         return cuda_status("conv_mid_kernel shared-memory attribute");
-    // the last layer's 26 KB of staged rows per 128-pixel CTA: ask for the
-    // largest shared-memory carve-out so that eight CTAs fit on an SM
-    if (cudaFuncSetAttribute(conv_last_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-        return cuda_status("conv_last_kernel carve-out attribute");
+    if (cudaFuncSetAttribute(conv_last_rows_kernel<kLastRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             last_rows_smem<kLastRows>()) != cudaSuccess)
+        return cuda_status("conv_last_rows_kernel shared-memory attribute");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return PYHST_OK;
 }
@@ -504,8 +533,9 @@ int forward_pass(const float *params, const float *z, float *out, int n, int H, 
             return rc;
         src = dst;
     }
-    conv_last_kernel<<<dim3((W + 127) / 128, H, n), 128, 0, st>>>(src, z, params, out, H, W);
-    return cuda_status("conv_last_kernel");
+    conv_last_rows_kernel<kLastRows><<<dim3((W + 127) / 128, (H + kLastRows - 1) / kLastRows, n), 128,
+                                        last_rows_smem<kLastRows>(), st>>>(src, z, params, out, H, W);
+    return cuda_status("conv_last_rows_kernel");
 }
 
 
