@@ -111,25 +111,29 @@ __global__ void __launch_bounds__(128) conv_first_kernel(const float *__restrict
                 const int yy = y + u - 1, xx = x + v - 1;
                 nb[3 * u + v] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? zi[(size_t)yy * W + xx] : 0.0f;
             }
-        float a[kC];                                     // per channel, taps summed in order 0 .. 8
+        // per channel, taps summed in order 0 .. 8; channel pairs share paired
+        // fmas (each half rounds as its scalar fma would)
+        float2 a[kC / 2];
 #pragma unroll
-        for (int ch = 0; ch < kC; ++ch) a[ch] = 0.0f;
+        for (int ch = 0; ch < kC / 2; ++ch) a[ch] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
+            const float2 zt = make_float2(nb[t], nb[t]);
 #pragma unroll
             for (int q = 0; q < kC / 4; ++q) {
                 const float4 w = *reinterpret_cast<const float4 *>(&sw[t * kC + 4 * q]);
-                a[4 * q] = fmaf(w.x, nb[t], a[4 * q]);
-                a[4 * q + 1] = fmaf(w.y, nb[t], a[4 * q + 1]);
-                a[4 * q + 2] = fmaf(w.z, nb[t], a[4 * q + 2]);
-                a[4 * q + 3] = fmaf(w.w, nb[t], a[4 * q + 3]);
+                a[2 * q] = fma2(make_float2(w.x, w.y), zt, a[2 * q]);
+                a[2 * q + 1] = fma2(make_float2(w.z, w.w), zt, a[2 * q + 1]);
             }
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             float o[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) o[k] = fmaxf(a[8 * c + k] + sb[8 * c + k], 0.0f);
+            for (int k = 0; k < 4; ++k) {
+                o[2 * k] = fmaxf(a[4 * c + k].x + sb[8 * c + 2 * k], 0.0f);
+                o[2 * k + 1] = fmaxf(a[4 * c + k].y + sb[8 * c + 2 * k + 1], 0.0f);
+            }
             so[c][threadIdx.x] = pack8(o);
         }
     }
