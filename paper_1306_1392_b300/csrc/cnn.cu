@@ -237,6 +237,10 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
     uint8_t *s_w = sm + 2 * kInBytes;
     __shared__ float s_bias[kC];
     __shared__ __align__(8) uint64_t bar_loaded[2], bar_mma[2], bar_tfree[2], bar_drain[kMmaWarps];
+    // a worker warp's 32 output pixels, chunk-major, on their way to coalesced
+    // stores (rows of 34 words: both the chunk-row writes and the
+    // pixel-major reads are free of bank conflicts)
+    __shared__ __align__(16) uint4 s_out[kWorkers / 32][4][34];
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -347,7 +351,8 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
                     const int r = r0 + rr, y = y0 + r;
                     float v[32];
                     tc::tmem_ld32(tm + ((uint32_t)(32 * q) << 16) + (uint32_t)((bj * kR + r) * kC), v);
-                    if (x < T.W && y < T.H) {
+                    const bool row_in = y < T.H;
+                    if (row_in && x < T.W) {
                         const size_t px = act_idx(img, y, x, 0, T.H, T.W);
                         if (kBwd) {
 #pragma unroll
@@ -362,8 +367,23 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
                             for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + s_bias[k], 0.0f);
                         }
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) out[px + c] = pack8(v + 8 * c);
+                        for (int c = 0; c < 4; ++c) s_out[ww][c][lane] = pack8(v + 8 * c);
                     }
+                    __syncwarp();
+                    // the warp's pixels x0 + 32 q .. + 31 are consecutive in NHWC: 16-byte word
+                    // e = 4 pixel + chunk of them, stored by lane e mod 32 (512 contiguous bytes per store)
+                    if (row_in) {
+                        const int xw = x0 + 32 * q, npx = min(32, T.W - xw);
+                        if (npx > 0) {
+                            uint4 *dst = out + act_idx(img, y, xw, 0, T.H, T.W);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const int e = lane + 32 * k;
+                                if ((e >> 2) < npx) dst[e] = s_out[ww][e & 3][e >> 2];
+                            }
+                        }
+                    }
+                    __syncwarp();
                 }
                 tc::fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bar_tfree[bj])) : "memory");
