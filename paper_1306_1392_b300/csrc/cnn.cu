@@ -404,10 +404,12 @@ __global__ void __launch_bounds__(kMidThreads, 1) conv_mid_kernel(const uint4 *_
 
 // ----------------------------------------------------------------- layer 8
 // r = sum over 3x3 x 32 of bf16(W_8) a_7, out = z + r + b_8.
-// Layer 8, several output rows per CTA: a CTA of 128 threads reconstructs
-// kLR rows x 128 pixels; its kLR + 2 input rows are staged once (the
-// single-row kernel above stages three rows per output row).  A thread owns
-// one column: each staged 8-channel chunk it unpacks feeds up to three of its
+// A CTA of 128 threads reconstructs kLR rows x 128 pixels; its kLR + 2 input
+// rows (130 pixels each, 64 B per pixel) are staged once in shared memory,
+// channel-chunk-major, by asynchronous 16-byte copies, so that a warp's reads
+// of one (tap, chunk) are 32 consecutive 16-byte words (staging three rows
+// per output row cost 4 % more over a forward pass).  A thread owns one
+// column: each staged 8-channel chunk it unpacks feeds up to three of its
 // output rows (kernel rows u = 0, 1, 2), the 24 weights of a (kernel column,
 // chunk) pair stay in registers while it walks the rows, and channel pairs
 // accumulate in paired float32 (two partial sums per row, added at the end).
