@@ -73,20 +73,34 @@ constexpr int kPTargetCtas = 148 * 3 * 4;   // below this, the rows are split in
 constexpr int kPBandWin = 128;              // chunks whose bands are computed at once (1 KB of shared memory)
 constexpr double kFix = 4294967296.0;   // 2^32
 
+// out = in^T for the 64 x 64 tile at (r0, c0) of a rows x cols array, by 32 x 8
+// threads (16 elements each; rows of 65 floats: conflict-free both ways)
+constexpr int kTT = 64;
+__device__ __forceinline__ void transpose_tile(const float *__restrict__ in, float *__restrict__ out, int rows,
+                                               int cols, int r0, int c0) {
+    __shared__ float tile[kTT][kTT + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int k = ty; k < kTT; k += 8)
+#pragma unroll
+        for (int h = 0; h < kTT; h += 32) {
+            const int r = r0 + k, c = c0 + tx + h;
+            if (r < rows && c < cols) tile[k][tx + h] = in[(size_t)r * cols + c];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k = ty; k < kTT; k += 8)
+#pragma unroll
+        for (int h = 0; h < kTT; h += 32) {
+            const int c = c0 + k, r = r0 + tx + h;
+            if (r < rows && c < cols) out[(size_t)c * rows + r] = tile[tx + h][k];
+        }
+}
+
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int rows,
                                  int cols) {
-    __shared__ float tile[32][33];
     const size_t off = (size_t)blockIdx.z * rows * cols;
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) tile[k][threadIdx.x] = in[off + (size_t)r * cols + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) out[off + (size_t)c * rows + r] = tile[threadIdx.x][k];
-    }
+    transpose_tile(in + off, out + off, rows, cols, blockIdx.y * kTT, blockIdx.x * kTT);
 }
 
 // One angle's walk over a row-major [R][C] array (image rows when |cos| >=
@@ -517,22 +531,11 @@ proj_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict_
                  s.pixel_size, it.z * kPG, it.y * kPB, -1, s.proj_nseg);
 }
 
-// Mixed batch transpose: CTA k moves 32 x 32 tile (items[k].y, items[k].z) of slice items[k].x.
+// Mixed batch transpose: CTA k moves 64 x 64 tile (items[k].y, items[k].z) of slice items[k].x.
 __global__ void transpose_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items) {
-    __shared__ float tile[32][33];
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
-    const int rows = s.ny, cols = s.nx;
-    const int c0 = it.y * 32, r0 = it.z * 32;
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) tile[k][threadIdx.x] = s.proj_in[(size_t)r * cols + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) s.proj_inT[(size_t)c * rows + r] = tile[threadIdx.x][k];
-    }
+    transpose_tile(s.proj_in, s.proj_inT, s.ny, s.nx, it.z * kTT, it.y * kTT);
 }
 
 }  // namespace
@@ -657,7 +660,7 @@ size_t project_scratch_bytes(const pyhst_geometry *g) {
 int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
                    float scale, float *xt, cudaStream_t st, int staging) {
     if (g->n_slices > 65535) return fail(PYHST_ERR_INVALID_ARG, "too many slices in one call (%d)", g->n_slices);
-    dim3 tb(32, 8), tg((g->nx + 31) / 32, (g->ny + 31) / 32, g->n_slices);
+    dim3 tb(32, 8), tg((g->nx + kTT - 1) / kTT, (g->ny + kTT - 1) / kTT, g->n_slices);
     transpose_kernel<<<tg, tb, 0, st>>>(img, xt, g->ny, g->nx);
     int rc = cuda_status("transpose kernel");
     if (rc) return rc;

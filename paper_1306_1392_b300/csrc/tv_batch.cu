@@ -424,8 +424,8 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     for (int a = 0; a < na; ++a)
         for (int b = 0; b < nb; ++b) pr.push_back(make_int4(s, b, a, 0));
     auto &tr = rep_only ? P.tr_r : P.tr;
-    for (int y = 0; y < (g.ny + 31) / 32; ++y)
-        for (int x = 0; x < (g.nx + 31) / 32; ++x) tr.push_back(make_int4(s, x, y, 0));
+    for (int y = 0; y < (g.ny + 63) / 64; ++y)     // the projector's transpose moves 64 x 64 tiles
+        for (int x = 0; x < (g.nx + 63) / 64; ++x) tr.push_back(make_int4(s, x, y, 0));
     auto &px = rep_only ? P.px_r : P.px;
     for (int y = 0; y < (g.ny + kPxRows - 1) / kPxRows; ++y)
         for (int x = 0; x < (g.nx + 31) / 32; ++x) px.push_back(make_int4(s, x, y, 0));
