@@ -247,10 +247,12 @@ def power_iteration(g: Geometry, v0, n_it=50):
 
 
 def fista(g: Geometry, sino, beta, L, n_iter, n_inner=20, tau=0.125, use_fista=True, x0=None, return_z=False,
-          return_gap=False):
+          return_gap=False, warm_dual=False):
     """ISTA/FISTA on Eq. 3; returns (x, energy history [n_iter]), then, with
     return_z, the prox input z of the last iteration and, with return_gap,
-    the ROF duality gap of every iteration's prox [n_iter]."""
+    the ROF duality gap of every iteration's prox [n_iter].  warm_dual: each
+    prox's dual field starts at the previous one's final field instead of
+    zero."""
     sino, ps = _c(sino)
     x = np.zeros((g.ny, g.nx)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     e = np.empty(n_iter)
@@ -259,7 +261,8 @@ def fista(g: Geometry, sino, beta, L, n_iter, n_inner=20, tau=0.125, use_fista=T
     gc = g._c()
     lib().orc_fista_z(ctypes.byref(gc), ps, D(beta), D(L), I64(n_iter), I64(n_inner), D(tau),
                       ctypes.c_int(1 if use_fista else 0), x.ctypes.data_as(PD), e.ctypes.data_as(PD),
-                      gp.ctypes.data_as(PD) if return_gap else None, z.ctypes.data_as(PD) if return_z else None)
+                      gp.ctypes.data_as(PD) if return_gap else None, z.ctypes.data_as(PD) if return_z else None,
+                      ctypes.c_int(1 if warm_dual else 0))
     out = (x, e) + ((z,) if return_z else ()) + ((gp,) if return_gap else ())
     return out
 

@@ -394,7 +394,7 @@ double orc_power_iteration(const orc_geom *g, double *v, int64_t n_it)
  * field; 0 when beta = 0, where the prox is the identity) */
 void orc_fista_z(const orc_geom *g, const double *sino, double beta, double L,
                  int64_t n_iter, int64_t n_inner, double tau, int fista,
-                 double *x, double *energy, double *gap, double *z_last)
+                 double *x, double *energy, double *gap, double *z_last, int warm_dual)
 {
     int64_t n = g->nx * g->ny, m = g->n_angles * g->n_bins;
     double *y = (double *)malloc(sizeof(double) * n);
@@ -412,8 +412,12 @@ void orc_fista_z(const orc_geom *g, const double *sino, double beta, double L,
         for (int64_t q = 0; q < m; q++) r[q] -= sino[q];
         PT_apply(g, r, grad);
         for (int64_t q = 0; q < n; q++) z[q] = y[q] - grad[q] / L;
-        memset(p1, 0, sizeof(double) * n);
-        memset(p2, 0, sizeof(double) * n);
+        /* the dual field starts at zero (the reading: a cold start), or with
+         * warm_dual at the previous iteration's final dual field */
+        if (k == 0 || !warm_dual) {
+            memset(p1, 0, sizeof(double) * n);
+            memset(p2, 0, sizeof(double) * n);
+        }
         orc_tv_prox(z, g->ny, g->nx, beta / L, tau, n_inner, p1, p2, x);
         if (gap) gap[k] = beta > 0.0 ? orc_rof_gap(z, g->ny, g->nx, beta / L, p1, p2) : 0.0;
         double tn = fista ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
@@ -433,7 +437,7 @@ void orc_fista(const orc_geom *g, const double *sino, double beta, double L,
                int64_t n_iter, int64_t n_inner, double tau, int fista,
                double *x, double *energy)
 {
-    orc_fista_z(g, sino, beta, L, n_iter, n_inner, tau, fista, x, energy, NULL, NULL);
+    orc_fista_z(g, sino, beta, L, n_iter, n_inner, tau, fista, x, energy, NULL, NULL, 0);
 }
 
 /* ---------------------------------------------------------------------

@@ -278,3 +278,30 @@ def test_fista_gap_history(orc):
     assert np.all(g0 == 0)
     first = [orc.fista(geo, y, beta, L, 1, n_inner=m, return_gap=True)[2][0] for m in (2, 8, 32, 128)]
     assert all(b < a for a, b in zip(first, first[1:])), first
+
+
+def test_fista_dual_warm_start(orc):
+    """The dual warm start (each prox's dual field starting at the previous
+    prox's final field): its first iteration is the cold start's, bit for bit;
+    with near-exact proxes (many inner steps) it reaches the cold-start
+    iterates; with few inner steps its proxes end closer to exact (smaller
+    duality gaps) once the prox inputs change slowly."""
+    geo = _tiny_geometry(orc, n=16, na=6, nb=24, seed=2)
+    g = np.random.default_rng(23)
+    xt = np.zeros((16, 16))
+    xt[3:11, 4:12] = 1.0
+    xt[6:9, 6:14] += 0.5
+    y = geo.P(xt) + 0.02 * g.standard_normal((6, 24))
+    L = 1.01 * orc.power_iteration(geo, g.standard_normal((16, 16)), 100)[0]
+    beta = 0.02
+    x1c, _ = orc.fista(geo, y, beta, L, 1, n_inner=5)
+    x1w, _ = orc.fista(geo, y, beta, L, 1, n_inner=5, warm_dual=True)
+    assert np.array_equal(x1c, x1w)
+    xc, _ = orc.fista(geo, y, beta, L, 8, n_inner=600)
+    xw, _ = orc.fista(geo, y, beta, L, 8, n_inner=600, warm_dual=True)
+    assert np.linalg.norm(xw - xc) <= 1e-6 * np.linalg.norm(xc)
+    _, _, gc = orc.fista(geo, y, beta, L, 30, n_inner=5, return_gap=True)
+    xw5, _, gw = orc.fista(geo, y, beta, L, 30, n_inner=5, return_gap=True, warm_dual=True)
+    assert gw[0] == gc[0]
+    assert np.mean(gw[10:]) < 0.5 * np.mean(gc[10:]), (np.mean(gw[10:]), np.mean(gc[10:]))
+    assert not np.array_equal(xw5, orc.fista(geo, y, beta, L, 30, n_inner=5)[0])
