@@ -232,13 +232,19 @@ typedef struct {
     int32_t warm_start;  /* 1: x holds the start iterate; 0: start from zeros       */
     double lipschitz;    /* L >= ||P||^2; 0: estimate 1.01 * lambda_max(P^T P)       */
     int32_t n_power_iter;/* power iterations of the estimate (from the all-ones image) */
+    int32_t warm_dual;   /* 1: each TV prox after the first starts its Chambolle steps
+                          * from the previous prox's final dual field (its input z
+                          * moves little between outer iterations); 0: from a zero
+                          * field, as the prox is defined (Sec. 3.1).  Changes the
+                          * iterates; ignored by the learned prox. */
 } pyhst_tv_opts;
 
 /* Solve x = argmin 1/2 ||sino - P x||^2 + beta TV(x) (Eq. 3) for each of the
  * n_slices slices of g, with P = pyhst_project's operator and TV the
  * isotropic total variation of Eq. 2 (forward differences, Neumann
  * boundary).  Each outer iteration takes a gradient step of length 1/L and
- * the prox of (beta/L) TV by n_inner Chambolle steps from a zero dual field.
+ * the prox of (beta/L) TV by n_inner Chambolle steps from a zero dual field
+ * (from the previous prox's field with warm_dual).
  *   sino   [n_slices][n_angles][n_bins]
  *   x      [n_slices][ny][nx]  in: start (if warm_start), out: last iterate
  *   energy [n_slices][n_iter] float64 DEVICE or NULL: Eq. 3 at every iterate

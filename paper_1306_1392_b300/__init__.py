@@ -110,10 +110,12 @@ class TvOptions:
     warm_start: bool = False
     lipschitz: float = 0.0
     n_power_iter: int = 50
+    warm_dual: bool = False
 
     def c(self) -> L.pyhst_tv_opts:
         return L.pyhst_tv_opts(self.beta, self.n_iter, self.n_inner, self.tau, int(bool(self.use_fista)),
-                               int(bool(self.warm_start)), self.lipschitz, self.n_power_iter)
+                               int(bool(self.warm_start)), self.lipschitz, self.n_power_iter,
+                               int(bool(self.warm_dual)))
 
 
 def pyhst_fbp_workspace_size(geom: Geometry, n_slices: int = 1, pad_len: int = 0, slices_per_pass: int = 4) -> int:

@@ -40,7 +40,7 @@ class pyhst_patch_problem(ctypes.Structure):
 class pyhst_tv_opts(ctypes.Structure):
     _fields_ = [("beta", c_float), ("n_iter", c_int32), ("n_inner", c_int32), ("tau", c_float),
                 ("use_fista", c_int32), ("warm_start", c_int32), ("lipschitz", c_double),
-                ("n_power_iter", c_int32)]
+                ("n_power_iter", c_int32), ("warm_dual", c_int32)]
 
 
 class pyhst_preproc(ctypes.Structure):

@@ -148,8 +148,9 @@ __global__ void fill_kernel(float *__restrict__ v, float val, size_t n) {
 }
 
 // n_inner Chambolle steps in launches of up to K fused steps (see
-// chambolle.cuh): launch 0 starts from a zero field and writes the "a"
-// buffers, launch m > 0 reads a (m odd) or b and writes the other.
+// chambolle.cuh).  m is the launch's parity index: m = 0 starts from a zero
+// field and writes the "a" buffers, m > 0 reads a (m odd) or b and writes the
+// other, so a chain of launches with consecutive indices hands the field on.
 template <int K>
 __global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, float *pb1, float *pb2,
@@ -167,7 +168,7 @@ chambolle_fused_kernel(const float *__restrict__ z, float *pa1, float *pa2, floa
 template <int K>
 int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
                        int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, float *x,
-                       bool keep_p) {
+                       bool keep_p, int q0) {
     constexpr int Th = chambolle_tile_h(K), Tw = chambolle_tile_w(K);
     const int tx = (nx + Tw - 1) / Tw, ty = (ny + Th - 1) / Th;
     const int L = chambolle_launches(n_inner, K);
@@ -181,13 +182,13 @@ int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float
             constexpr int Th1 = chambolle_tile_h(K + 1), Tw1 = chambolle_tile_w(K + 1);
             const int tx1 = (nx + Tw1 - 1) / Tw1, ty1 = (ny + Th1 - 1) / Th1;
             chambolle_fused_kernel<K + 1><<<dim3(tx1 * ty1, n_slices), kChThreads, kChSmem, st>>>(
-                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx1, x, keep_p);
+                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, q0 + m, steps, tx1, x, keep_p);
         } else {
             chambolle_fused_kernel<K><<<dim3(tx * ty, n_slices), kChThreads, kChSmem, st>>>(
-                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, m, steps, tx, nullptr, false);
+                z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, q0 + m, steps, tx, nullptr, false);
         }
     }
-    *final_a = (L & 1) == 1;
+    *final_a = ((q0 + L - 1) & 1) == 0;
     return cuda_status("Chambolle kernels");
 }
 
@@ -196,13 +197,15 @@ int launch_chambolle_k(const float *z, float *pa1, float *pa2, float *pb1, float
 // field ends in the a buffers.  With x given, the last launch writes the prox
 // x = z - lam div p there instead of the dual field (the divergence with
 // the Neumann boundary of Eq. 2, then one fma), and with keep_p the final
-// dual field as well.
+// dual field as well.  q0 is the parity index of the first launch: 0 starts
+// from a zero field; q0 > 0 starts from the field in the a buffers (q0 odd)
+// or b, such as the field a previous chain kept.
 int launch_chambolle(const float *z, float *pa1, float *pa2, float *pb1, float *pb2, const float *lam, float tau,
                      int nx, int ny, int n_slices, int n_inner, bool *final_a, cudaStream_t st, int K = 0,
-                     float *x = nullptr, bool keep_p = false) {
+                     float *x = nullptr, bool keep_p = false, int q0 = 0) {
     if (K <= 0) K = chambolle_k_for(nx, ny);
     PYHST_CHAMBOLLE_DISPATCH(K, launch_chambolle_k, z, pa1, pa2, pb1, pb2, lam, tau, nx, ny, n_slices, n_inner,
-                             final_a, st, x, keep_p)
+                             final_a, st, x, keep_p, q0)
 }
 
 // ROF duality gap of the prox (Eq. 2 with the quadratic term of the prox):
@@ -325,6 +328,7 @@ int check_tv_opts(const pyhst_tv_opts *o) {
         return fail(PYHST_ERR_INVALID_ARG, "lipschitz must be >= 0 (0: estimate)");
     if (o->lipschitz == 0.0 && o->n_power_iter < 1)
         return fail(PYHST_ERR_INVALID_ARG, "n_power_iter must be >= 1 when lipschitz is estimated");
+    if (o->warm_dual != 0 && o->warm_dual != 1) return fail(PYHST_ERR_INVALID_ARG, "warm_dual must be 0 or 1");
     return PYHST_OK;
 }
 
@@ -393,6 +397,7 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
     if ((rc = cuda_status("solver start"))) return rc;
 
     double t = 1.0;
+    bool dual_a = true;   // where the last prox left its dual field
     for (int k = 0; k < o->n_iter; ++k) {
         // gradient step: z = y - (1/L) P^T (P y - sino)
         if ((rc = launch_backproject(g, B.tab, BpSource{Ry, nullptr, y, B.sc.invL}, z, s, st))) return rc;
@@ -403,10 +408,14 @@ int tv_solve_enqueue(const pyhst_geometry *g, const float *sino, const pyhst_tv_
         if (hk.cnn_params) {
             if ((rc = cnn_forward(hk.cnn_params, z, xn, S, g->ny, g->nx, hk.cnn_ws, st))) return rc;
         } else if (o->beta > 0.0f) {
+            // warm_dual: after the first prox, start from the field the previous
+            // one kept (q0 = 1 reads the a buffers, 2 the b buffers)
+            const int q0 = (o->warm_dual && k > 0) ? (dual_a ? 1 : 2) : 0;
             bool fa;
             if ((rc = launch_chambolle(z, p1a, p2a, p1b, p2b, B.sc.lam, o->tau, g->nx, g->ny, S, o->n_inner, &fa, st,
-                                       0, xn, gap != nullptr)))
+                                       0, xn, gap != nullptr || o->warm_dual, q0)))
                 return rc;
+            dual_a = fa;
             if (gap) {
                 gap_partial<<<eg, kRedThreads, 0, st>>>(xn, fa ? p1a : p1b, fa ? p2a : p2b, g->nx, g->ny, B.part[2]);
                 finalize_gap<<<S, kRedThreads, 0, st>>>(B.part[2], B.sc.lam, gap, o->n_iter, k);

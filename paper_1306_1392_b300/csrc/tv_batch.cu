@@ -83,8 +83,10 @@ __device__ __forceinline__ bool px_of(const int4 it, const TvSlice &s, int r, in
 }
 __device__ __forceinline__ int px_items(const TvSlice &s) { return ((s.nx + 31) / 32) * ((s.ny + kPxRows - 1) / kPxRows); }
 
-// Launch m of the fused Chambolle steps (see chambolle.cuh) on tile
-// (items[k].y, items[k].z) of slice items[k].x; slices with beta = 0 skip.
+// Launch of parity index m of the fused Chambolle steps (see chambolle.cuh;
+// m = 0 starts from a zero field and writes the a buffers, m > 0 reads a for
+// m odd, else b, and writes the other) on tile (items[k].y, items[k].z) of
+// slice items[k].x; slices with beta = 0 skip.
 template <int K>
 __global__ void __launch_bounds__(kChThreads, kChMinBlocks)
 b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal sc, float tau, int m, int steps,
@@ -105,10 +107,11 @@ b_chambolle(const TvSlice *__restrict__ d, const int4 *__restrict__ items, Scal 
     const bool odd = m & 1;
     const float *s1 = odd ? s.p1a : s.p1b, *s2 = odd ? s.p2a : s.p2b;
     float *d1 = (m == 0 || !odd) ? s.p1a : s.p1b, *d2 = (m == 0 || !odd) ? s.p2a : s.p2b;
-    // keep_p: the last launch also writes the final dual field of slices that report the gap
+    // keep_p: the last launch also writes the final dual field, of every slice
+    // (2) or of the slices that report the gap (1)
     // z / lam in registers: faster than shared memory for this kernel on the B300 (same bits)
     chambolle_tile<K, false>(s.z, s1, s2, d1, d2, sc.lam[it.x], tau, s.nx, s.ny, it.z * Th, it.y * Tw, steps, m == 0,
-                             xn, keep_p && s.gap != nullptr);
+                             xn, keep_p == 2 || (keep_p == 1 && s.gap != nullptr));
 }
 
 template <int K>
@@ -122,29 +125,31 @@ int b_chambolle_attr(int K) { PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_attr_k) }
 
 template <int K>
 int b_chambolle_launches_k(int nch, const TvSlice *T, const int4 *items, int nchf, const int4 *items_f, Scal sc,
-                           float tau, int n_inner, int par, int keep_p, cudaStream_t st) {
+                           float tau, int n_inner, int par, int keep_p, int q0, cudaStream_t st) {
     const int Lc = chambolle_launches(n_inner, K);
     for (int m = 0; m + 1 < Lc; ++m) {
         ProfScope prof(kProfChambolle, st);
-        b_chambolle<K><<<nch, kChThreads, kChSmemRegs, st>>>(T, items, sc, tau, m, chambolle_steps(n_inner, m, K), -1, 0);
+        b_chambolle<K><<<nch, kChThreads, kChSmemRegs, st>>>(T, items, sc, tau, q0 + m,
+                                                             chambolle_steps(n_inner, m, K), -1, 0);
     }
     // the last launch writes x_new; it reads p one row above and one column left
     // of its tiles, so it takes the halo of K + 1 steps (same bits)
     {
         ProfScope prof(kProfChambolle, st);
-        b_chambolle<K + 1><<<nchf, kChThreads, kChSmemRegs, st>>>(T, items_f, sc, tau, Lc - 1,
+        b_chambolle<K + 1><<<nchf, kChThreads, kChSmemRegs, st>>>(T, items_f, sc, tau, q0 + Lc - 1,
                                                               chambolle_steps(n_inner, Lc - 1, K), par, keep_p);
     }
     return cuda_status("batched Chambolle kernels");
 }
-// All launches of the Chambolle steps of one iteration; the last one writes
-// x_new (xa for par = 1, xb for par = 0) instead of the dual field, and with
-// keep_p the final dual field too (in the a buffers when the number of
-// launches is odd) for the slices that report the duality gap.
+// All launches of the Chambolle steps of one iteration, with parity indices
+// q0, q0 + 1, ..; the last one writes x_new (xa for par = 1, xb for par = 0)
+// instead of the dual field, and with keep_p the final dual field too (in the
+// a buffers when its index is even): of every slice for keep_p = 2, of the
+// slices that report the duality gap for keep_p = 1.
 int b_chambolle_launches(int K, int nch, const TvSlice *T, const int4 *items, int nchf, const int4 *items_f, Scal sc,
-                         float tau, int n_inner, int par, int keep_p, cudaStream_t st) {
+                         float tau, int n_inner, int par, int keep_p, int q0, cudaStream_t st) {
     PYHST_CHAMBOLLE_DISPATCH(K, b_chambolle_launches_k, nch, T, items, nchf, items_f, sc, tau, n_inner, par, keep_p,
-                             st)
+                             q0, st)
 }
 
 // Duality-gap partial of a pixel item (the prox's gap, lam * sum of
@@ -580,6 +585,7 @@ int check_tv_opts_b(const pyhst_tv_opts *o) {
         return fail(PYHST_ERR_INVALID_ARG, "lipschitz must be >= 0 (0: estimate)");
     if (o->lipschitz == 0.0 && o->n_power_iter < 1)
         return fail(PYHST_ERR_INVALID_ARG, "n_power_iter must be >= 1 when lipschitz is estimated");
+    if (o->warm_dual != 0 && o->warm_dual != 1) return fail(PYHST_ERR_INVALID_ARG, "warm_dual must be 0 or 1");
     return PYHST_OK;
 }
 
@@ -697,7 +703,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     double *part_gap = reinterpret_cast<double *>(ws + L.part_gap);
     bool any_gap = false;
     for (int q = 0; q < n; ++q) any_gap = any_gap || items[q].gap != nullptr;
-    const int pa_final = (chambolle_launches(opts->n_inner, P.chK) - 1) % 2 == 0;
+    const int Lch = chambolle_launches(opts->n_inner, P.chK);
     const int npx = (int)P.px.size(), nsn = (int)P.sn.size(), nbp = (int)P.bp.size(), npr = (int)P.proj.size(),
               ntr = (int)P.tr.size(), nch = (int)P.ch.size(), nchf = (int)P.chf.size();
     const dim3 tb(kBT);
@@ -747,6 +753,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     if (own_graph && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return cuda_status("graph capture begin");
     double t = 1.0;
+    bool dual_a = true;     // where the last prox left its dual field
     bool identity = true;   // no slice has a TV term: skip the Chambolle steps
     for (int q = 0; q < n; ++q) identity = identity && tv[q].beta == 0.0f;
     for (int k = 0; k < opts->n_iter && !rc; ++k) {
@@ -754,9 +761,14 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
         rc = launch_backproject_batch(D_even, I + o_bp, nbp, false, st, P.bpNA);
         if (rc) break;
         if (!identity) {                        // the last Chambolle launch writes x_new
+            // warm_dual: after the first prox, start from the field the previous
+            // one kept (parity index 1 reads the a buffers, 2 the b buffers)
+            const int q0 = (opts->warm_dual && k > 0) ? (dual_a ? 1 : 2) : 0;
+            const int pa_final = ((q0 + Lch - 1) & 1) == 0;
             rc = b_chambolle_launches(P.chK, nch, T, I + o_ch, nchf, I + o_chf, sc, opts->tau, opts->n_inner, par,
-                                      any_gap ? 1 : 0, st);
+                                      opts->warm_dual ? 2 : (any_gap ? 1 : 0), q0, st);
             if (rc) break;
+            dual_a = pa_final;
             if (any_gap) b_gap_partial<<<npx, tb, 0, st>>>(T, I + o_px, par, pa_final, part_gap);
         } else {
             b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, 0, par, 1);

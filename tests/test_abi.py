@@ -98,7 +98,7 @@ def test_tv_argument_checks(L):
     g = _geom(L)
     ok = dict(beta=0.1, n_iter=5, n_inner=20, tau=0.125, use_fista=1, warm_start=0, lipschitz=0.0, n_power_iter=10)
     for k, v in [("beta", -1.0), ("n_iter", 0), ("n_inner", 0), ("tau", 0.0), ("tau", 0.3), ("lipschitz", -2.0),
-                 ("n_power_iter", 0)]:
+                 ("n_power_iter", 0), ("warm_dual", 2), ("warm_dual", -1)]:
         o = L.pyhst_tv_opts(**{**ok, k: v})
         rc = L.lib.pyhst_tv_solve(ctypes.byref(g), 8, ctypes.byref(o), 8, None, None, None, 256, 1 << 30, None)
         assert rc == L.PYHST_ERR_INVALID_ARG, (k, v)

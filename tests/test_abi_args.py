@@ -105,6 +105,9 @@ def test_tv_batch_argument_checks(L):
     assert call() == E
     assert L.lib.pyhst_last_error().decode() == "item 1: image 0 x 256 outside [1, 16384]^2"
     items[1].geom = _geom(L)
+    o.warm_dual = 2
+    assert call() == E and "warm_dual" in L.lib.pyhst_last_error().decode()
+    o.warm_dual = 0
     assert call(wsb=64) == L.PYHST_ERR_WORKSPACE
 
 
