@@ -526,14 +526,17 @@ def run_learned_prox(dev, n_eval=64):
     """Plain TV vs the learned solve (FBP, K_T FISTA-TV iterations, K_L ISTA
     steps with the trained CNN prox; the fastest (K_T, K_L) of a small grid
     that reaches plain TV's PSNR) at equal PSNR on 64 held-out seeded 512^2
-    foams (100 angles, Poisson 1e4); everything event-timed on the GPU."""
+    foams (100 angles, Poisson 1e4), against the fastest plain TV solve that
+    reaches it (from zero or the FBP, with 20 cold-started Chambolle steps or
+    5 / 10 warm-started ones per prox); everything event-timed on the GPU."""
     import numpy as np
     import torch
     from paper_1306_1392_b300 import train_prox
     params = torch.from_numpy(np.load(PROX_WEIGHTS).astype(np.float32)).to(dev)
     r = train_prox.evaluate(params, dev, n_eval=n_eval, ks=(), tv_long=0, hybrid_kt=(75, 100, 125, 150, 200),
                             tv_first=(25, 28, 30, 35, 40), learned_steps=(2, 3, 4, 5),
-                            tv_zero=(100, 125, 150, 175))
+                            tv_zero=(100, 125, 150, 175),
+                            tv_warm_dual=tuple((n_in, k) for n_in in (5, 10, 15, 20) for k in (80, 90, 100, 110, 125)))
     r["weights"] = "paper_1306_1392_b300/weights/prox_cnn_foam512.npy (train_prox.py)"
     return r
 

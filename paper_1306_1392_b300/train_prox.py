@@ -172,14 +172,16 @@ def train(inputs, targets, steps: int, batch: int = 16, crop: int = 128, lr: flo
 def evaluate(params, dev, n_eval: int = 64, ks=(1, 2, 3, 5), n_iter_tv: int = 200,
              L: float = None, variants=(("ista", False),), tv_long: int = 1000,
              hybrid_kl=(0,), hybrid_kt=(30, 40, 50, 75, 100), tv_first=(20, 25, 30, 35, 40),
-             learned_steps=(1, 2), tv_zero=()):
+             learned_steps=(1, 2), tv_zero=(), tv_warm_dual=()):
     """Plain TV vs the learned prox on held-out seeded foams (even seeds).
     The target PSNR is plain TV's after n_iter_tv iterations from zero.  The
     learned solve is FBP, K_T FISTA-TV iterations (tv_first), then K_L ISTA
     steps with the network as the prox (learned_steps); the fastest (K_T, K_L)
     whose mean PSNR reaches the target is compared (equal_psnr) with the
     fastest plain TV solve that reaches it: from zero with n_iter_tv or fewer
-    (tv_zero) iterations, or from the FBP (hybrid_kt with K_L = 0)."""
+    (tv_zero) iterations, from the FBP (hybrid_kt with K_L = 0), or from zero
+    with (n_inner, n_iter) of tv_warm_dual and each prox's dual field starting
+    at the previous prox's."""
     from . import TvOptions, pyhst_fbp, pyhst_pnp_solve, pyhst_tv_solve
     geo = geometry(dev)
     if L is None:
@@ -258,10 +260,17 @@ def evaluate(params, dev, n_eval: int = 64, ks=(1, 2, 3, 5), n_iter_tv: int = 20
                                                                          lipschitz=L), energy=False))
         ps = float(np.mean([psnr(x[i].double().cpu().numpy(), truth[i]) for i in range(n_eval)]))
         res["pnp"].append({"variant": "tv", "n_iter": KT, "s_per_slice": t / n_eval, "psnr_mean": ps})
+    for n_in, KT in tv_warm_dual:
+        (x, _, _), t = timed(lambda: pyhst_tv_solve(geo, sino, TvOptions(beta=BETA, n_iter=KT, n_inner=n_in,
+                                                                         lipschitz=L, warm_dual=True), energy=False))
+        ps = float(np.mean([psnr(x[i].double().cpu().numpy(), truth[i]) for i in range(n_eval)]))
+        res["pnp"].append({"variant": f"tv-warm-dual{n_in}", "n_iter": KT, "s_per_slice": t / n_eval,
+                           "psnr_mean": ps})
     plain = [{"variant": "tv", "n_iter": n_iter_tv, "s_per_slice": t_tv / n_eval, "psnr_mean": ps_tv}]
-    plain += [r for r in res["pnp"] if r["variant"] in ("tv", "fbp+tv")]
+    is_plain = lambda v: v in ("tv", "fbp+tv") or v.startswith("tv-warm-dual")
+    plain += [r for r in res["pnp"] if is_plain(r["variant"])]
     plain_best = min((r for r in plain if r["psnr_mean"] >= ps_tv), key=lambda r: r["s_per_slice"])
-    reach = [r for r in res["pnp"] if r["psnr_mean"] >= ps_tv and r["variant"] not in ("tv", "fbp+tv")]
+    reach = [r for r in res["pnp"] if r["psnr_mean"] >= ps_tv and not is_plain(r["variant"])]
     if reach:
         best = min(reach, key=lambda r: r["s_per_slice"])
         res["equal_psnr"] = {"target_psnr": ps_tv, "pnp_variant": best["variant"], "pnp_n_iter": best["n_iter"],
