@@ -133,7 +133,7 @@ int proj_segments(const pyhst_geometry *g);
 // stream capture that launches them).
 int set_proj_attr();
 int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
-                         const int4 *tr_items, int n_tr_items, int width, cudaStream_t st);
+                         const int4 *tr_items, int n_tr_items, int width, cudaStream_t st, int ns = 1);
 
 // ----------------------------------------------------------------- profiling
 // Opt-in per-launch timing (pyhst_profile_enable): events recorded on the

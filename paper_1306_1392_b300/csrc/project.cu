@@ -65,10 +65,16 @@ constexpr int kPR = 32;         // rows per chunk (the unit of re-anchoring, cli
 constexpr int kPRays = kPG / 2; // rays per thread
 // Rows per staged block: a whole chunk for the 256-column staging (whose
 // double buffer then still allows 3 CTAs per SM), half a chunk for the wider
-// ones.  The arithmetic is per chunk, so the bits do not depend on it.
-template <int PW> __host__ __device__ constexpr int prows() { return PW == 256 ? kPR : kPR / 2; }
-template <int PW> __host__ __device__ constexpr int pvec() { return prows<PW>() * PW / 4 / kPThreads; }   // copies per thread per block
-template <int PW> __host__ __device__ constexpr int psmem() { return 2 * prows<PW>() * PW * (int)sizeof(float); }  // double-buffered strip
+// ones, and half that again when a CTA walks NS = 2 slices of one geometry
+// (one staged plane per slice, the same 64 KB).  The arithmetic is per chunk,
+// so the bits do not depend on it.
+template <int PW, int NS = 1> __host__ __device__ constexpr int prows() { return (PW == 256 ? kPR : kPR / 2) / NS; }
+template <int PW, int NS = 1> __host__ __device__ constexpr int pvec() {      // copies per thread per block and plane
+    return prows<PW, NS>() * PW / 4 / kPThreads;
+}
+template <int PW, int NS = 1> __host__ __device__ constexpr int psmem() {     // double-buffered strips
+    return 2 * NS * prows<PW, NS>() * PW * (int)sizeof(float);
+}
 constexpr int kPTargetCtas = 148 * 3 * 4;   // below this, the rows are split into segments
 constexpr int kPBandWin = 128;              // chunks whose bands are computed at once (1 KB of shared memory)
 constexpr double kFix = 4294967296.0;   // 2^32
@@ -198,22 +204,27 @@ __device__ __forceinline__ void chunk_clip(const RayGeom *rg, int mask, int b0, 
 }
 
 struct WalkArgs {
-    const float *M;
+    const float *M[2];  // the walked array of each slice (M[0] only for one slice)
     int R, C;
     int b0, bhi, b;
     bool vec;       // float4 staging allowed (16-byte aligned rows)
 };
 
 // Walk the chunks [c_lo, c_hi) of one array for the rays of the masked
-// angles, staged in blocks of prows rows (one or two per chunk).  Only the
+// angles, staged in blocks of prows rows (one to four per chunk).  Only the
 // band of each block is staged.  The bands of up to kPBandWin blocks are
 // computed at once by all threads (the same integer bounds as chunk_band)
-// before those blocks are walked.
-template <int kPW>
-__device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 acc[2],
+// before those blocks are walked.  With kNS = 2 the same rays walk two
+// slices of one geometry at once: one staged plane per slice, the positions
+// and weights computed once for both, and each slice's sums formed exactly
+// as a one-slice walk forms them (the same bits).
+template <int kPW, int kNS>
+__device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, int mask, float2 (&acc)[kNS][2],
                                           float2 (*tot)[kPThreads], float scale, int per,
-                                          float (*strip)[prows<kPW>()][kPW], int2 *bands, int c_lo, int c_hi) {
-    constexpr int kPVec = pvec<kPW>(), kRows = prows<kPW>(), kSub = kPR / kRows;   // kSub blocks per chunk
+                                          float (*strip)[kNS][prows<kPW, kNS>()][kPW], int2 *bands, int c_lo,
+                                          int c_hi) {
+    constexpr int kPVec = pvec<kPW, kNS>(), kRows = prows<kPW, kNS>(), kSub = kPR / kRows;   // kSub blocks per chunk
+    constexpr int kPlane = kRows * kPW;                    // floats between two slices' staged rows
     constexpr int kFrac = 23;
     const int tid = threadIdx.x, lane = tid & 31;
     const int asub = lane >> 4;
@@ -242,32 +253,41 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
     auto load = [&](int k, int sbuf) {
         const int2 bd = bands[k - win0];
         const int r0 = row0 + k * kRows, nr = min(kRows, r_end - r0), L0 = bd.x & ~3, width = bd.y - L0 + 4;
+        // one copy of 16 (or 4 x 4) bytes into every slice's plane; a source
+        // size of 0 (outside the array or past the pass's rows) writes zeros
+        auto copy16 = [&](uint32_t dst, size_t off, bool in) {
+#pragma unroll
+            for (int q = 0; q < kNS; ++q)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + q * kPlane * 4),
+                             "l"(in ? w.M[q] + off : w.M[0]), "r"(in ? 16u : 0u) : "memory");
+        };
+        auto copy4x4 = [&](uint32_t dst, size_t off, int j, bool row_in) {
+#pragma unroll
+            for (int q = 0; q < kNS; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool in = row_in && (unsigned)(j + e) < (unsigned)w.C;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + q * kPlane * 4 + 4 * e),
+                                 "l"(in ? w.M[q] + off + e : w.M[0]), "r"(in ? 4u : 0u) : "memory");
+                }
+        };
         if constexpr ((4 * kPThreads) % kPW == 0) {
             // a thread copies the same 4 columns of rows rr0, rr0 + kStep, ...
             constexpr int kStep = 4 * kPThreads / kPW;
             const int col = (4 * tid) % kPW, rr0 = (4 * tid) / kPW, j = L0 + col;
             if (col < width) {
-                uint32_t dst = smem_addr(&strip[sbuf][rr0][col]);
-                const float *src = w.M + (size_t)(r0 + rr0) * w.C + j;
-                const size_t src_step = (size_t)kStep * w.C;
+                uint32_t dst = smem_addr(&strip[sbuf][0][rr0][col]);
+                size_t off = (size_t)(r0 + rr0) * w.C + j;
+                const size_t off_step = (size_t)kStep * w.C;
                 if (w.vec) {
                     const bool jin = j >= 0 && j + 3 < w.C;
 #pragma unroll
-                    for (int v = 0; v < kPVec; ++v, dst += kStep * kPW * 4, src += src_step) {
-                        const bool in = jin && rr0 + v * kStep < nr;
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
-                                     "l"(in ? src : w.M), "r"(in ? 16u : 0u) : "memory");
-                    }
+                    for (int v = 0; v < kPVec; ++v, dst += kStep * kPW * 4, off += off_step)
+                        copy16(dst, off, jin && rr0 + v * kStep < nr);
                 } else {
 #pragma unroll
-                    for (int v = 0; v < kPVec; ++v, dst += kStep * kPW * 4, src += src_step) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const bool in = rr0 + v * kStep < nr && (unsigned)(j + q) < (unsigned)w.C;
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * q),
-                                         "l"(in ? src + q : w.M), "r"(in ? 4u : 0u) : "memory");
-                        }
-                    }
+                    for (int v = 0; v < kPVec; ++v, dst += kStep * kPW * 4, off += off_step)
+                        copy4x4(dst, off, j, rr0 + v * kStep < nr);
                 }
             }
         } else {
@@ -276,20 +296,12 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                 const int e = (tid + v * kPThreads) * 4, rr = e / kPW, col = e - rr * kPW;
                 const int j = L0 + col;
                 if (col < width) {
-                    const uint32_t dst = smem_addr(&strip[sbuf][rr][col]);
-                    const float *row = w.M + (size_t)(r0 + rr) * w.C;
-                    if (w.vec) {
-                        const bool in = rr < nr && j >= 0 && j + 3 < w.C;
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
-                                     "l"(in ? row + j : w.M), "r"(in ? 16u : 0u) : "memory");
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const bool in = rr < nr && (unsigned)(j + q) < (unsigned)w.C;
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * q),
-                                         "l"(in ? row + j + q : w.M), "r"(in ? 4u : 0u) : "memory");
-                        }
-                    }
+                    const uint32_t dst = smem_addr(&strip[sbuf][0][rr][col]);
+                    const size_t off = (size_t)(r0 + rr) * w.C + j;
+                    if (w.vec)
+                        copy16(dst, off, rr < nr && j >= 0 && j + 3 < w.C);
+                    else
+                        copy4x4(dst, off, j, rr < nr);
                 }
             }
         }
@@ -347,16 +359,19 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                 for (int k = 0; k < kPRays; ++k) x32[k] += act[k] ? d : 0u;
             }
             L0_prev = L0;
-            const float *S = &strip[cur][0][0];
-            auto row = [&](const float *Sr) {   // one staged row: three taps per ray
-                float v[kPRays], q0[kPRays], q1[kPRays], q2[kPRays];
+            const float *S = &strip[cur][0][0][0];
+            auto row = [&](const float *Sr) {   // one staged row: three taps per ray and slice
+                float v[kPRays], q0[kNS][kPRays], q1[kNS][kPRays], q2[kNS][kPRays];
 #pragma unroll
                 for (int k = 0; k < kPRays; ++k) {
                     const float *q = Sr + (x32[k] >> kFrac) - 1;
                     v[k] = __uint_as_float((x32[k] & 0x7FFFFFu) | 0x3F800000u);   // 1 + frac in [1, 2)
-                    q0[k] = q[0];
-                    q1[k] = q[1];
-                    q2[k] = q[2];
+#pragma unroll
+                    for (int n = 0; n < kNS; ++n) {
+                        q0[n][k] = q[n * kPlane];
+                        q1[n][k] = q[n * kPlane + 1];
+                        q2[n][k] = q[n * kPlane + 2];
+                    }
                     x32[k] -= r32[k];
                 }
 #pragma unroll
@@ -368,9 +383,12 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                     const float2 wl = make_float2(__saturatef(t1[k] - ap.x), __saturatef(t1[k + 1] - ap.y));
                     const float2 wc = make_float2(c1[k] - fabsf(ap.x), c1[k + 1] - fabsf(ap.y));
                     const float2 wr = make_float2(__saturatef(t1[k] + ap.x), __saturatef(t1[k + 1] + ap.y));
-                    acc[p] = fma2(wl, make_float2(q0[k], q0[k + 1]), acc[p]);
-                    acc[p] = fma2(wc, make_float2(q1[k], q1[k + 1]), acc[p]);
-                    acc[p] = fma2(wr, make_float2(q2[k], q2[k + 1]), acc[p]);
+#pragma unroll
+                    for (int n = 0; n < kNS; ++n) {
+                        acc[n][p] = fma2(wl, make_float2(q0[n][k], q0[n][k + 1]), acc[n][p]);
+                        acc[n][p] = fma2(wc, make_float2(q1[n][k], q1[n][k + 1]), acc[n][p]);
+                        acc[n][p] = fma2(wr, make_float2(q2[n][k], q2[n][k + 1]), acc[n][p]);
+                    }
                 }
             };
             if (nr == kRows) {                  // full block: rows at constant offsets
@@ -386,10 +404,12 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
                 seg_left = per;
                 const float2 s2 = make_float2(scale, scale);
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    tot[p][tid] = add2(tot[p][tid], mul2(s2, acc[p]));
-                    acc[p] = make_float2(0.0f, 0.0f);
-                }
+                for (int n = 0; n < kNS; ++n)
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        tot[2 * n + p][tid] = add2(tot[2 * n + p][tid], mul2(s2, acc[n][p]));
+                        acc[n][p] = make_float2(0.0f, 0.0f);
+                    }
             }
             if (more) wait_loads();
             __syncthreads();
@@ -405,13 +425,21 @@ __device__ __forceinline__ void walk_pass(const WalkArgs &w, const RayGeom *rg, 
 // partials are added in order afterwards); seg < 0: it walks all segments and
 // adds them itself.  Both give the same bits, so the segmentation (a
 // property of the slice geometry) and not the launch decides the rounding.
-template <int kPW>
-__device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, const float *__restrict__ img,
-                                         const float *__restrict__ imgT, float *__restrict__ sino, int n_angles,
+// The CTA projects the kNS slices of one geometry in S (S.img[n], its
+// transpose S.imgT[n] -> S.sino[n]); every slice gets the bits of a one-slice
+// CTA.
+struct ProjSlices {
+    const float *img[2], *imgT[2];
+    float *sino[2];
+};
+
+template <int kPW, int kNS>
+__device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, const ProjSlices &S, int n_angles,
                                          int n_bins, int nx, int ny, double cx, double cy, float scale, int g0,
                                          int b0, int seg, int nseg) {
     extern __shared__ __align__(16) float proj_smem[];
-    float (*strip)[prows<kPW>()][kPW] = reinterpret_cast<float (*)[prows<kPW>()][kPW]>(proj_smem);
+    constexpr int kRows = prows<kPW, kNS>();
+    float (*strip)[kNS][kRows][kPW] = reinterpret_cast<float (*)[kNS][kRows][kPW]>(proj_smem);
     __shared__ RayGeom rg[kPG];
     __shared__ int2 bands_s[kPBandWin];
     __shared__ int phase_mask[2], fits_s, clip_s[2];
@@ -432,19 +460,27 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
     if (tid < kPG && rg[tid].major >= 0) atomicOr(&phase_mask[rg[tid].major], 1 << tid);
     __syncthreads();
 
-    float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};   // rays (0,1), (2,3): segment sums
-    __shared__ float2 tot[2][kPThreads];    // per thread: scaled sums of its finished segments
-    tot[0][tid] = tot[1][tid] = make_float2(0.0f, 0.0f);
+    float2 acc[kNS][2];                     // per slice, rays (0,1), (2,3): segment sums
+    __shared__ float2 tot[2 * kNS][kPThreads];  // per thread: scaled sums of its finished segments
+#pragma unroll
+    for (int n = 0; n < kNS; ++n) {
+        acc[n][0] = acc[n][1] = make_float2(0.0f, 0.0f);
+        tot[2 * n][tid] = tot[2 * n + 1][tid] = make_float2(0.0f, 0.0f);
+    }
 
     for (int major = 0; major < 2; ++major) {
         const int mask_all = phase_mask[major];
         if (!mask_all) continue;
         WalkArgs w;
-        w.M = major == 0 ? img : imgT;
         w.R = major == 0 ? ny : nx;
         w.C = major == 0 ? nx : ny;
         w.b0 = b0; w.bhi = bhi; w.b = b;
-        w.vec = (w.C % 4 == 0) && ((reinterpret_cast<uintptr_t>(w.M) & 15) == 0);
+        w.vec = w.C % 4 == 0;
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            w.M[n] = major == 0 ? S.img[n < kNS ? n : 0] : S.imgT[n < kNS ? n : 0];
+            w.vec = w.vec && (reinterpret_cast<uintptr_t>(w.M[n]) & 15) == 0;
+        }
         // Largest subset of consecutive angles (8, 4, 2, 1) whose bands fit:
         // the band of rows [r, r + n - 1] (n rows per staged block) has a
         // width convex in r, every block lies within the range of the first
@@ -453,7 +489,6 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
         // (127 sqrt 2 + 32 + 8 < 256).
         if (warp == 0) {
             int gs = kPG;
-            constexpr int kRows = prows<kPW>();
             const int last0 = max(0, w.R - kRows);
             for (; gs > 1; gs >>= 1) {
                 bool ok = true;
@@ -481,33 +516,53 @@ __device__ __forceinline__ void proj_cta(const AngleInfo *__restrict__ tab, cons
             __syncthreads();
             const int cl = max(c_lo, clip_s[0]), ch = min(c_hi, clip_s[1]);
             __syncthreads();
-            walk_pass(w, rg, m, acc, tot, scale, per, strip, bands_s, cl, ch);
+            walk_pass<kPW, kNS>(w, rg, m, acc, tot, scale, per, strip, bands_s, cl, ch);
         }
         __syncthreads();
     }
     if (b <= bhi) {
-        const float r[kPRays] = {tot[0][tid].x, tot[0][tid].y, tot[1][tid].x, tot[1][tid].y};
 #pragma unroll
-        for (int k = 0; k < kPRays; ++k) {
-            const int a = g0 + asub + 2 * k;
-            if (a < n_angles) sino[(size_t)a * n_bins + b] = r[k];
+        for (int n = 0; n < kNS; ++n) {
+            const float r[kPRays] = {tot[2 * n][tid].x, tot[2 * n][tid].y, tot[2 * n + 1][tid].x,
+                                     tot[2 * n + 1][tid].y};
+#pragma unroll
+            for (int k = 0; k < kPRays; ++k) {
+                const int a = g0 + asub + 2 * k;
+                if (a < n_angles) S.sino[n][(size_t)a * n_bins + b] = r[k];
+            }
         }
     }
 }
 
 // split: blockIdx.z = slice * nseg + segment, and the output is the partial
 // sinogram of the segment, part[slice][segment][angle][bin]; otherwise
-// blockIdx.z = slice and the CTA adds the segments itself.
-template <int PW>
+// blockIdx.z = slice (NS = 1) or the pair of slices 2 z, 2 z + 1 (NS = 2; the
+// last slice of an odd count is walked twice, both planes giving its bits)
+// and the CTA adds the segments itself.
+template <int PW, int NS>
 __global__ void __launch_bounds__(kPThreads, 3)
 proj_kernel(const AngleInfo *__restrict__ tab, const float *__restrict__ img, const float *__restrict__ imgT,
             float *__restrict__ sino, int n_angles, int n_bins, int nx, int ny, double cx, double cy,
-            float scale, int nseg, int split) {
+            float scale, int nseg, int split, int n_slices) {
     const int bz = (int)blockIdx.z;
-    const int slice = split ? bz / nseg : bz, seg = split ? bz % nseg : -1;
-    const size_t img_off = (size_t)slice * nx * ny;
-    proj_cta<PW>(tab, img + img_off, imgT + img_off, sino + (size_t)blockIdx.z * n_angles * n_bins, n_angles, n_bins,
-                 nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB, seg, nseg);
+    const size_t img_sz = (size_t)nx * ny, sino_sz = (size_t)n_angles * n_bins;
+    ProjSlices S;
+    if (NS == 1) {
+        const int slice = split ? bz / nseg : bz;
+        S.img[0] = S.img[1] = img + slice * img_sz;
+        S.imgT[0] = S.imgT[1] = imgT + slice * img_sz;
+        S.sino[0] = S.sino[1] = sino + (size_t)bz * sino_sz;
+    } else {
+        const int s0 = 2 * bz, s1 = min(2 * bz + 1, n_slices - 1);
+        S.img[0] = img + s0 * img_sz;
+        S.img[1] = img + s1 * img_sz;
+        S.imgT[0] = imgT + s0 * img_sz;
+        S.imgT[1] = imgT + s1 * img_sz;
+        S.sino[0] = sino + s0 * sino_sz;
+        S.sino[1] = sino + s1 * sino_sz;
+    }
+    proj_cta<PW, NS>(tab, S, n_angles, n_bins, nx, ny, cx, cy, scale, blockIdx.y * kPG, blockIdx.x * kPB,
+                     NS == 1 && split ? bz % nseg : -1, nseg);
 }
 
 // sino[s][k] = sum over segments (in order) of part[s][seg][k]
@@ -521,14 +576,26 @@ __global__ void proj_reduce_kernel(const float *__restrict__ part, float *__rest
     sino[(size_t)blockIdx.y * per_slice + k] = acc;
 }
 
-// Mixed batch: CTA k projects angle group items[k].z, bin block items[k].y of slice items[k].x.
-template <int PW>
+// Mixed batch: CTA k projects angle group items[k].z, bin block items[k].y of
+// slice items[k].x and, with NS = 2, of slice items[k].w too, a slice of the
+// same geometry (or items[k].x again).
+template <int PW, int NS>
 __global__ void __launch_bounds__(kPThreads, 3)
 proj_batch_kernel(const BatchSlice *__restrict__ slices, const int4 *__restrict__ items) {
     const int4 it = items[blockIdx.x];
     const BatchSlice s = slices[it.x];
-    proj_cta<PW>(s.tab, s.proj_in, s.proj_inT, s.proj_out, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy,
-                 s.pixel_size, it.z * kPG, it.y * kPB, -1, s.proj_nseg);
+    ProjSlices S;
+    S.img[0] = S.img[1] = s.proj_in;
+    S.imgT[0] = S.imgT[1] = s.proj_inT;
+    S.sino[0] = S.sino[1] = s.proj_out;
+    if (NS == 2) {
+        const BatchSlice &t = slices[it.w];
+        S.img[1] = t.proj_in;
+        S.imgT[1] = t.proj_inT;
+        S.sino[1] = t.proj_out;
+    }
+    proj_cta<PW, NS>(s.tab, S, s.n_angles, s.n_bins, s.nx, s.ny, s.cx, s.cy, s.pixel_size, it.z * kPG, it.y * kPB,
+                     -1, s.proj_nseg);
 }
 
 // Mixed batch transpose: CTA k moves 64 x 64 tile (items[k].y, items[k].z) of slice items[k].x.
@@ -562,23 +629,23 @@ int project_width(int nx, int ny, int n_angles) {
     return (double)std::max(nx, ny) > 2.0 * n_angles ? 512 : 256;
 }
 
+namespace {
+template <int PW, int NS>
+bool proj_attr_pw() {
+    return cudaFuncSetAttribute(proj_kernel<PW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<PW, NS>()) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(proj_batch_kernel<PW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                psmem<PW, NS>()) == cudaSuccess;
+}
+}  // namespace
+
 int set_proj_attr() {
     static bool done[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status("cudaGetDevice");
     if (dev >= 0 && dev < 64 && done[dev]) return PYHST_OK;
-    if (cudaFuncSetAttribute(proj_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<256>()) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(proj_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<384>()) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(proj_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<512>()) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(proj_batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<256>()) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(proj_batch_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<384>()) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(proj_batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem<512>()) !=
-            cudaSuccess)
+    if (!(proj_attr_pw<256, 1>() && proj_attr_pw<384, 1>() && proj_attr_pw<512, 1>() && proj_attr_pw<256, 2>() &&
+          proj_attr_pw<384, 2>() && proj_attr_pw<512, 2>()))
         return cuda_status("projection kernel shared-memory attribute");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return PYHST_OK;
@@ -590,8 +657,20 @@ int proj_blocks(int n_angles, int n_bins, int *nb, int *na) {
     return *nb * *na;
 }
 
+namespace {
+template <int NS>
+void proj_batch_launch(int width, const BatchSlice *slices, const int4 *items, int n, cudaStream_t st) {
+    if (width == 512)
+        proj_batch_kernel<512, NS><<<n, kPThreads, psmem<512, NS>(), st>>>(slices, items);
+    else if (width == 384)
+        proj_batch_kernel<384, NS><<<n, kPThreads, psmem<384, NS>(), st>>>(slices, items);
+    else
+        proj_batch_kernel<256, NS><<<n, kPThreads, psmem<256, NS>(), st>>>(slices, items);
+}
+}  // namespace
+
 int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n_proj_items,
-                         const int4 *tr_items, int n_tr_items, int width, cudaStream_t st) {
+                         const int4 *tr_items, int n_tr_items, int width, cudaStream_t st, int ns) {
     if (n_tr_items > 0) {
         transpose_batch_kernel<<<n_tr_items, dim3(32, 8), 0, st>>>(slices, tr_items);
         int rc = cuda_status("batched transpose kernel");
@@ -601,12 +680,10 @@ int launch_project_batch(const BatchSlice *slices, const int4 *proj_items, int n
     int rc = set_proj_attr();
     if (rc) return rc;
     ProfScope prof(kProfProject, st);
-    if (width == 512)
-        proj_batch_kernel<512><<<n_proj_items, kPThreads, psmem<512>(), st>>>(slices, proj_items);
-    else if (width == 384)
-        proj_batch_kernel<384><<<n_proj_items, kPThreads, psmem<384>(), st>>>(slices, proj_items);
+    if (ns == 2)
+        proj_batch_launch<2>(width, slices, proj_items, n_proj_items, st);
     else
-        proj_batch_kernel<256><<<n_proj_items, kPThreads, psmem<256>(), st>>>(slices, proj_items);
+        proj_batch_launch<1>(width, slices, proj_items, n_proj_items, st);
     return cuda_status("batched projection kernel");
 }
 
@@ -657,6 +734,25 @@ size_t project_scratch_bytes(const pyhst_geometry *g) {
     return align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices) + align_up(sizeof(float) * part);
 }
 
+namespace {
+template <int NS>
+void proj_launch(int width, dim3 grid, cudaStream_t st, const AngleInfo *tab, const float *img, const float *xt,
+                 float *dst, const pyhst_geometry *g, float scale, int nseg, int split) {
+    if (width == 512)
+        proj_kernel<512, NS><<<grid, kPThreads, psmem<512, NS>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
+                                                                        g->ny, g->cx, g->cy, scale, nseg, split,
+                                                                        g->n_slices);
+    else if (width == 384)
+        proj_kernel<384, NS><<<grid, kPThreads, psmem<384, NS>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
+                                                                        g->ny, g->cx, g->cy, scale, nseg, split,
+                                                                        g->n_slices);
+    else
+        proj_kernel<256, NS><<<grid, kPThreads, psmem<256, NS>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
+                                                                        g->ny, g->cx, g->cy, scale, nseg, split,
+                                                                        g->n_slices);
+}
+}  // namespace
+
 int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *img, float *sino,
                    float scale, float *xt, cudaStream_t st, int staging) {
     if (g->n_slices > 65535) return fail(PYHST_ERR_INVALID_ARG, "too many slices in one call (%d)", g->n_slices);
@@ -668,20 +764,18 @@ int launch_project(const pyhst_geometry *g, const AngleInfo *tab, const float *i
     const int nseg = proj_segments(g);
     const bool split = proj_split(g, nseg);
     float *part = xt + align_up(sizeof(float) * (size_t)g->nx * g->ny * g->n_slices) / sizeof(float);
-    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG, g->n_slices * (split ? nseg : 1));
+    // two slices per CTA unless the rows are split into segment CTAs
+    const int ns = !split && g->n_slices >= 2 ? 2 : 1;
+    dim3 grid((g->n_bins + kPB - 1) / kPB, (g->n_angles + kPG - 1) / kPG,
+              ns == 2 ? (g->n_slices + 1) / 2 : g->n_slices * (split ? nseg : 1));
     {
         ProfScope prof(kProfProject, st);
         float *dst = split ? part : sino;
         const int width = staging > 0 ? staging : project_width(g->nx, g->ny, g->n_angles);
-        if (width == 512)
-            proj_kernel<512><<<grid, kPThreads, psmem<512>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
-                                                                    g->ny, g->cx, g->cy, scale, nseg, split);
-        else if (width == 384)
-            proj_kernel<384><<<grid, kPThreads, psmem<384>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
-                                                                    g->ny, g->cx, g->cy, scale, nseg, split);
+        if (ns == 2)
+            proj_launch<2>(width, grid, st, tab, img, xt, dst, g, scale, nseg, 0);
         else
-            proj_kernel<256><<<grid, kPThreads, psmem<256>(), st>>>(tab, img, xt, dst, g->n_angles, g->n_bins, g->nx,
-                                                                    g->ny, g->cx, g->cy, scale, nseg, split);
+            proj_launch<1>(width, grid, st, tab, img, xt, dst, g, scale, nseg, split ? 1 : 0);
     }
     if ((rc = cuda_status("projection kernel"))) return rc;
     if (split) {

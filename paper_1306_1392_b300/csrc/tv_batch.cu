@@ -423,11 +423,12 @@ void add_items(Plan &P, int s, const pyhst_geometry &g, bool rep_only) {
     auto &bp = rep_only ? P.bp_r : P.bp;
     for (int y = 0; y < ty; ++y)
         for (int x = 0; x < tx; ++x) bp.push_back(make_int4(s, x, y, 0));
-    int nb, na;
-    proj_blocks(g.n_angles, g.n_bins, &nb, &na);
-    auto &pr = rep_only ? P.proj_r : P.proj;
-    for (int a = 0; a < na; ++a)
-        for (int b = 0; b < nb; ++b) pr.push_back(make_int4(s, b, a, 0));
+    if (rep_only) {   // the power iteration projects one slice per geometry (the pairs: make_plan)
+        int nb, na;
+        proj_blocks(g.n_angles, g.n_bins, &nb, &na);
+        for (int a = 0; a < na; ++a)
+            for (int b = 0; b < nb; ++b) P.proj_r.push_back(make_int4(s, b, a, s));
+    }
     auto &tr = rep_only ? P.tr_r : P.tr;
     for (int y = 0; y < (g.ny + 63) / 64; ++y)     // the projector's transpose moves 64 x 64 tiles
         for (int x = 0; x < (g.nx + 63) / 64; ++x) tr.push_back(make_int4(s, x, y, 0));
@@ -487,6 +488,23 @@ Plan make_plan(const pyhst_tv_item *items, int n) {
         add_items(P, s, g, false);
     }
     for (int r : P.reps) add_items(P, r, items[r].geom, true);
+    // projector items: each CTA walks two slices of one geometry (items[k].x
+    // and items[k].w), paired in list order within the geometry; an odd one
+    // out is paired with itself
+    {
+        std::map<int, std::vector<int>> members;
+        for (int s = 0; s < n; ++s) members[P.rep[s]].push_back(s);
+        for (int r : P.reps) {
+            const std::vector<int> &m = members[r];
+            int nb, na;
+            proj_blocks(items[r].geom.n_angles, items[r].geom.n_bins, &nb, &na);
+            for (size_t q = 0; q < m.size(); q += 2) {
+                const int s0 = m[q], s1 = q + 1 < m.size() ? m[q + 1] : m[q];
+                for (int a = 0; a < na; ++a)
+                    for (int b = 0; b < nb; ++b) P.proj.push_back(make_int4(s0, b, a, s1));
+            }
+        }
+    }
     auto width_group = [&](const int4 &it) {
         const pyhst_geometry &g = items[it.x].geom;
         const int w = project_width(g.nx, g.ny, g.n_angles);
@@ -711,24 +729,26 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     // ---- step size: power iteration on the representatives, or the caller's L
     if ((rc = set_proj_attr())) return rc;
     // projector: the transposes, then the items of each staging width (256, 384, 512 columns)
-    auto project = [&](const BatchSlice *D, size_t o_items, const int *cnt, size_t o_tr, int n_tr) {
-        int r = launch_project_batch(D, I + o_items, cnt[0], I + o_tr, n_tr, 256, st);
-        if (!r) r = launch_project_batch(D, I + o_items + cnt[0], cnt[1], nullptr, 0, 384, st);
-        if (!r) r = launch_project_batch(D, I + o_items + cnt[0] + cnt[1], cnt[2], nullptr, 0, 512, st);
+    // (ns: slices per projector CTA, 2 for the pairs of the solve, 1 for the
+    // power iteration's one slice per geometry)
+    auto project = [&](const BatchSlice *D, size_t o_items, const int *cnt, size_t o_tr, int n_tr, int ns) {
+        int r = launch_project_batch(D, I + o_items, cnt[0], I + o_tr, n_tr, 256, st, ns);
+        if (!r) r = launch_project_batch(D, I + o_items + cnt[0], cnt[1], nullptr, 0, 384, st, ns);
+        if (!r) r = launch_project_batch(D, I + o_items + cnt[0] + cnt[1], cnt[2], nullptr, 0, 512, st, ns);
         return r;
     };
     if (opts->lipschitz == 0.0) {
         const int npxr = (int)P.px_r.size(), nsnr = (int)P.sn_r.size();
         b_fill_v<<<npxr, tb, 0, st>>>(T, I + o_pxr);
         for (int it = 0; it < opts->n_power_iter; ++it) {
-            if ((rc = project(D_pow, o_projr, P.proj_r_cnt, o_trr, (int)P.tr_r.size())))
+            if ((rc = project(D_pow, o_projr, P.proj_r_cnt, o_trr, (int)P.tr_r.size(), 1)))
                 return rc;
             if ((rc = launch_backproject_batch(D_pow, I + o_bpr, (int)P.bp_r.size(), false, st, P.bpNA))) return rc;
             b_sqnorm_g<<<npxr, tb, 0, st>>>(T, I + o_pxr, part_px);
             b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_px, sc, 0);
             b_scale_v<<<npxr, tb, 0, st>>>(T, I + o_pxr, sc);
         }
-        if ((rc = project(D_pow, o_projr, P.proj_r_cnt, o_trr, (int)P.tr_r.size())))
+        if ((rc = project(D_pow, o_projr, P.proj_r_cnt, o_trr, (int)P.tr_r.size(), 1)))
             return rc;
         b_sqnorm_axa<<<nsnr, tb, 0, st>>>(T, I + o_snr, part_sn);
         b_finalize_norm<<<(int)P.reps.size(), tb, 0, st>>>(T, R, part_sn, sc, 1);
@@ -740,7 +760,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
     // ---- start
     b_copy_x<<<npx, tb, 0, st>>>(T, I + o_px, opts->warm_start ? 1 : 0, 0);
     if (opts->warm_start)
-        if ((rc = project(D_init, o_proj, P.proj_cnt, o_tr, ntr))) return rc;
+        if ((rc = project(D_init, o_proj, P.proj_cnt, o_tr, ntr, 2))) return rc;
     b_copy_sino_start<<<nsn, tb, 0, st>>>(T, I + o_sn, opts->warm_start ? 1 : 0);
     if ((rc = cuda_status("batch start"))) return rc;
 
@@ -774,7 +794,7 @@ extern "C" int pyhst_tv_solve_batch(const pyhst_tv_item *items, int32_t n_items,
             b_prox_final<<<npx, tb, 0, st>>>(T, I + o_px, sc, 0, par, 1);
         }
         if (any_gap) b_finalize_gap<<<n, tb, 0, st>>>(T, part_gap, sc, k);
-        rc = project(par ? D_odd : D_even, o_proj, P.proj_cnt, o_tr, ntr);
+        rc = project(par ? D_odd : D_even, o_proj, P.proj_cnt, o_tr, ntr, 2);
         if (rc) break;
         double w = 0.0;
         if (opts->use_fista) {

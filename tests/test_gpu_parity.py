@@ -514,6 +514,31 @@ def test_project_staging_widths_are_identical(P, orc, cuda_device, case):
     close(f64(outs[256][0]), ref)
 
 
+@pytest.mark.parametrize("case,ns", [(CASES[1], 3), (CASES[3], 2), (CASES[6], 5),
+                                     ((200, 1024, 1024, 1024, "uniform", 0.0, 9), 9),
+                                     ((2000, 2048, 2048, 2048, "uniform", 0.4, 12), 3)])
+def test_project_slice_pairs_equal_single_slices(P, cuda_device, case, ns):
+    """A stack's projection walks two slices per CTA (one staged plane each,
+    ray positions and weights computed once; an odd last slice is paired
+    with itself).  Every slice's sinogram equals, bit for bit, the projection
+    of that slice alone (one slice per CTA, or row-segment CTAs whose
+    partials are added in order), at every staging width.  The cases take
+    the paired path: images under 128 pixels on a side (no row segments),
+    and stacks with enough CTAs (9 x 1024^2 / 200 angles, 3 x 2048^2 / 2000)."""
+    na, nb, nx, ny, kind, off, seed = case
+    g, ang, axis, geo = _case(P, cuda_device, *case)
+    img = torch.from_numpy(g.standard_normal((ns, ny, nx)).astype(np.float32)).to(cuda_device)
+    try:
+        for width in (256, 384, 512):
+            P.pyhst_set_project_staging(nx, ny, na, width)
+            stack = P.pyhst_project(geo, img)
+            for z in range(ns):
+                one = P.pyhst_project(geo, img[z:z + 1].contiguous())
+                assert torch.equal(stack[z], one[0]), (width, z)
+    finally:
+        P.pyhst_set_project_staging(nx, ny, na, 0)
+
+
 def test_tv_batch_with_three_projector_widths(P, cuda_device):
     """Slices whose geometries take different staging widths run in one
     batched solve (one projector launch per width); the iterates are bitwise
