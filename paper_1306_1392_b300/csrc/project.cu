@@ -27,6 +27,13 @@
 // convex in the row, so checking the first and last blocks decides it.
 // When the grid would have few CTAs (few angles, few slices) the rows are
 // split into segments whose partial sinograms are added in a fixed order.
+// Otherwise a CTA walks two slices of one geometry at once (two slices of a
+// stack, or two batch slices that share the geometry): each slice has its own
+// staged plane, while the ray positions, hat weights, bands and copies'
+// index arithmetic are computed once for both; the taps of both slices are
+// added by the same paired fmas a one-slice walk uses, so each slice gets
+// the bits of its one-slice projection.  Half the rows per staged block keep
+// the double buffer at 64 KB.
 //
 // x*(b, r) = X0 + b dX - r rho is computed in 32.32 fixed point (int64), so the
 // staged bands, computed with the same integers, provably contain every tap
