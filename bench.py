@@ -527,8 +527,11 @@ def run_learned_prox(dev, n_eval=64):
     steps with the trained CNN prox; the fastest (K_T, K_L) of a small grid
     that reaches plain TV's PSNR) at equal PSNR on 64 held-out seeded 512^2
     foams (100 angles, Poisson 1e4), against the fastest plain TV solve that
-    reaches it (from zero or the FBP, with 20 cold-started Chambolle steps or
-    5 / 10 warm-started ones per prox); everything event-timed on the GPU."""
+    reaches it: with the paper's prox (20 Chambolle steps from a zero dual
+    field; from zero or the FBP) for ``speedup``, and among those and the
+    warm-started proxes (5-20 steps) for ``speedup_vs_any_tv``; the learned
+    solve's own TV phase may use warm-started proxes too.  Everything
+    event-timed on the GPU."""
     import numpy as np
     import torch
     from paper_1306_1392_b300 import train_prox
@@ -536,7 +539,8 @@ def run_learned_prox(dev, n_eval=64):
     r = train_prox.evaluate(params, dev, n_eval=n_eval, ks=(), tv_long=0, hybrid_kt=(75, 100, 125, 150, 200),
                             tv_first=(25, 28, 30, 35, 40), learned_steps=(2, 3, 4, 5),
                             tv_zero=(100, 125, 150, 175),
-                            tv_warm_dual=tuple((n_in, k) for n_in in (5, 10, 15, 20) for k in (80, 90, 100, 110, 125)))
+                            tv_warm_dual=tuple((n_in, k) for n_in in (5, 10, 15, 20) for k in (80, 90, 100, 110, 125)),
+                            learned_warm_dual=tuple((n_in, k, 4) for n_in in (10, 15) for k in (22, 25, 28)))
     r["weights"] = "paper_1306_1392_b300/weights/prox_cnn_foam512.npy (train_prox.py)"
     return r
 
