@@ -169,6 +169,40 @@ def train(inputs, targets, steps: int, batch: int = 16, crop: int = 128, lr: flo
     return params, hist
 
 
+def equal_psnr(rows, target, s_target):
+    """Time to the target PSNR, from measured solves.  rows: dicts with
+    variant, n_iter, s_per_slice, psnr_mean.  Plain TV variants are "tv"
+    (from zero), "fbp+tv" (from the FBP) and "tv-warm-dual<n>" (warm-started
+    proxes); every other variant is a learned solve, warm-started when its
+    name holds "warm-dual".  Each ratio compares like with like:
+    ``speedup``, the fastest solves reaching the target whose proxes all
+    start from a zero dual field (the paper's prox); ``speedup_vs_any_tv``,
+    the fastest with warm-started proxes allowed on both sides;
+    ``speedup_vs_tv_from_zero``, against s_target, the solve that sets the
+    target.  None when no learned solve reaches the target."""
+    is_cold = lambda v: "warm-dual" not in v          # every prox from a zero dual field
+    is_plain = lambda v: v in ("tv", "fbp+tv") or (v.startswith("tv-warm-dual") and "+" not in v)
+    fastest = lambda rs: min((r for r in rs if r["psnr_mean"] >= target), key=lambda r: r["s_per_slice"],
+                             default=None)
+    plain = [r for r in rows if is_plain(r["variant"])]
+    learned = [r for r in rows if not is_plain(r["variant"])]
+    tv_cold, tv_any = fastest([r for r in plain if is_cold(r["variant"])]), fastest(plain)
+    ln_cold, ln_any = fastest([r for r in learned if is_cold(r["variant"])]), fastest(learned)
+    if not (tv_cold and ln_cold and tv_any and ln_any):
+        return None
+    return {"target_psnr": target, "pnp_variant": ln_cold["variant"], "pnp_n_iter": ln_cold["n_iter"],
+            "pnp_s_per_slice": ln_cold["s_per_slice"], "pnp_psnr": ln_cold["psnr_mean"],
+            "tv_variant": tv_cold["variant"], "tv_n_iter": tv_cold["n_iter"],
+            "tv_s_per_slice": tv_cold["s_per_slice"], "tv_psnr": tv_cold["psnr_mean"],
+            "speedup": tv_cold["s_per_slice"] / ln_cold["s_per_slice"],
+            "any_pnp_variant": ln_any["variant"], "any_pnp_n_iter": ln_any["n_iter"],
+            "any_pnp_s_per_slice": ln_any["s_per_slice"], "any_pnp_psnr": ln_any["psnr_mean"],
+            "any_tv_variant": tv_any["variant"], "any_tv_n_iter": tv_any["n_iter"],
+            "any_tv_s_per_slice": tv_any["s_per_slice"], "any_tv_psnr": tv_any["psnr_mean"],
+            "speedup_vs_any_tv": tv_any["s_per_slice"] / ln_any["s_per_slice"],
+            "speedup_vs_tv_from_zero": s_target / ln_cold["s_per_slice"]}
+
+
 def evaluate(params, dev, n_eval: int = 64, ks=(1, 2, 3, 5), n_iter_tv: int = 200,
              L: float = None, variants=(("ista", False),), tv_long: int = 1000,
              hybrid_kl=(0,), hybrid_kt=(30, 40, 50, 75, 100), tv_first=(20, 25, 30, 35, 40),
@@ -276,31 +310,8 @@ def evaluate(params, dev, n_eval: int = 64, ks=(1, 2, 3, 5), n_iter_tv: int = 20
         ps = float(np.mean([psnr(x[i].double().cpu().numpy(), truth[i]) for i in range(n_eval)]))
         res["pnp"].append({"variant": f"tv-warm-dual{n_in}", "n_iter": KT, "s_per_slice": t / n_eval,
                            "psnr_mean": ps})
-    plain = [{"variant": "tv", "n_iter": n_iter_tv, "s_per_slice": t_tv / n_eval, "psnr_mean": ps_tv}]
-    is_cold = lambda v: "warm-dual" not in v          # every prox from a zero dual field (the paper's)
-    is_plain = lambda v: v in ("tv", "fbp+tv") or (v.startswith("tv-warm-dual") and "+" not in v)
-    plain += [r for r in res["pnp"] if is_plain(r["variant"])]
-    reach = [r for r in res["pnp"] if r["psnr_mean"] >= ps_tv and not is_plain(r["variant"])]
-    fastest = lambda rows: min((r for r in rows if r["psnr_mean"] >= ps_tv), key=lambda r: r["s_per_slice"],
-                               default=None)
-    tv_cold, tv_any = fastest([r for r in plain if is_cold(r["variant"])]), fastest(plain)
-    ln_cold, ln_any = fastest([r for r in reach if is_cold(r["variant"])]), fastest(reach)
-    if ln_cold and ln_any:
-        # each ratio compares like with like: the paper's prox on both sides,
-        # then warm-started proxes allowed on both sides
-        res["equal_psnr"] = {"target_psnr": ps_tv, "pnp_variant": ln_cold["variant"], "pnp_n_iter": ln_cold["n_iter"],
-                             "pnp_s_per_slice": ln_cold["s_per_slice"], "pnp_psnr": ln_cold["psnr_mean"],
-                             "tv_variant": tv_cold["variant"], "tv_n_iter": tv_cold["n_iter"],
-                             "tv_s_per_slice": tv_cold["s_per_slice"], "tv_psnr": tv_cold["psnr_mean"],
-                             "speedup": tv_cold["s_per_slice"] / ln_cold["s_per_slice"],
-                             "any_pnp_variant": ln_any["variant"], "any_pnp_n_iter": ln_any["n_iter"],
-                             "any_pnp_s_per_slice": ln_any["s_per_slice"], "any_pnp_psnr": ln_any["psnr_mean"],
-                             "any_tv_variant": tv_any["variant"], "any_tv_n_iter": tv_any["n_iter"],
-                             "any_tv_s_per_slice": tv_any["s_per_slice"], "any_tv_psnr": tv_any["psnr_mean"],
-                             "speedup_vs_any_tv": tv_any["s_per_slice"] / ln_any["s_per_slice"],
-                             "speedup_vs_tv_from_zero": (t_tv / n_eval) / ln_cold["s_per_slice"]}
-    else:
-        res["equal_psnr"] = None
+    res["equal_psnr"] = equal_psnr([{"variant": "tv", "n_iter": n_iter_tv, "s_per_slice": t_tv / n_eval,
+                                      "psnr_mean": ps_tv}] + res["pnp"], ps_tv, t_tv / n_eval)
     return res
 
 
