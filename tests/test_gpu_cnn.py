@@ -288,3 +288,26 @@ def test_wait_give_up_is_reported_and_the_next_call_succeeds():
     out = _run(params, z)                       # asserts the status word is clear again
     ref, _, _ = cnn.forward(params, z[0], rounding=True)
     np.testing.assert_array_equal(out[0], ref)
+
+
+def test_learned_prox_study_runs_small(cuda_device):
+    """The benchmark's learned-prox study end to end at a small size (2
+    held-out foams, short solves, one point of every grid): every solve is
+    timed and scored, and the equal-PSNR summary, when a learned solve
+    reaches the target, compares like with like."""
+    import os
+    from paper_1306_1392_b300 import train_prox
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    params = torch.from_numpy(np.load(os.path.join(root, "paper_1306_1392_b300", "weights",
+                                                   "prox_cnn_foam512.npy")).astype(np.float32)).to(cuda_device)
+    r = train_prox.evaluate(params, cuda_device, n_eval=2, ks=(1,), n_iter_tv=20, tv_long=0, hybrid_kt=(10,),
+                            tv_first=(8,), learned_steps=(2,), tv_zero=(15,), tv_warm_dual=((5, 15),),
+                            learned_warm_dual=((5, 8, 2),))
+    variants = {x["variant"] for x in r["pnp"]}
+    assert {"ista", "fbp+tv", "tv+ista2", "tv", "tv-warm-dual5", "tv-warm-dual5+ista2"} <= variants
+    assert all(x["s_per_slice"] > 0 and np.isfinite(x["psnr_mean"]) for x in r["pnp"])
+    e = r["equal_psnr"]
+    if e is not None:
+        assert "warm-dual" not in e["pnp_variant"] and "warm-dual" not in e["tv_variant"]
+        assert e["speedup"] == e["tv_s_per_slice"] / e["pnp_s_per_slice"]
+        assert e["any_tv_s_per_slice"] <= e["tv_s_per_slice"] and e["any_pnp_s_per_slice"] <= e["pnp_s_per_slice"]
