@@ -62,10 +62,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // The K steps on the registers of one thread.  kEdge: the region touches the
-// image border, so cells outside the image keep p = 0 and G = 0, and the
-// forward differences across the last image row / column are multiplied by 0
-// (m1, m2); inside the image every such factor is 1 and is left out, which
-// changes no bits.
+// image border.  Then the forward differences of the last image row / column
+// and of the rows / columns outside the image are multiplied by 0 (m1, m2;
+// inside the image every such factor is 1 and is left out, which changes no
+// bits).  That keeps p1 on the row above the image and p2 on the column left
+// of it at their initial +0 (a zero gradient leaves +0 at +0), the only
+// outside values a cell inside reads (its divergence reads p1 above and p2
+// to the left; its gradient reads G below and to the right, masked at the
+// last row and column), so the cells outside evolve freely without
+// changing a bit inside and need no masks of their own.
 //
 // Rows stream through a step: G of row i is formed from the dual field as it
 // was at the start of the step (row i - 1 is updated only after G of row i
@@ -76,11 +81,10 @@ template <bool kEdge, bool kZsSmem>
 __device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChRW / 2], const float2 (&zl)[kChRows],
                                                      float2 (&a1)[kChRows], float2 (&a2)[kChRows],
                                                      float (*xp)[kChRW], float (*xg)[kChRW], float tau, int steps,
-                                                     unsigned in_mask, const float (&m1)[kChRows],
+                                                     const float (&m1)[kChRows],
                                                      const float2 m2) {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float2 tau2 = make_float2(tau, tau), one2 = make_float2(1.0f, 1.0f);
-    auto in_cell = [&](int i, int j) { return ((in_mask >> (2 * i + j)) & 1u) != 0u; };
     // G of row i (old dual field); u: p1 of the row above
     auto form_g = [&](int i, float2 u) {
         float left = __shfl_up_sync(0xffffffffu, a2[i].y, 1);
@@ -89,12 +93,7 @@ __device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChRW / 
         float2 d = sub2(a1[i], u);
         d = add2(d, a2[i]);
         d = sub2(d, make_float2(left, a2[i].x));
-        float2 G = sub2(d, zz);
-        if (kEdge) {
-            if (!in_cell(i, 0)) G.x = 0.0f;
-            if (!in_cell(i, 1)) G.y = 0.0f;
-        }
-        return G;
+        return sub2(d, zz);
     };
     // update row i from G of rows i and i + 1
     auto update = [&](int i, float2 G, float2 dn) {
@@ -110,19 +109,8 @@ __device__ __forceinline__ void chambolle_steps_regs(const float2 (*zs)[kChRW / 
         const float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
         const float2 n1 = mul2(fma2(tau2, g1, a1[i]), inv);
         const float2 n2 = mul2(fma2(tau2, g2, a2[i]), inv);
-        if (!kEdge) {
-            a1[i] = n1;
-            a2[i] = n2;
-        } else {
-            if (in_cell(i, 0)) {
-                a1[i].x = n1.x;
-                a2[i].x = n2.x;
-            }
-            if (in_cell(i, 1)) {
-                a1[i].y = n1.y;
-                a2[i].y = n2.y;
-            }
-        }
+        a1[i] = n1;
+        a2[i] = n2;
     };
     for (int st = 0; st < steps; ++st) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
@@ -168,7 +156,6 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
             zl[i] = make_float2(v0, v1);
         }
     };
-    unsigned in_mask = 0;                                  // bit 2i + j: cell (i, j) inside the image
     if (!kEdge) {
         const size_t base = (size_t)(ri0 + r0) * nx + (size_t)(rj0 + c0);
         const float *zr = z + base;
@@ -189,13 +176,15 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
             }
         }
         m2 = make_float2(1.0f, 1.0f);
-        in_mask = 0xFFFFu;
     } else {
-        m2 = make_float2((rj0 + c0 + 1 < nx) ? 1.0f : 0.0f, (rj0 + c0 + 2 < nx) ? 1.0f : 0.0f);
+        // 1 on the image's columns / rows that have a forward difference, 0 on
+        // its last one and outside it
+        auto has_diff = [](int g, int n) { return g >= 0 && g + 1 < n ? 1.0f : 0.0f; };
+        m2 = make_float2(has_diff(rj0 + c0, nx), has_diff(rj0 + c0 + 1, nx));
 #pragma unroll
         for (int i = 0; i < kChRows; ++i) {
             const int gi = ri0 + r0 + i;
-            m1[i] = (gi + 1 < ny) ? 1.0f : 0.0f;
+            m1[i] = has_diff(gi, ny);
             float vz[2], v1s[2], v2s[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -203,7 +192,6 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
                 float v1 = 0.0f, v2 = 0.0f;
                 vz[j] = 0.0f;
                 if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
-                    in_mask |= 1u << (2 * i + j);
                     const size_t k = (size_t)gi * nx + gj;
                     vz[j] = __fmul_rn(z[k], inv_lam);
                     if (!first) {
@@ -223,7 +211,7 @@ __device__ __forceinline__ void chambolle_tile_body(const float *__restrict__ z,
     if (w == kChWarps - 1) *reinterpret_cast<float2 *>(&xg[kChWarps][2 * tx]) = make_float2(0.0f, 0.0f);
     *reinterpret_cast<float2 *>(&xp[w + 1][2 * tx]) = a1[kChRows - 1];
     __syncthreads();
-    chambolle_steps_regs<kEdge, kZsSmem>(zs, zl, a1, a2, xp, xg, tau, steps, in_mask, m1, m2);
+    chambolle_steps_regs<kEdge, kZsSmem>(zs, zl, a1, a2, xp, xg, tau, steps, m1, m2);
     // write the central tile: region rows kChK + 1 .. kChRH - kChK, columns kChK + 1 .. kChRW - kChK
     if (xout) {
         const float2 up = *reinterpret_cast<const float2 *>(&xp[w][2 * tx]);   // p1 row above the strip
