@@ -343,7 +343,7 @@ def pyhst_profile_enable(on: bool = True) -> None:
 
 def pyhst_profile_read(kernel: str):
     """(total ms, launches) of the recorded launches of "backproject",
-    "filter" or "project" since the last read."""
+    "filter", "project" or "chambolle" since the last read."""
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(L.lib.pyhst_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
