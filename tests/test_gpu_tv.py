@@ -569,3 +569,25 @@ def test_warm_dual_tightens_the_prox(P, cuda_device):
     print(f"\nmean prox gap, iterations 10-39: cold {g[False][10:].mean():.3e}, warm {g[True][10:].mean():.3e}")
     assert g[True][0] == g[False][0]
     assert g[True][10:].mean() < 0.5 * g[False][10:].mean()
+
+
+def test_batch_projector_pairs_with_odd_groups(P, cuda_device):
+    """The batched projector walks two slices of one geometry per CTA, paired
+    in list order within each geometry: a group of three slices (one pair and
+    one slice paired with itself), interleaved with a group of one, gives
+    every slice the bits of its single-slice solve."""
+    dev = cuda_device
+    specs = [(96, 30, 1), (72, 20, 2), (96, 30, 3), (96, 30, 4)]
+    geos, items = {}, []
+    for n, na, seed in specs:
+        if (n, na) not in geos:
+            fs = acq.foam_slice(n, na, seed=seed, truth=False)
+            geos[(n, na)] = P.Geometry(fs.angles.to(dev), fs.axis.to(dev), n, n, n, fs.pixel_size)
+        g = torch.Generator(device=dev).manual_seed(seed)
+        items.append((geos[(n, na)], torch.rand((na, n), device=dev, generator=g), None))
+    opts = P.TvOptions(beta=2e-3, n_iter=6, n_inner=8, lipschitz=30.0)
+    xs, _, _ = P.pyhst_tv_solve_batch(items, opts)
+    torch.cuda.synchronize()
+    for k, (geo, s, _) in enumerate(items):
+        x1, _, _ = P.pyhst_tv_solve(geo, s[None].contiguous(), opts, energy=False)
+        assert torch.equal(xs[k], x1[0]), k
