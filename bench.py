@@ -830,7 +830,8 @@ def run_ours(args, rank, world, local_rank):
                 "alu": {"achieved": alu, "peak": peak_ops, "unit": "T FP32 lane-ops/s", "frac": alu / peak_ops,
                         "basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz; "
                                  f"{OPS_PER_UPDATE} FP32 ops per update"},
-                "filter_share_of_step": fl_ms / ms}
+                "filter_share_of_step": fl_ms / ms,
+                "peak_check": peak_check(peak_smem, peak_ops)}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
@@ -874,6 +875,21 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": int(bp_n + fl_n + 3 * args.steps),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+
+
+def peak_check(peak_smem_tbs, peak_ops_t):
+    """The derived on-chip peaks against the library's microbenchmarks on
+    this GPU (pyhst_microbench: conflict-free 8-byte shared-memory loads on
+    every SM; independent FP32 fma chains, scalar and paired), run after the
+    timed region."""
+    import paper_1306_1392_b300 as P
+    smem = P.pyhst_microbench("smem_read", iters=8192) / 1e12
+    fma = P.pyhst_microbench("fp32_fma", iters=8192) / 1e12
+    fma2 = P.pyhst_microbench("fp32_fma2", iters=8192) / 1e12
+    return {"smem_read_tbs": smem, "smem_frac_of_derived": smem / peak_smem_tbs,
+            "fp32_fma_tflops": fma, "fp32_fma2_tflops": fma2,
+            "fma_lane_ops_frac_of_derived": fma / 2 / peak_ops_t,
+            "basis": "one launch each of 4 CTAs x 256 threads per SM, event-timed after a warm-up launch"}
 
 
 def run_kernel_case(args):

@@ -304,6 +304,20 @@ int pyhst_beta_scan(const pyhst_geometry *g, const float *sino, const float *bet
 int pyhst_profile_enable(int on);
 int pyhst_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
+/* Measurement support: microbenchmarks of the two on-chip rates that bound
+ * the back-projector and the projector, the denominators of their rooflines.
+ *   kind 0: shared-memory reads, 8-byte loads with no bank conflicts (256
+ *           bytes per warp instruction, two wavefronts); *units = bytes read;
+ *   kind 1: FP32 fma chains, scalar;        *units = flops (an fma is two);
+ *   kind 2: FP32 fma chains, paired f32x2;  *units = flops.
+ * One launch of 4 CTAs x 256 threads per SM, iters loop iterations, on the
+ * stream (asynchronous; time it with events around the call).  sink: DEVICE
+ * float buffer of pyhst_microbench_sink_floats() floats that receives the
+ * loops' results (values without meaning).  PYHST_ERR_INVALID_ARG for another
+ * kind, iters < 1 or NULL pointers. */
+size_t pyhst_microbench_sink_floats(void);
+int pyhst_microbench(int32_t kind, int32_t iters, float *sink, double *units, pyhst_stream_t stream);
+
 /* One slice of a mixed-size batch: its own geometry (n_slices is ignored),
  * sinogram [n_angles][n_bins], iterate x [ny][nx] (in: start if warm_start,
  * out: result), energy [n_iter] and prox duality gaps [n_iter] float64

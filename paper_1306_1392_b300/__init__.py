@@ -349,6 +349,31 @@ def pyhst_profile_read(kernel: str):
     return ms.value, n.value
 
 
+_MICROBENCH = {"smem_read": 0, "fp32_fma": 1, "fp32_fma2": 2}
+
+
+def pyhst_microbench(kind: str, iters: int = 4096, device=None) -> float:
+    """Rate of one microbenchmark launch on ``device`` (default: the current
+    CUDA device): "smem_read" in bytes/s of shared-memory reads, "fp32_fma"
+    and "fp32_fma2" (paired) in flop/s.  One warm-up launch, then one timed
+    with CUDA events on the current stream."""
+    if kind not in _MICROBENCH:
+        raise ValueError(f"kind must be one of {sorted(_MICROBENCH)}")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        sink = torch.empty(int(L.lib.pyhst_microbench_sink_floats()), dtype=torch.float32, device=dev)
+        units = ctypes.c_double()
+        run = lambda: _check(L.lib.pyhst_microbench(_MICROBENCH[kind], iters, _ptr(sink), ctypes.byref(units),  # noqa: E731
+                                                    _stream()))
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        return units.value / (e0.elapsed_time(e1) * 1e-3)
+
+
 def pyhst_backproject(geom: Geometry, sino: torch.Tensor, weight: float, out=None, workspace=None):
     """img = weight * sum_a L(sino_a, t_a); sino [n_slices, n_angles, n_bins]."""
     sino = _stack3(_cuda(sino, "sino", (torch.float32,)), "sino")

@@ -80,6 +80,8 @@ SIGNATURES = [
                                 c_void_p, c_void_p, c_size_t, c_void_p]),
     ("pyhst_profile_enable", c_int32, [c_int32]),
     ("pyhst_profile_read", c_int32, [ctypes.c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
+    ("pyhst_microbench_sink_floats", c_size_t, []),
+    ("pyhst_microbench", c_int32, [c_int32, c_int32, c_void_p, ctypes.POINTER(c_double), c_void_p]),
     ("pyhst_tv_batch_workspace_size", c_size_t, [ctypes.POINTER(pyhst_tv_item), c_int32,
                                                  ctypes.POINTER(pyhst_tv_opts)]),
     ("pyhst_tv_solve_batch", c_int32, [ctypes.POINTER(pyhst_tv_item), c_int32, ctypes.POINTER(pyhst_tv_opts),

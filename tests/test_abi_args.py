@@ -186,3 +186,15 @@ def test_fbp_pre_and_host_argument_checks(L):
         ctypes.byref(g), 0, data, 256, 512, flat, 8, 0, 0, 4096, spc, 1024, wsb, None)
     assert host(spc=0) == E and host(data=None) == E and host(flat=None) == E
     assert host(wsb=16) == L.PYHST_ERR_WORKSPACE
+
+
+def test_microbench_argument_checks(L):
+    """Invalid kinds, iteration counts and pointers are refused before any
+    launch."""
+    units = ctypes.c_double()
+    E = L.PYHST_ERR_INVALID_ARG
+    assert L.lib.pyhst_microbench(3, 10, 256, ctypes.byref(units), None) == E
+    assert L.lib.pyhst_microbench(-1, 10, 256, ctypes.byref(units), None) == E
+    assert L.lib.pyhst_microbench(0, 0, 256, ctypes.byref(units), None) == E
+    assert L.lib.pyhst_microbench(1, 10, None, ctypes.byref(units), None) == E
+    assert L.lib.pyhst_microbench(2, 10, 256, None, None) == E
