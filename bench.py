@@ -879,16 +879,20 @@ def run_ours(args, rank, world, local_rank):
 
 def peak_check(peak_smem_tbs, peak_ops_t):
     """The derived on-chip peaks against the library's microbenchmarks on
-    this GPU (pyhst_microbench: conflict-free 8-byte shared-memory loads on
-    every SM; independent FP32 fma chains, scalar and paired), run after the
-    timed region."""
+    this GPU, run after the timed region (pyhst_microbench on every SM:
+    conflict-free 8-byte shared-memory loads; independent FP32 fma chains,
+    scalar and paired; approximate reciprocal and square-root chains, the
+    MUFU operations of the XU pipe, 16 per clock and SM, that bound the
+    Chambolle steps)."""
     import paper_1306_1392_b300 as P
     smem = P.pyhst_microbench("smem_read", iters=8192) / 1e12
     fma = P.pyhst_microbench("fp32_fma", iters=8192) / 1e12
     fma2 = P.pyhst_microbench("fp32_fma2", iters=8192) / 1e12
+    mufu = P.pyhst_microbench("mufu", iters=4096) / 1e12
     return {"smem_read_tbs": smem, "smem_frac_of_derived": smem / peak_smem_tbs,
             "fp32_fma_tflops": fma, "fp32_fma2_tflops": fma2,
             "fma_lane_ops_frac_of_derived": fma / 2 / peak_ops_t,
+            "mufu_tops": mufu, "mufu_frac_of_derived": mufu / (peak_ops_t / 8),   # 16 of 128 lanes per clock
             "basis": "one launch each of 4 CTAs x 256 threads per SM, event-timed after a warm-up launch"}
 
 

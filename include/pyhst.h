@@ -304,12 +304,15 @@ int pyhst_beta_scan(const pyhst_geometry *g, const float *sino, const float *bet
 int pyhst_profile_enable(int on);
 int pyhst_profile_read(const char *kernel, double *total_ms, int64_t *launches);
 
-/* Measurement support: microbenchmarks of the two on-chip rates that bound
- * the back-projector and the projector, the denominators of their rooflines.
+/* Measurement support: microbenchmarks of the on-chip rates that bound the
+ * back-projector and the projector (shared memory, FP32) and the Chambolle
+ * steps (MUFU), the denominators of their rooflines.
  *   kind 0: shared-memory reads, 8-byte loads with no bank conflicts (256
  *           bytes per warp instruction, two wavefronts); *units = bytes read;
  *   kind 1: FP32 fma chains, scalar;        *units = flops (an fma is two);
- *   kind 2: FP32 fma chains, paired f32x2;  *units = flops.
+ *   kind 2: FP32 fma chains, paired f32x2;  *units = flops;
+ *   kind 3: approximate reciprocal and square-root chains (the XU pipe's
+ *           MUFU operations);               *units = MUFU operations.
  * One launch of 4 CTAs x 256 threads per SM, iters loop iterations, on the
  * stream (asynchronous; time it with events around the call).  sink: DEVICE
  * float buffer of pyhst_microbench_sink_floats() floats that receives the

@@ -349,13 +349,13 @@ def pyhst_profile_read(kernel: str):
     return ms.value, n.value
 
 
-_MICROBENCH = {"smem_read": 0, "fp32_fma": 1, "fp32_fma2": 2}
+_MICROBENCH = {"smem_read": 0, "fp32_fma": 1, "fp32_fma2": 2, "mufu": 3}
 
 
 def pyhst_microbench(kind: str, iters: int = 4096, device=None) -> float:
     """Rate of one microbenchmark launch on ``device`` (default: the current
     CUDA device): "smem_read" in bytes/s of shared-memory reads, "fp32_fma"
-    and "fp32_fma2" (paired) in flop/s.  One warm-up launch, then one timed
+    and "fp32_fma2" (paired) in flop/s, "mufu" in MUFU operations/s.  One warm-up launch, then one timed
     with CUDA events on the current stream."""
     if kind not in _MICROBENCH:
         raise ValueError(f"kind must be one of {sorted(_MICROBENCH)}")

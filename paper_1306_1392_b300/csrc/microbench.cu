@@ -1,7 +1,9 @@
-// Microbenchmarks of the on-chip rates that bound the back-projector and the
-// projector, the denominators of their rooflines: the shared-memory data
-// pipe (both kernels read their staged windows and bands through it; 128
-// bytes per clock and SM) and the FP32 fma rate (128 lanes per clock and SM).
+// Microbenchmarks of the on-chip rates that bound the hot-path kernels, the
+// denominators of their rooflines: the shared-memory data pipe (the
+// back-projector and the projector read their staged windows and bands
+// through it; 128 bytes per clock and SM), the FP32 fma rate (128 lanes per
+// clock and SM) and the MUFU rate of the XU pipe (16 per clock and SM; the
+// Chambolle steps take a square root and a reciprocal per cell).
 // Each kernel runs 4 CTAs of 256 threads on every SM; the caller times a
 // launch on its stream and divides the bytes or operations it reports.
 #include "common.cuh"
@@ -15,6 +17,7 @@ constexpr int kMbEntries = 4096;                       // float2 entries: 32 KB 
 constexpr int kMbLoads = kMbEntries / kMbThreads;      // loads per thread and iteration
 constexpr int kMbChains = 8;                           // independent fma chains per thread
 constexpr int kMbFmaUnroll = 8;                        // fmas per chain and iteration
+constexpr int kMbMufuUnroll = 4;                       // steps per chain and iteration
 
 // Each warp instruction reads 32 consecutive float2 (256 bytes: two
 // wavefronts, no bank conflicts) at a constant offset from the thread's base.
@@ -70,6 +73,30 @@ __global__ void __launch_bounds__(kMbThreads) fma_kernel(float *__restrict__ sin
     sink[blockIdx.x * kMbThreads + threadIdx.x] = s;
 }
 
+// kMbChains independent chains x <- sqrt(1 / x + 1) per thread (approximate
+// reciprocal and square root: two MUFU operations and one add per step; the
+// chains stay near the golden ratio).
+__global__ void __launch_bounds__(kMbThreads) mufu_kernel(float *__restrict__ sink, int iters) {
+    float x[kMbChains];
+#pragma unroll
+    for (int k = 0; k < kMbChains; ++k) x[k] = 1.0f + 1e-3f * (float)threadIdx.x + (float)k;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < kMbMufuUnroll; ++r)
+#pragma unroll
+            for (int k = 0; k < kMbChains; ++k) {
+                float y;
+                asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[k]));
+                y += 1.0f;
+                asm volatile("sqrt.approx.ftz.f32 %0, %1;" : "=f"(x[k]) : "f"(y));
+            }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMbChains; ++k) s += x[k];
+    sink[blockIdx.x * kMbThreads + threadIdx.x] = s;
+}
+
 int mb_ctas(int *ctas) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -90,7 +117,7 @@ extern "C" size_t pyhst_microbench_sink_floats(void) {
 
 extern "C" int pyhst_microbench(int32_t kind, int32_t iters, float *sink, double *units, pyhst_stream_t stream) {
     using namespace pyhst;
-    if (kind < 0 || kind > 2) return fail(PYHST_ERR_INVALID_ARG, "microbenchmark kind %d: need 0, 1 or 2", kind);
+    if (kind < 0 || kind > 3) return fail(PYHST_ERR_INVALID_ARG, "microbenchmark kind %d: need 0 to 3", kind);
     if (iters < 1) return fail(PYHST_ERR_INVALID_ARG, "iters must be >= 1");
     if (!sink || !units) return fail(PYHST_ERR_INVALID_ARG, "sink/units pointer is NULL");
     int ctas = 0;
@@ -101,6 +128,9 @@ extern "C" int pyhst_microbench(int32_t kind, int32_t iters, float *sink, double
     if (kind == 0) {
         smem_read_kernel<<<ctas, kMbThreads, 0, st>>>(sink, iters);
         *units = threads * iters * kMbLoads * sizeof(float2);                 // bytes read from shared memory
+    } else if (kind == 3) {
+        mufu_kernel<<<ctas, kMbThreads, 0, st>>>(sink, iters);
+        *units = threads * iters * kMbMufuUnroll * kMbChains * 2.0;          // MUFU operations
     } else {
         if (kind == 1)
             fma_kernel<false><<<ctas, kMbThreads, 0, st>>>(sink, iters, 0.999999f, 1e-6f);

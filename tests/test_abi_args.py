@@ -193,7 +193,7 @@ def test_microbench_argument_checks(L):
     launch."""
     units = ctypes.c_double()
     E = L.PYHST_ERR_INVALID_ARG
-    assert L.lib.pyhst_microbench(3, 10, 256, ctypes.byref(units), None) == E
+    assert L.lib.pyhst_microbench(4, 10, 256, ctypes.byref(units), None) == E
     assert L.lib.pyhst_microbench(-1, 10, 256, ctypes.byref(units), None) == E
     assert L.lib.pyhst_microbench(0, 0, 256, ctypes.byref(units), None) == E
     assert L.lib.pyhst_microbench(1, 10, None, ctypes.byref(units), None) == E

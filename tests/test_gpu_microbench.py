@@ -34,3 +34,11 @@ def test_fp32_fma_rate(P, cuda_device):
           f"paired {got2 / 1e12:.1f} TFLOP/s")
     assert 0.6 * derived < got <= 1.02 * derived
     assert got2 > 0.6 * derived
+
+
+def test_mufu_rate(P, cuda_device):
+    sms = torch.cuda.get_device_properties(cuda_device).multi_processor_count
+    derived = sms * 16 * SM_MAX_HZ                     # MUFU operations/s: 16 per clock and SM
+    got = P.pyhst_microbench("mufu", iters=2048, device=cuda_device)
+    print(f"\nMUFU {got / 1e12:.2f} T ops/s = {got / derived:.3f} of {derived / 1e12:.2f}")
+    assert 0.6 * derived < got <= 1.02 * derived
